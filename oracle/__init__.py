@@ -1,0 +1,312 @@
+"""FP64 CPU oracle for the PDD interface-node Monte Carlo (arXiv:1705.03666).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference legs import this package.  The product
+library never imports, links or calls it, and it imports nothing from the
+product: it is a ctypes wrapper around ``oracle.c`` (plain C, double
+precision) plus a few plain NumPy/SciPy routines for the deterministic stage of
+the method (the interface interpolation and the subdomain solve, Sec. 2.1).
+
+Each function cites the passage it follows.  Problems are described by the
+plain dictionaries that ``paper_1705_03666_gb300.workloads`` builds (names, not
+library enums), so that no constant is shared with the CUDA path.
+
+Parity status per function (what pins it is listed in the tests):
+  interface_solve    pinned (closed forms, FD brute force, invariants)
+  interface_jacobian pinned (linearity in theta; CRN finite differences)
+  branching_solve    pinned (ODE closed forms, travelling wave, CN solve)
+  spline_interface   pinned (reproduces cubics exactly; library routine)
+  subdomain_solve    pinned (dense solve, exact harmonic at O(h^2))
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+GEOMETRY = {"interval": 0, "unit_square": 1, "l_shape": 2, "unit_cube": 3,
+            "free_space": 4}
+PROBLEM = {"laplace_expcos": 1, "elliptic_manufactured": 2,
+           "poisson_fourier": 3, "bernal_acebron": 4, "poly1d": 5,
+           "torsion": 6, "kpp": 7}
+PSI = {"const": 0, "sigmoid": 1, "travelling": 2}
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("geometry", ctypes.c_int32),
+                ("dim", ctypes.c_int32), ("n_params", ctypes.c_int32),
+                ("params", ctypes.POINTER(ctypes.c_double)),
+                ("sigma", ctypes.c_double)]
+
+
+class _MC(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
+                ("n_paths", ctypes.c_int64), ("max_steps", ctypes.c_int64),
+                ("bridge", ctypes.c_int32), ("n_threads", ctypes.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc into liborc.so (no FMA contraction, so the
+    host results are the same on x86-64 and aarch64)."""
+    if force or not os.path.exists(_LIB) or \
+            os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11",
+                               "-D_GNU_SOURCE", "-shared", "-fPIC", "-o", tmp,
+                               _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P, M = ctypes.POINTER(_Problem), ctypes.POINTER(_MC)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lp = ctypes.POINTER(ctypes.c_int64)
+            ip = ctypes.POINTER(ctypes.c_int32)
+            up = ctypes.POINTER(ctypes.c_uint32)
+            lib.orc_philox4x32_10.argtypes = [up, up, up]
+            lib.orc_philox_stream.argtypes = [ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_int64, up]
+            lib.orc_eval_coeffs.argtypes = [P, dp, dp]
+            lib.orc_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_int64, dp, dp]
+            lib.orc_philox_constants.argtypes = [up]
+            lib.orc_interface_solve.argtypes = [P, dp, ctypes.c_int64, M,
+                                                ctypes.c_int64, dp, dp, lp, dp,
+                                                ip, lp, lp]
+            lib.orc_interface_solve.restype = ctypes.c_int
+            lib.orc_interface_jacobian.argtypes = [P, dp, ctypes.c_int64, M, dp, dp]
+            lib.orc_interface_jacobian.restype = ctypes.c_int
+            lib.orc_jacobian_width.argtypes = [P]
+            lib.orc_jacobian_width.restype = ctypes.c_int
+            lib.orc_branching_solve.argtypes = [P, dp, ctypes.c_int64, M,
+                                                ctypes.c_int64, ctypes.c_int32,
+                                                dp, dp, lp, lp, dp, ip]
+            lib.orc_branching_solve.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a, ct):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _problem(prob: dict):
+    params = np.ascontiguousarray(prob.get("params", np.zeros(0)), dtype=np.float64)
+    if params.size == 0:
+        params = np.zeros(1)
+    s = _Problem(PROBLEM[prob["problem"]], GEOMETRY[prob["geometry"]],
+                 int(prob["dim"]), int(params.size), _ptr(params, ctypes.c_double),
+                 float(prob.get("sigma", 1.0)))
+    return s, params  # keep params alive
+
+
+def _mc(seed, dt, n_paths, max_steps, bridge, n_threads):
+    return _MC(int(seed) & (2**64 - 1), float(dt), int(n_paths), int(max_steps),
+               int(bool(bridge)), int(n_threads or os.cpu_count() or 1))
+
+
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block (Salmon et al., SC'11)."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                          _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def philox_stream(seed, j0, c1, c2, c3, n_blocks):
+    """Blocks Philox((j0+b, c1, c2, c3), key=seed) for b < n_blocks, as u32[n,4]."""
+    lib = _load()
+    out = np.zeros((int(n_blocks), 4), dtype=np.uint32)
+    lib.orc_philox_stream(int(seed), int(j0), int(c1), int(c2), int(c3),
+                          int(n_blocks), _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def normals(seed, n_pairs, c1=0, c2=0, c3=9):
+    """2*n_pairs Box-Muller normals and n_pairs uniforms from Philox blocks
+    (j, c1, c2, c3), j < n_pairs (same maps the estimators use)."""
+    lib = _load()
+    z = np.zeros(2 * int(n_pairs))
+    u = np.zeros(int(n_pairs))
+    lib.orc_normals(int(seed), int(c1), int(c2), int(c3), int(n_pairs),
+                    _ptr(z, ctypes.c_double), _ptr(u, ctypes.c_double))
+    return z, u
+
+
+def philox_constants():
+    """(M0, M1, W0, W1) used by the oracle's Philox."""
+    lib = _load()
+    out = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox_constants(_ptr(out, ctypes.c_uint32))
+    return [int(v) for v in out]
+
+
+def eval_coeffs(prob: dict, x) -> np.ndarray:
+    """(b0, b1, b2, c, f, g) of the problem at x, in the paper's form
+    (1/2) sigma^2 Lap u + b.grad u + c u + f = 0 (Eq. 2.3-2.4)."""
+    lib = _load()
+    P, keep = _problem(prob)
+    xx = np.zeros(3)
+    xx[:len(x)] = x
+    out = np.zeros(6)
+    lib.orc_eval_coeffs(ctypes.byref(P), _ptr(xx, ctypes.c_double),
+                        _ptr(out, ctypes.c_double))
+    return out
+
+
+def interface_solve(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
+                    bridge=True, n_threads=None, path_offset=0,
+                    dump_paths=False):
+    """Monte Carlo estimate of u at each node (Eq. 2.1-2.9, Sec. 2.1 numerics).
+
+    Returns a dict with mean, se, n (per node), total_steps, capped, and, when
+    dump_paths, score[n, N] and steps[n, N] per path."""
+    lib = _load()
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, int(prob["dim"]))
+    n = nodes.shape[0]
+    P, keep = _problem(prob)
+    M = _mc(seed, dt, n_paths, max_steps, bridge, n_threads)
+    mean, se = np.zeros(n), np.zeros(n)
+    npaths = np.zeros(n, dtype=np.int64)
+    score = np.zeros((n, n_paths)) if dump_paths else None
+    steps = np.zeros((n, n_paths), dtype=np.int32) if dump_paths else None
+    ts, tc = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib.orc_interface_solve(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n,
+                                 ctypes.byref(M), int(path_offset),
+                                 _ptr(mean, ctypes.c_double), _ptr(se, ctypes.c_double),
+                                 _ptr(npaths, ctypes.c_int64),
+                                 _ptr(score, ctypes.c_double),
+                                 _ptr(steps, ctypes.c_int32), ctypes.byref(ts),
+                                 ctypes.byref(tc))
+    if rc != 0:
+        raise ValueError("oracle interface_solve: invalid arguments")
+    out = {"mean": mean, "se": se, "n": npaths, "total_steps": ts.value,
+           "capped": tc.value}
+    if dump_paths:
+        out["score"], out["steps"] = score, steps
+    return out
+
+
+def interface_jacobian(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
+                       bridge=True, n_threads=None):
+    """Per-node derivatives of u w.r.t. the family's parameters: theta (linear
+    boundary data, exact pathwise) then phi (drift, likelihood ratio).
+    Poisson-Fourier: [n, 64 + 16]; poly1d: [n, 2 + 2] for (g0, g1, b0, b1).
+    Returns (jac, jac_se)."""
+    lib = _load()
+    d = int(prob["dim"])
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, d)
+    n = nodes.shape[0]
+    P, keep = _problem(prob)
+    W = lib.orc_jacobian_width(ctypes.byref(P))
+    M = _mc(seed, dt, n_paths, max_steps, bridge, n_threads)
+    jac, jse = np.zeros((n, W)), np.zeros((n, W))
+    rc = lib.orc_interface_jacobian(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n,
+                                    ctypes.byref(M), _ptr(jac, ctypes.c_double),
+                                    _ptr(jse, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle interface_jacobian: invalid arguments")
+    return jac, jse
+
+
+def branching_solve(prob: dict, nodes_xt, *, seed, n_trees, max_particles=4096,
+                    max_depth=64, n_threads=None, dump_trees=False):
+    """Branching-diffusion estimate of u(x, t) for Eq. 3.1 / Sec. 3.2."""
+    lib = _load()
+    d = int(prob["dim"])
+    nodes_xt = np.ascontiguousarray(nodes_xt, dtype=np.float64).reshape(-1, d + 1)
+    n = nodes_xt.shape[0]
+    P, keep = _problem(prob)
+    M = _mc(seed, 1.0, n_trees, 1, False, n_threads)
+    mean, se = np.zeros(n), np.zeros(n)
+    kept = np.zeros(n, dtype=np.int64)
+    disc = np.zeros(n, dtype=np.int64)
+    ts = np.zeros((n, n_trees)) if dump_trees else None
+    tg = np.zeros((n, n_trees), dtype=np.int32) if dump_trees else None
+    rc = lib.orc_branching_solve(ctypes.byref(P), _ptr(nodes_xt, ctypes.c_double), n,
+                                 ctypes.byref(M), int(max_particles), int(max_depth),
+                                 _ptr(mean, ctypes.c_double), _ptr(se, ctypes.c_double),
+                                 _ptr(kept, ctypes.c_int64), _ptr(disc, ctypes.c_int64),
+                                 _ptr(ts, ctypes.c_double), _ptr(tg, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("oracle branching_solve: invalid arguments")
+    out = {"mean": mean, "se": se, "n": kept, "discarded": disc}
+    if dump_trees:
+        out["score"], out["segments"] = ts, tg
+    return out
+
+
+# --------------------------------------------------------------------------
+# Deterministic stage (Sec. 2.1: interpolator and subdomain solver)
+# --------------------------------------------------------------------------
+def spline_interface(s_nodes, values, s_query, end0, end1, s0=0.0, s1=1.0):
+    """Cubic spline with not-a-knot end conditions through (s0, end0),
+    (s_k, values_k), (s1, end1), evaluated at s_query (the interpolator that
+    turns nodal values into Dirichlet data on an interface, Sec. 2.1)."""
+    from scipy.interpolate import CubicSpline
+    s = np.concatenate([[s0], np.asarray(s_nodes, dtype=np.float64), [s1]])
+    v = np.concatenate([[end0], np.asarray(values, dtype=np.float64), [end1]])
+    return CubicSpline(s, v, bc_type="not-a-knot")(np.asarray(s_query, dtype=np.float64))
+
+
+def stencil_solve(u_boundary: np.ndarray, h, sigma: float = 1.0) -> np.ndarray:
+    """Exact solution of the 5-point (2-D) or 7-point (3-D) finite-difference
+    Laplace system on a tensor grid: interior values satisfy
+    sum_k (u[i+e_k] - 2 u[i] + u[i-e_k]) / h_k^2 = 0, boundary entries of
+    `u_boundary` are Dirichlet data (the subdomain solver of Sec. 2.1 for the
+    Laplace problem Eq. 1.1).  Direct sparse solve (SciPy), arrays indexed
+    [z][y][x] / [y][x]."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    u = np.array(u_boundary, dtype=np.float64, copy=True)
+    shape = u.shape
+    dim = u.ndim
+    h = np.broadcast_to(np.asarray(h, dtype=np.float64), (dim,))  # h per axis, x first
+    interior = np.zeros(shape, dtype=bool)
+    interior[tuple(slice(1, -1) for _ in range(dim))] = True
+    idx = -np.ones(shape, dtype=np.int64)
+    nint = int(interior.sum())
+    idx[interior] = np.arange(nint)
+    rows, cols, vals = [], [], []
+    rhs = np.zeros(nint)
+    pts = np.argwhere(interior)
+    diag = 0.0
+    for ax in range(dim):
+        diag += 2.0 / h[dim - 1 - ax] ** 2
+    for p in pts:
+        r = idx[tuple(p)]
+        rows.append(r); cols.append(r); vals.append(diag)
+        for ax in range(dim):
+            w = 1.0 / h[dim - 1 - ax] ** 2   # array axis ax <-> coordinate dim-1-ax
+            for sgn in (-1, 1):
+                q = p.copy(); q[ax] += sgn
+                j = idx[tuple(q)]
+                if j >= 0:
+                    rows.append(r); cols.append(j); vals.append(-w)
+                else:
+                    rhs[r] += w * u[tuple(q)]
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(nint, nint))
+    u[interior] = spla.spsolve(A, rhs)
+    return u

@@ -1,0 +1,847 @@
+/*
+ * oracle.c -- plain, slow FP64 CPU oracle for the interface-node Monte Carlo
+ * of Probabilistic Domain Decomposition (Bernal, dos Reis, Smith,
+ * arXiv:1705.03666).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this file; only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg load it.  It shares no code with the CUDA path:
+ * it has its own Philox, its own normal/uniform maps, its own coefficient
+ * formulas, geometry and stepping.  The only thing both sides agree on is the
+ * documented layout of the random streams (which counter feeds which draw),
+ * so that both consume identical 32-bit words.
+ *
+ * Everything is double precision and follows the paper's equations in the
+ * order they are written:
+ *   - Feynman-Kac / Dynkin representation, Eq. 2.1-2.2 (Laplace) and
+ *     Eq. 2.5-2.9 with the elliptic, purely Dirichlet reduction of Sec. 2.2
+ *     (u = E[g(X_tau) Y_tau + Z_tau], dX = b dt + sigma dW,
+ *      dY = c Y dt, dZ = f Y dt);
+ *   - Euler-Maruyama with a boundary test and the boundary-corrected
+ *     (Brownian-bridge, half-space) exit test the paper cites in Sec. 2.1;
+ *   - the Monte Carlo sample mean over independent realisations (Sec. 2);
+ *   - branching Brownian motion for the KPP-type equation Eq. 3.1 with
+ *     exponential lifetimes and offspring law alpha (Sec. 3.1, Assumption
+ *     3.1, the KPP representation of Sec. 3.1.1 and Algorithm 3.1 with
+ *     per-particle lifetimes), including the marked weights alpha_k/q_k of
+ *     Sec. 3.2;
+ *   - the likelihood-ratio derivative of the discrete scheme with respect to
+ *     drift parameters, and the exact pathwise derivative with respect to
+ *     linear boundary-data parameters.
+ *
+ * Readings where the paper is silent (exit point, bridge formula, left-point
+ * quadrature, stream layout, tree ordering) are listed in the design notes and
+ * restated at each function below.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Enumerations (integer values are part of the documented interface).       */
+/* ------------------------------------------------------------------------ */
+enum { ORC_GEOM_INTERVAL = 0, ORC_GEOM_UNIT_SQUARE = 1, ORC_GEOM_L_SHAPE = 2,
+       ORC_GEOM_UNIT_CUBE = 3, ORC_GEOM_FREE_SPACE = 4 };
+enum { ORC_PROB_LAPLACE_EXPCOS = 1, ORC_PROB_ELLIPTIC_MANUFACTURED = 2,
+       ORC_PROB_POISSON_FOURIER = 3, ORC_PROB_BERNAL_ACEBRON = 4,
+       ORC_PROB_POLY1D = 5, ORC_PROB_TORSION = 6, ORC_PROB_KPP = 7 };
+enum { ORC_PSI_CONST = 0, ORC_PSI_SIGMOID = 1, ORC_PSI_TRAVELLING = 2 };
+
+typedef struct {
+  int32_t kind, geometry, dim, n_params;
+  const double *params;
+  double sigma;
+} orc_problem;
+
+typedef struct {
+  uint64_t seed;
+  double dt;
+  int64_t n_paths;
+  int64_t max_steps;
+  int32_t bridge;
+  int32_t n_threads;
+} orc_mc;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, written from the description in Salmon, Moraes, Dror and   */
+/* Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): ten rounds,  */
+/* each multiplying counter words 0 and 2 by two fixed odd constants, taking */
+/* the 64-bit products apart into high and low halves, mixing the high      */
+/* halves with the other two words and the round key by XOR and permuting;  */
+/* the two key words are bumped by the Weyl constants between rounds.       */
+/* ------------------------------------------------------------------------ */
+static const uint32_t PHX_M0 = 0xD2511F53u, PHX_M1 = 0xCD9E8D57u;
+static const uint32_t PHX_W0 = 0x9E3779B9u, PHX_W1 = 0xBB67AE85u;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)PHX_M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)PHX_M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += PHX_W0;
+    k1 += PHX_W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Dump n_blocks consecutive Philox outputs for counters
+ * (j0 + b, c1, c2, c3), b = 0..n_blocks-1, key = (seed lo, seed hi).       */
+void orc_philox_stream(uint64_t seed, uint32_t j0, uint32_t c1, uint32_t c2,
+                       uint32_t c3, int64_t n_blocks, uint32_t *out) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t b = 0; b < n_blocks; ++b) {
+    uint32_t ctr[4] = {j0 + (uint32_t)b, c1, c2, c3};
+    orc_philox4x32_10(ctr, key, out + 4 * b);
+  }
+}
+
+/* Uniform on (0,1): U = (floor(w / 2^9) + 1/2) * 2^-23.  Every value is an
+ * odd multiple of 2^-24, never 0 or 1, and exactly representable in binary32
+ * as well as binary64.                                                     */
+static double unif(uint32_t w) {
+  return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+/* Box-Muller: two uniforms -> two independent standard normals.            */
+static void box_muller(uint32_t a, uint32_t b, double *z0, double *z1) {
+  double r = sqrt(-2.0 * log(unif(a)));
+  double th = 2.0 * M_PI * unif(b);
+  *z0 = r * cos(th);
+  *z1 = r * sin(th);
+}
+
+/* n normals BM(w0, w1) of blocks Philox((j, c1, c2, c3)), j = 0..n/2-1,
+ * and the matching uniforms unif(w2): for statistical checks of the maps.  */
+void orc_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
+                 int64_t n_pairs, double *z, double *u) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t j = 0; j < n_pairs; ++j) {
+    uint32_t ctr[4] = {(uint32_t)j, c1, c2, c3}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    box_muller(w[0], w[1], z + 2 * j, z + 2 * j + 1);
+    if (u) u[j] = unif(w[2]);
+  }
+}
+
+/* The four Philox constants (multipliers, then Weyl key increments).       */
+void orc_philox_constants(uint32_t out[4]) {
+  out[0] = PHX_M0; out[1] = PHX_M1; out[2] = PHX_W0; out[3] = PHX_W1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coefficients of the PDE in the paper's form (Eq. 2.3-2.4, elliptic limit): */
+/*   (1/2) sigma^2 Lap u + b.grad u + c u + f = 0 in Omega,  u = g on dOmega */
+/* c is the paper's c (<= 0), f the paper's f.                               */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 2.10 exact solution and the source that makes it exact (sigma^2 = 2,
+ * so the generator is the full Laplacian as written in Eq. 2.10).          */
+static double ba_u(double x, double y) {
+  return 2.0 * cos(2.0 * (y - 2.0) * x) + sin(3.0 * (x - 2.0) * y) + 3.1;
+}
+static double ba_h(double x, double y) { return cos(x + y) / (1.1 + sin(x + y)); }
+static double ba_c(double x, double y) {
+  return -(x * x + y * y) / (1.1 + sin(x + y));
+}
+static double ba_f(double x, double y) {
+  double A = 2.0 * (y - 2.0) * x, B = 3.0 * (x - 2.0) * y;
+  double ux = -4.0 * (y - 2.0) * sin(A) + 3.0 * y * cos(B);
+  double uy = -4.0 * x * sin(A) + 3.0 * (x - 2.0) * cos(B);
+  double lap = -8.0 * ((y - 2.0) * (y - 2.0) + x * x) * cos(A)
+               - 9.0 * (y * y + (x - 2.0) * (x - 2.0)) * sin(B);
+  /* Lap u + h (u_x + u_y) + c u + f = 0 */
+  return -(lap + ba_h(x, y) * (ux + uy) + ba_c(x, y) * ba_u(x, y));
+}
+
+/* Manufactured 3-D problem: (1/2) Lap u + b.grad u - u = F with
+ * u = sin(pi x) sin(pi y) e^z, b = (0.5 sin 2 pi y, 0.5 cos 2 pi x, 0).
+ * In the paper's form c = -1 and f = -F.                                  */
+static double em_u(const double *x) {
+  return sin(M_PI * x[0]) * sin(M_PI * x[1]) * exp(x[2]);
+}
+static double em_F(const double *x) {
+  double sx = sin(M_PI * x[0]), cx = cos(M_PI * x[0]);
+  double sy = sin(M_PI * x[1]), cy = cos(M_PI * x[1]);
+  double ez = exp(x[2]);
+  double u = sx * sy * ez;
+  double half_lap = 0.5 * (1.0 - 2.0 * M_PI * M_PI) * u;
+  double bgrad = 0.5 * sin(2.0 * M_PI * x[1]) * M_PI * cx * sy * ez
+               + 0.5 * cos(2.0 * M_PI * x[0]) * M_PI * sx * cy * ez;
+  return half_lap + bgrad - u;
+}
+
+static void coef_drift(const orc_problem *P, const double *x, double *b) {
+  b[0] = b[1] = b[2] = 0.0;
+  switch (P->kind) {
+  case ORC_PROB_ELLIPTIC_MANUFACTURED:
+    b[0] = 0.5 * sin(2.0 * M_PI * x[1]);
+    b[1] = 0.5 * cos(2.0 * M_PI * x[0]);
+    break;
+  case ORC_PROB_POISSON_FOURIER: {
+    /* params: theta[64] (theta_mn at m*8+n), then phi[16] */
+    const double *phi = P->params + 64;
+    for (int j = 1; j <= 8; ++j) {
+      b[0] += phi[j - 1] * sin(j * M_PI * x[1]);
+      b[1] += phi[8 + j - 1] * sin(j * M_PI * x[0]);
+    }
+    break;
+  }
+  case ORC_PROB_BERNAL_ACEBRON:
+    b[0] = b[1] = ba_h(x[0], x[1]);
+    break;
+  case ORC_PROB_POLY1D:
+    /* params: b0, b1, c0, f0, f1, g0, g1 */
+    b[0] = P->params[0] + P->params[1] * x[0];
+    break;
+  default:
+    break;
+  }
+}
+
+static double coef_c(const orc_problem *P, const double *x) {
+  switch (P->kind) {
+  case ORC_PROB_ELLIPTIC_MANUFACTURED: return -1.0;
+  case ORC_PROB_BERNAL_ACEBRON: return ba_c(x[0], x[1]);
+  case ORC_PROB_POLY1D: return P->params[2];
+  default: return 0.0;
+  }
+}
+
+static double coef_f(const orc_problem *P, const double *x) {
+  switch (P->kind) {
+  case ORC_PROB_ELLIPTIC_MANUFACTURED: return -em_F(x);
+  case ORC_PROB_POISSON_FOURIER: return 1.0;
+  case ORC_PROB_BERNAL_ACEBRON: return ba_f(x[0], x[1]);
+  case ORC_PROB_POLY1D: return P->params[3] + P->params[4] * x[0];
+  case ORC_PROB_TORSION: return 1.0;
+  default: return 0.0;
+  }
+}
+
+static double coef_g(const orc_problem *P, const double *x) {
+  switch (P->kind) {
+  case ORC_PROB_LAPLACE_EXPCOS: return exp(x[0]) * cos(x[1]);
+  case ORC_PROB_ELLIPTIC_MANUFACTURED: return em_u(x);
+  case ORC_PROB_POISSON_FOURIER: {
+    double s = 0.0;
+    for (int m = 0; m < 8; ++m)
+      for (int n = 0; n < 8; ++n)
+        s += P->params[m * 8 + n] * cos(m * M_PI * x[0]) * cos(n * M_PI * x[1]);
+    return s;
+  }
+  case ORC_PROB_BERNAL_ACEBRON: return ba_u(x[0], x[1]);
+  case ORC_PROB_POLY1D: return (x[0] < 0.5) ? P->params[5] : P->params[6];
+  default: return 0.0;
+  }
+}
+
+/* Coefficients at a point, for tests: out = (b0, b1, b2, c, f, g).        */
+void orc_eval_coeffs(const orc_problem *P, const double *x, double *out) {
+  double b[3];
+  coef_drift(P, x, b);
+  out[0] = b[0]; out[1] = b[1]; out[2] = b[2];
+  out[3] = coef_c(P, x);
+  out[4] = coef_f(P, x);
+  out[5] = coef_g(P, x);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry.  Boxes [0,1]^d and the L-shape [0,1]^2 minus (1/2,1]x(1/2,1].  */
+/* ------------------------------------------------------------------------ */
+static int in_notch(const double *x) { return x[0] > 0.5 && x[1] > 0.5; }
+
+static int inside_closed(int geom, int dim, const double *x) {
+  for (int k = 0; k < dim; ++k)
+    if (x[k] < 0.0 || x[k] > 1.0) return 0;
+  if (geom == ORC_GEOM_L_SHAPE && in_notch(x)) return 0;
+  return 1;
+}
+
+static int inside_open(int geom, int dim, const double *x) {
+  for (int k = 0; k < dim; ++k)
+    if (!(x[k] > 0.0 && x[k] < 1.0)) return 0;
+  if (geom == ORC_GEOM_L_SHAPE && x[0] >= 0.5 && x[1] >= 0.5) return 0;
+  return 1;
+}
+
+/* Faces.  Box: face 2k+s lies on x_k = s, inside is x_k > 0 (s=0) or
+ * x_k < 1 (s=1).  L-shape: the four outer faces of the square plus the two
+ * edges of the notch: face 4 on y = 1/2 (segment x in [1/2,1], inside y<1/2)
+ * and face 5 on x = 1/2 (segment y in [1/2,1], inside x < 1/2).           */
+static int n_faces(int geom, int dim) {
+  return geom == ORC_GEOM_L_SHAPE ? 6 : 2 * dim;
+}
+
+/* Distance from x to the line/plane of face j, measured positive on the
+ * domain side.  For the notch edges this is the distance to the edge segment
+ * (Euclidean), so that points far from the segment see no crossing.       */
+static double face_dist(int geom, int j, const double *x) {
+  if (geom == ORC_GEOM_L_SHAPE && j >= 4) {
+    double a, b; /* along-edge coordinate, normal distance */
+    if (j == 4) { a = x[0]; b = 0.5 - x[1]; }
+    else { a = x[1]; b = 0.5 - x[0]; }
+    if (a >= 0.5) return b;
+    double da = 0.5 - a;
+    return sqrt(da * da + b * b);
+  }
+  int k = j >> 1, s = j & 1;
+  return s ? 1.0 - x[k] : x[k];
+}
+
+/* Project x onto face j (set the face's coordinate to its value).          */
+static void face_project(int geom, int j, double *x) {
+  if (geom == ORC_GEOM_L_SHAPE && j >= 4) {
+    if (j == 4) { x[1] = 0.5; if (x[0] < 0.5) x[0] = 0.5; }
+    else { x[0] = 0.5; if (x[1] < 0.5) x[1] = 0.5; }
+    return;
+  }
+  x[j >> 1] = (double)(j & 1);
+}
+
+/* First point where the straight segment x0 -> x1 leaves the closed domain,
+ * given x0 inside and x1 outside.  The crossed coordinate is set exactly to
+ * the face value.                                                          */
+static void segment_exit(int geom, int dim, const double *x0, const double *x1,
+                         double *xe) {
+  double tbest = 2.0;
+  int kbest = -1;
+  double vbest = 0.0;
+  for (int k = 0; k < dim; ++k) {
+    if (x1[k] < 0.0) {
+      double t = x0[k] / (x0[k] - x1[k]);
+      if (t < tbest) { tbest = t; kbest = k; vbest = 0.0; }
+    } else if (x1[k] > 1.0) {
+      double t = (1.0 - x0[k]) / (x1[k] - x0[k]);
+      if (t < tbest) { tbest = t; kbest = k; vbest = 1.0; }
+    }
+  }
+  if (geom == ORC_GEOM_L_SHAPE) {
+    /* Entry into the open notch {x > 1/2, y > 1/2}: for each axis the
+     * parameter interval where that coordinate exceeds 1/2; the notch is
+     * entered at the later of the two interval starts.                     */
+    double lo = -1e300, hi = 1e300;
+    int kent = -1;
+    for (int k = 0; k < 2; ++k) {
+      double a = x0[k], d = x1[k] - x0[k];
+      double tl, th;
+      if (d == 0.0) {
+        if (a > 0.5) { tl = 0.0; th = 1.0; } else { tl = 2.0; th = -1.0; }
+      } else if (d > 0.0) {
+        tl = (0.5 - a) / d; th = 2.0;
+      } else {
+        tl = -1.0; th = (0.5 - a) / d;
+      }
+      if (tl > lo) { lo = tl; kent = k; }
+      if (th < hi) hi = th;
+    }
+    if (kent >= 0 && lo < hi && lo <= 1.0 && hi > 0.0) {
+      double tent = lo > 0.0 ? lo : 0.0;
+      if (tent < tbest) { tbest = tent; kbest = kent; vbest = 0.5; }
+    }
+  }
+  if (kbest < 0) { /* numerically degenerate: fall back to x1 clamped */
+    for (int k = 0; k < dim; ++k) xe[k] = fmin(1.0, fmax(0.0, x1[k]));
+    return;
+  }
+  for (int k = 0; k < dim; ++k) xe[k] = x0[k] + tbest * (x1[k] - x0[k]);
+  xe[kbest] = vbest;
+  for (int k = 0; k < dim; ++k) xe[k] = fmin(1.0, fmax(0.0, xe[k]));
+}
+
+/* Nearest face of x (used only for paths stopped by the step cap).        */
+static int nearest_face(int geom, int dim, const double *x) {
+  int jb = 0;
+  double db = 1e300;
+  for (int j = 0; j < n_faces(geom, dim); ++j) {
+    double d = face_dist(geom, j, x);
+    if (d < db) { db = d; jb = j; }
+  }
+  return jb;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One diffusion path (Eq. 2.8, Dirichlet/elliptic reduction).              */
+/*                                                                          */
+/* Stream layout: word k of path p of node i is word (k mod 4) of            */
+/*   Philox4x32-10(key = (seed lo, seed hi), ctr = (k div 4, p, i, 0)).      */
+/* Step n draws d normals xi_n and one uniform U_n:                          */
+/*   d = 1: xi = BM(w[4n], w[4n+1]).first,          U = w[4n+2]              */
+/*   d = 2: xi = BM(w[4n], w[4n+1]),                U = w[4n+2]              */
+/*   d = 3, n = 2m:   (a,b)=BM(w[8m],w[8m+1]), (c,e)=BM(w[8m+2],w[8m+3]),    */
+/*                    xi = (a,b,c), U = w[8m+6]                              */
+/*          n = 2m+1: (p,q)=BM(w[8m+4],w[8m+5]), xi = (e,p,q), U = w[8m+7]   */
+/*                                                                          */
+/* Step n -> n+1 (left-point rule for Y and Z, Eq. 2.8):                     */
+/*   X' = X + b(X) dt + sigma sqrt(dt) xi,  Y' = Y exp(c(X) dt),             */
+/*   Z' = Z + f(X) Y dt.                                                    */
+/* Exit at step n+1 if X' is outside the closed domain (exit point = first   */
+/* crossing of the segment X -> X'), else, with the bridge test on, if       */
+/* U < P = 1 - prod_j (1 - p_j), p_j = exp(-2 d_j d'_j / (sigma^2 dt)) over  */
+/* faces with 2 d_j d'_j / (sigma^2 dt) < 18 (exit point = X' projected on   */
+/* the face with the largest p_j).  Score = g(X_tau) Y' + Z'.                */
+/* A node on the boundary exits at step 0 with score g(x).                  */
+/* ------------------------------------------------------------------------ */
+/* Number of linear boundary-data parameters (theta) and drift parameters
+ * (phi) a family exposes to the derivative estimators.                     */
+static int n_theta(const orc_problem *P) {
+  return P->kind == ORC_PROB_POISSON_FOURIER ? 64 : P->kind == ORC_PROB_POLY1D ? 2 : 0;
+}
+static int n_phi(const orc_problem *P) {
+  return P->kind == ORC_PROB_POISSON_FOURIER ? 16 : P->kind == ORC_PROB_POLY1D ? 2 : 0;
+}
+
+/* d b / d phi_j at x (a d-vector).  Poisson-Fourier: b_x = sum_j phi_j
+ * sin(j pi y), b_y = sum_j phi_{8+j} sin(j pi x).  poly1d: b = b0 + b1 x.  */
+static void drift_dphi(const orc_problem *P, int j, const double *x, double *db) {
+  db[0] = db[1] = db[2] = 0.0;
+  if (P->kind == ORC_PROB_POISSON_FOURIER) {
+    if (j < 8) db[0] = sin((j + 1) * M_PI * x[1]);
+    else db[1] = sin((j - 7) * M_PI * x[0]);
+  } else if (P->kind == ORC_PROB_POLY1D) {
+    db[0] = j == 0 ? 1.0 : x[0];
+  }
+}
+
+/* d g / d theta_k at an exit point.  Poisson-Fourier: cos(m pi x) cos(n pi y)
+ * with k = 8m + n.  poly1d: g = g0 at x = 0, g1 at x = 1.                  */
+static double g_dtheta(const orc_problem *P, int k, const double *x) {
+  if (P->kind == ORC_PROB_POISSON_FOURIER)
+    return cos((k / 8) * M_PI * x[0]) * cos((k % 8) * M_PI * x[1]);
+  if (P->kind == ORC_PROB_POLY1D) return (k == 0) == (x[0] < 0.5) ? 1.0 : 0.0;
+  return 0.0;
+}
+
+static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
+                          uint32_t path, const double *x0, double *score,
+                          int32_t *steps, double *xexit, double *Lphi,
+                          double *yexit) {
+  const int dim = P->dim, geom = P->geometry;
+  const double dt = M->dt, sig = P->sigma;
+  const double sdt = sig * sqrt(dt);
+  const uint32_t key[2] = {(uint32_t)M->seed, (uint32_t)(M->seed >> 32)};
+  double X[3] = {0, 0, 0}, Xn[3] = {0, 0, 0}, Y = 1.0, Z = 0.0;
+  for (int k = 0; k < dim; ++k) X[k] = x0[k];
+  const int nphi = n_phi(P);
+  if (Lphi) for (int j = 0; j < nphi; ++j) Lphi[j] = 0.0;
+  if (yexit) *yexit = 1.0;
+  if (!inside_open(geom, dim, X)) {
+    *score = coef_g(P, X);
+    *steps = 0;
+    if (xexit) for (int k = 0; k < 3; ++k) xexit[k] = X[k];
+    return;
+  }
+  uint32_t A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
+  double spare = 0.0;
+  for (int64_t n = 0; n < M->max_steps; ++n) {
+    double xi[3] = {0, 0, 0}, U;
+    if (dim <= 2) {
+      uint32_t ctr[4] = {(uint32_t)n, path, node, 0u};
+      orc_philox4x32_10(ctr, key, A);
+      double z0, z1;
+      box_muller(A[0], A[1], &z0, &z1);
+      xi[0] = z0;
+      if (dim == 2) xi[1] = z1;
+      U = unif(A[2]);
+    } else {
+      uint32_t m = (uint32_t)(n >> 1);
+      if ((n & 1) == 0) {
+        uint32_t ca[4] = {2u * m, path, node, 0u};
+        uint32_t cb[4] = {2u * m + 1u, path, node, 0u};
+        orc_philox4x32_10(ca, key, A);
+        orc_philox4x32_10(cb, key, B);
+        double a, b, c, e;
+        box_muller(A[0], A[1], &a, &b);
+        box_muller(A[2], A[3], &c, &e);
+        xi[0] = a; xi[1] = b; xi[2] = c;
+        spare = e;
+        U = unif(B[2]);
+      } else {
+        double p, q;
+        box_muller(B[0], B[1], &p, &q);
+        xi[0] = spare; xi[1] = p; xi[2] = q;
+        U = unif(B[3]);
+      }
+    }
+    double b[3];
+    coef_drift(P, X, b);
+    double c = coef_c(P, X), f = coef_f(P, X);
+    if (Lphi) {
+      /* Likelihood-ratio increment of the Gaussian transition density of
+       * X' given X:  d/dphi_j log density = xi . db/dphi_j(X) sqrt(dt)/sigma */
+      for (int j = 0; j < nphi; ++j) {
+        double db[3];
+        drift_dphi(P, j, X, db);
+        double dot = 0.0;
+        for (int k = 0; k < dim; ++k) dot += xi[k] * db[k];
+        Lphi[j] += dot * sqrt(dt) / sig;
+      }
+    }
+    double Yn = Y * exp(c * dt);
+    double Zn = Z + f * Y * dt;
+    for (int k = 0; k < dim; ++k) Xn[k] = X[k] + b[k] * dt + sdt * xi[k];
+    if (!inside_closed(geom, dim, Xn)) {
+      double xe[3] = {0, 0, 0};
+      segment_exit(geom, dim, X, Xn, xe);
+      *score = coef_g(P, xe) * Yn + Zn;
+      *steps = (int32_t)(n + 1);
+      if (xexit) for (int k = 0; k < 3; ++k) xexit[k] = xe[k];
+      if (yexit) *yexit = Yn;
+      return;
+    }
+    if (M->bridge) {
+      double keep = 1.0, pbest = -1.0;
+      int jbest = -1;
+      for (int j = 0; j < n_faces(geom, dim); ++j) {
+        double d0 = face_dist(geom, j, X), d1 = face_dist(geom, j, Xn);
+        double a = 2.0 * d0 * d1 / (sig * sig * dt);
+        if (a < 18.0) {
+          double p = exp(-a);
+          keep *= (1.0 - p);
+          if (p > pbest) { pbest = p; jbest = j; }
+        }
+      }
+      double Pexit = 1.0 - keep;
+      if (jbest >= 0 && U < Pexit) {
+        double xe[3] = {Xn[0], Xn[1], Xn[2]};
+        face_project(geom, jbest, xe);
+        *score = coef_g(P, xe) * Yn + Zn;
+        *steps = (int32_t)(n + 1);
+        if (xexit) for (int k = 0; k < 3; ++k) xexit[k] = xe[k];
+        if (yexit) *yexit = Yn;
+        return;
+      }
+    }
+    for (int k = 0; k < dim; ++k) X[k] = Xn[k];
+    Y = Yn;
+    Z = Zn;
+  }
+  /* Step cap reached: score at the projection onto the nearest face.     */
+  double xe[3] = {X[0], X[1], X[2]};
+  face_project(geom, nearest_face(geom, dim, X), xe);
+  *score = coef_g(P, xe) * Y + Z;
+  *steps = (int32_t)(-M->max_steps);
+  if (xexit) for (int k = 0; k < 3; ++k) xexit[k] = xe[k];
+  if (yexit) *yexit = Y;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thread pool over nodes (results do not depend on the thread count).     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int tid, nthreads;
+  void (*fn)(void *ctx, int64_t i);
+  void *ctx;
+  int64_t n;
+} worker_arg;
+
+static void *worker_main(void *p) {
+  worker_arg *w = (worker_arg *)p;
+  for (int64_t i = w->tid; i < w->n; i += w->nthreads) w->fn(w->ctx, i);
+  return NULL;
+}
+
+static void parallel_for(int64_t n, int nthreads, void (*fn)(void *, int64_t),
+                         void *ctx) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 512) nthreads = 512;
+  if (nthreads == 1 || n <= 1) {
+    for (int64_t i = 0; i < n; ++i) fn(ctx, i);
+    return;
+  }
+  pthread_t th[512];
+  worker_arg args[512];
+  for (int t = 0; t < nthreads; ++t) {
+    args[t].tid = t; args[t].nthreads = nthreads; args[t].fn = fn;
+    args[t].ctx = ctx; args[t].n = n;
+    pthread_create(&th[t], NULL, worker_main, &args[t]);
+  }
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interface solve: per node, the sample mean and standard error of the     */
+/* path scores (Welford's running mean / sum of squared deviations).        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_problem *P;
+  const orc_mc *M;
+  const double *nodes;
+  double *mean, *se;
+  int64_t *npaths;
+  double *path_score;
+  int32_t *path_steps;
+  int64_t *steps_per_node, *capped_per_node;
+  int64_t path_offset;
+} solve_ctx;
+
+static void solve_node(void *vp, int64_t i) {
+  solve_ctx *S = (solve_ctx *)vp;
+  const int dim = S->P->dim;
+  const int64_t N = S->M->n_paths;
+  double mean = 0.0, m2 = 0.0;
+  int64_t steps_total = 0, capped = 0;
+  for (int64_t p = 0; p < N; ++p) {
+    double s;
+    int32_t st;
+    simulate_path(S->P, S->M, (uint32_t)i, (uint32_t)(p + S->path_offset),
+                  S->nodes + i * dim, &s, &st, NULL, NULL, NULL);
+    double delta = s - mean;
+    mean += delta / (double)(p + 1);
+    m2 += delta * (s - mean);
+    if (st < 0) { capped++; steps_total += -st; } else steps_total += st;
+    if (S->path_score) S->path_score[i * N + p] = s;
+    if (S->path_steps) S->path_steps[i * N + p] = st;
+  }
+  S->mean[i] = mean;
+  S->se[i] = N > 1 ? sqrt(m2 / (double)(N - 1) / (double)N) : 0.0;
+  if (S->npaths) S->npaths[i] = N;
+  S->steps_per_node[i] = steps_total;
+  S->capped_per_node[i] = capped;
+}
+
+/* Returns 0 on success, 1 on invalid arguments.                            */
+int orc_interface_solve(const orc_problem *P, const double *nodes, int64_t n,
+                        const orc_mc *M, int64_t path_offset, double *mean,
+                        double *se, int64_t *npaths, double *path_score,
+                        int32_t *path_steps, int64_t *total_steps,
+                        int64_t *total_capped) {
+  if (!P || !M || n < 0 || M->n_paths < 1 || M->dt <= 0.0 || P->dim < 1 ||
+      P->dim > 3 || M->max_steps < 1)
+    return 1;
+  int64_t *spn = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int64_t *cpn = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  solve_ctx S = {P, M, nodes, mean, se, npaths, path_score, path_steps,
+                 spn, cpn, path_offset};
+  parallel_for(n, M->n_threads, solve_node, &S);
+  int64_t ts = 0, tc = 0;
+  for (int64_t i = 0; i < n; ++i) { ts += spn[i]; tc += cpn[i]; }
+  if (total_steps) *total_steps = ts;
+  if (total_capped) *total_capped = tc;
+  free(spn);
+  free(cpn);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Derivatives of the node estimate (families with parameters):             */
+/*   J[i][k]         = E[dg/dtheta_k(X_tau) Y_tau]   k < n_theta            */
+/*                     (exact pathwise: the paths do not depend on theta);  */
+/*   J[i][n_theta+j] = E[s * L_j],  L_j = sum over the steps taken of       */
+/*                     xi_n . db/dphi_j(X_n) sqrt(dt)/sigma                 */
+/*                     (likelihood ratio of the discrete Gaussian transition */
+/*                     kernel; the bridge uniform and the exit rule do not  */
+/*                     depend on phi, so this is unbiased for the scheme).  */
+/* Poisson-Fourier: theta = 64 Fourier weights of g, phi = 16 drift weights. */
+/* poly1d: theta = (g0, g1), phi = (b0, b1).                                 */
+/* The paths are the same streams as the interface solve.                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_problem *P;
+  const orc_mc *M;
+  const double *nodes;
+  double *jac;    /* [n][W] */
+  double *jac_se; /* [n][W] or NULL */
+} grad_ctx;
+
+static void grad_node(void *vp, int64_t i) {
+  grad_ctx *G = (grad_ctx *)vp;
+  const orc_problem *P = G->P;
+  const int nt = n_theta(P), np_ = n_phi(P), W = nt + np_;
+  const int64_t N = G->M->n_paths;
+  double mean[80], m2[80];
+  for (int k = 0; k < W; ++k) mean[k] = m2[k] = 0.0;
+  for (int64_t p = 0; p < N; ++p) {
+    double s, xe[3], L[16], v[80], ye;
+    int32_t st;
+    simulate_path(P, G->M, (uint32_t)i, (uint32_t)p, G->nodes + i * P->dim, &s,
+                  &st, xe, L, &ye);
+    for (int k = 0; k < nt; ++k) v[k] = g_dtheta(P, k, xe) * ye;
+    for (int j = 0; j < np_; ++j) v[nt + j] = s * L[j];
+    for (int k = 0; k < W; ++k) {
+      double d = v[k] - mean[k];
+      mean[k] += d / (double)(p + 1);
+      m2[k] += d * (v[k] - mean[k]);
+    }
+  }
+  for (int k = 0; k < W; ++k) {
+    G->jac[i * W + k] = mean[k];
+    if (G->jac_se)
+      G->jac_se[i * W + k] = N > 1 ? sqrt(m2[k] / (double)(N - 1) / (double)N) : 0.0;
+  }
+}
+
+/* Width of a Jacobian row for this family (0: no parameters).             */
+int orc_jacobian_width(const orc_problem *P) { return n_theta(P) + n_phi(P); }
+
+int orc_interface_jacobian(const orc_problem *P, const double *nodes, int64_t n,
+                           const orc_mc *M, double *jac, double *jac_se) {
+  if (!P || !M || M->n_paths < 1 || n_theta(P) + n_phi(P) == 0 ||
+      P->n_params < (P->kind == ORC_PROB_POISSON_FOURIER ? 80 : 7))
+    return 1;
+  grad_ctx G = {P, M, nodes, jac, jac_se};
+  parallel_for(n, M->n_threads, grad_node, &G);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Branching Brownian motion for u_t = (1/2) Lap u + beta (sum_k alpha_k     */
+/* u^k - u), u(.,0) = psi (Eq. 3.1 with L = (1/2) Lap, free space), and its  */
+/* marked form (Sec. 3.2): particles live Exp(beta), move as independent     */
+/* Brownian motions, and at death are replaced by k offspring drawn with     */
+/* probability q_k, the tree weight being multiplied by alpha_k / q_k.  The  */
+/* score of a tree is weight * prod over particles alive at time t of        */
+/* psi(position).  u(x,t) = E[score] (Sec. 3.1.1; Algorithm 3.1 with         */
+/* per-particle lifetimes, which is equal in law to its global clock by the  */
+/* memoryless property).                                                    */
+/*                                                                          */
+/* params: [0] beta, [1] psi kind, [2] psi parameter, [3] K (max offspring  */
+/*         count, <= 7), [4..4+K] q_0..q_K, [5+K..5+2K] alpha_0..alpha_K.   */
+/* Tree order: depth-first; the root has id 0; when a particle branches     */
+/* into k children they get ids next_id .. next_id+k-1 and the lowest id is */
+/* processed first.  Particle id j of tree s at node i draws                */
+/* w = Philox(key, (j, s, i, 1)): lifetime from w0, the Brownian increment   */
+/* from BM(w1, w2), the offspring count from w3.                            */
+/* A tree whose particle count exceeds max_particles or whose pending stack */
+/* exceeds max_depth is discarded and counted (pruning, Algorithm 3.1).     */
+/* ------------------------------------------------------------------------ */
+static double psi_eval(int kind, double prm, const double *x) {
+  switch (kind) {
+  case ORC_PSI_CONST: return prm;
+  case ORC_PSI_SIGMOID: return 1.0 / (1.0 + exp(-prm * x[0]));
+  case ORC_PSI_TRAVELLING: {
+    double e = 1.0 + exp(prm * x[0]);
+    return 1.0 - 1.0 / (e * e);
+  }
+  default: return 0.0;
+  }
+}
+
+typedef struct {
+  const orc_problem *P;
+  const orc_mc *M;
+  const double *nodes_xt; /* [n][dim+1] */
+  int64_t max_particles;
+  int32_t max_depth;
+  double *mean, *se;
+  int64_t *n_kept, *n_discarded;
+  double *tree_score;   /* [n*N] or NULL; NaN for discarded */
+  int32_t *tree_segments; /* [n*N] or NULL; negative for discarded */
+} branch_ctx;
+
+typedef struct { double x[3]; double tb; uint32_t id; } particle;
+
+static void branch_node(void *vp, int64_t i) {
+  branch_ctx *C = (branch_ctx *)vp;
+  const orc_problem *P = C->P;
+  const int dim = P->dim;
+  const double beta = P->params[0];
+  const int psik = (int)P->params[1];
+  const double psip = P->params[2];
+  const int K = (int)P->params[3];
+  const double *q = P->params + 4, *alpha = P->params + 5 + K;
+  const double *xt = C->nodes_xt + i * (dim + 1);
+  const double t = xt[dim];
+  const uint32_t key[2] = {(uint32_t)C->M->seed, (uint32_t)(C->M->seed >> 32)};
+  const int64_t N = C->M->n_paths;
+  particle *stack = (particle *)malloc(sizeof(particle) * (size_t)(C->max_depth + 8));
+  double mean = 0.0, m2 = 0.0;
+  int64_t kept = 0, disc = 0;
+  for (int64_t s = 0; s < N; ++s) {
+    int sp = 0;
+    particle root;
+    for (int k = 0; k < 3; ++k) root.x[k] = k < dim ? xt[k] : 0.0;
+    root.tb = 0.0;
+    root.id = 0;
+    stack[sp++] = root;
+    uint32_t next_id = 1;
+    int64_t particles = 1;
+    int32_t segments = 0;
+    double prod = 1.0, weight = 1.0;
+    int bad = 0;
+    while (sp > 0) {
+      particle cur = stack[--sp];
+      uint32_t ctr[4] = {cur.id, (uint32_t)s, (uint32_t)i, 1u};
+      uint32_t w[4];
+      orc_philox4x32_10(ctr, key, w);
+      segments++;
+      double life = -log(unif(w[0])) / beta;
+      double tend = cur.tb + life;
+      int reaches = tend >= t;
+      if (reaches) tend = t;
+      double z0, z1;
+      box_muller(w[1], w[2], &z0, &z1);
+      double h = sqrt(tend - cur.tb);
+      cur.x[0] += h * z0;
+      if (dim >= 2) cur.x[1] += h * z1;
+      if (reaches) {
+        prod *= psi_eval(psik, psip, cur.x);
+        continue;
+      }
+      double u3 = unif(w[3]), cum = 0.0;
+      int k = K;
+      for (int kk = 0; kk <= K; ++kk) {
+        cum += q[kk];
+        if (u3 < cum) { k = kk; break; }
+      }
+      weight *= alpha[k] / q[k];
+      particles += k;
+      if (particles > C->max_particles || sp + k > C->max_depth) { bad = 1; break; }
+      for (int c = k - 1; c >= 0; --c) {
+        particle ch = cur;
+        ch.tb = tend;
+        ch.id = next_id + (uint32_t)c;
+        stack[sp++] = ch;
+      }
+      next_id += (uint32_t)k;
+    }
+    if (bad) {
+      disc++;
+      if (C->tree_score) C->tree_score[i * N + s] = NAN;
+      if (C->tree_segments) C->tree_segments[i * N + s] = -segments;
+      continue;
+    }
+    double sc = weight * prod;
+    kept++;
+    double d = sc - mean;
+    mean += d / (double)kept;
+    m2 += d * (sc - mean);
+    if (C->tree_score) C->tree_score[i * N + s] = sc;
+    if (C->tree_segments) C->tree_segments[i * N + s] = segments;
+  }
+  free(stack);
+  C->mean[i] = mean;
+  C->se[i] = kept > 1 ? sqrt(m2 / (double)(kept - 1) / (double)kept) : 0.0;
+  C->n_kept[i] = kept;
+  C->n_discarded[i] = disc;
+}
+
+int orc_branching_solve(const orc_problem *P, const double *nodes_xt, int64_t n,
+                        const orc_mc *M, int64_t max_particles,
+                        int32_t max_depth, double *mean, double *se,
+                        int64_t *n_kept, int64_t *n_discarded,
+                        double *tree_score, int32_t *tree_segments) {
+  if (!P || P->kind != ORC_PROB_KPP || P->dim < 1 || P->dim > 2 || !M ||
+      M->n_paths < 1 || P->n_params < 4)
+    return 1;
+  int K = (int)P->params[3];
+  if (K < 0 || K > 7 || P->n_params < 6 + 2 * K || P->params[0] <= 0.0) return 1;
+  branch_ctx C = {P, M, nodes_xt, max_particles, max_depth, mean, se,
+                  n_kept, n_discarded, tree_score, tree_segments};
+  parallel_for(n, M->n_threads, branch_node, &C);
+  return 0;
+}

@@ -1,0 +1,92 @@
+"""Pins for the oracle's random numbers (CPU only).
+
+Philox4x32-10 is the counter-based generator of Salmon, Moraes, Dror and Shaw
+(SC'11).  The oracle's copy is pinned here by what its published design fixes:
+the Weyl key increments are the golden ratio and sqrt(3)-1 scaled by 2^32, the
+multipliers are the published odd 32-bit constants, each output word depends
+on every counter bit (avalanche), distinct counters give distinct blocks, and
+the output is statistically uniform.  The uniform and normal maps are checked
+for range, exactness in binary32 and the moments / KS statistic of N(0,1).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def test_weyl_constants_from_definition(orc):
+    m0, m1, w0, w1 = orc.philox_constants()
+    golden = (math.sqrt(5.0) - 1.0) / 2.0
+    assert w0 == int(golden * 2 ** 32)
+    assert w1 == int((math.sqrt(3.0) - 1.0) * 2 ** 32)
+    # published multipliers: odd, 32-bit
+    assert m0 == 0xD2511F53 and m1 == 0xCD9E8D57
+    assert m0 & 1 and m1 & 1
+
+
+def test_philox_avalanche(orc):
+    rng = np.random.default_rng(1)
+    flips = []
+    for _ in range(200):
+        ctr = rng.integers(0, 2 ** 32, size=4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2 ** 32, size=2, dtype=np.uint64).astype(np.uint32)
+        base = orc.philox4x32_10(ctr, key)
+        bit = int(rng.integers(0, 128))
+        c2 = ctr.copy()
+        c2[bit // 32] ^= np.uint32(1 << (bit % 32))
+        out = orc.philox4x32_10(c2, key)
+        diff = np.bitwise_xor(base, out)
+        flips.append(sum(bin(int(v)).count("1") for v in diff))
+    flips = np.array(flips)
+    # 128 output bits, each should flip with probability 1/2
+    assert abs(flips.mean() - 64.0) < 2.0
+    assert flips.min() > 30
+
+
+def test_philox_key_sensitivity_and_distinct(orc):
+    a = orc.philox_stream(123, 0, 7, 8, 9, 4096)
+    b = orc.philox_stream(124, 0, 7, 8, 9, 4096)
+    assert not np.array_equal(a, b)
+    rows = {tuple(r) for r in a}
+    assert len(rows) == 4096
+
+
+def test_philox_uniformity(orc):
+    w = orc.philox_stream(0x1705036660000000, 0, 1, 2, 0, 1 << 16).ravel()
+    top = (w >> np.uint32(24)).astype(np.int64)
+    counts = np.bincount(top, minlength=256)
+    chi2 = ((counts - counts.mean()) ** 2 / counts.mean()).sum()
+    # chi-square with 255 dof: 99.9% quantile ~ 330
+    assert chi2 < 330
+    bits = np.unpackbits(w.view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.002
+    # lag-1 correlation of successive words as uniforms
+    u = w.astype(np.float64) / 2 ** 32
+    r = np.corrcoef(u[:-1], u[1:])[0, 1]
+    assert abs(r) < 0.01
+
+
+def test_uniform_map_range_and_binary32(orc):
+    _, u = orc.normals(5, 1 << 16)
+    assert u.min() > 0.0 and u.max() < 1.0
+    # odd multiples of 2^-24, exactly representable in binary32
+    k = u * 2 ** 24
+    assert np.all(k == np.round(k)) and np.all(np.round(k) % 2 == 1)
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)
+    assert u.min() >= 2.0 ** -24 and u.max() <= 1.0 - 2.0 ** -24
+
+
+def test_normal_moments_and_ks(orc):
+    z, _ = orc.normals(77, 1 << 18)
+    n = z.size
+    assert abs(z.mean()) < 4.0 / math.sqrt(n)
+    assert abs(z.var() - 1.0) < 4.0 * math.sqrt(2.0 / n)
+    assert abs(stats.skew(z)) < 4.0 * math.sqrt(6.0 / n)
+    assert abs(stats.kurtosis(z)) < 4.0 * math.sqrt(24.0 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # the two halves of a Box-Muller pair are uncorrelated
+    r = np.corrcoef(z[0::2], z[1::2])[0, 1]
+    assert abs(r) < 4.0 / math.sqrt(n / 2)
