@@ -1,0 +1,321 @@
+"""Benchmark: interface-node Monte Carlo of PDD on GB300.
+
+Workload: the 3-D elliptic problem (1/2) Lap u + b.grad u - u = F on the unit
+cube, 4096 interface nodes on the 9 internal planes of a 4x4x4 split, 1e5
+paths per node, dt = 1e-4, FP32 paths with FP64 reductions, Brownian-bridge
+exit test.  One step = one pdd_interface_solve over the whole node set (path
+kernel + per-node reduction + finalize).  Metric: path-steps per second (plus
+nodes per second at the achieved standard error).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pdd|reference]
+
+--impl reference times the FP64 CPU oracle (the slow, obviously correct
+restatement of the method) on the host cores, on a bounded node/path sample of
+the same workload.  Under torchrun each rank runs its own full-size batch (a
+different seed): the units are independent, so there is no collective on the
+data path and the scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1705_03666_gb300 import workloads as W  # noqa: E402
+
+METRIC = "path-steps/sec and interface nodes/sec at fixed std error; % of FP32/INT issue peak"
+UNIT = "path-steps/s"
+WORKLOAD = W.workload(2)
+
+# Algorithmic issue slots per path-step of the FP32 3-D path (one Philox block,
+# 1.5 Box-Muller pairs + 1 bridge uniform, the drift/source of the manufactured
+# problem, the Euler-Maruyama update and the exit tests), each elementary
+# operation or minimal transcendental sequence counted once; derivation in the
+# design notes.
+ALG_SLOTS_PER_PATH_STEP = 114
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def _oracle_sample(prob, nodes, node_ids, n_paths, threads):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.interface_solve(prob, nodes, node_ids=node_ids, seed=WORKLOAD["seed"],
+                               dt=WORKLOAD["dt"], n_paths=n_paths, n_threads=threads)
+    return time.perf_counter() - t0, r["total_steps"]
+
+
+def cpu_baseline(target_s: float = 12.0) -> dict:
+    """The FP64 oracle on the host cores, every 64th node, paths sized so the
+    run takes about target_s seconds."""
+    threads = os.cpu_count() or 1
+    ids = np.arange(0, 4096, 64)
+    nodes = WORKLOAD["nodes"][ids]
+    dt_cal, steps_cal = _oracle_sample(WORKLOAD["prob"], nodes, ids, 200, threads)
+    n_paths = int(max(200, min(20000, 200 * target_s / max(dt_cal, 1e-3))))
+    el, steps = _oracle_sample(WORKLOAD["prob"], nodes, ids, n_paths, threads)
+    return {"value": steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(ids)} nodes (every 64th) x {n_paths} paths, dt=1e-4, FP64, "
+                      f"{steps:.3e} path-steps in {el:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    ids = np.arange(0, 4096, 64)
+    nodes = WORKLOAD["nodes"][ids]
+    dt_cal, _ = _oracle_sample(WORKLOAD["prob"], nodes, ids, 100, threads)
+    n_paths = int(max(100, min(20000, 100 * 6.0 / max(dt_cal, 1e-3))))  # ~6 s per step
+    for _ in range(args.warmup):
+        _oracle_sample(WORKLOAD["prob"], nodes, ids, n_paths, threads)
+    tot_t, tot_steps = 0.0, 0
+    for _ in range(args.steps):
+        el, st = _oracle_sample(WORKLOAD["prob"], nodes, ids, n_paths, threads)
+        tot_t += el
+        tot_steps += st
+    value = tot_steps / tot_t
+    sample = f"{len(ids)} nodes (every 64th) x {n_paths} paths per step, dt=1e-4, FP64"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD["name"], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_pdd(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_03666_gb300 import api
+
+    w = WORKLOAD
+    seed = w["seed"] + 1000 * rank
+    nodes_h = torch.from_numpy(w["nodes"]).pin_memory()
+    nodes = nodes_h.to(dev)
+    n = nodes.shape[0]
+    kw = dict(seed=seed, dt=w["dt"], n_paths=w["n_paths"], precision="fp32", bridge=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    ctx = api.Context(w["prob"], dev)
+    out = (torch.empty(n, dtype=torch.float64, device=dev),
+           torch.empty(n, dtype=torch.float64, device=dev),
+           torch.empty(n, dtype=torch.int64, device=dev))
+    # path-steps per step (deterministic for a given seed): one diagnostic call
+    r = ctx.interface_solve(nodes, diag=True, out=out, **kw)
+    steps_per_call = r["path_steps"]
+    se_median = float(out[1].median())
+    for _ in range(max(0, args.warmup - 1)):
+        ctx.interface_solve(nodes, out=out, **kw)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index)
+    ctx.profile(True)
+    ctx.profile_read()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.4)
+    for i in range(args.steps):
+        flush.zero_()                       # L2 flush between steps (outside the events)
+        evs[i][0].record(stream)
+        ctx.interface_solve(nodes, out=out, **kw)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    kern_ms, kern_launches = ctx.profile_read()
+    ctx.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_total = sum(step_ms) / 1e3
+    t_max = torch.tensor([t_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_total = float(t_max.item())
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # nodes and D2H of (mean, se, n) inside the timed region
+    e2e_steps = max(1, min(args.steps, 2))
+    host_out = [torch.empty(n, dtype=torch.float64).pin_memory(),
+                torch.empty(n, dtype=torch.float64).pin_memory(),
+                torch.empty(n, dtype=torch.int64).pin_memory()]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        d_nodes = nodes_h.to(dev, non_blocking=True)
+        res = ctx.interface_solve(d_nodes, out=out, **kw)
+        host_out[0].copy_(res["mean"], non_blocking=True)
+        host_out[1].copy_(res["se"], non_blocking=True)
+        host_out[2].copy_(res["n"], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    ctx.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    value = world * args.steps * steps_per_call / t_total
+    nodes_per_s = world * args.steps * n / t_total
+    avg_kernel_s = kern_ms / 1e3 / max(1, kern_launches)
+    launches_per_step = kern_launches / max(1, args.steps)
+    alg_per_launch = ALG_SLOTS_PER_PATH_STEP * steps_per_call / max(1.0, launches_per_step)
+    achieved = alg_per_launch / avg_kernel_s / 1e9          # G issue slots / s
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_mhz = clk.get("sm_mhz") or 2070.0
+    peak = n_sm * 4 * 32 * f_mhz * 1e6 / 1e9                # G thread-issue slots / s
+    traffic = _ncu_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "nodes": n, "paths_per_node": w["n_paths"],
+                   "dt": w["dt"], "path_precision": "fp32 paths, fp64 reductions",
+                   "bridge": True, "path_steps_per_step": steps_per_call,
+                   "l2": "flushed between steps (256 MiB write outside the timed events); "
+                         "per-path scratch 1.6 GB > L2",
+                   "parallelism": f"independent batches per GPU x{world}"},
+        "nodes_per_s": nodes_per_s, "median_se": se_median,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "G issue-slots/s", "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "path_kernel<EllipticManufactured, Box<3>, float>",
+                     "alg_slots_per_path_step": ALG_SLOTS_PER_PATH_STEP,
+                     "kernel_ms_avg": avg_kernel_s * 1e3,
+                     "peak_basis": f"{n_sm} SMs x 4 warp-issue/clk x 32 lanes x {f_mhz:.0f} MHz "
+                                   "(median SM clock sampled during the timed region)"},
+        "clocks": clk,
+        "gpu_launches": int(args.steps * (launches_per_step + 2)),
+        "e2e": {"value": world * e2e_steps * steps_per_call / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(nodes_h.numel() * 8),
+                "d2h_bytes_per_step": int(n * 24)},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the path kernel from the committed ncu summary,
+    when one exists for the current kernel (None otherwise)."""
+    p = os.path.join(ROOT, "profiles", "path_kernel_elliptic3d_traffic.json")
+    try:
+        with open(p) as f:
+            return json.load(f).get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pdd", "reference"], default="pdd")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_pdd(args)
+
+
+if __name__ == "__main__":
+    main()

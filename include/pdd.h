@@ -1,0 +1,195 @@
+/*
+ * pdd.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot path
+ * of Probabilistic Domain Decomposition (PDD; Bernal, dos Reis, Smith,
+ * arXiv:1705.03666): Monte Carlo Feynman-Kac estimates of a PDE solution at
+ * interface nodes (stage one of PDD, Sec. 2 and Fig. 2.2), the branching
+ * representation of semilinear problems (Sec. 3), and the deterministic
+ * stage two (interface interpolation and independent subdomain solves,
+ * Sec. 2.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named d_* are DEVICE pointers on the context's device, owned by
+ *    the caller, contiguous, little-endian, row-major.  Host pointers are
+ *    named without the prefix.  Nothing is retained after a call returns.
+ *  - All device work is enqueued on the context's CUDA stream; calls return
+ *    after enqueueing, except where a host-side output (pdd_diag counters,
+ *    iteration counts) is requested, in which case the call synchronises the
+ *    stream before returning.
+ *  - Errors are returned as pdd_status, never thrown, trapped or printed;
+ *    pdd_last_error() gives a one-line description of the last failure on a
+ *    context.  PDD_ECAP is non-fatal: results are valid, but some paths or
+ *    trees hit a cap and were counted (see pdd_diag).
+ *  - Same inputs (seed, nodes, parameters) give bitwise-identical outputs:
+ *    random numbers are counter-based (Philox4x32-10) and every reduction has
+ *    a fixed order.
+ *  - A context is bound to one device and one stream and is not thread-safe.
+ *    The library owns the context and its device scratch (grown on demand,
+ *    freed by pdd_destroy).
+ */
+#ifndef PDD_H
+#define PDD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PDD_API __attribute__((visibility("default")))
+#else
+#define PDD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PDD_OK = 0,
+  PDD_EINVAL = 1,   /* invalid argument (sizes, NaN parameters, null pointers) */
+  PDD_ENOMEM = 2,   /* device allocation failed */
+  PDD_ECUDA = 3,    /* a CUDA runtime call failed (message in pdd_last_error) */
+  PDD_ETIMEOUT = 4, /* a bounded device loop ran out of iterations */
+  PDD_ECAP = 5      /* non-fatal: some paths/trees were capped and counted */
+} pdd_status;
+
+/* Domains.  Boxes are [0,1]^d; the L-shape is [0,1]^2 minus (1/2,1]x(1/2,1]. */
+enum {
+  PDD_GEOM_INTERVAL = 0,
+  PDD_GEOM_UNIT_SQUARE = 1,
+  PDD_GEOM_L_SHAPE = 2,
+  PDD_GEOM_UNIT_CUBE = 3,
+  PDD_GEOM_FREE_SPACE = 4
+};
+
+/* PDE families, written in the paper's elliptic form (Eq. 2.3-2.4 with the
+ * time dependence dropped, Sec. 2.2):
+ *   (1/2) sigma^2 Lap u + b . grad u + c u + f = 0 in Omega, u = g on dOmega.
+ * LAPLACE_EXPCOS          Eq. 1.1 with g = e^x cos y (harmonic), d = 2.
+ * ELLIPTIC_MANUFACTURED   d = 3, b = (0.5 sin 2 pi y, 0.5 cos 2 pi x, 0),
+ *                         c = -1, f chosen so that u = sin(pi x) sin(pi y) e^z,
+ *                         g = u on the boundary.
+ * POISSON_FOURIER         d = 2, f = 1, c = 0, params = theta[64] then phi[16]:
+ *                         g = sum_{m,n<8} theta[8m+n] cos(m pi x) cos(n pi y),
+ *                         b = (sum_j phi[j-1] sin(j pi y),
+ *                              sum_j phi[7+j] sin(j pi x)), j = 1..8.
+ * KPP                     u_t = (1/2) Lap u + beta (sum_k alpha_k u^k - u),
+ *                         u(.,0) = psi, free space, d = 1 or 2 (Eq. 3.1 and
+ *                         Sec. 3.2).  params: [0] beta, [1] psi kind
+ *                         (0 const, 1 sigmoid 1/(1+e^{-a x1}), 2 travelling
+ *                         1-(1+e^{a x1})^-2), [2] psi parameter (c or a),
+ *                         [3] K = max offspring count (<= 7), [4..4+K] q_k
+ *                         (sampling law), [5+K..5+2K] alpha_k.            */
+enum {
+  PDD_PROB_LAPLACE_EXPCOS = 1,
+  PDD_PROB_ELLIPTIC_MANUFACTURED = 2,
+  PDD_PROB_POISSON_FOURIER = 3,
+  PDD_PROB_KPP = 7
+};
+
+/* Arithmetic of the per-step path state. */
+enum { PDD_FP32 = 0, PDD_FP64 = 1 };
+
+typedef struct {
+  int32_t kind;          /* PDD_PROB_* */
+  int32_t geometry;      /* PDD_GEOM_* */
+  int32_t dim;           /* spatial dimension d */
+  int32_t n_params;      /* length of params */
+  const double *params;  /* host; copied by pdd_create */
+  double sigma;          /* generator (1/2) sigma^2 Lap + b . grad (sigma > 0) */
+} pdd_problem;
+
+typedef struct {
+  uint64_t seed;         /* Philox key */
+  double dt;             /* Euler-Maruyama time step (> 0) */
+  int64_t n_paths;       /* paths per node (>= 1) */
+  int64_t max_steps;     /* per-path step cap (>= 1, <= 2^31-1); capped paths
+                            are scored at the nearest face and counted */
+  int64_t path_offset;   /* index of the first path (resume/extend a run) */
+  int32_t precision;     /* PDD_FP32 or PDD_FP64 path arithmetic */
+  int32_t bridge;        /* 1: Brownian-bridge exit test, 0: plain test */
+} pdd_mc_params;
+
+/* Optional diagnostics.  Inputs: the two optional device buffers receive, for
+ * every (node, path) in node-major order, the path's score (FP64) and its exit
+ * step (0 for a node on the boundary, -max_steps for a capped path).
+ * Outputs (host, valid when the call returns): total Euler steps taken and the
+ * number of capped paths/trees. */
+typedef struct {
+  double *d_path_score;    /* [n * n_paths] or NULL */
+  int32_t *d_path_steps;   /* [n * n_paths] or NULL */
+  int64_t path_steps;      /* out */
+  int64_t capped;          /* out */
+} pdd_diag;
+
+typedef struct pdd_ctx pdd_ctx;
+
+/* Create a context for one problem on `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The problem's params
+ * are copied.  Returns PDD_EINVAL for an unknown family, a dimension or
+ * geometry the family does not support, sigma <= 0, a non-finite parameter or
+ * a KPP offspring law that is not a probability distribution (Assumption 3.1
+ * for q; alpha may be any real weights, Sec. 3.2).                          */
+PDD_API pdd_status pdd_create(pdd_ctx **out, const pdd_problem *problem, int device,
+                      void *cuda_stream);
+
+/* Rebind the context to another stream on the same device. */
+PDD_API pdd_status pdd_set_stream(pdd_ctx *ctx, void *cuda_stream);
+
+/* Stage one of PDD for linear problems (Sec. 2, Fig. 2.2): for each node
+ * x_i (d_nodes is [n][dim] FP64, inside the closed domain) estimate
+ * u(x_i) = E[g(X_tau) Y_tau + Z_tau] (Eq. 2.1, 2.5-2.9 in the elliptic
+ * Dirichlet reduction) from n_paths Euler-Maruyama paths with the plain or
+ * Brownian-bridge exit test (the boundary-corrected integrators cited in
+ * Sec. 2.1).  Writes d_mean[n], d_se[n] (standard error of the mean, FP64)
+ * and, if non-NULL, d_npaths[n] (int64).  A node on the boundary gets
+ * u = g(x_i) with zero error.  Path i of node j uses the Philox stream
+ * (key = seed, counter = (block, path_offset + i, j, 0)); the per-step use of
+ * that stream is fixed (2-D: one block per step, normals from words 0-1 by
+ * Box-Muller, bridge uniform from word 2; 3-D: two blocks per pair of steps).
+ * With diag non-NULL the call synchronises and returns PDD_ECAP if some path
+ * hit max_steps, PDD_EINVAL if a node lies outside the closed domain (its
+ * mean is NaN either way).                                                 */
+PDD_API pdd_status pdd_interface_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                               const pdd_mc_params *mc, double *d_mean,
+                               double *d_se, int64_t *d_npaths,
+                               pdd_diag *diag);
+
+/* Launch-shape and memory knobs of the path kernels (no effect on results,
+ * which do not depend on scheduling):
+ *   blocks_per_sm    resident 256-thread blocks per SM for the persistent
+ *                    path kernels (0 = the occupancy maximum);
+ *   wave_max_paths   paths per wave: each wave stores one score per path in
+ *                    the context's scratch (4 or 8 bytes per path) and is
+ *                    reduced before the next starts (0 = default 2^29).     */
+PDD_API pdd_status pdd_set_tuning(pdd_ctx *ctx, int blocks_per_sm,
+                                  int64_t wave_max_paths);
+
+/* Kernel timing.  With profiling on, the library records a CUDA event pair on
+ * the context's stream around every launch of its dominant kernel (the path
+ * kernel of pdd_interface_solve).  pdd_profile_read synchronises the stream and
+ * returns the summed elapsed milliseconds and the launch count since the last
+ * read (or since profiling was switched on), then resets both.            */
+PDD_API pdd_status pdd_profile(pdd_ctx *ctx, int enable);
+PDD_API pdd_status pdd_profile_read(pdd_ctx *ctx, double *kernel_ms,
+                                    int64_t *launches);
+
+/* Philox4x32-10 (Salmon et al., SC'11) blocks for counters
+ * (j0 + b, c1, c2, c3), b < n_blocks, key = (seed low, seed high), written to
+ * d_out[n_blocks][4].  Exposes the generator the estimators consume, so that
+ * its stream can be checked bit for bit.                                    */
+PDD_API pdd_status pdd_philox_stream(pdd_ctx *ctx, uint64_t seed, uint32_t j0,
+                             uint32_t c1, uint32_t c2, uint32_t c3,
+                             int64_t n_blocks, uint32_t *d_out);
+
+/* Release the context and its device scratch (synchronises its stream). */
+PDD_API void pdd_destroy(pdd_ctx *ctx);
+
+/* Static description of a status code. */
+PDD_API const char *pdd_status_string(pdd_status status);
+
+/* One-line description of the last failure on ctx ("" if none). */
+PDD_API const char *pdd_last_error(const pdd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDD_H */

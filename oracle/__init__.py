@@ -87,7 +87,7 @@ def _load():
                                         ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_int64, dp, dp]
             lib.orc_philox_constants.argtypes = [up]
-            lib.orc_interface_solve.argtypes = [P, dp, ctypes.c_int64, M,
+            lib.orc_interface_solve.argtypes = [P, dp, ctypes.c_int64, lp, M,
                                                 ctypes.c_int64, dp, dp, lp, dp,
                                                 ip, lp, lp]
             lib.orc_interface_solve.restype = ctypes.c_int
@@ -178,11 +178,14 @@ def eval_coeffs(prob: dict, x) -> np.ndarray:
 
 def interface_solve(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
                     bridge=True, n_threads=None, path_offset=0,
-                    dump_paths=False):
+                    dump_paths=False, node_ids=None):
     """Monte Carlo estimate of u at each node (Eq. 2.1-2.9, Sec. 2.1 numerics).
 
-    Returns a dict with mean, se, n (per node), total_steps, capped, and, when
-    dump_paths, score[n, N] and steps[n, N] per path."""
+    node_ids (optional) gives the node index each node's random streams use
+    (default: its position), so a subset of a large node list can be
+    recomputed on the same streams.  Returns a dict with mean, se, n (per
+    node), total_steps, capped, and, when dump_paths, score[n, N] and
+    steps[n, N] per path."""
     lib = _load()
     nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, int(prob["dim"]))
     n = nodes.shape[0]
@@ -193,7 +196,11 @@ def interface_solve(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
     score = np.zeros((n, n_paths)) if dump_paths else None
     steps = np.zeros((n, n_paths), dtype=np.int32) if dump_paths else None
     ts, tc = ctypes.c_int64(0), ctypes.c_int64(0)
+    ids = None if node_ids is None else np.ascontiguousarray(node_ids, dtype=np.int64)
+    if ids is not None and ids.shape != (n,):
+        raise ValueError("node_ids must have one entry per node")
     rc = lib.orc_interface_solve(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n,
+                                 _ptr(ids, ctypes.c_int64),
                                  ctypes.byref(M), int(path_offset),
                                  _ptr(mean, ctypes.c_double), _ptr(se, ctypes.c_double),
                                  _ptr(npaths, ctypes.c_int64),

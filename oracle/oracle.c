@@ -587,6 +587,7 @@ typedef struct {
   int32_t *path_steps;
   int64_t *steps_per_node, *capped_per_node;
   int64_t path_offset;
+  const int64_t *node_ids; /* stream node index per node, or NULL (= i) */
 } solve_ctx;
 
 static void solve_node(void *vp, int64_t i) {
@@ -598,7 +599,8 @@ static void solve_node(void *vp, int64_t i) {
   for (int64_t p = 0; p < N; ++p) {
     double s;
     int32_t st;
-    simulate_path(S->P, S->M, (uint32_t)i, (uint32_t)(p + S->path_offset),
+    uint32_t sid = (uint32_t)(S->node_ids ? S->node_ids[i] : i);
+    simulate_path(S->P, S->M, sid, (uint32_t)(p + S->path_offset),
                   S->nodes + i * dim, &s, &st, NULL, NULL, NULL);
     double delta = s - mean;
     mean += delta / (double)(p + 1);
@@ -616,7 +618,8 @@ static void solve_node(void *vp, int64_t i) {
 
 /* Returns 0 on success, 1 on invalid arguments.                            */
 int orc_interface_solve(const orc_problem *P, const double *nodes, int64_t n,
-                        const orc_mc *M, int64_t path_offset, double *mean,
+                        const int64_t *node_ids, const orc_mc *M,
+                        int64_t path_offset, double *mean,
                         double *se, int64_t *npaths, double *path_score,
                         int32_t *path_steps, int64_t *total_steps,
                         int64_t *total_capped) {
@@ -626,7 +629,7 @@ int orc_interface_solve(const orc_problem *P, const double *nodes, int64_t n,
   int64_t *spn = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   int64_t *cpn = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   solve_ctx S = {P, M, nodes, mean, se, npaths, path_score, path_steps,
-                 spn, cpn, path_offset};
+                 spn, cpn, path_offset, node_ids};
   parallel_for(n, M->n_threads, solve_node, &S);
   int64_t ts = 0, tc = 0;
   for (int64_t i = 0; i < n; ++i) { ts += spn[i]; tc += cpn[i]; }

@@ -1,0 +1,101 @@
+"""ctypes view of libpdd.so (include/pdd.h).  Argument marshalling only.
+
+Loading fails loudly when the library is missing or a symbol is absent: there
+is no CPU or Python fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpdd.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "pdd.h")
+
+PDD_OK, PDD_EINVAL, PDD_ENOMEM, PDD_ECUDA, PDD_ETIMEOUT, PDD_ECAP = range(6)
+GEOMETRY = {"interval": 0, "unit_square": 1, "l_shape": 2, "unit_cube": 3, "free_space": 4}
+PROBLEM = {"laplace_expcos": 1, "elliptic_manufactured": 2, "poisson_fourier": 3, "kpp": 7}
+PRECISION = {"fp32": 0, "fp64": 1}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("geometry", ctypes.c_int32),
+                ("dim", ctypes.c_int32), ("n_params", ctypes.c_int32),
+                ("params", ctypes.POINTER(ctypes.c_double)), ("sigma", ctypes.c_double)]
+
+
+class MCParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
+                ("n_paths", ctypes.c_int64), ("max_steps", ctypes.c_int64),
+                ("path_offset", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("bridge", ctypes.c_int32)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("d_path_score", ctypes.c_void_p), ("d_path_steps", ctypes.c_void_p),
+                ("path_steps", ctypes.c_int64), ("capped", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP, _I64, _U32, _U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+_SIGS = {
+    "pdd_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Problem),
+                                  ctypes.c_int, _VP]),
+    "pdd_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "pdd_set_tuning": (ctypes.c_int, [_VP, ctypes.c_int, _I64]),
+    "pdd_interface_solve": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(MCParams), _VP, _VP,
+                                           _VP, ctypes.POINTER(Diag)]),
+    "pdd_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pdd_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "pdd_philox_stream": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _U32, _I64, _VP]),
+    "pdd_destroy": (None, [_VP]),
+    "pdd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pdd_last_error": (ctypes.c_char_p, [_VP]),
+}
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions include/pdd.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"PDD_API\s+[\w\s\*]*?\b(pdd_\w+)\s*\(", text)))
+
+
+def load() -> ctypes.CDLL:
+    """Load libpdd.so (it must have been built, e.g. by __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libpdd.so not found at {LIB_PATH}: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` (no fallback exists)")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)  # AttributeError if the symbol is missing
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class PDDError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"pdd status {status}: {message}")
+        self.status = status
+
+
+def check(status: int, ctx=None, allow=(PDD_OK,)) -> int:
+    if status in allow:
+        return status
+    lib = load()
+    msg = lib.pdd_status_string(status).decode()
+    if ctx:
+        extra = lib.pdd_last_error(ctx).decode()
+        if extra:
+            msg = f"{msg}: {extra}"
+    raise PDDError(status, msg)

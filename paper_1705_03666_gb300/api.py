@@ -1,0 +1,145 @@
+"""Python face of the C ABI: the same operations as include/pdd.h, with torch
+tensors for device memory and torch's current CUDA stream.  Every step of the
+method runs in libpdd.so; this module only checks types and marshals pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_F64, _I64, _I32, _U32 = torch.float64, torch.int64, torch.int32, torch.uint32
+
+
+def _stream_handle(device: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_f64(t, device, shape_last=None) -> torch.Tensor:
+    t = torch.as_tensor(t, dtype=_F64)
+    if t.device != device:
+        t = t.to(device, non_blocking=True)
+    return t.contiguous()
+
+
+class Context:
+    """A library context for one problem (a dict from ``workloads``)."""
+
+    def __init__(self, prob: dict, device: int | torch.device = 0):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        self.prob = prob
+        params = np.ascontiguousarray(prob.get("params", np.zeros(0)), dtype=np.float64)
+        self._params = params
+        p = _lib.Problem(_lib.PROBLEM[prob["problem"]], _lib.GEOMETRY[prob["geometry"]],
+                         int(prob["dim"]), int(params.size),
+                         params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         float(prob.get("sigma", 1.0)))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.pdd_create(ctypes.byref(h), ctypes.byref(p), self.device.index,
+                                     _stream_handle(self.device))
+        _lib.check(st)
+        self.handle = h
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pdd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _bind_stream(self):
+        _lib.check(self.lib.pdd_set_stream(self.handle, _stream_handle(self.device)), self.handle)
+
+    def set_tuning(self, blocks_per_sm: int = 0, wave_max_paths: int = 0):
+        """pdd_set_tuning: launch shape / wave size (results unchanged)."""
+        _lib.check(self.lib.pdd_set_tuning(self.handle, int(blocks_per_sm), int(wave_max_paths)),
+                   self.handle)
+
+    def profile(self, enable: bool = True):
+        """pdd_profile: time every path-kernel launch with CUDA events."""
+        _lib.check(self.lib.pdd_profile(self.handle, int(bool(enable))), self.handle)
+
+    def profile_read(self):
+        """pdd_profile_read: (summed kernel ms, launches) since the last read."""
+        ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.pdd_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n)),
+                       self.handle)
+        return ms.value, n.value
+
+    # ------------------------------------------------------------------
+    def interface_solve(self, nodes, *, seed: int, dt: float, n_paths: int,
+                        max_steps: int = 2**31 - 1, precision: str = "fp32",
+                        bridge: bool = True, path_offset: int = 0,
+                        dump_paths: bool = False, diag: bool = False, out=None) -> dict:
+        """pdd_interface_solve on torch tensors.
+
+        nodes: [n, dim] float64 (CUDA tensor, or a CPU tensor that is copied).
+        Returns mean, se (float64 [n]) and n (int64 [n]) as CUDA tensors; with
+        diag or dump_paths also path_steps / capped (host ints) and, with
+        dump_paths, score [n, n_paths] float64 and steps [n, n_paths] int32."""
+        dim = int(self.prob["dim"])
+        nodes = _dev_f64(nodes, self.device).reshape(-1, dim)
+        n = nodes.shape[0]
+        if out is None:
+            mean = torch.empty(n, dtype=_F64, device=self.device)
+            se = torch.empty(n, dtype=_F64, device=self.device)
+            npaths = torch.empty(n, dtype=_I64, device=self.device)
+        else:
+            mean, se, npaths = out
+        mc = _lib.MCParams(int(seed) & (2**64 - 1), float(dt), int(n_paths), int(max_steps),
+                           int(path_offset), _lib.PRECISION[precision], int(bool(bridge)))
+        res = {"mean": mean, "se": se, "n": npaths}
+        dg = None
+        if diag or dump_paths:
+            dg = _lib.Diag()
+            if dump_paths:
+                res["score"] = torch.empty((n, int(n_paths)), dtype=_F64, device=self.device)
+                res["steps"] = torch.empty((n, int(n_paths)), dtype=_I32, device=self.device)
+                dg.d_path_score = res["score"].data_ptr()
+                dg.d_path_steps = res["steps"].data_ptr()
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_interface_solve(self.handle, nodes.data_ptr(), n, ctypes.byref(mc),
+                                              mean.data_ptr(), se.data_ptr(), npaths.data_ptr(),
+                                              ctypes.byref(dg) if dg is not None else None)
+        res["status"] = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ECAP))
+        if dg is not None:
+            res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
+        return res
+
+    def philox_stream(self, seed: int, j0: int, c1: int, c2: int, c3: int, n_blocks: int):
+        """pdd_philox_stream: uint32 [n_blocks, 4] CUDA tensor."""
+        out = torch.empty((int(n_blocks), 4), dtype=torch.int32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_philox_stream(self.handle, int(seed) & (2**64 - 1), int(j0),
+                                            int(c1), int(c2), int(c3), int(n_blocks),
+                                            out.data_ptr())
+        _lib.check(st, self.handle)
+        return out
+
+
+def interface_solve_host(prob: dict, nodes: np.ndarray, **kw) -> dict:
+    """End-to-end call with host inputs and outputs: pinned host -> device copy
+    of the nodes, pdd_interface_solve, device -> host copy of the results."""
+    with Context(prob) as ctx:
+        h = torch.from_numpy(np.ascontiguousarray(nodes, dtype=np.float64)).pin_memory()
+        r = ctx.interface_solve(h, **kw)
+        return {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in r.items()}

@@ -1,0 +1,185 @@
+// api.cu -- the extern "C" entry points of include/pdd.h: argument checks,
+// context lifetime and dispatch to the kernel translation units.
+#include <cmath>
+#include <new>
+
+#include "ctx.hpp"
+
+using pdd::fail;
+
+namespace {
+
+bool finite_params(const pdd_problem *p) {
+  for (int i = 0; i < p->n_params; ++i)
+    if (!std::isfinite(p->params[i])) return false;
+  return true;
+}
+
+// Family / dimension / geometry combinations that have kernels, and the KPP
+// offspring law check (q a probability distribution, Assumption 3.1; alpha_k
+// real weights with q_k > 0 wherever alpha_k != 0, Sec. 3.2).
+const char *check_problem(const pdd_problem *p) {
+  if (!(p->sigma > 0.0) || !std::isfinite(p->sigma)) return "sigma must be > 0";
+  if (p->n_params < 0 || p->n_params > pdd::kMaxParams) return "n_params out of range";
+  if (p->n_params > 0 && !p->params) return "params is NULL";
+  if (!finite_params(p)) return "non-finite parameter";
+  switch (p->kind) {
+    case PDD_PROB_LAPLACE_EXPCOS:
+      if (p->dim != 2 || p->geometry != PDD_GEOM_UNIT_SQUARE)
+        return "LAPLACE_EXPCOS needs dim 2 on the unit square";
+      return nullptr;
+    case PDD_PROB_ELLIPTIC_MANUFACTURED:
+      if (p->dim != 3 || p->geometry != PDD_GEOM_UNIT_CUBE)
+        return "ELLIPTIC_MANUFACTURED needs dim 3 on the unit cube";
+      return nullptr;
+    case PDD_PROB_POISSON_FOURIER:
+      if (p->dim != 2 || p->geometry != PDD_GEOM_UNIT_SQUARE)
+        return "POISSON_FOURIER needs dim 2 on the unit square";
+      if (p->n_params < 80) return "POISSON_FOURIER needs 80 params (theta[64], phi[16])";
+      return nullptr;
+    case PDD_PROB_KPP: {
+      if (p->dim < 1 || p->dim > 2 || p->geometry != PDD_GEOM_FREE_SPACE)
+        return "KPP needs dim 1 or 2 in free space";
+      if (p->n_params < 4) return "KPP needs params";
+      if (!(p->params[0] > 0.0)) return "KPP beta must be > 0";
+      const double kind = p->params[1];
+      if (kind != 0.0 && kind != 1.0 && kind != 2.0) return "unknown psi kind";
+      const double Kd = p->params[3];
+      if (Kd != std::floor(Kd) || Kd < 0.0 || Kd > 7.0) return "K must be an integer in [0,7]";
+      const int K = static_cast<int>(Kd);
+      if (p->n_params < 6 + 2 * K) return "KPP needs q[0..K] and alpha[0..K]";
+      double sum = 0.0;
+      for (int k = 0; k <= K; ++k) {
+        const double q = p->params[4 + k], al = p->params[5 + K + k];
+        if (q < 0.0) return "q_k must be >= 0";
+        if (al != 0.0 && !(q > 0.0)) return "q_k must be > 0 where alpha_k != 0";
+        sum += q;
+      }
+      if (std::fabs(sum - 1.0) > 1e-12) return "q must sum to 1";
+      return nullptr;
+    }
+    default:
+      return "unknown problem kind";
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+pdd_status pdd_create(pdd_ctx **out, const pdd_problem *problem, int device, void *cuda_stream) {
+  if (!out || !problem) return PDD_EINVAL;
+  *out = nullptr;
+  if (const char *why = check_problem(problem)) {
+    (void)why;
+    return PDD_EINVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return device < 0 ? PDD_EINVAL : PDD_ECUDA;
+  }
+  pdd_ctx *ctx = new (std::nothrow) pdd_ctx();
+  if (!ctx) return PDD_ENOMEM;
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->prob = *problem;
+  ctx->params.assign(problem->params, problem->params + problem->n_params);
+  ctx->prob.params = ctx->params.data();
+  ctx->mc.n_params = problem->n_params;
+  for (int i = 0; i < problem->n_params; ++i) {
+    ctx->mc.prm[i] = problem->params[i];
+    ctx->mc.prmf[i] = static_cast<float>(problem->params[i]);
+  }
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return PDD_ECUDA;
+  }
+  *out = ctx;
+  return PDD_OK;
+}
+
+pdd_status pdd_set_stream(pdd_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return PDD_OK;
+}
+
+pdd_status pdd_set_tuning(pdd_ctx *ctx, int blocks_per_sm, int64_t wave_max_paths) {
+  if (!ctx || blocks_per_sm < 0 || blocks_per_sm > 64 || wave_max_paths < 0) return PDD_EINVAL;
+  ctx->path_blocks_per_sm = blocks_per_sm;
+  ctx->wave_max_paths = wave_max_paths > 0 ? static_cast<uint64_t>(wave_max_paths) : (1ull << 29);
+  return PDD_OK;
+}
+
+pdd_status pdd_interface_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                               const pdd_mc_params *mc, double *d_mean, double *d_se,
+                               int64_t *d_npaths, pdd_diag *diag) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::interface_solve_impl(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
+}
+
+pdd_status pdd_profile(pdd_ctx *ctx, int enable) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->profiling = enable != 0;
+  ctx->prof_used = 0;
+  return PDD_OK;
+}
+
+pdd_status pdd_profile_read(pdd_ctx *ctx, double *kernel_ms, int64_t *launches) {
+  if (!ctx || !kernel_ms || !launches) return PDD_EINVAL;
+  *kernel_ms = 0.0;
+  *launches = 0;
+  cudaSetDevice(ctx->device);
+  PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  for (size_t k = 0; k < ctx->prof_used; ++k) {
+    float ms = 0.0f;
+    PDD_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->prof_events[k].first,
+                                           ctx->prof_events[k].second));
+    *kernel_ms += ms;
+  }
+  *launches = static_cast<int64_t>(ctx->prof_used);
+  ctx->prof_used = 0;
+  return PDD_OK;
+}
+
+pdd_status pdd_philox_stream(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
+                             uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::philox_stream_impl(ctx, seed, j0, c1, c2, c3, n_blocks, d_out);
+}
+
+void pdd_destroy(pdd_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  for (auto &e : ctx->prof_events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  cudaGetLastError();
+  delete ctx;
+}
+
+const char *pdd_status_string(pdd_status s) {
+  switch (s) {
+    case PDD_OK: return "ok";
+    case PDD_EINVAL: return "invalid argument";
+    case PDD_ENOMEM: return "device allocation failed";
+    case PDD_ECUDA: return "CUDA runtime error";
+    case PDD_ETIMEOUT: return "bounded device loop ran out of iterations";
+    case PDD_ECAP: return "some paths or trees were capped (results valid, counted)";
+    default: return "unknown status";
+  }
+}
+
+const char *pdd_last_error(const pdd_ctx *ctx) {
+  return ctx ? ctx->last_error.c_str() : "";
+}
+
+}  // extern "C"

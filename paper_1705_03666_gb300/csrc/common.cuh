@@ -1,0 +1,166 @@
+// common.cuh -- device building blocks shared by the PDD kernels:
+// counter-based random numbers, the uniform / normal / exponential maps, math
+// overloads for the two path precisions, and compensated FP64 sums.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pdd {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Ten rounds; each
+// multiplies counter words 0 and 2 by the two round multipliers, keeps the
+// low halves, and XORs the high halves into words 1 and 3 together with the
+// round key; the key is advanced by the Weyl increments between rounds.  The
+// ten round keys depend only on the seed, so the host precomputes them
+// (RoundKeys) and they reach the kernel as constant-bank parameters.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+struct RoundKeys {
+  uint32_t k[20];  // (k0 + r W0, k1 + r W1) for r = 0..9
+};
+
+inline RoundKeys make_round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0;
+    rk.k[2 * r + 1] = k1;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                          uint32_t c3, const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+    const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ rk.k[2 * r];
+    const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ rk.k[2 * r + 1];
+    c1 = static_cast<uint32_t>(p1);
+    c3 = static_cast<uint32_t>(p0);
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Per-path precomputation: counter words 1 (path) and 2 (node) are fixed for
+// a path and word 3 (stream tag) is a constant, so half of round one depends
+// only on (path, node, tag).
+struct PhiloxPath {
+  uint32_t r0_w0;  // hi(M1 * node) ^ path ^ rk0   (round-one output word 0)
+  uint32_t r0_w1;  // lo(M1 * node)                (round-one output word 1)
+  uint32_t tag;    // counter word 3
+};
+
+__device__ __forceinline__ PhiloxPath philox_path(uint32_t path, uint32_t node,
+                                                  uint32_t tag, const RoundKeys &rk) {
+  const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * node;
+  PhiloxPath pp;
+  pp.r0_w0 = static_cast<uint32_t>(p1 >> 32) ^ path ^ rk.k[0];
+  pp.r0_w1 = static_cast<uint32_t>(p1);
+  pp.tag = tag;
+  return pp;
+}
+
+// Same value as philox10(j, path, node, tag, rk).
+__device__ __forceinline__ uint4 philox10_path(uint32_t j, const PhiloxPath &pp,
+                                               const RoundKeys &rk) {
+  const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * j;
+  uint32_t c0 = pp.r0_w0;
+  uint32_t c1 = pp.r0_w1;
+  uint32_t c2 = static_cast<uint32_t>(p0 >> 32) ^ pp.tag ^ rk.k[1];
+  uint32_t c3 = static_cast<uint32_t>(p0);
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    const uint64_t q0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+    const uint64_t q1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+    const uint32_t n0 = static_cast<uint32_t>(q1 >> 32) ^ c1 ^ rk.k[2 * r];
+    const uint32_t n2 = static_cast<uint32_t>(q0 >> 32) ^ c3 ^ rk.k[2 * r + 1];
+    c1 = static_cast<uint32_t>(q1);
+    c3 = static_cast<uint32_t>(q0);
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// ---------------------------------------------------------------------------
+// Uniform on (0,1): U = (floor(w / 2^9) + 1/2) 2^-23, an odd multiple of 2^-24
+// that binary32 and binary64 both hold exactly (so both path precisions and
+// the FP64 oracle draw the same U from the same word).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float unif_f(uint32_t w) {
+  // 1 + k 2^-23 minus (1 - 2^-24): exact (Sterbenz), = (2k+1) 2^-24
+  return __int_as_float(0x3f800000u | (w >> 9)) - 0.999999940395355224609375f;
+}
+__device__ __forceinline__ double unif_d(uint32_t w) {
+  return static_cast<double>((w >> 9) * 2u + 1u) * 5.9604644775390625e-08;  // 2^-24
+}
+
+template <typename R> __device__ __forceinline__ R unif(uint32_t w);
+template <> __device__ __forceinline__ float unif<float>(uint32_t w) { return unif_f(w); }
+template <> __device__ __forceinline__ double unif<double>(uint32_t w) { return unif_d(w); }
+
+// ---------------------------------------------------------------------------
+// Math overloads (CUDA's own accurate library functions in both precisions).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_cos(float x) { return cosf(x); }
+__device__ __forceinline__ double m_cos(double x) { return cos(x); }
+__device__ __forceinline__ void m_sincospi(float x, float *s, float *c) { sincospif(x, s, c); }
+__device__ __forceinline__ void m_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
+__device__ __forceinline__ float m_sinpi(float x) { return sinpif(x); }
+__device__ __forceinline__ double m_sinpi(double x) { return sinpi(x); }
+
+// Box-Muller: r = sqrt(-2 ln U_a), angle 2 pi U_b; (r cos, r sin).
+template <typename R>
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, R &z0, R &z1) {
+  const R r = m_sqrt(R(-2) * m_log(unif<R>(a)));
+  R s, c;
+  m_sincospi(R(2) * unif<R>(b), &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// ---------------------------------------------------------------------------
+// Compensated (Neumaier) FP64 accumulator and its exact merge.
+// ---------------------------------------------------------------------------
+struct CSum {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double v) {
+    const double t = s + v;
+    c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ void merge(const CSum &o) {
+    add(o.s);
+    c += o.c;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+__device__ __forceinline__ CSum shfl_xor(const CSum &v, int m) {
+  CSum o;
+  o.s = __shfl_xor_sync(kFull, v.s, m);
+  o.c = __shfl_xor_sync(kFull, v.c, m);
+  return o;
+}
+
+}  // namespace pdd

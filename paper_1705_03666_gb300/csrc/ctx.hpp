@@ -1,0 +1,107 @@
+// ctx.hpp -- the library context behind the C ABI (include/pdd.h): device,
+// stream, problem constants and the library-owned device scratch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pdd.h"
+#include "models.cuh"
+
+struct pdd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  pdd_problem prob{};
+  std::vector<double> params;
+  pdd::ModelConst mc{};
+  int num_sms = 0;
+  // library-owned scratch, grown on demand
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  std::string last_error;
+  // launch shape of the path kernels (warps per block fixed at compile time;
+  // resident blocks per SM chosen by the occupancy query or the tuner)
+  int path_blocks_per_sm = 0;
+  uint64_t wave_max_paths = 1ull << 29;
+  // kernel timing (pdd_profile): event pairs recorded around path launches
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  size_t prof_used = 0;
+};
+
+namespace pdd {
+
+inline pdd_status fail(pdd_ctx *ctx, pdd_status st, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return st;
+}
+
+inline pdd_status cuda_fail(pdd_ctx *ctx, cudaError_t e, const char *where) {
+  return fail(ctx, PDD_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define PDD_CUDA_TRY(ctx, expr)                                   \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) return ::pdd::cuda_fail(ctx, _e, #expr); \
+  } while (0)
+
+// Make sure the scratch holds at least `bytes`; grows by reallocation.
+inline pdd_status ensure_scratch(pdd_ctx *ctx, size_t bytes) {
+  if (ctx->scratch_bytes >= bytes) return PDD_OK;
+  if (ctx->scratch) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+  }
+  size_t want = bytes + (bytes >> 3);
+  cudaError_t e = cudaMalloc(&ctx->scratch, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, PDD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", want,
+                cudaGetErrorString(e));
+  }
+  ctx->scratch_bytes = want;
+  return PDD_OK;
+}
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Event pair for the next profiled launch (nullptr events when profiling is
+// off or event creation failed).
+inline std::pair<cudaEvent_t, cudaEvent_t> prof_slot(pdd_ctx *ctx) {
+  if (!ctx->profiling) return {nullptr, nullptr};
+  if (ctx->prof_used == ctx->prof_events.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return {nullptr, nullptr};
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return {nullptr, nullptr};
+    }
+    ctx->prof_events.push_back({a, b});
+  }
+  return ctx->prof_events[ctx->prof_used++];
+}
+
+// Entry points implemented in the kernel translation units.
+pdd_status interface_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                const pdd_mc_params *mc, double *d_mean, double *d_se,
+                                int64_t *d_npaths, pdd_diag *diag);
+pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
+                              uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
+
+}  // namespace pdd

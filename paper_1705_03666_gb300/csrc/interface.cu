@@ -1,0 +1,189 @@
+// interface.cu -- host side of pdd_interface_solve: scratch layout, waves,
+// launches of the path kernel and the per-node reduction, diagnostics.
+#include <cmath>
+#include <cstring>
+
+#include "ctx.hpp"
+#include "path_kernel.cuh"
+#include "reduce.cuh"
+
+namespace pdd {
+
+__global__ void philox_stream_kernel(RoundKeys rk, uint32_t j0, uint32_t c1, uint32_t c2,
+                                     uint32_t c3, int64_t n, uint4 *out) {
+  for (int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; b < n;
+       b += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[b] = philox10(j0 + static_cast<uint32_t>(b), c1, c2, c3, rk);
+}
+
+pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
+                              uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out) {
+  if (n_blocks < 0) return fail(ctx, PDD_EINVAL, "n_blocks < 0");
+  if (n_blocks == 0) return PDD_OK;
+  if (!d_out) return fail(ctx, PDD_EINVAL, "d_out is NULL");
+  if (reinterpret_cast<uintptr_t>(d_out) % 16)
+    return fail(ctx, PDD_EINVAL, "d_out must be 16-byte aligned");
+  PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int grid = static_cast<int>(std::min<int64_t>((n_blocks + 255) / 256, 4096));
+  philox_stream_kernel<<<grid, 256, 0, ctx->stream>>>(make_round_keys(seed), j0, c1, c2, c3,
+                                                       n_blocks, reinterpret_cast<uint4 *>(d_out));
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  return PDD_OK;
+}
+
+// Scratch layout for one interface solve (offsets in bytes):
+//   [0, 256)            counters (4 x u64) and the wave cursor
+//   [256, +n*24)        per-node running (count, mean, M2)
+//   [.., +wave*sizeof R) per-path scores of the current wave
+struct SolveLayout {
+  size_t acc_off, score_off, total;
+};
+
+template <typename R>
+static SolveLayout solve_layout(int64_t n, uint64_t wave) {
+  SolveLayout L;
+  L.acc_off = 256;
+  L.score_off = align_up(L.acc_off + static_cast<size_t>(n) * sizeof(NodeAcc), 256);
+  L.total = align_up(L.score_off + wave * sizeof(R), 256);
+  return L;
+}
+
+static double constant_kill(int kind) {
+  return kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0;
+}
+
+template <class Model, class Geom, typename R>
+static pdd_status run_paths(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                            const pdd_mc_params *mc, double *d_mean, double *d_se,
+                            int64_t *d_npaths, pdd_diag *diag) {
+  const uint64_t N = static_cast<uint64_t>(mc->n_paths);
+  const uint64_t total = static_cast<uint64_t>(n) * N;
+  const uint64_t wave = std::min<uint64_t>(total, ctx->wave_max_paths);
+  const SolveLayout L = solve_layout<R>(n, wave);
+  pdd_status st = ensure_scratch(ctx, L.total);
+  if (st != PDD_OK) return st;
+  char *base = static_cast<char *>(ctx->scratch);
+  auto *counters = reinterpret_cast<unsigned long long *>(base);
+  auto *cursor = counters + 4;
+  auto *acc = reinterpret_cast<NodeAcc *>(base + L.acc_off);
+  R *score = reinterpret_cast<R *>(base + L.score_off);
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, L.score_off, ctx->stream));
+
+  PathArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.nodes = d_nodes;
+  a.n_paths = N;
+  a.path_offset = static_cast<uint64_t>(mc->path_offset);
+  a.cursor = cursor;
+  a.counters = counters;
+  a.score = score;
+  a.rk = make_round_keys(mc->seed);
+  const double sig = ctx->prob.sigma, dt = mc->dt;
+  a.inv_s2dt = 1.0 / (sig * sig * dt);
+  a.dt_d = dt;
+  a.sdt_d = sig * std::sqrt(dt);
+  a.thr_d = 9.0 * sig * sig * dt;
+  a.ecdt_d = std::exp(constant_kill(ctx->prob.kind) * dt);
+  a.dt_f = static_cast<float>(a.dt_d);
+  a.sdt_f = static_cast<float>(a.sdt_d);
+  a.thr_f = static_cast<float>(a.thr_d);
+  a.ecdt_hi = static_cast<float>(a.ecdt_d);
+  a.ecdt_lo = static_cast<float>(a.ecdt_d - static_cast<double>(a.ecdt_hi));
+  a.max_steps = static_cast<int32_t>(mc->max_steps);
+  a.bridge = mc->bridge ? 1 : 0;
+  a.mc = ctx->mc;
+
+  auto kern = path_kernel<Model, Geom, R>;
+  int bps = 0;
+  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlock, 0));
+  if (bps < 1) bps = 1;
+  if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
+  const uint64_t lanes_needed = (wave + 31) / 32;  // warps needed at most
+  uint64_t grid = static_cast<uint64_t>(bps) * ctx->num_sms;
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (lanes_needed * 32 + kPathBlock - 1) / kPathBlock));
+
+  for (uint64_t b0 = 0; b0 < total; b0 += wave) {
+    const uint64_t b1 = std::min(total, b0 + wave);
+    if (b0 > 0) PDD_CUDA_TRY(ctx, cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), ctx->stream));
+    a.begin = b0;
+    a.end = b1;
+    a.steps = (diag && diag->d_path_steps) ? diag->d_path_steps + b0 : nullptr;
+    const auto ev = prof_slot(ctx);
+    if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
+    kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
+    if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
+    const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
+    reduce_wave_kernel<R><<<static_cast<unsigned>(node_hi - node_lo + 1), kReduceBlock, 0,
+                            ctx->stream>>>(score, b0, b1, N, node_lo, acc);
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
+    if (diag && diag->d_path_score) {
+      const uint64_t cnt = b1 - b0;
+      const unsigned g = static_cast<unsigned>(std::min<uint64_t>((cnt + 255) / 256, 8192));
+      widen_scores_kernel<R><<<g, 256, 0, ctx->stream>>>(score, diag->d_path_score + b0, cnt);
+      PDD_CUDA_TRY(ctx, cudaGetLastError());
+    }
+  }
+  finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(
+      acc, n, d_mean, d_se, d_npaths);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+
+  if (diag) {
+    unsigned long long h[4] = {0, 0, 0, 0};
+    PDD_CUDA_TRY(ctx, cudaMemcpyAsync(h, counters, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    diag->path_steps = static_cast<int64_t>(h[0]);
+    diag->capped = static_cast<int64_t>(h[1]);
+    if (h[2]) return fail(ctx, PDD_EINVAL, "%llu paths started outside the closed domain", h[2]);
+    if (h[1]) return fail(ctx, PDD_ECAP, "%llu paths hit max_steps", h[1]);
+  }
+  return PDD_OK;
+}
+
+template <class Model, class Geom>
+static pdd_status run_prec(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                           const pdd_mc_params *mc, double *d_mean, double *d_se,
+                           int64_t *d_npaths, pdd_diag *diag) {
+  if (mc->precision == PDD_FP64)
+    return run_paths<Model, Geom, double>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
+  return run_paths<Model, Geom, float>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
+}
+
+pdd_status interface_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                const pdd_mc_params *mc, double *d_mean, double *d_se,
+                                int64_t *d_npaths, pdd_diag *diag) {
+  if (!mc) return fail(ctx, PDD_EINVAL, "mc is NULL");
+  if (n < 0 || n > (int64_t(1) << 32)) return fail(ctx, PDD_EINVAL, "n out of range");
+  if (mc->n_paths < 1) return fail(ctx, PDD_EINVAL, "n_paths < 1");
+  if (mc->path_offset < 0 || mc->path_offset + mc->n_paths > (int64_t(1) << 32))
+    return fail(ctx, PDD_EINVAL, "path indices must fit in 32 bits");
+  if (!(mc->dt > 0.0) || !std::isfinite(mc->dt)) return fail(ctx, PDD_EINVAL, "dt must be > 0");
+  if (mc->max_steps < 1 || mc->max_steps > 2147483647LL)
+    return fail(ctx, PDD_EINVAL, "max_steps out of range");
+  if (mc->precision != PDD_FP32 && mc->precision != PDD_FP64)
+    return fail(ctx, PDD_EINVAL, "unknown precision");
+  if (ctx->prob.kind == PDD_PROB_KPP)
+    return fail(ctx, PDD_EINVAL, "KPP problems use pdd_branching_solve");
+  if (n > 0 && (!d_nodes || !d_mean || !d_se)) return fail(ctx, PDD_EINVAL, "null buffer");
+  if (static_cast<double>(n) * static_cast<double>(mc->n_paths) > 9.0e18)
+    return fail(ctx, PDD_EINVAL, "too many paths");
+  if (diag) {
+    diag->path_steps = 0;
+    diag->capped = 0;
+  }
+  if (n == 0) return PDD_OK;
+  PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  switch (ctx->prob.kind) {
+    case PDD_PROB_LAPLACE_EXPCOS:
+      return run_prec<LaplaceExpCos, Box<2>>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
+    case PDD_PROB_ELLIPTIC_MANUFACTURED:
+      return run_prec<EllipticManufactured, Box<3>>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths,
+                                                     diag);
+    case PDD_PROB_POISSON_FOURIER:
+      return run_prec<PoissonFourier, Box<2>>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
+    default:
+      return fail(ctx, PDD_EINVAL, "problem kind %d has no path kernel", ctx->prob.kind);
+  }
+}
+
+}  // namespace pdd

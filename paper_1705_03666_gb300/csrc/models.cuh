@@ -1,0 +1,223 @@
+// models.cuh -- PDE families and domains for the path kernels.
+//
+// A model supplies, in the paper's elliptic form (Eq. 2.3-2.4, Sec. 2.2)
+//   (1/2) sigma^2 Lap u + b . grad u + c u + f = 0 in Omega,  u = g on dOmega,
+// the drift b, the killing rate c (the paper's c <= 0), the source f and the
+// boundary data g, evaluated in the path precision R.  A geometry supplies the
+// closed/open membership tests, the faces used by the bridge exit test, the
+// first crossing of a step segment and projections onto faces.
+#pragma once
+
+#include "common.cuh"
+
+namespace pdd {
+
+constexpr int kMaxParams = 96;
+
+// Problem constants passed by value with every launch.
+struct ModelConst {
+  double prm[kMaxParams];
+  float prmf[kMaxParams];
+  int32_t n_params;
+};
+
+template <typename R> __device__ __forceinline__ R prm(const ModelConst &mc, int i);
+template <> __device__ __forceinline__ float prm<float>(const ModelConst &mc, int i) { return mc.prmf[i]; }
+template <> __device__ __forceinline__ double prm<double>(const ModelConst &mc, int i) { return mc.prm[i]; }
+
+// ---------------------------------------------------------------------------
+// Eq. 1.1 with harmonic data g = e^x cos y (no drift, killing or source).
+// ---------------------------------------------------------------------------
+struct LaplaceExpCos {
+  static constexpr int D = 2;
+  static constexpr bool kDrift = false, kSource = false;
+  static constexpr int kKill = 0;  // 0: none, 1: constant, 2: variable
+  template <typename R>
+  __device__ __forceinline__ static void coeffs(const ModelConst &, const R *, R *, R &) {}
+  template <typename R>
+  __device__ __forceinline__ static R g(const ModelConst &, const R *x) {
+    return m_exp(x[0]) * m_cos(x[1]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// (1/2) Lap u + b . grad u - u = F on [0,1]^3, b = (0.5 sin 2 pi y,
+// 0.5 cos 2 pi x, 0), manufactured from u = sin(pi x) sin(pi y) e^z.
+// Paper form: c = -1 (constant), f = -F.  With sx = sin(pi x) etc.:
+//   b0 = sy cy, b1 = 1/2 - sx^2,
+//   F  = ((1 - 2 pi^2)/2 - 1) u + pi (sy cy) cx sy e^z + pi (1/2 - sx^2) sx cy e^z.
+// ---------------------------------------------------------------------------
+struct EllipticManufactured {
+  static constexpr int D = 3;
+  static constexpr bool kDrift = true, kSource = true;
+  static constexpr int kKill = 1;  // c = -1
+  template <typename R>
+  __device__ __forceinline__ static void coeffs(const ModelConst &, const R *x, R *b, R &f) {
+    R sx, cx, sy, cy;
+    m_sincospi(x[0], &sx, &cx);
+    m_sincospi(x[1], &sy, &cy);
+    const R ez = m_exp(x[2]);
+    const R syz = sy * ez;
+    const R b0 = sy * cy;
+    const R b1 = R(0.5) - sx * sx;
+    b[0] = b0;
+    b[1] = b1;
+    b[2] = R(0);
+    constexpr double kPi = 3.14159265358979323846;
+    const R a_u = R(0.5 * (1.0 - 2.0 * kPi * kPi) - 1.0);
+    const R F = a_u * sx * syz + R(kPi) * (b0 * cx * syz + b1 * sx * cy * ez);
+    f = -F;
+  }
+  template <typename R>
+  __device__ __forceinline__ static R g(const ModelConst &, const R *x) {
+    return m_sinpi(x[0]) * m_sinpi(x[1]) * m_exp(x[2]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Poisson problem (1/2) Lap u + b_phi . grad u = -1 (paper's f = 1) with
+// Fourier boundary data g_theta.  params = theta[64] (theta[8m+n]) then phi[16].
+//   g  = sum_{m,n<8} theta_mn cos(m pi x) cos(n pi y),
+//   b  = (sum_{j=1..8} phi_j sin(j pi y), sum_{j=1..8} phi_{8+j} sin(j pi x)).
+// sin(j pi t) and cos(m pi t) come from the Chebyshev recurrences
+//   s_{j+1} = 2 cos(pi t) s_j - s_{j-1},  c_{m+1} = 2 cos(pi t) c_m - c_{m-1}.
+// ---------------------------------------------------------------------------
+struct PoissonFourier {
+  static constexpr int D = 2;
+  static constexpr bool kDrift = true, kSource = true;
+  static constexpr int kKill = 0;
+  template <typename R>
+  __device__ __forceinline__ static void sines(R t, R *s) {  // s[j-1] = sin(j pi t)
+    R s1, c1;
+    m_sincospi(t, &s1, &c1);
+    const R two_c = R(2) * c1;
+    s[0] = s1;
+    s[1] = two_c * s1;
+#pragma unroll
+    for (int j = 2; j < 8; ++j) s[j] = two_c * s[j - 1] - s[j - 2];
+  }
+  template <typename R>
+  __device__ __forceinline__ static void cosines(R t, R *c) {  // c[m] = cos(m pi t)
+    R s1, c1;
+    m_sincospi(t, &s1, &c1);
+    const R two_c = R(2) * c1;
+    c[0] = R(1);
+    c[1] = c1;
+#pragma unroll
+    for (int m = 2; m < 8; ++m) c[m] = two_c * c[m - 1] - c[m - 2];
+  }
+  template <typename R>
+  __device__ __forceinline__ static void coeffs(const ModelConst &mc, const R *x, R *b, R &f) {
+    R sy[8], sx[8];
+    sines(x[1], sy);
+    sines(x[0], sx);
+    R b0 = R(0), b1 = R(0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      b0 += prm<R>(mc, 64 + j) * sy[j];
+      b1 += prm<R>(mc, 72 + j) * sx[j];
+    }
+    b[0] = b0;
+    b[1] = b1;
+    f = R(1);
+  }
+  template <typename R>
+  __device__ __forceinline__ static R g(const ModelConst &mc, const R *x) {
+    R cx[8], cy[8];
+    cosines(x[0], cx);
+    cosines(x[1], cy);
+    R s = R(0);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      R row = R(0);
+#pragma unroll
+      for (int n = 0; n < 8; ++n) row += prm<R>(mc, 8 * m + n) * cy[n];
+      s += cx[m] * row;
+    }
+    return s;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Geometry: the box [0,1]^D.  Face j = 2k + s lies on x_k = s.
+// ---------------------------------------------------------------------------
+template <int D>
+struct Box {
+  static constexpr int kFaces = 2 * D;
+
+  template <typename R>
+  __device__ __forceinline__ static bool inside_closed(const R *x) {
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) in = in && (x[k] >= R(0)) && (x[k] <= R(1));
+    return in;
+  }
+  template <typename R>
+  __device__ __forceinline__ static bool inside_open(const R *x) {
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) in = in && (x[k] > R(0)) && (x[k] < R(1));
+    return in;
+  }
+  // Distance to the plane of face j, positive on the domain side.
+  template <typename R>
+  __device__ __forceinline__ static R face_dist(int j, const R *x) {
+    const R v = x[j >> 1];
+    return (j & 1) ? R(1) - v : v;
+  }
+  // Cheap filter: is any face close enough that 2 d d' < 18 sigma^2 dt could
+  // hold?  (thr = 9 sigma^2 dt.)
+  template <typename R>
+  __device__ __forceinline__ static bool near_any(const R *x0, const R *x1, R thr) {
+    bool nr = false;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      nr = nr || (x0[k] * x1[k] < thr) || ((R(1) - x0[k]) * (R(1) - x1[k]) < thr);
+    }
+    return nr;
+  }
+  template <typename R>
+  __device__ __forceinline__ static void project(int j, R *x) {
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k == (j >> 1)) x[k] = R(j & 1);
+  }
+  // First crossing of the segment x0 -> x1 (x0 inside, x1 outside): the
+  // smallest crossing parameter over the violated coordinates; the crossed
+  // coordinate is set exactly to its face and the rest clamped to [0,1].
+  template <typename R>
+  __device__ __forceinline__ static void segment_exit(const R *x0, const R *x1, R *xe) {
+    R tb = R(2);
+    int kb = 0;
+    R vb = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (x1[k] < R(0)) {
+        const R t = x0[k] / (x0[k] - x1[k]);
+        if (t < tb) { tb = t; kb = k; vb = R(0); }
+      } else if (x1[k] > R(1)) {
+        const R t = (R(1) - x0[k]) / (x1[k] - x0[k]);
+        if (t < tb) { tb = t; kb = k; vb = R(1); }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      R v = x0[k] + tb * (x1[k] - x0[k]);
+      v = (k == kb) ? vb : v;
+      xe[k] = fmin(R(1), fmax(R(0), v));
+    }
+  }
+  template <typename R>
+  __device__ __forceinline__ static int nearest_face(const R *x) {
+    int jb = 0;
+    R db = face_dist<R>(0, x);
+#pragma unroll
+    for (int j = 1; j < kFaces; ++j) {
+      const R d = face_dist<R>(j, x);
+      if (d < db) { db = d; jb = j; }
+    }
+    return jb;
+  }
+};
+
+}  // namespace pdd

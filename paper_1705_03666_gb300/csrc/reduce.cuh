@@ -1,0 +1,89 @@
+// reduce.cuh -- per-node sample mean / standard error of per-path scores
+// (the Monte Carlo estimator of Sec. 2: the mean over independent
+// realisations, with its statistical error).
+//
+// Each wave of the path index space is reduced by one block per node: the
+// block sums the shifted scores (s - K, with K the node's first score in the
+// wave) and their squares with compensated FP64 accumulators, combines the
+// threads in a fixed tree (warp shuffles, then shared memory), and merges the
+// wave's (count, mean, M2) into the node's running triple with Chan's formula.
+// Waves are processed in order, so the result is deterministic.
+#pragma once
+
+#include "common.cuh"
+
+namespace pdd {
+
+constexpr int kReduceBlock = 256;
+
+struct NodeAcc {  // running (count, mean, M2) per node, FP64
+  double n, mean, m2;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kReduceBlock)
+reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
+                   uint64_t n_paths, uint64_t node_lo, NodeAcc *acc) {
+  const uint64_t node = node_lo + blockIdx.x;
+  const uint64_t lo = max(begin, node * n_paths);
+  const uint64_t hi = min(end, (node + 1) * n_paths);
+  if (lo >= hi) return;
+  const R *s = score + (lo - begin);
+  const uint64_t cnt = hi - lo;
+  const double K = static_cast<double>(s[0]);
+  CSum s1, s2;
+  for (uint64_t i = threadIdx.x; i < cnt; i += kReduceBlock) {
+    const double v = static_cast<double>(s[i]) - K;
+    s1.add(v);
+    s2.add(v * v);
+  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    s1.merge(shfl_xor(s1, m));
+    s2.merge(shfl_xor(s2, m));
+  }
+  __shared__ CSum sh1[kReduceBlock / 32], sh2[kReduceBlock / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh1[warp] = s1;
+    sh2[warp] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    CSum t1 = sh1[0], t2 = sh2[0];
+    for (int w = 1; w < kReduceBlock / 32; ++w) {
+      t1.merge(sh1[w]);
+      t2.merge(sh2[w]);
+    }
+    const double nb = static_cast<double>(cnt);
+    const double S1 = t1.value(), S2 = t2.value();
+    const double mean_b = K + S1 / nb;
+    const double m2_b = fmax(0.0, S2 - S1 * S1 / nb);
+    NodeAcc A = acc[node];
+    const double nt = A.n + nb;
+    const double d = mean_b - A.mean;
+    A.mean = A.mean + d * (nb / nt);
+    A.m2 = A.m2 + m2_b + d * d * (A.n * nb / nt);
+    A.n = nt;
+    acc[node] = A;
+  }
+}
+
+__global__ void finalize_kernel(const NodeAcc *acc, int64_t n_nodes, double *mean,
+                                double *se, int64_t *npaths) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n_nodes) return;
+  const NodeAcc A = acc[i];
+  mean[i] = A.mean;
+  se[i] = A.n > 1.0 ? sqrt(A.m2 / (A.n - 1.0) / A.n) : 0.0;
+  if (npaths) npaths[i] = static_cast<int64_t>(A.n);
+}
+
+template <typename R>
+__global__ void widen_scores_kernel(const R *__restrict__ src, double *dst, uint64_t count) {
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    dst[i] = static_cast<double>(src[i]);
+}
+
+}  // namespace pdd

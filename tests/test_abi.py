@@ -1,0 +1,61 @@
+"""C-ABI checks that need no GPU: the library builds, loads, and exports every
+function include/pdd.h declares; the Python binding covers the same set."""
+import ctypes
+import subprocess
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_03666_gb300 import build as b
+    b.build()
+    from paper_1705_03666_gb300 import _lib
+    return _lib
+
+
+def test_header_symbols_exported(lib):
+    names = lib.header_symbols()
+    assert "pdd_interface_solve" in names and "pdd_create" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in names if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    # nothing but the C ABI is exported
+    assert all(n.startswith("pdd_") for n in exported), sorted(exported)
+
+
+def test_binding_matches_header(lib):
+    assert sorted(lib._SIGS) == lib.header_symbols()
+    cdll = lib.load()
+    for n in lib.header_symbols():
+        assert getattr(cdll, n) is not None
+
+
+def test_status_strings_without_gpu(lib):
+    cdll = lib.load()
+    assert cdll.pdd_status_string(0) == b"ok"
+    assert cdll.pdd_status_string(5).startswith(b"some paths")
+
+
+def test_create_rejects_invalid_problem_without_gpu(lib):
+    """Argument checks run before any device call."""
+    import numpy as np
+    cdll = lib.load()
+    params = np.zeros(1)
+    bad = lib.Problem(2, 1, 3, 0, params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0)
+    h = ctypes.c_void_p()
+    assert cdll.pdd_create(ctypes.byref(h), ctypes.byref(bad), 0, None) == lib.PDD_EINVAL
+    neg = lib.Problem(1, 1, 2, 0, params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), -1.0)
+    assert cdll.pdd_create(ctypes.byref(h), ctypes.byref(neg), 0, None) == lib.PDD_EINVAL
+    # KPP with q not summing to one (Assumption 3.1)
+    kp = np.array([1.0, 1.0, 4.0, 2.0, 0.0, 0.0, 0.5, 0.0, 0.0, 0.5])
+    kpp = lib.Problem(7, 4, 2, kp.size, kp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0)
+    assert cdll.pdd_create(ctypes.byref(h), ctypes.byref(kpp), 0, None) == lib.PDD_EINVAL
+
+
+def test_struct_layouts(lib):
+    assert ctypes.sizeof(lib.Problem) == 32
+    assert ctypes.sizeof(lib.MCParams) == 48
+    assert ctypes.sizeof(lib.Diag) == 32

@@ -1,0 +1,198 @@
+"""GPU parity of pdd_interface_solve against the FP64 oracle (shared streams).
+
+Both sides consume the same Philox4x32-10 words, so every path is the same
+random path.  The FP64 path kernel must reproduce the oracle's exit steps and
+scores to rounding.  The FP32 path kernel differs from FP64 by rounding of the
+position, so a rare path takes its exit decision at a different step (an "exit
+flip"); flips are counted and must stay rare, and the node means over the
+remaining paths must agree to 1e-5 relative.  Full-size runs are checked on
+sampled nodes and against the closed-form solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_03666_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FLIP_MAX_FP32 = 2e-3      # fraction of paths allowed to change exit step / face
+NODE_REL_TOL = 1e-5       # per-node relative agreement on matched paths
+PATH_TOL_FP32 = 1e-4      # per-path score agreement (relative to max(1, |s|))
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_03666_gb300 import api as a
+    assert torch.cuda.is_available()
+    return a
+
+
+def _compare(g, o, path_tol):
+    sg = g["score"].cpu().numpy()
+    stg = g["steps"].cpu().numpy()
+    so, sto = o["score"], o["steps"]
+    matched = (stg == sto) & (np.abs(sg - so) <= path_tol * np.maximum(1.0, np.abs(so)))
+    cnt = matched.sum(1)
+    mg = np.where(matched, sg, 0.0).sum(1) / np.maximum(cnt, 1)
+    mo = np.where(matched, so, 0.0).sum(1) / np.maximum(cnt, 1)
+    scale = np.maximum(np.abs(mo), 0.1 * np.sqrt((so ** 2).mean(1)))
+    rel = np.abs(mg - mo) / scale
+    return {"flip_frac": 1.0 - matched.mean(), "node_rel": rel, "matched": matched,
+            "min_count": cnt.min()}
+
+
+def test_philox_bit_exact(api, orc):
+    cases = [(W.SEED_BASE + 2, 0, 5, 7, 0, 1 << 20),
+             (0, 2 ** 32 - 1000, 2 ** 32 - 1, 0, 1, 4096),
+             (2 ** 64 - 1, 123, 0, 4095, 0, 4096)]
+    with api.Context(W.laplace_expcos()) as ctx:
+        for seed, j0, c1, c2, c3, nb in cases:
+            g = ctx.philox_stream(seed, j0, c1, c2, c3, nb).cpu().numpy().view(np.uint32)
+            o = orc.philox_stream(seed, j0, c1, c2, c3, nb)
+            assert np.array_equal(g, o), (seed, j0, c1, c2, c3)
+
+
+def test_laplace_fp64_matches_oracle_path_by_path(api, orc):
+    w = W.workload(1)
+    kw = dict(seed=w["seed"], dt=w["dt"], n_paths=4000)
+    with api.Context(w["prob"]) as ctx:
+        g = ctx.interface_solve(torch.from_numpy(w["nodes"]), precision="fp64", dump_paths=True, **kw)
+    o = orc.interface_solve(w["prob"], w["nodes"], dump_paths=True, **kw)
+    c = _compare(g, o, 1e-12)
+    assert c["flip_frac"] <= 1e-4
+    mg = g["mean"].cpu().numpy()
+    np.testing.assert_allclose(mg, o["mean"], rtol=1e-10)
+    np.testing.assert_allclose(g["se"].cpu().numpy(), o["se"], rtol=1e-6)
+    assert np.array_equal(g["n"].cpu().numpy(), o["n"])
+    assert g["path_steps"] == o["total_steps"]
+
+
+@pytest.mark.parametrize("dt,stride,n_paths", [(1e-3, 64, 3001), (1e-4, 256, 1000)])
+def test_elliptic_fp32_matches_oracle(api, orc, dt, stride, n_paths):
+    w = W.workload(2)
+    nodes = w["nodes"][::stride]
+    kw = dict(seed=w["seed"], dt=dt, n_paths=n_paths)
+    with api.Context(w["prob"]) as ctx:
+        g = ctx.interface_solve(torch.from_numpy(nodes), precision="fp32", dump_paths=True, **kw)
+    o = orc.interface_solve(w["prob"], nodes, dump_paths=True, **kw)
+    c = _compare(g, o, PATH_TOL_FP32)
+    print(f"dt={dt}: flip fraction {c['flip_frac']:.2e}, max node rel {c['node_rel'].max():.2e}")
+    assert c["flip_frac"] <= FLIP_MAX_FP32
+    assert c["node_rel"].max() <= NODE_REL_TOL
+    # the per-node statistics themselves (all paths) agree within the flips' reach
+    se = o["se"]
+    assert np.all(np.abs(g["mean"].cpu().numpy() - o["mean"]) <= 0.5 * se + 1e-6)
+
+
+def test_elliptic_fp64_matches_oracle(api, orc):
+    w = W.workload(2)
+    nodes = w["nodes"][::512]
+    kw = dict(seed=w["seed"], dt=1e-3, n_paths=1000)
+    with api.Context(w["prob"]) as ctx:
+        g = ctx.interface_solve(torch.from_numpy(nodes), precision="fp64", dump_paths=True, **kw)
+    o = orc.interface_solve(w["prob"], nodes, dump_paths=True, **kw)
+    c = _compare(g, o, 1e-11)
+    assert c["flip_frac"] <= 1e-4
+    np.testing.assert_allclose(g["mean"].cpu().numpy(), o["mean"], rtol=1e-10)
+
+
+def test_poisson_fourier_fp32_matches_oracle(api, orc):
+    w = W.workload(5)
+    nodes = w["nodes"][::64]
+    kw = dict(seed=w["seed"], dt=1e-3, n_paths=2000)
+    with api.Context(w["prob"]) as ctx:
+        g = ctx.interface_solve(torch.from_numpy(nodes), precision="fp32", dump_paths=True, **kw)
+    o = orc.interface_solve(w["prob"], nodes, dump_paths=True, **kw)
+    c = _compare(g, o, PATH_TOL_FP32)
+    assert c["flip_frac"] <= FLIP_MAX_FP32
+    assert c["node_rel"].max() <= NODE_REL_TOL
+
+
+def test_waves_and_launch_shape_do_not_change_results(api):
+    w = W.workload(2)
+    nodes = torch.from_numpy(w["nodes"][::128])
+    kw = dict(seed=w["seed"], dt=1e-3, n_paths=2999, precision="fp32", dump_paths=True)
+    with api.Context(w["prob"]) as ctx:
+        a = ctx.interface_solve(nodes, **kw)
+        ctx.set_tuning(blocks_per_sm=1, wave_max_paths=10007)  # ragged waves across nodes
+        b = ctx.interface_solve(nodes, **kw)
+        ctx.set_tuning(0, 0)
+        c = ctx.interface_solve(nodes, **kw)
+    assert torch.equal(a["score"], b["score"]) and torch.equal(a["steps"], b["steps"])
+    assert torch.equal(a["mean"], c["mean"]) and torch.equal(a["se"], c["se"])  # deterministic
+    np.testing.assert_allclose(a["mean"].cpu().numpy(), b["mean"].cpu().numpy(), rtol=1e-13)
+    np.testing.assert_allclose(a["se"].cpu().numpy(), b["se"].cpu().numpy(), rtol=1e-9)
+    assert a["path_steps"] == b["path_steps"]
+
+
+def test_edge_cases(api):
+    w = W.workload(1)
+    with api.Context(w["prob"]) as ctx:
+        # empty input: nothing to do
+        r = ctx.interface_solve(torch.zeros((0, 2), dtype=torch.float64), seed=1, dt=1e-3,
+                                n_paths=10, diag=True)
+        assert r["mean"].numel() == 0 and r["path_steps"] == 0
+        # a single path of a single node
+        r = ctx.interface_solve(torch.tensor([[0.5, 0.5]]), seed=1, dt=1e-3, n_paths=1, diag=True)
+        assert r["n"].item() == 1 and r["se"].item() == 0.0 and r["path_steps"] > 0
+        # nodes on the boundary: u = g exactly, zero error, zero steps
+        bn = np.array([[0.0, 0.3], [0.5, 1.0], [1.0, 0.0]])
+        r = ctx.interface_solve(torch.from_numpy(bn), seed=1, dt=1e-3, n_paths=33,
+                                precision="fp64", dump_paths=True)
+        g = np.exp(bn[:, 0]) * np.cos(bn[:, 1])
+        np.testing.assert_allclose(r["mean"].cpu().numpy(), g, rtol=1e-15)
+        assert np.all(r["se"].cpu().numpy() == 0.0)
+        assert int(r["steps"].abs().sum()) == 0
+        # step cap: every path capped, counted, status ECAP
+        r = ctx.interface_solve(torch.tensor([[0.5, 0.5]]), seed=1, dt=1e-7, n_paths=100,
+                                max_steps=3, diag=True)
+        assert r["status"] == 5 and r["capped"] == 100 and r["path_steps"] == 300
+        # a node outside the closed domain is an invalid input
+        from paper_1705_03666_gb300._lib import PDDError
+        with pytest.raises(PDDError):
+            ctx.interface_solve(torch.tensor([[1.5, 0.5]]), seed=1, dt=1e-3, n_paths=4, diag=True)
+        # invalid arguments are rejected before any launch
+        with pytest.raises(PDDError):
+            ctx.interface_solve(torch.tensor([[0.5, 0.5]]), seed=1, dt=-1.0, n_paths=4)
+        with pytest.raises(PDDError):
+            ctx.interface_solve(torch.tensor([[0.5, 0.5]]), seed=1, dt=1e-3, n_paths=0)
+
+
+def test_elliptic_full_size_closed_form(api):
+    """The 4096-node, 1e5-path, dt = 1e-4 workload against the exact solution."""
+    w = W.workload(2)
+    with api.Context(w["prob"]) as ctx:
+        r = ctx.interface_solve(torch.from_numpy(w["nodes"]), seed=w["seed"], dt=w["dt"],
+                                n_paths=w["n_paths"], precision="fp32", diag=True)
+    x = w["nodes"]
+    exact = np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) * np.exp(x[:, 2])
+    mean, se = r["mean"].cpu().numpy(), r["se"].cpu().numpy()
+    z = (mean - exact) / se
+    print(f"full size: path-steps {r['path_steps']:.3e}, mean |z| {np.abs(z).mean():.3f}, "
+          f"max |z| {np.abs(z).max():.2f}, capped {r['capped']}")
+    assert np.all(np.abs(mean - exact) <= 4.5 * se + 3e-4)   # 4096 nodes: 4.5 sigma
+    assert abs(z.mean()) < 0.25 and 0.8 < z.std() < 1.25
+    assert r["capped"] == 0
+
+
+def test_elliptic_full_size_sampled_parity(api, orc):
+    """Full-size launch (the benchmark's configuration); sampled nodes against
+    the oracle path by path, on the full run's streams."""
+    w = W.workload(2)
+    sample = np.array([0, 1365, 2730, 4095])
+    with api.Context(w["prob"]) as ctx:
+        r = ctx.interface_solve(torch.from_numpy(w["nodes"]), seed=w["seed"], dt=w["dt"],
+                                n_paths=w["n_paths"], precision="fp32", dump_paths=True)
+        g = {"score": r["score"][sample], "steps": r["steps"][sample]}
+        del r
+        torch.cuda.empty_cache()
+    o = orc.interface_solve(w["prob"], w["nodes"][sample], node_ids=sample, seed=w["seed"],
+                            dt=w["dt"], n_paths=w["n_paths"], dump_paths=True)
+    c = _compare(g, o, PATH_TOL_FP32)
+    print(f"sampled full-size parity: flip fraction {c['flip_frac']:.2e}, "
+          f"max node rel {c['node_rel'].max():.2e}")
+    assert c["flip_frac"] <= FLIP_MAX_FP32
+    assert c["node_rel"].max() <= NODE_REL_TOL
