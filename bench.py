@@ -179,7 +179,8 @@ def run_pdd(args):
     nodes_h = torch.from_numpy(w["nodes"]).pin_memory()
     nodes = nodes_h.to(dev)
     n = nodes.shape[0]
-    kw = dict(seed=seed, dt=w["dt"], n_paths=w["n_paths"], precision="fp32", bridge=True)
+    n_paths = args.paths or w["n_paths"]
+    kw = dict(seed=seed, dt=w["dt"], n_paths=n_paths, precision="fp32", bridge=True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     ctx = api.Context(w["prob"], dev)
@@ -263,7 +264,9 @@ def run_pdd(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": w["name"], "nodes": n, "paths_per_node": w["n_paths"],
+        "config": {"workload": w["name"] if n_paths == w["n_paths"] else
+                   f"{w['name']} (profiling case: {n_paths} paths/node)",
+                   "nodes": n, "paths_per_node": n_paths,
                    "dt": w["dt"], "path_precision": "fp32 paths, fp64 reductions",
                    "bridge": True, "path_steps_per_step": steps_per_call,
                    "l2": "flushed between steps (256 MiB write outside the timed events); "
@@ -308,6 +311,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["pdd", "reference"], default="pdd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", type=int, default=None,
+                    help="paths per node (profiling runs only; the benchmark uses 1e5)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -152,6 +152,73 @@ PDD_API pdd_status pdd_interface_solve(pdd_ctx *ctx, const double *d_nodes, int6
                                double *d_se, int64_t *d_npaths,
                                pdd_diag *diag);
 
+/* Monte Carlo parameters of the branching estimator. */
+typedef struct {
+  uint64_t seed;          /* Philox key */
+  int64_t n_trees;        /* trees per node (>= 1) */
+  int64_t tree_offset;    /* index of the first tree (resume/extend a run) */
+  int64_t max_particles;  /* pruning: a tree with more particles is discarded
+                             and counted (Algorithm 3.1), >= 1, <= 2^31 */
+  int32_t max_depth;      /* pending-particle stack cap per tree, 1..64; a
+                             tree exceeding it is discarded and counted */
+  int32_t reserved;       /* must be 0 */
+} pdd_branch_params;
+
+/* Stage one of PDD for the semilinear KPP-type problem (Sec. 3.1-3.2,
+ * Algorithm 3.1): for each space-time node (d_nodes_xt is [n][dim+1] FP64:
+ * position then time t >= 0) estimate u(x, t) = E[W prod_{alive at t}
+ * psi(X^(k)_t)] from n_trees branching Brownian motions with Exp(beta)
+ * lifetimes and offspring law q, W the product of alpha_k / q_k over the
+ * branchings (W = 1 when alpha = q).  Writes d_mean[n], d_se[n] and, if
+ * non-NULL, d_nkept[n] (trees kept after pruning).  Tree s of node i uses
+ * the Philox stream (key = seed, counter = (particle id, tree_offset + s, i,
+ * 1)) with depth-first particle ids.  Positions and times are FP32, the
+ * product and the weights FP64.  With diag non-NULL the call synchronises;
+ * diag->d_path_score receives per-tree scores (NaN if discarded),
+ * d_path_steps per-tree segment counts (negative if discarded), path_steps
+ * the total segments and capped the discarded trees (status PDD_ECAP when
+ * non-zero).  A node whose trees are all discarded gets NaN.             */
+PDD_API pdd_status pdd_branching_solve(pdd_ctx *ctx, const double *d_nodes_xt,
+                                       int64_t n, const pdd_branch_params *bp,
+                                       double *d_mean, double *d_se,
+                                       int64_t *d_nkept, pdd_diag *diag);
+
+/* Stage two of PDD (Sec. 2.1, Fig. 2.2) for the Laplace family (Eq. 1.1):
+ * the interpolator and the subdomain solver.  The subdomain is the box
+ * [lo[0], hi[0]] x [lo[1], hi[1]] inside the unit square, discretised by an
+ * n[0] x n[1] grid including its boundary (n[2] must be 1).  One side is an
+ * artificial interface (axis iface_axis, at lo when iface_side = 0, at hi
+ * when 1); its Dirichlet data are the cubic spline with not-a-knot end
+ * conditions through the interface end points (value g, as they lie on the
+ * physical boundary) and the m >= 2 Monte Carlo nodes (d_iface_s: node
+ * coordinates along the interface, strictly increasing inside the side;
+ * d_iface_vals: node values, both FP64 device arrays).  The other sides get
+ * g.  The interior solves the 5-point system
+ *   (u_{i+1,j} - 2u_{ij} + u_{i-1,j})/hx^2 + (u_{i,j+1} - 2u_{ij} + u_{i,j-1})/hy^2 = 0
+ * by conjugate gradients (stop at ||r||_2 <= tol ||b||_2) or Jacobi sweeps
+ * (stop when max |u^{k+1} - u^k| < tol), at most max_iter iterations.
+ * d_u is [n[1]][n[0]] FP64 (row = y), written in full.  *iters and *resid
+ * (host) receive the iteration count and the final residual measure; the call
+ * synchronises.  Returns PDD_ETIMEOUT when max_iter ran out first (d_u holds
+ * the last iterate).                                                      */
+enum { PDD_STENCIL_CG = 0, PDD_STENCIL_JACOBI = 1 };
+
+typedef struct {
+  double lo[3], hi[3];
+  int32_t n[3];
+  int32_t iface_axis;
+  int32_t iface_side;
+  int32_t method;       /* PDD_STENCIL_CG or PDD_STENCIL_JACOBI */
+  int64_t max_iter;
+  double tol;
+} pdd_subdomain;
+
+PDD_API pdd_status pdd_subdomain_solve(pdd_ctx *ctx, const pdd_subdomain *sd,
+                                       const double *d_iface_s,
+                                       const double *d_iface_vals, int64_t m,
+                                       double *d_u, int64_t *iters,
+                                       double *resid);
+
 /* Launch-shape and memory knobs of the path kernels (no effect on results,
  * which do not depend on scheduling):
  *   blocks_per_sm    resident 256-thread blocks per SM for the persistent

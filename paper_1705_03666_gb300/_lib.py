@@ -33,6 +33,19 @@ class MCParams(ctypes.Structure):
                 ("bridge", ctypes.c_int32)]
 
 
+class BranchParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_trees", ctypes.c_int64),
+                ("tree_offset", ctypes.c_int64), ("max_particles", ctypes.c_int64),
+                ("max_depth", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Subdomain(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("n", ctypes.c_int32 * 3), ("iface_axis", ctypes.c_int32),
+                ("iface_side", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("max_iter", ctypes.c_int64), ("tol", ctypes.c_double)]
+
+
 class Diag(ctypes.Structure):
     _fields_ = [("d_path_score", ctypes.c_void_p), ("d_path_steps", ctypes.c_void_p),
                 ("path_steps", ctypes.c_int64), ("capped", ctypes.c_int64)]
@@ -52,6 +65,11 @@ _SIGS = {
     "pdd_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pdd_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64)]),
+    "pdd_branching_solve": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(BranchParams), _VP,
+                                           _VP, _VP, ctypes.POINTER(Diag)]),
+    "pdd_subdomain_solve": (ctypes.c_int, [_VP, ctypes.POINTER(Subdomain), _VP, _VP, _I64, _VP,
+                                           ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "pdd_philox_stream": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _U32, _I64, _VP]),
     "pdd_destroy": (None, [_VP]),
     "pdd_status_string": (ctypes.c_char_p, [ctypes.c_int]),

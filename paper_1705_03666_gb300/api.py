@@ -124,6 +124,65 @@ class Context:
             res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
         return res
 
+    def branching_solve(self, nodes_xt, *, seed: int, n_trees: int, max_particles: int = 4096,
+                        max_depth: int = 64, tree_offset: int = 0, dump_trees: bool = False,
+                        diag: bool = False, out=None) -> dict:
+        """pdd_branching_solve: nodes_xt [n, dim+1] float64 (position, then t).
+
+        Returns mean, se, n (trees kept); with diag/dump_trees also segments
+        (total) and discarded (host ints); with dump_trees score [n, n_trees]
+        (NaN = discarded) and segs [n, n_trees] (negative = discarded)."""
+        dim = int(self.prob["dim"])
+        nodes_xt = _dev_f64(nodes_xt, self.device).reshape(-1, dim + 1)
+        n = nodes_xt.shape[0]
+        if out is None:
+            mean = torch.empty(n, dtype=_F64, device=self.device)
+            se = torch.empty(n, dtype=_F64, device=self.device)
+            kept = torch.empty(n, dtype=_I64, device=self.device)
+        else:
+            mean, se, kept = out
+        bp = _lib.BranchParams(int(seed) & (2**64 - 1), int(n_trees), int(tree_offset),
+                               int(max_particles), int(max_depth), 0)
+        res = {"mean": mean, "se": se, "n": kept}
+        dg = None
+        if diag or dump_trees:
+            dg = _lib.Diag()
+            if dump_trees:
+                res["score"] = torch.empty((n, int(n_trees)), dtype=_F64, device=self.device)
+                res["segs"] = torch.empty((n, int(n_trees)), dtype=_I32, device=self.device)
+                dg.d_path_score = res["score"].data_ptr()
+                dg.d_path_steps = res["segs"].data_ptr()
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_branching_solve(self.handle, nodes_xt.data_ptr(), n, ctypes.byref(bp),
+                                              mean.data_ptr(), se.data_ptr(), kept.data_ptr(),
+                                              ctypes.byref(dg) if dg is not None else None)
+        res["status"] = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ECAP))
+        if dg is not None:
+            res["segments"], res["discarded"] = int(dg.path_steps), int(dg.capped)
+        return res
+
+    def subdomain_solve(self, lo, hi, n, iface_axis: int, iface_side: int, iface_s, iface_vals,
+                        *, method: str = "cg", max_iter: int = 100000, tol: float = 1e-12,
+                        out=None) -> dict:
+        """pdd_subdomain_solve on a 2-D box: returns u [n[1], n[0]] (CUDA), iters, resid."""
+        s = _dev_f64(iface_s, self.device).reshape(-1)
+        v = _dev_f64(iface_vals, self.device).reshape(-1)
+        nx, ny = int(n[0]), int(n[1])
+        u = out if out is not None else torch.empty((ny, nx), dtype=_F64, device=self.device)
+        sd = _lib.Subdomain((ctypes.c_double * 3)(lo[0], lo[1], 0.0),
+                            (ctypes.c_double * 3)(hi[0], hi[1], 0.0),
+                            (ctypes.c_int32 * 3)(nx, ny, 1), int(iface_axis), int(iface_side),
+                            {"cg": 0, "jacobi": 1}[method], int(max_iter), float(tol))
+        it, res = ctypes.c_int64(0), ctypes.c_double(0.0)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_subdomain_solve(self.handle, ctypes.byref(sd), s.data_ptr(),
+                                              v.data_ptr(), s.numel(), u.data_ptr(),
+                                              ctypes.byref(it), ctypes.byref(res))
+        status = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ETIMEOUT))
+        return {"u": u, "iters": it.value, "resid": res.value, "status": status}
+
     def philox_stream(self, seed: int, j0: int, c1: int, c2: int, c3: int, n_blocks: int):
         """pdd_philox_stream: uint32 [n_blocks, 4] CUDA tensor."""
         out = torch.empty((int(n_blocks), 4), dtype=torch.int32, device=self.device)

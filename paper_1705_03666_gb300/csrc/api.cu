@@ -122,6 +122,23 @@ pdd_status pdd_interface_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   return pdd::interface_solve_impl(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
 }
 
+pdd_status pdd_branching_solve(pdd_ctx *ctx, const double *d_nodes_xt, int64_t n,
+                               const pdd_branch_params *bp, double *d_mean, double *d_se,
+                               int64_t *d_nkept, pdd_diag *diag) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  if (bp && bp->reserved != 0) return fail(ctx, PDD_EINVAL, "reserved must be 0");
+  return pdd::branching_solve_impl(ctx, d_nodes_xt, n, bp, d_mean, d_se, d_nkept, diag);
+}
+
+pdd_status pdd_subdomain_solve(pdd_ctx *ctx, const pdd_subdomain *sd, const double *d_iface_s,
+                               const double *d_iface_vals, int64_t m, double *d_u,
+                               int64_t *iters, double *resid) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::subdomain_solve_impl(ctx, sd, d_iface_s, d_iface_vals, m, d_u, iters, resid);
+}
+
 pdd_status pdd_profile(pdd_ctx *ctx, int enable) {
   if (!ctx) return PDD_EINVAL;
   ctx->profiling = enable != 0;

@@ -1,0 +1,123 @@
+// branching.cu -- host side of pdd_branching_solve: waves of trees, launches
+// of the branching kernel and the NaN-skipping per-node reduction.
+#include <cmath>
+#include <cstring>
+
+#include "branch_kernel.cuh"
+#include "ctx.hpp"
+#include "reduce.cuh"
+
+namespace pdd {
+
+template <int D>
+static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t n,
+                                const pdd_branch_params *bp, double *d_mean, double *d_se,
+                                int64_t *d_nkept, pdd_diag *diag) {
+  const uint64_t N = static_cast<uint64_t>(bp->n_trees);
+  const uint64_t total = static_cast<uint64_t>(n) * N;
+  const uint64_t wave = std::min<uint64_t>(total, ctx->wave_max_paths);
+  const size_t acc_off = 256;
+  const size_t score_off = align_up(acc_off + static_cast<size_t>(n) * sizeof(NodeAcc), 256);
+  const size_t bytes = align_up(score_off + wave * sizeof(double), 256);
+  pdd_status st = ensure_scratch(ctx, bytes);
+  if (st != PDD_OK) return st;
+  char *base = static_cast<char *>(ctx->scratch);
+  auto *counters = reinterpret_cast<unsigned long long *>(base);
+  auto *cursor = counters + 4;
+  auto *acc = reinterpret_cast<NodeAcc *>(base + acc_off);
+  double *score = reinterpret_cast<double *>(base + score_off);
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, score_off, ctx->stream));
+
+  const double *prm = ctx->params.data();
+  BranchArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.nodes_xt = d_nodes_xt;
+  a.n_trees = N;
+  a.tree_offset = static_cast<uint64_t>(bp->tree_offset);
+  a.cursor = cursor;
+  a.counters = counters;
+  a.score = score;
+  a.rk = make_round_keys(bp->seed);
+  a.inv_beta = static_cast<float>(1.0 / prm[0]);
+  a.psi_kind = static_cast<int32_t>(prm[1]);
+  a.psi_prm = static_cast<float>(prm[2]);
+  a.K = static_cast<int32_t>(prm[3]);
+  double cum = 0.0;
+  for (int k = 0; k <= a.K; ++k) {
+    const double q = prm[4 + k], al = prm[5 + a.K + k];
+    cum += q;
+    a.cum[k] = cum;
+    a.ratio[k] = q > 0.0 ? al / q : 0.0;
+  }
+  a.max_particles = bp->max_particles;
+  a.max_depth = bp->max_depth;
+
+  auto kern = branch_kernel<D>;
+  int bps = 0;
+  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kBranchBlock, 0));
+  if (bps < 1) bps = 1;
+  if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
+  uint64_t grid = static_cast<uint64_t>(bps) * ctx->num_sms;
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (wave + kBranchBlock - 1) / kBranchBlock));
+
+  for (uint64_t b0 = 0; b0 < total; b0 += wave) {
+    const uint64_t b1 = std::min(total, b0 + wave);
+    if (b0 > 0) PDD_CUDA_TRY(ctx, cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), ctx->stream));
+    a.begin = b0;
+    a.end = b1;
+    a.segs = (diag && diag->d_path_steps) ? diag->d_path_steps + b0 : nullptr;
+    const auto ev = prof_slot(ctx);
+    if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
+    kern<<<static_cast<unsigned>(grid), kBranchBlock, 0, ctx->stream>>>(a);
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
+    if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
+    const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
+    reduce_wave_kernel<double, true><<<static_cast<unsigned>(node_hi - node_lo + 1), kReduceBlock,
+                                       0, ctx->stream>>>(score, b0, b1, N, node_lo, acc);
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
+    if (diag && diag->d_path_score)
+      PDD_CUDA_TRY(ctx, cudaMemcpyAsync(diag->d_path_score + b0, score, (b1 - b0) * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(
+      acc, n, d_mean, d_se, d_nkept);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  if (diag) {
+    unsigned long long h[4] = {0, 0, 0, 0};
+    PDD_CUDA_TRY(ctx, cudaMemcpyAsync(h, counters, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    diag->path_steps = static_cast<int64_t>(h[0]);
+    diag->capped = static_cast<int64_t>(h[1]);
+    if (h[1]) return fail(ctx, PDD_ECAP, "%llu trees discarded by the caps", h[1]);
+  }
+  return PDD_OK;
+}
+
+pdd_status branching_solve_impl(pdd_ctx *ctx, const double *d_nodes_xt, int64_t n,
+                                const pdd_branch_params *bp, double *d_mean, double *d_se,
+                                int64_t *d_nkept, pdd_diag *diag) {
+  if (!bp) return fail(ctx, PDD_EINVAL, "params is NULL");
+  if (ctx->prob.kind != PDD_PROB_KPP)
+    return fail(ctx, PDD_EINVAL, "pdd_branching_solve needs a KPP problem");
+  if (n < 0 || n > (int64_t(1) << 32)) return fail(ctx, PDD_EINVAL, "n out of range");
+  if (bp->n_trees < 1) return fail(ctx, PDD_EINVAL, "n_trees < 1");
+  if (bp->tree_offset < 0 || bp->tree_offset + bp->n_trees > (int64_t(1) << 32))
+    return fail(ctx, PDD_EINVAL, "tree indices must fit in 32 bits");
+  if (bp->max_particles < 1) return fail(ctx, PDD_EINVAL, "max_particles < 1");
+  if (bp->max_particles > (int64_t(1) << 31))
+    return fail(ctx, PDD_EINVAL, "max_particles above 2^31 (particle ids are 32-bit)");
+  if (bp->max_depth < 1 || bp->max_depth > kBranchMaxDepth)
+    return fail(ctx, PDD_EINVAL, "max_depth must be in [1, %d]", kBranchMaxDepth);
+  if (n > 0 && (!d_nodes_xt || !d_mean || !d_se)) return fail(ctx, PDD_EINVAL, "null buffer");
+  if (diag) {
+    diag->path_steps = 0;
+    diag->capped = 0;
+  }
+  if (n == 0) return PDD_OK;
+  PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  if (ctx->prob.dim == 1)
+    return run_branching<1>(ctx, d_nodes_xt, n, bp, d_mean, d_se, d_nkept, diag);
+  return run_branching<2>(ctx, d_nodes_xt, n, bp, d_mean, d_se, d_nkept, diag);
+}
+
+}  // namespace pdd

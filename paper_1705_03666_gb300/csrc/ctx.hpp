@@ -101,6 +101,12 @@ inline std::pair<cudaEvent_t, cudaEvent_t> prof_slot(pdd_ctx *ctx) {
 pdd_status interface_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                                 const pdd_mc_params *mc, double *d_mean, double *d_se,
                                 int64_t *d_npaths, pdd_diag *diag);
+pdd_status branching_solve_impl(pdd_ctx *ctx, const double *d_nodes_xt, int64_t n,
+                                const pdd_branch_params *bp, double *d_mean, double *d_se,
+                                int64_t *d_nkept, pdd_diag *diag);
+pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const double *d_iface_s,
+                                const double *d_iface_vals, int64_t m, double *d_u,
+                                int64_t *iters, double *resid);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

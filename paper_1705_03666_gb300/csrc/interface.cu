@@ -87,8 +87,7 @@ static pdd_status run_paths(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   a.dt_f = static_cast<float>(a.dt_d);
   a.sdt_f = static_cast<float>(a.sdt_d);
   a.thr_f = static_cast<float>(a.thr_d);
-  a.ecdt_hi = static_cast<float>(a.ecdt_d);
-  a.ecdt_lo = static_cast<float>(a.ecdt_d - static_cast<double>(a.ecdt_hi));
+  a.l2cdt_f = static_cast<float>(constant_kill(ctx->prob.kind) * dt * 1.4426950408889634);
   a.max_steps = static_cast<int32_t>(mc->max_steps);
   a.bridge = mc->bridge ? 1 : 0;
   a.mc = ctx->mc;

@@ -15,7 +15,8 @@
 // first crossing of the segment), else, with the bridge test, exit when
 // U < P = 1 - prod_j (1 - exp(-2 d_j d'_j / (sigma^2 dt))) over faces with
 // 2 d_j d'_j < 18 sigma^2 dt (exit point = X' projected on the face with the
-// largest term).  P is formed in FP64 whatever the path precision.
+// largest term).  P is accumulated without cancellation (bridge_exit) and
+// near-ties of the FP32 path are decided in FP64.
 // Score = g(X_tau) Y' + Z' (Eq. 2.7).
 #pragma once
 
@@ -40,32 +41,82 @@ struct PathArgs {
   double dt_d, sdt_d, thr_d;    // FP64 path: dt, sigma sqrt(dt), 9 sigma^2 dt
   double ecdt_d;                // e^{c dt} for constant killing (FP64)
   float dt_f, sdt_f, thr_f;     // FP32 path
-  float ecdt_hi, ecdt_lo;       // e^{c dt} as an unevaluated float sum
+  float l2cdt_f;                // c dt log2(e) for constant killing (FP32)
   int32_t max_steps;
   int32_t bridge;
   ModelConst mc;
 };
 
+// Constant killing: Y_n = e^{c n dt}.  Every path runs through the same
+// sequence Y_0, Y_1, ..., so a rounded recurrence Y <- Y e^{c dt} would carry
+// the same rounding error into every path (in binary32 it drifts by ~1e-5
+// over 500 steps); the FP32 path therefore evaluates Y_n from n directly
+// (exp2 of n c dt log2 e, a few ulp, no accumulation).  In FP64 the
+// recurrence is accurate to n ulp and is kept.
 template <typename R> struct StepConst;
 template <> struct StepConst<float> {
-  float dt, sdt, thr, e_hi, e_lo;
+  float dt, sdt, thr, l2cdt, inv_s2dt;
   __device__ __forceinline__ StepConst(const PathArgs &a)
-      : dt(a.dt_f), sdt(a.sdt_f), thr(a.thr_f), e_hi(a.ecdt_hi), e_lo(a.ecdt_lo) {}
-  __device__ __forceinline__ float kill(float y) const { return fmaf(y, e_lo, y * e_hi); }
+      : dt(a.dt_f), sdt(a.sdt_f), thr(a.thr_f), l2cdt(a.l2cdt_f),
+        inv_s2dt(static_cast<float>(a.inv_s2dt)) {}
+  __device__ __forceinline__ float kill(float, int32_t n_next) const {
+    return exp2f(static_cast<float>(n_next) * l2cdt);
+  }
 };
 template <> struct StepConst<double> {
-  double dt, sdt, thr, e;
+  double dt, sdt, thr, e, inv_s2dt;
   __device__ __forceinline__ StepConst(const PathArgs &a)
-      : dt(a.dt_d), sdt(a.sdt_d), thr(a.thr_d), e(a.ecdt_d) {}
-  __device__ __forceinline__ double kill(double y) const { return y * e; }
+      : dt(a.dt_d), sdt(a.sdt_d), thr(a.thr_d), e(a.ecdt_d), inv_s2dt(a.inv_s2dt) {}
+  __device__ __forceinline__ double kill(double y, int32_t) const { return y * e; }
 };
+
+// Brownian-bridge exit probability over the faces within reach,
+// P = 1 - prod_j (1 - p_j), p_j = exp(-2 d_j d'_j / (sigma^2 dt)), accumulated
+// as P <- P + p_j (1 - P) (no cancellation, so accurate for tiny P).  FP32
+// path: compensated binary32, and a decision with |U - P| within 2^-18 P is
+// re-taken from the same distances in FP64.  Returns the face with the
+// largest p_j, or -1 when no face is within reach or U >= P.
+template <class Geom, typename R>
+__device__ __forceinline__ int bridge_exit(const StepConst<R> &k, const R *X, const R *Xn,
+                                           R U) {
+  R P = R(0), pbest = R(-1);
+  int jbest = -1;
+#pragma unroll
+  for (int j = 0; j < Geom::kFaces; ++j) {
+    const R aa = R(2) * Geom::face_dist(j, X) * Geom::face_dist(j, Xn) * k.inv_s2dt;
+    if (aa < R(18)) {
+      const R p = m_exp(-aa);
+      P = P + p * (R(1) - P);
+      if (p > pbest) { pbest = p; jbest = j; }
+    }
+  }
+  if (jbest < 0) return -1;
+  bool take = U < P;
+  if constexpr (sizeof(R) == 4) {
+    if (fabsf(U - P) <= 3.814697265625e-06f * P) {  // near tie: FP64 from the same distances
+      double Pd = 0.0;
+      const double s = 2.0 * static_cast<double>(k.inv_s2dt);
+#pragma unroll
+      for (int j = 0; j < Geom::kFaces; ++j) {
+        const double aa = s * static_cast<double>(Geom::face_dist(j, X)) *
+                          static_cast<double>(Geom::face_dist(j, Xn));
+        if (aa < 18.0) {
+          const double p = exp(-aa);
+          Pd = Pd + p * (1.0 - Pd);
+        }
+      }
+      take = static_cast<double>(U) < Pd;
+    }
+  }
+  return take ? jbest : -1;
+}
 
 // One Euler-Maruyama step with the exit test.  Returns true on exit, with
 // the score in `s`.  X, Y, Z advance only when the path stays inside.
 template <class Model, class Geom, typename R>
 __device__ __forceinline__ bool em_step(const PathArgs &a, const StepConst<R> &k,
                                         R *X, R &Y, R &Z, const R *xi, uint32_t uw,
-                                        R &s) {
+                                        int32_t n, R &s) {
   constexpr int D = Model::D;
   R b[D];
   R f = R(0);
@@ -78,7 +129,7 @@ __device__ __forceinline__ bool em_step(const PathArgs &a, const StepConst<R> &k
   R Zn = Z;
   if constexpr (Model::kSource) Zn = Z + f * Y * k.dt;
   R Yn = Y;
-  if constexpr (Model::kKill == 1) Yn = k.kill(Y);
+  if constexpr (Model::kKill == 1) Yn = k.kill(Y, n + 1);
   if (!Geom::inside_closed(Xn)) {
     R xe[D];
     Geom::segment_exit(X, Xn, xe);
@@ -86,20 +137,8 @@ __device__ __forceinline__ bool em_step(const PathArgs &a, const StepConst<R> &k
     return true;
   }
   if (a.bridge && Geom::near_any(X, Xn, k.thr)) {
-    double keep = 1.0, pbest = -1.0;
-    int jbest = -1;
-#pragma unroll
-    for (int j = 0; j < Geom::kFaces; ++j) {
-      const double d0 = static_cast<double>(Geom::face_dist(j, X));
-      const double d1 = static_cast<double>(Geom::face_dist(j, Xn));
-      const double aa = 2.0 * d0 * d1 * a.inv_s2dt;
-      if (aa < 18.0) {
-        const double p = exp(-aa);
-        keep *= (1.0 - p);
-        if (p > pbest) { pbest = p; jbest = j; }
-      }
-    }
-    if (jbest >= 0 && static_cast<double>(unif<R>(uw)) < 1.0 - keep) {
+    const int jbest = bridge_exit<Geom, R>(k, X, Xn, unif<R>(uw));
+    if (jbest >= 0) {
       R xe[D];
 #pragma unroll
       for (int d = 0; d < D; ++d) xe[d] = Xn[d];
@@ -186,7 +225,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
       R xi[3], e;
       box_muller<R>(A.x, A.y, xi[0], xi[1]);
       box_muller<R>(A.z, A.w, xi[2], e);
-      done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, B.z, s);
+      done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, B.z, n, s);
       ++n;
       if (!done && n < a.max_steps) {
         R p, q;
@@ -194,7 +233,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
         xi[0] = e;
         xi[1] = p;
         xi[2] = q;
-        done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, B.w, s);
+        done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, B.w, n, s);
         ++n;
       }
     } else {
@@ -202,7 +241,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
       R xi[2], z1;
       box_muller<R>(A.x, A.y, xi[0], z1);
       if constexpr (D == 2) xi[1] = z1;
-      done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, A.z, s);
+      done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, A.z, n, s);
       ++n;
     }
     int32_t st = n;

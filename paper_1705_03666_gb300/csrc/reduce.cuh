@@ -20,7 +20,9 @@ struct NodeAcc {  // running (count, mean, M2) per node, FP64
   double n, mean, m2;
 };
 
-template <typename R>
+// kSkipNaN: NaN scores mark discarded samples (pruned trees) and are left
+// out of the count; the shift K is then 0 (scores are bounded weights).
+template <typename R, bool kSkipNaN = false>
 __global__ void __launch_bounds__(kReduceBlock)
 reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
                    uint64_t n_paths, uint64_t node_lo, NodeAcc *acc) {
@@ -30,10 +32,13 @@ reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
   if (lo >= hi) return;
   const R *s = score + (lo - begin);
   const uint64_t cnt = hi - lo;
-  const double K = static_cast<double>(s[0]);
+  const double K = kSkipNaN ? 0.0 : static_cast<double>(s[0]);
   CSum s1, s2;
+  unsigned long long kept = 0;
   for (uint64_t i = threadIdx.x; i < cnt; i += kReduceBlock) {
     const double v = static_cast<double>(s[i]) - K;
+    if (kSkipNaN && isnan(v)) continue;
+    ++kept;
     s1.add(v);
     s2.add(v * v);
   }
@@ -41,21 +46,27 @@ reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
   for (int m = 16; m > 0; m >>= 1) {
     s1.merge(shfl_xor(s1, m));
     s2.merge(shfl_xor(s2, m));
+    kept += __shfl_xor_sync(kFull, kept, m);
   }
   __shared__ CSum sh1[kReduceBlock / 32], sh2[kReduceBlock / 32];
+  __shared__ unsigned long long shk[kReduceBlock / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     sh1[warp] = s1;
     sh2[warp] = s2;
+    shk[warp] = kept;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     CSum t1 = sh1[0], t2 = sh2[0];
+    unsigned long long tk = shk[0];
     for (int w = 1; w < kReduceBlock / 32; ++w) {
       t1.merge(sh1[w]);
       t2.merge(sh2[w]);
+      tk += shk[w];
     }
-    const double nb = static_cast<double>(cnt);
+    if (tk == 0) return;
+    const double nb = static_cast<double>(tk);
     const double S1 = t1.value(), S2 = t2.value();
     const double mean_b = K + S1 / nb;
     const double m2_b = fmax(0.0, S2 - S1 * S1 / nb);
@@ -69,13 +80,13 @@ reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
   }
 }
 
-__global__ void finalize_kernel(const NodeAcc *acc, int64_t n_nodes, double *mean,
+static __global__ void finalize_kernel(const NodeAcc *acc, int64_t n_nodes, double *mean,
                                 double *se, int64_t *npaths) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n_nodes) return;
   const NodeAcc A = acc[i];
-  mean[i] = A.mean;
-  se[i] = A.n > 1.0 ? sqrt(A.m2 / (A.n - 1.0) / A.n) : 0.0;
+  mean[i] = A.n > 0.0 ? A.mean : static_cast<double>(NAN);  // no sample kept
+  se[i] = A.n > 1.0 ? sqrt(A.m2 / (A.n - 1.0) / A.n) : (A.n > 0.0 ? 0.0 : static_cast<double>(NAN));
   if (npaths) npaths[i] = static_cast<int64_t>(A.n);
 }
 

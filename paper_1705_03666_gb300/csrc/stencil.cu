@@ -1,0 +1,328 @@
+// stencil.cu -- stage two of PDD (Sec. 2.1, Fig. 2.2): the interface
+// interpolator and the subdomain solver for the Laplace problem (Eq. 1.1).
+//
+// 1. spline_kernel: a cubic spline with not-a-knot end conditions through the
+//    interface end points (values of g, which they lie on) and the Monte Carlo
+//    node values (one thread; tridiagonal after eliminating the not-a-knot
+//    rows).
+// 2. fill_kernel: Dirichlet data on the grid boundary -- g on the physical
+//    sides, the spline on the interface side -- and a zero interior.
+// 3. cg_kernel / jacobi_kernel: the 5-point system
+//      (u[i+1,j] - 2u + u[i-1,j]) / hx^2 + (u[i,j+1] - 2u + u[i,j-1]) / hy^2 = 0
+//    by conjugate gradients (one CTA, vectors L2-resident, fixed-order block
+//    reductions) or Jacobi sweeps, both bounded by max_iter.
+#include <cmath>
+#include <cstring>
+
+#include "ctx.hpp"
+
+namespace pdd {
+
+constexpr int kStencilBlock = 1024;
+
+// ---- spline ---------------------------------------------------------------
+// Knots s[0..K] (increasing), values y[0..K], second derivatives M[0..K].
+// Interior rows: h_{i-1} M_{i-1} + 2 (h_{i-1} + h_i) M_i + h_i M_{i+1}
+//                = 6 ((y_{i+1} - y_i)/h_i - (y_i - y_{i-1})/h_{i-1}),
+// not-a-knot:    h_1 M_0 - (h_0 + h_1) M_1 + h_0 M_2 = 0 and the mirror row,
+// which are used to eliminate M_0 and M_K; Thomas algorithm on M_1..M_{K-1}.
+__global__ void spline_kernel(const double *s, const double *y, int K, double *M, double *work) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double *a = work, *b = work + (K + 1), *c = work + 2 * (K + 1), *d = work + 3 * (K + 1);
+  for (int i = 1; i < K; ++i) {
+    const double h0 = s[i] - s[i - 1], h1 = s[i + 1] - s[i];
+    a[i] = h0;
+    b[i] = 2.0 * (h0 + h1);
+    c[i] = h1;
+    d[i] = 6.0 * ((y[i + 1] - y[i]) / h1 - (y[i] - y[i - 1]) / h0);
+  }
+  const double h0 = s[1] - s[0], h1 = s[2] - s[1];
+  const double hl = s[K] - s[K - 1], hm = s[K - 1] - s[K - 2];
+  if (K == 3) {
+    // rows 1 and 2 only; M0 = ((h0+h1) M1 - h0 M2)/h1, M3 = ((hm+hl) M2 - hl M1)/hm
+    const double b1 = b[1] + a[1] * (h0 + h1) / h1, c1 = c[1] - a[1] * h0 / h1;
+    const double a2 = a[2] - c[2] * hl / hm, b2 = b[2] + c[2] * (hm + hl) / hm;
+    const double det = b1 * b2 - c1 * a2;
+    M[1] = (d[1] * b2 - c1 * d[2]) / det;
+    M[2] = (b1 * d[2] - a2 * d[1]) / det;
+  } else {
+    b[1] += a[1] * (h0 + h1) / h1;
+    c[1] -= a[1] * h0 / h1;
+    a[1] = 0.0;
+    b[K - 1] += c[K - 1] * (hm + hl) / hm;
+    a[K - 1] -= c[K - 1] * hl / hm;
+    c[K - 1] = 0.0;
+    for (int i = 2; i < K; ++i) {
+      const double w = a[i] / b[i - 1];
+      b[i] -= w * c[i - 1];
+      d[i] -= w * d[i - 1];
+    }
+    M[K - 1] = d[K - 1] / b[K - 1];
+    for (int i = K - 2; i >= 1; --i) M[i] = (d[i] - c[i] * M[i + 1]) / b[i];
+  }
+  M[0] = ((h0 + h1) * M[1] - h0 * M[2]) / h1;
+  M[K] = ((hm + hl) * M[K - 1] - hl * M[K - 2]) / hm;
+}
+
+__device__ double spline_eval(const double *s, const double *y, const double *M, int K, double t) {
+  int lo = 0, hi = K;
+  while (hi - lo > 1) {  // s[lo] <= t < s[hi]
+    const int mid = (lo + hi) >> 1;
+    if (s[mid] <= t) lo = mid; else hi = mid;
+  }
+  const double h = s[lo + 1] - s[lo];
+  const double A = s[lo + 1] - t, B = t - s[lo];
+  return M[lo] * A * A * A / (6.0 * h) + M[lo + 1] * B * B * B / (6.0 * h) +
+         (y[lo] / h - M[lo] * h / 6.0) * A + (y[lo + 1] / h - M[lo + 1] * h / 6.0) * B;
+}
+
+// Interface knots: s[0] and s[K] are the interface end points, where the data
+// are g; s[1..K-1] are the node coordinates along the interface.
+__global__ void knots_kernel(const double *node_s, const double *vals, int64_t m, double s_lo,
+                             double s_hi, double fixed, int along_axis, double *s, double *y) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i > m + 1) return;
+  if (i == 0 || i == m + 1) {
+    const double t = i == 0 ? s_lo : s_hi;
+    const double x = along_axis == 1 ? fixed : t, yy = along_axis == 1 ? t : fixed;
+    s[i] = t;
+    y[i] = exp(x) * cos(yy);  // g of the Laplace family, Eq. 1.1 data
+  } else {
+    s[i] = node_s[i - 1];
+    y[i] = vals[i - 1];
+  }
+}
+
+// Boundary data and zero interior on an [ny][nx] grid.
+__global__ void fill_kernel(double *u, int nx, int ny, double x0, double y0, double hx,
+                            double hy, int iface_axis, int iface_side, const double *s,
+                            const double *y, const double *M, int K) {
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (idx >= static_cast<int64_t>(nx) * ny) return;
+  const int i = static_cast<int>(idx % nx), j = static_cast<int>(idx / nx);
+  const bool bnd = i == 0 || j == 0 || i == nx - 1 || j == ny - 1;
+  if (!bnd) {
+    u[idx] = 0.0;
+    return;
+  }
+  const double x = x0 + i * hx, yy = y0 + j * hy;
+  bool on_iface;
+  double t;
+  if (iface_axis == 0) {
+    on_iface = i == (iface_side ? nx - 1 : 0);
+    t = yy;
+  } else {
+    on_iface = j == (iface_side ? ny - 1 : 0);
+    t = x;
+  }
+  u[idx] = on_iface ? spline_eval(s, y, M, K, t) : exp(x) * cos(yy);
+}
+
+// ---- block reductions (fixed order) ---------------------------------------
+__device__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kStencilBlock / 32; ++w) t += sh[w];
+    sh[32] = t;
+  }
+  __syncthreads();
+  const double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_max(double v, double *sh) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, m));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kStencilBlock / 32; ++w) t = fmax(t, sh[w]);
+    sh[32] = t;
+  }
+  __syncthreads();
+  const double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// Conjugate gradients on the interior unknowns of A = -Lap_h (SPD).  With the
+// interior initialised to 0, r0 = Lap_h(u) over the full grid = b.
+__global__ void __launch_bounds__(kStencilBlock)
+cg_kernel(double *u, int nx, int ny, double ihx2, double ihy2, double *r, double *p, double *q,
+          int64_t max_iter, double tol, int64_t *iters_out, double *resid_out) {
+  __shared__ double sh[33];
+  const int64_t N = static_cast<int64_t>(nx) * ny;
+  const double diag = 2.0 * ihx2 + 2.0 * ihy2;
+  double rr_loc = 0.0;
+  for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) {
+    const int i = static_cast<int>(k % nx), j = static_cast<int>(k / nx);
+    double v = 0.0;
+    if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1)
+      v = ihx2 * (u[k - 1] + u[k + 1]) + ihy2 * (u[k - nx] + u[k + nx]) - diag * u[k];
+    r[k] = v;
+    p[k] = v;
+    rr_loc += v * v;
+  }
+  double rr = block_sum(rr_loc, sh);
+  const double bnorm = sqrt(rr);
+  int64_t it = 0;
+  double res = bnorm > 0.0 ? 1.0 : 0.0;
+  while (it < max_iter && bnorm > 0.0 && sqrt(rr) > tol * bnorm) {
+    double pq_loc = 0.0;
+    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) {
+      const int i = static_cast<int>(k % nx), j = static_cast<int>(k / nx);
+      double v = 0.0;
+      if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
+        const double pw = i > 1 ? p[k - 1] : 0.0, pe = i < nx - 2 ? p[k + 1] : 0.0;
+        const double ps = j > 1 ? p[k - nx] : 0.0, pn = j < ny - 2 ? p[k + nx] : 0.0;
+        v = diag * p[k] - ihx2 * (pw + pe) - ihy2 * (ps + pn);
+      }
+      q[k] = v;
+      pq_loc += p[k] * v;
+    }
+    const double pq = block_sum(pq_loc, sh);
+    const double alpha = rr / pq;
+    double rn_loc = 0.0;
+    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) {
+      const int i = static_cast<int>(k % nx), j = static_cast<int>(k / nx);
+      if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
+        u[k] += alpha * p[k];
+        const double rk = r[k] - alpha * q[k];
+        r[k] = rk;
+        rn_loc += rk * rk;
+      }
+    }
+    const double rn = block_sum(rn_loc, sh);
+    const double beta = rn / rr;
+    rr = rn;
+    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) p[k] = r[k] + beta * p[k];
+    __syncthreads();
+    ++it;
+    res = sqrt(rr) / bnorm;
+  }
+  if (threadIdx.x == 0) {
+    *iters_out = it;
+    *resid_out = res;
+  }
+}
+
+// Jacobi sweeps u <- (ihx2 (W + E) + ihy2 (S + N)) / diag, ping-pong between
+// u and tmp; stops when the largest update is below tol or after max_iter.
+__global__ void __launch_bounds__(kStencilBlock)
+jacobi_kernel(double *u, double *tmp, int nx, int ny, double ihx2, double ihy2, int64_t max_iter,
+              double tol, int64_t *iters_out, double *resid_out) {
+  __shared__ double sh[33];
+  const int64_t N = static_cast<int64_t>(nx) * ny;
+  const double inv_diag = 1.0 / (2.0 * ihx2 + 2.0 * ihy2);
+  for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) tmp[k] = u[k];
+  __syncthreads();
+  double *src = u, *dst = tmp;
+  int64_t it = 0;
+  double change = 0.0;
+  while (it < max_iter) {
+    double mx = 0.0;
+    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) {
+      const int i = static_cast<int>(k % nx), j = static_cast<int>(k / nx);
+      if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
+        const double v = (ihx2 * (src[k - 1] + src[k + 1]) + ihy2 * (src[k - nx] + src[k + nx])) * inv_diag;
+        mx = fmax(mx, fabs(v - src[k]));
+        dst[k] = v;
+      }
+    }
+    change = block_max(mx, sh);
+    double *t = src;
+    src = dst;
+    dst = t;
+    ++it;
+    if (change < tol) break;
+  }
+  if (src != u)
+    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) u[k] = src[k];
+  if (threadIdx.x == 0) {
+    *iters_out = it;
+    *resid_out = change;
+  }
+}
+
+pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const double *d_iface_s,
+                                const double *d_iface_vals, int64_t m, double *d_u,
+                                int64_t *iters, double *resid) {
+  if (!sd || !d_u || !iters || !resid) return fail(ctx, PDD_EINVAL, "null argument");
+  if (ctx->prob.kind != PDD_PROB_LAPLACE_EXPCOS)
+    return fail(ctx, PDD_EINVAL, "the subdomain solver covers the Laplace family (Eq. 1.1)");
+  const int nx = sd->n[0], ny = sd->n[1];
+  if (nx < 3 || ny < 3 || sd->n[2] != 1) return fail(ctx, PDD_EINVAL, "grid must be 2-D, >= 3x3");
+  if (static_cast<int64_t>(nx) * ny > (int64_t(1) << 26)) return fail(ctx, PDD_EINVAL, "grid too large");
+  if (!(sd->hi[0] > sd->lo[0]) || !(sd->hi[1] > sd->lo[1])) return fail(ctx, PDD_EINVAL, "empty box");
+  if (sd->lo[0] < 0.0 || sd->lo[1] < 0.0 || sd->hi[0] > 1.0 || sd->hi[1] > 1.0)
+    return fail(ctx, PDD_EINVAL, "box must lie in the unit square");
+  if (sd->iface_axis < 0 || sd->iface_axis > 1 || sd->iface_side < 0 || sd->iface_side > 1)
+    return fail(ctx, PDD_EINVAL, "bad interface side");
+  if (m < 2 || !d_iface_s || !d_iface_vals) return fail(ctx, PDD_EINVAL, "need >= 2 interface nodes");
+  if (sd->max_iter < 0 || !(sd->tol >= 0.0)) return fail(ctx, PDD_EINVAL, "bad stopping rule");
+  if (sd->method != PDD_STENCIL_CG && sd->method != PDD_STENCIL_JACOBI)
+    return fail(ctx, PDD_EINVAL, "unknown method");
+  PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int K = static_cast<int>(m) + 1;
+  const size_t npts = static_cast<size_t>(nx) * ny;
+  const size_t knot_bytes = align_up(static_cast<size_t>(K + 1) * sizeof(double), 256);
+  // scratch: s, y, M, work(4 x), then 3 grid vectors, then 2 result words
+  const size_t off_s = 0, off_y = knot_bytes, off_M = 2 * knot_bytes, off_w = 3 * knot_bytes;
+  const size_t off_v = off_w + 4 * knot_bytes;
+  const size_t vec = align_up(npts * sizeof(double), 256);
+  const size_t off_out = off_v + 3 * vec;
+  pdd_status st = ensure_scratch(ctx, off_out + 256);
+  if (st != PDD_OK) return st;
+  char *base = static_cast<char *>(ctx->scratch);
+  double *s = reinterpret_cast<double *>(base + off_s), *y = reinterpret_cast<double *>(base + off_y);
+  double *M = reinterpret_cast<double *>(base + off_M), *w = reinterpret_cast<double *>(base + off_w);
+  double *v0 = reinterpret_cast<double *>(base + off_v);
+  double *v1 = reinterpret_cast<double *>(base + off_v + vec);
+  double *v2 = reinterpret_cast<double *>(base + off_v + 2 * vec);
+  auto *it_d = reinterpret_cast<int64_t *>(base + off_out);
+  auto *res_d = reinterpret_cast<double *>(base + off_out + 8);
+
+  const int ax = sd->iface_axis, along = 1 - ax;
+  const double fixed = sd->iface_side ? sd->hi[ax] : sd->lo[ax];
+  knots_kernel<<<static_cast<unsigned>((m + 2 + 255) / 256), 256, 0, ctx->stream>>>(
+      d_iface_s, d_iface_vals, m, sd->lo[along], sd->hi[along], fixed, along, s, y);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  spline_kernel<<<1, 32, 0, ctx->stream>>>(s, y, K, M, w);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  const double hx = (sd->hi[0] - sd->lo[0]) / (nx - 1), hy = (sd->hi[1] - sd->lo[1]) / (ny - 1);
+  fill_kernel<<<static_cast<unsigned>((npts + 255) / 256), 256, 0, ctx->stream>>>(
+      d_u, nx, ny, sd->lo[0], sd->lo[1], hx, hy, ax, sd->iface_side, s, y, M, K);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  const double ihx2 = 1.0 / (hx * hx), ihy2 = 1.0 / (hy * hy);
+  const auto ev = prof_slot(ctx);
+  if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
+  if (sd->method == PDD_STENCIL_CG)
+    cg_kernel<<<1, kStencilBlock, 0, ctx->stream>>>(d_u, nx, ny, ihx2, ihy2, v0, v1, v2,
+                                                    sd->max_iter, sd->tol, it_d, res_d);
+  else
+    jacobi_kernel<<<1, kStencilBlock, 0, ctx->stream>>>(d_u, v0, nx, ny, ihx2, ihy2,
+                                                        sd->max_iter, sd->tol, it_d, res_d);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
+  int64_t h_it = 0;
+  double h_res = 0.0;
+  PDD_CUDA_TRY(ctx, cudaMemcpyAsync(&h_it, it_d, sizeof h_it, cudaMemcpyDeviceToHost, ctx->stream));
+  PDD_CUDA_TRY(ctx, cudaMemcpyAsync(&h_res, res_d, sizeof h_res, cudaMemcpyDeviceToHost, ctx->stream));
+  PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  *iters = h_it;
+  *resid = h_res;
+  if (h_it >= sd->max_iter && !(h_res <= sd->tol))
+    return fail(ctx, PDD_ETIMEOUT, "stopping rule not met after %lld iterations (%.3e)",
+                static_cast<long long>(h_it), h_res);
+  return PDD_OK;
+}
+
+}  // namespace pdd

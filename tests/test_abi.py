@@ -59,3 +59,5 @@ def test_struct_layouts(lib):
     assert ctypes.sizeof(lib.Problem) == 32
     assert ctypes.sizeof(lib.MCParams) == 48
     assert ctypes.sizeof(lib.Diag) == 32
+    assert ctypes.sizeof(lib.BranchParams) == 40
+    assert ctypes.sizeof(lib.Subdomain) == 88

@@ -1,0 +1,88 @@
+"""GPU checks of stage two (Sec. 2.1): interface spline + subdomain solve,
+against the oracle's SciPy spline and sparse direct solve of the same 5-point
+system, and the whole two-stage PDD of the 2-D Laplace workload against the
+exact harmonic solution."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_03666_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_03666_gb300 import api as a
+    return a
+
+
+def _oracle_subdomain(orc, lo, hi, n, side, s_nodes, vals):
+    nx, ny = n
+    x = np.linspace(lo[0], hi[0], nx)
+    y = np.linspace(lo[1], hi[1], ny)
+    X, Y = np.meshgrid(x, y)
+    u = np.exp(X) * np.cos(Y)
+    u[1:-1, 1:-1] = 0.0
+    col = nx - 1 if side else 0
+    xf = x[col]
+    u[:, col] = orc.spline_interface(s_nodes, vals, y, np.exp(xf) * np.cos(lo[1]),
+                                     np.exp(xf) * np.cos(hi[1]), lo[1], hi[1])
+    return orc.stencil_solve(u, ((hi[0] - lo[0]) / (nx - 1), (hi[1] - lo[1]) / (ny - 1)))
+
+
+@pytest.mark.parametrize("side,lo,hi", [(1, (0.0, 0.0), (0.5, 1.0)), (0, (0.5, 0.0), (1.0, 1.0))])
+def test_cg_matches_direct_solve(api, orc, side, lo, hi):
+    s = W.nodes_cfg1(16)[:, 1]
+    rng = np.random.default_rng(3)
+    vals = np.exp(0.5) * np.cos(s) + 1e-3 * rng.standard_normal(16)   # noisy MC-like data
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.subdomain_solve(lo, hi, (129, 129), 0, side, torch.from_numpy(s),
+                                torch.from_numpy(vals), method="cg", tol=1e-13)
+    ref = _oracle_subdomain(orc, lo, hi, (129, 129), side, s, vals)
+    assert r["status"] == 0 and r["resid"] <= 1e-13
+    assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-10
+
+
+def test_jacobi_matches_direct_solve(api, orc):
+    s = np.array([0.2, 0.45, 0.6, 0.9])
+    vals = np.exp(0.5) * np.cos(s)
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.subdomain_solve((0.0, 0.0), (0.5, 1.0), (17, 33), 0, 1, torch.from_numpy(s),
+                                torch.from_numpy(vals), method="jacobi", tol=1e-14,
+                                max_iter=200000)
+    ref = _oracle_subdomain(orc, (0.0, 0.0), (0.5, 1.0), (17, 33), 1, s, vals)
+    assert r["status"] == 0
+    assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-10
+
+
+def test_iteration_cap_reported(api):
+    s = np.array([0.3, 0.6, 0.8])
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.subdomain_solve((0.0, 0.0), (0.5, 1.0), (65, 65), 0, 1, torch.from_numpy(s),
+                                torch.from_numpy(np.cos(s)), method="jacobi", tol=0.0,
+                                max_iter=10)
+    assert r["status"] == 4 and r["iters"] == 10
+
+
+def test_two_stage_pdd_laplace(api):
+    """Stage one (16 nodes, 1e4 FP64 paths, dt = 1e-3) then stage two on both
+    subdomains (129 x 129, CG): error of the glued solution against e^x cos y
+    is at the Monte Carlo level."""
+    w = W.workload(1)
+    with api.Context(w["prob"]) as ctx:
+        r = ctx.interface_solve(torch.from_numpy(w["nodes"]), seed=w["seed"], dt=w["dt"],
+                                n_paths=w["n_paths"], precision="fp64")
+        s = torch.from_numpy(w["nodes"][:, 1])
+        left = ctx.subdomain_solve((0.0, 0.0), (0.5, 1.0), (129, 129), 0, 1, s, r["mean"])
+        right = ctx.subdomain_solve((0.5, 0.0), (1.0, 1.0), (129, 129), 0, 0, s, r["mean"])
+    se_max = float(r["se"].max())
+    for part, (x0, x1) in ((left, (0.0, 0.5)), (right, (0.5, 1.0))):
+        x = np.linspace(x0, x1, 129)
+        y = np.linspace(0.0, 1.0, 129)
+        X, Y = np.meshgrid(x, y)
+        err = np.max(np.abs(part["u"].cpu().numpy() - np.exp(X) * np.cos(Y)))
+        assert part["status"] == 0
+        assert err < 4.0 * se_max + 1e-3, err
