@@ -62,7 +62,8 @@ enum {
 /* PDE families, written in the paper's elliptic form (Eq. 2.3-2.4 with the
  * time dependence dropped, Sec. 2.2):
  *   (1/2) sigma^2 Lap u + b . grad u + c u + f = 0 in Omega, u = g on dOmega.
- * LAPLACE_EXPCOS          Eq. 1.1 with g = e^x cos y (harmonic), d = 2.
+ * LAPLACE_EXPCOS          Eq. 1.1 with g = e^x cos y (harmonic), d = 2, on the
+ *                         unit square or the L-shape.
  * ELLIPTIC_MANUFACTURED   d = 3, b = (0.5 sin 2 pi y, 0.5 cos 2 pi x, 0),
  *                         c = -1, f chosen so that u = sin(pi x) sin(pi y) e^z,
  *                         g = u on the boundary.
@@ -98,7 +99,7 @@ typedef struct {
 
 typedef struct {
   uint64_t seed;         /* Philox key */
-  double dt;             /* Euler-Maruyama time step (> 0) */
+  double dt;             /* Euler-Maruyama time step (> 0, sigma^2 dt <= 1/36) */
   int64_t n_paths;       /* paths per node (>= 1) */
   int64_t max_steps;     /* per-path step cap (>= 1, <= 2^31-1); capped paths
                             are scored at the nearest face and counted */
@@ -115,6 +116,9 @@ typedef struct {
 typedef struct {
   double *d_path_score;    /* [n * n_paths] or NULL */
   int32_t *d_path_steps;   /* [n * n_paths] or NULL */
+  double *d_path_aux;      /* pdd_interface_grad only: [n * n_paths][18] per-path
+                              exit point (x, y) and likelihood-ratio sums
+                              L_1..L_16, or NULL */
   int64_t path_steps;      /* out */
   int64_t capped;          /* out */
 } pdd_diag;
@@ -151,6 +155,73 @@ PDD_API pdd_status pdd_interface_solve(pdd_ctx *ctx, const double *d_nodes, int6
                                const pdd_mc_params *mc, double *d_mean,
                                double *d_se, int64_t *d_npaths,
                                pdd_diag *diag);
+
+/* Derivatives of stage one (POISSON_FOURIER family, FP32 paths): for each
+ * node the Jacobian row of the estimate with respect to theta (64 Fourier
+ * weights of g) and phi (16 drift weights), computed on the same paths as
+ * pdd_interface_solve with the same mc (the paths are re-simulated from their
+ * Philox keys; nothing is kept from the forward call):
+ *   J[i][k]      = E[cos(m pi X_tau,x) cos(n pi X_tau,y)], k = 8m + n (exact
+ *                  pathwise derivative: the paths do not depend on theta);
+ *   J[i][64 + j] = E[s L_j], L_j = sum over the steps of xi . db/dphi_j(X)
+ *                  sqrt(dt)/sigma (likelihood ratio of the Euler-Maruyama
+ *                  transition density; the exit rule does not depend on phi).
+ * d_jac / d_jac_se ([n][80] FP64, optional) receive J and its standard errors.
+ * With d_grad_out ([n] FP64 cotangent) the vector-Jacobian products
+ * d_dtheta[64] = sum_i w_i J[i][0:64] and d_dphi[16] = sum_i w_i J[i][64:80]
+ * are written (either may be NULL).  Optional diag as for
+ * pdd_interface_solve, plus d_path_aux.                                    */
+PDD_API pdd_status pdd_interface_grad(pdd_ctx *ctx, const double *d_nodes,
+                                      int64_t n, const pdd_mc_params *mc,
+                                      const double *d_grad_out, double *d_jac,
+                                      double *d_jac_se, double *d_dtheta,
+                                      double *d_dphi, pdd_diag *diag);
+
+/* Replace the problem's parameters (same family and length), e.g. new
+ * theta/phi between forward evaluations.  Host array, copied.             */
+PDD_API pdd_status pdd_set_params(pdd_ctx *ctx, const double *params,
+                                  int32_t n_params);
+
+/* Batched, variance-adaptive stage one over a heterogeneous node set.
+ * Nodes may belong to different problems (up to 4 pdd_problem entries:
+ * LAPLACE_EXPCOS on the unit square or the L-shape, ELLIPTIC_MANUFACTURED on
+ * the unit cube, POISSON_FOURIER on the unit square) and carry their own
+ * time step.  Per node i (paths are FP32, sums FP64):
+ *   1. a pilot of n_pilot paths gives the sample variance s_i^2;
+ *   2. N_i = clamp(ceil(s_i^2 / target_se^2), max(n_min, n_pilot), n_max);
+ *   3. paths n_pilot .. N_i - 1 are added and the estimate uses all N_i.
+ * Node i's path p uses the same Philox stream as pdd_interface_solve
+ * (counter = (block, p, i, 0)).  The work list of the second pass is built
+ * on the device, and one persistent launch consumes it (lanes take chunks of
+ * `chunk` consecutive paths of one node), so the call has no host round trip.
+ * With use_graph != 0 the whole sequence is captured once into a CUDA graph
+ * (rebuilt when any argument or the scratch changes) and replayed; this
+ * needs a non-default stream.  Writes d_mean[n], d_se[n] and, if non-NULL,
+ * d_npaths[n] (= N_i).  diag (optional) reports total steps / capped paths
+ * and synchronises.                                                        */
+typedef struct {
+  const double *d_nodes;     /* [n][3] FP64 (z ignored by 2-D problems) */
+  const int32_t *d_problem;  /* [n] index into the problems array */
+  const double *d_dt;        /* [n] Euler-Maruyama step, sigma^2 dt <= 1/36 */
+  int64_t n;
+} pdd_batch_nodes;
+
+typedef struct {
+  uint64_t seed;
+  int64_t n_pilot;           /* pilot paths per node (>= 2) */
+  int64_t n_min, n_max;      /* clamp of the adaptive path count */
+  double target_se;          /* standard error aimed for (> 0) */
+  int64_t max_steps;         /* per-path step cap */
+  int32_t chunk;             /* paths per lane-chunk (0 = tuned default) */
+  int32_t bridge;            /* Brownian-bridge exit test on/off */
+} pdd_batch_params;
+
+PDD_API pdd_status pdd_batch_solve(pdd_ctx *ctx, const pdd_problem *problems,
+                                   int32_t n_problems,
+                                   const pdd_batch_nodes *nodes,
+                                   const pdd_batch_params *bp, double *d_mean,
+                                   double *d_se, int64_t *d_npaths,
+                                   int32_t use_graph, pdd_diag *diag);
 
 /* Monte Carlo parameters of the branching estimator. */
 typedef struct {

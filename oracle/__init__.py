@@ -91,7 +91,7 @@ def _load():
                                                 ctypes.c_int64, dp, dp, lp, dp,
                                                 ip, lp, lp]
             lib.orc_interface_solve.restype = ctypes.c_int
-            lib.orc_interface_jacobian.argtypes = [P, dp, ctypes.c_int64, M, dp, dp]
+            lib.orc_interface_jacobian.argtypes = [P, dp, ctypes.c_int64, M, dp, dp, dp, ip]
             lib.orc_interface_jacobian.restype = ctypes.c_int
             lib.orc_jacobian_width.argtypes = [P]
             lib.orc_jacobian_width.restype = ctypes.c_int
@@ -217,11 +217,12 @@ def interface_solve(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
 
 
 def interface_jacobian(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
-                       bridge=True, n_threads=None):
+                       bridge=True, n_threads=None, dump_paths=False):
     """Per-node derivatives of u w.r.t. the family's parameters: theta (linear
     boundary data, exact pathwise) then phi (drift, likelihood ratio).
     Poisson-Fourier: [n, 64 + 16]; poly1d: [n, 2 + 2] for (g0, g1, b0, b1).
-    Returns (jac, jac_se)."""
+    Returns (jac, jac_se), or with dump_paths (jac, jac_se, rec, steps): rec
+    is [n, N, 4 + n_phi] per path (score, exit point x, y, z, L_1..L_nphi)."""
     lib = _load()
     d = int(prob["dim"])
     nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, d)
@@ -230,11 +231,17 @@ def interface_jacobian(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
     W = lib.orc_jacobian_width(ctypes.byref(P))
     M = _mc(seed, dt, n_paths, max_steps, bridge, n_threads)
     jac, jse = np.zeros((n, W)), np.zeros((n, W))
+    nphi = {"poisson_fourier": 16, "poly1d": 2}.get(prob["problem"], 0)
+    rec = np.zeros((n, int(n_paths), 4 + nphi)) if dump_paths else None
+    steps = np.zeros((n, int(n_paths)), dtype=np.int32) if dump_paths else None
     rc = lib.orc_interface_jacobian(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n,
                                     ctypes.byref(M), _ptr(jac, ctypes.c_double),
-                                    _ptr(jse, ctypes.c_double))
+                                    _ptr(jse, ctypes.c_double), _ptr(rec, ctypes.c_double),
+                                    _ptr(steps, ctypes.c_int32))
     if rc != 0:
         raise ValueError("oracle interface_jacobian: invalid arguments")
+    if dump_paths:
+        return jac, jse, rec, steps
     return jac, jse
 
 

@@ -659,6 +659,8 @@ typedef struct {
   const double *nodes;
   double *jac;    /* [n][W] */
   double *jac_se; /* [n][W] or NULL */
+  double *rec;    /* [n][N][4 + n_phi]: s, exit point (3), L_j; or NULL */
+  int32_t *steps; /* [n][N] or NULL */
 } grad_ctx;
 
 static void grad_node(void *vp, int64_t i) {
@@ -673,6 +675,12 @@ static void grad_node(void *vp, int64_t i) {
     int32_t st;
     simulate_path(P, G->M, (uint32_t)i, (uint32_t)p, G->nodes + i * P->dim, &s,
                   &st, xe, L, &ye);
+    if (G->rec) {
+      double *r = G->rec + ((size_t)i * (size_t)N + (size_t)p) * (size_t)(4 + np_);
+      r[0] = s; r[1] = xe[0]; r[2] = xe[1]; r[3] = xe[2];
+      for (int j = 0; j < np_; ++j) r[4 + j] = L[j];
+    }
+    if (G->steps) G->steps[i * N + p] = st;
     for (int k = 0; k < nt; ++k) v[k] = g_dtheta(P, k, xe) * ye;
     for (int j = 0; j < np_; ++j) v[nt + j] = s * L[j];
     for (int k = 0; k < W; ++k) {
@@ -692,11 +700,12 @@ static void grad_node(void *vp, int64_t i) {
 int orc_jacobian_width(const orc_problem *P) { return n_theta(P) + n_phi(P); }
 
 int orc_interface_jacobian(const orc_problem *P, const double *nodes, int64_t n,
-                           const orc_mc *M, double *jac, double *jac_se) {
+                           const orc_mc *M, double *jac, double *jac_se,
+                           double *path_rec, int32_t *path_steps) {
   if (!P || !M || M->n_paths < 1 || n_theta(P) + n_phi(P) == 0 ||
       P->n_params < (P->kind == ORC_PROB_POISSON_FOURIER ? 80 : 7))
     return 1;
-  grad_ctx G = {P, M, nodes, jac, jac_se};
+  grad_ctx G = {P, M, nodes, jac, jac_se, path_rec, path_steps};
   parallel_for(n, M->n_threads, grad_node, &G);
   return 0;
 }

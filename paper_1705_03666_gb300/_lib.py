@@ -46,9 +46,22 @@ class Subdomain(ctypes.Structure):
                 ("max_iter", ctypes.c_int64), ("tol", ctypes.c_double)]
 
 
+class BatchNodes(ctypes.Structure):
+    _fields_ = [("d_nodes", ctypes.c_void_p), ("d_problem", ctypes.c_void_p),
+                ("d_dt", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_pilot", ctypes.c_int64),
+                ("n_min", ctypes.c_int64), ("n_max", ctypes.c_int64),
+                ("target_se", ctypes.c_double), ("max_steps", ctypes.c_int64),
+                ("chunk", ctypes.c_int32), ("bridge", ctypes.c_int32)]
+
+
 class Diag(ctypes.Structure):
     _fields_ = [("d_path_score", ctypes.c_void_p), ("d_path_steps", ctypes.c_void_p),
-                ("path_steps", ctypes.c_int64), ("capped", ctypes.c_int64)]
+                ("d_path_aux", ctypes.c_void_p), ("path_steps", ctypes.c_int64),
+                ("capped", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -70,6 +83,12 @@ _SIGS = {
     "pdd_subdomain_solve": (ctypes.c_int, [_VP, ctypes.POINTER(Subdomain), _VP, _VP, _I64, _VP,
                                            ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_double)]),
+    "pdd_interface_grad": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(MCParams), _VP, _VP,
+                                          _VP, _VP, _VP, ctypes.POINTER(Diag)]),
+    "pdd_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
+    "pdd_batch_solve": (ctypes.c_int, [_VP, ctypes.POINTER(Problem), ctypes.c_int32,
+                                       ctypes.POINTER(BatchNodes), ctypes.POINTER(BatchParams),
+                                       _VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(Diag)]),
     "pdd_philox_stream": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _U32, _I64, _VP]),
     "pdd_destroy": (None, [_VP]),
     "pdd_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -183,6 +183,101 @@ class Context:
         status = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ETIMEOUT))
         return {"u": u, "iters": it.value, "resid": res.value, "status": status}
 
+    def set_params(self, params):
+        """pdd_set_params: new parameter values for the same family."""
+        arr = np.ascontiguousarray(params, dtype=np.float64).reshape(-1)
+        _lib.check(self.lib.pdd_set_params(self.handle,
+                                           arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           int(arr.size)), self.handle)
+        self._params = arr
+        self.prob = dict(self.prob, params=arr)
+
+    def interface_grad(self, nodes, *, seed: int, dt: float, n_paths: int, grad_out=None,
+                       jacobian: bool = True, max_steps: int = 2**31 - 1, bridge: bool = True,
+                       path_offset: int = 0, dump_paths: bool = False, diag: bool = False) -> dict:
+        """pdd_interface_grad: jac/jac_se [n, 80] and, with grad_out [n], dtheta [64]
+        and dphi [16] (all float64 CUDA tensors)."""
+        dim = int(self.prob["dim"])
+        nodes = _dev_f64(nodes, self.device).reshape(-1, dim)
+        n = nodes.shape[0]
+        res = {}
+        jac = jse = gout = dth = dph = None
+        if jacobian:
+            jac = res["jac"] = torch.empty((n, 80), dtype=_F64, device=self.device)
+            jse = res["jac_se"] = torch.empty((n, 80), dtype=_F64, device=self.device)
+        if grad_out is not None:
+            gout = _dev_f64(grad_out, self.device).reshape(-1)
+            if gout.numel() != n:
+                raise ValueError("grad_out must have one entry per node")
+            dth = res["dtheta"] = torch.empty(64, dtype=_F64, device=self.device)
+            dph = res["dphi"] = torch.empty(16, dtype=_F64, device=self.device)
+        mc = _lib.MCParams(int(seed) & (2**64 - 1), float(dt), int(n_paths), int(max_steps),
+                           int(path_offset), _lib.PRECISION["fp32"], int(bool(bridge)))
+        dg = None
+        if diag or dump_paths:
+            dg = _lib.Diag()
+            if dump_paths:
+                res["score"] = torch.empty((n, int(n_paths)), dtype=_F64, device=self.device)
+                res["steps"] = torch.empty((n, int(n_paths)), dtype=_I32, device=self.device)
+                res["aux"] = torch.empty((n, int(n_paths), 18), dtype=_F64, device=self.device)
+                dg.d_path_score = res["score"].data_ptr()
+                dg.d_path_steps = res["steps"].data_ptr()
+                dg.d_path_aux = res["aux"].data_ptr()
+        ptr = lambda t: t.data_ptr() if t is not None else None
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_interface_grad(self.handle, nodes.data_ptr(), n, ctypes.byref(mc),
+                                             ptr(gout), ptr(jac), ptr(jse), ptr(dth), ptr(dph),
+                                             ctypes.byref(dg) if dg is not None else None)
+        res["status"] = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ECAP))
+        if dg is not None:
+            res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
+        return res
+
+    def batch_solve(self, problems, nodes, problem_index, dt, *, seed: int, n_pilot: int,
+                    n_min: int, n_max: int, target_se: float, max_steps: int = 2**31 - 1,
+                    chunk: int = 0, bridge: bool = True, use_graph: bool = False,
+                    diag: bool = False, out=None) -> dict:
+        """pdd_batch_solve: problems is a list of workload dicts; nodes [n, 3]
+        float64, problem_index [n] int32, dt [n] float64 (CUDA or CPU tensors)."""
+        probs = []
+        keep = []
+        for pr in problems:
+            prm = np.ascontiguousarray(pr.get("params", np.zeros(0)), dtype=np.float64)
+            buf = prm if prm.size else np.zeros(1)
+            keep.append(buf)
+            probs.append(_lib.Problem(_lib.PROBLEM[pr["problem"]], _lib.GEOMETRY[pr["geometry"]],
+                                      int(pr["dim"]), int(prm.size),
+                                      buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      float(pr.get("sigma", 1.0))))
+        arr = (_lib.Problem * len(probs))(*probs)
+        nodes = _dev_f64(nodes, self.device).reshape(-1, 3)
+        pidx = torch.as_tensor(problem_index, dtype=torch.int32).to(self.device).contiguous()
+        dts = _dev_f64(dt, self.device).reshape(-1)
+        n = nodes.shape[0]
+        if out is None:
+            mean = torch.empty(n, dtype=_F64, device=self.device)
+            se = torch.empty(n, dtype=_F64, device=self.device)
+            cnt = torch.empty(n, dtype=_I64, device=self.device)
+        else:
+            mean, se, cnt = out
+        bn = _lib.BatchNodes(nodes.data_ptr(), pidx.data_ptr(), dts.data_ptr(), n)
+        bp = _lib.BatchParams(int(seed) & (2**64 - 1), int(n_pilot), int(n_min), int(n_max),
+                              float(target_se), int(max_steps), int(chunk), int(bool(bridge)))
+        dg = _lib.Diag() if diag else None
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_batch_solve(self.handle, arr, len(probs), ctypes.byref(bn),
+                                          ctypes.byref(bp), mean.data_ptr(), se.data_ptr(),
+                                          cnt.data_ptr(), int(bool(use_graph)),
+                                          ctypes.byref(dg) if dg is not None else None)
+        res = {"mean": mean, "se": se, "n": cnt,
+               "status": _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ECAP)),
+               "_keep": (nodes, pidx, dts)}
+        if dg is not None:
+            res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
+        return res
+
     def philox_stream(self, seed: int, j0: int, c1: int, c2: int, c3: int, n_blocks: int):
         """pdd_philox_stream: uint32 [n_blocks, 4] CUDA tensor."""
         out = torch.empty((int(n_blocks), 4), dtype=torch.int32, device=self.device)
@@ -202,3 +297,37 @@ def interface_solve_host(prob: dict, nodes: np.ndarray, **kw) -> dict:
         h = torch.from_numpy(np.ascontiguousarray(nodes, dtype=np.float64)).pin_memory()
         r = ctx.interface_solve(h, **kw)
         return {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in r.items()}
+
+
+class InterfaceValues(torch.autograd.Function):
+    """u(nodes; theta, phi) for the Poisson-Fourier family as a differentiable
+    function of (theta [64], phi [16]).  Forward: pdd_interface_solve with the
+    given parameters.  Backward: pdd_interface_grad with the incoming
+    cotangent, on the same random streams (paths re-simulated from their
+    Philox keys, nothing stored)."""
+
+    @staticmethod
+    def forward(fctx, theta, phi, pdd_ctx, nodes, mc):
+        params = torch.cat([theta.detach().reshape(-1), phi.detach().reshape(-1)])
+        params = params.to("cpu", torch.float64).numpy()
+        pdd_ctx.set_params(params)
+        r = pdd_ctx.interface_solve(nodes, precision="fp32", **mc)
+        fctx.pdd_ctx, fctx.nodes, fctx.mc, fctx.params = pdd_ctx, nodes, mc, params
+        fctx.devices = (theta.device, phi.device)
+        fctx.dtypes = (theta.dtype, phi.dtype)
+        return r["mean"].clone()
+
+    @staticmethod
+    def backward(fctx, grad_u):
+        pdd_ctx = fctx.pdd_ctx
+        pdd_ctx.set_params(fctx.params)
+        g = pdd_ctx.interface_grad(fctx.nodes, grad_out=grad_u.detach().to(torch.float64),
+                                   jacobian=False, **fctx.mc)
+        dth = g["dtheta"].to(fctx.devices[0], fctx.dtypes[0])
+        dph = g["dphi"].to(fctx.devices[1], fctx.dtypes[1])
+        return dth, dph, None, None, None
+
+
+def interface_values(theta, phi, pdd_ctx: Context, nodes, **mc):
+    """Differentiable node estimates (see InterfaceValues)."""
+    return InterfaceValues.apply(theta, phi, pdd_ctx, nodes, mc)

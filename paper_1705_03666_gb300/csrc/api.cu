@@ -25,8 +25,8 @@ const char *check_problem(const pdd_problem *p) {
   if (!finite_params(p)) return "non-finite parameter";
   switch (p->kind) {
     case PDD_PROB_LAPLACE_EXPCOS:
-      if (p->dim != 2 || p->geometry != PDD_GEOM_UNIT_SQUARE)
-        return "LAPLACE_EXPCOS needs dim 2 on the unit square";
+      if (p->dim != 2 || (p->geometry != PDD_GEOM_UNIT_SQUARE && p->geometry != PDD_GEOM_L_SHAPE))
+        return "LAPLACE_EXPCOS needs dim 2 on the unit square or the L-shape";
       return nullptr;
     case PDD_PROB_ELLIPTIC_MANUFACTURED:
       if (p->dim != 3 || p->geometry != PDD_GEOM_UNIT_CUBE)
@@ -139,6 +139,43 @@ pdd_status pdd_subdomain_solve(pdd_ctx *ctx, const pdd_subdomain *sd, const doub
   return pdd::subdomain_solve_impl(ctx, sd, d_iface_s, d_iface_vals, m, d_u, iters, resid);
 }
 
+pdd_status pdd_interface_grad(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                              const pdd_mc_params *mc, const double *d_grad_out, double *d_jac,
+                              double *d_jac_se, double *d_dtheta, double *d_dphi,
+                              pdd_diag *diag) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::interface_grad_impl(ctx, d_nodes, n, mc, d_grad_out, d_jac, d_jac_se, d_dtheta,
+                                  d_dphi, diag);
+}
+
+pdd_status pdd_set_params(pdd_ctx *ctx, const double *params, int32_t n_params) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  if (n_params != ctx->prob.n_params) return fail(ctx, PDD_EINVAL, "n_params differs");
+  if (n_params > 0 && !params) return fail(ctx, PDD_EINVAL, "params is NULL");
+  pdd_problem p = ctx->prob;
+  p.params = params;
+  if (const char *why = check_problem(&p)) return fail(ctx, PDD_EINVAL, "%s", why);
+  ctx->params.assign(params, params + n_params);
+  ctx->prob.params = ctx->params.data();
+  for (int i = 0; i < n_params; ++i) {
+    ctx->mc.prm[i] = params[i];
+    ctx->mc.prmf[i] = static_cast<float>(params[i]);
+  }
+  return PDD_OK;
+}
+
+pdd_status pdd_batch_solve(pdd_ctx *ctx, const pdd_problem *problems, int32_t n_problems,
+                           const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
+                           double *d_mean, double *d_se, int64_t *d_npaths, int32_t use_graph,
+                           pdd_diag *diag) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::batch_solve_impl(ctx, problems, n_problems, nodes, bp, d_mean, d_se, d_npaths,
+                               use_graph, diag);
+}
+
 pdd_status pdd_profile(pdd_ctx *ctx, int enable) {
   if (!ctx) return PDD_EINVAL;
   ctx->profiling = enable != 0;
@@ -175,6 +212,7 @@ void pdd_destroy(pdd_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
   for (auto &e : ctx->prof_events) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);

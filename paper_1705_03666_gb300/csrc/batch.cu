@@ -1,0 +1,351 @@
+// batch.cu -- pdd_batch_solve: variance-adaptive interface solve over a
+// heterogeneous batch of nodes, as one device-driven pipeline that can be
+// captured once in a CUDA graph and replayed.
+//
+//   1. pilot: n_pilot paths per node (lane-chunk queue, batch_kernel);
+//   2. per node: pilot mean and variance s^2, path count
+//      N_i = clamp(ceil(s^2 / SE*^2), max(n_min, n_pilot), n_max);
+//   3. exclusive scan of the per-node chunk counts of paths [n_pilot, N_i);
+//   4. main pass over that device-built work list (same persistent kernel);
+//   5. per node: pilot and main partials merged in chunk order (Chan).
+// Paths [0, N_i) of node i are the streams pdd_interface_solve would use, so
+// the pilot paths are part of the final estimate.
+#include <cmath>
+#include <cstring>
+
+#include "batch_kernel.cuh"
+#include "ctx.hpp"
+#include "reduce.cuh"
+
+namespace pdd {
+
+constexpr int kScanBlock = 1024;
+
+// Pilot work list: every node gets paths [0, n_pilot).
+__global__ void batch_pilot_setup(int64_t n, int64_t n_pilot, int32_t K, int64_t *chunk_off,
+                                  int64_t *first, int64_t *end, double *shift) {
+  const int64_t cpn = (n_pilot + K - 1) / K;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i <= n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    chunk_off[i] = i * cpn;
+    if (i < n) {
+      first[i] = 0;
+      end[i] = n_pilot;
+      shift[i] = 0.0;
+    }
+  }
+}
+
+// Per node: merge the pilot chunk partials (fixed order) into (n, mean, M2),
+// choose N_i and write the main work list's per-node entries.
+__global__ void batch_pilot_stats(int64_t n, int64_t n_pilot, int32_t K, const ChunkPartial *part,
+                                  double inv_se2, int64_t n_min, int64_t n_max, NodeAcc *pilot,
+                                  int64_t *first2, int64_t *end2, double *shift2, int64_t *count2) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const int64_t cpn = (n_pilot + K - 1) / K;
+  double nt = 0.0, mean = 0.0, m2 = 0.0;
+  for (int64_t c = 0; c < cpn; ++c) {
+    const ChunkPartial P = part[i * cpn + c];
+    if (P.n <= 0.0) continue;
+    const double mb = P.s1 / P.n;
+    const double m2b = fmax(0.0, P.s2 - P.s1 * mb);
+    const double tot = nt + P.n, d = mb - mean;
+    mean += d * (P.n / tot);
+    m2 += m2b + d * d * (nt * P.n / tot);
+    nt = tot;
+  }
+  pilot[i] = NodeAcc{nt, mean, m2};
+  const double var = nt > 1.0 ? m2 / (nt - 1.0) : 0.0;
+  double want = ceil(var * inv_se2);
+  const int64_t lo = max(n_min, n_pilot);
+  int64_t Ni = want >= static_cast<double>(n_max) ? n_max : static_cast<int64_t>(want);
+  Ni = max(lo, min(n_max, Ni));
+  if (isnan(var)) Ni = lo;
+  first2[i] = n_pilot;
+  end2[i] = Ni;
+  shift2[i] = mean;
+  count2[i] = (Ni - n_pilot + K - 1) / K;
+}
+
+// Exclusive scan of count[0..n) into off[0..n] (single block, fixed order).
+__global__ void __launch_bounds__(kScanBlock)
+batch_scan(int64_t n, const int64_t *count, int64_t *off) {
+  __shared__ int64_t part[kScanBlock];
+  const int64_t per = (n + kScanBlock - 1) / kScanBlock;
+  const int64_t b = threadIdx.x * per, e = min(n, b + per);
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += count[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int t = 0; t < kScanBlock; ++t) {
+      const int64_t v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+    off[n] = acc;
+  }
+  __syncthreads();
+  int64_t acc = part[threadIdx.x];
+  for (int64_t i = b; i < e; ++i) {
+    off[i] = acc;
+    acc += count[i];
+  }
+}
+
+// Per node: pilot triple merged with the main chunk partials (shifted by the
+// pilot mean) in chunk order; writes mean, standard error and path count.
+__global__ void batch_final(int64_t n, const NodeAcc *pilot, const int64_t *off2,
+                            const double *shift2, const ChunkPartial *part2, double *mean_out,
+                            double *se_out, int64_t *n_out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const NodeAcc A = pilot[i];
+  double nt = A.n, mean = A.mean, m2 = A.m2;
+  const double K = shift2[i];
+  for (int64_t c = off2[i]; c < off2[i + 1]; ++c) {
+    const ChunkPartial P = part2[c];
+    if (P.n <= 0.0) continue;
+    const double mb_shift = P.s1 / P.n;
+    const double mb = K + mb_shift;
+    const double m2b = fmax(0.0, P.s2 - P.s1 * mb_shift);
+    const double tot = nt + P.n, d = mb - mean;
+    mean += d * (P.n / tot);
+    m2 += m2b + d * d * (nt * P.n / tot);
+    nt = tot;
+  }
+  mean_out[i] = mean;
+  se_out[i] = nt > 1.0 ? sqrt(m2 / (nt - 1.0) / nt) : 0.0;
+  if (n_out) n_out[i] = static_cast<int64_t>(nt);
+}
+
+namespace {
+
+int combo_of(const pdd_problem &p) {
+  if (p.kind == PDD_PROB_LAPLACE_EXPCOS && p.dim == 2 && p.geometry == PDD_GEOM_UNIT_SQUARE)
+    return kComboSquareLaplace;
+  if (p.kind == PDD_PROB_LAPLACE_EXPCOS && p.dim == 2 && p.geometry == PDD_GEOM_L_SHAPE)
+    return kComboLShapeLaplace;
+  if (p.kind == PDD_PROB_ELLIPTIC_MANUFACTURED && p.dim == 3 && p.geometry == PDD_GEOM_UNIT_CUBE)
+    return kComboCubeElliptic;
+  if (p.kind == PDD_PROB_POISSON_FOURIER && p.dim == 2 && p.geometry == PDD_GEOM_UNIT_SQUARE &&
+      p.n_params >= 80)
+    return kComboSquarePoisson;
+  return -1;
+}
+
+struct BatchLayout {
+  size_t off_first, off_end, off_shift, off_chunk, off_first2, off_end2, off_shift2, off_cnt2,
+      off_chunk2, off_pilot, off_part, off_part2, total;
+  int64_t pilot_chunks, main_chunks_max;
+};
+
+BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K) {
+  BatchLayout L;
+  size_t o = 256;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  const size_t nn = static_cast<size_t>(n);
+  L.off_first = take(nn * 8);
+  L.off_end = take(nn * 8);
+  L.off_shift = take(nn * 8);
+  L.off_chunk = take((nn + 1) * 8);
+  L.off_first2 = take(nn * 8);
+  L.off_end2 = take(nn * 8);
+  L.off_shift2 = take(nn * 8);
+  L.off_cnt2 = take(nn * 8);
+  L.off_chunk2 = take((nn + 1) * 8);
+  L.off_pilot = take(nn * sizeof(NodeAcc));
+  L.pilot_chunks = n * ((bp->n_pilot + K - 1) / K);
+  const int64_t extra = std::max<int64_t>(0, bp->n_max - bp->n_pilot);
+  L.main_chunks_max = n * ((extra + K - 1) / K);
+  L.off_part = take(static_cast<size_t>(L.pilot_chunks) * sizeof(ChunkPartial));
+  L.off_part2 = take(static_cast<size_t>(std::max<int64_t>(1, L.main_chunks_max)) *
+                     sizeof(ChunkPartial));
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const BatchLayout &Lay,
+                                const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
+                                int32_t K, unsigned grid, double *d_mean, double *d_se,
+                                int64_t *d_npaths) {
+  char *base = static_cast<char *>(ctx->scratch);
+  auto *counters = reinterpret_cast<unsigned long long *>(base);
+  auto *cursor = counters + 4;
+  auto *first = reinterpret_cast<int64_t *>(base + Lay.off_first);
+  auto *end = reinterpret_cast<int64_t *>(base + Lay.off_end);
+  auto *shift = reinterpret_cast<double *>(base + Lay.off_shift);
+  auto *chunk = reinterpret_cast<int64_t *>(base + Lay.off_chunk);
+  auto *first2 = reinterpret_cast<int64_t *>(base + Lay.off_first2);
+  auto *end2 = reinterpret_cast<int64_t *>(base + Lay.off_end2);
+  auto *shift2 = reinterpret_cast<double *>(base + Lay.off_shift2);
+  auto *cnt2 = reinterpret_cast<int64_t *>(base + Lay.off_cnt2);
+  auto *chunk2 = reinterpret_cast<int64_t *>(base + Lay.off_chunk2);
+  auto *pilot = reinterpret_cast<NodeAcc *>(base + Lay.off_pilot);
+  auto *part = reinterpret_cast<ChunkPartial *>(base + Lay.off_part);
+  auto *part2 = reinterpret_cast<ChunkPartial *>(base + Lay.off_part2);
+  const int64_t n = nodes->n;
+  const unsigned nb = static_cast<unsigned>((n + 255) / 256);
+
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, 256, ctx->stream));
+  batch_pilot_setup<<<nb + 1, 256, 0, ctx->stream>>>(n, bp->n_pilot, K, chunk, first, end, shift);
+  BatchArgs a = proto;
+  a.chunk_off = chunk;
+  a.first = first;
+  a.end = end;
+  a.shift = shift;
+  a.cursor = cursor;
+  a.counters = counters;
+  a.partial = part;
+  batch_kernel<<<grid, kBatchBlock, 0, ctx->stream>>>(a);
+  batch_pilot_stats<<<nb, 256, 0, ctx->stream>>>(n, bp->n_pilot, K, part,
+                                                 1.0 / (bp->target_se * bp->target_se),
+                                                 bp->n_min, bp->n_max, pilot, first2, end2, shift2,
+                                                 cnt2);
+  batch_scan<<<1, kScanBlock, 0, ctx->stream>>>(n, cnt2, chunk2);
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), ctx->stream));
+  a.chunk_off = chunk2;
+  a.first = first2;
+  a.end = end2;
+  a.shift = shift2;
+  a.partial = part2;
+  const auto ev = prof_slot(ctx);
+  if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
+  batch_kernel<<<grid, kBatchBlock, 0, ctx->stream>>>(a);
+  if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
+  batch_final<<<nb, 256, 0, ctx->stream>>>(n, pilot, chunk2, shift2, part2, d_mean, d_se,
+                                           d_npaths);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  return PDD_OK;
+}
+
+pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n_problems,
+                            const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
+                            double *d_mean, double *d_se, int64_t *d_npaths, int32_t use_graph,
+                            pdd_diag *diag) {
+  if (!problems || !nodes || !bp) return fail(ctx, PDD_EINVAL, "null argument");
+  if (n_problems < 1 || n_problems > kMaxBatchProblems)
+    return fail(ctx, PDD_EINVAL, "n_problems must be in [1, %d]", kMaxBatchProblems);
+  if (nodes->n < 0 || nodes->n > (int64_t(1) << 31)) return fail(ctx, PDD_EINVAL, "n out of range");
+  if (bp->n_pilot < 2 || bp->n_min < 1 || bp->n_max < bp->n_pilot || bp->n_max < bp->n_min)
+    return fail(ctx, PDD_EINVAL, "need 2 <= n_pilot <= n_max and n_min <= n_max");
+  if (bp->n_max > (int64_t(1) << 32)) return fail(ctx, PDD_EINVAL, "n_max above 2^32");
+  if (!(bp->target_se > 0.0) || !std::isfinite(bp->target_se))
+    return fail(ctx, PDD_EINVAL, "target_se must be > 0");
+  if (bp->max_steps < 1 || bp->max_steps > 2147483647LL)
+    return fail(ctx, PDD_EINVAL, "max_steps out of range");
+  if (bp->chunk < 0 || bp->chunk > (1 << 20)) return fail(ctx, PDD_EINVAL, "chunk out of range");
+  if (nodes->n > 0 && (!nodes->d_nodes || !nodes->d_problem || !nodes->d_dt || !d_mean || !d_se))
+    return fail(ctx, PDD_EINVAL, "null buffer");
+  BatchArgs proto;
+  std::memset(&proto, 0, sizeof proto);
+  for (int p = 0; p < n_problems; ++p) {
+    const pdd_problem &P = problems[p];
+    const int combo = combo_of(P);
+    if (combo < 0) return fail(ctx, PDD_EINVAL, "problem %d has no batch kernel", p);
+    if (!(P.sigma > 0.0) || !std::isfinite(P.sigma)) return fail(ctx, PDD_EINVAL, "sigma");
+    if (P.n_params < 0 || P.n_params > kMaxParams || (P.n_params > 0 && !P.params))
+      return fail(ctx, PDD_EINVAL, "params");
+    BatchProblem &B = proto.probs[p];
+    B.combo = combo;
+    B.bridge = bp->bridge ? 1 : 0;
+    B.sigma = P.sigma;
+    B.c_kill = P.kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0;
+    B.mc.n_params = P.n_params;
+    for (int i = 0; i < P.n_params; ++i) {
+      if (!std::isfinite(P.params[i])) return fail(ctx, PDD_EINVAL, "non-finite parameter");
+      B.mc.prm[i] = P.params[i];
+      B.mc.prmf[i] = static_cast<float>(P.params[i]);
+    }
+  }
+  proto.n_probs = n_problems;
+  proto.nodes = nodes->d_nodes;
+  proto.prob = nodes->d_problem;
+  proto.dt = nodes->d_dt;
+  proto.n = nodes->n;
+  proto.rk = make_round_keys(bp->seed);
+  proto.max_steps = static_cast<int32_t>(bp->max_steps);
+  const int32_t K = bp->chunk > 0 ? bp->chunk : (ctx->batch_chunk > 0 ? ctx->batch_chunk : 256);
+  proto.K = K;
+  if (diag) {
+    diag->path_steps = 0;
+    diag->capped = 0;
+  }
+  if (nodes->n == 0) return PDD_OK;
+  PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const BatchLayout Lay = batch_layout(nodes->n, bp, K);
+  pdd_status st = ensure_scratch(ctx, Lay.total);
+  if (st != PDD_OK) return st;
+  int bps = 0;
+  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel, kBatchBlock, 0));
+  if (bps < 1) bps = 1;
+  if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
+  const unsigned grid = static_cast<unsigned>(bps * ctx->num_sms);
+
+  if (!use_graph) {
+    st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, grid, d_mean, d_se, d_npaths);
+    if (st != PDD_OK) return st;
+  } else {
+    if (!ctx->stream) return fail(ctx, PDD_EINVAL, "graph capture needs a non-default stream");
+    // the graph bakes in every pointer and scalar: rebuild when any changes
+    BatchGraphKey key{};
+    key.nodes = *nodes;
+    key.bp = *bp;
+    key.out[0] = d_mean;
+    key.out[1] = d_se;
+    key.out[2] = d_npaths;
+    key.scratch = ctx->scratch;
+    key.grid = grid;
+    key.K = K;
+    key.probs_hash = 0;
+    const unsigned char *pb = reinterpret_cast<const unsigned char *>(proto.probs);
+    for (size_t i = 0; i < sizeof(proto.probs); ++i)
+      key.probs_hash = (key.probs_hash ^ pb[i]) * 1099511628211ull;
+    if (!ctx->batch_graph || std::memcmp(&key, &ctx->batch_key, sizeof key) != 0) {
+      if (ctx->batch_graph) {
+        cudaGraphExecDestroy(ctx->batch_graph);
+        ctx->batch_graph = nullptr;
+      }
+      const bool prof = ctx->profiling;
+      ctx->profiling = false;  // no event records inside the capture
+      PDD_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, grid, d_mean, d_se, d_npaths);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+      ctx->profiling = prof;
+      if (st != PDD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+      const cudaError_t ei = cudaGraphInstantiate(&ctx->batch_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+      ctx->batch_key = key;
+    }
+    const auto ev = prof_slot(ctx);
+    if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
+    PDD_CUDA_TRY(ctx, cudaGraphLaunch(ctx->batch_graph, ctx->stream));
+    if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
+  }
+  if (diag) {
+    unsigned long long h[4] = {0, 0, 0, 0};
+    PDD_CUDA_TRY(ctx, cudaMemcpyAsync(h, ctx->scratch, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    diag->path_steps = static_cast<int64_t>(h[0]);
+    diag->capped = static_cast<int64_t>(h[1]);
+    if (h[2]) return fail(ctx, PDD_EINVAL, "%llu nodes outside the closed domain", h[2]);
+    if (h[1]) return fail(ctx, PDD_ECAP, "%llu paths hit max_steps", h[1]);
+  }
+  return PDD_OK;
+}
+
+}  // namespace pdd

@@ -1,0 +1,267 @@
+// batch_kernel.cuh -- one persistent work-queue launch over a heterogeneous,
+// ragged batch of interface nodes (several domains and PDE families, per-node
+// time steps, per-node path counts).
+//
+// The unit of queued work is a lane-chunk: up to K consecutive paths of one
+// node, run one after the other by a single lane, which accumulates their
+// shifted scores (s - K_i), squares and step counts in registers (FP64 sums)
+// and writes one partial per chunk.  A lane that finishes its chunk takes the
+// next chunk from a warp-aggregated global cursor, so lanes never wait for one
+// another; partials are indexed by chunk, so the per-node merge (fixed order)
+// does not depend on scheduling.  Chunk counts may live in device memory, so
+// a launch sized on the host can consume a work list produced on the device
+// (the adaptive pass), and the whole pipeline can be captured in a CUDA graph.
+#pragma once
+
+#include "path_kernel.cuh"
+
+namespace pdd {
+
+constexpr int kMaxBatchProblems = 4;
+
+// Domain/family combinations the batch kernel dispatches on.
+enum : int32_t {
+  kComboSquareLaplace = 0,   // LaplaceExpCos on Box<2>
+  kComboLShapeLaplace = 1,   // LaplaceExpCos on LShape
+  kComboCubeElliptic = 2,    // EllipticManufactured on Box<3>
+  kComboSquarePoisson = 3    // PoissonFourier on Box<2>
+};
+
+struct BatchProblem {
+  ModelConst mc;
+  int32_t combo;
+  int32_t bridge;
+  double sigma;
+  double c_kill;  // constant killing rate (paper's c)
+};
+
+struct ChunkPartial {  // n, sum (s - K_i), sum (s - K_i)^2
+  double n, s1, s2;
+};
+
+struct BatchArgs {
+  const double *nodes;      // [n][3] (z ignored by 2-D families)
+  const int32_t *prob;      // [n] index into probs
+  const double *dt;         // [n]
+  int64_t n;
+  // work list: node i owns chunks [chunk_off[i], chunk_off[i+1]) covering
+  // paths [first[i], end[i]) in pieces of K; chunk_off[n] = total chunks
+  const int64_t *chunk_off;
+  const int64_t *first;
+  const int64_t *end;
+  const double *shift;      // [n] per-node shift K_i of the sums
+  int32_t K;
+  unsigned long long *cursor;
+  unsigned long long *counters;  // [0] path steps, [1] capped, [2] bad nodes
+  ChunkPartial *partial;    // [chunk_off[n]]
+  RoundKeys rk;
+  int32_t max_steps;
+  int32_t n_probs;
+  BatchProblem probs[kMaxBatchProblems];
+};
+
+struct BatchEnv {
+  const ModelConst &mc;
+  int32_t bridge;
+};
+
+// Lane state that survives across loop iterations.
+struct BatchLane {
+  float X[3];
+  float Y, Z;
+  int32_t n;
+  PhiloxPath pp;
+};
+
+// One loop unit of a path of family Model on domain Geom: one step for d <= 2,
+// a pair of steps (two Philox blocks) for d = 3.  Returns true when the path
+// exited (score in s); the caller handles the step cap.
+template <class Model, class Geom>
+__device__ __forceinline__ bool batch_unit(const BatchEnv &env, const StepConst<float> &k,
+                                           const RoundKeys &rk, int32_t max_steps, BatchLane &L,
+                                           float &s) {
+  constexpr int D = Model::D;
+  float xe[D], lr[1];
+  bool done;
+  if constexpr (D == 3) {
+    const uint32_t j = static_cast<uint32_t>(L.n);
+    const uint4 A = philox10_path(j, L.pp, rk);
+    const uint4 B = philox10_path(j + 1u, L.pp, rk);
+    float xi[3], e;
+    box_muller<float>(A.x, A.y, xi[0], xi[1]);
+    box_muller<float>(A.z, A.w, xi[2], e);
+    done = em_step<Model, Geom, float, false>(env, k, L.X, L.Y, L.Z, xi, B.z, L.n, s, xe, lr);
+    ++L.n;
+    if (!done && L.n < max_steps) {
+      float p, q;
+      box_muller<float>(B.x, B.y, p, q);
+      xi[0] = e;
+      xi[1] = p;
+      xi[2] = q;
+      done = em_step<Model, Geom, float, false>(env, k, L.X, L.Y, L.Z, xi, B.w, L.n, s, xe, lr);
+      ++L.n;
+    }
+  } else {
+    const uint4 A = philox10_path(static_cast<uint32_t>(L.n), L.pp, rk);
+    float xi[2], z1;
+    box_muller<float>(A.x, A.y, xi[0], z1);
+    xi[1] = z1;
+    done = em_step<Model, Geom, float, false>(env, k, L.X, L.Y, L.Z, xi, A.z, L.n, s, xe, lr);
+    ++L.n;
+  }
+  return done;
+}
+
+// Score of a capped path: g at the projection on the nearest face.
+template <class Model, class Geom>
+__device__ __forceinline__ float batch_capped(const ModelConst &mc, const BatchLane &L) {
+  constexpr int D = Model::D;
+  float xe[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) xe[d] = L.X[d];
+  Geom::project(Geom::nearest_face(xe), xe);
+  return Model::g(mc, xe) * L.Y + L.Z;
+}
+
+template <class Model, class Geom>
+__device__ __forceinline__ bool batch_inside(const float *x) {
+  return Geom::inside_open(x);
+}
+template <class Model, class Geom>
+__device__ __forceinline__ bool batch_closed(const float *x) {
+  return Geom::inside_closed(x);
+}
+
+#define PDD_BATCH_DISPATCH(combo, ...)                                                      \
+  switch (combo) {                                                                         \
+    case kComboSquareLaplace: { using M = LaplaceExpCos; using G = Box<2>; __VA_ARGS__; break; } \
+    case kComboLShapeLaplace: { using M = LaplaceExpCos; using G = LShape; __VA_ARGS__; break; } \
+    case kComboCubeElliptic: {                                                             \
+      using M = EllipticManufactured; using G = Box<3>; __VA_ARGS__; break;                 \
+    }                                                                                      \
+    default: { using M = PoissonFourier; using G = Box<2>; __VA_ARGS__; break; }           \
+  }
+
+constexpr int kBatchBlock = 256;
+
+__global__ void __launch_bounds__(kBatchBlock)
+batch_kernel(const __grid_constant__ BatchArgs a) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const uint64_t total = static_cast<uint64_t>(a.chunk_off[a.n]);
+  BatchLane L;
+  StepConst<float> k;
+  int32_t pi = 0, combo = 0;
+  uint32_t node = 0;
+  int64_t path = 0, path_end = 0;
+  uint64_t chunk = 0;
+  double shift = 0.0, s1 = 0.0, s2 = 0.0, cnt = 0.0;
+  bool active = false, need = true;
+  unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
+
+  for (;;) {
+    for (;;) {
+      const unsigned needmask = __ballot_sync(kFull, need);
+      if (!needmask) break;
+      const int leader = __ffs(needmask) - 1;
+      unsigned long long base = 0;
+      if (static_cast<int>(lane) == leader)
+        base = atomicAdd(a.cursor, static_cast<unsigned long long>(__popc(needmask)));
+      base = __shfl_sync(kFull, base, leader);
+      if (need) {
+        need = false;
+        const unsigned long long c = base + __popc(needmask & lt_mask);
+        if (c < total) {
+          chunk = c;
+          // node owning chunk c: last i with chunk_off[i] <= c
+          int64_t lo = 0, hi = a.n;
+          while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (static_cast<uint64_t>(a.chunk_off[mid]) <= c) lo = mid; else hi = mid;
+          }
+          node = static_cast<uint32_t>(lo);
+          const int64_t j = static_cast<int64_t>(c) - a.chunk_off[lo];
+          path = a.first[lo] + j * a.K;
+          path_end = min(a.end[lo], path + a.K);
+          pi = a.prob[lo];
+          const BatchProblem &P = a.probs[pi];
+          combo = P.combo;
+          const double dtd = a.dt[lo];
+          k = make_step_const(dtd, P.sigma, P.c_kill);
+          shift = a.shift ? a.shift[lo] : 0.0;
+          s1 = s2 = cnt = 0.0;
+          L.X[0] = static_cast<float>(a.nodes[lo * 3 + 0]);
+          L.X[1] = static_cast<float>(a.nodes[lo * 3 + 1]);
+          L.X[2] = static_cast<float>(a.nodes[lo * 3 + 2]);
+          bool open = true, closed = true;
+          PDD_BATCH_DISPATCH(combo, open = batch_inside<M, G>(L.X); closed = batch_closed<M, G>(L.X));
+          if (!open) {
+            // node on (or, invalid, outside) the boundary: every path scores g
+            float gv = 0.f;
+            PDD_BATCH_DISPATCH(combo, gv = M::g(P.mc, L.X));
+            double v = closed ? static_cast<double>(gv) - shift : static_cast<double>(NAN);
+            if (!closed) ++my_bad;
+            cnt = static_cast<double>(path_end - path);
+            a.partial[chunk] = ChunkPartial{cnt, cnt * v, cnt * v * v};
+            need = true;
+          } else {
+            L.Y = 1.f;
+            L.Z = 0.f;
+            L.n = 0;
+            L.pp = philox_path(static_cast<uint32_t>(path), node, 0u, a.rk);
+            active = true;
+          }
+        }
+      }
+    }
+    if (!__any_sync(kFull, active)) break;
+    if (!active) continue;
+
+    const BatchProblem &P = a.probs[pi];
+    const BatchEnv env{P.mc, P.bridge};
+    float s = 0.f;
+    bool done = false;
+    PDD_BATCH_DISPATCH(combo, done = (batch_unit<M, G>(env, k, a.rk, a.max_steps, L, s)));
+    if (!done && L.n >= a.max_steps) {
+      PDD_BATCH_DISPATCH(combo, s = batch_capped<M, G>(P.mc, L));
+      ++my_capped;
+      done = true;
+    }
+    if (done) {
+      const double v = static_cast<double>(s) - shift;
+      s1 += v;
+      s2 = fma(v, v, s2);
+      cnt += 1.0;
+      my_steps += static_cast<unsigned long long>(L.n);
+      ++path;
+      if (path < path_end) {
+        L.X[0] = static_cast<float>(a.nodes[static_cast<uint64_t>(node) * 3 + 0]);
+        L.X[1] = static_cast<float>(a.nodes[static_cast<uint64_t>(node) * 3 + 1]);
+        L.X[2] = static_cast<float>(a.nodes[static_cast<uint64_t>(node) * 3 + 2]);
+        L.Y = 1.f;
+        L.Z = 0.f;
+        L.n = 0;
+        L.pp = philox_path(static_cast<uint32_t>(path), node, 0u, a.rk);
+      } else {
+        a.partial[chunk] = ChunkPartial{cnt, s1, s2};
+        active = false;
+        need = true;
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    my_steps += __shfl_xor_sync(kFull, my_steps, m);
+    my_capped += __shfl_xor_sync(kFull, my_capped, m);
+    my_bad += __shfl_xor_sync(kFull, my_bad, m);
+  }
+  if (lane == 0) {
+    if (my_steps) atomicAdd(&a.counters[0], my_steps);
+    if (my_capped) atomicAdd(&a.counters[1], my_capped);
+    if (my_bad) atomicAdd(&a.counters[2], my_bad);
+  }
+}
+
+#undef PDD_BATCH_DISPATCH
+
+}  // namespace pdd

@@ -139,6 +139,41 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, R &z0, R &z1)
   z1 = r * s;
 }
 
+// binary32 Box-Muller with the hardware sine/cosine.  The angle is centred,
+// theta = 2 pi (U_b - 1/2) in (-pi, pi), where the hardware sin/cos have an
+// absolute error below 2^-21.4; cos(2 pi U_b) = -cos theta and
+// sin(2 pi U_b) = -sin theta.  ln U_a keeps CUDA's accurate logf (a fast log
+// loses all accuracy as U_a -> 1); the square root is y * rsqrt(y)
+// (y >= 1.19e-7, never 0).
+template <>
+__device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1) {
+  const float y = -2.0f * logf(unif_f(a));
+  const float mr = -(y * rsqrtf(y));
+  float s, c;
+  __sincosf(6.28318530717958648f * (unif_f(b) - 0.5f), &s, &c);
+  z0 = mr * c;
+  z1 = mr * s;
+}
+
+// sin(pi x), cos(pi x) for x in [0, 1] (points of the closed unit box).  FP32:
+// hardware sin/cos of pi x in [0, pi], absolute error below 2^-21.4 -- used
+// for drift and source values inside the domain, never for boundary data.
+__device__ __forceinline__ void sincospi01(float x, float *s, float *c) {
+  __sincosf(3.14159265358979324f * x, s, c);
+}
+__device__ __forceinline__ void sincospi01(double x, double *s, double *c) { sincospi(x, s, c); }
+
+// e^x for moderate x: FP32 hardware exp2 of x log2 e (about 2 ulp).
+__device__ __forceinline__ float exp_fast(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_fast(double x) { return exp(x); }
+
+// 2^x by the hardware unit (about 2 ulp relative).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---------------------------------------------------------------------------
 // Compensated (Neumaier) FP64 accumulator and its exact merge.
 // ---------------------------------------------------------------------------

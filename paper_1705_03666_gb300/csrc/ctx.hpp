@@ -13,6 +13,17 @@
 #include "../../include/pdd.h"
 #include "models.cuh"
 
+// Everything a captured batch graph depends on.
+struct BatchGraphKey {
+  pdd_batch_nodes nodes;
+  pdd_batch_params bp;
+  void *out[3];
+  void *scratch;
+  unsigned grid;
+  int32_t K;
+  unsigned long long probs_hash;
+};
+
 struct pdd_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -28,6 +39,10 @@ struct pdd_ctx {
   // resident blocks per SM chosen by the occupancy query or the tuner)
   int path_blocks_per_sm = 0;
   uint64_t wave_max_paths = 1ull << 29;
+  // batch solve: lane-chunk size and the cached graph of the last call
+  int batch_chunk = 0;
+  cudaGraphExec_t batch_graph = nullptr;
+  BatchGraphKey batch_key{};
   // kernel timing (pdd_profile): event pairs recorded around path launches
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
@@ -107,6 +122,14 @@ pdd_status branching_solve_impl(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
 pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const double *d_iface_s,
                                 const double *d_iface_vals, int64_t m, double *d_u,
                                 int64_t *iters, double *resid);
+pdd_status interface_grad_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                               const pdd_mc_params *mc, const double *d_grad_out, double *d_jac,
+                               double *d_jac_se, double *d_dtheta, double *d_dphi,
+                               pdd_diag *diag);
+pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n_problems,
+                            const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
+                            double *d_mean, double *d_se, int64_t *d_npaths, int32_t use_graph,
+                            pdd_diag *diag);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

@@ -161,6 +161,8 @@ pdd_status interface_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
     return fail(ctx, PDD_EINVAL, "max_steps out of range");
   if (mc->precision != PDD_FP32 && mc->precision != PDD_FP64)
     return fail(ctx, PDD_EINVAL, "unknown precision");
+  if (ctx->prob.sigma * ctx->prob.sigma * mc->dt > 1.0 / 36.0)
+    return fail(ctx, PDD_EINVAL, "sigma^2 dt must be <= 1/36");
   if (ctx->prob.kind == PDD_PROB_KPP)
     return fail(ctx, PDD_EINVAL, "KPP problems use pdd_branching_solve");
   if (n > 0 && (!d_nodes || !d_mean || !d_se)) return fail(ctx, PDD_EINVAL, "null buffer");
@@ -174,6 +176,8 @@ pdd_status interface_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   switch (ctx->prob.kind) {
     case PDD_PROB_LAPLACE_EXPCOS:
+      if (ctx->prob.geometry == PDD_GEOM_L_SHAPE)
+        return run_prec<LaplaceExpCos, LShape>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
       return run_prec<LaplaceExpCos, Box<2>>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
     case PDD_PROB_ELLIPTIC_MANUFACTURED:
       return run_prec<EllipticManufactured, Box<3>>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths,

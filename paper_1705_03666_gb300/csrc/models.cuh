@@ -54,9 +54,9 @@ struct EllipticManufactured {
   template <typename R>
   __device__ __forceinline__ static void coeffs(const ModelConst &, const R *x, R *b, R &f) {
     R sx, cx, sy, cy;
-    m_sincospi(x[0], &sx, &cx);
-    m_sincospi(x[1], &sy, &cy);
-    const R ez = m_exp(x[2]);
+    sincospi01(x[0], &sx, &cx);
+    sincospi01(x[1], &sy, &cy);
+    const R ez = exp_fast(x[2]);
     const R syz = sy * ez;
     const R b0 = sy * cy;
     const R b1 = R(0.5) - sx * sx;
@@ -87,9 +87,9 @@ struct PoissonFourier {
   static constexpr bool kDrift = true, kSource = true;
   static constexpr int kKill = 0;
   template <typename R>
-  __device__ __forceinline__ static void sines(R t, R *s) {  // s[j-1] = sin(j pi t)
+  __device__ __forceinline__ static void sines(R t, R *s) {  // s[j-1] = sin(j pi t), t in [0,1]
     R s1, c1;
-    m_sincospi(t, &s1, &c1);
+    sincospi01(t, &s1, &c1);
     const R two_c = R(2) * c1;
     s[0] = s1;
     s[1] = two_c * s1;
@@ -121,6 +121,27 @@ struct PoissonFourier {
     b[1] = b1;
     f = R(1);
   }
+  // coeffs plus the likelihood-ratio increments of the 16 drift weights:
+  // L_j += xi . db/dphi_j (X), db/dphi_j = (sin(j pi y), 0) for j <= 8 and
+  // (0, sin((j-8) pi x)) for j > 8 (scaled by sqrt(dt)/sigma at the exit).
+  template <typename R>
+  __device__ __forceinline__ static void coeffs_lr(const ModelConst &mc, const R *x, R *b, R &f,
+                                                   const R *xi, R *L) {
+    R sy[8], sx[8];
+    sines(x[1], sy);
+    sines(x[0], sx);
+    R b0 = R(0), b1 = R(0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      b0 += prm<R>(mc, 64 + j) * sy[j];
+      b1 += prm<R>(mc, 72 + j) * sx[j];
+      L[j] += xi[0] * sy[j];
+      L[8 + j] += xi[1] * sx[j];
+    }
+    b[0] = b0;
+    b[1] = b1;
+    f = R(1);
+  }
   template <typename R>
   __device__ __forceinline__ static R g(const ModelConst &mc, const R *x) {
     R cx[8], cy[8];
@@ -144,6 +165,7 @@ struct PoissonFourier {
 template <int D>
 struct Box {
   static constexpr int kFaces = 2 * D;
+  static constexpr bool kFastScreen = true;  // one candidate face per axis
 
   template <typename R>
   __device__ __forceinline__ static bool inside_closed(const R *x) {
@@ -165,16 +187,43 @@ struct Box {
     const R v = x[j >> 1];
     return (j & 1) ? R(1) - v : v;
   }
-  // Cheap filter: is any face close enough that 2 d d' < 18 sigma^2 dt could
-  // hold?  (thr = 9 sigma^2 dt.)
+  // Bridge candidates.  For axis k the products d d' for its two faces are
+  // x0 x1 and (1 - x0)(1 - x1); both can be below 9 sigma^2 dt only when
+  // sigma^2 dt > 1/36 (excluded by the caller), so one face per axis -- the
+  // one with the smaller product -- is the only one that can contribute.
+  // prod[k] = that product, face[k] = its index; returns whether any axis has
+  // prod < thr (thr = 9 sigma^2 dt, i.e. 2 d d' / (sigma^2 dt) < 18).
   template <typename R>
-  __device__ __forceinline__ static bool near_any(const R *x0, const R *x1, R thr) {
+  __device__ __forceinline__ static bool near_faces(const R *x0, const R *x1, R thr, R *prod,
+                                                    int *face) {
     bool nr = false;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      nr = nr || (x0[k] * x1[k] < thr) || ((R(1) - x0[k]) * (R(1) - x1[k]) < thr);
+      const R lo = x0[k] * x1[k], hi = (R(1) - x0[k]) * (R(1) - x1[k]);
+      const bool up = hi < lo;
+      prod[k] = up ? hi : lo;
+      face[k] = 2 * k + (up ? 1 : 0);
+      nr = nr || (prod[k] < thr);
     }
     return nr;
+  }
+  // Bridge screening of a step X -> X' inside the closed box: for axis k the
+  // products d d' of its two faces are x_k x'_k and (1 - x_k)(1 - x'_k).
+  // prod[k] = the smaller one, face[k] its face (the other face of the axis
+  // cannot be within reach while sigma^2 dt <= 1/36); returns the minimum
+  // over the axes (the nearest face's d d').
+  template <typename R>
+  __device__ __forceinline__ static R screen(const R *x0, const R *x1, R *prod, int *face) {
+    R mn = R(1);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const R lo = x0[k] * x1[k], hi = (R(1) - x0[k]) * (R(1) - x1[k]);
+      const bool up = hi < lo;
+      prod[k] = up ? hi : lo;
+      face[k] = 2 * k + (up ? 1 : 0);
+      mn = fmin(mn, prod[k]);
+    }
+    return mn;
   }
   template <typename R>
   __device__ __forceinline__ static void project(int j, R *x) {
@@ -202,6 +251,115 @@ struct Box {
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
+      R v = x0[k] + tb * (x1[k] - x0[k]);
+      v = (k == kb) ? vb : v;
+      xe[k] = fmin(R(1), fmax(R(0), v));
+    }
+  }
+  template <typename R>
+  __device__ __forceinline__ static int nearest_face(const R *x) {
+    int jb = 0;
+    R db = face_dist<R>(0, x);
+#pragma unroll
+    for (int j = 1; j < kFaces; ++j) {
+      const R d = face_dist<R>(j, x);
+      if (d < db) { db = d; jb = j; }
+    }
+    return jb;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Geometry: the L-shape [0,1]^2 minus the open notch (1/2,1] x (1/2,1].
+// Faces 0-3 are the four sides of the square (as half-planes, face 2k+s on
+// x_k = s); face 4 is the notch edge y = 1/2, x in [1/2, 1] (domain side
+// y < 1/2) and face 5 the notch edge x = 1/2, y in [1/2, 1] (domain side
+// x < 1/2).  Distances to the notch edges are distances to the segments, so
+// points away from an edge see no crossing (the re-entrant corner is handled
+// by the half-plane formula only approximately, like every corner).
+// ---------------------------------------------------------------------------
+struct LShape {
+  static constexpr int kFaces = 6;
+  static constexpr bool kFastScreen = false;
+
+  template <typename R>
+  __device__ __forceinline__ static bool inside_closed(const R *x) {
+    return x[0] >= R(0) && x[0] <= R(1) && x[1] >= R(0) && x[1] <= R(1) &&
+           !(x[0] > R(0.5) && x[1] > R(0.5));
+  }
+  template <typename R>
+  __device__ __forceinline__ static bool inside_open(const R *x) {
+    return x[0] > R(0) && x[0] < R(1) && x[1] > R(0) && x[1] < R(1) &&
+           !(x[0] >= R(0.5) && x[1] >= R(0.5));
+  }
+  template <typename R>
+  __device__ __forceinline__ static R face_dist(int j, const R *x) {
+    if (j < 4) {
+      const R v = x[j >> 1];
+      return (j & 1) ? R(1) - v : v;
+    }
+    const R a = j == 4 ? x[0] : x[1];          // along the edge
+    const R b = R(0.5) - (j == 4 ? x[1] : x[0]);  // towards the domain
+    if (a >= R(0.5)) return b;
+    const R da = R(0.5) - a;
+    return m_sqrt(da * da + b * b);
+  }
+  template <typename R>
+  __device__ __forceinline__ static void project(int j, R *x) {
+    if (j < 4) {
+      x[j >> 1] = R(j & 1);
+    } else if (j == 4) {
+      x[1] = R(0.5);
+      x[0] = fmax(x[0], R(0.5));
+    } else {
+      x[0] = R(0.5);
+      x[1] = fmax(x[1], R(0.5));
+    }
+  }
+  // First crossing of x0 -> x1 (x0 inside, x1 outside): the square's sides
+  // as for the box, and entry into the notch at the later of the parameters
+  // where each coordinate passes 1/2.
+  template <typename R>
+  __device__ __forceinline__ static void segment_exit(const R *x0, const R *x1, R *xe) {
+    R tb = R(2), vb = R(0);
+    int kb = -1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (x1[k] < R(0)) {
+        const R t = x0[k] / (x0[k] - x1[k]);
+        if (t < tb) { tb = t; kb = k; vb = R(0); }
+      } else if (x1[k] > R(1)) {
+        const R t = (R(1) - x0[k]) / (x1[k] - x0[k]);
+        if (t < tb) { tb = t; kb = k; vb = R(1); }
+      }
+    }
+    R lo = R(-1e30), hi = R(1e30);
+    int kent = -1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const R a = x0[k], d = x1[k] - x0[k];
+      R tl, th;
+      if (d == R(0)) {
+        if (a > R(0.5)) { tl = R(0); th = R(1); } else { tl = R(2); th = R(-1); }
+      } else if (d > R(0)) {
+        tl = (R(0.5) - a) / d; th = R(2);
+      } else {
+        tl = R(-1); th = (R(0.5) - a) / d;
+      }
+      if (tl > lo) { lo = tl; kent = k; }
+      if (th < hi) hi = th;
+    }
+    if (kent >= 0 && lo < hi && lo <= R(1) && hi > R(0)) {
+      const R tent = lo > R(0) ? lo : R(0);
+      if (tent < tb) { tb = tent; kb = kent; vb = R(0.5); }
+    }
+    if (kb < 0) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) xe[k] = fmin(R(1), fmax(R(0), x1[k]));
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
       R v = x0[k] + tb * (x1[k] - x0[k]);
       v = (k == kb) ? vb : v;
       xe[k] = fmin(R(1), fmax(R(0), v));

@@ -44,6 +44,7 @@ struct PathArgs {
   float l2cdt_f;                // c dt log2(e) for constant killing (FP32)
   int32_t max_steps;
   int32_t bridge;
+  float lr_scale;               // sqrt(dt) / sigma (gradient mode)
   ModelConst mc;
 };
 
@@ -56,11 +57,17 @@ struct PathArgs {
 template <typename R> struct StepConst;
 template <> struct StepConst<float> {
   float dt, sdt, thr, l2cdt, inv_s2dt;
+  StepConst() = default;
   __device__ __forceinline__ StepConst(const PathArgs &a)
       : dt(a.dt_f), sdt(a.sdt_f), thr(a.thr_f), l2cdt(a.l2cdt_f),
         inv_s2dt(static_cast<float>(a.inv_s2dt)) {}
   __device__ __forceinline__ float kill(float, int32_t n_next) const {
-    return exp2f(static_cast<float>(n_next) * l2cdt);
+    return ex2_approx(static_cast<float>(n_next) * l2cdt);
+  }
+  // e^{-a} for a >= 0 (hardware exp2, ~2 ulp; a near-tie decision is redone
+  // in FP64 by the caller).
+  __device__ __forceinline__ float exp_neg(float a) const {
+    return ex2_approx(-1.4426950408889634f * a);
   }
 };
 template <> struct StepConst<double> {
@@ -68,7 +75,21 @@ template <> struct StepConst<double> {
   __device__ __forceinline__ StepConst(const PathArgs &a)
       : dt(a.dt_d), sdt(a.sdt_d), thr(a.thr_d), e(a.ecdt_d), inv_s2dt(a.inv_s2dt) {}
   __device__ __forceinline__ double kill(double y, int32_t) const { return y * e; }
+  __device__ __forceinline__ double exp_neg(double a) const { return exp(-a); }
 };
+
+// FP32 step constants for time step dt, generator (1/2) sigma^2 Lap and a
+// constant killing rate c, rounded from the same FP64 expressions the host
+// uses for PathArgs.
+__device__ __forceinline__ StepConst<float> make_step_const(double dt, double sigma, double c) {
+  StepConst<float> k;
+  k.dt = static_cast<float>(dt);
+  k.sdt = static_cast<float>(sigma * sqrt(dt));
+  k.thr = static_cast<float>(9.0 * sigma * sigma * dt);
+  k.l2cdt = static_cast<float>(c * dt * 1.4426950408889634);
+  k.inv_s2dt = static_cast<float>(1.0 / (sigma * sigma * dt));
+  return k;
+}
 
 // Brownian-bridge exit probability over the faces within reach,
 // P = 1 - prod_j (1 - p_j), p_j = exp(-2 d_j d'_j / (sigma^2 dt)), accumulated
@@ -76,30 +97,29 @@ template <> struct StepConst<double> {
 // path: compensated binary32, and a decision with |U - P| within 2^-18 P is
 // re-taken from the same distances in FP64.  Returns the face with the
 // largest p_j, or -1 when no face is within reach or U >= P.
-template <class Geom, typename R>
-__device__ __forceinline__ int bridge_exit(const StepConst<R> &k, const R *X, const R *Xn,
+template <int NC, typename R>
+__device__ __forceinline__ int bridge_exit(const StepConst<R> &k, const R *prod, const int *face,
                                            R U) {
   R P = R(0), pbest = R(-1);
   int jbest = -1;
 #pragma unroll
-  for (int j = 0; j < Geom::kFaces; ++j) {
-    const R aa = R(2) * Geom::face_dist(j, X) * Geom::face_dist(j, Xn) * k.inv_s2dt;
+  for (int c = 0; c < NC; ++c) {
+    const R aa = R(2) * prod[c] * k.inv_s2dt;
     if (aa < R(18)) {
       const R p = m_exp(-aa);
       P = P + p * (R(1) - P);
-      if (p > pbest) { pbest = p; jbest = j; }
+      if (p > pbest) { pbest = p; jbest = face[c]; }
     }
   }
   if (jbest < 0) return -1;
   bool take = U < P;
   if constexpr (sizeof(R) == 4) {
-    if (fabsf(U - P) <= 3.814697265625e-06f * P) {  // near tie: FP64 from the same distances
+    if (fabsf(U - P) <= 3.814697265625e-06f * P) {  // near tie: FP64 from the same products
       double Pd = 0.0;
       const double s = 2.0 * static_cast<double>(k.inv_s2dt);
 #pragma unroll
-      for (int j = 0; j < Geom::kFaces; ++j) {
-        const double aa = s * static_cast<double>(Geom::face_dist(j, X)) *
-                          static_cast<double>(Geom::face_dist(j, Xn));
+      for (int c = 0; c < NC; ++c) {
+        const double aa = s * static_cast<double>(prod[c]);
         if (aa < 18.0) {
           const double p = exp(-aa);
           Pd = Pd + p * (1.0 - Pd);
@@ -111,18 +131,66 @@ __device__ __forceinline__ int bridge_exit(const StepConst<R> &k, const R *X, co
   return take ? jbest : -1;
 }
 
+// Bridge over all faces of a general domain (distances from Geom::face_dist):
+// P = 1 - prod_j (1 - p_j) accumulated as P + p (1 - P) over the faces with
+// 2 d d' / (sigma^2 dt) < 18; FP32 near-ties decided in FP64.  Returns the
+// face with the largest p_j if U < P, else -1.
+template <class Geom, typename R>
+__device__ __forceinline__ int bridge_generic(const StepConst<R> &k, const R *X, const R *Xn, R U) {
+  R P = R(0), pbest = R(-1);
+  int jbest = -1;
+  R dd[Geom::kFaces];
+#pragma unroll
+  for (int j = 0; j < Geom::kFaces; ++j) {
+    dd[j] = Geom::face_dist(j, X) * Geom::face_dist(j, Xn);
+    const R aa = R(2) * dd[j] * k.inv_s2dt;
+    if (aa < R(18)) {
+      const R p = k.exp_neg(aa);
+      P = P + p * (R(1) - P);
+      if (p > pbest) { pbest = p; jbest = j; }
+    }
+  }
+  if (jbest < 0) return -1;
+  bool take = U < P;
+  if constexpr (sizeof(R) == 4) {
+    if (fabsf(U - P) <= 3.814697265625e-06f * P) {
+      double Pd = 0.0;
+      const double s = 2.0 * static_cast<double>(k.inv_s2dt);
+#pragma unroll
+      for (int j = 0; j < Geom::kFaces; ++j) {
+        const double aa = s * static_cast<double>(dd[j]);
+        if (aa < 18.0) {
+          const double p = exp(-aa);
+          Pd = Pd + p * (1.0 - Pd);
+        }
+      }
+      take = static_cast<double>(U) < Pd;
+    }
+  }
+  return take ? jbest : -1;
+}
+
+// Number of likelihood-ratio accumulators carried per path (gradient mode).
+constexpr int kMaxLR = 16;
+
 // One Euler-Maruyama step with the exit test.  Returns true on exit, with
-// the score in `s`.  X, Y, Z advance only when the path stays inside.
-template <class Model, class Geom, typename R>
-__device__ __forceinline__ bool em_step(const PathArgs &a, const StepConst<R> &k,
+// the score in `s` and the exit point in `xe`.  X, Y, Z advance only when the
+// path stays inside.  With kLR the drift-weight likelihood-ratio sums L are
+// advanced by this step's noise (the step that exits included).
+template <class Model, class Geom, typename R, bool kLR, class Env>
+__device__ __forceinline__ bool em_step(const Env &a, const StepConst<R> &k,
                                         R *X, R &Y, R &Z, const R *xi, uint32_t uw,
-                                        int32_t n, R &s) {
+                                        int32_t n, R &s, R *xe, R *L) {
   constexpr int D = Model::D;
   R b[D];
   R f = R(0);
 #pragma unroll
   for (int d = 0; d < D; ++d) b[d] = R(0);
-  if constexpr (Model::kDrift || Model::kSource) Model::coeffs(a.mc, X, b, f);
+  if constexpr (kLR) {
+    Model::coeffs_lr(a.mc, X, b, f, xi, L);
+  } else if constexpr (Model::kDrift || Model::kSource) {
+    Model::coeffs(a.mc, X, b, f);
+  }
   R Xn[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) Xn[d] = X[d] + b[d] * k.dt + k.sdt * xi[d];
@@ -130,16 +198,60 @@ __device__ __forceinline__ bool em_step(const PathArgs &a, const StepConst<R> &k
   if constexpr (Model::kSource) Zn = Z + f * Y * k.dt;
   R Yn = Y;
   if constexpr (Model::kKill == 1) Yn = k.kill(Y, n + 1);
-  if (!Geom::inside_closed(Xn)) {
-    R xe[D];
+  if (!Geom::inside_closed(Xn)) {  // X' outside the closed domain
     Geom::segment_exit(X, Xn, xe);
     s = Model::g(a.mc, xe) * Yn + Zn;
     return true;
   }
-  if (a.bridge && Geom::near_any(X, Xn, k.thr)) {
-    const int jbest = bridge_exit<Geom, R>(k, X, Xn, unif<R>(uw));
-    if (jbest >= 0) {
-      R xe[D];
+  if constexpr (!Geom::kFastScreen) {
+    // general domains: every face within reach, P = 1 - prod (1 - p_j)
+    if (a.bridge) {
+      const int jbest = bridge_generic<Geom, R>(k, X, Xn, unif<R>(uw));
+      if (jbest >= 0) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) xe[d] = Xn[d];
+        Geom::project(jbest, xe);
+        s = Model::g(a.mc, xe) * Yn + Zn;
+        return true;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) X[d] = Xn[d];
+    Y = Yn;
+    Z = Zn;
+    return false;
+  } else {
+  R prod[D];
+  int face[D];
+  const R mn = Geom::screen(X, Xn, prod, face);
+  // Bridge: the single-face probability exp(-2 min d d' / (sigma^2 dt)) is
+  // formed without a branch; a step within reach of two or more faces
+  // (near an edge or corner) takes the general combination.
+  bool cross = false;
+  if (a.bridge) {
+    const R U = unif<R>(uw);
+    int near = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) near += prod[d] < k.thr ? 1 : 0;
+    if (near > 1) {
+      cross = bridge_exit<D, R>(k, prod, face, U) >= 0;
+    } else {
+      const R p = k.exp_neg(R(2) * mn * k.inv_s2dt);
+      cross = U < p;
+      if constexpr (sizeof(R) == 4) {
+        if (fabsf(U - p) <= 3.814697265625e-06f * p)  // near tie: FP64
+          cross = static_cast<double>(U) <
+                  exp(-2.0 * static_cast<double>(mn) * static_cast<double>(k.inv_s2dt));
+      }
+    }
+  }
+  if (cross) {
+    int jbest = face[0];
+    R pmin = prod[0];
+#pragma unroll
+    for (int d = 1; d < D; ++d)
+      if (prod[d] < pmin) { pmin = prod[d]; jbest = face[d]; }
+    {
 #pragma unroll
       for (int d = 0; d < D; ++d) xe[d] = Xn[d];
       Geom::project(jbest, xe);
@@ -152,12 +264,44 @@ __device__ __forceinline__ bool em_step(const PathArgs &a, const StepConst<R> &k
   Y = Yn;
   Z = Zn;
   return false;
+  }
 }
 
-template <class Model, class Geom, typename R>
+// Per-path record of the gradient mode: score, exit point, and the
+// likelihood-ratio sums L_j (already scaled by sqrt(dt)/sigma).
+struct GradRec {
+  float s, x, y, z;
+  float L[kMaxLR];
+};
+
+// Result of one path: its score (forward mode) or its gradient record.
+template <int D, typename R, bool kLR>
+__device__ __forceinline__ void write_result(const PathArgs &a, uint64_t slot, R s, int32_t st,
+                                             const R *xe, const R *L) {
+  if constexpr (kLR) {
+    GradRec *rec = static_cast<GradRec *>(a.score) + slot;
+    float4 *o = reinterpret_cast<float4 *>(rec);
+    o[0] = make_float4(static_cast<float>(s), static_cast<float>(xe[0]),
+                       D > 1 ? static_cast<float>(xe[D > 1 ? 1 : 0]) : 0.f,
+                       D > 2 ? static_cast<float>(xe[D > 2 ? 2 : 0]) : 0.f);
+    const float c = a.lr_scale;
+#pragma unroll
+    for (int q = 0; q < kMaxLR / 4; ++q)
+      o[1 + q] = make_float4(c * static_cast<float>(L[4 * q]), c * static_cast<float>(L[4 * q + 1]),
+                             c * static_cast<float>(L[4 * q + 2]), c * static_cast<float>(L[4 * q + 3]));
+  } else {
+    static_cast<R *>(a.score)[slot] = s;
+  }
+  if (a.steps) a.steps[slot] = st;
+}
+
+template <class Model, class Geom, typename R, bool kLR = false>
 __global__ void __launch_bounds__(kPathBlock)
 path_kernel(const __grid_constant__ PathArgs a) {
   constexpr int D = Model::D;
+  constexpr int NL = kLR ? kMaxLR : 1;
+  R L[NL];
+  R xe[D];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
   const StepConst<R> k(a);
@@ -168,7 +312,6 @@ path_kernel(const __grid_constant__ PathArgs a) {
   int32_t n = 0;
   bool active = false, need = true;
   unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
-  R *score = static_cast<R *>(a.score);
 
   for (;;) {
     // ---- refill: lanes without a path take the next indices of the wave
@@ -194,6 +337,8 @@ path_kernel(const __grid_constant__ PathArgs a) {
           Y = R(1);
           Z = R(0);
           n = 0;
+#pragma unroll
+          for (int j = 0; j < NL; ++j) L[j] = R(0);
           if (!Geom::inside_open(X)) {
             // Node on the boundary: tau = 0, u = g (Eq. 2.1).  Outside the
             // closed domain: invalid input, NaN score, counted.
@@ -202,8 +347,9 @@ path_kernel(const __grid_constant__ PathArgs a) {
               s = R(NAN);
               ++my_bad;
             }
-            score[slot] = s;
-            if (a.steps) a.steps[slot] = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) xe[d] = X[d];
+            write_result<D, R, kLR>(a, slot, s, 0, xe, L);
             need = true;
           } else {
             active = true;
@@ -225,7 +371,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
       R xi[3], e;
       box_muller<R>(A.x, A.y, xi[0], xi[1]);
       box_muller<R>(A.z, A.w, xi[2], e);
-      done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, B.z, n, s);
+      done = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, B.z, n, s, xe, L);
       ++n;
       if (!done && n < a.max_steps) {
         R p, q;
@@ -233,7 +379,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
         xi[0] = e;
         xi[1] = p;
         xi[2] = q;
-        done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, B.w, n, s);
+        done = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, B.w, n, s, xe, L);
         ++n;
       }
     } else {
@@ -241,13 +387,12 @@ path_kernel(const __grid_constant__ PathArgs a) {
       R xi[2], z1;
       box_muller<R>(A.x, A.y, xi[0], z1);
       if constexpr (D == 2) xi[1] = z1;
-      done = em_step<Model, Geom, R>(a, k, X, Y, Z, xi, A.z, n, s);
+      done = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, A.z, n, s, xe, L);
       ++n;
     }
     int32_t st = n;
     if (!done && n >= a.max_steps) {
       // step cap: score at the projection on the nearest face, counted
-      R xe[D];
 #pragma unroll
       for (int d = 0; d < D; ++d) xe[d] = X[d];
       Geom::project(Geom::nearest_face(X), xe);
@@ -257,8 +402,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
       done = true;
     }
     if (done) {
-      score[slot] = s;
-      if (a.steps) a.steps[slot] = st;
+      write_result<D, R, kLR>(a, slot, s, st, xe, L);
       my_steps += static_cast<unsigned long long>(n);
       active = false;
       need = true;

@@ -159,6 +159,11 @@ def workload(k: int) -> dict:
                 "prob": elliptic_manufactured(), "nodes": nodes_cube_planes(4096),
                 "seed": SEED_BASE + 2, "dt": 1e-4, "n_paths": 100_000,
                 "precision": "fp32", "bridge": True}
+    if k == 3:
+        mix = batch_mix()
+        return {"name": "batch_square7000_lshape7000_cube6000_adaptive_se1e-4",
+                **mix, "seed": SEED_BASE + 3, "n_pilot": 1000, "n_min": 1000,
+                "n_max": 1_000_000, "target_se": 1e-4}
     if k == 4:
         return {"name": "kpp2d_1024nodes_1e5trees_beta1",
                 "prob": kpp("sigmoid", 4.0, 1.0), "nodes": nodes_kpp(),
@@ -170,6 +175,39 @@ def workload(k: int) -> dict:
                 "seed": SEED_BASE + 5, "dt": 1e-3, "n_paths": 100_000,
                 "precision": "fp32", "bridge": True}
     raise ValueError(f"no workload {k}")
+
+
+def nodes_lshape_interfaces(count: int) -> np.ndarray:
+    """Nodes on the L-shape's interfaces: alternately on x = 1/2, y in (0, 1/2)
+    and on y = 1/2, x in (0, 1/2), equispaced along each segment (the two
+    artificial interfaces that cut the L into three squares)."""
+    a = (count + 1) // 2
+    b = count - a
+    ya = np.arange(1, a + 1, dtype=np.float64) / (2 * (a + 1))
+    xb = np.arange(1, b + 1, dtype=np.float64) / (2 * (b + 1))
+    pts = np.concatenate([np.stack([np.full_like(ya, 0.5), ya], 1),
+                          np.stack([xb, np.full_like(xb, 0.5)], 1)])
+    return pts
+
+
+def batch_mix(square: int = 7000, lshape: int = 7000, cube: int = 6000, seed: int = 3) -> dict:
+    """The heterogeneous batch: Laplace on the unit square (interface x = 1/2),
+    Laplace on the L-shape (its two interfaces), and the 3-D elliptic problem
+    (internal planes of the cube); per-node dt drawn from {1e-3, 1e-4} with
+    NumPy seed `seed`.  Returns problems, nodes [n, 3], problem index, dt."""
+    rng = np.random.default_rng(seed)
+    sq = np.stack([np.full(square, 0.5), np.arange(1, square + 1) / (square + 1)], 1)
+    ls = nodes_lshape_interfaces(lshape)
+    cb = nodes_cube_planes(cube)
+    nodes = np.zeros((square + lshape + cube, 3))
+    nodes[:square, :2] = sq
+    nodes[square:square + lshape, :2] = ls
+    nodes[square + lshape:] = cb
+    pidx = np.concatenate([np.zeros(square), np.ones(lshape), np.full(cube, 2)]).astype(np.int32)
+    dt = np.where(rng.random(len(nodes)) < 0.5, 1e-3, 1e-4)
+    return {"problems": [laplace_expcos("unit_square"), laplace_expcos("l_shape"),
+                         elliptic_manufactured()],
+            "nodes": nodes, "problem_index": pidx, "dt": dt}
 
 
 def every_kth_node(nodes: np.ndarray, k: int) -> np.ndarray:

@@ -58,6 +58,6 @@ def test_create_rejects_invalid_problem_without_gpu(lib):
 def test_struct_layouts(lib):
     assert ctypes.sizeof(lib.Problem) == 32
     assert ctypes.sizeof(lib.MCParams) == 48
-    assert ctypes.sizeof(lib.Diag) == 32
+    assert ctypes.sizeof(lib.Diag) == 40
     assert ctypes.sizeof(lib.BranchParams) == 40
     assert ctypes.sizeof(lib.Subdomain) == 88
