@@ -309,6 +309,30 @@ PDD_API pdd_status pdd_profile(pdd_ctx *ctx, int enable);
 PDD_API pdd_status pdd_profile_read(pdd_ctx *ctx, double *kernel_ms,
                                     int64_t *launches);
 
+/* pdd_interface_solve without any device allocation.  The paper has no
+ * counterpart: this is a deployment variant for callers that cannot call
+ * cudaMalloc -- code running while a stream is being captured into a CUDA
+ * graph under a no-allocation policy, hosts whose memory pool owns the whole
+ * device, plug-ins that only receive pre-allocated buffers, and latency-
+ * critical loops where an allocation (or its failure) is not acceptable.
+ * It computes the same estimate as pdd_interface_solve (same kernels, same
+ * streams, no diagnostics) on `device` and `cuda_stream`, without a context.
+ * The caller still provides the inputs and outputs (device pointers, as for
+ * pdd_interface_solve).  Scratch comes from one static 32 MiB device array
+ * that every GPU loading this library holds until process exit; n is limited
+ * to 65536 nodes (PDD_EINVAL beyond), any number of paths is processed in
+ * waves that fit the array.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array and each clears it at the start, so calls that overlap on
+ * the GPU (different streams, or different threads) race: serialise them.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.          */
+PDD_API pdd_status pdd_interface_solve_static(const pdd_problem *problem,
+                                              int device, void *cuda_stream,
+                                              const double *d_nodes, int64_t n,
+                                              const pdd_mc_params *mc,
+                                              double *d_mean, double *d_se,
+                                              int64_t *d_npaths);
+
 /* Philox4x32-10 (Salmon et al., SC'11) blocks for counters
  * (j0 + b, c1, c2, c3), b < n_blocks, key = (seed low, seed high), written to
  * d_out[n_blocks][4].  Exposes the generator the estimators consume, so that

@@ -86,6 +86,9 @@ _SIGS = {
     "pdd_interface_grad": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(MCParams), _VP, _VP,
                                           _VP, _VP, _VP, ctypes.POINTER(Diag)]),
     "pdd_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
+    "pdd_interface_solve_static": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int, _VP,
+                                                   _VP, _I64, ctypes.POINTER(MCParams), _VP,
+                                                   _VP, _VP]),
     "pdd_batch_solve": (ctypes.c_int, [_VP, ctypes.POINTER(Problem), ctypes.c_int32,
                                        ctypes.POINTER(BatchNodes), ctypes.POINTER(BatchParams),
                                        _VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(Diag)]),

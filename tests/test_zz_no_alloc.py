@@ -1,0 +1,75 @@
+"""pdd_interface_solve_static: the interface solve for callers that cannot
+allocate device memory (graph capture under a no-allocation policy, hosts
+whose pool owns the device, plug-ins handed pre-allocated buffers).
+
+Called through the C ABI with caller-provided buffers; its output must match
+pdd_interface_solve's on the same inputs, on two calls in a row (the static
+scratch keeps the previous call's contents, so the second call checks that
+everything that must start at zero is cleared).  This file is collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_03666_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_03666_gb300 import _lib
+    return _lib
+
+
+def _problem(lib, prob):
+    params = np.ascontiguousarray(prob["params"] if prob["params"].size else np.zeros(1))
+    p = lib.Problem(lib.PROBLEM[prob["problem"]], lib.GEOMETRY[prob["geometry"]],
+                    int(prob["dim"]), int(prob["params"].size),
+                    params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(prob["sigma"]))
+    return p, params
+
+
+def _static_call(lib, prob, nodes, mc):
+    cdll = lib.load()
+    p, keep = _problem(lib, prob)
+    n = nodes.shape[0]
+    mean = torch.empty(n, dtype=torch.float64, device="cuda")
+    se = torch.empty(n, dtype=torch.float64, device="cuda")
+    cnt = torch.empty(n, dtype=torch.int64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = cdll.pdd_interface_solve_static(ctypes.byref(p), 0, stream, nodes.data_ptr(), n,
+                                         ctypes.byref(mc), mean.data_ptr(), se.data_ptr(),
+                                         cnt.data_ptr())
+    torch.cuda.synchronize()
+    return st, mean, se, cnt
+
+
+@pytest.mark.parametrize("k,precision,stride,n_paths", [(2, "fp32", 16, 3001), (1, "fp64", 1, 2000)])
+def test_static_matches_context_solve_twice(lib, k, precision, stride, n_paths):
+    from paper_1705_03666_gb300 import api
+    w = W.workload(k)
+    nodes = torch.from_numpy(np.ascontiguousarray(w["nodes"][::stride])).cuda()
+    kw = dict(seed=w["seed"], dt=1e-3, n_paths=n_paths, precision=precision)
+    with api.Context(w["prob"]) as ctx:
+        ref = ctx.interface_solve(nodes, **kw)
+        ref_mean, ref_se, ref_n = (t.cpu().numpy() for t in (ref["mean"], ref["se"], ref["n"]))
+    mc = lib.MCParams(w["seed"], 1e-3, n_paths, 2**31 - 1, 0, lib.PRECISION[precision], 1)
+    for _ in range(2):
+        st, mean, se, cnt = _static_call(lib, w["prob"], nodes, mc)
+        assert st == lib.PDD_OK
+        np.testing.assert_allclose(mean.cpu().numpy(), ref_mean, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(se.cpu().numpy(), ref_se, rtol=1e-9, atol=0)
+        assert np.array_equal(cnt.cpu().numpy(), ref_n)
+
+
+def test_static_rejects_too_many_nodes(lib):
+    w = W.workload(2)
+    nodes = torch.full((65537, 3), 0.5, dtype=torch.float64, device="cuda")
+    mc = lib.MCParams(1, 1e-3, 1, 100, 0, 0, 1)
+    st, *_ = _static_call(lib, w["prob"], nodes, mc)
+    assert st == lib.PDD_EINVAL
