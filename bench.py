@@ -242,7 +242,25 @@ def run_pdd(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
+
+    # the plain one-node-per-launch form at the same paths per node (equal SE)
+    naive = None
+    if not args.no_naive:
+        torch.cuda.synchronize()
+        n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0.record(stream)
+        rn = ctx.interface_solve_naive(nodes, seed=seed, dt=w["dt"], n_paths=n_paths)
+        n1.record(stream)
+        torch.cuda.synchronize()
+        naive_ms = n0.elapsed_time(n1)
+        naive = {"ms_per_step": naive_ms, "speedup": naive_ms / (1e3 * t_total / args.steps),
+                 "median_se": float(rn["se"].median()),
+                 "form": "one launch per node, one thread per path, block sums + FP64 atomics"}
     ctx.close()
+
+    batch = None
+    if not args.no_batch:
+        batch = run_batch_once(api, dev, scale=args.batch_scale)
 
     if rank != 0:
         if world > 1:
@@ -286,11 +304,49 @@ def run_pdd(args):
                 "h2d_bytes_per_step": int(nodes_h.numel() * 8),
                 "d2h_bytes_per_step": int(n * 24)},
     }
+    if naive is not None:
+        line["vs_naive_equal_se"] = naive
+    if batch is not None:
+        line["batch_adaptive"] = batch
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batch_once(api, dev, scale: float = 0.05) -> dict:
+    """The heterogeneous adaptive batch (unit square / L-shape / unit cube,
+    per-node dt in {1e-3, 1e-4}) at a reduced scale: target SE 1e-4/sqrt(scale)
+    and n_max = 1e6 * scale; one warm-up call builds and replays the graph,
+    one timed replay."""
+    import torch
+    w = W.workload(3)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        ctx = api.Context(w["problems"][0], dev)
+        kw = dict(seed=w["seed"], n_pilot=w["n_pilot"], n_min=w["n_min"],
+                  n_max=int(w["n_max"] * scale), target_se=w["target_se"] / scale ** 0.5,
+                  use_graph=True)
+        args = (w["problems"], torch.from_numpy(w["nodes"]).to(dev),
+                torch.from_numpy(w["problem_index"]).to(dev), torch.from_numpy(w["dt"]).to(dev))
+        r = ctx.batch_solve(*args, diag=True, **kw)   # capture + replay, counts steps
+        steps = r["path_steps"]
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        r = ctx.batch_solve(*args, **kw)               # graph replay
+        b1.record(stream)
+        stream.synchronize()
+        ms = b0.elapsed_time(b1)
+        npaths = r["n"].double()
+        out = {"workload": w["name"] + f" at scale {scale}", "ms": ms,
+               "path_steps": steps, "path_steps_per_s": steps / (ms / 1e3),
+               "nodes": int(r["n"].numel()), "nodes_per_s": r["n"].numel() / (ms / 1e3),
+               "paths": float(npaths.sum()), "median_se": float(r["se"].median()),
+               "target_se": kw["target_se"], "n_max": kw["n_max"],
+               "launch": "pilot + main persistent launches in one captured CUDA graph"}
+        ctx.close()
+    return out
 
 
 def _ncu_traffic():
@@ -311,6 +367,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["pdd", "reference"], default="pdd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-naive", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-scale", type=float, default=0.05)
     ap.add_argument("--paths", type=int, default=None,
                     help="paths per node (profiling runs only; the benchmark uses 1e5)")
     args = ap.parse_args()

@@ -290,6 +290,16 @@ PDD_API pdd_status pdd_subdomain_solve(pdd_ctx *ctx, const pdd_subdomain *sd,
                                        double *d_u, int64_t *iters,
                                        double *resid);
 
+/* The plain GPU form of pdd_interface_solve, kept as a comparison baseline:
+ * one kernel launch per node, one thread per path, block sums added to FP64
+ * node accumulators with atomics (so the last bits depend on scheduling), no
+ * work queue, no graph.  Same estimator and random streams as
+ * pdd_interface_solve (FP32 paths only).  Writes d_mean, d_se, d_npaths.  */
+PDD_API pdd_status pdd_interface_solve_naive(pdd_ctx *ctx, const double *d_nodes,
+                                             int64_t n, const pdd_mc_params *mc,
+                                             double *d_mean, double *d_se,
+                                             int64_t *d_npaths);
+
 /* Launch-shape and memory knobs of the path kernels (no effect on results,
  * which do not depend on scheduling):
  *   blocks_per_sm    resident 256-thread blocks per SM for the persistent

@@ -278,6 +278,26 @@ class Context:
             res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
         return res
 
+    def interface_solve_naive(self, nodes, *, seed: int, dt: float, n_paths: int,
+                              max_steps: int = 2**31 - 1, bridge: bool = True, out=None) -> dict:
+        """pdd_interface_solve_naive (one launch per node, thread per path)."""
+        dim = int(self.prob["dim"])
+        nodes = _dev_f64(nodes, self.device).reshape(-1, dim)
+        n = nodes.shape[0]
+        if out is None:
+            out = (torch.empty(n, dtype=_F64, device=self.device),
+                   torch.empty(n, dtype=_F64, device=self.device),
+                   torch.empty(n, dtype=_I64, device=self.device))
+        mc = _lib.MCParams(int(seed) & (2**64 - 1), float(dt), int(n_paths), int(max_steps), 0,
+                           _lib.PRECISION["fp32"], int(bool(bridge)))
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_interface_solve_naive(self.handle, nodes.data_ptr(), n,
+                                                    ctypes.byref(mc), out[0].data_ptr(),
+                                                    out[1].data_ptr(), out[2].data_ptr())
+        _lib.check(st, self.handle)
+        return {"mean": out[0], "se": out[1], "n": out[2]}
+
     def philox_stream(self, seed: int, j0: int, c1: int, c2: int, c3: int, n_blocks: int):
         """pdd_philox_stream: uint32 [n_blocks, 4] CUDA tensor."""
         out = torch.empty((int(n_blocks), 4), dtype=torch.int32, device=self.device)

@@ -176,6 +176,14 @@ pdd_status pdd_batch_solve(pdd_ctx *ctx, const pdd_problem *problems, int32_t n_
                                use_graph, diag);
 }
 
+pdd_status pdd_interface_solve_naive(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                     const pdd_mc_params *mc, double *d_mean, double *d_se,
+                                     int64_t *d_npaths) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::interface_solve_naive_impl(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths);
+}
+
 pdd_status pdd_profile(pdd_ctx *ctx, int enable) {
   if (!ctx) return PDD_EINVAL;
   ctx->profiling = enable != 0;
