@@ -300,6 +300,26 @@ PDD_API pdd_status pdd_interface_solve_naive(pdd_ctx *ctx, const double *d_nodes
                                              double *d_mean, double *d_se,
                                              int64_t *d_npaths);
 
+/* Autotuner (launch shape only; results never depend on it).  Runs the
+ * given interface solve (use a reduced n_paths: each candidate runs
+ * repeats + 1 times) for every resident-blocks-per-SM count the device
+ * allows (up to 8), times each on the context's stream, keeps the fastest
+ * (fewer blocks on ties within 1%) in the context and reports it.
+ * d_scratch_out is a caller buffer of 2n doubles for the trial outputs.
+ * Synchronises.                                                            */
+PDD_API pdd_status pdd_autotune(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                const pdd_mc_params *mc, double *d_scratch_out,
+                                int32_t repeats, int32_t *best_blocks_per_sm,
+                                double *best_ms);
+
+/* Same for pdd_batch_solve's lane-chunk size (32 .. 1024 paths). */
+PDD_API pdd_status pdd_autotune_batch(pdd_ctx *ctx, const pdd_problem *problems,
+                                      int32_t n_problems,
+                                      const pdd_batch_nodes *nodes,
+                                      const pdd_batch_params *bp,
+                                      double *d_scratch_out, int32_t repeats,
+                                      int32_t *best_chunk, double *best_ms);
+
 /* Launch-shape and memory knobs of the path kernels (no effect on results,
  * which do not depend on scheduling):
  *   blocks_per_sm    resident 256-thread blocks per SM for the persistent

@@ -94,6 +94,13 @@ _SIGS = {
                                        _VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(Diag)]),
     "pdd_interface_solve_naive": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(MCParams), _VP,
                                                  _VP, _VP]),
+    "pdd_autotune": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(MCParams), _VP, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_double)]),
+    "pdd_autotune_batch": (ctypes.c_int, [_VP, ctypes.POINTER(Problem), ctypes.c_int32,
+                                          ctypes.POINTER(BatchNodes), ctypes.POINTER(BatchParams),
+                                          _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_double)]),
     "pdd_philox_stream": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _U32, _I64, _VP]),
     "pdd_destroy": (None, [_VP]),
     "pdd_status_string": (ctypes.c_char_p, [ctypes.c_int]),

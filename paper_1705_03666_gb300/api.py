@@ -298,6 +298,24 @@ class Context:
         _lib.check(st, self.handle)
         return {"mean": out[0], "se": out[1], "n": out[2]}
 
+    def autotune(self, nodes, *, seed: int, dt: float, n_paths: int, precision: str = "fp32",
+                 bridge: bool = True, repeats: int = 2) -> dict:
+        """pdd_autotune: pick the resident blocks per SM of the path kernels."""
+        dim = int(self.prob["dim"])
+        nodes = _dev_f64(nodes, self.device).reshape(-1, dim)
+        n = nodes.shape[0]
+        scratch = torch.empty(2 * n, dtype=_F64, device=self.device)
+        mc = _lib.MCParams(int(seed) & (2**64 - 1), float(dt), int(n_paths), 2**31 - 1, 0,
+                           _lib.PRECISION[precision], int(bool(bridge)))
+        b, ms = ctypes.c_int32(0), ctypes.c_double(0.0)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_autotune(self.handle, nodes.data_ptr(), n, ctypes.byref(mc),
+                                       scratch.data_ptr(), int(repeats), ctypes.byref(b),
+                                       ctypes.byref(ms))
+        _lib.check(st, self.handle)
+        return {"blocks_per_sm": b.value, "ms": ms.value}
+
     def philox_stream(self, seed: int, j0: int, c1: int, c2: int, c3: int, n_blocks: int):
         """pdd_philox_stream: uint32 [n_blocks, 4] CUDA tensor."""
         out = torch.empty((int(n_blocks), 4), dtype=torch.int32, device=self.device)

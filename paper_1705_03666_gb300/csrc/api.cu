@@ -184,6 +184,25 @@ pdd_status pdd_interface_solve_naive(pdd_ctx *ctx, const double *d_nodes, int64_
   return pdd::interface_solve_naive_impl(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths);
 }
 
+pdd_status pdd_autotune(pdd_ctx *ctx, const double *d_nodes, int64_t n, const pdd_mc_params *mc,
+                        double *d_scratch_out, int32_t repeats, int32_t *best_blocks_per_sm,
+                        double *best_ms) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::autotune_impl(ctx, d_nodes, n, mc, d_scratch_out, repeats, best_blocks_per_sm,
+                            best_ms);
+}
+
+pdd_status pdd_autotune_batch(pdd_ctx *ctx, const pdd_problem *problems, int32_t n_problems,
+                              const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
+                              double *d_scratch_out, int32_t repeats, int32_t *best_chunk,
+                              double *best_ms) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::autotune_batch_impl(ctx, problems, n_problems, nodes, bp, d_scratch_out, repeats,
+                                  best_chunk, best_ms);
+}
+
 pdd_status pdd_profile(pdd_ctx *ctx, int enable) {
   if (!ctx) return PDD_EINVAL;
   ctx->profiling = enable != 0;

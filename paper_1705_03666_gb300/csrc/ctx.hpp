@@ -133,6 +133,13 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
 pdd_status interface_solve_naive_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                                       const pdd_mc_params *mc, double *d_mean, double *d_se,
                                       int64_t *d_npaths);
+pdd_status autotune_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n, const pdd_mc_params *mc,
+                         double *d_scratch_out, int32_t repeats, int32_t *best_bps,
+                         double *best_ms);
+pdd_status autotune_batch_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n_problems,
+                               const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
+                               double *d_scratch_out, int32_t repeats, int32_t *best_chunk,
+                               double *best_ms);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

@@ -205,3 +205,15 @@ def test_elliptic_full_size_sampled_parity(api, orc):
           f"max node rel {c['node_rel'].max():.2e}")
     assert c["flip_frac"] <= FLIP_MAX_FP32
     assert c["node_rel"].max() <= NODE_REL_TOL
+
+
+def test_autotune_picks_a_shape_and_keeps_results(api):
+    w = W.workload(2)
+    nodes = torch.from_numpy(w["nodes"][::8])
+    kw = dict(seed=w["seed"], dt=1e-3, n_paths=500, precision="fp32")
+    with api.Context(w["prob"]) as ctx:
+        before = ctx.interface_solve(nodes, **kw)["mean"].clone()
+        t = ctx.autotune(nodes, repeats=1, **kw)
+        after = ctx.interface_solve(nodes, **kw)["mean"]
+    assert 1 <= t["blocks_per_sm"] <= 8 and t["ms"] > 0
+    assert torch.equal(before, after)
