@@ -349,14 +349,36 @@ def run_batch_once(api, dev, scale: float = 0.05) -> dict:
     return out
 
 
+KERNEL_SOURCES = ("paper_1705_03666_gb300/csrc/path_kernel.cuh",
+                  "paper_1705_03666_gb300/csrc/models.cuh",
+                  "paper_1705_03666_gb300/csrc/common.cuh")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _ncu_traffic():
-    """DRAM bytes per launch of the path kernel from the committed ncu summary,
-    when one exists for the current kernel (None otherwise)."""
-    p = os.path.join(ROOT, "profiles", "path_kernel_elliptic3d_traffic.json")
+    """DRAM bytes per launch of the path kernel from the committed ncu
+    summary, while the kernel sources are the ones it was measured on (None
+    otherwise)."""
+    p = os.path.join(ROOT, "profiles", "path_kernel_elliptic3d_4096x1e5_dram.md")
     try:
+        fields = {}
         with open(p) as f:
-            return json.load(f).get("dram_bytes_per_launch")
-    except (OSError, ValueError):
+            for line in f:
+                if ":" in line and not line.startswith(("#", "|", " ")):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("kernel_source_sha1") != kernel_source_hash():
+            return None
+        return int(fields["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
         return None
 
 

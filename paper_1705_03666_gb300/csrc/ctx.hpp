@@ -10,7 +10,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/pdd.h"
+#include "pdd.h"
 #include "models.cuh"
 
 // Everything a captured batch graph depends on.
