@@ -371,6 +371,15 @@ PDD_API pdd_status pdd_philox_stream(pdd_ctx *ctx, uint64_t seed, uint32_t j0,
                              uint32_t c1, uint32_t c2, uint32_t c3,
                              int64_t n_blocks, uint32_t *d_out);
 
+/* The FP32 standard normals and uniforms the path kernels draw: for pair j
+ * (j < n_pairs) the Box-Muller pair of words 0 and 1 of
+ * Philox((j, c1, c2, c3), key = seed) into d_z[2j], d_z[2j+1] and the
+ * uniform of word 2 into d_u[j] (d_u may be NULL).  Exposes the binary32
+ * normal generator so that it can be checked against an FP64 one.        */
+PDD_API pdd_status pdd_normals(pdd_ctx *ctx, uint64_t seed, uint32_t c1,
+                               uint32_t c2, uint32_t c3, int64_t n_pairs,
+                               float *d_z, float *d_u);
+
 /* Release the context and its device scratch (synchronises its stream). */
 PDD_API void pdd_destroy(pdd_ctx *ctx);
 

@@ -101,6 +101,7 @@ _SIGS = {
                                           ctypes.POINTER(BatchNodes), ctypes.POINTER(BatchParams),
                                           _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_double)]),
+    "pdd_normals": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _I64, _VP, _VP]),
     "pdd_philox_stream": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _U32, _I64, _VP]),
     "pdd_destroy": (None, [_VP]),
     "pdd_status_string": (ctypes.c_char_p, [ctypes.c_int]),

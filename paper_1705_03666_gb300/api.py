@@ -316,6 +316,17 @@ class Context:
         _lib.check(st, self.handle)
         return {"blocks_per_sm": b.value, "ms": ms.value}
 
+    def normals(self, seed: int, n_pairs: int, c1: int = 0, c2: int = 0, c3: int = 9):
+        """pdd_normals: (z [2 n_pairs] float32, u [n_pairs] float32) CUDA tensors."""
+        z = torch.empty(2 * int(n_pairs), dtype=torch.float32, device=self.device)
+        u = torch.empty(int(n_pairs), dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_normals(self.handle, int(seed) & (2**64 - 1), int(c1), int(c2),
+                                      int(c3), int(n_pairs), z.data_ptr(), u.data_ptr())
+        _lib.check(st, self.handle)
+        return z, u
+
     def philox_stream(self, seed: int, j0: int, c1: int, c2: int, c3: int, n_blocks: int):
         """pdd_philox_stream: uint32 [n_blocks, 4] CUDA tensor."""
         out = torch.empty((int(n_blocks), 4), dtype=torch.int32, device=self.device)

@@ -227,6 +227,13 @@ pdd_status pdd_profile_read(pdd_ctx *ctx, double *kernel_ms, int64_t *launches) 
   return PDD_OK;
 }
 
+pdd_status pdd_normals(pdd_ctx *ctx, uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
+                       int64_t n_pairs, float *d_z, float *d_u) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::normals_impl(ctx, seed, c1, c2, c3, n_pairs, d_z, d_u);
+}
+
 pdd_status pdd_philox_stream(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                              uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out) {
   if (!ctx) return PDD_EINVAL;

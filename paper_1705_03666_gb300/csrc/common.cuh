@@ -142,12 +142,34 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, R &z0, R &z1)
 // binary32 Box-Muller with the hardware sine/cosine.  The angle is centred,
 // theta = 2 pi (U_b - 1/2) in (-pi, pi), where the hardware sin/cos have an
 // absolute error below 2^-21.4; cos(2 pi U_b) = -cos theta and
-// sin(2 pi U_b) = -sin theta.  ln U_a keeps CUDA's accurate logf (a fast log
-// loses all accuracy as U_a -> 1); the square root is y * rsqrt(y)
-// (y >= 1.19e-7, never 0).
+// sin(2 pi U_b) = -sin theta.  -2 ln U_a comes from neg2log (accurate as
+// U_a -> 1, where a hardware log loses all accuracy); the square root is
+// y * rsqrt(y) (y >= 1.19e-7, never 0).
+// -2 ln u for u in (0, 1), binary32, from the atanh series of the logarithm:
+// write u = 2^e m with m in [sqrt(1/2), sqrt(2)) (exponent split on the bit
+// pattern), then ln u = e ln 2 + 2 atanh(t), t = (m - 1)/(m + 1), |t| <= 0.1716,
+// atanh t = t (1 + t^2/3 + t^4/5 + t^6/7 + t^8/9 + ...), truncation below
+// 3.5e-10 relative.  m - 1 is exact (Sterbenz), so the relative accuracy holds
+// as u -> 1, where a hardware log2 loses it.  e is converted with the
+// 1.5 * 2^23 magic constant (exact for |e| < 2^22).
+__device__ __forceinline__ float neg2log(float u) {
+  const uint32_t bits = __float_as_uint(u);
+  const int32_t e = static_cast<int32_t>(bits - 0x3f3504f3u) >> 23;
+  const float m = __uint_as_float(bits - (static_cast<uint32_t>(e) << 23));
+  const float t = __fdividef(m - 1.0f, m + 1.0f);
+  const float s = t * t;
+  float p = fmaf(s, 1.0f / 9.0f, 1.0f / 7.0f);
+  p = fmaf(s, p, 1.0f / 5.0f);
+  p = fmaf(s, p, 1.0f / 3.0f);
+  p = fmaf(s, p, 1.0f);
+  const float ef = __int_as_float(0x4b400000 + e) - 12582912.0f;
+  // -2 ln u = -2 ln2 e - 4 t p
+  return fmaf(-1.3862943611198906f, ef, -4.0f * t * p);
+}
+
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1) {
-  const float y = -2.0f * logf(unif_f(a));
+  const float y = neg2log(unif_f(a));
   const float mr = -(y * rsqrtf(y));
   float s, c;
   __sincosf(6.28318530717958648f * (unif_f(b) - 0.5f), &s, &c);

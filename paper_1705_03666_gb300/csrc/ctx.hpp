@@ -140,6 +140,8 @@ pdd_status autotune_batch_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_
                                const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
                                double *d_scratch_out, int32_t repeats, int32_t *best_chunk,
                                double *best_ms);
+pdd_status normals_impl(pdd_ctx *ctx, uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
+                        int64_t n_pairs, float *d_z, float *d_u);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

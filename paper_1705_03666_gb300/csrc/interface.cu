@@ -16,6 +16,33 @@ __global__ void philox_stream_kernel(RoundKeys rk, uint32_t j0, uint32_t c1, uin
     out[b] = philox10(j0 + static_cast<uint32_t>(b), c1, c2, c3, rk);
 }
 
+// FP32 normals and uniforms exactly as the path kernels form them:
+// pair j: BM(w0, w1) of Philox((j, c1, c2, c3)), uniform of w2.
+__global__ void normals_kernel(RoundKeys rk, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n,
+                               float *z, float *u) {
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+       j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint4 w = philox10(static_cast<uint32_t>(j), c1, c2, c3, rk);
+    float z0, z1;
+    box_muller<float>(w.x, w.y, z0, z1);
+    z[2 * j] = z0;
+    z[2 * j + 1] = z1;
+    if (u) u[j] = unif_f(w.z);
+  }
+}
+
+pdd_status normals_impl(pdd_ctx *ctx, uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
+                        int64_t n_pairs, float *d_z, float *d_u) {
+  if (n_pairs < 0 || (n_pairs > 0 && !d_z)) return fail(ctx, PDD_EINVAL, "bad arguments");
+  if (n_pairs == 0) return PDD_OK;
+  PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int grid = static_cast<int>(std::min<int64_t>((n_pairs + 255) / 256, 8192));
+  normals_kernel<<<grid, 256, 0, ctx->stream>>>(make_round_keys(seed), c1, c2, c3, n_pairs, d_z,
+                                                d_u);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  return PDD_OK;
+}
+
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out) {
   if (n_blocks < 0) return fail(ctx, PDD_EINVAL, "n_blocks < 0");

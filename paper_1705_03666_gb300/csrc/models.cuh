@@ -187,31 +187,36 @@ struct Box {
     const R v = x[j >> 1];
     return (j & 1) ? R(1) - v : v;
   }
-  // Bridge candidates.  For axis k the products d d' for its two faces are
-  // x0 x1 and (1 - x0)(1 - x1); both can be below 9 sigma^2 dt only when
-  // sigma^2 dt > 1/36 (excluded by the caller), so one face per axis -- the
-  // one with the smaller product -- is the only one that can contribute.
-  // prod[k] = that product, face[k] = its index; returns whether any axis has
-  // prod < thr (thr = 9 sigma^2 dt, i.e. 2 d d' / (sigma^2 dt) < 18).
+  // Screening of a step X -> X' (X strictly inside).  Per axis k:
+  //   m[k] = min(x_k x'_k, (1 - x_k)(1 - x'_k)), the d d' of the axis' face
+  //          that can be within bridge reach (the other one cannot while
+  //          sigma^2 dt <= 1/36);
+  //   min(x'_k, 1 - x'_k) >= 0 exactly when x'_k lies in [0, 1] (1 - x' is
+  //          exact near 1, so the sign is exact).
+  // Returns the smallest m in mn and the smallest min(x', 1 - x') in ins
+  // (ins < 0: X' is outside the closed box).
   template <typename R>
-  __device__ __forceinline__ static bool near_faces(const R *x0, const R *x1, R thr, R *prod,
-                                                    int *face) {
-    bool nr = false;
+  __device__ __forceinline__ static void screen_min(const R *x0, const R *x1, R *m, R &mn,
+                                                    R &ins) {
+    mn = R(1);
+    ins = R(1);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const R lo = x0[k] * x1[k], hi = (R(1) - x0[k]) * (R(1) - x1[k]);
-      const bool up = hi < lo;
-      prod[k] = up ? hi : lo;
-      face[k] = 2 * k + (up ? 1 : 0);
-      nr = nr || (prod[k] < thr);
+      const R o1 = R(1) - x1[k];
+      m[k] = fmin(x0[k] * x1[k], (R(1) - x0[k]) * o1);
+      mn = fmin(mn, m[k]);
+      ins = fmin(ins, fmin(x1[k], o1));
     }
-    return nr;
   }
-  // Bridge screening of a step X -> X' inside the closed box: for axis k the
-  // products d d' of its two faces are x_k x'_k and (1 - x_k)(1 - x'_k).
-  // prod[k] = the smaller one, face[k] its face (the other face of the axis
-  // cannot be within reach while sigma^2 dt <= 1/36); returns the minimum
-  // over the axes (the nearest face's d d').
+  // Second smallest of m[0..D-1] (D <= 3): below the reach threshold means
+  // the step is within reach of two faces (an edge or a corner).
+  template <typename R>
+  __device__ __forceinline__ static R second_min(const R *m) {
+    if constexpr (D == 1) return R(1);
+    else if constexpr (D == 2) return fmax(m[0], m[1]);
+    else return fmax(fmin(m[0], m[1]), fmin(fmax(m[0], m[1]), m[2]));
+  }
+  // Candidate faces with their d d' (rarely needed: corners and exits).
   template <typename R>
   __device__ __forceinline__ static R screen(const R *x0, const R *x1, R *prod, int *face) {
     R mn = R(1);

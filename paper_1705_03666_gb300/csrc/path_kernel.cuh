@@ -106,7 +106,7 @@ __device__ __forceinline__ int bridge_exit(const StepConst<R> &k, const R *prod,
   for (int c = 0; c < NC; ++c) {
     const R aa = R(2) * prod[c] * k.inv_s2dt;
     if (aa < R(18)) {
-      const R p = m_exp(-aa);
+      const R p = k.exp_neg(aa);
       P = P + p * (R(1) - P);
       if (p > pbest) { pbest = p; jbest = face[c]; }
     }
@@ -198,12 +198,12 @@ __device__ __forceinline__ bool em_step(const Env &a, const StepConst<R> &k,
   if constexpr (Model::kSource) Zn = Z + f * Y * k.dt;
   R Yn = Y;
   if constexpr (Model::kKill == 1) Yn = k.kill(Y, n + 1);
-  if (!Geom::inside_closed(Xn)) {  // X' outside the closed domain
-    Geom::segment_exit(X, Xn, xe);
-    s = Model::g(a.mc, xe) * Yn + Zn;
-    return true;
-  }
   if constexpr (!Geom::kFastScreen) {
+    if (!Geom::inside_closed(Xn)) {  // X' outside the closed domain
+      Geom::segment_exit(X, Xn, xe);
+      s = Model::g(a.mc, xe) * Yn + Zn;
+      return true;
+    }
     // general domains: every face within reach, P = 1 - prod (1 - p_j)
     if (a.bridge) {
       const int jbest = bridge_generic<Geom, R>(k, X, Xn, unif<R>(uw));
@@ -215,43 +215,44 @@ __device__ __forceinline__ bool em_step(const Env &a, const StepConst<R> &k,
         return true;
       }
     }
-#pragma unroll
-    for (int d = 0; d < D; ++d) X[d] = Xn[d];
-    Y = Yn;
-    Z = Zn;
-    return false;
   } else {
-  R prod[D];
-  int face[D];
-  const R mn = Geom::screen(X, Xn, prod, face);
-  // Bridge: the single-face probability exp(-2 min d d' / (sigma^2 dt)) is
-  // formed without a branch; a step within reach of two or more faces
-  // (near an edge or corner) takes the general combination.
-  bool cross = false;
-  if (a.bridge) {
-    const R U = unif<R>(uw);
-    int near = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) near += prod[d] < k.thr ? 1 : 0;
-    if (near > 1) {
-      cross = bridge_exit<D, R>(k, prod, face, U) >= 0;
-    } else {
-      const R p = k.exp_neg(R(2) * mn * k.inv_s2dt);
-      cross = U < p;
-      if constexpr (sizeof(R) == 4) {
-        if (fabsf(U - p) <= 3.814697265625e-06f * p)  // near tie: FP64
-          cross = static_cast<double>(U) <
-                  exp(-2.0 * static_cast<double>(mn) * static_cast<double>(k.inv_s2dt));
+    R m[D], mn, ins;
+    Geom::screen_min(X, Xn, m, mn, ins);
+    if (ins < R(0)) {  // X' outside the closed box
+      Geom::segment_exit(X, Xn, xe);
+      s = Model::g(a.mc, xe) * Yn + Zn;
+      return true;
+    }
+    // Bridge: the single-face probability exp(-2 min d d' / (sigma^2 dt)) is
+    // formed without a branch; a step within reach of two or more faces (an
+    // edge or a corner) takes the general combination.
+    bool cross = false;
+    if (a.bridge) {
+      const R U = unif<R>(uw);
+      if (Geom::second_min(m) < k.thr) {
+        R prod[D];
+        int face[D];
+        Geom::screen(X, Xn, prod, face);
+        cross = bridge_exit<D, R>(k, prod, face, U) >= 0;
+      } else {
+        const R p = k.exp_neg(R(2) * mn * k.inv_s2dt);
+        cross = U < p;
+        if constexpr (sizeof(R) == 4) {
+          if (fabsf(U - p) <= 3.814697265625e-06f * p)  // near tie: FP64
+            cross = static_cast<double>(U) <
+                    exp(-2.0 * static_cast<double>(mn) * static_cast<double>(k.inv_s2dt));
+        }
       }
     }
-  }
-  if (cross) {
-    int jbest = face[0];
-    R pmin = prod[0];
+    if (cross) {
+      R prod[D];
+      int face[D];
+      Geom::screen(X, Xn, prod, face);
+      int jbest = face[0];
+      R pmin = prod[0];
 #pragma unroll
-    for (int d = 1; d < D; ++d)
-      if (prod[d] < pmin) { pmin = prod[d]; jbest = face[d]; }
-    {
+      for (int d = 1; d < D; ++d)
+        if (prod[d] < pmin) { pmin = prod[d]; jbest = face[d]; }
 #pragma unroll
       for (int d = 0; d < D; ++d) xe[d] = Xn[d];
       Geom::project(jbest, xe);
@@ -264,7 +265,6 @@ __device__ __forceinline__ bool em_step(const Env &a, const StepConst<R> &k,
   Y = Yn;
   Z = Zn;
   return false;
-  }
 }
 
 // Per-path record of the gradient mode: score, exit point, and the

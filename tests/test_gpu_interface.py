@@ -55,6 +55,20 @@ def test_philox_bit_exact(api, orc):
             assert np.array_equal(g, o), (seed, j0, c1, c2, c3)
 
 
+def test_fp32_normals_match_oracle(api, orc):
+    """The binary32 Box-Muller normals (custom -2 ln u, hardware sin/cos on a
+    centred angle) against the oracle's FP64 normals from the same words."""
+    n = 1 << 22
+    with api.Context(W.laplace_expcos()) as ctx:
+        z, u = ctx.normals(W.SEED_BASE + 7, n, 3, 4, 9)
+    zo, uo = orc.normals(W.SEED_BASE + 7, n, 3, 4, 9)
+    z, u = z.cpu().numpy().astype(np.float64), u.cpu().numpy().astype(np.float64)
+    assert np.array_equal(u, uo)                               # exact uniforms
+    err = np.abs(z - zo)
+    assert err.max() < 2e-6 * max(1.0, np.abs(zo).max())     # ~1e-7 relative + trig
+    assert np.mean(err) < 2e-7
+
+
 def test_laplace_fp64_matches_oracle_path_by_path(api, orc):
     w = W.workload(1)
     kw = dict(seed=w["seed"], dt=w["dt"], n_paths=4000)
