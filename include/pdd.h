@@ -147,7 +147,8 @@ PDD_API pdd_status pdd_set_stream(pdd_ctx *ctx, void *cuda_stream);
  * u = g(x_i) with zero error.  Path i of node j uses the Philox stream
  * (key = seed, counter = (block, path_offset + i, j, 0)); the per-step use of
  * that stream is fixed (2-D: one block per step, normals from words 0-1 by
- * Box-Muller, bridge uniform from word 2; 3-D: two blocks per pair of steps).
+ * Box-Muller, bridge uniform from word 2; 3-D: three blocks per four steps,
+ * normals from the word pairs, bridge uniforms from the words' low bytes).
  * With diag non-NULL the call synchronises and returns PDD_ECAP if some path
  * hit max_steps, PDD_EINVAL if a node lies outside the closed domain (its
  * mean is NaN either way).                                                 */

@@ -382,9 +382,9 @@ static int nearest_face(int geom, int dim, const double *x) {
 /* Step n draws d normals xi_n and one uniform U_n:                          */
 /*   d = 1: xi = BM(w[4n], w[4n+1]).first,          U = w[4n+2]              */
 /*   d = 2: xi = BM(w[4n], w[4n+1]),                U = w[4n+2]              */
-/*   d = 3, n = 2m:   (a,b)=BM(w[8m],w[8m+1]), (c,e)=BM(w[8m+2],w[8m+3]),    */
-/*                    xi = (a,b,c), U = w[8m+6]                              */
-/*          n = 2m+1: (p,q)=BM(w[8m+4],w[8m+5]), xi = (e,p,q), U = w[8m+7]   */
+/*   d = 3, n = 4q + j: blocks 3q..3q+2 give words v0..v11 and normals     */
+/*                    z0..z11 = BM(v0,v1), ..., BM(v10,v11); xi = z[3j..3j+2], */
+/*                    U from the low bytes of v[3j], v[3j+1], v[3j+2]        */
 /*                                                                          */
 /* Step n -> n+1 (left-point rule for Y and Z, Eq. 2.8):                     */
 /*   X' = X + b(X) dt + sigma sqrt(dt) xi,  Y' = Y exp(c(X) dt),             */
@@ -445,8 +445,8 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
     if (xexit) for (int k = 0; k < 3; ++k) xexit[k] = X[k];
     return;
   }
-  uint32_t A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
-  double spare = 0.0;
+  uint32_t A[4] = {0, 0, 0, 0}, W12[12];
+  double N12[12];
   for (int64_t n = 0; n < M->max_steps; ++n) {
     double xi[3] = {0, 0, 0}, U;
     if (dim <= 2) {
@@ -458,24 +458,25 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
       if (dim == 2) xi[1] = z1;
       U = unif(A[2]);
     } else {
-      uint32_t m = (uint32_t)(n >> 1);
-      if ((n & 1) == 0) {
-        uint32_t ca[4] = {2u * m, path, node, 0u};
-        uint32_t cb[4] = {2u * m + 1u, path, node, 0u};
-        orc_philox4x32_10(ca, key, A);
-        orc_philox4x32_10(cb, key, B);
-        double a, b, c, e;
-        box_muller(A[0], A[1], &a, &b);
-        box_muller(A[2], A[3], &c, &e);
-        xi[0] = a; xi[1] = b; xi[2] = c;
-        spare = e;
-        U = unif(B[2]);
-      } else {
-        double p, q;
-        box_muller(B[0], B[1], &p, &q);
-        xi[0] = spare; xi[1] = p; xi[2] = q;
-        U = unif(B[3]);
+      /* d = 3: steps 4q .. 4q+3 use the 12 words w[0..11] of blocks 3q,
+       * 3q+1, 3q+2; normals nrm[0..11] = Box-Muller of the word pairs
+       * (w0,w1), ..., (w10,w11); step 4q+j takes nrm[3j..3j+2] and the
+       * uniform of the word whose bytes 3, 2, 1 are the low bytes of
+       * w[3j+2], w[3j+1], w[3j] (bits the Box-Muller maps do not use).   */
+      uint32_t q = (uint32_t)(n >> 2);
+      int j = (int)(n & 3);
+      if (j == 0) {
+        for (int b = 0; b < 3; ++b) {
+          uint32_t cb[4] = {3u * q + (uint32_t)b, path, node, 0u};
+          orc_philox4x32_10(cb, key, W12 + 4 * b);
+        }
+        for (int pr = 0; pr < 6; ++pr)
+          box_muller(W12[2 * pr], W12[2 * pr + 1], &N12[2 * pr], &N12[2 * pr + 1]);
       }
+      xi[0] = N12[3 * j]; xi[1] = N12[3 * j + 1]; xi[2] = N12[3 * j + 2];
+      uint32_t wu = ((W12[3 * j + 2] & 255u) << 24) | ((W12[3 * j + 1] & 255u) << 16) |
+                    ((W12[3 * j] & 255u) << 8);
+      U = unif(wu);
     }
     double b[3];
     coef_drift(P, X, b);

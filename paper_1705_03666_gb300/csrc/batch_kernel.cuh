@@ -73,43 +73,15 @@ struct BatchLane {
   PhiloxPath pp;
 };
 
-// One loop unit of a path of family Model on domain Geom: one step for d <= 2,
-// a pair of steps (two Philox blocks) for d = 3.  Returns true when the path
-// exited (score in s); the caller handles the step cap.
+// One loop unit (path_unit) of a path of family Model on domain Geom.
+// Returns true when the path exited (score in s); the caller handles the cap.
 template <class Model, class Geom>
 __device__ __forceinline__ bool batch_unit(const BatchEnv &env, const StepConst<float> &k,
                                            const RoundKeys &rk, int32_t max_steps, BatchLane &L,
                                            float &s) {
-  constexpr int D = Model::D;
-  float xe[D], lr[1];
-  bool done;
-  if constexpr (D == 3) {
-    const uint32_t j = static_cast<uint32_t>(L.n);
-    const uint4 A = philox10_path(j, L.pp, rk);
-    const uint4 B = philox10_path(j + 1u, L.pp, rk);
-    float xi[3], e;
-    box_muller<float>(A.x, A.y, xi[0], xi[1]);
-    box_muller<float>(A.z, A.w, xi[2], e);
-    done = em_step<Model, Geom, float, false>(env, k, L.X, L.Y, L.Z, xi, B.z, L.n, s, xe, lr);
-    ++L.n;
-    if (!done && L.n < max_steps) {
-      float p, q;
-      box_muller<float>(B.x, B.y, p, q);
-      xi[0] = e;
-      xi[1] = p;
-      xi[2] = q;
-      done = em_step<Model, Geom, float, false>(env, k, L.X, L.Y, L.Z, xi, B.w, L.n, s, xe, lr);
-      ++L.n;
-    }
-  } else {
-    const uint4 A = philox10_path(static_cast<uint32_t>(L.n), L.pp, rk);
-    float xi[2], z1;
-    box_muller<float>(A.x, A.y, xi[0], z1);
-    xi[1] = z1;
-    done = em_step<Model, Geom, float, false>(env, k, L.X, L.Y, L.Z, xi, A.z, L.n, s, xe, lr);
-    ++L.n;
-  }
-  return done;
+  float xe[Model::D], lr[1];
+  return path_unit<Model, Geom, float, false>(env, k, L.pp, rk, max_steps, L.X, L.Y, L.Z, L.n, s,
+                                              xe, lr);
 }
 
 // Score of a capped path: g at the projection on the nearest face.

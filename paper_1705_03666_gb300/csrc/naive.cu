@@ -29,33 +29,8 @@ naive_node_kernel(const __grid_constant__ PathArgs a, uint32_t node, double *acc
     const PhiloxPath pp = philox_path(static_cast<uint32_t>(p + a.path_offset), node, 0u, a.rk);
     bool done = !Geom::inside_open(X);
     if (done) s = Model::g(a.mc, X);
-    while (!done && n < a.max_steps) {
-      if constexpr (D == 3) {
-        const uint4 A = philox10_path(static_cast<uint32_t>(n), pp, a.rk);
-        const uint4 B = philox10_path(static_cast<uint32_t>(n) + 1u, pp, a.rk);
-        float xi[3], e;
-        box_muller<float>(A.x, A.y, xi[0], xi[1]);
-        box_muller<float>(A.z, A.w, xi[2], e);
-        done = em_step<Model, Geom, float, false>(a, k, X, Y, Z, xi, B.z, n, s, xe, lr);
-        ++n;
-        if (!done && n < a.max_steps) {
-          float q0, q1;
-          box_muller<float>(B.x, B.y, q0, q1);
-          xi[0] = e;
-          xi[1] = q0;
-          xi[2] = q1;
-          done = em_step<Model, Geom, float, false>(a, k, X, Y, Z, xi, B.w, n, s, xe, lr);
-          ++n;
-        }
-      } else {
-        const uint4 A = philox10_path(static_cast<uint32_t>(n), pp, a.rk);
-        float xi[2], z1;
-        box_muller<float>(A.x, A.y, xi[0], z1);
-        xi[1] = z1;
-        done = em_step<Model, Geom, float, false>(a, k, X, Y, Z, xi, A.z, n, s, xe, lr);
-        ++n;
-      }
-    }
+    while (!done && n < a.max_steps)
+      done = path_unit<Model, Geom, float, false>(a, k, pp, a.rk, a.max_steps, X, Y, Z, n, s, xe, lr);
     if (!done) {
 #pragma unroll
       for (int d = 0; d < D; ++d) xe[d] = X[d];

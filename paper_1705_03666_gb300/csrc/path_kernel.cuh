@@ -173,14 +173,25 @@ __device__ __forceinline__ int bridge_generic(const StepConst<R> &k, const R *X,
 // Number of likelihood-ratio accumulators carried per path (gradient mode).
 constexpr int kMaxLR = 16;
 
-// One Euler-Maruyama step with the exit test.  Returns true on exit, with
-// the score in `s` and the exit point in `xe`.  X, Y, Z advance only when the
-// path stays inside.  With kLR the drift-weight likelihood-ratio sums L are
-// advanced by this step's noise (the step that exits included).
+// FP64 re-decision of a near tie U ~ exp(-2 m / (sigma^2 dt)) (kept out of
+// line: it almost never runs and would otherwise be inlined at every step).
+static __device__ __noinline__ bool bridge_tie_fp64(float U, float mn, float inv_s2dt) {
+  return static_cast<double>(U) <
+         exp(-2.0 * static_cast<double>(mn) * static_cast<double>(inv_s2dt));
+}
+
+// Exit codes of em_step.
+constexpr int kStepContinue = -2;
+constexpr int kStepHardExit = -1;   // >= 0: bridge exit through that face
+
+// One Euler-Maruyama step with the exit test.  On kStepContinue, X, Y, Z
+// advance; on an exit, X keeps the start of the step, Xn receives its end,
+// Y and Z receive their exit values, and the caller resolves the exit point
+// (exit_score) once per unit.  With kLR the drift-weight likelihood-ratio
+// sums L are advanced by this step's noise (the exiting step included).
 template <class Model, class Geom, typename R, bool kLR, class Env>
-__device__ __forceinline__ bool em_step(const Env &a, const StepConst<R> &k,
-                                        R *X, R &Y, R &Z, const R *xi, uint32_t uw,
-                                        int32_t n, R &s, R *xe, R *L) {
+__device__ __forceinline__ int em_step(const Env &a, const StepConst<R> &k, R *X, R &Y, R &Z,
+                                       const R *xi, uint32_t uw, int32_t n, R *Xn, R *L) {
   constexpr int D = Model::D;
   R b[D];
   R f = R(0);
@@ -191,44 +202,31 @@ __device__ __forceinline__ bool em_step(const Env &a, const StepConst<R> &k,
   } else if constexpr (Model::kDrift || Model::kSource) {
     Model::coeffs(a.mc, X, b, f);
   }
-  R Xn[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) Xn[d] = X[d] + b[d] * k.dt + k.sdt * xi[d];
   R Zn = Z;
   if constexpr (Model::kSource) Zn = Z + f * Y * k.dt;
   R Yn = Y;
   if constexpr (Model::kKill == 1) Yn = k.kill(Y, n + 1);
+  Y = Yn;
+  Z = Zn;
   if constexpr (!Geom::kFastScreen) {
-    if (!Geom::inside_closed(Xn)) {  // X' outside the closed domain
-      Geom::segment_exit(X, Xn, xe);
-      s = Model::g(a.mc, xe) * Yn + Zn;
-      return true;
-    }
+    if (!Geom::inside_closed(Xn)) return kStepHardExit;
     // general domains: every face within reach, P = 1 - prod (1 - p_j)
     if (a.bridge) {
       const int jbest = bridge_generic<Geom, R>(k, X, Xn, unif<R>(uw));
-      if (jbest >= 0) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) xe[d] = Xn[d];
-        Geom::project(jbest, xe);
-        s = Model::g(a.mc, xe) * Yn + Zn;
-        return true;
-      }
+      if (jbest >= 0) return jbest;
     }
   } else {
     R m[D], mn, ins;
     Geom::screen_min(X, Xn, m, mn, ins);
-    if (ins < R(0)) {  // X' outside the closed box
-      Geom::segment_exit(X, Xn, xe);
-      s = Model::g(a.mc, xe) * Yn + Zn;
-      return true;
-    }
+    if (ins < R(0)) return kStepHardExit;  // X' outside the closed box
     // Bridge: the single-face probability exp(-2 min d d' / (sigma^2 dt)) is
     // formed without a branch; a step within reach of two or more faces (an
     // edge or a corner) takes the general combination.
-    bool cross = false;
     if (a.bridge) {
       const R U = unif<R>(uw);
+      bool cross;
       if (Geom::second_min(m) < k.thr) {
         R prod[D];
         int face[D];
@@ -238,33 +236,102 @@ __device__ __forceinline__ bool em_step(const Env &a, const StepConst<R> &k,
         const R p = k.exp_neg(R(2) * mn * k.inv_s2dt);
         cross = U < p;
         if constexpr (sizeof(R) == 4) {
-          if (fabsf(U - p) <= 3.814697265625e-06f * p)  // near tie: FP64
-            cross = static_cast<double>(U) <
-                    exp(-2.0 * static_cast<double>(mn) * static_cast<double>(k.inv_s2dt));
+          if (fabsf(U - p) <= 3.814697265625e-06f * p) cross = bridge_tie_fp64(U, mn, k.inv_s2dt);
         }
       }
-    }
-    if (cross) {
-      R prod[D];
-      int face[D];
-      Geom::screen(X, Xn, prod, face);
-      int jbest = face[0];
-      R pmin = prod[0];
+      if (cross) {
+        R prod[D];
+        int face[D];
+        Geom::screen(X, Xn, prod, face);
+        int jbest = face[0];
+        R pmin = prod[0];
 #pragma unroll
-      for (int d = 1; d < D; ++d)
-        if (prod[d] < pmin) { pmin = prod[d]; jbest = face[d]; }
-#pragma unroll
-      for (int d = 0; d < D; ++d) xe[d] = Xn[d];
-      Geom::project(jbest, xe);
-      s = Model::g(a.mc, xe) * Yn + Zn;
-      return true;
+        for (int d = 1; d < D; ++d)
+          if (prod[d] < pmin) { pmin = prod[d]; jbest = face[d]; }
+        return jbest;
+      }
     }
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) X[d] = Xn[d];
-  Y = Yn;
-  Z = Zn;
-  return false;
+  return kStepContinue;
+}
+
+// Exit point of a step that left the domain (first crossing of X -> Xn) or
+// crossed a face by the bridge (Xn projected on it), and the path's score
+// g(X_tau) Y + Z (Eq. 2.7).
+template <class Model, class Geom, typename R>
+__device__ __forceinline__ R exit_score(const ModelConst &mc, int code, const R *X, const R *Xn,
+                                        R Y, R Z, R *xe) {
+  constexpr int D = Model::D;
+  if (code == kStepHardExit) {
+    Geom::segment_exit(X, Xn, xe);
+  } else {
+#pragma unroll
+    for (int d = 0; d < D; ++d) xe[d] = Xn[d];
+    Geom::project(code, xe);
+  }
+  return Model::g(mc, xe) * Y + Z;
+}
+
+// Word whose bytes 3, 2, 1 are the low bytes of c, b, a: the bridge uniform
+// of a 3-D step comes from bits the Box-Muller maps (bits 9..31) do not use.
+__device__ __forceinline__ uint32_t low_bytes_word(uint32_t a, uint32_t b, uint32_t c) {
+  return __byte_perm(__byte_perm(a, b, 0x0400u), c, 0x4210u);
+}
+
+// One loop unit of a path.  d <= 2: one step n from Philox block n (normals
+// BM(w0, w1), bridge uniform w2).  d = 3: steps 4q .. 4q+3 from blocks 3q,
+// 3q+1, 3q+2, formed as the steps need them: normals z0..z11 = BM of the word
+// pairs (w0,w1) .. (w10,w11), step 4q+j takes z[3j..3j+2] and the uniform of
+// low_bytes_word(w[3j], w[3j+1], w[3j+2]).  n counts the steps taken; the unit
+// stops at an exit (returns true, score in s) or at max_steps.
+template <class Model, class Geom, typename R, bool kLR, class Env>
+__device__ __forceinline__ bool path_unit(const Env &a, const StepConst<R> &k, const PhiloxPath &pp,
+                                          const RoundKeys &rk, int32_t max_steps, R *X, R &Y,
+                                          R &Z, int32_t &n, R &s, R *xe, R *L) {
+  constexpr int D = Model::D;
+  R Xn[D];
+  int code;
+  if constexpr (D == 3) {
+    const uint32_t q3 = 3u * (static_cast<uint32_t>(n) >> 2);
+    do {
+      const uint4 A = philox10_path(q3, pp, rk);
+      R xi[3], z3;
+      box_muller<R>(A.x, A.y, xi[0], xi[1]);
+      box_muller<R>(A.z, A.w, xi[2], z3);
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, low_bytes_word(A.x, A.y, A.z), n, Xn, L);
+      ++n;
+      if (code != kStepContinue || n >= max_steps) break;
+      const uint4 B = philox10_path(q3 + 1u, pp, rk);
+      xi[0] = z3;
+      box_muller<R>(B.x, B.y, xi[1], xi[2]);
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, low_bytes_word(A.w, B.x, B.y), n, Xn, L);
+      ++n;
+      if (code != kStepContinue || n >= max_steps) break;
+      const uint4 C = philox10_path(q3 + 2u, pp, rk);
+      R z9;
+      box_muller<R>(B.z, B.w, xi[0], xi[1]);
+      box_muller<R>(C.x, C.y, xi[2], z9);
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, low_bytes_word(B.z, B.w, C.x), n, Xn, L);
+      ++n;
+      if (code != kStepContinue || n >= max_steps) break;
+      xi[0] = z9;
+      box_muller<R>(C.z, C.w, xi[1], xi[2]);
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, low_bytes_word(C.y, C.z, C.w), n, Xn, L);
+      ++n;
+    } while (false);
+  } else {
+    const uint4 A = philox10_path(static_cast<uint32_t>(n), pp, rk);
+    R xi[2], z1;
+    box_muller<R>(A.x, A.y, xi[0], z1);
+    xi[1] = z1;
+    code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, A.z, n, Xn, L);
+    ++n;
+  }
+  if (code == kStepContinue) return false;
+  s = exit_score<Model, Geom, R>(a.mc, code, X, Xn, Y, Z, xe);
+  return true;
 }
 
 // Per-path record of the gradient mode: score, exit point, and the
@@ -362,34 +429,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
 
     // ---- advance the lane's path
     R s = R(0);
-    bool done;
-    if constexpr (D == 3) {
-      // pair of steps 2m, 2m+1 from Philox blocks 2m and 2m+1
-      const uint32_t j = static_cast<uint32_t>(n);  // n is even here
-      const uint4 A = philox10_path(j, pp, a.rk);
-      const uint4 B = philox10_path(j + 1u, pp, a.rk);
-      R xi[3], e;
-      box_muller<R>(A.x, A.y, xi[0], xi[1]);
-      box_muller<R>(A.z, A.w, xi[2], e);
-      done = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, B.z, n, s, xe, L);
-      ++n;
-      if (!done && n < a.max_steps) {
-        R p, q;
-        box_muller<R>(B.x, B.y, p, q);
-        xi[0] = e;
-        xi[1] = p;
-        xi[2] = q;
-        done = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, B.w, n, s, xe, L);
-        ++n;
-      }
-    } else {
-      const uint4 A = philox10_path(static_cast<uint32_t>(n), pp, a.rk);
-      R xi[2], z1;
-      box_muller<R>(A.x, A.y, xi[0], z1);
-      if constexpr (D == 2) xi[1] = z1;
-      done = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, A.z, n, s, xe, L);
-      ++n;
-    }
+    bool done = path_unit<Model, Geom, R, kLR>(a, k, pp, a.rk, a.max_steps, X, Y, Z, n, s, xe, L);
     int32_t st = n;
     if (!done && n >= a.max_steps) {
       // step cap: score at the projection on the nearest face, counted
