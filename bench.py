@@ -261,6 +261,9 @@ def run_pdd(args):
     batch = None
     if not args.no_batch:
         batch = run_batch_once(api, dev, scale=args.batch_scale)
+    others = None
+    if not args.no_others and world == 1:
+        others = run_other_workloads(api, dev)
 
     if rank != 0:
         if world > 1:
@@ -308,11 +311,77 @@ def run_pdd(args):
         line["vs_naive_equal_se"] = naive
     if batch is not None:
         line["batch_adaptive"] = batch
+    if others is not None:
+        line["other_workloads"] = others
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed(stream, fn):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_other_workloads(api, dev) -> dict:
+    """One timed call (after one warm-up) of each other workload at full size:
+    KPP branching (1024 space-time nodes x 1e5 trees), the Poisson-Fourier
+    forward solve and its gradient (2048 nodes x 1e5 paths, dt = 1e-3), and
+    stage two of the 2-D Laplace workload (two 129 x 129 CG solves)."""
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    w = W.workload(4)
+    with api.Context(w["prob"], dev) as ctx:
+        nodes = torch.from_numpy(w["nodes"]).to(dev)
+        kw = dict(seed=w["seed"], n_trees=w["n_trees"], max_particles=w["max_particles"],
+                  max_depth=w["max_depth"])
+        r = ctx.branching_solve(nodes, diag=True, **kw)
+        ms, _ = _timed(stream, lambda: ctx.branching_solve(nodes, **kw))
+        out["kpp_branching"] = {"workload": w["name"], "ms": ms,
+                                "trees_per_s": len(w["nodes"]) * w["n_trees"] / (ms / 1e3),
+                                "segments_per_s": r["segments"] / (ms / 1e3),
+                                "nodes_per_s": len(w["nodes"]) / (ms / 1e3),
+                                "median_se": float(r["se"].median())}
+    w = W.workload(5)
+    with api.Context(w["prob"], dev) as ctx:
+        nodes = torch.from_numpy(w["nodes"]).to(dev)
+        kw = dict(seed=w["seed"], dt=w["dt"], n_paths=w["n_paths"])
+        r = ctx.interface_solve(nodes, diag=True, precision="fp32", **kw)
+        ms_f, _ = _timed(stream, lambda: ctx.interface_solve(nodes, precision="fp32", **kw))
+        gout = torch.ones(len(w["nodes"]), dtype=torch.float64, device=dev)
+        ctx.interface_grad(nodes, grad_out=gout, jacobian=False, **kw)
+        ms_g, _ = _timed(stream, lambda: ctx.interface_grad(nodes, grad_out=gout, **kw))
+        out["poisson_fourier_gradient"] = {
+            "workload": w["name"], "forward_ms": ms_f, "gradient_ms": ms_g,
+            "path_steps_per_s_forward": r["path_steps"] / (ms_f / 1e3),
+            "path_steps_per_s_gradient": r["path_steps"] / (ms_g / 1e3),
+            "outputs": "jacobian [2048, 80] + vjp (dtheta[64], dphi[16])"}
+    w = W.workload(1)
+    with api.Context(w["prob"], dev) as ctx:
+        r = ctx.interface_solve(torch.from_numpy(w["nodes"]).to(dev), seed=w["seed"], dt=w["dt"],
+                                n_paths=w["n_paths"], precision="fp64")
+        s = torch.from_numpy(w["nodes"][:, 1]).to(dev)
+        args_l = ((0.0, 0.0), (0.5, 1.0), (129, 129), 0, 1, s, r["mean"])
+        args_r = ((0.5, 0.0), (1.0, 1.0), (129, 129), 0, 0, s, r["mean"])
+        ctx.subdomain_solve(*args_l)
+        ms, (a, bb) = _timed(stream, lambda: (ctx.subdomain_solve(*args_l),
+                                              ctx.subdomain_solve(*args_r)))
+        iters = a["iters"] + bb["iters"]
+        alg_bytes = iters * 129 * 129 * 13 * 8
+        out["stage_two_cg"] = {"grids": "2 x 129 x 129", "ms": ms, "iterations": iters,
+                               "achieved_gbs": alg_bytes / (ms / 1e3) / 1e9,
+                               "bytes_model": "13 FP64 vector accesses per point per CG iteration",
+                               "residence": "L2/shared-resident (0.27 MB per vector)"}
+    return out
 
 
 def run_batch_once(api, dev, scale: float = 0.05) -> dict:
@@ -391,6 +460,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-naive", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--batch-scale", type=float, default=0.05)
     ap.add_argument("--paths", type=int, default=None,
                     help="paths per node (profiling runs only; the benchmark uses 1e5)")

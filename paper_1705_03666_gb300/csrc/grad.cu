@@ -11,8 +11,8 @@
 //                      and the exit rule do not depend on phi).
 // The path kernel runs in its gradient mode and writes one 80-byte record per
 // path (score, exit point, L); jac_reduce_kernel forms the per-node means of the
-// 80 components with compensated FP64 sums in a fixed order; vjp_kernel
-// contracts them with a cotangent over the nodes.
+// 80 components with FP64 sums in a fixed order; vjp_kernel contracts them
+// with a cotangent over the nodes.
 #include <cmath>
 #include <cstring>
 
@@ -23,9 +23,16 @@
 namespace pdd {
 
 constexpr int kJacW = 80;       // 64 theta + 16 phi components
-constexpr int kJacGroups = 4;   // path groups per component in a block
-constexpr int kJacBlock = kJacW * kJacGroups;
+constexpr int kJacLanes = 8;    // threads per path: thread m owns cos(m pi x)
+constexpr int kJacBlock = 256;  // 32 path groups x 8
+constexpr int kJacGroups = kJacBlock / kJacLanes;
 
+// Per node (one block): for each path record, thread m of a path group forms
+// cos(m pi x) and, by the Chebyshev recurrence from cos(pi y), cos(n pi y) for
+// n = 0..7, and accumulates its eight theta components (8m + n) and the two
+// phi components m and 8 + m (s * L_j) with their squares, in FP64; the 32
+// groups are combined in a fixed order and merged into the node's running
+// (count, mean, M2) per component (Chan).
 __global__ void __launch_bounds__(kJacBlock)
 jac_reduce_kernel(const GradRec *__restrict__ rec, uint64_t begin, uint64_t end,
                   uint64_t n_paths, uint64_t node_lo, NodeAcc *jacc) {
@@ -35,38 +42,65 @@ jac_reduce_kernel(const GradRec *__restrict__ rec, uint64_t begin, uint64_t end,
   if (lo >= hi) return;
   const GradRec *r = rec + (lo - begin);
   const uint64_t cnt = hi - lo;
-  const int c = threadIdx.x % kJacW, grp = threadIdx.x / kJacW;
-  const float fm = static_cast<float>(c / 8), fn = static_cast<float>(c % 8);
-  CSum s1, s2;
+  const int m = threadIdx.x % kJacLanes, grp = threadIdx.x / kJacLanes;
+  const float fm = static_cast<float>(m);
+  double s1[10], s2[10];
+#pragma unroll
+  for (int c = 0; c < 10; ++c) s1[c] = s2[c] = 0.0;
   for (uint64_t p = grp; p < cnt; p += kJacGroups) {
-    double v;
-    if (c < 64)
-      v = static_cast<double>(cospif(fm * r[p].x) * cospif(fn * r[p].y));
-    else
-      v = static_cast<double>(r[p].s) * static_cast<double>(r[p].L[c - 64]);
-    s1.add(v);
-    s2.add(v * v);
-  }
-  __shared__ CSum sh1[kJacBlock], sh2[kJacBlock];
-  sh1[threadIdx.x] = s1;
-  sh2[threadIdx.x] = s2;
-  __syncthreads();
-  if (grp == 0) {
-    for (int g = 1; g < kJacGroups; ++g) {
-      s1.merge(sh1[g * kJacW + c]);
-      s2.merge(sh2[g * kJacW + c]);
+    const float x = r[p].x, y = r[p].y;
+    const float cxm = cospif(fm * x);
+    float sy1, cy1;
+    sincospif(y, &sy1, &cy1);
+    const float two_c = 2.0f * cy1;
+    float cprev = 1.0f, ccur = cy1;
+    float v[10];
+    v[0] = cxm;
+    v[1] = cxm * cy1;
+#pragma unroll
+    for (int n = 2; n < 8; ++n) {
+      const float cn = two_c * ccur - cprev;
+      cprev = ccur;
+      ccur = cn;
+      v[n] = cxm * cn;
     }
+    const float sc = r[p].s;
+    v[8] = sc * r[p].L[m];
+    v[9] = sc * r[p].L[8 + m];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) {
+      const double d = static_cast<double>(v[c]);
+      s1[c] += d;
+      s2[c] = fma(d, d, s2[c]);
+    }
+  }
+  __shared__ double sh1[kJacGroups][kJacLanes * 10], sh2[kJacGroups][kJacLanes * 10];
+#pragma unroll
+  for (int c = 0; c < 10; ++c) {
+    sh1[grp][m * 10 + c] = s1[c];
+    sh2[grp][m * 10 + c] = s2[c];
+  }
+  __syncthreads();
+  // 80 threads finish one component each: slot t = m*10 + c
+  if (threadIdx.x < kJacLanes * 10) {
+    const int t = threadIdx.x;
+    double S1 = 0.0, S2 = 0.0;
+    for (int gq = 0; gq < kJacGroups; ++gq) {
+      S1 += sh1[gq][t];
+      S2 += sh2[gq][t];
+    }
+    const int mm = t / 10, c = t % 10;
+    const int comp = c < 8 ? 8 * mm + c : (c == 8 ? 64 + mm : 72 + mm);
     const double nb = static_cast<double>(cnt);
-    const double S1 = s1.value(), S2 = s2.value();
     const double mean_b = S1 / nb;
-    const double m2_b = fmax(0.0, S2 - S1 * S1 / nb);
-    NodeAcc A = jacc[node * kJacW + c];
+    const double m2_b = fmax(0.0, S2 - S1 * mean_b);
+    NodeAcc A = jacc[node * kJacW + comp];
     const double nt = A.n + nb;
     const double d = mean_b - A.mean;
     A.mean = A.mean + d * (nb / nt);
     A.m2 = A.m2 + m2_b + d * d * (A.n * nb / nt);
     A.n = nt;
-    jacc[node * kJacW + c] = A;
+    jacc[node * kJacW + comp] = A;
   }
 }
 

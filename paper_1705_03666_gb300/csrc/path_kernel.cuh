@@ -396,7 +396,12 @@ path_kernel(const __grid_constant__ PathArgs a) {
         const unsigned long long g = a.begin + q;
         if (g < a.end) {
           slot = q;
-          const uint64_t node = g / a.n_paths;
+          uint64_t node;
+          if (a.end <= 0xffffffffull) {  // 32-bit division when the indices fit
+            node = static_cast<uint32_t>(g) / static_cast<uint32_t>(a.n_paths);
+          } else {
+            node = g / a.n_paths;
+          }
           const uint64_t path = g - node * a.n_paths + a.path_offset;
           pp = philox_path(static_cast<uint32_t>(path), static_cast<uint32_t>(node), 0u, a.rk);
 #pragma unroll
