@@ -15,6 +15,7 @@ Parity status per function (what pins it is listed in the tests):
   interface_solve    pinned (closed forms, FD brute force, invariants)
   interface_jacobian pinned (linearity in theta; CRN finite differences)
   branching_solve    pinned (ODE closed forms, travelling wave, CN solve)
+  wos_solve          pinned (harmonic data, O(eps) bias, boundary nodes)
   spline_interface   pinned (reproduces cubics exactly; library routine)
   subdomain_solve    pinned (dense solve, exact harmonic at O(h^2))
 """
@@ -95,6 +96,9 @@ def _load():
             lib.orc_interface_jacobian.restype = ctypes.c_int
             lib.orc_jacobian_width.argtypes = [P]
             lib.orc_jacobian_width.restype = ctypes.c_int
+            lib.orc_wos_solve.argtypes = [P, dp, ctypes.c_int64, lp, M, ctypes.c_double,
+                                          dp, dp, lp, dp, ip, lp]
+            lib.orc_wos_solve.restype = ctypes.c_int
             lib.orc_branching_solve.argtypes = [P, dp, ctypes.c_int64, M,
                                                 ctypes.c_int64, ctypes.c_int32,
                                                 dp, dp, lp, lp, dp, ip]
@@ -243,6 +247,34 @@ def interface_jacobian(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
     if dump_paths:
         return jac, jse, rec, steps
     return jac, jse
+
+
+def wos_solve(prob: dict, nodes, *, seed, n_paths, eps, max_steps=10**6, n_threads=None,
+              dump_paths=False, node_ids=None):
+    """Walk on Spheres for Eq. 1.1 (Sec. 2.1): mean, se, n per node, total
+    steps, and with dump_paths per-path score[n, N] and steps[n, N]."""
+    lib = _load()
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, int(prob["dim"]))
+    n = nodes.shape[0]
+    P, keep = _problem(prob)
+    M = _mc(seed, 1.0, n_paths, max_steps, False, n_threads)
+    mean, se = np.zeros(n), np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    score = np.zeros((n, n_paths)) if dump_paths else None
+    steps = np.zeros((n, n_paths), dtype=np.int32) if dump_paths else None
+    ids = None if node_ids is None else np.ascontiguousarray(node_ids, dtype=np.int64)
+    ts = ctypes.c_int64(0)
+    rc = lib.orc_wos_solve(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n,
+                           _ptr(ids, ctypes.c_int64), ctypes.byref(M), float(eps),
+                           _ptr(mean, ctypes.c_double), _ptr(se, ctypes.c_double),
+                           _ptr(cnt, ctypes.c_int64), _ptr(score, ctypes.c_double),
+                           _ptr(steps, ctypes.c_int32), ctypes.byref(ts))
+    if rc != 0:
+        raise ValueError("oracle wos_solve: invalid arguments")
+    out = {"mean": mean, "se": se, "n": cnt, "total_steps": ts.value}
+    if dump_paths:
+        out["score"], out["steps"] = score, steps
+    return out
 
 
 def branching_solve(prob: dict, nodes_xt, *, seed, n_trees, max_particles=4096,

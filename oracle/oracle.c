@@ -858,3 +858,88 @@ int orc_branching_solve(const orc_problem *P, const double *nodes_xt, int64_t n,
   parallel_for(n, M->n_threads, branch_node, &C);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Walk on Spheres for the Laplace problem Eq. 1.1 (Sec. 2.1 names it as the */
+/* scheme to use for stopped Brownian motion): from x, jump to a uniform     */
+/* point on the circle of radius d(x) = distance to the boundary (the       */
+/* largest circle inside the domain); stop when d(x) <= eps and score g at   */
+/* the projection of x on the nearest face.  E[g(X_stop)] -> u(x) as        */
+/* eps -> 0 (bias O(eps)), with no time-step bias.  d(x) = min over faces of */
+/* face_dist, which never exceeds the true distance to the boundary (outer  */
+/* faces are treated as full lines).  Step n of path p at node i takes the  */
+/* angle 2 pi U, U = unif(word n mod 4 of Philox(key, (n div 4, p, i, 2))). */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_problem *P;
+  const orc_mc *M;
+  const double *nodes;
+  const int64_t *node_ids;
+  double eps;
+  double *mean, *se;
+  int64_t *npaths;
+  double *path_score;
+  int32_t *path_steps;
+  int64_t *steps_per_node;
+} wos_ctx;
+
+static void wos_node(void *vp, int64_t i) {
+  wos_ctx *W = (wos_ctx *)vp;
+  const orc_problem *P = W->P;
+  const int geom = P->geometry, dim = P->dim;
+  const int64_t N = W->M->n_paths;
+  const uint32_t key[2] = {(uint32_t)W->M->seed, (uint32_t)(W->M->seed >> 32)};
+  const uint32_t sid = (uint32_t)(W->node_ids ? W->node_ids[i] : i);
+  double mean = 0.0, m2 = 0.0;
+  int64_t steps_total = 0;
+  for (int64_t p = 0; p < N; ++p) {
+    double X[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) X[k] = W->nodes[i * dim + k];
+    uint32_t blk[4] = {0, 0, 0, 0};
+    int64_t n = 0;
+    for (;;) {
+      int jb = nearest_face(geom, dim, X);
+      double d = face_dist(geom, jb, X);
+      if (d <= W->eps || n >= W->M->max_steps) {
+        face_project(geom, jb, X);
+        break;
+      }
+      if ((n & 3) == 0) {
+        uint32_t ctr[4] = {(uint32_t)(n >> 2), (uint32_t)p, sid, 2u};
+        orc_philox4x32_10(ctr, key, blk);
+      }
+      double th = 2.0 * M_PI * unif(blk[n & 3]);
+      X[0] += d * cos(th);
+      X[1] += d * sin(th);
+      ++n;
+    }
+    double sc = coef_g(P, X);
+    double delta = sc - mean;
+    mean += delta / (double)(p + 1);
+    m2 += delta * (sc - mean);
+    steps_total += n;
+    if (W->path_score) W->path_score[i * N + p] = sc;
+    if (W->path_steps) W->path_steps[i * N + p] = (int32_t)n;
+  }
+  W->mean[i] = mean;
+  W->se[i] = N > 1 ? sqrt(m2 / (double)(N - 1) / (double)N) : 0.0;
+  if (W->npaths) W->npaths[i] = N;
+  W->steps_per_node[i] = steps_total;
+}
+
+int orc_wos_solve(const orc_problem *P, const double *nodes, int64_t n,
+                  const int64_t *node_ids, const orc_mc *M, double eps,
+                  double *mean, double *se, int64_t *npaths, double *path_score,
+                  int32_t *path_steps, int64_t *total_steps) {
+  if (!P || P->kind != ORC_PROB_LAPLACE_EXPCOS || P->dim != 2 || !M ||
+      M->n_paths < 1 || !(eps > 0.0))
+    return 1;
+  int64_t *spn = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  wos_ctx W = {P, M, nodes, node_ids, eps, mean, se, npaths, path_score, path_steps, spn};
+  parallel_for(n, M->n_threads, wos_node, &W);
+  int64_t ts = 0;
+  for (int64_t i = 0; i < n; ++i) ts += spn[i];
+  if (total_steps) *total_steps = ts;
+  free(spn);
+  return 0;
+}
