@@ -103,6 +103,12 @@ def _load():
                                                 ctypes.c_int64, ctypes.c_int32,
                                                 dp, dp, lp, lp, dp, ip]
             lib.orc_branching_solve.restype = ctypes.c_int
+            lib.orc_branching_grid_solve.argtypes = [P, dp, ctypes.c_int64, dp, ctypes.c_int32,
+                                                     M, ctypes.c_int64, ctypes.c_int32,
+                                                     dp, dp, lp, lp, dp, ip]
+            lib.orc_branching_grid_solve.restype = ctypes.c_int
+            lib.orc_grid_ticks_per_unit.argtypes = [ctypes.c_double]
+            lib.orc_grid_ticks_per_unit.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -302,6 +308,43 @@ def branching_solve(prob: dict, nodes_xt, *, seed, n_trees, max_particles=4096,
     if dump_trees:
         out["score"], out["segments"] = ts, tg
     return out
+
+
+def branching_grid_solve(prob: dict, nodes, times, *, seed, n_trees, dt=1e-3,
+                         bridge=True, max_particles=4096, max_depth=64, n_threads=None,
+                         dump_trees=False):
+    """Branching estimate of u(x, T_i) for every time of the grid `times` from
+    one tree per sample (Algorithm 3.1), in free space or with absorbing
+    boundaries and boundary data g (Eq. 3.2).  mean/se are [n, m]."""
+    lib = _load()
+    d = int(prob["dim"])
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, d)
+    times = np.ascontiguousarray(times, dtype=np.float64).ravel()
+    n, m = nodes.shape[0], times.size
+    P, keep = _problem(prob)
+    M = _mc(seed, dt, n_trees, 1, bridge, n_threads)
+    mean, se = np.zeros((n, m)), np.zeros((n, m))
+    kept = np.zeros(n, dtype=np.int64)
+    disc = np.zeros(n, dtype=np.int64)
+    ts = np.zeros((n, n_trees, m)) if dump_trees else None
+    tg = np.zeros((n, n_trees), dtype=np.int32) if dump_trees else None
+    rc = lib.orc_branching_grid_solve(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n,
+                                      _ptr(times, ctypes.c_double), m, ctypes.byref(M),
+                                      int(max_particles), int(max_depth),
+                                      _ptr(mean, ctypes.c_double), _ptr(se, ctypes.c_double),
+                                      _ptr(kept, ctypes.c_int64), _ptr(disc, ctypes.c_int64),
+                                      _ptr(ts, ctypes.c_double), _ptr(tg, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("oracle branching_grid_solve: invalid arguments")
+    out = {"mean": mean, "se": se, "n": kept, "discarded": disc}
+    if dump_trees:
+        out["score"], out["steps"] = ts, tg
+    return out
+
+
+def grid_ticks_per_unit(t_max: float) -> float:
+    """Integer time scale of the grid solver: 2^(31 - e) for t_max = f 2^e."""
+    return _load().orc_grid_ticks_per_unit(float(t_max))
 
 
 # --------------------------------------------------------------------------

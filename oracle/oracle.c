@@ -51,7 +51,7 @@ enum { ORC_GEOM_INTERVAL = 0, ORC_GEOM_UNIT_SQUARE = 1, ORC_GEOM_L_SHAPE = 2,
 enum { ORC_PROB_LAPLACE_EXPCOS = 1, ORC_PROB_ELLIPTIC_MANUFACTURED = 2,
        ORC_PROB_POISSON_FOURIER = 3, ORC_PROB_BERNAL_ACEBRON = 4,
        ORC_PROB_POLY1D = 5, ORC_PROB_TORSION = 6, ORC_PROB_KPP = 7 };
-enum { ORC_PSI_CONST = 0, ORC_PSI_SIGMOID = 1, ORC_PSI_TRAVELLING = 2 };
+enum { ORC_PSI_CONST = 0, ORC_PSI_SIGMOID = 1, ORC_PSI_TRAVELLING = 2, ORC_PSI_SINE = 3 };
 
 typedef struct {
   int32_t kind, geometry, dim, n_params;
@@ -732,7 +732,7 @@ int orc_interface_jacobian(const orc_problem *P, const double *nodes, int64_t n,
 /* A tree whose particle count exceeds max_particles or whose pending stack */
 /* exceeds max_depth is discarded and counted (pruning, Algorithm 3.1).     */
 /* ------------------------------------------------------------------------ */
-static double psi_eval(int kind, double prm, const double *x) {
+static double psi_eval(int kind, double prm, const double *x, int dim) {
   switch (kind) {
   case ORC_PSI_CONST: return prm;
   case ORC_PSI_SIGMOID: return 1.0 / (1.0 + exp(-prm * x[0]));
@@ -740,6 +740,7 @@ static double psi_eval(int kind, double prm, const double *x) {
     double e = 1.0 + exp(prm * x[0]);
     return 1.0 - 1.0 / (e * e);
   }
+  case ORC_PSI_SINE: return sin(M_PI * x[0]) * (dim > 1 ? sin(M_PI * x[1]) : 1.0);
   default: return 0.0;
   }
 }
@@ -802,7 +803,7 @@ static void branch_node(void *vp, int64_t i) {
       cur.x[0] += h * z0;
       if (dim >= 2) cur.x[1] += h * z1;
       if (reaches) {
-        prod *= psi_eval(psik, psip, cur.x);
+        prod *= psi_eval(psik, psip, cur.x, dim);
         continue;
       }
       double u3 = unif(w[3]), cum = 0.0;
@@ -856,6 +857,263 @@ int orc_branching_solve(const orc_problem *P, const double *nodes_xt, int64_t n,
   branch_ctx C = {P, M, nodes_xt, max_particles, max_depth, mean, se,
                   n_kept, n_discarded, tree_score, tree_segments};
   parallel_for(n, M->n_threads, branch_node, &C);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Branching Brownian motion on a time grid, with absorbing boundaries       */
+/* (Eq. 3.2) and one tree per node for every time point (Algorithm 3.1).     */
+/*                                                                          */
+/* u(x, t) = E[ prod over the particles of the tree run for a time t of     */
+/*   psi(X_t) if the particle is alive at t, or g(X_tau, t - tau) if it     */
+/*   hit the boundary at tau <= t ]  (Eq. 3.2; alpha_k / q_k weights of      */
+/*   Sec. 3.2 for branchings before t).                                     */
+/* The tree restricted to [0, T_i] is a tree run for a time T_i, so one tree */
+/* scores every T_i of the grid (Algorithm 3.1 evaluates the particles      */
+/* alive at each T_i).  Free space: no boundary, and Brownian increments    */
+/* are exact, so a particle moves in one piece between grid times.  Boxes   */
+/* and the L-shape: the particle moves in steps of at most dt, each with    */
+/* the exit test of the linear paths (hard exit at the segment crossing,    */
+/* else the half-space bridge probability over faces with a < 18; exit at  */
+/* the end of the step).                                                    */
+/*                                                                          */
+/* Boundary data g(x, s) by the psi kind (the exact solution of the         */
+/* unbounded problem where there is one): const c -> the solution of         */
+/* v' = beta (v^2 - v), v(0) = c, i.e. c / (c + (1 - c) e^{beta s});        */
+/* sigmoid -> psi(x); travelling (parameter a) -> 1 - (1 + e^{a x1 - 5 beta */
+/* s / 6})^-2, the travelling wave of u_t = (1/2) u'' + beta (u^2 - u) when  */
+/* a = sqrt(beta / 3); sine -> 0.                                           */
+/*                                                                          */
+/* Times are integers ("ticks") of 2^-k with k = 31 - e, T_m = f 2^e,        */
+/* f in [1/2, 1): T_i -> floor(T_i 2^k + 1/2), dt -> max(1, floor(dt 2^k +  */
+/* 1/2)), a lifetime E -> floor(E 2^k) (capped at 2^32 - 1).  A particle     */
+/* born at tick b with lifetime ticks e lives to min(b + e, T_m); its walk   */
+/* is cut at every grid time and at most dt apart.  Streams: particle id of */
+/* tree s at node i draws block j from Philox(key, ((id << 20) | j, s, i,   */
+/* 3)); j = 0: lifetime -ln U(w0) / beta, offspring count from U(w3) by the */
+/* inverse CDF of q; j >= 1: step j, normals BM(w0, w1), bridge U(w2).       */
+/* Order and pruning as for the free-space trees.                           */
+/* ------------------------------------------------------------------------ */
+static double g_bound(int kind, double prm, double beta, const double *x, double s,
+                      int dim) {
+  switch (kind) {
+  case ORC_PSI_CONST: return prm / (prm + (1.0 - prm) * exp(beta * s));
+  case ORC_PSI_SIGMOID: return psi_eval(kind, prm, x, dim);
+  case ORC_PSI_TRAVELLING: {
+    double e = 1.0 + exp(prm * x[0] - 5.0 * beta * s / 6.0);
+    return 1.0 - 1.0 / (e * e);
+  }
+  default: return 0.0;
+  }
+}
+
+typedef struct {
+  const orc_problem *P;
+  const orc_mc *M;
+  const double *nodes; /* [n][dim] */
+  const uint32_t *T;   /* [m] ticks */
+  int m;
+  uint32_t dt_ticks;
+  double tps;          /* ticks per unit time, 2^k */
+  int64_t max_particles;
+  int32_t max_depth;
+  double *mean, *se;   /* [n][m] */
+  int64_t *n_kept, *n_discarded;
+  double *tree_score;  /* [n][N][m] or NULL */
+  int32_t *tree_steps; /* [n][N] or NULL */
+} gbranch_ctx;
+
+typedef struct { double x[2]; uint32_t tb; uint32_t id; } gparticle;
+
+static void gbranch_node(void *vp, int64_t i) {
+  gbranch_ctx *C = (gbranch_ctx *)vp;
+  const orc_problem *P = C->P;
+  const int dim = P->dim, geom = P->geometry, m = C->m;
+  const int bounded = geom != ORC_GEOM_FREE_SPACE;
+  const double beta = P->params[0];
+  const int psik = (int)P->params[1];
+  const double psip = P->params[2];
+  const int K = (int)P->params[3];
+  const double *q = P->params + 4, *alpha = P->params + 5 + K;
+  const uint32_t key[2] = {(uint32_t)C->M->seed, (uint32_t)(C->M->seed >> 32)};
+  const int64_t N = C->M->n_paths;
+  const uint32_t Tm = C->T[m - 1];
+  gparticle *stack = (gparticle *)malloc(sizeof(gparticle) * (size_t)(C->max_depth + 8));
+  double *prod = (double *)malloc(sizeof(double) * (size_t)m);
+  double *mean = C->mean + i * m, *m2 = (double *)calloc((size_t)m, sizeof(double));
+  for (int k = 0; k < m; ++k) mean[k] = 0.0;
+  int64_t kept = 0, disc = 0;
+  for (int64_t s = 0; s < N; ++s) {
+    for (int k = 0; k < m; ++k) prod[k] = 1.0;
+    int sp = 0, bad = 0;
+    gparticle root;
+    root.x[0] = C->nodes[i * dim];
+    root.x[1] = dim > 1 ? C->nodes[i * dim + 1] : 0.0;
+    root.tb = 0;
+    root.id = 0;
+    stack[sp++] = root;
+    uint32_t next_id = 1;
+    int64_t particles = 1;
+    int32_t steps = 0;
+    if (bounded && !inside_open(geom, dim, root.x)) {
+      /* on the boundary: absorbed at time 0 */
+      for (int k = 0; k < m; ++k)
+        prod[k] = g_bound(psik, psip, beta, root.x, C->T[k] / C->tps, dim);
+      sp = 0;
+    }
+    while (sp > 0) {
+      gparticle cur = stack[--sp];
+      uint32_t w[4];
+      uint32_t ctr[4] = {(cur.id << 20), (uint32_t)s, (uint32_t)i, 3u};
+      orc_philox4x32_10(ctr, key, w);
+      double life = -log(unif(w[0])) / beta;
+      double lt = life * C->tps;
+      uint64_t e = lt >= 4294967295.0 ? 4294967295ull : (uint64_t)lt;
+      uint64_t tend64 = (uint64_t)cur.tb + e;
+      uint32_t tend = tend64 < Tm ? (uint32_t)tend64 : Tm;
+      int ti = 0;
+      while (ti < m && C->T[ti] <= cur.tb) ++ti;
+      uint32_t t = cur.tb, j = 1;
+      double X[2] = {cur.x[0], cur.x[1]};
+      int exited = 0;
+      while (t < tend) {
+        uint32_t nxt = tend;
+        if (ti < m && C->T[ti] < nxt) nxt = C->T[ti];
+        if (bounded && nxt - t > C->dt_ticks) nxt = t + C->dt_ticks;
+        double h = (double)(nxt - t) / C->tps;
+        uint32_t cj[4] = {(cur.id << 20) | j, (uint32_t)s, (uint32_t)i, 3u};
+        uint32_t v[4];
+        orc_philox4x32_10(cj, key, v);
+        ++j;
+        ++steps;
+        double z0, z1;
+        box_muller(v[0], v[1], &z0, &z1);
+        double Xn[3] = {X[0] + sqrt(h) * z0, dim > 1 ? X[1] + sqrt(h) * z1 : 0.0, 0.0};
+        if (bounded) {
+          double xe[3] = {0, 0, 0};
+          int out = 0;
+          double X3[3] = {X[0], X[1], 0.0};
+          if (!inside_closed(geom, dim, Xn)) {
+            segment_exit(geom, dim, X3, Xn, xe);
+            out = 1;
+          } else if (C->M->bridge) {
+            double keep = 1.0, pbest = -1.0;
+            int jbest = -1;
+            for (int f = 0; f < n_faces(geom, dim); ++f) {
+              double a = 2.0 * face_dist(geom, f, X3) * face_dist(geom, f, Xn) / h;
+              if (a < 18.0) {
+                double p = exp(-a);
+                keep *= 1.0 - p;
+                if (p > pbest) { pbest = p; jbest = f; }
+              }
+            }
+            if (jbest >= 0 && unif(v[2]) < 1.0 - keep) {
+              for (int k = 0; k < 3; ++k) xe[k] = Xn[k];
+              face_project(geom, jbest, xe);
+              out = 1;
+            }
+          }
+          if (out) {
+            /* absorbed at the end of the step: every later grid time sees g */
+            for (int k = ti; k < m; ++k)
+              prod[k] *= g_bound(psik, psip, beta, xe, (double)(C->T[k] - nxt) / C->tps, dim);
+            exited = 1;
+            break;
+          }
+        }
+        X[0] = Xn[0];
+        X[1] = Xn[1];
+        t = nxt;
+        if (ti < m && t == C->T[ti]) {
+          prod[ti] *= psi_eval(psik, psip, X, dim);
+          ++ti;
+        }
+      }
+      if (exited || tend == Tm) continue;
+      /* lifetime over before T_m: branch */
+      double u3 = unif(w[3]), cum = 0.0;
+      int k = K;
+      for (int kk = 0; kk <= K; ++kk) {
+        cum += q[kk];
+        if (u3 < cum) { k = kk; break; }
+      }
+      double r = alpha[k] / q[k];
+      for (int kk = ti; kk < m; ++kk) prod[kk] *= r;
+      particles += k;
+      if (particles > C->max_particles || sp + k > C->max_depth) { bad = 1; break; }
+      for (int c = k - 1; c >= 0; --c) {
+        gparticle ch;
+        ch.x[0] = X[0];
+        ch.x[1] = X[1];
+        ch.tb = tend;
+        ch.id = next_id + (uint32_t)c;
+        stack[sp++] = ch;
+      }
+      next_id += (uint32_t)k;
+    }
+    if (C->tree_steps) C->tree_steps[i * N + s] = bad ? -steps : steps;
+    if (bad) {
+      disc++;
+      if (C->tree_score)
+        for (int k = 0; k < m; ++k) C->tree_score[(i * N + s) * m + k] = NAN;
+      continue;
+    }
+    kept++;
+    for (int k = 0; k < m; ++k) {
+      double d = prod[k] - mean[k];
+      mean[k] += d / (double)kept;
+      m2[k] += d * (prod[k] - mean[k]);
+      if (C->tree_score) C->tree_score[(i * N + s) * m + k] = prod[k];
+    }
+  }
+  for (int k = 0; k < m; ++k)
+    C->se[i * m + k] = kept > 1 ? sqrt(m2[k] / (double)(kept - 1) / (double)kept) : 0.0;
+  C->n_kept[i] = kept;
+  C->n_discarded[i] = disc;
+  free(stack);
+  free(prod);
+  free(m2);
+}
+
+/* Tick scale for a grid ending at T_m: 2^k with k = 31 - e, T_m = f 2^e.    */
+double orc_grid_ticks_per_unit(double Tm) {
+  int e = 0;
+  frexp(Tm, &e);
+  return ldexp(1.0, 31 - e);
+}
+
+int orc_branching_grid_solve(const orc_problem *P, const double *nodes, int64_t n,
+                             const double *times, int32_t m, const orc_mc *M,
+                             int64_t max_particles, int32_t max_depth, double *mean,
+                             double *se, int64_t *n_kept, int64_t *n_discarded,
+                             double *tree_score, int32_t *tree_steps) {
+  if (!P || P->kind != ORC_PROB_KPP || P->dim < 1 || P->dim > 2 || !M ||
+      M->n_paths < 1 || P->n_params < 4 || m < 1 || m > 32)
+    return 1;
+  int K = (int)P->params[3];
+  if (K < 0 || K > 7 || P->n_params < 6 + 2 * K || P->params[0] <= 0.0) return 1;
+  if (max_particles < 1 || max_particles > 4096) return 1;
+  for (int k = 0; k < m; ++k)
+    if (!(times[k] > 0.0) || (k > 0 && !(times[k] > times[k - 1]))) return 1;
+  const int bounded = P->geometry != ORC_GEOM_FREE_SPACE;
+  double tps = orc_grid_ticks_per_unit(times[m - 1]);
+  uint32_t *T = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m);
+  for (int k = 0; k < m; ++k) T[k] = (uint32_t)floor(times[k] * tps + 0.5);
+  double dtt = bounded ? floor(M->dt * tps + 0.5) : 4294967295.0;
+  uint32_t dt_ticks = dtt < 1.0 ? 1u : dtt > 4294967295.0 ? 4294967295u : (uint32_t)dtt;
+  int ok = 1;
+  for (int k = 1; k < m; ++k) ok = ok && T[k] > T[k - 1];
+  /* at most 2^20 - 1 step blocks per particle */
+  if (bounded && (double)T[m - 1] / dt_ticks + m + 2 > 1048575.0) ok = 0;
+  for (int64_t i = 0; ok && bounded && i < n; ++i) {
+    double x[3] = {nodes[i * P->dim], P->dim > 1 ? nodes[i * P->dim + 1] : 0.0, 0.0};
+    if (!inside_closed(P->geometry, P->dim, x)) ok = 0;
+  }
+  if (!ok) { free(T); return 1; }
+  gbranch_ctx C = {P, M, nodes, T, m, dt_ticks, tps, max_particles, max_depth,
+                   mean, se, n_kept, n_discarded, tree_score, tree_steps};
+  parallel_for(n, M->n_threads, gbranch_node, &C);
+  free(T);
   return 0;
 }
 

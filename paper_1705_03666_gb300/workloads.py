@@ -84,16 +84,18 @@ def torsion(geometry: str = "unit_square", dim: int = 2) -> dict:
 
 
 def kpp(psi: str = "sigmoid", psi_param: float = 4.0, beta: float = 1.0,
-        q=(0.0, 0.0, 1.0), alpha=None, dim: int = 2) -> dict:
+        q=(0.0, 0.0, 1.0), alpha=None, dim: int = 2, geometry: str = "free_space") -> dict:
     """u_t = (1/2) Lap u + beta (sum_k alpha_k u^k - u), u(.,0) = psi (Eq. 3.1,
-    Sec. 3.2 when alpha != q).  psi in {const, sigmoid, travelling}:
-    const c; 1/(1+exp(-a x1)); 1 - (1+exp(a x1))^-2."""
+    Sec. 3.2 when alpha != q).  psi in {const, sigmoid, travelling, sine}:
+    const c; 1/(1+exp(-a x1)); 1 - (1+exp(a x1))^-2; prod_k sin(pi x_k).
+    A bounded geometry (interval, unit_square, l_shape) adds absorbing
+    boundaries with data g(x, s) fixed by the psi kind (Eq. 3.2)."""
     q = np.asarray(q, dtype=np.float64)
     alpha = q.copy() if alpha is None else np.asarray(alpha, dtype=np.float64)
     K = len(q) - 1
-    kind = {"const": 0.0, "sigmoid": 1.0, "travelling": 2.0}[psi]
+    kind = {"const": 0.0, "sigmoid": 1.0, "travelling": 2.0, "sine": 3.0}[psi]
     params = np.concatenate([[beta, kind, psi_param, float(K)], q, alpha])
-    return {"problem": "kpp", "geometry": "free_space", "dim": dim, "sigma": 1.0,
+    return {"problem": "kpp", "geometry": geometry, "dim": dim, "sigma": 1.0,
             "params": params}
 
 
