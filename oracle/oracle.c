@@ -250,6 +250,42 @@ static double coef_g(const orc_problem *P, const double *x) {
   }
 }
 
+/* Reflecting faces (Eq. 2.4 with dOmega_R non-empty): on a reflecting face
+ * the condition is du/dN = phi u + psi, N the outward normal, phi <= 0.
+ * The Laplace, 3-D manufactured and torsion families accept two optional
+ * parameters [reflect mask (bit j: face j of the box is reflecting), phi];
+ * psi is what keeps the family's exact solution exact, du/dN - phi u
+ * (Laplace: u = e^x cos y; 3-D: the manufactured u), and 0 for torsion
+ * (homogeneous Robin data).  Boxes only.                                   */
+static int reflect_mask(const orc_problem *P) {
+  if (P->kind != ORC_PROB_LAPLACE_EXPCOS && P->kind != ORC_PROB_ELLIPTIC_MANUFACTURED &&
+      P->kind != ORC_PROB_TORSION)
+    return 0;
+  if (P->geometry == ORC_GEOM_L_SHAPE || P->geometry == ORC_GEOM_FREE_SPACE) return 0;
+  if (P->n_params < 2) return 0;
+  return (int)P->params[0] & ((1 << (2 * P->dim)) - 1);
+}
+
+static double robin_psi(const orc_problem *P, int j, const double *x) {
+  const int k = j >> 1;
+  const double s = (j & 1) ? 1.0 : -1.0; /* outward normal = s e_k */
+  const double phi = P->params[1];
+  double grad[3] = {0, 0, 0}, u = 0.0;
+  if (P->kind == ORC_PROB_LAPLACE_EXPCOS) {
+    u = exp(x[0]) * cos(x[1]);
+    grad[0] = u;
+    grad[1] = -exp(x[0]) * sin(x[1]);
+  } else if (P->kind == ORC_PROB_ELLIPTIC_MANUFACTURED) {
+    u = em_u(x);
+    grad[0] = M_PI * cos(M_PI * x[0]) * sin(M_PI * x[1]) * exp(x[2]);
+    grad[1] = M_PI * sin(M_PI * x[0]) * cos(M_PI * x[1]) * exp(x[2]);
+    grad[2] = u;
+  } else {
+    return 0.0;
+  }
+  return s * grad[k] - phi * u;
+}
+
 /* Coefficients at a point, for tests: out = (b0, b1, b2, c, f, g).        */
 void orc_eval_coeffs(const orc_problem *P, const double *x, double *out) {
   double b[3];
@@ -439,7 +475,16 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
   const int nphi = n_phi(P);
   if (Lphi) for (int j = 0; j < nphi; ++j) Lphi[j] = 0.0;
   if (yexit) *yexit = 1.0;
-  if (!inside_open(geom, dim, X)) {
+  const int rmask = reflect_mask(P);
+  const double phiR = rmask ? P->params[1] : 0.0;
+  /* a start on an absorbing face exits at once; on a reflecting face the
+   * walk starts normally */
+  int on_abs = !inside_closed(geom, dim, X);
+  for (int k = 0; k < dim && !on_abs; ++k)
+    on_abs = (X[k] <= 0.0 && !((rmask >> (2 * k)) & 1)) ||
+             (X[k] >= 1.0 && !((rmask >> (2 * k + 1)) & 1));
+  if (geom == ORC_GEOM_L_SHAPE && !inside_open(geom, dim, X)) on_abs = 1;
+  if (on_abs) {
     *score = coef_g(P, X);
     *steps = 0;
     if (xexit) for (int k = 0; k < 3; ++k) xexit[k] = X[k];
@@ -492,9 +537,48 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
         Lphi[j] += dot * sqrt(dt) / sig;
       }
     }
-    double Yn = Y * exp(c * dt);
-    double Zn = Z + f * Y * dt;
     for (int k = 0; k < dim; ++k) Xn[k] = X[k] + b[k] * dt + sdt * xi[k];
+    /* Reflection (Lepingle's scheme for a half-space): on a reflecting face
+     * j with distances y (start) and y' (free end), the Brownian bridge's
+     * minimum over the step is m = (y + y' - sqrt((y' - y)^2 - 2 sigma^2 dt
+     * ln U')) / 2 with U' uniform; the local time increment is L = max(0,
+     * -m) and the end point is pushed in by L.  U' for axis k is word k of
+     * Philox((n, p, i, 4)); it matters only when 2 y y' / (sigma^2 dt) < 18
+     * (else L = 0 for every U' >= 2^-24).  Along the local time the
+     * weights solve dY = phi Y dxi, dZ = psi Y dxi exactly for psi frozen
+     * at the end point projected on face j: Z gains psi Y (e^{phi L} - 1) /
+     * phi (psi Y L when phi = 0) and Y gains the factor e^{phi L}; then
+     * the time part, Y' = Y e^{c dt}, Z' = Z + f Y dt (left point).        */
+    double yr = Y, zr = 0.0;
+    if (rmask) {
+      uint32_t R[4];
+      int have_r = 0;
+      for (int j = 0; j < 2 * dim; ++j) {
+        if (!((rmask >> j) & 1)) continue;
+        double y0 = face_dist(geom, j, X), y1 = face_dist(geom, j, Xn);
+        if (2.0 * y0 * y1 / (sig * sig * dt) >= 18.0) continue;
+        if (!have_r) {
+          uint32_t cr[4] = {(uint32_t)n, path, node, 4u};
+          orc_philox4x32_10(cr, key, R);
+          have_r = 1;
+        }
+        int k = j >> 1;
+        double dy = y1 - y0;
+        double mn = 0.5 * (y0 + y1 - sqrt(dy * dy - 2.0 * sig * sig * dt * log(unif(R[k]))));
+        double L = mn < 0.0 ? -mn : 0.0;
+        if (L > 0.0) {
+          if (j & 1) { Xn[k] -= L; if (Xn[k] > 1.0) Xn[k] = 1.0; }
+          else { Xn[k] += L; if (Xn[k] < 0.0) Xn[k] = 0.0; }
+          double xp[3] = {Xn[0], Xn[1], Xn[2]};
+          xp[k] = (double)(j & 1);
+          double g1 = phiR != 0.0 ? expm1(phiR * L) / phiR : L;
+          zr += robin_psi(P, j, xp) * yr * g1;
+          yr *= exp(phiR * L);
+        }
+      }
+    }
+    double Yn = yr * exp(c * dt);
+    double Zn = Z + f * Y * dt + zr;
     if (!inside_closed(geom, dim, Xn)) {
       double xe[3] = {0, 0, 0};
       segment_exit(geom, dim, X, Xn, xe);
@@ -508,6 +592,7 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
       double keep = 1.0, pbest = -1.0;
       int jbest = -1;
       for (int j = 0; j < n_faces(geom, dim); ++j) {
+        if ((rmask >> j) & 1) continue; /* reflecting: no exit */
         double d0 = face_dist(geom, j, X), d1 = face_dist(geom, j, Xn);
         double a = 2.0 * d0 * d1 / (sig * sig * dt);
         if (a < 18.0) {
@@ -533,7 +618,14 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
   }
   /* Step cap reached: score at the projection onto the nearest face.     */
   double xe[3] = {X[0], X[1], X[2]};
-  face_project(geom, nearest_face(geom, dim, X), xe);
+  int jn = -1;
+  double dn = 1e300;
+  for (int j = 0; j < n_faces(geom, dim); ++j) {
+    if ((rmask >> j) & 1) continue;
+    double d = face_dist(geom, j, X);
+    if (d < dn) { dn = d; jn = j; }
+  }
+  if (jn >= 0) face_project(geom, jn, xe);
   *score = coef_g(P, xe) * Y + Z;
   *steps = (int32_t)(-M->max_steps);
   if (xexit) for (int k = 0; k < 3; ++k) xexit[k] = xe[k];

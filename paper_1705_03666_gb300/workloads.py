@@ -38,17 +38,31 @@ def r2_points(count: int, offset: float = 0.5) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Problems
 # --------------------------------------------------------------------------
-def laplace_expcos(geometry: str = "unit_square") -> dict:
-    """Eq. 1.1 on the unit square (or L-shape) with harmonic g = e^x cos y."""
+def _robin(reflect, phi: float) -> np.ndarray:
+    """Optional reflecting faces: [mask, phi] with bit j of the mask for face
+    j = 2k + s of the box (x_k = s), Robin condition du/dN = phi u + psi."""
+    if not reflect:
+        return np.zeros(0)
+    mask = 0
+    for j in reflect:
+        mask |= 1 << int(j)
+    return np.array([float(mask), float(phi)])
+
+
+def laplace_expcos(geometry: str = "unit_square", reflect=None, phi: float = 0.0) -> dict:
+    """Eq. 1.1 on the unit square (or L-shape) with harmonic g = e^x cos y;
+    faces listed in `reflect` carry Robin data du/dN = phi u + psi with psi
+    chosen so that e^x cos y stays exact (Eq. 2.4)."""
     return {"problem": "laplace_expcos", "geometry": geometry, "dim": 2,
-            "sigma": 1.0, "params": np.zeros(0)}
+            "sigma": 1.0, "params": _robin(reflect, phi)}
 
 
-def elliptic_manufactured() -> dict:
+def elliptic_manufactured(reflect=None, phi: float = 0.0) -> dict:
     """(1/2) Lap u + b.grad u - u = F on [0,1]^3, b = (0.5 sin 2 pi y,
-    0.5 cos 2 pi x, 0), F manufactured from u = sin(pi x) sin(pi y) e^z."""
+    0.5 cos 2 pi x, 0), F manufactured from u = sin(pi x) sin(pi y) e^z;
+    optional reflecting faces with Robin data that keep u exact."""
     return {"problem": "elliptic_manufactured", "geometry": "unit_cube",
-            "dim": 3, "sigma": 1.0, "params": np.zeros(0)}
+            "dim": 3, "sigma": 1.0, "params": _robin(reflect, phi)}
 
 
 def poisson_fourier(seed: int = 5, phi_scale: float = 0.1) -> dict:
@@ -77,10 +91,11 @@ def poly1d(b0=0.0, b1=0.0, c0=0.0, f0=0.0, f1=0.0, g0=0.0, g1=0.0) -> dict:
             "params": np.array([b0, b1, c0, f0, f1, g0, g1], dtype=np.float64)}
 
 
-def torsion(geometry: str = "unit_square", dim: int = 2) -> dict:
-    """(1/2) Lap u = -1, u = 0 on the boundary: u(x) = E[tau]."""
+def torsion(geometry: str = "unit_square", dim: int = 2, reflect=None, phi: float = 0.0) -> dict:
+    """(1/2) Lap u = -1, u = 0 on the boundary: u(x) = E[tau]; faces in
+    `reflect` carry du/dN = phi u instead."""
     return {"problem": "torsion", "geometry": geometry, "dim": dim, "sigma": 1.0,
-            "params": np.zeros(0)}
+            "params": _robin(reflect, phi)}
 
 
 def kpp(psi: str = "sigmoid", psi_param: float = 4.0, beta: float = 1.0,
@@ -177,6 +192,21 @@ def workload(k: int) -> dict:
                 "seed": SEED_BASE + 5, "dt": 1e-3, "n_paths": 100_000,
                 "precision": "fp32", "bridge": True}
     raise ValueError(f"no workload {k}")
+
+
+def kpp_bounded_square(n_trees: int = 100_000) -> dict:
+    """Eq. 3.2 on the unit square: u_t = (1/2) Lap u + beta (u^2 - u) with
+    beta = 4, psi and boundary data from the travelling wave
+    1 - (1 + e^{a x - 5 beta t / 6})^-2, a = sqrt(beta / 3) (exact solution);
+    nodes on the interfaces x in {1/4, 1/2, 3/4}, y = k/17 (k = 1..16), 16
+    grid times T_i = i/16 scored by one tree per sample, dt = 1e-3."""
+    beta = 4.0
+    y = np.arange(1, 17, dtype=np.float64) / 17.0
+    nodes = np.concatenate([np.stack([np.full_like(y, x), y], 1) for x in (0.25, 0.5, 0.75)])
+    return {"name": "kpp_bounded_square_48nodes_16times_1e5trees_beta4_dt1e-3",
+            "prob": kpp("travelling", float(np.sqrt(beta / 3.0)), beta, geometry="unit_square"),
+            "nodes": nodes, "times": np.arange(1, 17, dtype=np.float64) / 16.0,
+            "seed": SEED_BASE + 6, "n_trees": n_trees, "dt": 1e-3}
 
 
 def nodes_lshape_interfaces(count: int) -> np.ndarray:
