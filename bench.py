@@ -37,12 +37,13 @@ METRIC = "path-steps/sec and interface nodes/sec at fixed std error; % of FP32/I
 UNIT = "path-steps/s"
 WORKLOAD = W.workload(2)
 
-# Algorithmic issue slots per path-step of the FP32 3-D path (one Philox block,
-# 1.5 Box-Muller pairs + 1 bridge uniform, the drift/source of the manufactured
-# problem, the Euler-Maruyama update and the exit tests), each elementary
-# operation or minimal transcendental sequence counted once; derivation in the
-# design notes.
-ALG_SLOTS_PER_PATH_STEP = 114
+# Algorithmic issue slots per path-step of the FP32 3-D path (three quarters
+# of a Philox block -- three words per step --, 1.5 Box-Muller pairs, one
+# bridge uniform from the words' spare low bits, the drift/source of the
+# manufactured problem, the Euler-Maruyama update and the exit tests), each
+# elementary operation or minimal transcendental sequence counted once;
+# derivation in the design notes.
+ALG_SLOTS_PER_PATH_STEP = 105
 
 
 def _env_rank():
@@ -334,8 +335,12 @@ def _timed(stream, fn):
 def run_other_workloads(api, dev) -> dict:
     """One timed call (after one warm-up) of each other workload at full size:
     KPP branching (1024 space-time nodes x 1e5 trees), the Poisson-Fourier
-    forward solve and its gradient (2048 nodes x 1e5 paths, dt = 1e-3), and
-    stage two of the 2-D Laplace workload (two 129 x 129 CG solves)."""
+    forward solve and its gradient (2048 nodes x 1e5 paths, dt = 1e-3),
+    stage two of the 2-D Laplace workload (two 129 x 129 CG solves), Walk
+    on Spheres against Euler-Maruyama on that workload's 16 nodes, the KPP
+    nodes with one tree per sample for all 16 times (Algorithm 3.1), the
+    bounded-domain KPP problem (Eq. 3.2) on the unit square, and the 2-D
+    Laplace nodes with Neumann and Robin faces (Eq. 2.4)."""
     import torch
     out = {}
     stream = torch.cuda.current_stream(dev)
@@ -351,6 +356,36 @@ def run_other_workloads(api, dev) -> dict:
                                 "segments_per_s": r["segments"] / (ms / 1e3),
                                 "nodes_per_s": len(w["nodes"]) / (ms / 1e3),
                                 "median_se": float(r["se"].median())}
+        # Algorithm 3.1's time-point sharing on the same 1024 space-time
+        # nodes: 64 positions x 16 times, one tree per sample for all times
+        pos = torch.from_numpy(np.ascontiguousarray(w["nodes"][::16, :2])).to(dev)
+        times = w["nodes"][:16, 2]
+        kw_g = dict(seed=w["seed"] + 1, n_trees=w["n_trees"], max_particles=w["max_particles"],
+                    max_depth=w["max_depth"])
+        rg = ctx.branching_grid_solve(pos, times, diag=True, **kw_g)
+        ms_g, _ = _timed(stream, lambda: ctx.branching_grid_solve(pos, times, **kw_g))
+        out["kpp_time_shared"] = {
+            "workload": w["name"] + " as 64 positions x 16 times", "ms": ms_g,
+            "estimates_per_s": 1024 * w["n_trees"] / (ms_g / 1e3),
+            "trees_per_s": 64 * w["n_trees"] / (ms_g / 1e3),
+            "speedup_vs_per_node_trees": ms / ms_g,
+            "median_se": float(rg["se"].median())}
+    wb = W.kpp_bounded_square()
+    with api.Context(wb["prob"], dev) as ctx:
+        nodes = torch.from_numpy(wb["nodes"]).to(dev)
+        kw_b = dict(seed=wb["seed"], n_trees=wb["n_trees"], dt=wb["dt"])
+        rb = ctx.branching_grid_solve(nodes, wb["times"], diag=True, **kw_b)
+        ms_b, _ = _timed(stream, lambda: ctx.branching_grid_solve(nodes, wb["times"], **kw_b))
+        a = float(np.sqrt(4.0 / 3.0))
+        exact = 1 - (1 + np.exp(a * wb["nodes"][:, :1] - 5 * 4.0 * wb["times"][None, :] / 6)) ** -2
+        err = np.abs(rb["mean"].cpu().numpy() - exact)
+        out["kpp_bounded_square"] = {
+            "workload": wb["name"], "ms": ms_b,
+            "trees_per_s": len(wb["nodes"]) * wb["n_trees"] / (ms_b / 1e3),
+            "steps_per_s": rb["steps"] / (ms_b / 1e3),
+            "steps_per_tree": rb["steps"] / (len(wb["nodes"]) * wb["n_trees"]),
+            "max_abs_err_vs_travelling_wave": float(err.max()),
+            "max_err_over_se": float((err / rb["se"].cpu().numpy()).max())}
     w = W.workload(5)
     with api.Context(w["prob"], dev) as ctx:
         nodes = torch.from_numpy(w["nodes"]).to(dev)
@@ -381,6 +416,44 @@ def run_other_workloads(api, dev) -> dict:
                                "achieved_gbs": alg_bytes / (ms / 1e3) / 1e9,
                                "bytes_model": "13 FP64 vector accesses per point per CG iteration",
                                "residence": "L2/shared-resident (0.27 MB per vector)"}
+        # Walk on Spheres against Euler-Maruyama + bridge on the same 16 nodes,
+        # 1e6 walks / paths per node in FP32: time, jumps or steps per walk, and
+        # the largest error against the harmonic solution e^x cos y.
+        nodes = torch.from_numpy(w["nodes"]).to(dev)
+        exact = torch.exp(nodes[:, 0]) * torch.cos(nodes[:, 1])
+        N = 1_000_000
+        kw_w = dict(seed=w["seed"], n_paths=N, eps=1e-4, precision="fp32")
+        kw_e = dict(seed=w["seed"], n_paths=N, dt=w["dt"], precision="fp32")
+        rw = ctx.wos_solve(nodes, diag=True, **kw_w)
+        re = ctx.interface_solve(nodes, diag=True, **kw_e)
+        ms_w, _ = _timed(stream, lambda: ctx.wos_solve(nodes, **kw_w))
+        ms_e, _ = _timed(stream, lambda: ctx.interface_solve(nodes, **kw_e))
+        out["wos_vs_em_laplace2d"] = {
+            "nodes": len(w["nodes"]), "walks_per_node": N,
+            "wos": {"eps": 1e-4, "ms": ms_w, "jumps_per_walk": rw["path_steps"] / (16 * N),
+                    "walks_per_s": 16 * N / (ms_w / 1e3),
+                    "max_abs_err": float((rw["mean"] - exact).abs().max()),
+                    "median_se": float(rw["se"].median())},
+            "em_bridge": {"dt": w["dt"], "ms": ms_e, "steps_per_path": re["path_steps"] / (16 * N),
+                          "paths_per_s": 16 * N / (ms_e / 1e3),
+                          "max_abs_err": float((re["mean"] - exact).abs().max()),
+                          "median_se": float(re["se"].median())}}
+    # Mixed boundary conditions (Eq. 2.4): face y = 0 Neumann and face
+    # x = 1 Robin (phi = -2), e^x cos y exact, on the same 16 nodes.
+    wr = W.laplace_expcos(reflect=[1, 2], phi=-2.0)
+    with api.Context(wr, dev) as ctx:
+        nodes = torch.from_numpy(W.nodes_cfg1(16)).to(dev)
+        exact = torch.exp(nodes[:, 0]) * torch.cos(nodes[:, 1])
+        kw_r = dict(seed=W.SEED_BASE + 7, n_paths=1_000_000, dt=1e-3, precision="fp32")
+        rr = ctx.interface_solve(nodes, diag=True, **kw_r)
+        ms_r, _ = _timed(stream, lambda: ctx.interface_solve(nodes, **kw_r))
+        out["laplace2d_robin_faces"] = {
+            "faces": "y = 0 Neumann, x = 1 Robin phi = -2, others Dirichlet",
+            "nodes": 16, "paths_per_node": 1_000_000, "dt": 1e-3, "ms": ms_r,
+            "path_steps_per_s": rr["path_steps"] / (ms_r / 1e3),
+            "steps_per_path": rr["path_steps"] / 16e6,
+            "max_abs_err": float((rr["mean"] - exact).abs().max()),
+            "median_se": float(rr["se"].median())}
     return out
 
 

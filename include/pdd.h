@@ -72,10 +72,13 @@ enum {
  *                         b = (sum_j phi[j-1] sin(j pi y),
  *                              sum_j phi[7+j] sin(j pi x)), j = 1..8.
  * KPP                     u_t = (1/2) Lap u + beta (sum_k alpha_k u^k - u),
- *                         u(.,0) = psi, free space, d = 1 or 2 (Eq. 3.1 and
- *                         Sec. 3.2).  params: [0] beta, [1] psi kind
- *                         (0 const, 1 sigmoid 1/(1+e^{-a x1}), 2 travelling
- *                         1-(1+e^{a x1})^-2), [2] psi parameter (c or a),
+ *                         u(.,0) = psi, d = 1 or 2, free space (Eq. 3.1 and
+ *                         Sec. 3.2) or, for pdd_branching_grid_solve, the
+ *                         interval / unit square / L-shape with absorbing
+ *                         boundaries (Eq. 3.2).  params: [0] beta, [1] psi
+ *                         kind (0 const, 1 sigmoid 1/(1+e^{-a x1}), 2
+ *                         travelling 1-(1+e^{a x1})^-2, 3 sine
+ *                         prod_k sin(pi x_k)), [2] psi parameter (c or a),
  *                         [3] K = max offspring count (<= 7), [4..4+K] q_k
  *                         (sampling law), [5+K..5+2K] alpha_k.            */
 enum {
@@ -224,6 +227,31 @@ PDD_API pdd_status pdd_batch_solve(pdd_ctx *ctx, const pdd_problem *problems,
                                    double *d_se, int64_t *d_npaths,
                                    int32_t use_graph, pdd_diag *diag);
 
+/* Walk on Spheres for the Laplace problem (Eq. 1.1; Sec. 2.1 recommends it
+ * for stopped Brownian motion): from x the walk jumps to a uniform point on
+ * the largest circle inside the domain (radius = distance to the nearest
+ * face; the L-shape's notch edges by segment distance) and stops when that
+ * distance is <= eps, scoring g at the projection on the nearest face.
+ * No time step; bias O(eps); O(log 1/eps) jumps per walk.  Walk p of node i
+ * takes jump n's angle 2 pi U from word n mod 4 of Philox(key = seed,
+ * counter = (n div 4, path_offset + p, i, 2)).  LAPLACE_EXPCOS problems
+ * (unit square or L-shape).  Outputs and diag as for pdd_interface_solve
+ * (path_steps counts jumps).                                               */
+typedef struct {
+  uint64_t seed;
+  int64_t n_paths;
+  int64_t path_offset;
+  int64_t max_steps;     /* jump cap (walks that hit it are counted) */
+  double eps;            /* stopping shell, (0, 1/2); FP32 needs >= 1e-6 */
+  int32_t precision;     /* PDD_FP32 or PDD_FP64 */
+  int32_t reserved;      /* must be 0 */
+} pdd_wos_params;
+
+PDD_API pdd_status pdd_wos_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                 const pdd_wos_params *wp, double *d_mean,
+                                 double *d_se, int64_t *d_npaths,
+                                 pdd_diag *diag);
+
 /* Monte Carlo parameters of the branching estimator. */
 typedef struct {
   uint64_t seed;          /* Philox key */
@@ -244,7 +272,8 @@ typedef struct {
  * branchings (W = 1 when alpha = q).  Writes d_mean[n], d_se[n] and, if
  * non-NULL, d_nkept[n] (trees kept after pruning).  Tree s of node i uses
  * the Philox stream (key = seed, counter = (particle id, tree_offset + s, i,
- * 1)) with depth-first particle ids.  Positions and times are FP32, the
+ * 1)) with depth-first particle ids.  psi kinds: const, sigmoid,
+ * travelling wave, sine (problem parameters, see pdd_problem).  Positions and times are FP32, the
  * product and the weights FP64.  With diag non-NULL the call synchronises;
  * diag->d_path_score receives per-tree scores (NaN if discarded),
  * d_path_steps per-tree segment counts (negative if discarded), path_steps
@@ -254,6 +283,55 @@ PDD_API pdd_status pdd_branching_solve(pdd_ctx *ctx, const double *d_nodes_xt,
                                        int64_t n, const pdd_branch_params *bp,
                                        double *d_mean, double *d_se,
                                        int64_t *d_nkept, pdd_diag *diag);
+
+/* Parameters of the time-grid branching estimator. */
+typedef struct {
+  uint64_t seed;          /* Philox key */
+  int64_t n_trees;        /* trees per node (>= 1) */
+  int64_t tree_offset;    /* index of the first tree */
+  int64_t max_particles;  /* pruning cap, 1..4096 (12-bit particle ids) */
+  int32_t max_depth;      /* pending-particle stack cap, 1..64 */
+  int32_t bridge;         /* bounded domains: 1 = Brownian-bridge exit test */
+  double dt;              /* bounded domains: largest step of a walk (> 0) */
+} pdd_grid_branch_params;
+
+/* The KPP-type problem of pdd_branching_solve on a time grid, with one tree
+ * per sample scoring every grid time (Algorithm 3.1 evaluates the particles
+ * alive at each T_i), in free space (Eq. 3.1) or, when the problem's
+ * geometry is the interval (1-D), the unit square or the L-shape (2-D), with
+ * absorbing boundaries (Eq. 3.2): a particle that hits the boundary at tau
+ * contributes g(X_tau, T_i - tau) to every T_i >= tau, a particle alive at
+ * T_i contributes psi(X_{T_i}), and the weights alpha_k / q_k of Sec. 3.2
+ * enter the times after each branching.  Boundary data by the psi kind:
+ * const c -> c / (c + (1 - c) e^{beta s}); sigmoid -> psi(x); travelling
+ * wave (parameter a) -> 1 - (1 + e^{a x1 - 5 beta s / 6})^-2; sine
+ * (psi = prod_k sin(pi x_k)) -> 0.
+ * d_nodes is [n][dim] FP64 (device); h_times [m] (host, 1 <= m <= 32) are
+ * the grid times, positive and increasing.  Times are integer ticks of
+ * 2^-k, k = 31 - e for T_m = f 2^e (f in [1/2, 1)): T_i and dt are rounded
+ * to ticks, lifetimes truncated; a particle's walk is cut at every grid time,
+ * at its lifetime's end and, in a bounded domain, at most dt ticks apart,
+ * each piece with the exit test of pdd_interface_solve (hard exit at the
+ * segment crossing; with bridge, the half-space crossing probability over
+ * the faces within reach, exit at the face of largest probability).
+ * Particle id of tree s at node i draws block j of Philox(key = seed,
+ * counter = ((id << 20) | j, tree_offset + s, i, 3)): block 0 gives the
+ * lifetime -ln U(w0) / beta and the offspring count from U(w3); block j >= 1
+ * the normals BM(w0, w1) and the bridge uniform U(w2) of step j.  Positions,
+ * lifetimes and tree products are FP32, the per-node sums FP64.  Writes
+ * d_mean[n][m], d_se[n][m]
+ * and, if non-NULL, d_nkept[n].  With diag non-NULL the call synchronises:
+ * d_path_score receives [n][n_trees][m] tree scores (NaN if discarded),
+ * d_path_steps [n][n_trees] step counts (negative if discarded), path_steps
+ * the total steps, capped the discarded trees (PDD_ECAP when non-zero); a
+ * node outside the closed domain gives PDD_EINVAL (NaN without diag).
+ * PDD_EINVAL also for more than 2^20 - 1 steps per particle.             */
+PDD_API pdd_status pdd_branching_grid_solve(pdd_ctx *ctx, const double *d_nodes,
+                                            int64_t n, const double *h_times,
+                                            int32_t m,
+                                            const pdd_grid_branch_params *bp,
+                                            double *d_mean, double *d_se,
+                                            int64_t *d_nkept, pdd_diag *diag);
 
 /* Stage two of PDD (Sec. 2.1, Fig. 2.2) for the Laplace family (Eq. 1.1):
  * the interpolator and the subdomain solver.  The subdomain is the box

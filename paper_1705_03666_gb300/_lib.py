@@ -39,6 +39,13 @@ class BranchParams(ctypes.Structure):
                 ("max_depth", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class GridBranchParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_trees", ctypes.c_int64),
+                ("tree_offset", ctypes.c_int64), ("max_particles", ctypes.c_int64),
+                ("max_depth", ctypes.c_int32), ("bridge", ctypes.c_int32),
+                ("dt", ctypes.c_double)]
+
+
 class Subdomain(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("n", ctypes.c_int32 * 3), ("iface_axis", ctypes.c_int32),
@@ -56,6 +63,13 @@ class BatchParams(ctypes.Structure):
                 ("n_min", ctypes.c_int64), ("n_max", ctypes.c_int64),
                 ("target_se", ctypes.c_double), ("max_steps", ctypes.c_int64),
                 ("chunk", ctypes.c_int32), ("bridge", ctypes.c_int32)]
+
+
+class WosParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_paths", ctypes.c_int64),
+                ("path_offset", ctypes.c_int64), ("max_steps", ctypes.c_int64),
+                ("eps", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Diag(ctypes.Structure):
@@ -102,6 +116,11 @@ _SIGS = {
                                           _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_double)]),
     "pdd_normals": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _I64, _VP, _VP]),
+    "pdd_wos_solve": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(WosParams), _VP, _VP, _VP,
+                                     ctypes.POINTER(Diag)]),
+    "pdd_branching_grid_solve": (ctypes.c_int, [_VP, _VP, _I64, _VP, ctypes.c_int32,
+                                                ctypes.POINTER(GridBranchParams), _VP, _VP, _VP,
+                                                ctypes.POINTER(Diag)]),
     "pdd_philox_stream": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _U32, _I64, _VP]),
     "pdd_destroy": (None, [_VP]),
     "pdd_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -162,6 +162,45 @@ class Context:
             res["segments"], res["discarded"] = int(dg.path_steps), int(dg.capped)
         return res
 
+    def branching_grid_solve(self, nodes, times, *, seed: int, n_trees: int, dt: float = 1e-3,
+                             bridge: bool = True, max_particles: int = 4096, max_depth: int = 64,
+                             tree_offset: int = 0, dump_trees: bool = False,
+                             diag: bool = False) -> dict:
+        """pdd_branching_grid_solve: nodes [n, dim] float64, times [m] (host).
+
+        Returns mean [n, m], se [n, m], n (trees kept) [n]; with diag/dump_trees
+        also steps (total) and discarded (host ints); with dump_trees score
+        [n, n_trees, m] (NaN = discarded) and tree_steps [n, n_trees]."""
+        dim = int(self.prob["dim"])
+        nodes = _dev_f64(nodes, self.device).reshape(-1, dim)
+        n = nodes.shape[0]
+        tm = np.ascontiguousarray(np.asarray(times, dtype=np.float64).ravel())
+        m = int(tm.size)
+        mean = torch.empty((n, m), dtype=_F64, device=self.device)
+        se = torch.empty((n, m), dtype=_F64, device=self.device)
+        kept = torch.empty(n, dtype=_I64, device=self.device)
+        bp = _lib.GridBranchParams(int(seed) & (2**64 - 1), int(n_trees), int(tree_offset),
+                                   int(max_particles), int(max_depth), int(bool(bridge)), float(dt))
+        res = {"mean": mean, "se": se, "n": kept}
+        dg = None
+        if diag or dump_trees:
+            dg = _lib.Diag()
+            if dump_trees:
+                res["score"] = torch.empty((n, int(n_trees), m), dtype=_F64, device=self.device)
+                res["tree_steps"] = torch.empty((n, int(n_trees)), dtype=_I32, device=self.device)
+                dg.d_path_score = res["score"].data_ptr()
+                dg.d_path_steps = res["tree_steps"].data_ptr()
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_branching_grid_solve(
+                self.handle, nodes.data_ptr(), n, tm.ctypes.data, m, ctypes.byref(bp),
+                mean.data_ptr(), se.data_ptr(), kept.data_ptr(),
+                ctypes.byref(dg) if dg is not None else None)
+        res["status"] = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ECAP))
+        if dg is not None:
+            res["steps"], res["discarded"] = int(dg.path_steps), int(dg.capped)
+        return res
+
     def subdomain_solve(self, lo, hi, n, iface_axis: int, iface_side: int, iface_s, iface_vals,
                         *, method: str = "cg", max_iter: int = 100000, tol: float = 1e-12,
                         out=None) -> dict:
@@ -326,6 +365,36 @@ class Context:
                                       int(c3), int(n_pairs), z.data_ptr(), u.data_ptr())
         _lib.check(st, self.handle)
         return z, u
+
+    def wos_solve(self, nodes, *, seed: int, n_paths: int, eps: float,
+                  max_steps: int = 10**6, precision: str = "fp32", path_offset: int = 0,
+                  dump_paths: bool = False, diag: bool = False) -> dict:
+        """pdd_wos_solve (Walk on Spheres, Laplace problem)."""
+        nodes = _dev_f64(nodes, self.device).reshape(-1, 2)
+        n = nodes.shape[0]
+        mean = torch.empty(n, dtype=_F64, device=self.device)
+        se = torch.empty(n, dtype=_F64, device=self.device)
+        cnt = torch.empty(n, dtype=_I64, device=self.device)
+        wp = _lib.WosParams(int(seed) & (2**64 - 1), int(n_paths), int(path_offset),
+                            int(max_steps), float(eps), _lib.PRECISION[precision], 0)
+        res = {"mean": mean, "se": se, "n": cnt}
+        dg = None
+        if diag or dump_paths:
+            dg = _lib.Diag()
+            if dump_paths:
+                res["score"] = torch.empty((n, int(n_paths)), dtype=_F64, device=self.device)
+                res["steps"] = torch.empty((n, int(n_paths)), dtype=_I32, device=self.device)
+                dg.d_path_score = res["score"].data_ptr()
+                dg.d_path_steps = res["steps"].data_ptr()
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_wos_solve(self.handle, nodes.data_ptr(), n, ctypes.byref(wp),
+                                        mean.data_ptr(), se.data_ptr(), cnt.data_ptr(),
+                                        ctypes.byref(dg) if dg is not None else None)
+        res["status"] = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ECAP))
+        if dg is not None:
+            res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
+        return res
 
     def philox_stream(self, seed: int, j0: int, c1: int, c2: int, c3: int, n_blocks: int):
         """pdd_philox_stream: uint32 [n_blocks, 4] CUDA tensor."""

@@ -15,6 +15,18 @@ bool finite_params(const pdd_problem *p) {
   return true;
 }
 
+// Optional reflecting faces: params = [] or [mask, phi], mask an integer with
+// one bit per face of the box, phi <= 0 (Eq. 2.4 requires phi <= 0).
+const char *check_robin(const pdd_problem *p) {
+  if (p->n_params == 0) return nullptr;
+  if (p->n_params != 2) return "reflecting-face params are [mask, phi]";
+  const double m = p->params[0];
+  if (m != std::floor(m) || m < 0.0 || m >= static_cast<double>(1 << (2 * p->dim)))
+    return "reflect mask must be an integer with one bit per face";
+  if (p->params[1] > 0.0) return "Robin phi must be <= 0";
+  return nullptr;
+}
+
 // Family / dimension / geometry combinations that have kernels, and the KPP
 // offspring law check (q a probability distribution, Assumption 3.1; alpha_k
 // real weights with q_k > 0 wherever alpha_k != 0, Sec. 3.2).
@@ -27,23 +39,28 @@ const char *check_problem(const pdd_problem *p) {
     case PDD_PROB_LAPLACE_EXPCOS:
       if (p->dim != 2 || (p->geometry != PDD_GEOM_UNIT_SQUARE && p->geometry != PDD_GEOM_L_SHAPE))
         return "LAPLACE_EXPCOS needs dim 2 on the unit square or the L-shape";
-      return nullptr;
+      if (p->geometry == PDD_GEOM_L_SHAPE && p->n_params > 0 && p->params[0] != 0.0)
+        return "reflecting faces need the unit square";
+      return check_robin(p);
     case PDD_PROB_ELLIPTIC_MANUFACTURED:
       if (p->dim != 3 || p->geometry != PDD_GEOM_UNIT_CUBE)
         return "ELLIPTIC_MANUFACTURED needs dim 3 on the unit cube";
-      return nullptr;
+      return check_robin(p);
     case PDD_PROB_POISSON_FOURIER:
       if (p->dim != 2 || p->geometry != PDD_GEOM_UNIT_SQUARE)
         return "POISSON_FOURIER needs dim 2 on the unit square";
       if (p->n_params < 80) return "POISSON_FOURIER needs 80 params (theta[64], phi[16])";
       return nullptr;
     case PDD_PROB_KPP: {
-      if (p->dim < 1 || p->dim > 2 || p->geometry != PDD_GEOM_FREE_SPACE)
-        return "KPP needs dim 1 or 2 in free space";
+      if (p->dim < 1 || p->dim > 2) return "KPP needs dim 1 or 2";
+      if (p->geometry != PDD_GEOM_FREE_SPACE &&
+          !(p->dim == 1 && p->geometry == PDD_GEOM_INTERVAL) &&
+          !(p->dim == 2 && (p->geometry == PDD_GEOM_UNIT_SQUARE || p->geometry == PDD_GEOM_L_SHAPE)))
+        return "KPP geometry: free space, the interval (1-D), the unit square or the L-shape (2-D)";
       if (p->n_params < 4) return "KPP needs params";
       if (!(p->params[0] > 0.0)) return "KPP beta must be > 0";
       const double kind = p->params[1];
-      if (kind != 0.0 && kind != 1.0 && kind != 2.0) return "unknown psi kind";
+      if (kind != 0.0 && kind != 1.0 && kind != 2.0 && kind != 3.0) return "unknown psi kind";
       const double Kd = p->params[3];
       if (Kd != std::floor(Kd) || Kd < 0.0 || Kd > 7.0) return "K must be an integer in [0,7]";
       const int K = static_cast<int>(Kd);
@@ -201,6 +218,24 @@ pdd_status pdd_autotune_batch(pdd_ctx *ctx, const pdd_problem *problems, int32_t
   ctx->last_error.clear();
   return pdd::autotune_batch_impl(ctx, problems, n_problems, nodes, bp, d_scratch_out, repeats,
                                   best_chunk, best_ms);
+}
+
+pdd_status pdd_wos_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n, const pdd_wos_params *wp,
+                         double *d_mean, double *d_se, int64_t *d_npaths, pdd_diag *diag) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  if (wp && wp->reserved != 0) return fail(ctx, PDD_EINVAL, "reserved must be 0");
+  return pdd::wos_solve_impl(ctx, d_nodes, n, wp, d_mean, d_se, d_npaths, diag);
+}
+
+pdd_status pdd_branching_grid_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                    const double *h_times, int32_t m,
+                                    const pdd_grid_branch_params *bp, double *d_mean,
+                                    double *d_se, int64_t *d_nkept, pdd_diag *diag) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::branching_grid_solve_impl(ctx, d_nodes, n, h_times, m, bp, d_mean, d_se, d_nkept,
+                                        diag);
 }
 
 pdd_status pdd_profile(pdd_ctx *ctx, int enable) {

@@ -29,6 +29,8 @@ pdd_status autotune_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n, const p
                          double *best_ms) {
   if (!mc || !d_nodes || n < 1 || !d_scratch_out || repeats < 1 || repeats > 16)
     return fail(ctx, PDD_EINVAL, "autotune needs nodes, a 2n-double output buffer, repeats 1..16");
+  if (reflect_mask(ctx) != 0)
+    return fail(ctx, PDD_EINVAL, "autotune covers the absorbing-boundary path kernels");
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   int max_bps = 0;
   // occupancy bound of the dominant kernel family (all path kernels are 256 threads)
@@ -78,6 +80,8 @@ pdd_status autotune_batch_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_
                                double *best_ms) {
   if (!bp || !nodes || nodes->n < 1 || !d_scratch_out || repeats < 1 || repeats > 16)
     return fail(ctx, PDD_EINVAL, "autotune needs nodes, a 2n-double output buffer, repeats 1..16");
+  if (reflect_mask(ctx) != 0)
+    return fail(ctx, PDD_EINVAL, "autotune covers the absorbing-boundary path kernels");
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   EventPair ev;
   PDD_CUDA_TRY(ctx, cudaEventCreate(&ev.a));

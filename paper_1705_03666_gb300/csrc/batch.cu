@@ -251,6 +251,9 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
     const pdd_problem &P = problems[p];
     const int combo = combo_of(P);
     if (combo < 0) return fail(ctx, PDD_EINVAL, "problem %d has no batch kernel", p);
+    if ((P.kind == PDD_PROB_LAPLACE_EXPCOS || P.kind == PDD_PROB_ELLIPTIC_MANUFACTURED) &&
+        P.n_params > 0 && P.params && P.params[0] != 0.0)
+      return fail(ctx, PDD_EINVAL, "problem %d has reflecting faces (no batch kernel)", p);
     if (!(P.sigma > 0.0) || !std::isfinite(P.sigma)) return fail(ctx, PDD_EINVAL, "sigma");
     if (P.n_params < 0 || P.n_params > kMaxParams || (P.n_params > 0 && !P.params))
       return fail(ctx, PDD_EINVAL, "params");

@@ -39,7 +39,7 @@ struct BranchArgs {
   int32_t *segs;                // [end - begin] or null
   RoundKeys rk;
   float inv_beta;
-  int32_t psi_kind;             // 0 const, 1 sigmoid, 2 travelling wave
+  int32_t psi_kind;             // 0 const, 1 sigmoid, 2 travelling wave, 3 sine
   float psi_prm;
   int32_t K;                    // largest offspring count
   double cum[kMaxOffspring + 1];   // cumulative q, summed in index order
@@ -48,14 +48,16 @@ struct BranchArgs {
   int32_t max_depth;
 };
 
-__device__ __forceinline__ float psi_eval(const BranchArgs &a, float x1) {
+template <int D>
+__device__ __forceinline__ float psi_eval(const BranchArgs &a, float x1, float x2) {
   switch (a.psi_kind) {
     case 0: return a.psi_prm;
     case 1: return 1.0f / (1.0f + expf(-a.psi_prm * x1));
-    default: {
+    case 2: {
       const float e = 1.0f + expf(a.psi_prm * x1);
       return 1.0f - 1.0f / (e * e);
     }
+    default: return sinpif(x1) * (D > 1 ? sinpif(x2) : 1.0f);
   }
 }
 
@@ -130,7 +132,7 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
     ++segments;
     bool tree_done = false, bad = false, pop = false;
     if (reaches) {
-      prod *= static_cast<double>(psi_eval(a, x0));
+      prod *= static_cast<double>(psi_eval<D>(a, x0, x1));
       pop = true;
     } else {
       const double u3 = unif_d(w.w);

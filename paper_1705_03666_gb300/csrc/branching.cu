@@ -99,6 +99,9 @@ pdd_status branching_solve_impl(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
   if (!bp) return fail(ctx, PDD_EINVAL, "params is NULL");
   if (ctx->prob.kind != PDD_PROB_KPP)
     return fail(ctx, PDD_EINVAL, "pdd_branching_solve needs a KPP problem");
+  if (ctx->prob.geometry != PDD_GEOM_FREE_SPACE)
+    return fail(ctx, PDD_EINVAL, "pdd_branching_solve is the free-space estimator; bounded "
+                                 "domains use pdd_branching_grid_solve");
   if (n < 0 || n > (int64_t(1) << 32)) return fail(ctx, PDD_EINVAL, "n out of range");
   if (bp->n_trees < 1) return fail(ctx, PDD_EINVAL, "n_trees < 1");
   if (bp->tree_offset < 0 || bp->tree_offset + bp->n_trees > (int64_t(1) << 32))

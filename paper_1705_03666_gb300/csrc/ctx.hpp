@@ -51,6 +51,16 @@ struct pdd_ctx {
 
 namespace pdd {
 
+// Reflecting faces of the problem (bit j: face j of the box), from the
+// optional [mask, phi] parameters of the Laplace and 3-D manufactured
+// families; 0 for every other problem.
+inline int reflect_mask(const pdd_ctx *ctx) {
+  if (ctx->prob.kind != PDD_PROB_LAPLACE_EXPCOS && ctx->prob.kind != PDD_PROB_ELLIPTIC_MANUFACTURED)
+    return 0;
+  if (ctx->params.size() < 2) return 0;
+  return static_cast<int>(ctx->params[0]);
+}
+
 inline pdd_status fail(pdd_ctx *ctx, pdd_status st, const char *fmt, ...) {
   if (ctx) {
     char buf[512];
@@ -142,6 +152,15 @@ pdd_status autotune_batch_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_
                                double *best_ms);
 pdd_status normals_impl(pdd_ctx *ctx, uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
                         int64_t n_pairs, float *d_z, float *d_u);
+pdd_status wos_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n, const pdd_wos_params *wp,
+                          double *d_mean, double *d_se, int64_t *d_npaths, pdd_diag *diag);
+pdd_status branching_grid_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                     const double *h_times, int32_t m,
+                                     const pdd_grid_branch_params *bp, double *d_mean,
+                                     double *d_se, int64_t *d_nkept, pdd_diag *diag);
+pdd_status reflect_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                              const pdd_mc_params *mc, double *d_mean, double *d_se,
+                              int64_t *d_npaths, pdd_diag *diag);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

@@ -201,6 +201,8 @@ pdd_status interface_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   }
   if (n == 0) return PDD_OK;
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  if (reflect_mask(ctx) != 0)
+    return reflect_solve_impl(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
   switch (ctx->prob.kind) {
     case PDD_PROB_LAPLACE_EXPCOS:
       if (ctx->prob.geometry == PDD_GEOM_L_SHAPE)

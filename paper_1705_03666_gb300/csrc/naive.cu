@@ -124,6 +124,8 @@ pdd_status interface_solve_naive_impl(pdd_ctx *ctx, const double *d_nodes, int64
       mc->path_offset < 0 || mc->path_offset + mc->n_paths > (int64_t(1) << 32) ||
       ctx->prob.sigma * ctx->prob.sigma * mc->dt > 1.0 / 36.0)
     return fail(ctx, PDD_EINVAL, "invalid parameters for the naive solve (FP32 only)");
+  if (reflect_mask(ctx) != 0)
+    return fail(ctx, PDD_EINVAL, "the naive solve has no reflecting faces");
   if (n == 0) return PDD_OK;
   if (!d_nodes || !d_mean || !d_se) return fail(ctx, PDD_EINVAL, "null buffer");
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));

@@ -20,6 +20,67 @@ struct NodeAcc {  // running (count, mean, M2) per node, FP64
   double n, mean, m2;
 };
 
+// Per-thread accumulation.  Binary32 scores are summed on the FP32 pipe as
+// two-float values (Knuth's TwoSum: a ~48-bit significand, far below the
+// scores' own rounding), the shift s - K split exactly into two floats and
+// the square's rounding error recovered with an FMA; binary64 scores are
+// summed plainly in FP64 (a few thousand terms per thread).  FP64 is a
+// 1/64-rate pipe on this part, so a compensated FP64 sum per score would
+// make the reduction, not the paths, the cost of short-path workloads.
+// Threads are then combined with compensated FP64 sums in a fixed tree.
+struct F2Sum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+  }
+};
+
+template <typename R, bool kSkipNaN>
+struct ThreadSums;
+template <bool kSkipNaN>
+struct ThreadSums<float, kSkipNaN> {
+  F2Sum s1, s2;
+  unsigned long long kept = 0;
+  __device__ __forceinline__ void add(float v, float K) {
+    if (kSkipNaN && isnan(v)) return;
+    ++kept;
+    const float d = v - K;  // d + dl = v - K exactly
+    const float bb = d - v;
+    const float dl = (v - (d - bb)) + (-K - bb);
+    s1.add(d);
+    s1.lo += dl;
+    const float q = d * d;
+    const float e = fmaf(d, d, -q);
+    s2.add(q);
+    s2.lo += e + 2.0f * d * dl;
+  }
+  __device__ __forceinline__ void out(CSum &c1, CSum &c2) const {
+    c1.add(static_cast<double>(s1.hi));
+    c1.add(static_cast<double>(s1.lo));
+    c2.add(static_cast<double>(s2.hi));
+    c2.add(static_cast<double>(s2.lo));
+  }
+};
+template <bool kSkipNaN>
+struct ThreadSums<double, kSkipNaN> {
+  double s1 = 0.0, s2 = 0.0;
+  unsigned long long kept = 0;
+  __device__ __forceinline__ void add(double v, double K) {
+    if (kSkipNaN && isnan(v)) return;
+    ++kept;
+    const double d = v - K;
+    s1 += d;
+    s2 = fma(d, d, s2);
+  }
+  __device__ __forceinline__ void out(CSum &c1, CSum &c2) const {
+    c1.add(s1);
+    c2.add(s2);
+  }
+};
+
 // kSkipNaN: NaN scores mark discarded samples (pruned trees) and are left
 // out of the count; the shift K is then 0 (scores are bounded weights).
 template <typename R, bool kSkipNaN = false>
@@ -32,16 +93,13 @@ reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
   if (lo >= hi) return;
   const R *s = score + (lo - begin);
   const uint64_t cnt = hi - lo;
-  const double K = kSkipNaN ? 0.0 : static_cast<double>(s[0]);
+  const R Kr = kSkipNaN ? R(0) : s[0];
+  const double K = static_cast<double>(Kr);
+  ThreadSums<R, kSkipNaN> ts;
+  for (uint64_t i = threadIdx.x; i < cnt; i += kReduceBlock) ts.add(s[i], Kr);
   CSum s1, s2;
-  unsigned long long kept = 0;
-  for (uint64_t i = threadIdx.x; i < cnt; i += kReduceBlock) {
-    const double v = static_cast<double>(s[i]) - K;
-    if (kSkipNaN && isnan(v)) continue;
-    ++kept;
-    s1.add(v);
-    s2.add(v * v);
-  }
+  ts.out(s1, s2);
+  unsigned long long kept = ts.kept;
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) {
     s1.merge(shfl_xor(s1, m));

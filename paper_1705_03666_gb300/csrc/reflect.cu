@@ -1,0 +1,403 @@
+// reflect.cu -- interface paths with reflecting faces: the mixed BVP of
+// Eq. 2.4 (Robin data du/dN = phi u + psi on the reflecting part of the
+// boundary) through the local-time system of Eq. 2.9: X is pushed back into
+// the domain by the local time xi (dX = ... - N dxi), Y gains phi Y dxi and
+// Z gains psi Y dxi.
+//
+// A step is the Euler-Maruyama step of the path kernel (same streams, tag 0)
+// followed, for every reflecting face within bridge reach, by Lepingle's
+// half-space reflection: with distances y (start) and y' (free end), the
+// Brownian bridge's minimum is m = (y + y' - sqrt((y' - y)^2 - 2 sigma^2 dt
+// ln U')) / 2, the local time L = max(0, -m), and the end point moves in by
+// L.  U' for axis k is word k of Philox((n, p, i, 4)), drawn only when a
+// reflecting face is within reach (2 y y' / (sigma^2 dt) < 18; beyond, L = 0
+// for every U' >= 2^-24).  Along the local time the weights are integrated
+// exactly with psi frozen at the end point's projection: Z += psi Y (e^{phi
+// L} - 1) / phi, Y *= e^{phi L}; then the time part as in the path kernel
+// (left point).  Absorbing faces keep the hard-exit and bridge tests.
+// Y is formed as exp(n c dt + sum phi L) so binary32 rounding does not
+// accumulate along the path.  A generic per-face loop (not the screened
+// fast path of path_kernel.cuh): reflecting problems are not the hot
+// configuration.
+#include <cmath>
+#include <cstring>
+
+#include "ctx.hpp"
+#include "models.cuh"
+#include "path_kernel.cuh"
+#include "reduce.cuh"
+#include "warp_queue.cuh"
+
+namespace pdd {
+
+struct ReflectArgs {
+  const double *nodes;
+  uint64_t n_paths, path_offset, begin, end;
+  unsigned long long *cursor;
+  unsigned long long *counters;  // [0] steps, [1] capped, [2] bad nodes
+  void *score;
+  int32_t *steps;
+  RoundKeys rk;
+  double dt, sdt, s2dt, cdt, phi;  // dt, sigma sqrt(dt), sigma^2 dt, c dt, Robin phi
+  int32_t mask;                    // bit j: face j reflects
+  int32_t max_steps, bridge;
+  ModelConst mc;
+};
+
+__device__ __forceinline__ float m_cospi(float x) { return cospif(x); }
+__device__ __forceinline__ double m_cospi(double x) { return cospi(x); }
+__device__ __forceinline__ float m_sin(float x) { return sinf(x); }
+__device__ __forceinline__ double m_sin(double x) { return sin(x); }
+
+// Outward-normal derivative of the family's exact solution on face j.
+template <class Model> struct RobinData;
+template <> struct RobinData<LaplaceExpCos> {
+  template <typename R>
+  __device__ static R dudn(int j, const R *x) {
+    const R e = m_exp(x[0]);
+    const R g = (j >> 1) == 0 ? e * m_cos(x[1]) : -e * m_sin(x[1]);
+    return (j & 1) ? g : -g;
+  }
+  template <typename R>
+  __device__ static R u(const R *x) { return m_exp(x[0]) * m_cos(x[1]); }
+};
+template <> struct RobinData<EllipticManufactured> {
+  template <typename R>
+  __device__ static R dudn(int j, const R *x) {
+    constexpr double kPi = 3.14159265358979323846;
+    const int k = j >> 1;
+    const R ez = m_exp(x[2]);
+    R g;
+    if (k == 0) g = R(kPi) * m_cospi(x[0]) * m_sinpi(x[1]) * ez;
+    else if (k == 1) g = R(kPi) * m_sinpi(x[0]) * m_cospi(x[1]) * ez;
+    else g = m_sinpi(x[0]) * m_sinpi(x[1]) * ez;
+    return (j & 1) ? g : -g;
+  }
+  template <typename R>
+  __device__ static R u(const R *x) { return m_sinpi(x[0]) * m_sinpi(x[1]) * m_exp(x[2]); }
+};
+
+template <typename R> __device__ __forceinline__ R r_exp(R v);
+template <> __device__ __forceinline__ float r_exp<float>(float v) { return expf(v); }
+template <> __device__ __forceinline__ double r_exp<double>(double v) { return exp(v); }
+template <typename R> __device__ __forceinline__ R r_expm1(R v);
+template <> __device__ __forceinline__ float r_expm1<float>(float v) { return expm1f(v); }
+template <> __device__ __forceinline__ double r_expm1<double>(double v) { return expm1(v); }
+template <typename R> __device__ __forceinline__ R r_log(R v);
+template <> __device__ __forceinline__ float r_log<float>(float v) { return logf(v); }
+template <> __device__ __forceinline__ double r_log<double>(double v) { return log(v); }
+
+template <class Model, typename R>
+__global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_constant__ ReflectArgs a) {
+  constexpr int D = Model::D;
+  using G = Box<D>;
+  const unsigned lane = threadIdx.x & 31u;
+  const R dt = static_cast<R>(a.dt), sdt = static_cast<R>(a.sdt), s2dt = static_cast<R>(a.s2dt);
+  const R cdt = static_cast<R>(a.cdt), phi = static_cast<R>(a.phi);
+  const R inv_s2dt = R(1) / s2dt;
+  R X[3] = {R(0), R(0), R(0)};
+  R Z = R(0), sphil = R(0);  // source sum; phi * (local time so far)
+  PhiloxPath pp{0, 0, 0};
+  uint32_t path = 0, node = 0;
+  uint32_t W[12];
+  R N12[12];
+  int32_t n = 0;
+  uint64_t slot = 0;
+  bool active = false, need = true;
+  unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
+  R *score = static_cast<R *>(a.score);
+  WarpQueue wq;
+  const unsigned long long total = a.end - a.begin;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    W[k] = 0;
+    N12[k] = R(0);
+  }
+
+  for (;;) {
+    while (__any_sync(kFull, need)) {
+      unsigned long long q = 0;
+      if (warp_claim<32>(wq, a.cursor, total, need, q)) {
+        slot = q;
+        const unsigned long long g = a.begin + q;
+        const uint64_t nd = g / a.n_paths;
+        node = static_cast<uint32_t>(nd);
+        path = static_cast<uint32_t>(g - nd * a.n_paths + a.path_offset);
+        pp = philox_path(path, node, 0u, a.rk);
+#pragma unroll
+        for (int k = 0; k < D; ++k) X[k] = static_cast<R>(a.nodes[nd * D + k]);
+        n = 0;
+        Z = R(0);
+        sphil = R(0);
+        bool on_abs = !G::template inside_closed<R>(X);
+        const bool bad = on_abs;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          on_abs = on_abs || (X[k] <= R(0) && !((a.mask >> (2 * k)) & 1)) ||
+                   (X[k] >= R(1) && !((a.mask >> (2 * k + 1)) & 1));
+        if (bad) {
+          score[slot] = R(NAN);
+          if (a.steps) a.steps[slot] = 0;
+          ++my_bad;
+          need = true;
+        } else if (on_abs) {
+          score[slot] = Model::template g<R>(a.mc, X);
+          if (a.steps) a.steps[slot] = 0;
+          need = true;
+        } else {
+          active = true;
+        }
+      }
+    }
+    if (!__any_sync(kFull, active)) break;
+    if (!active) continue;
+
+    // ---- normals and the bridge uniform (stream layout of the path kernel)
+    R xi[3] = {R(0), R(0), R(0)};
+    uint32_t wu;
+    if constexpr (D <= 2) {
+      const uint4 w = philox10_path(static_cast<uint32_t>(n), pp, a.rk);
+      box_muller<R>(w.x, w.y, xi[0], xi[1]);
+      if (D == 1) xi[1] = R(0);
+      wu = w.z;
+    } else {
+      const int jj = n & 3;
+      if (jj == 0) {
+        const uint32_t q3 = 3u * static_cast<uint32_t>(n >> 2);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const uint4 w = philox10_path(q3 + b, pp, a.rk);
+          W[4 * b] = w.x;
+          W[4 * b + 1] = w.y;
+          W[4 * b + 2] = w.z;
+          W[4 * b + 3] = w.w;
+        }
+#pragma unroll
+        for (int p2 = 0; p2 < 6; ++p2) box_muller<R>(W[2 * p2], W[2 * p2 + 1], N12[2 * p2], N12[2 * p2 + 1]);
+      }
+      uint32_t w0, w1, w2;
+      switch (jj) {
+        case 0: xi[0] = N12[0]; xi[1] = N12[1]; xi[2] = N12[2]; w0 = W[0]; w1 = W[1]; w2 = W[2]; break;
+        case 1: xi[0] = N12[3]; xi[1] = N12[4]; xi[2] = N12[5]; w0 = W[3]; w1 = W[4]; w2 = W[5]; break;
+        case 2: xi[0] = N12[6]; xi[1] = N12[7]; xi[2] = N12[8]; w0 = W[6]; w1 = W[7]; w2 = W[8]; break;
+        default: xi[0] = N12[9]; xi[1] = N12[10]; xi[2] = N12[11]; w0 = W[9]; w1 = W[10]; w2 = W[11]; break;
+      }
+      wu = ((w2 & 255u) << 24) | ((w1 & 255u) << 16) | ((w0 & 255u) << 8);
+    }
+
+    // ---- Euler-Maruyama step (left point)
+    R b[3] = {R(0), R(0), R(0)}, f = R(0);
+    Model::template coeffs<R>(a.mc, X, b, f);
+    const R Y = r_exp<R>(static_cast<R>(n) * cdt + sphil);
+    R Xn[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) Xn[k] = X[k] + b[k] * dt + sdt * xi[k];
+
+    // ---- reflection on reflecting faces within reach
+    R yr = Y, zr = R(0);
+    bool have_r = false;
+    uint4 rw = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int j = 0; j < 2 * D; ++j) {
+      if (!((a.mask >> j) & 1)) continue;
+      const R y0 = G::template face_dist<R>(j, X), y1 = G::template face_dist<R>(j, Xn);
+      if (R(2) * y0 * y1 * inv_s2dt >= R(18)) continue;
+      if (!have_r) {
+        rw = philox10(static_cast<uint32_t>(n), path, node, 4u, a.rk);
+        have_r = true;
+      }
+      const int k = j >> 1;
+      const uint32_t wk = k == 0 ? rw.x : k == 1 ? rw.y : rw.z;
+      const R dy = y1 - y0;
+      const R mn = R(0.5) * (y0 + y1 - m_sqrt(dy * dy - R(2) * s2dt * r_log<R>(unif<R>(wk))));
+      const R L = mn < R(0) ? -mn : R(0);
+      if (L > R(0)) {
+        if (j & 1) Xn[k] = fmin(Xn[k] - L, R(1));
+        else Xn[k] = fmax(Xn[k] + L, R(0));
+        R xp[3] = {Xn[0], Xn[1], Xn[2]};
+        xp[k] = R(j & 1);
+        const R psi = RobinData<Model>::template dudn<R>(j, xp) - phi * RobinData<Model>::template u<R>(xp);
+        const R g1 = phi != R(0) ? r_expm1<R>(phi * L) / phi : L;
+        zr += psi * yr * g1;
+        yr *= r_exp<R>(phi * L);
+        sphil += phi * L;
+      }
+    }
+    const R Yn = r_exp<R>(static_cast<R>(n + 1) * cdt + sphil);
+    const R Zn = Z + f * Y * dt + zr;
+
+    // ---- exit through absorbing faces
+    bool out = false;
+    R xe[3] = {Xn[0], Xn[1], Xn[2]};
+    if (!G::template inside_closed<R>(Xn)) {
+      G::template segment_exit<R>(X, Xn, xe);
+      out = true;
+    } else if (a.bridge) {
+      R P = R(0), pb = R(-1);
+      int jb = -1;
+#pragma unroll
+      for (int j = 0; j < 2 * D; ++j) {
+        if ((a.mask >> j) & 1) continue;
+        const R e = R(2) * G::template face_dist<R>(j, X) * G::template face_dist<R>(j, Xn) * inv_s2dt;
+        if (e < R(18)) {
+          const R p = r_exp<R>(-e);
+          P = P + p * (R(1) - P);
+          if (p > pb) {
+            pb = p;
+            jb = j;
+          }
+        }
+      }
+      if (jb >= 0 && unif<R>(wu) < P) {
+#pragma unroll
+        for (int j = 0; j < 2 * D; ++j)
+          if (j == jb) G::template project<R>(j, xe);
+        out = true;
+      }
+    }
+    ++n;
+    if (out) {
+      score[slot] = Model::template g<R>(a.mc, xe) * Yn + Zn;
+      if (a.steps) a.steps[slot] = n;
+      my_steps += static_cast<unsigned long long>(n);
+      active = false;
+      need = true;
+      continue;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) X[k] = Xn[k];
+    Z = Zn;
+    if (n >= a.max_steps) {
+      // cap: score at the projection on the nearest absorbing face
+      int jn = -1;
+      R dn = R(1e30);
+#pragma unroll
+      for (int j = 0; j < 2 * D; ++j) {
+        if ((a.mask >> j) & 1) continue;
+        const R d = G::template face_dist<R>(j, X);
+        if (d < dn) {
+          dn = d;
+          jn = j;
+        }
+      }
+      R xc[3] = {X[0], X[1], X[2]};
+#pragma unroll
+      for (int j = 0; j < 2 * D; ++j)
+        if (j == jn) G::template project<R>(j, xc);
+      score[slot] = Model::template g<R>(a.mc, xc) * Yn + Zn;
+      if (a.steps) a.steps[slot] = -n;
+      my_steps += static_cast<unsigned long long>(n);
+      ++my_capped;
+      active = false;
+      need = true;
+    }
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    my_steps += __shfl_xor_sync(kFull, my_steps, s);
+    my_capped += __shfl_xor_sync(kFull, my_capped, s);
+    my_bad += __shfl_xor_sync(kFull, my_bad, s);
+  }
+  if (lane == 0) {
+    if (my_steps) atomicAdd(&a.counters[0], my_steps);
+    if (my_capped) atomicAdd(&a.counters[1], my_capped);
+    if (my_bad) atomicAdd(&a.counters[2], my_bad);
+  }
+}
+
+template <class Model, typename R>
+static pdd_status run_reflect(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                              const pdd_mc_params *mc, double *d_mean, double *d_se,
+                              int64_t *d_npaths, pdd_diag *diag) {
+  const uint64_t N = static_cast<uint64_t>(mc->n_paths);
+  const uint64_t total = static_cast<uint64_t>(n) * N;
+  const uint64_t wave = std::min<uint64_t>(total, ctx->wave_max_paths);
+  const size_t acc_off = 256;
+  const size_t score_off = align_up(acc_off + static_cast<size_t>(n) * sizeof(NodeAcc), 256);
+  pdd_status st = ensure_scratch(ctx, align_up(score_off + wave * sizeof(R), 256));
+  if (st != PDD_OK) return st;
+  char *base = static_cast<char *>(ctx->scratch);
+  auto *counters = reinterpret_cast<unsigned long long *>(base);
+  auto *acc = reinterpret_cast<NodeAcc *>(base + acc_off);
+  R *score = reinterpret_cast<R *>(base + score_off);
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, score_off, ctx->stream));
+  ReflectArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.nodes = d_nodes;
+  a.n_paths = N;
+  a.path_offset = static_cast<uint64_t>(mc->path_offset);
+  a.cursor = counters + 4;
+  a.counters = counters;
+  a.score = score;
+  a.rk = make_round_keys(mc->seed);
+  const double sig = ctx->prob.sigma;
+  a.dt = mc->dt;
+  a.sdt = sig * std::sqrt(mc->dt);
+  a.s2dt = sig * sig * mc->dt;
+  a.cdt = (ctx->prob.kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0) * mc->dt;
+  a.mask = static_cast<int32_t>(ctx->params[0]);
+  a.phi = ctx->params[1];
+  a.max_steps = static_cast<int32_t>(mc->max_steps);
+  a.bridge = mc->bridge ? 1 : 0;
+  a.mc = ctx->mc;
+  auto kern = reflect_kernel<Model, R>;
+  int bps = 0;
+  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlock, 0));
+  if (bps < 1) bps = 1;
+  if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
+  uint64_t grid = static_cast<uint64_t>(bps) * ctx->num_sms;
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (wave + kPathBlock - 1) / kPathBlock));
+  for (uint64_t b0 = 0; b0 < total; b0 += wave) {
+    const uint64_t b1 = std::min(total, b0 + wave);
+    if (b0 > 0) PDD_CUDA_TRY(ctx, cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), ctx->stream));
+    a.begin = b0;
+    a.end = b1;
+    a.steps = (diag && diag->d_path_steps) ? diag->d_path_steps + b0 : nullptr;
+    const auto ev = prof_slot(ctx);
+    if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
+    kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
+    if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
+    const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
+    reduce_wave_kernel<R><<<static_cast<unsigned>(node_hi - node_lo + 1), kReduceBlock, 0,
+                            ctx->stream>>>(score, b0, b1, N, node_lo, acc);
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
+    if (diag && diag->d_path_score) {
+      const uint64_t cnt = b1 - b0;
+      const unsigned g = static_cast<unsigned>(std::min<uint64_t>((cnt + 255) / 256, 8192));
+      widen_scores_kernel<R><<<g, 256, 0, ctx->stream>>>(score, diag->d_path_score + b0, cnt);
+      PDD_CUDA_TRY(ctx, cudaGetLastError());
+    }
+  }
+  finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(acc, n, d_mean,
+                                                                                d_se, d_npaths);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  if (diag) {
+    unsigned long long h[4] = {0, 0, 0, 0};
+    PDD_CUDA_TRY(ctx, cudaMemcpyAsync(h, counters, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    diag->path_steps = static_cast<int64_t>(h[0]);
+    diag->capped = static_cast<int64_t>(h[1]);
+    if (h[2]) return fail(ctx, PDD_EINVAL, "%llu paths started outside the closed domain", h[2]);
+    if (h[1]) return fail(ctx, PDD_ECAP, "%llu paths hit max_steps", h[1]);
+  }
+  return PDD_OK;
+}
+
+pdd_status reflect_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                              const pdd_mc_params *mc, double *d_mean, double *d_se,
+                              int64_t *d_npaths, pdd_diag *diag) {
+  const bool fp64 = mc->precision == PDD_FP64;
+  switch (ctx->prob.kind) {
+    case PDD_PROB_LAPLACE_EXPCOS:
+      return fp64 ? run_reflect<LaplaceExpCos, double>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag)
+                  : run_reflect<LaplaceExpCos, float>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
+    case PDD_PROB_ELLIPTIC_MANUFACTURED:
+      return fp64 ? run_reflect<EllipticManufactured, double>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag)
+                  : run_reflect<EllipticManufactured, float>(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
+    default:
+      return fail(ctx, PDD_EINVAL, "reflecting faces need the Laplace or the 3-D manufactured family");
+  }
+}
+
+}  // namespace pdd

@@ -54,8 +54,13 @@ bool supported(const pdd_problem *p) {
   for (int i = 0; i < p->n_params; ++i)
     if (!std::isfinite(p->params[i])) return false;
   switch (p->kind) {
-    case PDD_PROB_LAPLACE_EXPCOS: return p->dim == 2 && p->geometry == PDD_GEOM_UNIT_SQUARE;
-    case PDD_PROB_ELLIPTIC_MANUFACTURED: return p->dim == 3 && p->geometry == PDD_GEOM_UNIT_CUBE;
+    // reflecting faces ([mask, phi] with mask != 0) have their own kernel
+    case PDD_PROB_LAPLACE_EXPCOS:
+      return p->dim == 2 && p->geometry == PDD_GEOM_UNIT_SQUARE &&
+             (p->n_params == 0 || p->params[0] == 0.0);
+    case PDD_PROB_ELLIPTIC_MANUFACTURED:
+      return p->dim == 3 && p->geometry == PDD_GEOM_UNIT_CUBE &&
+             (p->n_params == 0 || p->params[0] == 0.0);
     case PDD_PROB_POISSON_FOURIER:
       return p->dim == 2 && p->geometry == PDD_GEOM_UNIT_SQUARE && p->n_params >= 80;
     default: return false;

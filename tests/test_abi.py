@@ -61,3 +61,5 @@ def test_struct_layouts(lib):
     assert ctypes.sizeof(lib.Diag) == 40
     assert ctypes.sizeof(lib.BranchParams) == 40
     assert ctypes.sizeof(lib.Subdomain) == 88
+    assert ctypes.sizeof(lib.WosParams) == 48
+    assert ctypes.sizeof(lib.GridBranchParams) == 48

@@ -1,0 +1,139 @@
+"""GPU parity of pdd_branching_grid_solve (Algorithm 3.1 time-point sharing,
+Eq. 3.2 absorbing boundaries) against the FP64 oracle on shared Philox
+streams.  Integer tick times make every walk's cut points identical on both
+sides; binary32 positions can move a rare exit decision, which changes that
+tree's step count ("flip", counted).  Node means over matched trees agree to
+1e-5 relative at every grid time."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_03666_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NODE_REL_TOL = 1e-5
+TREE_TOL = 1e-4
+T8 = np.arange(1, 9) / 8.0
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_03666_gb300 import api as a
+    assert torch.cuda.is_available()
+    return a
+
+
+def _parity(api, orc, prob, nodes, times, flip_max, **kw):
+    o = orc.branching_grid_solve(prob, nodes, times, dump_trees=True, **kw)
+    with api.Context(prob) as ctx:
+        g = ctx.branching_grid_solve(torch.from_numpy(nodes), times, dump_trees=True, **kw)
+    sg, so = g["score"].cpu().numpy(), o["score"]
+    stg, sto = g["tree_steps"].cpu().numpy(), o["steps"]
+    nan_g, nan_o = np.isnan(sg).any(2), np.isnan(so).any(2)
+    ok = ~nan_g & ~nan_o
+    close = np.all(np.abs(sg - so) <= TREE_TOL * np.maximum(1.0, np.abs(so)), axis=2)
+    matched = ok & (stg == sto) & close
+    flip = 1.0 - matched.sum() / max(1, ok.sum())
+    assert flip <= flip_max, flip
+    # pruning decisions agree except on flipped trees
+    assert np.mean(nan_g != nan_o) <= flip_max
+    cnt = matched.sum(1)
+    assert cnt.min() > 0
+    mg = np.where(matched[:, :, None], sg, 0).sum(1) / cnt[:, None]
+    mo = np.where(matched[:, :, None], so, 0).sum(1) / cnt[:, None]
+    rel = np.abs(mg - mo) / np.maximum(np.abs(mo), 0.05)
+    assert rel.max() <= NODE_REL_TOL, rel.max()
+    return g, o, flip
+
+
+def test_bounded_square_travelling_wave(api, orc):
+    beta = 4.0
+    prob = W.kpp("travelling", np.sqrt(beta / 3), beta, geometry="unit_square")
+    nodes = np.array([[0.5, 0.5], [0.25, 0.3], [0.8, 0.6], [0.05, 0.5], [0.5, 0.97]])
+    g, o, flip = _parity(api, orc, prob, nodes, T8, 2e-3, seed=W.SEED_BASE + 41, n_trees=3000, dt=1e-3)
+    assert g["steps"] > 0
+
+
+def test_bounded_lshape_constant_and_interval_sine(api, orc):
+    prob = W.kpp("const", 0.3, 2.0, geometry="l_shape")
+    nodes = np.array([[0.25, 0.75], [0.45, 0.45], [0.75, 0.25], [0.49, 0.2]])
+    _parity(api, orc, prob, nodes, T8, 2e-3, seed=5, n_trees=3000, dt=2e-3)
+    prob = W.kpp("sine", 0.0, 1e-12, dim=1, geometry="interval")
+    _parity(api, orc, prob, np.array([[0.5], [0.2], [0.9]]), np.array([0.02, 0.05, 0.1, 0.2]),
+            2e-3, seed=6, n_trees=3000, dt=1e-4)
+
+
+def test_bridge_off_and_marked_law(api, orc):
+    prob = W.kpp("travelling", 0.5, 1.0, geometry="unit_square", q=(0.2, 0.3, 0.5),
+                 alpha=(0.5, -0.2, 0.7))
+    nodes = np.array([[0.5, 0.5], [0.3, 0.8]])
+    _parity(api, orc, prob, nodes, T8, 2e-3, seed=7, n_trees=3000, dt=1e-3, bridge=False)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_free_space_grid(api, orc, dim):
+    prob = W.kpp("sigmoid", 4.0, 1.0, dim=dim)
+    nodes = W.nodes_kpp(n_x2=4, n_t=1)[:, :dim]
+    times = np.arange(1, 17) / 16.0
+    _parity(api, orc, prob, nodes, times, 1e-3, seed=W.SEED_BASE + 42, n_trees=2000)
+
+
+def test_pruning_matches_oracle(api, orc):
+    prob = W.kpp("const", 0.5, 3.0, dim=1)
+    g, o, _ = _parity(api, orc, prob, np.array([[0.0]]), np.array([0.5, 1.0]), 1e-3, seed=8,
+                      n_trees=2000, max_particles=6, max_depth=4)
+    assert o["discarded"][0] > 100
+    with api.Context(prob) as ctx:
+        r = ctx.branching_grid_solve(torch.zeros(1, 1), [0.5, 1.0], seed=8, n_trees=2000,
+                                     max_particles=6, max_depth=4, diag=True)
+    assert r["discarded"] == o["discarded"][0] and r["status"] != 0
+    assert int(r["n"][0]) == o["n"][0]
+
+
+def test_time_sharing_agrees_with_per_node_trees(api):
+    """The KPP workload's 1024 space-time nodes (64 positions x 16 times,
+    sigmoid data, 1e5 trees): one shared tree per sample (Algorithm 3.1)
+    against independent trees per (x, t) (pdd_branching_solve): the two
+    estimators agree within their combined standard errors."""
+    w = W.workload(4)
+    xt = w["nodes"]
+    pos = xt[::16, :2]
+    times = xt[:16, 2]
+    with api.Context(w["prob"]) as ctx:
+        a = ctx.branching_solve(torch.from_numpy(xt), seed=w["seed"], n_trees=w["n_trees"])
+        b = ctx.branching_grid_solve(torch.from_numpy(pos), times, seed=w["seed"] + 1,
+                                     n_trees=w["n_trees"], diag=True)
+    ma, sa = a["mean"].cpu().numpy().reshape(64, 16), a["se"].cpu().numpy().reshape(64, 16)
+    mb, sb = b["mean"].cpu().numpy(), b["se"].cpu().numpy()
+    z = (ma - mb) / np.sqrt(sa ** 2 + sb ** 2)
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    assert b["discarded"] == 0
+
+
+def test_edge_cases(api):
+    sq = W.kpp("travelling", 0.5, 1.0, geometry="unit_square")
+    with api.Context(sq) as ctx:
+        r = ctx.branching_grid_solve(torch.zeros(0, 2), T8, seed=1, n_trees=4)
+        assert r["mean"].shape == (0, 8)
+        # on the boundary: absorbed at time 0, score g(x, T_i)
+        r = ctx.branching_grid_solve(torch.tensor([[0.0, 0.3]]), T8, seed=1, n_trees=5,
+                                     dump_trees=True)
+        ex = 1 - (1 + np.exp(-5 * T8 / 6)) ** -2
+        assert np.allclose(r["mean"].cpu().numpy()[0], ex, rtol=1e-6)
+        assert int(r["tree_steps"].abs().sum()) == 0
+        bad = [dict(times=T8[::-1]), dict(times=np.zeros(1)), dict(times=np.arange(1, 34) / 33),
+               dict(max_particles=5000), dict(max_depth=65), dict(dt=0.0), dict(dt=1e-9),
+               dict(n_trees=0)]
+        for b in bad:
+            kw = dict(times=T8, seed=1, n_trees=4, dt=1e-3)
+            kw.update(b)
+            t = kw.pop("times")
+            with pytest.raises(Exception):
+                ctx.branching_grid_solve(torch.tensor([[0.5, 0.5]]), t, **kw)
+        with pytest.raises(Exception):   # outside the closed domain
+            ctx.branching_grid_solve(torch.tensor([[1.5, 0.5]]), T8, seed=1, n_trees=4, diag=True)
+        with pytest.raises(Exception):   # the free-space estimator refuses a bounded problem
+            ctx.branching_solve(torch.tensor([[0.5, 0.5, 1.0]]), seed=1, n_trees=4)

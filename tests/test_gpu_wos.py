@@ -1,0 +1,136 @@
+"""GPU parity of pdd_wos_solve (Walk on Spheres, Eq. 1.1, Sec. 2.1) against
+the FP64 oracle on shared Philox streams (tag 2).  The FP64 kernel must
+reproduce every walk's jump count and score to rounding; the FP32 kernel's
+walks may stop one jump apart where a distance sits at eps to within
+binary32 rounding (counted, rare), and node means over matched walks agree
+to 1e-5 relative.  Binary32 positions carry ~1e-7 of rounding after a walk
+and the final distance has a density ~1/eps near eps, so at eps = 1e-4 a few
+walks in a thousand stop one jump apart (more near the L-shape's re-entrant
+corner, where walks take more jumps)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_03666_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NODE_REL_TOL = 1e-5
+FLIP_MAX_FP32 = 1e-2
+L_NODES = np.array([[0.25, 0.75], [0.75, 0.25], [0.4, 0.4], [0.1, 0.5], [0.5, 0.45],
+                    [0.45, 0.5], [0.49, 0.49], [0.05, 0.95]])
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_03666_gb300 import api as a
+    assert torch.cuda.is_available()
+    return a
+
+
+def _matched(g, o, tol):
+    sg, stg = g["score"].cpu().numpy(), g["steps"].cpu().numpy()
+    m = (stg == o["steps"]) & (np.abs(sg - o["score"]) <= tol * np.maximum(1.0, np.abs(o["score"])))
+    return m, sg
+
+
+@pytest.mark.parametrize("geom,nodes", [("unit_square", W.nodes_cfg1(16)), ("l_shape", L_NODES)])
+def test_fp64_walk_by_walk(api, orc, geom, nodes):
+    prob = W.laplace_expcos(geom)
+    kw = dict(seed=W.SEED_BASE + 1, n_paths=3000, eps=1e-4)
+    o = orc.wos_solve(prob, nodes, dump_paths=True, **kw)
+    with api.Context(prob) as ctx:
+        g = ctx.wos_solve(torch.from_numpy(nodes), precision="fp64", dump_paths=True, diag=True, **kw)
+    m, sg = _matched(g, o, 1e-9)
+    assert m.mean() >= 1 - 1e-4, 1 - m.mean()
+    if m.all():
+        np.testing.assert_allclose(g["mean"].cpu().numpy(), o["mean"], rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(g["se"].cpu().numpy(), o["se"], rtol=1e-8, atol=1e-13)
+    assert g["path_steps"] == int(g["steps"].cpu().numpy().astype(np.int64).sum())
+    assert np.all(g["n"].cpu().numpy() == 3000) and g["capped"] == 0
+
+
+@pytest.mark.parametrize("geom,nodes", [("unit_square", W.nodes_cfg1(16)), ("l_shape", L_NODES)])
+def test_fp32_matches_oracle(api, orc, geom, nodes):
+    prob = W.laplace_expcos(geom)
+    kw = dict(seed=W.SEED_BASE + 11, n_paths=4000, eps=1e-4)
+    o = orc.wos_solve(prob, nodes, dump_paths=True, **kw)
+    with api.Context(prob) as ctx:
+        g = ctx.wos_solve(torch.from_numpy(nodes), precision="fp32", dump_paths=True, **kw)
+    m, sg = _matched(g, o, 1e-4)
+    assert 1 - m.mean() <= FLIP_MAX_FP32, 1 - m.mean()
+    cnt = m.sum(1)
+    mg = np.where(m, sg, 0).sum(1) / cnt
+    mo = np.where(m, o["score"], 0).sum(1) / cnt
+    assert np.all(np.abs(mg - mo) <= NODE_REL_TOL * np.maximum(np.abs(mo), 0.1)), np.abs(mg - mo).max()
+
+
+def test_path_offset_waves_and_launch_shape(api, orc):
+    """Walks p of a run with path_offset k are walks k + p of the oracle; waves
+    that split nodes and a one-block-per-SM grid change nothing."""
+    nodes = W.nodes_cfg1(5)
+    prob = W.laplace_expcos()
+    o = orc.wos_solve(prob, nodes, seed=7, n_paths=1500, eps=1e-3, dump_paths=True)
+    with api.Context(prob) as ctx:
+        g0 = ctx.wos_solve(torch.from_numpy(nodes), seed=7, n_paths=1000, path_offset=500,
+                           eps=1e-3, precision="fp64", dump_paths=True)
+        ctx.set_tuning(blocks_per_sm=1, wave_max_paths=777)
+        g1 = ctx.wos_solve(torch.from_numpy(nodes), seed=7, n_paths=1000, path_offset=500,
+                           eps=1e-3, precision="fp64", dump_paths=True)
+        ctx.set_tuning(0, 0)
+    assert np.array_equal(g0["steps"].cpu().numpy(), o["steps"][:, 500:])
+    np.testing.assert_allclose(g0["score"].cpu().numpy(), o["score"][:, 500:], rtol=1e-12, atol=1e-12)
+    for k in ("score", "steps"):
+        assert torch.equal(g0[k], g1[k]), k
+    # waves split a node's walks, so its compensated partial sums merge in
+    # another order
+    np.testing.assert_allclose(g0["mean"].cpu().numpy(), g1["mean"].cpu().numpy(), rtol=1e-13)
+    np.testing.assert_allclose(g0["se"].cpu().numpy(), g1["se"].cpu().numpy(), rtol=1e-9)
+
+
+def test_edge_cases(api):
+    prob = W.laplace_expcos()
+    with api.Context(prob) as ctx:
+        r = ctx.wos_solve(torch.zeros(0, 2), seed=1, n_paths=10, eps=1e-3)
+        assert r["mean"].numel() == 0
+        # on the boundary: no jump, score g(x) exactly
+        b = torch.tensor([[0.0, 0.4], [1.0, 0.3], [0.2, 1.0], [0.7, 0.0]], dtype=torch.float64)
+        for prec in ("fp32", "fp64"):
+            r = ctx.wos_solve(b, seed=1, n_paths=33, eps=1e-3, precision=prec, dump_paths=True)
+            assert int(r["steps"].abs().sum()) == 0
+            ex = torch.exp(b[:, 0]) * torch.cos(b[:, 1])
+            assert torch.allclose(r["mean"].cpu(), ex, rtol=1e-6, atol=1e-7)
+            assert torch.all(r["se"].cpu() == 0)
+        # a jump cap is reported, not hidden
+        r = ctx.wos_solve(torch.tensor([[0.5, 0.5]]), seed=1, n_paths=64, eps=1e-6, max_steps=2,
+                          diag=True)
+        assert r["capped"] > 0 and r["status"] != 0
+        for bad in (dict(eps=0.0), dict(eps=0.6), dict(eps=1e-7, precision="fp32"),
+                    dict(n_paths=0), dict(max_steps=0)):
+            kw = dict(seed=1, n_paths=8, eps=1e-3, precision="fp64")
+            kw.update(bad)
+            with pytest.raises(Exception):
+                ctx.wos_solve(torch.tensor([[0.5, 0.5]]), **kw)
+        with pytest.raises(Exception):
+            ctx.wos_solve(torch.tensor([[1.5, 0.5]]), seed=1, n_paths=8, eps=1e-3, diag=True)
+    with api.Context(W.elliptic_manufactured()) as ctx:
+        with pytest.raises(Exception):
+            ctx.wos_solve(torch.tensor([[0.5, 0.5, 0.5]]), seed=1, n_paths=8, eps=1e-3)
+    with api.Context(W.laplace_expcos("l_shape")) as ctx:
+        with pytest.raises(Exception):   # inside the notch
+            ctx.wos_solve(torch.tensor([[0.75, 0.75]]), seed=1, n_paths=8, eps=1e-3, diag=True)
+
+
+def test_full_size_closed_form(api):
+    """16 interface nodes x 1e6 walks, eps = 1e-5 (FP32): the harmonic
+    solution e^x cos y within 4.5 sigma plus an O(eps) shell bias."""
+    nodes = W.nodes_cfg1(16)
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.wos_solve(torch.from_numpy(nodes), seed=W.SEED_BASE + 21, n_paths=1_000_000,
+                          eps=1e-5, precision="fp32", diag=True)
+    ex = np.exp(nodes[:, 0]) * np.cos(nodes[:, 1])
+    m, se = r["mean"].cpu().numpy(), r["se"].cpu().numpy()
+    assert np.all(np.abs(m - ex) <= 4.5 * se + 3e-5), np.abs(m - ex) / se
+    assert r["capped"] == 0
