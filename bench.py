@@ -412,9 +412,18 @@ def run_other_workloads(api, dev) -> dict:
                                               ctx.subdomain_solve(*args_r)))
         iters = a["iters"] + bb["iters"]
         alg_bytes = iters * 129 * 129 * 13 * 8
-        out["stage_two_cg"] = {"grids": "2 x 129 x 129", "ms": ms, "iterations": iters,
-                               "achieved_gbs": alg_bytes / (ms / 1e3) / 1e9,
-                               "bytes_model": "13 FP64 vector accesses per point per CG iteration",
+        ctx.subdomain_solve(*args_l, method="cg_mixed")
+        ms_m, (am, bm) = _timed(stream, lambda: (ctx.subdomain_solve(*args_l, method="cg_mixed"),
+                                                 ctx.subdomain_solve(*args_r, method="cg_mixed")))
+        out["stage_two_cg"] = {"grids": "2 x 129 x 129", "tol": 1e-12,
+                               "fp64_cg": {"ms": ms, "iterations": iters,
+                                           "achieved_gbs": alg_bytes / (ms / 1e3) / 1e9},
+                               "mixed_cg": {"ms": ms_m, "fp32_iterations": am["iters"] + bm["iters"],
+                                            "final_resid": max(am["resid"], bm["resid"]),
+                                            "max_abs_diff_vs_fp64_cg": float(max(
+                                                (am["u"] - a["u"]).abs().max(),
+                                                (bm["u"] - bb["u"]).abs().max()))},
+                               "bytes_model": "13 vector accesses per point per CG iteration",
                                "residence": "L2/shared-resident (0.27 MB per vector)"}
         # Walk on Spheres against Euler-Maruyama + bridge on the same 16 nodes,
         # 1e6 walks / paths per node in FP32: time, jumps or steps per walk, and

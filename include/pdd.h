@@ -273,9 +273,10 @@ typedef struct {
  * non-NULL, d_nkept[n] (trees kept after pruning).  Tree s of node i uses
  * the Philox stream (key = seed, counter = (particle id, tree_offset + s, i,
  * 1)) with depth-first particle ids.  psi kinds: const, sigmoid,
- * travelling wave, sine (problem parameters, see pdd_problem).  Positions and times are FP32, the
- * product and the weights FP64.  With diag non-NULL the call synchronises;
- * diag->d_path_score receives per-tree scores (NaN if discarded),
+ * travelling wave, sine (problem parameters, see pdd_problem).  Positions,
+ * times, the product and the weights are FP32, the per-node sums FP64.
+ * With diag non-NULL the call synchronises; diag->d_path_score receives
+ * per-tree scores (NaN if discarded),
  * d_path_steps per-tree segment counts (negative if discarded), path_steps
  * the total segments and capped the discarded trees (status PDD_ECAP when
  * non-zero).  A node whose trees are all discarded gets NaN.             */
@@ -345,20 +346,24 @@ PDD_API pdd_status pdd_branching_grid_solve(pdd_ctx *ctx, const double *d_nodes,
  * d_iface_vals: node values, both FP64 device arrays).  The other sides get
  * g.  The interior solves the 5-point system
  *   (u_{i+1,j} - 2u_{ij} + u_{i-1,j})/hx^2 + (u_{i,j+1} - 2u_{ij} + u_{i,j-1})/hy^2 = 0
- * by conjugate gradients (stop at ||r||_2 <= tol ||b||_2) or Jacobi sweeps
- * (stop when max |u^{k+1} - u^k| < tol), at most max_iter iterations.
+ * by conjugate gradients in FP64 (stop at ||r||_2 <= tol ||b||_2), by FP32
+ * conjugate gradients inside FP64 iterative refinement (CG_MIXED: the FP64
+ * residual is scaled and solved to 1e-4 in FP32, the correction added in
+ * FP64; same FP64 stopping rule; iterations count the FP32 ones), or Jacobi
+ * sweeps (stop when max |u^{k+1} - u^k| < tol), at most max_iter
+ * iterations.
  * d_u is [n[1]][n[0]] FP64 (row = y), written in full.  *iters and *resid
  * (host) receive the iteration count and the final residual measure; the call
  * synchronises.  Returns PDD_ETIMEOUT when max_iter ran out first (d_u holds
  * the last iterate).                                                      */
-enum { PDD_STENCIL_CG = 0, PDD_STENCIL_JACOBI = 1 };
+enum { PDD_STENCIL_CG = 0, PDD_STENCIL_JACOBI = 1, PDD_STENCIL_CG_MIXED = 2 };
 
 typedef struct {
   double lo[3], hi[3];
   int32_t n[3];
   int32_t iface_axis;
   int32_t iface_side;
-  int32_t method;       /* PDD_STENCIL_CG or PDD_STENCIL_JACOBI */
+  int32_t method;       /* PDD_STENCIL_CG, _JACOBI or _CG_MIXED */
   int64_t max_iter;
   double tol;
 } pdd_subdomain;

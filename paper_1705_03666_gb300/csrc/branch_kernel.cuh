@@ -7,9 +7,11 @@
 //
 // One lane owns one tree at a time and walks it depth-first; the pending
 // siblings of the current lineage live in a per-lane stack (local memory,
-// only its top few entries are touched).  Lanes take new trees from a warp-
-// aggregated global cursor (lane refill), and each tree's score goes to its
-// own slot, so the per-node reduction does not depend on scheduling.
+// only its top few entries are touched).  Warps claim trees in chunks
+// (warp_queue.cuh), and each tree's score goes to its own slot, so the
+// per-node reduction does not depend on scheduling.  The tree's product,
+// weight and offspring choice are binary32: FP64 is a 1/64-rate pipe on
+// this part and these operations sit in divergent per-segment code.
 //
 // Tree order (shared with the oracle): the root has id 0; a particle that
 // branches into k children gives them ids next_id .. next_id + k - 1 and the
@@ -22,12 +24,14 @@
 #pragma once
 
 #include "common.cuh"
+#include "warp_queue.cuh"
 
 namespace pdd {
 
 constexpr int kBranchBlock = 256;
 constexpr int kBranchMaxDepth = 64;
 constexpr int kMaxOffspring = 7;
+constexpr unsigned kBranchChunk = 64;  // trees claimed per warp-level atomic
 
 struct BranchArgs {
   const double *nodes_xt;       // [n][D + 1]: position, then time t
@@ -35,15 +39,15 @@ struct BranchArgs {
   uint64_t begin, end;          // tree index range of this wave
   unsigned long long *cursor;
   unsigned long long *counters; // [0] segments, [1] discarded trees
-  double *score;                // [end - begin]; NaN for discarded trees
+  float *score;                 // [end - begin]; NaN for discarded trees
   int32_t *segs;                // [end - begin] or null
   RoundKeys rk;
   float inv_beta;
   int32_t psi_kind;             // 0 const, 1 sigmoid, 2 travelling wave, 3 sine
   float psi_prm;
   int32_t K;                    // largest offspring count
-  double cum[kMaxOffspring + 1];   // cumulative q, summed in index order
-  double ratio[kMaxOffspring + 1]; // alpha_k / q_k (1 for classical weights)
+  float cum[kMaxOffspring + 1];    // cumulative q (FP64 sums, rounded)
+  float ratio[kMaxOffspring + 1];  // alpha_k / q_k (1 for classical weights)
   int64_t max_particles;
   int32_t max_depth;
 };
@@ -65,7 +69,6 @@ template <int D>
 __global__ void __launch_bounds__(kBranchBlock)
 branch_kernel(const __grid_constant__ BranchArgs a) {
   const unsigned lane = threadIdx.x & 31u;
-  const unsigned lt_mask = (1u << lane) - 1u;
   float4 stk[kBranchMaxDepth];  // pending particles: (x1, x2, t_birth, id bits)
   int sp = 0;
   // current particle
@@ -74,45 +77,37 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
   // current tree
   uint32_t node = 0, tree = 0, next_id = 0;
   float t = 0.f;
-  double prod = 1.0, weight = 1.0;
+  float prod = 1.0f, weight = 1.0f;
   int64_t particles = 0;
   int32_t segments = 0;
   uint64_t slot = 0;
   bool active = false, need = true;
   unsigned long long my_segs = 0, my_disc = 0;
+  WarpQueue wq;
+  const unsigned long long total = a.end - a.begin;
 
   for (;;) {
-    for (;;) {
-      const unsigned needmask = __ballot_sync(kFull, need);
-      if (!needmask) break;
-      const int leader = __ffs(needmask) - 1;
-      unsigned long long base = 0;
-      if (static_cast<int>(lane) == leader)
-        base = atomicAdd(a.cursor, static_cast<unsigned long long>(__popc(needmask)));
-      base = __shfl_sync(kFull, base, leader);
-      if (need) {
-        need = false;
-        const unsigned long long q = base + __popc(needmask & lt_mask);
+    while (__any_sync(kFull, need)) {
+      unsigned long long q = 0;
+      if (warp_claim<kBranchChunk>(wq, a.cursor, total, need, q)) {
+        slot = q;
         const unsigned long long g = a.begin + q;
-        if (g < a.end) {
-          slot = q;
-          const uint64_t nd = g / a.n_trees;
-          node = static_cast<uint32_t>(nd);
-          tree = static_cast<uint32_t>(g - nd * a.n_trees + a.tree_offset);
-          const double *xt = a.nodes_xt + nd * (D + 1);
-          x0 = static_cast<float>(xt[0]);
-          x1 = D == 2 ? static_cast<float>(xt[1]) : 0.f;
-          t = static_cast<float>(xt[D]);
-          tb = 0.f;
-          id = 0;
-          next_id = 1;
-          sp = 0;
-          prod = 1.0;
-          weight = 1.0;
-          particles = 1;
-          segments = 0;
-          active = true;
-        }
+        const uint64_t nd = g / a.n_trees;
+        node = static_cast<uint32_t>(nd);
+        tree = static_cast<uint32_t>(g - nd * a.n_trees + a.tree_offset);
+        const double *xt = a.nodes_xt + nd * (D + 1);
+        x0 = static_cast<float>(xt[0]);
+        x1 = D == 2 ? static_cast<float>(xt[1]) : 0.f;
+        t = static_cast<float>(xt[D]);
+        tb = 0.f;
+        id = 0;
+        next_id = 1;
+        sp = 0;
+        prod = 1.0f;
+        weight = 1.0f;
+        particles = 1;
+        segments = 0;
+        active = true;
       }
     }
     if (!__any_sync(kFull, active)) break;
@@ -132,10 +127,10 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
     ++segments;
     bool tree_done = false, bad = false, pop = false;
     if (reaches) {
-      prod *= static_cast<double>(psi_eval<D>(a, x0, x1));
+      prod *= psi_eval<D>(a, x0, x1);
       pop = true;
     } else {
-      const double u3 = unif_d(w.w);
+      const float u3 = unif_f(w.w);
       int k = a.K;
       for (int kk = 0; kk <= a.K; ++kk) {
         if (u3 < a.cum[kk]) {
@@ -170,7 +165,7 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
       }
     }
     if (tree_done) {
-      a.score[slot] = bad ? static_cast<double>(NAN) : weight * prod;
+      a.score[slot] = bad ? NAN : weight * prod;
       if (a.segs) a.segs[slot] = bad ? -segments : segments;
       my_segs += static_cast<unsigned long long>(segments);
       if (bad) ++my_disc;

@@ -18,14 +18,14 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
   const uint64_t wave = std::min<uint64_t>(total, ctx->wave_max_paths);
   const size_t acc_off = 256;
   const size_t score_off = align_up(acc_off + static_cast<size_t>(n) * sizeof(NodeAcc), 256);
-  const size_t bytes = align_up(score_off + wave * sizeof(double), 256);
+  const size_t bytes = align_up(score_off + wave * sizeof(float), 256);
   pdd_status st = ensure_scratch(ctx, bytes);
   if (st != PDD_OK) return st;
   char *base = static_cast<char *>(ctx->scratch);
   auto *counters = reinterpret_cast<unsigned long long *>(base);
   auto *cursor = counters + 4;
   auto *acc = reinterpret_cast<NodeAcc *>(base + acc_off);
-  double *score = reinterpret_cast<double *>(base + score_off);
+  float *score = reinterpret_cast<float *>(base + score_off);
   PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, score_off, ctx->stream));
 
   const double *prm = ctx->params.data();
@@ -46,8 +46,8 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
   for (int k = 0; k <= a.K; ++k) {
     const double q = prm[4 + k], al = prm[5 + a.K + k];
     cum += q;
-    a.cum[k] = cum;
-    a.ratio[k] = q > 0.0 ? al / q : 0.0;
+    a.cum[k] = static_cast<float>(cum);
+    a.ratio[k] = static_cast<float>(q > 0.0 ? al / q : 0.0);
   }
   a.max_particles = bp->max_particles;
   a.max_depth = bp->max_depth;
@@ -72,12 +72,15 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
     PDD_CUDA_TRY(ctx, cudaGetLastError());
     if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
     const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
-    reduce_wave_kernel<double, true><<<static_cast<unsigned>(node_hi - node_lo + 1), kReduceBlock,
+    reduce_wave_kernel<float, true><<<static_cast<unsigned>(node_hi - node_lo + 1), kReduceBlock,
                                        0, ctx->stream>>>(score, b0, b1, N, node_lo, acc);
     PDD_CUDA_TRY(ctx, cudaGetLastError());
-    if (diag && diag->d_path_score)
-      PDD_CUDA_TRY(ctx, cudaMemcpyAsync(diag->d_path_score + b0, score, (b1 - b0) * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, ctx->stream));
+    if (diag && diag->d_path_score) {
+      const uint64_t cnt = b1 - b0;
+      const unsigned g = static_cast<unsigned>(std::min<uint64_t>((cnt + 255) / 256, 8192));
+      widen_scores_kernel<float><<<g, 256, 0, ctx->stream>>>(score, diag->d_path_score + b0, cnt);
+      PDD_CUDA_TRY(ctx, cudaGetLastError());
+    }
   }
   finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(
       acc, n, d_mean, d_se, d_nkept);

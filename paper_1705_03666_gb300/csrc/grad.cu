@@ -11,7 +11,7 @@
 //                      and the exit rule do not depend on phi).
 // The path kernel runs in its gradient mode and writes one 80-byte record per
 // path (score, exit point, L); jac_reduce_kernel forms the per-node means of the
-// 80 components with FP64 sums in a fixed order; vjp_kernel contracts them
+// 80 components with compensated sums in a fixed order; vjp_kernel contracts them
 // with a cotangent over the nodes.
 #include <cmath>
 #include <cstring>
@@ -30,8 +30,9 @@ constexpr int kJacGroups = kJacBlock / kJacLanes;
 // Per node (one block): for each path record, thread m of a path group forms
 // cos(m pi x) and, by the Chebyshev recurrence from cos(pi y), cos(n pi y) for
 // n = 0..7, and accumulates its eight theta components (8m + n) and the two
-// phi components m and 8 + m (s * L_j) with their squares, in FP64; the 32
-// groups are combined in a fixed order and merged into the node's running
+// phi components m and 8 + m (s * L_j) with their squares as two-float sums
+// on the FP32 pipe (~48-bit; FP64 is a 1/64-rate pipe here); the 32 groups
+// are combined in FP64 in a fixed order and merged into the node's running
 // (count, mean, M2) per component (Chan).
 __global__ void __launch_bounds__(kJacBlock)
 jac_reduce_kernel(const GradRec *__restrict__ rec, uint64_t begin, uint64_t end,
@@ -44,9 +45,7 @@ jac_reduce_kernel(const GradRec *__restrict__ rec, uint64_t begin, uint64_t end,
   const uint64_t cnt = hi - lo;
   const int m = threadIdx.x % kJacLanes, grp = threadIdx.x / kJacLanes;
   const float fm = static_cast<float>(m);
-  double s1[10], s2[10];
-#pragma unroll
-  for (int c = 0; c < 10; ++c) s1[c] = s2[c] = 0.0;
+  F2Sum s1[10], s2[10];  // two-float sums on the FP32 pipe (see reduce.cuh)
   for (uint64_t p = grp; p < cnt; p += kJacGroups) {
     const float x = r[p].x, y = r[p].y;
     const float cxm = cospif(fm * x);
@@ -69,16 +68,17 @@ jac_reduce_kernel(const GradRec *__restrict__ rec, uint64_t begin, uint64_t end,
     v[9] = sc * r[p].L[8 + m];
 #pragma unroll
     for (int c = 0; c < 10; ++c) {
-      const double d = static_cast<double>(v[c]);
-      s1[c] += d;
-      s2[c] = fma(d, d, s2[c]);
+      s1[c].add(v[c]);
+      const float q = v[c] * v[c];
+      s2[c].add(q);
+      s2[c].lo += fmaf(v[c], v[c], -q);
     }
   }
   __shared__ double sh1[kJacGroups][kJacLanes * 10], sh2[kJacGroups][kJacLanes * 10];
 #pragma unroll
   for (int c = 0; c < 10; ++c) {
-    sh1[grp][m * 10 + c] = s1[c];
-    sh2[grp][m * 10 + c] = s2[c];
+    sh1[grp][m * 10 + c] = static_cast<double>(s1[c].hi) + static_cast<double>(s1[c].lo);
+    sh2[grp][m * 10 + c] = static_cast<double>(s2[c].hi) + static_cast<double>(s2[c].lo);
   }
   __syncthreads();
   // 80 threads finish one component each: slot t = m*10 + c

@@ -188,13 +188,16 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
     // ---- Euler-Maruyama step (left point)
     R b[3] = {R(0), R(0), R(0)}, f = R(0);
     Model::template coeffs<R>(a.mc, X, b, f);
-    const R Y = r_exp<R>(static_cast<R>(n) * cdt + sphil);
+    // Y at the step's start; needed every step only with a source term
+    constexpr bool kYStep = Model::kSource;
+    const R Y = kYStep ? r_exp<R>(static_cast<R>(n) * cdt + sphil) : R(0);
     R Xn[3];
 #pragma unroll
     for (int k = 0; k < D; ++k) Xn[k] = X[k] + b[k] * dt + sdt * xi[k];
 
     // ---- reflection on reflecting faces within reach
     R yr = Y, zr = R(0);
+    bool have_y = kYStep;
     bool have_r = false;
     uint4 rw = make_uint4(0, 0, 0, 0);
 #pragma unroll
@@ -217,14 +220,17 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
         R xp[3] = {Xn[0], Xn[1], Xn[2]};
         xp[k] = R(j & 1);
         const R psi = RobinData<Model>::template dudn<R>(j, xp) - phi * RobinData<Model>::template u<R>(xp);
+        if (!have_y) {
+          yr = r_exp<R>(static_cast<R>(n) * cdt + sphil);
+          have_y = true;
+        }
         const R g1 = phi != R(0) ? r_expm1<R>(phi * L) / phi : L;
         zr += psi * yr * g1;
         yr *= r_exp<R>(phi * L);
         sphil += phi * L;
       }
     }
-    const R Yn = r_exp<R>(static_cast<R>(n + 1) * cdt + sphil);
-    const R Zn = Z + f * Y * dt + zr;
+    const R Zn = kYStep ? Z + f * Y * dt + zr : Z + zr;
 
     // ---- exit through absorbing faces
     bool out = false;
@@ -257,6 +263,7 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
     }
     ++n;
     if (out) {
+      const R Yn = r_exp<R>(static_cast<R>(n) * cdt + sphil);  // n already advanced
       score[slot] = Model::template g<R>(a.mc, xe) * Yn + Zn;
       if (a.steps) a.steps[slot] = n;
       my_steps += static_cast<unsigned long long>(n);
@@ -284,6 +291,7 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
 #pragma unroll
       for (int j = 0; j < 2 * D; ++j)
         if (j == jn) G::template project<R>(j, xc);
+      const R Yn = r_exp<R>(static_cast<R>(n) * cdt + sphil);
       score[slot] = Model::template g<R>(a.mc, xc) * Yn + Zn;
       if (a.steps) a.steps[slot] = -n;
       my_steps += static_cast<unsigned long long>(n);

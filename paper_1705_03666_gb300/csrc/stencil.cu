@@ -7,10 +7,11 @@
 //    rows).
 // 2. fill_kernel: Dirichlet data on the grid boundary -- g on the physical
 //    sides, the spline on the interface side -- and a zero interior.
-// 3. cg_kernel / jacobi_kernel: the 5-point system
+// 3. cg_kernel / cg_mixed_kernel / jacobi_kernel: the 5-point system
 //      (u[i+1,j] - 2u + u[i-1,j]) / hx^2 + (u[i,j+1] - 2u + u[i,j-1]) / hy^2 = 0
-//    by conjugate gradients (one CTA, vectors L2-resident, fixed-order block
-//    reductions) or Jacobi sweeps, both bounded by max_iter.
+//    by conjugate gradients in FP64 or as FP32 CG inside FP64 iterative
+//    refinement (one CTA, vectors L2-resident, fixed-order block reductions),
+//    or Jacobi sweeps, all bounded by max_iter.
 #include <cmath>
 #include <cstring>
 
@@ -153,17 +154,60 @@ __device__ double block_max(double v, double *sh) {
   return r;
 }
 
+// Grid position of a block-strided flat index k = threadIdx.x + t * blockDim,
+// advanced without divisions (the 64-bit k / nx, k % nx of a plain loop cost
+// more than the stencil arithmetic).
+struct GridWalk {
+  int k, i, j, di, dj, nx;
+  __device__ __forceinline__ GridWalk(int nx_) : nx(nx_) {
+    k = threadIdx.x;
+    i = k % nx;
+    j = k / nx;
+    di = kStencilBlock % nx;
+    dj = kStencilBlock / nx;
+  }
+  __device__ __forceinline__ void next() {
+    k += kStencilBlock;
+    i += di;
+    j += dj;
+    if (i >= nx) {
+      i -= nx;
+      ++j;
+    }
+  }
+};
+
+// FP32 block sum in a fixed tree (warp shuffles, then warp 0 over the 32
+// warp partials), broadcast to every thread.
+__device__ float block_sum_f(float v, float *sh) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    float t = sh[lane];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(kFull, t, m);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  const float r = sh[32];
+  __syncthreads();
+  return r;
+}
+
 // Conjugate gradients on the interior unknowns of A = -Lap_h (SPD).  With the
 // interior initialised to 0, r0 = Lap_h(u) over the full grid = b.
 __global__ void __launch_bounds__(kStencilBlock)
 cg_kernel(double *u, int nx, int ny, double ihx2, double ihy2, double *r, double *p, double *q,
           int64_t max_iter, double tol, int64_t *iters_out, double *resid_out) {
   __shared__ double sh[33];
-  const int64_t N = static_cast<int64_t>(nx) * ny;
+  const int N = nx * ny;
   const double diag = 2.0 * ihx2 + 2.0 * ihy2;
   double rr_loc = 0.0;
-  for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) {
-    const int i = static_cast<int>(k % nx), j = static_cast<int>(k / nx);
+  for (GridWalk w(nx); w.k < N; w.next()) {
+    const int k = w.k, i = w.i, j = w.j;
     double v = 0.0;
     if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1)
       v = ihx2 * (u[k - 1] + u[k + 1]) + ihy2 * (u[k - nx] + u[k + nx]) - diag * u[k];
@@ -177,8 +221,8 @@ cg_kernel(double *u, int nx, int ny, double ihx2, double ihy2, double *r, double
   double res = bnorm > 0.0 ? 1.0 : 0.0;
   while (it < max_iter && bnorm > 0.0 && sqrt(rr) > tol * bnorm) {
     double pq_loc = 0.0;
-    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) {
-      const int i = static_cast<int>(k % nx), j = static_cast<int>(k / nx);
+    for (GridWalk w(nx); w.k < N; w.next()) {
+      const int k = w.k, i = w.i, j = w.j;
       double v = 0.0;
       if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
         const double pw = i > 1 ? p[k - 1] : 0.0, pe = i < nx - 2 ? p[k + 1] : 0.0;
@@ -191,8 +235,8 @@ cg_kernel(double *u, int nx, int ny, double ihx2, double ihy2, double *r, double
     const double pq = block_sum(pq_loc, sh);
     const double alpha = rr / pq;
     double rn_loc = 0.0;
-    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) {
-      const int i = static_cast<int>(k % nx), j = static_cast<int>(k / nx);
+    for (GridWalk w(nx); w.k < N; w.next()) {
+      const int k = w.k, i = w.i, j = w.j;
       if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
         u[k] += alpha * p[k];
         const double rk = r[k] - alpha * q[k];
@@ -203,10 +247,119 @@ cg_kernel(double *u, int nx, int ny, double ihx2, double ihy2, double *r, double
     const double rn = block_sum(rn_loc, sh);
     const double beta = rn / rr;
     rr = rn;
-    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) p[k] = r[k] + beta * p[k];
+    for (int k = threadIdx.x; k < N; k += kStencilBlock) p[k] = r[k] + beta * p[k];
     __syncthreads();
     ++it;
     res = sqrt(rr) / bnorm;
+  }
+  if (threadIdx.x == 0) {
+    *iters_out = it;
+    *resid_out = res;
+  }
+}
+
+// Mixed-precision conjugate gradients (iterative refinement): the FP64
+// residual r = b - A u is formed, scaled to unit norm and rounded to FP32;
+// CG in FP32 (vectors, arithmetic and fixed-tree block sums) solves A e = r
+// to a relative residual of 1e-4, or just below what the stopping rule still
+// needs; u += ||r|| e in FP64; repeat until the FP64 residual meets the
+// stopping rule.  FP64 runs at 1/64 of the FP32 rate on this part and one
+// CTA owns the solve, so the inner iterations are what the FP32 pipe makes
+// cheap; the answer is the FP64 solution to the same tolerance.  rf/ef
+// share v0 and pf/qf share v1 (two FP32 vectors per FP64-sized buffer), the
+// FP64 residual is r64.
+template <bool kSmem>
+__global__ void __launch_bounds__(kStencilBlock)
+cg_mixed_kernel(double *u, int nx, int ny, double ihx2, double ihy2, double *v0, double *v1,
+                double *r64, int64_t max_iter, double tol, int64_t *iters_out, double *resid_out) {
+  __shared__ double sh[33];
+  __shared__ float shf[33];
+  extern __shared__ float dsm[];
+  const int N = nx * ny;
+  float *rf, *ef, *pf, *qf;
+  if constexpr (kSmem) {  // the three FP32 vectors in shared memory; A p recomputed
+    rf = dsm;
+    pf = dsm + N;
+    ef = dsm + 2 * N;
+    qf = nullptr;
+  } else {
+    rf = reinterpret_cast<float *>(v0);
+    ef = rf + N;
+    pf = reinterpret_cast<float *>(v1);
+    qf = pf + N;
+  }
+  const double diag = 2.0 * ihx2 + 2.0 * ihy2;
+  const float diag_f = static_cast<float>(diag), ihx2_f = static_cast<float>(ihx2),
+              ihy2_f = static_cast<float>(ihy2);
+  // A p at an interior point (zero Dirichlet data for the correction)
+  auto apply = [&](int k, int i, int j) -> float {
+    const float pw = i > 1 ? pf[k - 1] : 0.f, pe = i < nx - 2 ? pf[k + 1] : 0.f;
+    const float ps = j > 1 ? pf[k - nx] : 0.f, pn = j < ny - 2 ? pf[k + nx] : 0.f;
+    return diag_f * pf[k] - ihx2_f * (pw + pe) - ihy2_f * (ps + pn);
+  };
+  constexpr float kInnerTol = 1e-4f;
+  constexpr int kMaxOuter = 64;
+  int64_t it = 0;
+  double bnorm = 0.0, res = 0.0;
+  for (int outer = 0; outer < kMaxOuter; ++outer) {
+    // FP64 residual of the current iterate (interior unknowns)
+    double rr_loc = 0.0;
+    for (GridWalk w(nx); w.k < N; w.next()) {
+      const int k = w.k, i = w.i, j = w.j;
+      double v = 0.0;
+      if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1)
+        v = ihx2 * (u[k - 1] + u[k + 1]) + ihy2 * (u[k - nx] + u[k + nx]) - diag * u[k];
+      r64[k] = v;
+      rr_loc += v * v;
+    }
+    const double rnorm = sqrt(block_sum(rr_loc, sh));
+    if (outer == 0) bnorm = rnorm;
+    res = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    if (!(bnorm > 0.0) || res <= tol || it >= max_iter) break;
+    // reduce the residual by 1e-4, or by just what the stopping rule needs
+    const float need = static_cast<float>(0.5 * tol / res);
+    const float tol_in = need > kInnerTol ? need : kInnerTol;
+    const double sc = 1.0 / rnorm;
+    float rr_f = 0.f;
+    for (int k = threadIdx.x; k < N; k += kStencilBlock) {
+      const float v = static_cast<float>(r64[k] * sc);
+      rf[k] = v;
+      pf[k] = v;
+      ef[k] = 0.f;
+      rr_f += v * v;
+    }
+    float rr = block_sum_f(rr_f, shf);
+    const float stop = tol_in * tol_in * rr;
+    while (it < max_iter && rr > stop) {
+      float pq_f = 0.f;
+      for (GridWalk w(nx); w.k < N; w.next()) {
+        const int k = w.k, i = w.i, j = w.j;
+        const float v = (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) ? apply(k, i, j) : 0.f;
+        if constexpr (!kSmem) qf[k] = v;
+        pq_f += pf[k] * v;
+      }
+      const float pq = block_sum_f(pq_f, shf);
+      const float alpha = rr / pq;
+      float rn_f = 0.f;
+      for (GridWalk w(nx); w.k < N; w.next()) {
+        const int k = w.k, i = w.i, j = w.j;
+        float q;
+        if constexpr (kSmem) q = (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) ? apply(k, i, j) : 0.f;
+        else q = qf[k];
+        ef[k] += alpha * pf[k];
+        const float rk = rf[k] - alpha * q;
+        rf[k] = rk;
+        rn_f += rk * rk;
+      }
+      const float rn = block_sum_f(rn_f, shf);
+      const float beta = rn / rr;
+      rr = rn;
+      for (int k = threadIdx.x; k < N; k += kStencilBlock) pf[k] = rf[k] + beta * pf[k];
+      __syncthreads();
+      ++it;
+    }
+    for (int k = threadIdx.x; k < N; k += kStencilBlock) u[k] += static_cast<double>(ef[k]) * rnorm;
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
     *iters_out = it;
@@ -220,17 +373,17 @@ __global__ void __launch_bounds__(kStencilBlock)
 jacobi_kernel(double *u, double *tmp, int nx, int ny, double ihx2, double ihy2, int64_t max_iter,
               double tol, int64_t *iters_out, double *resid_out) {
   __shared__ double sh[33];
-  const int64_t N = static_cast<int64_t>(nx) * ny;
+  const int N = nx * ny;
   const double inv_diag = 1.0 / (2.0 * ihx2 + 2.0 * ihy2);
-  for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) tmp[k] = u[k];
+  for (int k = threadIdx.x; k < N; k += kStencilBlock) tmp[k] = u[k];
   __syncthreads();
   double *src = u, *dst = tmp;
   int64_t it = 0;
   double change = 0.0;
   while (it < max_iter) {
     double mx = 0.0;
-    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) {
-      const int i = static_cast<int>(k % nx), j = static_cast<int>(k / nx);
+    for (GridWalk w(nx); w.k < N; w.next()) {
+      const int k = w.k, i = w.i, j = w.j;
       if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
         const double v = (ihx2 * (src[k - 1] + src[k + 1]) + ihy2 * (src[k - nx] + src[k + nx])) * inv_diag;
         mx = fmax(mx, fabs(v - src[k]));
@@ -245,7 +398,7 @@ jacobi_kernel(double *u, double *tmp, int nx, int ny, double ihx2, double ihy2, 
     if (change < tol) break;
   }
   if (src != u)
-    for (int64_t k = threadIdx.x; k < N; k += kStencilBlock) u[k] = src[k];
+    for (int k = threadIdx.x; k < N; k += kStencilBlock) u[k] = src[k];
   if (threadIdx.x == 0) {
     *iters_out = it;
     *resid_out = change;
@@ -268,7 +421,8 @@ pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const dou
     return fail(ctx, PDD_EINVAL, "bad interface side");
   if (m < 2 || !d_iface_s || !d_iface_vals) return fail(ctx, PDD_EINVAL, "need >= 2 interface nodes");
   if (sd->max_iter < 0 || !(sd->tol >= 0.0)) return fail(ctx, PDD_EINVAL, "bad stopping rule");
-  if (sd->method != PDD_STENCIL_CG && sd->method != PDD_STENCIL_JACOBI)
+  if (sd->method != PDD_STENCIL_CG && sd->method != PDD_STENCIL_JACOBI &&
+      sd->method != PDD_STENCIL_CG_MIXED)
     return fail(ctx, PDD_EINVAL, "unknown method");
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const int K = static_cast<int>(m) + 1;
@@ -307,7 +461,23 @@ pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const dou
   if (sd->method == PDD_STENCIL_CG)
     cg_kernel<<<1, kStencilBlock, 0, ctx->stream>>>(d_u, nx, ny, ihx2, ihy2, v0, v1, v2,
                                                     sd->max_iter, sd->tol, it_d, res_d);
-  else
+  else if (sd->method == PDD_STENCIL_CG_MIXED) {
+    // the three FP32 vectors in shared memory when they fit (129 x 129: 200 KB)
+    const size_t smem = 3 * npts * sizeof(float);
+    int max_smem = 0;
+    PDD_CUDA_TRY(ctx, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                             ctx->device));
+    if (smem + 1024 <= static_cast<size_t>(max_smem)) {
+      PDD_CUDA_TRY(ctx, cudaFuncSetAttribute(cg_mixed_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem)));
+      cg_mixed_kernel<true><<<1, kStencilBlock, smem, ctx->stream>>>(
+          d_u, nx, ny, ihx2, ihy2, v0, v1, v2, sd->max_iter, sd->tol, it_d, res_d);
+    } else {
+      cg_mixed_kernel<false><<<1, kStencilBlock, 0, ctx->stream>>>(
+          d_u, nx, ny, ihx2, ihy2, v0, v1, v2, sd->max_iter, sd->tol, it_d, res_d);
+    }
+  } else
     jacobi_kernel<<<1, kStencilBlock, 0, ctx->stream>>>(d_u, v0, nx, ny, ihx2, ihy2,
                                                         sd->max_iter, sd->tol, it_d, res_d);
   PDD_CUDA_TRY(ctx, cudaGetLastError());

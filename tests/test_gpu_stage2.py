@@ -33,14 +33,15 @@ def _oracle_subdomain(orc, lo, hi, n, side, s_nodes, vals):
     return orc.stencil_solve(u, ((hi[0] - lo[0]) / (nx - 1), (hi[1] - lo[1]) / (ny - 1)))
 
 
+@pytest.mark.parametrize("method", ["cg", "cg_mixed"])
 @pytest.mark.parametrize("side,lo,hi", [(1, (0.0, 0.0), (0.5, 1.0)), (0, (0.5, 0.0), (1.0, 1.0))])
-def test_cg_matches_direct_solve(api, orc, side, lo, hi):
+def test_cg_matches_direct_solve(api, orc, side, lo, hi, method):
     s = W.nodes_cfg1(16)[:, 1]
     rng = np.random.default_rng(3)
     vals = np.exp(0.5) * np.cos(s) + 1e-3 * rng.standard_normal(16)   # noisy MC-like data
     with api.Context(W.laplace_expcos()) as ctx:
         r = ctx.subdomain_solve(lo, hi, (129, 129), 0, side, torch.from_numpy(s),
-                                torch.from_numpy(vals), method="cg", tol=1e-13)
+                                torch.from_numpy(vals), method=method, tol=1e-13)
     ref = _oracle_subdomain(orc, lo, hi, (129, 129), side, s, vals)
     assert r["status"] == 0 and r["resid"] <= 1e-13
     assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-10
@@ -86,3 +87,17 @@ def test_two_stage_pdd_laplace(api):
         err = np.max(np.abs(part["u"].cpu().numpy() - np.exp(X) * np.cos(Y)))
         assert part["status"] == 0
         assert err < 4.0 * se_max + 1e-3, err
+
+
+def test_mixed_cg_on_an_anisotropic_and_ragged_grid(api, orc):
+    """FP32 CG inside FP64 refinement reaches the FP64 answer on a grid
+    whose sizes are not multiples of the block (97 x 201, hx != hy)."""
+    s = np.linspace(0.05, 0.95, 9)
+    vals = np.exp(0.5) * np.cos(s)
+    lo, hi = (0.0, 0.0), (0.5, 1.0)
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.subdomain_solve(lo, hi, (97, 201), 0, 1, torch.from_numpy(s),
+                                torch.from_numpy(vals), method="cg_mixed", tol=1e-12)
+    ref = _oracle_subdomain(orc, lo, hi, (97, 201), 1, s, vals)
+    assert r["status"] == 0 and r["resid"] <= 1e-12
+    assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-9
