@@ -81,10 +81,10 @@ template <int D>
 __device__ __forceinline__ float grid_psi(const GridArgs &a, const float *x) {
   switch (a.psi_kind) {
     case 0: return a.psi_prm;
-    case 1: return 1.0f / (1.0f + expf(-a.psi_prm * x[0]));
+    case 1: return __fdividef(1.0f, 1.0f + expf(-a.psi_prm * x[0]));
     case 2: {
       const float e = 1.0f + expf(a.psi_prm * x[0]);
-      return 1.0f - 1.0f / (e * e);
+      return 1.0f - __fdividef(1.0f, e * e);
     }
     default: return sinpif(x[0]) * (D > 1 ? sinpif(x[1]) : 1.0f);
   }
@@ -99,7 +99,7 @@ __device__ __forceinline__ float grid_g(const GridArgs &a, const float *x, float
     case 1: return grid_psi<D>(a, x);
     case 2: {
       const float e = 1.0f + expf(a.psi_prm * x[0] - (5.0f / 6.0f) * a.beta_f * s);
-      return 1.0f - 1.0f / (e * e);
+      return 1.0f - __fdividef(1.0f, e * e);
     }
     default: return 0.0f;
   }
@@ -144,8 +144,13 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
   constexpr bool kBounded = GeomTraits<Geom>::kBounded;
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Tm = a.T[a.m - 1];
-  float4 stk[kBranchMaxDepth];  // pending particles: (x1, x2, birth tick, id)
-  float prod[kGridMaxTimes];
+  float4 stk[kBranchMaxDepth];  // pending particles: (x1, x2, birth tick, id | ti << 16)
+  // per-time products in shared memory (bank = lane): a local array indexed
+  // by the running time index lives in local memory, whose footprint over the
+  // grid exceeds L2 and went to DRAM
+  __shared__ float sprod[kGridMaxTimes][kBranchBlock];
+  float *prod_col = &sprod[0][threadIdx.x];
+#define PROD(k) prod_col[(k) * kBranchBlock]
   int sp = 0;
   float X[2] = {0.f, 0.f};
   uint32_t id = 0, t = 0, tend = 0, j = 0, u_off = 0;
@@ -158,59 +163,64 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
   bool active = false, need = true;
   unsigned long long my_steps = 0, my_disc = 0, my_bad = 0;
   WarpQueue wq;
+  NodeCache<float, D> nc;
   const unsigned long long total = a.end - a.begin;
 
   for (;;) {
-    while (__any_sync(kFull, need)) {
-      unsigned long long q = 0;
-      if (warp_claim<kGridChunk>(wq, a.cursor, total, need, q)) {
-        slot = q;
-        const unsigned long long g = a.begin + q;
-        const uint64_t nd = g / a.n_trees;
-        node = static_cast<uint32_t>(nd);
-        tree = static_cast<uint32_t>(g - nd * a.n_trees + a.tree_offset);
-        X[0] = static_cast<float>(a.nodes[nd * D]);
-        X[1] = D > 1 ? static_cast<float>(a.nodes[nd * D + 1]) : 0.f;
-        for (int k = 0; k < a.m; ++k) prod[k] = 1.0f;
-        t = 0;
-        id = 0;
-        next_id = 1;
-        sp = 0;
-        particles = 1;
-        nsteps = 0;
-        start = true;
-        bool done = false;
-        if constexpr (kBounded) {
-          if (!Geom::template inside_closed<float>(X)) {
-            for (int k = 0; k < a.m; ++k) a.score[k * a.wave + slot] = NAN;
-            if (a.steps) a.steps[slot] = 0;
-            ++my_bad;
-            done = true;
-          } else if (!Geom::template inside_open<float>(X)) {
-            // on the boundary: absorbed at time 0
-            for (int k = 0; k < a.m; ++k)
-              a.score[k * a.wave + slot] = grid_g<D>(a, X, static_cast<float>(a.T[k]) * a.inv_tps);
-            if (a.steps) a.steps[slot] = 0;
-            done = true;
+    if (claim_time(active)) {
+      need = !active;
+      while (__any_sync(kFull, need)) {
+        unsigned long long q = 0;
+        if (warp_claim<kGridChunk>(wq, a.cursor, total, need, q)) {
+          slot = q;
+          const unsigned long long g = a.begin + q;
+          nc.locate(g, a.n_trees, a.end, a.nodes);
+          node = static_cast<uint32_t>(nc.node);
+          tree = static_cast<uint32_t>(g - nc.lo + a.tree_offset);
+          X[0] = nc.x[0];
+          X[1] = D > 1 ? nc.x[D > 1 ? 1 : 0] : 0.f;
+          for (int k = 0; k < a.m; ++k) PROD(k) = 1.0f;
+          t = 0;
+          ti = 0;  // T_1 > 0
+          id = 0;
+          next_id = 1;
+          sp = 0;
+          particles = 1;
+          nsteps = 0;
+          start = true;
+          bool done = false;
+          if constexpr (kBounded) {
+            if (!Geom::template inside_closed<float>(X)) {
+              for (int k = 0; k < a.m; ++k) a.score[k * a.wave + slot] = NAN;
+              if (a.steps) a.steps[slot] = 0;
+              ++my_bad;
+              done = true;
+            } else if (!Geom::template inside_open<float>(X)) {
+              // on the boundary: absorbed at time 0
+              for (int k = 0; k < a.m; ++k)
+                a.score[k * a.wave + slot] = grid_g<D>(a, X, static_cast<float>(a.T[k]) * a.inv_tps);
+              if (a.steps) a.steps[slot] = 0;
+              done = true;
+            }
           }
+          if (done) need = true;
+          else active = true;
         }
-        if (done) need = true;
-        else active = true;
       }
+      if (!__any_sync(kFull, active)) break;
     }
-    if (!__any_sync(kFull, active)) break;
     if (!active) continue;
 
     if (start) {
       // lifetime of the current particle (block 0 of its stream)
       const uint4 w = philox10(id << 20, tree, node, 3u, a.rk);
-      const float ltk = -logf(unif_f(w.x)) * a.inv_beta * a.tps;
+      const float ltk = 0.5f * neg2log(unif_f(w.x)) * a.inv_beta * a.tps;
       const uint64_t e = ltk >= 4294967040.0f ? 4294967295ull : static_cast<uint64_t>(__float2uint_rz(ltk));
       const uint64_t te = static_cast<uint64_t>(t) + e;
       tend = te < Tm ? static_cast<uint32_t>(te) : Tm;
       u_off = w.w;
-      ti = 0;
-      while (ti < a.m && a.T[ti] <= t) ++ti;
+      // ti (first grid time after t) is carried: a child starts where its
+      // parent's walk ended, after the parent scored any grid time equal to t
       j = 1;
       start = false;
     }
@@ -233,7 +243,7 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
         float xe[2] = {0.f, 0.f};
         if (grid_exit<Geom, D>(a, X, Xn, h, v.z, xe)) {
           for (int k = ti; k < a.m; ++k)
-            prod[k] *= grid_g<D>(a, xe, static_cast<float>(a.T[k] - nxt) * a.inv_tps);
+            PROD(k) *= grid_g<D>(a, xe, static_cast<float>(a.T[k] - nxt) * a.inv_tps);
           pdone = true;
         }
       }
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
         X[1] = Xn[1];
         t = nxt;
         if (ti < a.m && t == a.T[ti]) {
-          prod[ti] *= grid_psi<D>(a, X);
+          PROD(ti) *= grid_psi<D>(a, X);
           ++ti;
         }
       }
@@ -262,7 +272,8 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
           }
         }
         const float r = a.ratio[k];
-        for (int kk = ti; kk < a.m; ++kk) prod[kk] *= r;
+        if (r != 1.0f)  // classical weights: nothing to do
+          for (int kk = ti; kk < a.m; ++kk) PROD(kk) *= r;
         particles += k;
         if (particles > a.max_particles || sp + k > a.max_depth) {
           bad = true;
@@ -271,7 +282,8 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
           pdone = true;
         } else {
           for (int c = k - 1; c >= 1; --c)
-            stk[sp++] = make_float4(X[0], X[1], __uint_as_float(tend), __uint_as_float(next_id + c));
+            stk[sp++] = make_float4(X[0], X[1], __uint_as_float(tend),
+                                    __uint_as_float((next_id + c) | (static_cast<uint32_t>(ti) << 16)));
           id = next_id;
           next_id += k;
           start = true;  // continue with the first child from (X, tend)
@@ -286,13 +298,14 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
         X[0] = p.x;
         X[1] = p.y;
         t = __float_as_uint(p.z);
-        id = __float_as_uint(p.w);
+        id = __float_as_uint(p.w) & 0xffffu;
+        ti = static_cast<int>(__float_as_uint(p.w) >> 16);
         start = true;
       }
     }
     if (tree_done) {
       for (int k = 0; k < a.m; ++k)
-        a.score[k * a.wave + slot] = bad ? NAN : prod[k];
+        a.score[k * a.wave + slot] = bad ? NAN : PROD(k);
       if (a.steps) a.steps[slot] = bad ? -nsteps : nsteps;
       my_steps += static_cast<unsigned long long>(nsteps);
       if (bad) ++my_disc;
@@ -311,6 +324,7 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
     if (my_disc) atomicAdd(&a.counters[1], my_disc);
     if (my_bad) atomicAdd(&a.counters[2], my_bad);
   }
+#undef PROD
 }
 
 // acc is [m][n]; outputs are [n][m].

@@ -56,10 +56,10 @@ template <int D>
 __device__ __forceinline__ float psi_eval(const BranchArgs &a, float x1, float x2) {
   switch (a.psi_kind) {
     case 0: return a.psi_prm;
-    case 1: return 1.0f / (1.0f + expf(-a.psi_prm * x1));
+    case 1: return __fdividef(1.0f, 1.0f + expf(-a.psi_prm * x1));
     case 2: {
       const float e = 1.0f + expf(a.psi_prm * x1);
-      return 1.0f - 1.0f / (e * e);
+      return 1.0f - __fdividef(1.0f, e * e);
     }
     default: return sinpif(x1) * (D > 1 ? sinpif(x2) : 1.0f);
   }
@@ -87,35 +87,42 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
   const unsigned long long total = a.end - a.begin;
 
   for (;;) {
-    while (__any_sync(kFull, need)) {
-      unsigned long long q = 0;
-      if (warp_claim<kBranchChunk>(wq, a.cursor, total, need, q)) {
-        slot = q;
-        const unsigned long long g = a.begin + q;
-        const uint64_t nd = g / a.n_trees;
-        node = static_cast<uint32_t>(nd);
-        tree = static_cast<uint32_t>(g - nd * a.n_trees + a.tree_offset);
-        const double *xt = a.nodes_xt + nd * (D + 1);
-        x0 = static_cast<float>(xt[0]);
-        x1 = D == 2 ? static_cast<float>(xt[1]) : 0.f;
-        t = static_cast<float>(xt[D]);
-        tb = 0.f;
-        id = 0;
-        next_id = 1;
-        sp = 0;
-        prod = 1.0f;
-        weight = 1.0f;
-        particles = 1;
-        segments = 0;
-        active = true;
+    if (claim_time<1>(active)) {
+      need = !active;
+      while (__any_sync(kFull, need)) {
+        unsigned long long q = 0;
+        if (warp_claim<kBranchChunk>(wq, a.cursor, total, need, q)) {
+          slot = q;
+          const unsigned long long g = a.begin + q;
+          // trees take ~2.5 segments: a per-lane node cache costs more in
+          // registers (occupancy) than the division it saves
+          const uint64_t nd = a.end <= 0xffffffffull
+                                  ? static_cast<uint32_t>(g) / static_cast<uint32_t>(a.n_trees)
+                                  : g / a.n_trees;
+          node = static_cast<uint32_t>(nd);
+          tree = static_cast<uint32_t>(g - nd * a.n_trees + a.tree_offset);
+          const double *xt = a.nodes_xt + nd * (D + 1);
+          x0 = static_cast<float>(xt[0]);
+          x1 = D == 2 ? static_cast<float>(xt[1]) : 0.f;
+          t = static_cast<float>(xt[D]);
+          tb = 0.f;
+          id = 0;
+          next_id = 1;
+          sp = 0;
+          prod = 1.0f;
+          weight = 1.0f;
+          particles = 1;
+          segments = 0;
+          active = true;
+        }
       }
+      if (!__any_sync(kFull, active)) break;
     }
-    if (!__any_sync(kFull, active)) break;
     if (!active) continue;
 
     // ---- one particle segment
     const uint4 w = philox10(id, tree, node, 1u, a.rk);
-    const float life = -logf(unif_f(w.x)) * a.inv_beta;
+    const float life = 0.5f * neg2log(unif_f(w.x)) * a.inv_beta;  // -ln U / beta
     float tend = tb + life;
     const bool reaches = tend >= t;
     if (reaches) tend = t;

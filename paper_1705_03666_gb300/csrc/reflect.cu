@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
   unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
   R *score = static_cast<R *>(a.score);
   WarpQueue wq;
+  NodeCache<R, D> nc;
   const unsigned long long total = a.end - a.begin;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
@@ -120,12 +121,12 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
       if (warp_claim<32>(wq, a.cursor, total, need, q)) {
         slot = q;
         const unsigned long long g = a.begin + q;
-        const uint64_t nd = g / a.n_paths;
-        node = static_cast<uint32_t>(nd);
-        path = static_cast<uint32_t>(g - nd * a.n_paths + a.path_offset);
+        nc.locate(g, a.n_paths, a.end, a.nodes);
+        node = static_cast<uint32_t>(nc.node);
+        path = static_cast<uint32_t>(g - nc.lo + a.path_offset);
         pp = philox_path(path, node, 0u, a.rk);
 #pragma unroll
-        for (int k = 0; k < D; ++k) X[k] = static_cast<R>(a.nodes[nd * D + k]);
+        for (int k = 0; k < D; ++k) X[k] = nc.x[k];
         n = 0;
         Z = R(0);
         sphil = R(0);

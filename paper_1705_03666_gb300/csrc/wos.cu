@@ -78,41 +78,49 @@ __global__ void __launch_bounds__(kPathBlock) wos_kernel(const __grid_constant__
   unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
   R *score = static_cast<R *>(a.score);
   WarpQueue wq;
+  NodeCache<R, 2> nc;
   const unsigned long long total = a.end - a.begin;
+  bool pending = false;  // stopped walk whose score is written at the next claim
   for (;;) {
-    while (__any_sync(kFull, need)) {
-      unsigned long long q = 0;
-      if (warp_claim<kWosChunk>(wq, a.cursor, total, need, q)) {
-        slot = q;
-        const unsigned long long g = a.begin + q;
-        const uint64_t node = g / a.n_paths;
-        const uint64_t path = g - node * a.n_paths + a.path_offset;
-        pp = philox_path(static_cast<uint32_t>(path), static_cast<uint32_t>(node), 2u, a.rk);
-        X[0] = static_cast<R>(a.nodes[node * 2]);
-        X[1] = static_cast<R>(a.nodes[node * 2 + 1]);
-        n = 0;
-        if (!Geom::inside_closed(X)) {
-          score[slot] = R(NAN);
-          if (a.steps) a.steps[slot] = 0;
-          ++my_bad;
-          need = true;
-        } else {
-          active = true;
+    if (claim_time(active)) {
+      if (pending) {
+        score[slot] = LaplaceExpCos::g<R>(a.mc, X);
+        if (a.steps) a.steps[slot] = n;
+        my_steps += static_cast<unsigned long long>(n);
+        pending = false;
+      }
+      need = !active;
+      while (__any_sync(kFull, need)) {
+        unsigned long long q = 0;
+        if (warp_claim<kWosChunk>(wq, a.cursor, total, need, q)) {
+          slot = q;
+          const unsigned long long g = a.begin + q;
+          nc.locate(g, a.n_paths, a.end, a.nodes);
+          const uint64_t path = g - nc.lo + a.path_offset;
+          pp = philox_path(static_cast<uint32_t>(path), static_cast<uint32_t>(nc.node), 2u, a.rk);
+          X[0] = nc.x[0];
+          X[1] = nc.x[1];
+          n = 0;
+          if (!Geom::inside_closed(X)) {
+            score[slot] = R(NAN);
+            if (a.steps) a.steps[slot] = 0;
+            ++my_bad;
+            need = true;
+          } else {
+            active = true;
+          }
         }
       }
+      if (!__any_sync(kFull, active)) break;
     }
-    if (!__any_sync(kFull, active)) break;
     if (!active) continue;
     int jb;
     const R d = wos_nearest<Geom, R>(X, jb);
     if (d <= eps || n >= a.max_steps) {
       if (n >= a.max_steps && d > eps) ++my_capped;
       wos_project<Geom, R>(jb, X);
-      score[slot] = LaplaceExpCos::g<R>(a.mc, X);
-      if (a.steps) a.steps[slot] = n;
-      my_steps += static_cast<unsigned long long>(n);
       active = false;
-      need = true;
+      pending = true;
       continue;
     }
     if ((n & 3) == 0) blk = philox10_path(static_cast<uint32_t>(n >> 2), pp, a.rk);
