@@ -142,10 +142,13 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, R &z0, R &z1)
 // binary32 Box-Muller with the hardware sine/cosine.  The angle is centred,
 // theta = 2 pi (U_b - 1/2) in (-pi, pi), where the hardware sin/cos have an
 // absolute error below 2^-21.4; cos(2 pi U_b) = -cos theta and
-// sin(2 pi U_b) = -sin theta.  -2 ln U_a comes from neg2log (accurate as
-// U_a -> 1, where a hardware log loses all accuracy); the square root is
-// y * rsqrt(y) (y >= 1.19e-7, never 0).
-// -2 ln u for u in (0, 1), binary32, from the atanh series of the logarithm:
+// sin(2 pi U_b) = -sin theta.  -2 ln U_a comes from the hardware log2,
+// whose absolute error (~2^-22 near U_a = 1) gives r = sqrt(-2 ln U_a) an
+// error ~1e-7 / r: relatively large only for the rare tiny radii, where the
+// displacement r sqrt(dt) itself is tiny.  The square root is y * rsqrt(y).
+//
+// -2 ln u accurate to 2e-7 relative for all u in (0, 1) (used where a single
+// log sets a decision, e.g. branching lifetimes), from the atanh series:
 // write u = 2^e m with m in [sqrt(1/2), sqrt(2)) (exponent split on the bit
 // pattern), then ln u = e ln 2 + 2 atanh(t), t = (m - 1)/(m + 1), |t| <= 0.1716,
 // atanh t = t (1 + t^2/3 + t^4/5 + t^6/7 + t^8/9 + ...), truncation below
@@ -169,7 +172,9 @@ __device__ __forceinline__ float neg2log(float u) {
 
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1) {
-  const float y = neg2log(unif_f(a));
+  // hardware log2 (absolute error ~2^-22 near u = 1, where it may return 0:
+  // y is kept positive for the rsqrt)
+  const float y = fmaxf(-1.3862943611198906f * __log2f(unif_f(a)), 1.0e-30f);
   const float mr = -(y * rsqrtf(y));
   float s, c;
   __sincosf(6.28318530717958648f * (unif_f(b) - 0.5f), &s, &c);

@@ -56,8 +56,13 @@ def test_philox_bit_exact(api, orc):
 
 
 def test_fp32_normals_match_oracle(api, orc):
-    """The binary32 Box-Muller normals (custom -2 ln u, hardware sin/cos on a
-    centred angle) against the oracle's FP64 normals from the same words."""
+    """The binary32 Box-Muller normals (hardware log2 for -2 ln u, hardware
+    sin/cos on a centred angle) against the oracle's FP64 normals from the
+    same words.  Error model: the hardware log2 has an absolute error of order
+    2^-22, so r^2 = -2 ln u carries ~2e-7 absolute and r = sqrt(r^2) carries
+    ~1e-7 / r; sin/cos add ~4e-7 r; rounding ~1e-7 |z|.  The bound below is
+    that model with a safety factor; it is loose only for the rare pairs
+    with a tiny radius (a 1e-3 radius has probability 5e-7)."""
     n = 1 << 22
     with api.Context(W.laplace_expcos()) as ctx:
         z, u = ctx.normals(W.SEED_BASE + 7, n, 3, 4, 9)
@@ -65,8 +70,13 @@ def test_fp32_normals_match_oracle(api, orc):
     z, u = z.cpu().numpy().astype(np.float64), u.cpu().numpy().astype(np.float64)
     assert np.array_equal(u, uo)                               # exact uniforms
     err = np.abs(z - zo)
-    assert err.max() < 2e-6 * max(1.0, np.abs(zo).max())     # ~1e-7 relative + trig
-    assert np.mean(err) < 2e-7
+    r = np.repeat(np.hypot(zo[0::2], zo[1::2]), 2)
+    bound = 4e-7 / np.maximum(r, 1e-4) + 2e-6 * np.maximum(1.0, np.abs(zo))
+    assert np.all(err <= bound), (err / bound).max()
+    assert np.mean(err) < 5e-7
+    # away from tiny radii the normals are accurate to a few 1e-7
+    big = r > 0.5
+    assert np.max(err[big] / np.maximum(1.0, np.abs(zo[big]))) < 2e-6
 
 
 def test_laplace_fp64_matches_oracle_path_by_path(api, orc):
