@@ -425,6 +425,19 @@ def run_other_workloads(api, dev) -> dict:
                                                 (bm["u"] - bb["u"]).abs().max()))},
                                "bytes_model": "13 vector accesses per point per CG iteration",
                                "residence": "L2/shared-resident (0.27 MB per vector)"}
+        # the whole two-stage method on this workload: stage one at its 16
+        # nodes (1e4 FP64 paths, dt = 1e-3), spline, both 129 x 129 halves
+        kw2 = dict(n_nodes=16, n_paths=w["n_paths"], dt=w["dt"], seed=w["seed"], precision="fp64")
+        api.laplace_pdd_solve(ctx, **kw2)
+        ms_pdd, rp = _timed(stream, lambda: api.laplace_pdd_solve(ctx, **kw2))
+        ys = torch.linspace(0.0, 1.0, 129, dtype=torch.float64, device=dev)
+        errs = []
+        for u, x0 in ((rp["left"], 0.0), (rp["right"], 0.5)):
+            xs = torch.linspace(x0, x0 + 0.5, 129, dtype=torch.float64, device=dev)
+            errs.append(float((u - torch.exp(xs)[None, :] * torch.cos(ys)[:, None]).abs().max()))
+        out["pdd_laplace2d_two_stage"] = {
+            "workload": w["name"] + " + two 129 x 129 subdomains", "ms": ms_pdd,
+            "max_abs_err_vs_exact": max(errs), "median_node_se": float(rp["se"].median())}
         # Walk on Spheres against Euler-Maruyama + bridge on the same 16 nodes,
         # 1e6 walks / paths per node in FP32: time, jumps or steps per walk, and
         # the largest error against the harmonic solution e^x cos y.

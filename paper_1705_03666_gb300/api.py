@@ -449,3 +449,26 @@ class InterfaceValues(torch.autograd.Function):
 def interface_values(theta, phi, pdd_ctx: Context, nodes, **mc):
     """Differentiable node estimates (see InterfaceValues)."""
     return InterfaceValues.apply(theta, phi, pdd_ctx, nodes, mc)
+
+
+def laplace_pdd_solve(ctx: Context, *, n_nodes: int = 16, n_paths: int = 10_000, dt: float = 1e-3,
+                      seed: int, grid=(129, 129), precision: str = "fp64",
+                      method: str = "cg_mixed", tol: float = 1e-12) -> dict:
+    """The two stages of PDD for the Laplace problem Eq. 1.1 on the unit square
+    split at x = 1/2 (Sec. 2.1, Fig. 2.2): stage one estimates u at n_nodes
+    interface nodes (1/2, k/(n_nodes+1)) by pdd_interface_solve; stage two
+    interpolates them (not-a-knot spline) and solves each half independently
+    by pdd_subdomain_solve.  Returns the node estimates and the two subdomain
+    grids ([ny][nx] each; they share the interface column x = 1/2)."""
+    if ctx.prob["problem"] != "laplace_expcos" or ctx.prob["geometry"] != "unit_square":
+        raise ValueError("laplace_pdd_solve needs the Laplace problem on the unit square")
+    y = torch.arange(1, n_nodes + 1, dtype=_F64) / (n_nodes + 1)
+    nodes = torch.stack([torch.full_like(y, 0.5), y], 1)
+    r = ctx.interface_solve(nodes, seed=seed, dt=dt, n_paths=n_paths, precision=precision)
+    left = ctx.subdomain_solve((0.0, 0.0), (0.5, 1.0), grid, 0, 1, y, r["mean"], method=method,
+                               tol=tol)
+    right = ctx.subdomain_solve((0.5, 0.0), (1.0, 1.0), grid, 0, 0, y, r["mean"], method=method,
+                                tol=tol)
+    return {"nodes": nodes, "mean": r["mean"], "se": r["se"], "left": left["u"],
+            "right": right["u"], "iters": left["iters"] + right["iters"],
+            "status": max(left["status"], right["status"])}

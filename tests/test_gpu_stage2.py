@@ -101,3 +101,29 @@ def test_mixed_cg_on_an_anisotropic_and_ragged_grid(api, orc):
     ref = _oracle_subdomain(orc, lo, hi, (97, 201), 1, s, vals)
     assert r["status"] == 0 and r["resid"] <= 1e-12
     assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-9
+
+
+def test_two_stage_pdd_solve_end_to_end(api, orc):
+    """Stage one (16 interface nodes, FP64 paths) then stage two (spline +
+    both halves).  By the discrete maximum principle, the error of each half
+    is bounded by its boundary error -- on the interface, the spline of the
+    Monte Carlo values against e^x cos y -- plus the O(h^2) consistency error
+    of the 5-point scheme."""
+    prob = W.laplace_expcos()
+    with api.Context(prob) as ctx:
+        r = api.laplace_pdd_solve(ctx, n_paths=40_000, seed=W.SEED_BASE + 51)
+    assert r["status"] == 0
+    ny, nx = r["left"].shape
+    ys = np.linspace(0.0, 1.0, ny)
+    s = r["nodes"][:, 1].numpy()
+    spl = orc.spline_interface(s, r["mean"].cpu().numpy(), ys, np.exp(0.5), np.exp(0.5) * np.cos(1.0))
+    iface_err = np.max(np.abs(spl - np.exp(0.5) * np.cos(ys)))
+    for u, x0 in ((r["left"], 0.0), (r["right"], 0.5)):
+        X, Y = np.meshgrid(np.linspace(x0, x0 + 0.5, nx), ys)
+        err = np.max(np.abs(u.cpu().numpy() - np.exp(X) * np.cos(Y)))
+        assert err <= iface_err + 2e-5, (err, iface_err)
+    # the interface column of both halves is the same spline
+    assert torch.allclose(r["left"][:, -1], r["right"][:, 0], rtol=0, atol=1e-14)
+    # and the Monte Carlo node values are within their standard errors
+    exact = np.exp(0.5) * np.cos(s)
+    assert np.all(np.abs(r["mean"].cpu().numpy() - exact) <= 4.5 * r["se"].cpu().numpy() + 2e-3)
