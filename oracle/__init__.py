@@ -107,6 +107,9 @@ def _load():
                                                      M, ctypes.c_int64, ctypes.c_int32,
                                                      dp, dp, lp, lp, dp, ip]
             lib.orc_branching_grid_solve.restype = ctypes.c_int
+            lib.orc_mlmc_level.argtypes = [P, dp, ctypes.c_int64, M, ctypes.c_int32,
+                                           ctypes.c_int32, dp, dp, dp, dp, dp, ip, lp]
+            lib.orc_mlmc_level.restype = ctypes.c_int
             lib.orc_grid_ticks_per_unit.argtypes = [ctypes.c_double]
             lib.orc_grid_ticks_per_unit.restype = ctypes.c_double
             _lib = lib
@@ -340,6 +343,45 @@ def branching_grid_solve(prob: dict, nodes, times, *, seed, n_trees, dt=1e-3,
     if dump_trees:
         out["score"], out["steps"] = ts, tg
     return out
+
+
+def mlmc_level(prob: dict, nodes, *, seed, dt0, level, refine=2, n_paths, max_steps=10**8,
+               bridge=True, n_threads=None, dump_paths=False):
+    """One level of the multilevel estimator (Sec. 2.1): mean and variance per
+    node of P_l - P_{l-1} (P_0 at level 0) from coupled fine/coarse Euler
+    paths, plus the fine and coarse means."""
+    lib = _load()
+    d = int(prob["dim"])
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, d)
+    n = nodes.shape[0]
+    P, keep = _problem(prob)
+    M = _mc(seed, dt0, n_paths, max_steps, bridge, n_threads)
+    mean, var, fm, cm = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)
+    diff = np.zeros((n, n_paths)) if dump_paths else None
+    steps = np.zeros((n, n_paths), dtype=np.int32) if dump_paths else None
+    cap = ctypes.c_int64(0)
+    rc = lib.orc_mlmc_level(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n, ctypes.byref(M),
+                            int(level), int(refine), _ptr(mean, ctypes.c_double),
+                            _ptr(var, ctypes.c_double), _ptr(fm, ctypes.c_double),
+                            _ptr(cm, ctypes.c_double), _ptr(diff, ctypes.c_double),
+                            _ptr(steps, ctypes.c_int32), ctypes.byref(cap))
+    if rc != 0:
+        raise ValueError("oracle mlmc_level: invalid arguments")
+    out = {"mean": mean, "var": var, "fine_mean": fm, "coarse_mean": cm, "capped": cap.value}
+    if dump_paths:
+        out["diff"], out["steps"] = diff, steps
+    return out
+
+
+def mlmc_solve(prob: dict, nodes, *, seed, dt0, refine=2, n_per_level, bridge=True,
+               n_threads=None):
+    """Multilevel estimate: sum of the level means; se = sqrt(sum var_l / N_l)."""
+    levels = [mlmc_level(prob, nodes, seed=seed, dt0=dt0, level=l, refine=refine, n_paths=N,
+                         bridge=bridge, n_threads=n_threads)
+              for l, N in enumerate(n_per_level)]
+    mean = sum(L["mean"] for L in levels)
+    se = np.sqrt(sum(L["var"] / N for L, N in zip(levels, n_per_level)))
+    return {"mean": mean, "se": se, "levels": levels}
 
 
 def grid_ticks_per_unit(t_max: float) -> float:

@@ -953,6 +953,166 @@ int orc_branching_solve(const orc_problem *P, const double *nodes_xt, int64_t n,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Multilevel Monte Carlo for the interface estimate (Sec. 2.1 names Giles'  */
+/* multilevel method as the next acceleration of the Euler scheme):          */
+/*   E[P_L] = E[P_0] + sum_{l=1..L} E[P_l - P_{l-1}],                       */
+/* P_l the score of the Euler-Maruyama path with step dt_l = dt_0 / R^l     */
+/* (R = refine).  Level l >= 1 samples a coupled pair: the fine path with   */
+/* dt_l and the coarse path with dt_{l-1} driven by the same Brownian       */
+/* motion, the coarse increment being the sum of the R fine ones; each path */
+/* stops at its own exit (hard exit or the half-space bridge test of the    */
+/* linear paths) and the pair is done when both are.  Fine step k of sample */
+/* p at node i reads Philox(key, (k, p, i, 16 + l)): normals BM(w0, w1),    */
+/* bridge uniform U(w2); the coarse step that closes a group of R fine       */
+/* steps takes the uniform of the group's last fine step (independent of   */
+/* every normal, so each path has the law of the plain scheme at its step;   */
+/* the pair shares it to couple the exit decisions).  Level 0 is the plain  */
+/* scheme with step dt_0 on tag 16.  Dimensions 1 and 2, Dirichlet data.    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double X[3], Y, Z;
+  int done;
+  double score;
+} mlmc_walk;
+
+/* One Euler-Maruyama step of a walk with time step dt and Brownian increment
+ * dW (already scaled), exit tests with the bridge uniform U (left point for
+ * Y and Z, exit at the end of the step).                                  */
+static void mlmc_step(const orc_problem *P, const orc_mc *M, double dt, const double *dW,
+                      double U, mlmc_walk *w) {
+  const int dim = P->dim, geom = P->geometry;
+  const double sig = P->sigma;
+  double b[3];
+  coef_drift(P, w->X, b);
+  const double c = coef_c(P, w->X), f = coef_f(P, w->X);
+  double Xn[3] = {0, 0, 0};
+  for (int k = 0; k < dim; ++k) Xn[k] = w->X[k] + b[k] * dt + sig * dW[k];
+  const double Yn = w->Y * exp(c * dt);
+  const double Zn = w->Z + f * w->Y * dt;
+  if (!inside_closed(geom, dim, Xn)) {
+    double xe[3] = {0, 0, 0};
+    segment_exit(geom, dim, w->X, Xn, xe);
+    w->score = coef_g(P, xe) * Yn + Zn;
+    w->done = 1;
+    return;
+  }
+  if (M->bridge) {
+    double keep = 1.0, pbest = -1.0;
+    int jbest = -1;
+    for (int j = 0; j < n_faces(geom, dim); ++j) {
+      double a = 2.0 * face_dist(geom, j, w->X) * face_dist(geom, j, Xn) / (sig * sig * dt);
+      if (a < 18.0) {
+        double p = exp(-a);
+        keep *= 1.0 - p;
+        if (p > pbest) { pbest = p; jbest = j; }
+      }
+    }
+    if (jbest >= 0 && U < 1.0 - keep) {
+      double xe[3] = {Xn[0], Xn[1], Xn[2]};
+      face_project(geom, jbest, xe);
+      w->score = coef_g(P, xe) * Yn + Zn;
+      w->done = 1;
+      return;
+    }
+  }
+  for (int k = 0; k < dim; ++k) w->X[k] = Xn[k];
+  w->Y = Yn;
+  w->Z = Zn;
+}
+
+static void mlmc_cap(const orc_problem *P, mlmc_walk *w) {
+  double xe[3] = {w->X[0], w->X[1], w->X[2]};
+  face_project(P->geometry, nearest_face(P->geometry, P->dim, w->X), xe);
+  w->score = coef_g(P, xe) * w->Y + w->Z;
+  w->done = 1;
+}
+
+typedef struct {
+  const orc_problem *P;
+  const orc_mc *M;
+  const double *nodes;
+  int level, refine;
+  double *mean, *var, *fine_mean, *coarse_mean, *path_diff;
+  int32_t *path_steps;
+  int64_t *capped;
+} mlmc_ctx;
+
+static void mlmc_node(void *vp, int64_t i) {
+  mlmc_ctx *C = (mlmc_ctx *)vp;
+  const orc_problem *P = C->P;
+  const orc_mc *M = C->M;
+  const int dim = P->dim, l = C->level, R = C->refine;
+  const double dtf = M->dt / pow((double)R, (double)l);
+  const double sdf = sqrt(dtf);
+  const uint32_t key[2] = {(uint32_t)M->seed, (uint32_t)(M->seed >> 32)};
+  const int64_t N = M->n_paths;
+  double m = 0.0, m2 = 0.0, mf = 0.0, mc = 0.0;
+  int64_t caps = 0;
+  for (int64_t p = 0; p < N; ++p) {
+    mlmc_walk fw, cw;
+    memset(&fw, 0, sizeof fw);
+    for (int k = 0; k < dim; ++k) fw.X[k] = C->nodes[i * dim + k];
+    fw.Y = 1.0;
+    cw = fw;
+    if (!inside_open(P->geometry, dim, fw.X)) {
+      fw.score = cw.score = coef_g(P, fw.X);
+      fw.done = cw.done = 1;
+    }
+    if (l == 0) cw.done = 1;
+    double dWc[3] = {0, 0, 0};
+    int64_t k = 0;
+    while (!(fw.done && cw.done) && k < M->max_steps) {
+      uint32_t ctr[4] = {(uint32_t)k, (uint32_t)p, (uint32_t)i, 16u + (uint32_t)l}, w[4];
+      orc_philox4x32_10(ctr, key, w);
+      double z0, z1;
+      box_muller(w[0], w[1], &z0, &z1);
+      const double dW[3] = {sdf * z0, dim > 1 ? sdf * z1 : 0.0, 0.0};
+      const double U = unif(w[2]);
+      if (!fw.done) mlmc_step(P, M, dtf, dW, U, &fw);
+      for (int d = 0; d < dim; ++d) dWc[d] += dW[d];
+      ++k;
+      if (l > 0 && k % R == 0) {
+        if (!cw.done) mlmc_step(P, M, dtf * R, dWc, U, &cw);
+        dWc[0] = dWc[1] = dWc[2] = 0.0;
+      }
+    }
+    if (!fw.done) { mlmc_cap(P, &fw); ++caps; }
+    if (l > 0 && !cw.done) { mlmc_cap(P, &cw); ++caps; }
+    const double y = l > 0 ? fw.score - cw.score : fw.score;
+    const double d = y - m;
+    m += d / (double)(p + 1);
+    m2 += d * (y - m);
+    mf += (fw.score - mf) / (double)(p + 1);
+    if (l > 0) mc += (cw.score - mc) / (double)(p + 1);
+    if (C->path_diff) C->path_diff[i * N + p] = y;
+    if (C->path_steps) C->path_steps[i * N + p] = (int32_t)k;
+  }
+  C->mean[i] = m;
+  C->var[i] = N > 1 ? m2 / (double)(N - 1) : 0.0;
+  if (C->fine_mean) C->fine_mean[i] = mf;
+  if (C->coarse_mean) C->coarse_mean[i] = mc;
+  C->capped[i] = caps;
+}
+
+int orc_mlmc_level(const orc_problem *P, const double *nodes, int64_t n, const orc_mc *M,
+                   int32_t level, int32_t refine, double *mean, double *var,
+                   double *fine_mean, double *coarse_mean, double *path_diff,
+                   int32_t *path_steps, int64_t *total_capped) {
+  if (!P || !M || n < 0 || M->n_paths < 1 || !(M->dt > 0.0) || P->dim < 1 || P->dim > 2 ||
+      M->max_steps < 1 || level < 0 || level > 12 || refine < 2 || refine > 16)
+    return 1;
+  int64_t *cap = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  mlmc_ctx C = {P, M, nodes, level, refine, mean, var, fine_mean, coarse_mean,
+                path_diff, path_steps, cap};
+  parallel_for(n, M->n_threads, mlmc_node, &C);
+  int64_t tc = 0;
+  for (int64_t i = 0; i < n; ++i) tc += cap[i];
+  if (total_capped) *total_capped = tc;
+  free(cap);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Branching Brownian motion on a time grid, with absorbing boundaries       */
 /* (Eq. 3.2) and one tree per node for every time point (Algorithm 3.1).     */
 /*                                                                          */
