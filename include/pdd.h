@@ -285,6 +285,39 @@ PDD_API pdd_status pdd_branching_solve(pdd_ctx *ctx, const double *d_nodes_xt,
                                        double *d_mean, double *d_se,
                                        int64_t *d_nkept, pdd_diag *diag);
 
+/* One level of the multilevel Monte Carlo estimator (Sec. 2.1 names Giles'
+ * multilevel method as the next acceleration of the Euler scheme):
+ *   E[P_L] = E[P_0] + sum_{l=1..L} E[P_l - P_{l-1}],
+ * P_l the score of the Euler-Maruyama path (Eq. 2.8, with the exit test of
+ * pdd_interface_solve) with step dt_l = dt0 / refine^l.  Level l >= 1 draws
+ * coupled pairs: the fine path with dt_l and the coarse path with dt_{l-1}
+ * driven by the same Brownian motion (coarse increment = sum of the refine
+ * fine increments), each stopping at its own exit.  Fine step k of pair p at
+ * node i reads Philox(key = seed, counter = (k, p, i, 16 + level)): normals
+ * BM(w0, w1), bridge uniform U(w2); a coarse step takes the uniform of the
+ * last fine step of its group.  Level 0 is the plain scheme with dt0.
+ * Dirichlet data, 2-D families (LAPLACE_EXPCOS on the square or L-shape,
+ * POISSON_FOURIER).  Writes, per node, d_mean (mean of P_l - P_{l-1}, or of
+ * P_0), d_var (its sample variance) and, if non-NULL, the fine and coarse
+ * means.  The caller sums the levels: mean = sum of means, se = sqrt(sum
+ * var_l / n_paths_l).  diag as for pdd_interface_solve (path_steps counts
+ * fine steps; d_path_score receives P_l - P_{l-1} per pair).            */
+typedef struct {
+  uint64_t seed;
+  int64_t n_paths;     /* pairs per node at this level */
+  int64_t max_steps;   /* fine-step cap per pair (capped walks are counted) */
+  double dt0;          /* level-0 step; sigma^2 dt0 <= 1/36 */
+  int32_t level;       /* 0..12 */
+  int32_t refine;      /* step ratio between levels, 2..16 */
+  int32_t precision;   /* PDD_FP32 or PDD_FP64 */
+  int32_t bridge;      /* 1 = bridge exit test */
+} pdd_mlmc_params;
+
+PDD_API pdd_status pdd_mlmc_level(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                  const pdd_mlmc_params *mp, double *d_mean,
+                                  double *d_var, double *d_fine_mean,
+                                  double *d_coarse_mean, pdd_diag *diag);
+
 /* Parameters of the time-grid branching estimator. */
 typedef struct {
   uint64_t seed;          /* Philox key */

@@ -46,6 +46,13 @@ class GridBranchParams(ctypes.Structure):
                 ("dt", ctypes.c_double)]
 
 
+class MlmcParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_paths", ctypes.c_int64),
+                ("max_steps", ctypes.c_int64), ("dt0", ctypes.c_double),
+                ("level", ctypes.c_int32), ("refine", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("bridge", ctypes.c_int32)]
+
+
 class Subdomain(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("n", ctypes.c_int32 * 3), ("iface_axis", ctypes.c_int32),
@@ -121,6 +128,8 @@ _SIGS = {
     "pdd_branching_grid_solve": (ctypes.c_int, [_VP, _VP, _I64, _VP, ctypes.c_int32,
                                                 ctypes.POINTER(GridBranchParams), _VP, _VP, _VP,
                                                 ctypes.POINTER(Diag)]),
+    "pdd_mlmc_level": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(MlmcParams), _VP, _VP, _VP,
+                                      _VP, ctypes.POINTER(Diag)]),
     "pdd_philox_stream": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _U32, _I64, _VP]),
     "pdd_destroy": (None, [_VP]),
     "pdd_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -201,6 +201,45 @@ class Context:
             res["steps"], res["discarded"] = int(dg.path_steps), int(dg.capped)
         return res
 
+    def mlmc_level(self, nodes, *, seed: int, dt0: float, level: int, n_paths: int,
+                   refine: int = 2, max_steps: int = 2**31 - 1, precision: str = "fp32",
+                   bridge: bool = True, dump_paths: bool = False, diag: bool = False) -> dict:
+        """pdd_mlmc_level: mean/var of P_l - P_{l-1} per node, fine and coarse means."""
+        nodes = _dev_f64(nodes, self.device).reshape(-1, int(self.prob["dim"]))
+        n = nodes.shape[0]
+        res = {k: torch.empty(n, dtype=_F64, device=self.device)
+               for k in ("mean", "var", "fine_mean", "coarse_mean")}
+        mp = _lib.MlmcParams(int(seed) & (2**64 - 1), int(n_paths), int(max_steps), float(dt0),
+                             int(level), int(refine), _lib.PRECISION[precision], int(bool(bridge)))
+        dg = None
+        if diag or dump_paths:
+            dg = _lib.Diag()
+            if dump_paths:
+                res["diff"] = torch.empty((n, int(n_paths)), dtype=_F64, device=self.device)
+                res["steps"] = torch.empty((n, int(n_paths)), dtype=_I32, device=self.device)
+                dg.d_path_score = res["diff"].data_ptr()
+                dg.d_path_steps = res["steps"].data_ptr()
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_mlmc_level(self.handle, nodes.data_ptr(), n, ctypes.byref(mp),
+                                         res["mean"].data_ptr(), res["var"].data_ptr(),
+                                         res["fine_mean"].data_ptr(), res["coarse_mean"].data_ptr(),
+                                         ctypes.byref(dg) if dg is not None else None)
+        res["status"] = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ECAP))
+        if dg is not None:
+            res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
+        return res
+
+    def mlmc_solve(self, nodes, *, seed: int, dt0: float, n_per_level, refine: int = 2,
+                   precision: str = "fp32", bridge: bool = True) -> dict:
+        """Multilevel estimate: sum of the level means, se = sqrt(sum var_l / N_l)."""
+        levels = [self.mlmc_level(nodes, seed=seed, dt0=dt0, level=l, n_paths=int(N),
+                                  refine=refine, precision=precision, bridge=bridge)
+                  for l, N in enumerate(n_per_level)]
+        mean = sum(L["mean"] for L in levels)
+        se = torch.sqrt(sum(L["var"] / float(N) for L, N in zip(levels, n_per_level)))
+        return {"mean": mean, "se": se, "levels": levels}
+
     def subdomain_solve(self, lo, hi, n, iface_axis: int, iface_side: int, iface_s, iface_vals,
                         *, method: str = "cg", max_iter: int = 100000, tol: float = 1e-12,
                         out=None) -> dict:

@@ -238,6 +238,14 @@ pdd_status pdd_branching_grid_solve(pdd_ctx *ctx, const double *d_nodes, int64_t
                                         diag);
 }
 
+pdd_status pdd_mlmc_level(pdd_ctx *ctx, const double *d_nodes, int64_t n, const pdd_mlmc_params *mp,
+                          double *d_mean, double *d_var, double *d_fine_mean, double *d_coarse_mean,
+                          pdd_diag *diag) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  return pdd::mlmc_level_impl(ctx, d_nodes, n, mp, d_mean, d_var, d_fine_mean, d_coarse_mean, diag);
+}
+
 pdd_status pdd_profile(pdd_ctx *ctx, int enable) {
   if (!ctx) return PDD_EINVAL;
   ctx->profiling = enable != 0;

@@ -161,6 +161,9 @@ pdd_status branching_grid_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_
 pdd_status reflect_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                               const pdd_mc_params *mc, double *d_mean, double *d_se,
                               int64_t *d_npaths, pdd_diag *diag);
+pdd_status mlmc_level_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n, const pdd_mlmc_params *mp,
+                           double *d_mean, double *d_var, double *d_fine, double *d_coarse,
+                           pdd_diag *diag);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

@@ -63,3 +63,4 @@ def test_struct_layouts(lib):
     assert ctypes.sizeof(lib.Subdomain) == 88
     assert ctypes.sizeof(lib.WosParams) == 48
     assert ctypes.sizeof(lib.GridBranchParams) == 48
+    assert ctypes.sizeof(lib.MlmcParams) == 48

@@ -1,0 +1,99 @@
+"""GPU parity of pdd_mlmc_level against the FP64 oracle on shared Philox
+streams: every coupled pair (fine path with dt_l, coarse path with dt_{l-1}
+on the summed fine increments) is compared one by one.  FP64 pairs agree to
+rounding; FP32 pairs may change an exit decision of either walk (counted,
+rare), and the node means over matched pairs agree to 1e-5 of the scores'
+scale."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_03666_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_03666_gb300 import api as a
+    assert torch.cuda.is_available()
+    return a
+
+
+def _pairs(api, orc, prob, nodes, precision, tol, flip_max, **kw):
+    o = orc.mlmc_level(prob, nodes, dump_paths=True, **kw)
+    kw_g = dict(kw)
+    kw_g["n_paths"] = kw_g.pop("n_paths")
+    with api.Context(prob) as ctx:
+        g = ctx.mlmc_level(torch.from_numpy(nodes), precision=precision, dump_paths=True, diag=True,
+                           **kw_g)
+    dg, sg = g["diff"].cpu().numpy(), g["steps"].cpu().numpy()
+    scale = np.maximum(1.0, np.abs(o["fine_mean"]))[:, None]
+    m = (sg == o["steps"]) & (np.abs(dg - o["diff"]) <= tol * scale)
+    flip = 1.0 - m.mean()
+    assert flip <= flip_max, flip
+    cnt = m.sum(1)
+    mg = np.where(m, dg, 0).sum(1) / cnt
+    mo = np.where(m, o["diff"], 0).sum(1) / cnt
+    assert np.all(np.abs(mg - mo) <= 1e-5 * scale[:, 0]), np.abs(mg - mo).max()
+    return g, o
+
+
+@pytest.mark.parametrize("level", [0, 1, 3])
+def test_fp64_pairs(api, orc, level):
+    prob = W.laplace_expcos()
+    g, o = _pairs(api, orc, prob, W.nodes_cfg1(6), "fp64", 1e-9, 1e-4, seed=W.SEED_BASE + 61,
+                  dt0=4e-3, level=level, n_paths=2000)
+    np.testing.assert_allclose(g["fine_mean"].cpu().numpy(), o["fine_mean"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(g["coarse_mean"].cpu().numpy(), o["coarse_mean"], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("level,refine", [(1, 2), (2, 4)])
+def test_fp32_pairs_laplace_and_lshape(api, orc, level, refine):
+    for geom, nodes in (("unit_square", W.nodes_cfg1(6)),
+                        ("l_shape", np.array([[0.25, 0.75], [0.4, 0.4], [0.75, 0.25]]))):
+        _pairs(api, orc, W.laplace_expcos(geom), nodes, "fp32", 1e-4, 4e-3, seed=W.SEED_BASE + 62,
+               dt0=4e-3, level=level, refine=refine, n_paths=3000)
+
+
+def test_fp32_pairs_poisson_fourier(api, orc):
+    w = W.workload(5)
+    _pairs(api, orc, w["prob"], w["nodes"][::256], "fp32", 1e-4, 4e-3, seed=W.SEED_BASE + 63,
+           dt0=4e-3, level=2, n_paths=2000)
+
+
+def test_mlmc_solve_at_size(api):
+    """16 nodes, four levels (dt 4e-3 .. 5e-4), 4e5 .. 5e4 pairs: the
+    harmonic solution within 4.5 sigma plus the finest level's O(dt) bias."""
+    nodes = W.nodes_cfg1(16)
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.mlmc_solve(torch.from_numpy(nodes), seed=W.SEED_BASE + 64, dt0=4e-3,
+                           n_per_level=[400_000, 200_000, 100_000, 50_000])
+    exact = np.exp(nodes[:, 0]) * np.cos(nodes[:, 1])
+    m, se = r["mean"].cpu().numpy(), r["se"].cpu().numpy()
+    assert np.all(np.abs(m - exact) <= 4.5 * se + 1e-3), (m - exact) / se
+    v = [L["var"].cpu().numpy() for L in r["levels"]]
+    # the difference variances are far below the single-level variance (less
+    # so at the nodes next to the boundary, whose scores vary least) and decay
+    assert np.median(v[1] / v[0]) < 0.2 and np.all(v[1] < 0.5 * v[0])
+    assert np.all(v[3] < v[1])
+
+
+def test_edge_cases(api):
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.mlmc_level(torch.zeros(0, 2), seed=1, dt0=1e-3, level=1, n_paths=4)
+        assert r["mean"].numel() == 0
+        b = torch.tensor([[0.0, 0.3]])
+        r0 = ctx.mlmc_level(b, seed=1, dt0=1e-3, level=0, n_paths=8)
+        r1 = ctx.mlmc_level(b, seed=1, dt0=1e-3, level=2, n_paths=8)
+        assert abs(r0["mean"].item() - np.cos(0.3)) < 1e-6 and r1["mean"].item() == 0.0
+        for bad in (dict(level=13), dict(refine=1), dict(dt0=0.1), dict(n_paths=0)):
+            kw = dict(seed=1, dt0=1e-3, level=1, n_paths=4)
+            kw.update(bad)
+            with pytest.raises(Exception):
+                ctx.mlmc_level(torch.tensor([[0.5, 0.5]]), **kw)
+    with api.Context(W.elliptic_manufactured()) as ctx:
+        with pytest.raises(Exception):
+            ctx.mlmc_level(torch.tensor([[0.5, 0.5, 0.5]]), seed=1, dt0=1e-3, level=1, n_paths=4)
