@@ -57,10 +57,14 @@ struct PathArgs {
 template <typename R> struct StepConst;
 template <> struct StepConst<float> {
   float dt, sdt, thr, l2cdt, inv_s2dt;
+  float b2;  // -2 log2(e) / (sigma^2 dt): exp(-2 m / (sigma^2 dt)) = 2^(b2 m)
   StepConst() = default;
   __device__ __forceinline__ StepConst(const PathArgs &a)
       : dt(a.dt_f), sdt(a.sdt_f), thr(a.thr_f), l2cdt(a.l2cdt_f),
-        inv_s2dt(static_cast<float>(a.inv_s2dt)) {}
+        inv_s2dt(static_cast<float>(a.inv_s2dt)),
+        b2(static_cast<float>(-2.0 * 1.4426950408889634 * a.inv_s2dt)) {}
+  // half-space crossing probability for a step with d d' = m
+  __device__ __forceinline__ float cross_p(float m) const { return ex2_approx(b2 * m); }
   __device__ __forceinline__ float kill(float, int32_t n_next) const {
     return ex2_approx(static_cast<float>(n_next) * l2cdt);
   }
@@ -76,6 +80,7 @@ template <> struct StepConst<double> {
       : dt(a.dt_d), sdt(a.sdt_d), thr(a.thr_d), e(a.ecdt_d), inv_s2dt(a.inv_s2dt) {}
   __device__ __forceinline__ double kill(double y, int32_t) const { return y * e; }
   __device__ __forceinline__ double exp_neg(double a) const { return exp(-a); }
+  __device__ __forceinline__ double cross_p(double m) const { return exp(-2.0 * m * inv_s2dt); }
 };
 
 // FP32 step constants for time step dt, generator (1/2) sigma^2 Lap and a
@@ -88,6 +93,7 @@ __device__ __forceinline__ StepConst<float> make_step_const(double dt, double si
   k.thr = static_cast<float>(9.0 * sigma * sigma * dt);
   k.l2cdt = static_cast<float>(c * dt * 1.4426950408889634);
   k.inv_s2dt = static_cast<float>(1.0 / (sigma * sigma * dt));
+  k.b2 = static_cast<float>(-2.0 * 1.4426950408889634 / (sigma * sigma * dt));
   return k;
 }
 
@@ -233,7 +239,7 @@ __device__ __forceinline__ int em_step(const Env &a, const StepConst<R> &k, R *X
         Geom::screen(X, Xn, prod, face);
         cross = bridge_exit<D, R>(k, prod, face, U) >= 0;
       } else {
-        const R p = k.exp_neg(R(2) * mn * k.inv_s2dt);
+        const R p = k.cross_p(mn);
         cross = U < p;
         if constexpr (sizeof(R) == 4) {
           if (fabsf(U - p) <= 3.814697265625e-06f * p) cross = bridge_tie_fp64(U, mn, k.inv_s2dt);
