@@ -16,6 +16,12 @@ Parity status per function (what pins it is listed in the tests):
   interface_jacobian pinned (linearity in theta; CRN finite differences)
   branching_solve    pinned (ODE closed forms, travelling wave, CN solve)
   wos_solve          pinned (harmonic data, O(eps) bias, boundary nodes)
+  branching_grid_solve pinned (KPP ODE with matching boundary data, travelling
+                     wave, heat mode, bridge bias, marked law at every T_i)
+  mlmc_level         pinned (harmonic telescoping sum, coarse = previous
+                     level's law under a biased dt, level 0, variance decay)
+  interface_solve with reflecting faces pinned (1-D Neumann/Robin torsion,
+                     harmonic data with Neumann/Robin faces, 3-D Robin)
   spline_interface   pinned (reproduces cubics exactly; library routine)
   subdomain_solve    pinned (dense solve, exact harmonic at O(h^2))
 """

@@ -27,7 +27,15 @@
  *     Sec. 3.2;
  *   - the likelihood-ratio derivative of the discrete scheme with respect to
  *     drift parameters, and the exact pathwise derivative with respect to
- *     linear boundary-data parameters.
+ *     linear boundary-data parameters;
+ *   - reflecting (Neumann/Robin) faces of the mixed problem Eq. 2.4 through
+ *     the local-time terms of Eq. 2.9 (Lepingle's half-space reflection);
+ *   - Walk on Spheres for the Laplace problem (the scheme Sec. 2.1 names for
+ *     stopped Brownian motion);
+ *   - branching trees on a time grid (Algorithm 3.1's time-point sharing),
+ *     in free space or with absorbing boundaries (Eq. 3.2);
+ *   - one level of the multilevel estimator (Giles' method, Sec. 2.1) with
+ *     coupled fine/coarse Euler paths.
  *
  * Readings where the paper is silent (exit point, bridge formula, left-point
  * quadrature, stream layout, tree ordering) are listed in the design notes and
