@@ -38,12 +38,14 @@ __global__ void batch_pilot_setup(int64_t n, int64_t n_pilot, int32_t K, int64_t
 
 // Per node: merge the pilot chunk partials (fixed order) into (n, mean, M2),
 // choose N_i and write the main work list's per-node entries.
-__global__ void batch_pilot_stats(int64_t n, int64_t n_pilot, int32_t K, const ChunkPartial *part,
-                                  double inv_se2, int64_t n_min, int64_t n_max, NodeAcc *pilot,
-                                  int64_t *first2, int64_t *end2, double *shift2, int64_t *count2) {
+// Kp: paths per pilot chunk; K: paths per main-pass chunk.
+__global__ void batch_pilot_stats(int64_t n, int64_t n_pilot, int32_t Kp, int32_t K,
+                                  const ChunkPartial *part, double inv_se2, int64_t n_min,
+                                  int64_t n_max, NodeAcc *pilot, int64_t *first2, int64_t *end2,
+                                  double *shift2, int64_t *count2) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
-  const int64_t cpn = (n_pilot + K - 1) / K;
+  const int64_t cpn = (n_pilot + Kp - 1) / Kp;
   double nt = 0.0, mean = 0.0, m2 = 0.0;
   for (int64_t c = 0; c < cpn; ++c) {
     const ChunkPartial P = part[i * cpn + c];
@@ -142,7 +144,7 @@ struct BatchLayout {
   int64_t pilot_chunks, main_chunks_max;
 };
 
-BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K) {
+BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K, int32_t Kp) {
   BatchLayout L;
   size_t o = 256;
   auto take = [&](size_t bytes) {
@@ -161,7 +163,7 @@ BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K) {
   L.off_cnt2 = take(nn * 8);
   L.off_chunk2 = take((nn + 1) * 8);
   L.off_pilot = take(nn * sizeof(NodeAcc));
-  L.pilot_chunks = n * ((bp->n_pilot + K - 1) / K);
+  L.pilot_chunks = n * ((bp->n_pilot + Kp - 1) / Kp);
   const int64_t extra = std::max<int64_t>(0, bp->n_max - bp->n_pilot);
   L.main_chunks_max = n * ((extra + K - 1) / K);
   L.off_part = take(static_cast<size_t>(L.pilot_chunks) * sizeof(ChunkPartial));
@@ -175,7 +177,7 @@ BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K) {
 
 static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const BatchLayout &Lay,
                                 const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
-                                int32_t K, unsigned grid, double *d_mean, double *d_se,
+                                int32_t K, int32_t Kp, unsigned grid, double *d_mean, double *d_se,
                                 int64_t *d_npaths) {
   char *base = static_cast<char *>(ctx->scratch);
   auto *counters = reinterpret_cast<unsigned long long *>(base);
@@ -196,8 +198,9 @@ static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const Batc
   const unsigned nb = static_cast<unsigned>((n + 255) / 256);
 
   PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, 256, ctx->stream));
-  batch_pilot_setup<<<nb + 1, 256, 0, ctx->stream>>>(n, bp->n_pilot, K, chunk, first, end, shift);
+  batch_pilot_setup<<<nb + 1, 256, 0, ctx->stream>>>(n, bp->n_pilot, Kp, chunk, first, end, shift);
   BatchArgs a = proto;
+  a.K = Kp;
   a.chunk_off = chunk;
   a.first = first;
   a.end = end;
@@ -206,12 +209,13 @@ static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const Batc
   a.counters = counters;
   a.partial = part;
   batch_kernel<<<grid, kBatchBlock, 0, ctx->stream>>>(a);
-  batch_pilot_stats<<<nb, 256, 0, ctx->stream>>>(n, bp->n_pilot, K, part,
+  batch_pilot_stats<<<nb, 256, 0, ctx->stream>>>(n, bp->n_pilot, Kp, K, part,
                                                  1.0 / (bp->target_se * bp->target_se),
                                                  bp->n_min, bp->n_max, pilot, first2, end2, shift2,
                                                  cnt2);
   batch_scan<<<1, kScanBlock, 0, ctx->stream>>>(n, cnt2, chunk2);
   PDD_CUDA_TRY(ctx, cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), ctx->stream));
+  a.K = K;
   a.chunk_off = chunk2;
   a.first = first2;
   a.end = end2;
@@ -284,17 +288,22 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
   }
   if (nodes->n == 0) return PDD_OK;
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  const BatchLayout Lay = batch_layout(nodes->n, bp, K);
-  pdd_status st = ensure_scratch(ctx, Lay.total);
-  if (st != PDD_OK) return st;
   int bps = 0;
   PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel, kBatchBlock, 0));
   if (bps < 1) bps = 1;
   if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
   const unsigned grid = static_cast<unsigned>(bps * ctx->num_sms);
+  // pilot chunks: the pilot is small (n_pilot paths per node), and chunks of
+  // K paths could leave lanes without work; aim at >= 8 chunks per lane
+  const double pilot_paths = static_cast<double>(nodes->n) * static_cast<double>(bp->n_pilot);
+  const double per_lane = pilot_paths / (8.0 * grid * kBatchBlock);
+  const int32_t Kp = static_cast<int32_t>(std::max(1.0, std::min<double>(K, std::floor(per_lane))));
+  const BatchLayout Lay = batch_layout(nodes->n, bp, K, Kp);
+  pdd_status st = ensure_scratch(ctx, Lay.total);
+  if (st != PDD_OK) return st;
 
   if (!use_graph) {
-    st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, grid, d_mean, d_se, d_npaths);
+    st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, Kp, grid, d_mean, d_se, d_npaths);
     if (st != PDD_OK) return st;
   } else {
     if (!ctx->stream) return fail(ctx, PDD_EINVAL, "graph capture needs a non-default stream");
@@ -320,7 +329,7 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
       const bool prof = ctx->profiling;
       ctx->profiling = false;  // no event records inside the capture
       PDD_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, grid, d_mean, d_se, d_npaths);
+      st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, Kp, grid, d_mean, d_se, d_npaths);
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
       ctx->profiling = prof;

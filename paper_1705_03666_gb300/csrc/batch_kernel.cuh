@@ -14,6 +14,7 @@
 #pragma once
 
 #include "path_kernel.cuh"
+#include "reduce.cuh"
 
 namespace pdd {
 
@@ -127,7 +128,13 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
   uint32_t node = 0;
   int64_t path = 0, path_end = 0;
   uint64_t chunk = 0;
-  double shift = 0.0, s1 = 0.0, s2 = 0.0, cnt = 0.0;
+  // per-chunk sums of (s - K_i) and its square as two-float values on the
+  // FP32 pipe (FP64 adds per path, at 1/64 rate in divergent code, were a
+  // visible cost); the chunk partial is written in FP64
+  float shift_f = 0.f;
+  double shift = 0.0;
+  F2Sum s1, s2;
+  int32_t cnt = 0;
   bool active = false, need = true;
   unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
 
@@ -161,7 +168,10 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
           const double dtd = a.dt[lo];
           k = make_step_const(dtd, P.sigma, P.c_kill);
           shift = a.shift ? a.shift[lo] : 0.0;
-          s1 = s2 = cnt = 0.0;
+          shift_f = static_cast<float>(shift);
+          s1 = F2Sum();
+          s2 = F2Sum();
+          cnt = 0;
           L.X[0] = static_cast<float>(a.nodes[lo * 3 + 0]);
           L.X[1] = static_cast<float>(a.nodes[lo * 3 + 1]);
           L.X[2] = static_cast<float>(a.nodes[lo * 3 + 2]);
@@ -173,8 +183,8 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
             PDD_BATCH_DISPATCH(combo, gv = M::g(P.mc, L.X));
             double v = closed ? static_cast<double>(gv) - shift : static_cast<double>(NAN);
             if (!closed) ++my_bad;
-            cnt = static_cast<double>(path_end - path);
-            a.partial[chunk] = ChunkPartial{cnt, cnt * v, cnt * v * v};
+            const double c = static_cast<double>(path_end - path);
+            a.partial[chunk] = ChunkPartial{c, c * v, c * v * v};
             need = true;
           } else {
             L.Y = 1.f;
@@ -200,10 +210,17 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
       done = true;
     }
     if (done) {
-      const double v = static_cast<double>(s) - shift;
-      s1 += v;
-      s2 = fma(v, v, s2);
-      cnt += 1.0;
+      // s - shift_f split exactly into two floats (the shift is rounded to
+      // FP32 once per chunk; the FP64 partial corrects for shift - shift_f)
+      const float d = s - shift_f;
+      const float bb = d - s;
+      const float dl = (s - (d - bb)) + (-shift_f - bb);
+      s1.add(d);
+      s1.lo += dl;
+      const float q = d * d;
+      s2.add(q);
+      s2.lo += fmaf(d, d, -q) + 2.0f * d * dl;
+      ++cnt;
       my_steps += static_cast<unsigned long long>(L.n);
       ++path;
       if (path < path_end) {
@@ -215,7 +232,13 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
         L.n = 0;
         L.pp = philox_path(static_cast<uint32_t>(path), node, 0u, a.rk);
       } else {
-        a.partial[chunk] = ChunkPartial{cnt, s1, s2};
+        // sums of v = s - shift_f; with e = shift - shift_f the partial holds
+        // sum (v - e) = S1 - n e and sum (v - e)^2 = S2 - 2 e S1 + n e^2
+        const double n_d = static_cast<double>(cnt);
+        const double S1 = static_cast<double>(s1.hi) + static_cast<double>(s1.lo);
+        const double S2 = static_cast<double>(s2.hi) + static_cast<double>(s2.lo);
+        const double e = shift - static_cast<double>(shift_f);
+        a.partial[chunk] = ChunkPartial{n_d, S1 - n_d * e, S2 - 2.0 * e * S1 + n_d * e * e};
         active = false;
         need = true;
       }
