@@ -290,6 +290,11 @@ void pdd_destroy(pdd_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
+  for (int k = 0; k < 3; ++k) {
+    if (ctx->batch_side[k]) cudaStreamDestroy(ctx->batch_side[k]);
+    if (ctx->batch_join[k]) cudaEventDestroy(ctx->batch_join[k]);
+  }
+  if (ctx->batch_fork) cudaEventDestroy(ctx->batch_fork);
   for (auto &e : ctx->prof_events) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);

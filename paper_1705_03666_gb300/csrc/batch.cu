@@ -2,6 +2,8 @@
 // heterogeneous batch of nodes, as one device-driven pipeline that can be
 // captured once in a CUDA graph and replayed.
 //
+//   0. the nodes are grouped by domain/family (stable partition on the
+//      device); chunk lists follow that order, one kernel per family;
 //   1. pilot: n_pilot paths per node (lane-chunk queue, batch_kernel);
 //   2. per node: pilot mean and variance s^2, path count
 //      N_i = clamp(ceil(s^2 / SE*^2), max(n_min, n_pilot), n_max);
@@ -21,6 +23,56 @@ namespace pdd {
 
 constexpr int kScanBlock = 1024;
 
+// Stable partition of the nodes by family: perm[j] is the node at position j,
+// family c holds positions [cstart[c], cstart[c+1]) (c = 0..3); nodes whose
+// problem index is out of range go to the end, [cstart[4], n), which no
+// kernel processes (their results are NaN, counted as bad nodes).
+// One block; each thread takes a contiguous segment of nodes, so the order
+// within a family is the node order.
+__global__ void __launch_bounds__(kScanBlock)
+batch_partition(int64_t n, const int32_t *prob, int32_t n_probs, int4 combo_of_prob,
+                int32_t *perm, int64_t *cstart, unsigned long long *bad) {
+  __shared__ int64_t part[kScanBlock];
+  __shared__ int64_t base;
+  const int cp[4] = {combo_of_prob.x, combo_of_prob.y, combo_of_prob.z, combo_of_prob.w};
+  const int64_t per = (n + kScanBlock - 1) / kScanBlock;
+  const int64_t b = threadIdx.x * per, e = min(n, b + per);
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c = 0; c <= 4; ++c) {
+    int64_t cnt = 0;
+    for (int64_t i = b; i < e; ++i) {
+      const int32_t pi = prob[i];
+      const int ci = (pi >= 0 && pi < n_probs) ? cp[pi] : 4;
+      cnt += ci == c;
+    }
+    part[threadIdx.x] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      cstart[c] = base;
+      int64_t acc = base;
+      for (int t = 0; t < kScanBlock; ++t) {
+        const int64_t v = part[t];
+        part[t] = acc;
+        acc += v;
+      }
+      base = acc;
+      if (c == 4) {
+        cstart[5] = acc;
+        if (acc > cstart[4]) atomicAdd(bad, static_cast<unsigned long long>(acc - cstart[4]));
+      }
+    }
+    __syncthreads();
+    int64_t pos = part[threadIdx.x];
+    for (int64_t i = b; i < e; ++i) {
+      const int32_t pi = prob[i];
+      const int ci = (pi >= 0 && pi < n_probs) ? cp[pi] : 4;
+      if (ci == c) perm[pos++] = static_cast<int32_t>(i);
+    }
+    __syncthreads();
+  }
+}
+
 // Pilot work list: every node gets paths [0, n_pilot).
 __global__ void batch_pilot_setup(int64_t n, int64_t n_pilot, int32_t K, int64_t *chunk_off,
                                   int64_t *first, int64_t *end, double *shift) {
@@ -38,17 +90,29 @@ __global__ void batch_pilot_setup(int64_t n, int64_t n_pilot, int32_t K, int64_t
 
 // Per node: merge the pilot chunk partials (fixed order) into (n, mean, M2),
 // choose N_i and write the main work list's per-node entries.
-// Kp: paths per pilot chunk; K: paths per main-pass chunk.
+// Kp: paths per pilot chunk; K: paths per main-pass chunk.  Runs over
+// positions j (node i = perm[j]): the pilot chunks of position j are
+// [j cpn, (j + 1) cpn); count2 is written by position (the main scan's order)
+// and the other outputs by node.  Positions of invalid nodes get no chunks.
 __global__ void batch_pilot_stats(int64_t n, int64_t n_pilot, int32_t Kp, int32_t K,
+                                  const int32_t *perm, const int64_t *cstart,
                                   const ChunkPartial *part, double inv_se2, int64_t n_min,
                                   int64_t n_max, NodeAcc *pilot, int64_t *first2, int64_t *end2,
                                   double *shift2, int64_t *count2) {
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
+  const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (j >= n) return;
+  const int64_t i = perm[j];
+  if (j >= cstart[4]) {
+    pilot[i] = NodeAcc{0.0, 0.0, 0.0};
+    first2[i] = end2[i] = n_pilot;
+    shift2[i] = 0.0;
+    count2[j] = 0;
+    return;
+  }
   const int64_t cpn = (n_pilot + Kp - 1) / Kp;
   double nt = 0.0, mean = 0.0, m2 = 0.0;
   for (int64_t c = 0; c < cpn; ++c) {
-    const ChunkPartial P = part[i * cpn + c];
+    const ChunkPartial P = part[j * cpn + c];
     if (P.n <= 0.0) continue;
     const double mb = P.s1 / P.n;
     const double m2b = fmax(0.0, P.s2 - P.s1 * mb);
@@ -67,7 +131,7 @@ __global__ void batch_pilot_stats(int64_t n, int64_t n_pilot, int32_t Kp, int32_
   first2[i] = n_pilot;
   end2[i] = Ni;
   shift2[i] = mean;
-  count2[i] = (Ni - n_pilot + K - 1) / K;
+  count2[j] = (Ni - n_pilot + K - 1) / K;
 }
 
 // Exclusive scan of count[0..n) into off[0..n] (single block, fixed order).
@@ -99,15 +163,22 @@ batch_scan(int64_t n, const int64_t *count, int64_t *off) {
 
 // Per node: pilot triple merged with the main chunk partials (shifted by the
 // pilot mean) in chunk order; writes mean, standard error and path count.
-__global__ void batch_final(int64_t n, const NodeAcc *pilot, const int64_t *off2,
-                            const double *shift2, const ChunkPartial *part2, double *mean_out,
-                            double *se_out, int64_t *n_out) {
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
+__global__ void batch_final(int64_t n, const int32_t *perm, const int64_t *cstart,
+                            const NodeAcc *pilot, const int64_t *off2, const double *shift2,
+                            const ChunkPartial *part2, double *mean_out, double *se_out,
+                            int64_t *n_out) {
+  const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (j >= n) return;
+  const int64_t i = perm[j];
+  if (j >= cstart[4]) {  // problem index out of range
+    mean_out[i] = se_out[i] = static_cast<double>(NAN);
+    if (n_out) n_out[i] = 0;
+    return;
+  }
   const NodeAcc A = pilot[i];
   double nt = A.n, mean = A.mean, m2 = A.m2;
   const double K = shift2[i];
-  for (int64_t c = off2[i]; c < off2[i + 1]; ++c) {
+  for (int64_t c = off2[j]; c < off2[j + 1]; ++c) {
     const ChunkPartial P = part2[c];
     if (P.n <= 0.0) continue;
     const double mb_shift = P.s1 / P.n;
@@ -140,7 +211,7 @@ int combo_of(const pdd_problem &p) {
 
 struct BatchLayout {
   size_t off_first, off_end, off_shift, off_chunk, off_first2, off_end2, off_shift2, off_cnt2,
-      off_chunk2, off_pilot, off_part, off_part2, total;
+      off_chunk2, off_pilot, off_perm, off_cstart, off_part, off_part2, total;
   int64_t pilot_chunks, main_chunks_max;
 };
 
@@ -163,6 +234,8 @@ BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K, int32
   L.off_cnt2 = take(nn * 8);
   L.off_chunk2 = take((nn + 1) * 8);
   L.off_pilot = take(nn * sizeof(NodeAcc));
+  L.off_perm = take(nn * sizeof(int32_t));
+  L.off_cstart = take(8 * sizeof(int64_t));
   L.pilot_chunks = n * ((bp->n_pilot + Kp - 1) / Kp);
   const int64_t extra = std::max<int64_t>(0, bp->n_max - bp->n_pilot);
   L.main_chunks_max = n * ((extra + K - 1) / K);
@@ -175,13 +248,63 @@ BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K, int32
 
 }  // namespace
 
+// One launch of each present family's kernel over its chunk range.  The
+// first family runs on the context's stream, the others on side streams
+// forked from it and joined back (event record / wait, which stream capture
+// records as graph dependencies), so the families' kernels overlap and the
+// tail of one (lanes idle while its last chunks finish) is filled by another.
+static pdd_status launch_families(pdd_ctx *ctx, const BatchArgs &a, const unsigned *grid) {
+  int launched = 0;
+  for (int c = 0; c < 4; ++c) {
+    if (!grid[c]) continue;
+    cudaStream_t s = ctx->stream;
+    if (launched > 0) {  // side stream launched - 1
+      if (launched == 1) PDD_CUDA_TRY(ctx, cudaEventRecord(ctx->batch_fork, ctx->stream));
+      s = ctx->batch_side[launched - 1];
+      PDD_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->batch_fork, 0));
+    }
+    switch (c) {
+      case kComboSquareLaplace:
+        batch_kernel<kComboSquareLaplace><<<grid[c], kBatchBlock, 0, s>>>(a);
+        break;
+      case kComboLShapeLaplace:
+        batch_kernel<kComboLShapeLaplace><<<grid[c], kBatchBlock, 0, s>>>(a);
+        break;
+      case kComboCubeElliptic:
+        batch_kernel<kComboCubeElliptic><<<grid[c], kBatchBlock, 0, s>>>(a);
+        break;
+      default:
+        batch_kernel<kComboSquarePoisson><<<grid[c], kBatchBlock, 0, s>>>(a);
+        break;
+    }
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
+    if (launched > 0) {
+      PDD_CUDA_TRY(ctx, cudaEventRecord(ctx->batch_join[launched - 1], s));
+      PDD_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->batch_join[launched - 1], 0));
+    }
+    ++launched;
+  }
+  return PDD_OK;
+}
+
+// Side streams and events for launch_families (created once per context).
+static pdd_status ensure_side_streams(pdd_ctx *ctx) {
+  if (ctx->batch_fork) return PDD_OK;
+  for (int k = 0; k < 3; ++k) {
+    PDD_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->batch_side[k], cudaStreamNonBlocking));
+    PDD_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->batch_join[k], cudaEventDisableTiming));
+  }
+  PDD_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->batch_fork, cudaEventDisableTiming));
+  return PDD_OK;
+}
+
 static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const BatchLayout &Lay,
                                 const pdd_batch_nodes *nodes, const pdd_batch_params *bp,
-                                int32_t K, int32_t Kp, unsigned grid, double *d_mean, double *d_se,
+                                int32_t K, int32_t Kp, const unsigned *grid, int4 combo_of_prob,
+                                int32_t n_probs, double *d_mean, double *d_se,
                                 int64_t *d_npaths) {
   char *base = static_cast<char *>(ctx->scratch);
   auto *counters = reinterpret_cast<unsigned long long *>(base);
-  auto *cursor = counters + 4;
   auto *first = reinterpret_cast<int64_t *>(base + Lay.off_first);
   auto *end = reinterpret_cast<int64_t *>(base + Lay.off_end);
   auto *shift = reinterpret_cast<double *>(base + Lay.off_shift);
@@ -192,29 +315,37 @@ static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const Batc
   auto *cnt2 = reinterpret_cast<int64_t *>(base + Lay.off_cnt2);
   auto *chunk2 = reinterpret_cast<int64_t *>(base + Lay.off_chunk2);
   auto *pilot = reinterpret_cast<NodeAcc *>(base + Lay.off_pilot);
+  auto *perm = reinterpret_cast<int32_t *>(base + Lay.off_perm);
+  auto *cstart = reinterpret_cast<int64_t *>(base + Lay.off_cstart);
+  auto *cursors = counters + 8;  // one per family
   auto *part = reinterpret_cast<ChunkPartial *>(base + Lay.off_part);
   auto *part2 = reinterpret_cast<ChunkPartial *>(base + Lay.off_part2);
   const int64_t n = nodes->n;
   const unsigned nb = static_cast<unsigned>((n + 255) / 256);
 
   PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, 256, ctx->stream));
+  batch_partition<<<1, kScanBlock, 0, ctx->stream>>>(n, nodes->d_problem, n_probs, combo_of_prob,
+                                                     perm, cstart, counters + 2);
   batch_pilot_setup<<<nb + 1, 256, 0, ctx->stream>>>(n, bp->n_pilot, Kp, chunk, first, end, shift);
   BatchArgs a = proto;
+  a.perm = perm;
+  a.cstart = cstart;
   a.K = Kp;
   a.chunk_off = chunk;
   a.first = first;
   a.end = end;
   a.shift = shift;
-  a.cursor = cursor;
+  a.cursor = cursors;
   a.counters = counters;
   a.partial = part;
-  batch_kernel<<<grid, kBatchBlock, 0, ctx->stream>>>(a);
-  batch_pilot_stats<<<nb, 256, 0, ctx->stream>>>(n, bp->n_pilot, Kp, K, part,
+  pdd_status st = launch_families(ctx, a, grid);
+  if (st != PDD_OK) return st;
+  batch_pilot_stats<<<nb, 256, 0, ctx->stream>>>(n, bp->n_pilot, Kp, K, perm, cstart, part,
                                                  1.0 / (bp->target_se * bp->target_se),
                                                  bp->n_min, bp->n_max, pilot, first2, end2, shift2,
                                                  cnt2);
   batch_scan<<<1, kScanBlock, 0, ctx->stream>>>(n, cnt2, chunk2);
-  PDD_CUDA_TRY(ctx, cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), ctx->stream));
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(cursors, 0, 4 * sizeof(unsigned long long), ctx->stream));
   a.K = K;
   a.chunk_off = chunk2;
   a.first = first2;
@@ -223,10 +354,11 @@ static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const Batc
   a.partial = part2;
   const auto ev = prof_slot(ctx);
   if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
-  batch_kernel<<<grid, kBatchBlock, 0, ctx->stream>>>(a);
+  st = launch_families(ctx, a, grid);
+  if (st != PDD_OK) return st;
   if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
-  batch_final<<<nb, 256, 0, ctx->stream>>>(n, pilot, chunk2, shift2, part2, d_mean, d_se,
-                                           d_npaths);
+  batch_final<<<nb, 256, 0, ctx->stream>>>(n, perm, cstart, pilot, chunk2, shift2, part2, d_mean,
+                                           d_se, d_npaths);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
   return PDD_OK;
 }
@@ -288,22 +420,41 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
   }
   if (nodes->n == 0) return PDD_OK;
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  int bps = 0;
-  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel, kBatchBlock, 0));
-  if (bps < 1) bps = 1;
-  if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
-  const unsigned grid = static_cast<unsigned>(bps * ctx->num_sms);
+  // one kernel per family present in the problem list, each sized by its own
+  // occupancy (0 = family absent)
+  unsigned grid[4] = {0, 0, 0, 0};
+  int cp[4] = {4, 4, 4, 4};
+  for (int p = 0; p < n_problems; ++p) {
+    const int c = proto.probs[p].combo;
+    cp[p] = c;
+    if (grid[c]) continue;
+    int bps = 0;
+    const void *fn = c == kComboSquareLaplace ? reinterpret_cast<const void *>(batch_kernel<kComboSquareLaplace>)
+                   : c == kComboLShapeLaplace ? reinterpret_cast<const void *>(batch_kernel<kComboLShapeLaplace>)
+                   : c == kComboCubeElliptic  ? reinterpret_cast<const void *>(batch_kernel<kComboCubeElliptic>)
+                                              : reinterpret_cast<const void *>(batch_kernel<kComboSquarePoisson>);
+    PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBatchBlock, 0));
+    if (bps < 1) bps = 1;
+    if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
+    grid[c] = static_cast<unsigned>(bps * ctx->num_sms);
+  }
+  const int4 combo_of_prob = make_int4(cp[0], cp[1], cp[2], cp[3]);
+  unsigned max_grid = 0;
+  for (int c = 0; c < 4; ++c) max_grid = std::max(max_grid, grid[c]);
   // pilot chunks: the pilot is small (n_pilot paths per node), and chunks of
   // K paths could leave lanes without work; aim at >= 8 chunks per lane
   const double pilot_paths = static_cast<double>(nodes->n) * static_cast<double>(bp->n_pilot);
-  const double per_lane = pilot_paths / (8.0 * grid * kBatchBlock);
+  const double per_lane = pilot_paths / (8.0 * max_grid * kBatchBlock);
   const int32_t Kp = static_cast<int32_t>(std::max(1.0, std::min<double>(K, std::floor(per_lane))));
   const BatchLayout Lay = batch_layout(nodes->n, bp, K, Kp);
   pdd_status st = ensure_scratch(ctx, Lay.total);
   if (st != PDD_OK) return st;
+  st = ensure_side_streams(ctx);
+  if (st != PDD_OK) return st;
 
   if (!use_graph) {
-    st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, Kp, grid, d_mean, d_se, d_npaths);
+    st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, Kp, grid, combo_of_prob, n_problems,
+                       d_mean, d_se, d_npaths);
     if (st != PDD_OK) return st;
   } else {
     if (!ctx->stream) return fail(ctx, PDD_EINVAL, "graph capture needs a non-default stream");
@@ -315,7 +466,7 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
     key.out[1] = d_se;
     key.out[2] = d_npaths;
     key.scratch = ctx->scratch;
-    key.grid = grid;
+    for (int c = 0; c < 4; ++c) key.grid[c] = grid[c];
     key.K = K;
     key.probs_hash = 0;
     const unsigned char *pb = reinterpret_cast<const unsigned char *>(proto.probs);
@@ -329,7 +480,8 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
       const bool prof = ctx->profiling;
       ctx->profiling = false;  // no event records inside the capture
       PDD_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, Kp, grid, d_mean, d_se, d_npaths);
+      st = enqueue_batch(ctx, proto, Lay, nodes, bp, K, Kp, grid, combo_of_prob, n_problems,
+                       d_mean, d_se, d_npaths);
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
       ctx->profiling = prof;

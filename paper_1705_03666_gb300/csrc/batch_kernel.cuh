@@ -4,13 +4,20 @@
 //
 // The unit of queued work is a lane-chunk: up to K consecutive paths of one
 // node, run one after the other by a single lane, which accumulates their
-// shifted scores (s - K_i), squares and step counts in registers (FP64 sums)
-// and writes one partial per chunk.  A lane that finishes its chunk takes the
-// next chunk from a warp-aggregated global cursor, so lanes never wait for one
-// another; partials are indexed by chunk, so the per-node merge (fixed order)
-// does not depend on scheduling.  Chunk counts may live in device memory, so
-// a launch sized on the host can consume a work list produced on the device
-// (the adaptive pass), and the whole pipeline can be captured in a CUDA graph.
+// shifted scores (s - K_i) and squares in registers and writes one partial
+// per chunk.  A lane that finishes its chunk takes the next chunk from a
+// warp-aggregated cursor, so lanes never wait for one another; partials are
+// indexed by chunk, so the per-node merge (fixed order) does not depend on
+// scheduling.  Chunk counts may live in device memory, so a launch sized on
+// the host can consume a work list produced on the device (the adaptive
+// pass), and the whole pipeline can be captured in a CUDA graph.
+//
+// The nodes are grouped by domain/family (a stable partition built on the
+// device, `perm`), the chunk list follows that order, and each family runs
+// its own instantiation of the kernel over its own chunk range: a kernel
+// compiled for one family has the registers and the code of that family's
+// path unit only.  (One kernel dispatching on the family per lane ran at
+// about half the speed of the plain path kernel on the same paths.)
 #pragma once
 
 #include "path_kernel.cuh"
@@ -45,14 +52,19 @@ struct BatchArgs {
   const int32_t *prob;      // [n] index into probs
   const double *dt;         // [n]
   int64_t n;
-  // work list: node i owns chunks [chunk_off[i], chunk_off[i+1]) covering
-  // paths [first[i], end[i]) in pieces of K; chunk_off[n] = total chunks
+  // node order grouped by family: perm[j] is the node at position j; family c
+  // holds positions [cstart[c], cstart[c+1])
+  const int32_t *perm;
+  const int64_t *cstart;
+  // work list, in that order: the node at position j owns chunks
+  // [chunk_off[j], chunk_off[j+1]) covering paths [first[i], end[i]) of node
+  // i = perm[j] in pieces of K; chunk_off[n] = total chunks
   const int64_t *chunk_off;
   const int64_t *first;
   const int64_t *end;
   const double *shift;      // [n] per-node shift K_i of the sums
   int32_t K;
-  unsigned long long *cursor;
+  unsigned long long *cursor;  // [4]: one per family
   unsigned long long *counters;  // [0] path steps, [1] capped, [2] bad nodes
   ChunkPartial *partial;    // [chunk_off[n]]
   RoundKeys rk;
@@ -105,26 +117,30 @@ __device__ __forceinline__ bool batch_closed(const float *x) {
   return Geom::inside_closed(x);
 }
 
-#define PDD_BATCH_DISPATCH(combo, ...)                                                      \
-  switch (combo) {                                                                         \
-    case kComboSquareLaplace: { using M = LaplaceExpCos; using G = Box<2>; __VA_ARGS__; break; } \
-    case kComboLShapeLaplace: { using M = LaplaceExpCos; using G = LShape; __VA_ARGS__; break; } \
-    case kComboCubeElliptic: {                                                             \
-      using M = EllipticManufactured; using G = Box<3>; __VA_ARGS__; break;                 \
-    }                                                                                      \
-    default: { using M = PoissonFourier; using G = Box<2>; __VA_ARGS__; break; }           \
-  }
+template <int C> struct ComboTraits;
+template <> struct ComboTraits<kComboSquareLaplace> { using M = LaplaceExpCos; using G = Box<2>; };
+template <> struct ComboTraits<kComboLShapeLaplace> { using M = LaplaceExpCos; using G = LShape; };
+template <> struct ComboTraits<kComboCubeElliptic> { using M = EllipticManufactured; using G = Box<3>; };
+template <> struct ComboTraits<kComboSquarePoisson> { using M = PoissonFourier; using G = Box<2>; };
 
 constexpr int kBatchBlock = 256;
 
+template <int C>
 __global__ void __launch_bounds__(kBatchBlock)
 batch_kernel(const __grid_constant__ BatchArgs a) {
+  using M = typename ComboTraits<C>::M;
+  using G = typename ComboTraits<C>::G;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const uint64_t total = static_cast<uint64_t>(a.chunk_off[a.n]);
+  // this family's positions and chunks
+  const int64_t jlo = a.cstart[C], jhi = a.cstart[C + 1];
+  if (jlo >= jhi) return;
+  const uint64_t c_lo = static_cast<uint64_t>(a.chunk_off[jlo]);
+  const uint64_t c_hi = static_cast<uint64_t>(a.chunk_off[jhi]);
+  unsigned long long *cursor = a.cursor + C;
   BatchLane L;
   StepConst<float> k;
-  int32_t pi = 0, combo = 0;
+  int32_t pi = 0;
   uint32_t node = 0;
   int64_t path = 0, path_end = 0;
   uint64_t chunk = 0;
@@ -145,46 +161,43 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
       const int leader = __ffs(needmask) - 1;
       unsigned long long base = 0;
       if (static_cast<int>(lane) == leader)
-        base = atomicAdd(a.cursor, static_cast<unsigned long long>(__popc(needmask)));
+        base = atomicAdd(cursor, static_cast<unsigned long long>(__popc(needmask)));
       base = __shfl_sync(kFull, base, leader);
       if (need) {
         need = false;
-        const unsigned long long c = base + __popc(needmask & lt_mask);
-        if (c < total) {
+        const unsigned long long c = c_lo + base + __popc(needmask & lt_mask);
+        if (c < c_hi) {
           chunk = c;
-          // node owning chunk c: last i with chunk_off[i] <= c
-          int64_t lo = 0, hi = a.n;
+          // position owning chunk c: last j in [jlo, jhi) with chunk_off[j] <= c
+          int64_t lo = jlo, hi = jhi;
           while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
             if (static_cast<uint64_t>(a.chunk_off[mid]) <= c) lo = mid; else hi = mid;
           }
-          node = static_cast<uint32_t>(lo);
-          const int64_t j = static_cast<int64_t>(c) - a.chunk_off[lo];
-          path = a.first[lo] + j * a.K;
-          path_end = min(a.end[lo], path + a.K);
-          pi = a.prob[lo];
+          const int64_t i = a.perm[lo];
+          node = static_cast<uint32_t>(i);
+          const int64_t jj = static_cast<int64_t>(c) - a.chunk_off[lo];
+          path = a.first[i] + jj * a.K;
+          path_end = min(a.end[i], path + a.K);
+          pi = a.prob[i];
           const BatchProblem &P = a.probs[pi];
-          combo = P.combo;
-          const double dtd = a.dt[lo];
-          k = make_step_const(dtd, P.sigma, P.c_kill);
-          shift = a.shift ? a.shift[lo] : 0.0;
+          k = make_step_const(a.dt[i], P.sigma, P.c_kill);
+          shift = a.shift ? a.shift[i] : 0.0;
           shift_f = static_cast<float>(shift);
           s1 = F2Sum();
           s2 = F2Sum();
           cnt = 0;
-          L.X[0] = static_cast<float>(a.nodes[lo * 3 + 0]);
-          L.X[1] = static_cast<float>(a.nodes[lo * 3 + 1]);
-          L.X[2] = static_cast<float>(a.nodes[lo * 3 + 2]);
-          bool open = true, closed = true;
-          PDD_BATCH_DISPATCH(combo, open = batch_inside<M, G>(L.X); closed = batch_closed<M, G>(L.X));
-          if (!open) {
+          L.X[0] = static_cast<float>(a.nodes[i * 3 + 0]);
+          L.X[1] = static_cast<float>(a.nodes[i * 3 + 1]);
+          L.X[2] = static_cast<float>(a.nodes[i * 3 + 2]);
+          if (!batch_inside<M, G>(L.X)) {
             // node on (or, invalid, outside) the boundary: every path scores g
-            float gv = 0.f;
-            PDD_BATCH_DISPATCH(combo, gv = M::g(P.mc, L.X));
-            double v = closed ? static_cast<double>(gv) - shift : static_cast<double>(NAN);
+            const bool closed = batch_closed<M, G>(L.X);
+            const double v = closed ? static_cast<double>(M::g(P.mc, L.X)) - shift
+                                    : static_cast<double>(NAN);
             if (!closed) ++my_bad;
-            const double c = static_cast<double>(path_end - path);
-            a.partial[chunk] = ChunkPartial{c, c * v, c * v * v};
+            const double cn = static_cast<double>(path_end - path);
+            a.partial[chunk] = ChunkPartial{cn, cn * v, cn * v * v};
             need = true;
           } else {
             L.Y = 1.f;
@@ -202,10 +215,9 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
     const BatchProblem &P = a.probs[pi];
     const BatchEnv env{P.mc, P.bridge};
     float s = 0.f;
-    bool done = false;
-    PDD_BATCH_DISPATCH(combo, done = (batch_unit<M, G>(env, k, a.rk, a.max_steps, L, s)));
+    bool done = batch_unit<M, G>(env, k, a.rk, a.max_steps, L, s);
     if (!done && L.n >= a.max_steps) {
-      PDD_BATCH_DISPATCH(combo, s = batch_capped<M, G>(P.mc, L));
+      s = batch_capped<M, G>(P.mc, L);
       ++my_capped;
       done = true;
     }
@@ -257,6 +269,6 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
   }
 }
 
-#undef PDD_BATCH_DISPATCH
+
 
 }  // namespace pdd

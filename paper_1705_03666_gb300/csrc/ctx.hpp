@@ -19,7 +19,7 @@ struct BatchGraphKey {
   pdd_batch_params bp;
   void *out[3];
   void *scratch;
-  unsigned grid;
+  unsigned grid[4];
   int32_t K;
   unsigned long long probs_hash;
 };
@@ -43,6 +43,12 @@ struct pdd_ctx {
   int batch_chunk = 0;
   cudaGraphExec_t batch_graph = nullptr;
   BatchGraphKey batch_key{};
+  // batch solve: side streams and events that run the per-family kernels
+  // concurrently (forked from and joined back into `stream`); created on
+  // first use
+  cudaStream_t batch_side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t batch_fork = nullptr;
+  cudaEvent_t batch_join[3] = {nullptr, nullptr, nullptr};
   // kernel timing (pdd_profile): event pairs recorded around path launches
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
