@@ -187,25 +187,20 @@ struct Box {
     const R v = x[j >> 1];
     return (j & 1) ? R(1) - v : v;
   }
-  // Screening of a step X -> X' (X strictly inside).  Per axis k:
+  // Screening of a step X -> X' (X in the closed box).  Per axis k,
   //   m[k] = min(x_k x'_k, (1 - x_k)(1 - x'_k)), the d d' of the axis' face
   //          that can be within bridge reach (the other one cannot while
   //          sigma^2 dt <= 1/36);
-  //   min(x'_k, 1 - x'_k) >= 0 exactly when x'_k lies in [0, 1] (1 - x' is
-  //          exact near 1, so the sign is exact).
-  // Returns the smallest m in mn and the smallest min(x', 1 - x') in ins
-  // (ins < 0: X' is outside the closed box).
+  // mn = the smallest m[k].  mn > 0 puts X' strictly inside the box: with x_k
+  // in [0, 1], both products of an axis are positive only for x'_k in (0, 1)
+  // (a rounded product keeps its sign; an underflow to zero gives mn = 0).
   template <typename R>
-  __device__ __forceinline__ static void screen_min(const R *x0, const R *x1, R *m, R &mn,
-                                                    R &ins) {
+  __device__ __forceinline__ static void screen_min(const R *x0, const R *x1, R *m, R &mn) {
     mn = R(1);
-    ins = R(1);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const R o1 = R(1) - x1[k];
-      m[k] = fmin(x0[k] * x1[k], (R(1) - x0[k]) * o1);
+      m[k] = fmin(x0[k] * x1[k], (R(1) - x0[k]) * (R(1) - x1[k]));
       mn = fmin(mn, m[k]);
-      ins = fmin(ins, fmin(x1[k], o1));
     }
   }
   // Second smallest of m[0..D-1] (D <= 3): below the reach threshold means

@@ -2,9 +2,10 @@
 //
 // One persistent launch advances every (node, path) of a wave of the global,
 // node-major path index space g = node * n_paths + p.  Each lane owns one
-// path at a time; when its path exits the lane takes the next index from a
-// warp-aggregated atomic cursor, so no lane waits for a long path of another
-// node (lane refill) and the only idle time is at the very end of the wave.
+// path at a time; when its path exits the lane takes the next path from its
+// warp's stash of set-up paths (refilled 32 indices at a time from an atomic
+// cursor), so no lane waits for a long path of another node (lane refill) and
+// the only idle time is at the very end of the wave.
 // A path's score and exit step go to a per-path slot; a separate reduction
 // (reduce.cu) forms the per-node mean and standard error in a fixed order, so
 // the result does not depend on which lane ran which path.
@@ -65,6 +66,15 @@ template <> struct StepConst<float> {
         b2(static_cast<float>(-2.0 * 1.4426950408889634 * a.inv_s2dt)) {}
   // half-space crossing probability for a step with d d' = m
   __device__ __forceinline__ float cross_p(float m) const { return ex2_approx(b2 * m); }
+  // Bound on every crossing probability of a step whose smallest d d' over
+  // D candidate faces is m: 1 - prod_j (1 - p_j) <= D p(m), raised by the
+  // factor 2^(2^-12) = 1 + 1.7e-4, which covers the near-tie window (2^-18
+  // relative) and the rounding of the exponents (< 1e-5 relative for the
+  // probabilities above 2^-26 that a uniform can fall below).
+  template <int D> __device__ __forceinline__ float cross_bound(float m) const {
+    constexpr float kOff = (D == 1 ? 0.0f : D == 2 ? 1.0f : 1.5849625007211562f) + 2.44140625e-4f;
+    return ex2_approx(fmaf(b2, m, kOff));
+  }
   __device__ __forceinline__ float kill(float, int32_t n_next) const {
     return ex2_approx(static_cast<float>(n_next) * l2cdt);
   }
@@ -81,6 +91,9 @@ template <> struct StepConst<double> {
   __device__ __forceinline__ double kill(double y, int32_t) const { return y * e; }
   __device__ __forceinline__ double exp_neg(double a) const { return exp(-a); }
   __device__ __forceinline__ double cross_p(double m) const { return exp(-2.0 * m * inv_s2dt); }
+  template <int D> __device__ __forceinline__ double cross_bound(double m) const {
+    return static_cast<double>(D) * 1.0000001 * exp(-2.0 * m * inv_s2dt);
+  }
 };
 
 // FP32 step constants for time step dt, generator (1/2) sigma^2 Lap and a
@@ -224,37 +237,43 @@ __device__ __forceinline__ int em_step(const Env &a, const StepConst<R> &k, R *X
       if (jbest >= 0) return jbest;
     }
   } else {
-    R m[D], mn, ins;
-    Geom::screen_min(X, Xn, m, mn, ins);
-    if (ins < R(0)) return kStepHardExit;  // X' outside the closed box
-    // Bridge: the single-face probability exp(-2 min d d' / (sigma^2 dt)) is
-    // formed without a branch; a step within reach of two or more faces (an
-    // edge or a corner) takes the general combination.
+    R m[D], mn;
+    Geom::screen_min(X, Xn, m, mn);
+    // mn > 0: X' strictly inside; otherwise the exact test decides
+    if (!(mn > R(0)) && !Geom::inside_closed(Xn)) return kStepHardExit;
     if (a.bridge) {
       const R U = unif<R>(uw);
-      bool cross;
-      if (Geom::second_min(m) < k.thr) {
-        R prod[D];
-        int face[D];
-        Geom::screen(X, Xn, prod, face);
-        cross = bridge_exit<D, R>(k, prod, face, U) >= 0;
-      } else {
-        const R p = k.cross_p(mn);
-        cross = U < p;
-        if constexpr (sizeof(R) == 4) {
-          if (fabsf(U - p) <= 3.814697265625e-06f * p) cross = bridge_tie_fp64(U, mn, k.inv_s2dt);
+      // At most steps U lies above every crossing probability the step can
+      // have (and above its near-tie window): one bound decides that, and the
+      // probability itself is formed only below it.  A step within reach of
+      // one face crosses with exp(-2 min d d' / (sigma^2 dt)); a step within
+      // reach of two or more faces (an edge or a corner) takes the general
+      // combination.
+      if (U < k.template cross_bound<D>(mn)) {
+        bool cross;
+        if (Geom::second_min(m) < k.thr) {
+          R prod[D];
+          int face[D];
+          Geom::screen(X, Xn, prod, face);
+          cross = bridge_exit<D, R>(k, prod, face, U) >= 0;
+        } else {
+          const R p = k.cross_p(mn);
+          cross = U < p;
+          if constexpr (sizeof(R) == 4) {
+            if (fabsf(U - p) <= 3.814697265625e-06f * p) cross = bridge_tie_fp64(U, mn, k.inv_s2dt);
+          }
         }
-      }
-      if (cross) {
-        R prod[D];
-        int face[D];
-        Geom::screen(X, Xn, prod, face);
-        int jbest = face[0];
-        R pmin = prod[0];
+        if (cross) {
+          R prod[D];
+          int face[D];
+          Geom::screen(X, Xn, prod, face);
+          int jbest = face[0];
+          R pmin = prod[0];
 #pragma unroll
-        for (int d = 1; d < D; ++d)
-          if (prod[d] < pmin) { pmin = prod[d]; jbest = face[d]; }
-        return jbest;
+          for (int d = 1; d < D; ++d)
+            if (prod[d] < pmin) { pmin = prod[d]; jbest = face[d]; }
+          return jbest;
+        }
       }
     }
   }
@@ -291,13 +310,14 @@ __device__ __forceinline__ uint32_t low_bytes_word(uint32_t a, uint32_t b, uint3
 // 3q+1, 3q+2, formed as the steps need them: normals z0..z11 = BM of the word
 // pairs (w0,w1) .. (w10,w11), step 4q+j takes z[3j..3j+2] and the uniform of
 // low_bytes_word(w[3j], w[3j+1], w[3j+2]).  n counts the steps taken; the unit
-// stops at an exit (returns true, score in s) or at max_steps.
+// stops at an exit (returns its code, X the start and Xn the end of the
+// exiting step) or at max_steps (returns kStepContinue).
 template <class Model, class Geom, typename R, bool kLR, class Env>
-__device__ __forceinline__ bool path_unit(const Env &a, const StepConst<R> &k, const PhiloxPath &pp,
-                                          const RoundKeys &rk, int32_t max_steps, R *X, R &Y,
-                                          R &Z, int32_t &n, R &s, R *xe, R *L) {
+__device__ __forceinline__ int path_unit_code(const Env &a, const StepConst<R> &k,
+                                              const PhiloxPath &pp, const RoundKeys &rk,
+                                              int32_t max_steps, R *X, R &Y, R &Z, int32_t &n,
+                                              R *Xn, R *L) {
   constexpr int D = Model::D;
-  R Xn[D];
   int code;
   if constexpr (D == 3) {
     const uint32_t q3 = 3u * (static_cast<uint32_t>(n) >> 2);
@@ -335,6 +355,17 @@ __device__ __forceinline__ bool path_unit(const Env &a, const StepConst<R> &k, c
     code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, A.z, n, Xn, L);
     ++n;
   }
+  return code;
+}
+
+// path_unit_code followed, at an exit, by the path's score (returns true,
+// score in s, exit point in xe).
+template <class Model, class Geom, typename R, bool kLR, class Env>
+__device__ __forceinline__ bool path_unit(const Env &a, const StepConst<R> &k, const PhiloxPath &pp,
+                                          const RoundKeys &rk, int32_t max_steps, R *X, R &Y,
+                                          R &Z, int32_t &n, R &s, R *xe, R *L) {
+  R Xn[Model::D];
+  const int code = path_unit_code<Model, Geom, R, kLR>(a, k, pp, rk, max_steps, X, Y, Z, n, Xn, L);
   if (code == kStepContinue) return false;
   s = exit_score<Model, Geom, R>(a.mc, code, X, Xn, Y, Z, xe);
   return true;
@@ -368,96 +399,244 @@ __device__ __forceinline__ void write_result(const PathArgs &a, uint64_t slot, R
   if (a.steps) a.steps[slot] = st;
 }
 
+// Per-warp staging in shared memory (one column per lane).  Claiming and
+// setting up a path (atomic, node division, Philox key, FP64 node load) and
+// scoring an ended path (exit point, accurate g) happen once per path, at
+// times that differ from lane to lane: done where they occur, each would run
+// with one lane of the warp active.  Instead a warp claims 32 consecutive
+// paths at once and sets them all up with every lane busy (StartStash), and
+// ended paths are parked (ExitQueue) and scored 32 at a time.  Every path
+// writes its own slot, so the results do not depend on this order.
+template <int D, typename R>
+struct StartStash {
+  unsigned long long slot[32];  // index in the wave
+  uint32_t w0[32], w1[32];      // PhiloxPath words (tag 0)
+  R x[D][32];                   // start point
+};
+template <int D, typename R>
+struct ExitQueue {
+  unsigned long long slot[32];
+  int32_t st[32], code[32];     // step count (or -max_steps) and exit code
+  R x[D][32], xn[D][32], y[32], z[32];
+};
+template <int D, typename R, bool kQueue>
+struct PathStage {
+  StartStash<D, R> start;
+  ExitQueue<D, R> exit;
+};
+template <int D, typename R>
+struct PathStage<D, R, false> {
+  StartStash<D, R> start;
+};
+
+// Exit code of a path stopped by the step cap: scored at the projection of
+// its last point on the nearest face.
+constexpr int kStepCapped = -3;
+
+// Called by all 32 lanes: claim the next 32 indices of the wave, set each up,
+// score at once the ones that start on the boundary (tau = 0, u = g, Eq. 2.1)
+// or outside the closed domain (invalid input: NaN, counted), and stage the
+// interior ones.  Returns how many were staged (warp-uniform).
+template <class Model, class Geom, typename R, bool kLR>
+__device__ __forceinline__ int stage_starts(const PathArgs &a, StartStash<Model::D, R> &st,
+                                            unsigned long long span, bool &exhausted,
+                                            unsigned long long &my_bad) {
+  constexpr int D = Model::D;
+  const unsigned lane = threadIdx.x & 31u;
+  __syncwarp();  // earlier reads of the stash are done
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(a.cursor, 32ull);
+  base = __shfl_sync(kFull, base, 0);
+  if (base + 32 >= span) exhausted = true;
+  const unsigned long long q = base + lane;
+  bool interior = false;
+  R x[D];
+  PhiloxPath pp{0, 0, 0};
+  if (q < span) {
+    const unsigned long long g = a.begin + q;
+    uint64_t node;
+    if (a.end <= 0xffffffffull) {  // 32-bit division when the indices fit
+      node = static_cast<uint32_t>(g) / static_cast<uint32_t>(a.n_paths);
+    } else {
+      node = g / a.n_paths;
+    }
+    const uint64_t path = g - node * a.n_paths + a.path_offset;
+    pp = philox_path(static_cast<uint32_t>(path), static_cast<uint32_t>(node), 0u, a.rk);
+#pragma unroll
+    for (int d = 0; d < D; ++d) x[d] = static_cast<R>(a.nodes[node * D + d]);
+    interior = Geom::inside_open(x);
+    if (!interior) {
+      R s = Model::g(a.mc, x);
+      if (!Geom::inside_closed(x)) {
+        s = R(NAN);
+        ++my_bad;
+      }
+      R L0[kLR ? kMaxLR : 1];
+#pragma unroll
+      for (int j = 0; j < (kLR ? kMaxLR : 1); ++j) L0[j] = R(0);
+      write_result<D, R, kLR>(a, q, s, 0, x, L0);
+    }
+  }
+  const unsigned im = __ballot_sync(kFull, interior);
+  if (interior) {
+    const int e = __popc(im & ((1u << lane) - 1u));
+    st.slot[e] = q;
+    st.w0[e] = pp.r0_w0;
+    st.w1[e] = pp.r0_w1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) st.x[d][e] = x[d];
+  }
+  __syncwarp();
+  return __popc(im);
+}
+
+// Called by all 32 lanes: score the first cnt parked paths, one per lane, and
+// write their results.
+template <class Model, class Geom, typename R>
+__device__ __forceinline__ void flush_exits(const PathArgs &a, ExitQueue<Model::D, R> &q, int cnt) {
+  constexpr int D = Model::D;
+  const int lane = static_cast<int>(threadIdx.x & 31u);
+  __syncwarp();
+  if (lane < cnt) {
+    R X[D], Xn[D], xe[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      X[d] = q.x[d][lane];
+      Xn[d] = q.xn[d][lane];
+    }
+    const int code = q.code[lane];
+    R s;
+    if (code == kStepCapped) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) xe[d] = X[d];
+      Geom::project(Geom::nearest_face(X), xe);
+      s = Model::g(a.mc, xe) * q.y[lane] + q.z[lane];
+    } else {
+      s = exit_score<Model, Geom, R>(a.mc, code, X, Xn, q.y[lane], q.z[lane], xe);
+    }
+    R L0[1] = {R(0)};
+    write_result<D, R, false>(a, q.slot[lane], s, q.st[lane], xe, L0);
+  }
+  __syncwarp();
+}
+
 template <class Model, class Geom, typename R, bool kLR = false>
 __global__ void __launch_bounds__(kPathBlock)
 path_kernel(const __grid_constant__ PathArgs a) {
   constexpr int D = Model::D;
   constexpr int NL = kLR ? kMaxLR : 1;
+  __shared__ PathStage<D, R, !kLR> stage_all[kPathBlock / 32];
+  PathStage<D, R, !kLR> &stage = stage_all[threadIdx.x >> 5];
   R L[NL];
-  R xe[D];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
   const StepConst<R> k(a);
-  R X[D];
+  const unsigned long long span = a.end - a.begin;
+  R X[D], Xn[D];
   R Y = R(1), Z = R(0);
   PhiloxPath pp{0, 0, 0};
-  uint64_t slot = 0;
+  unsigned long long slot = 0;
   int32_t n = 0;
-  bool active = false, need = true;
+  bool active = false;
+  int n_start = 0, n_exit = 0;  // stash / queue fill (warp-uniform)
+  bool exhausted = false;       // the wave's indices are all claimed (warp-uniform)
   unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
 
   for (;;) {
-    // ---- refill: lanes without a path take the next indices of the wave
-    for (;;) {
-      const unsigned needmask = __ballot_sync(kFull, need);
-      if (!needmask) break;
-      const int leader = __ffs(needmask) - 1;
-      unsigned long long base = 0;
-      if (static_cast<int>(lane) == leader)
-        base = atomicAdd(a.cursor, static_cast<unsigned long long>(__popc(needmask)));
-      base = __shfl_sync(kFull, base, leader);
-      if (need) {
-        need = false;
-        const unsigned long long q = base + __popc(needmask & lt_mask);
-        const unsigned long long g = a.begin + q;
-        if (g < a.end) {
-          slot = q;
-          uint64_t node;
-          if (a.end <= 0xffffffffull) {  // 32-bit division when the indices fit
-            node = static_cast<uint32_t>(g) / static_cast<uint32_t>(a.n_paths);
-          } else {
-            node = g / a.n_paths;
-          }
-          const uint64_t path = g - node * a.n_paths + a.path_offset;
-          pp = philox_path(static_cast<uint32_t>(path), static_cast<uint32_t>(node), 0u, a.rk);
+    // ---- idle lanes take staged paths; the stash is refilled when empty
+    unsigned needmask = __ballot_sync(kFull, !active);
+    while (needmask) {
+      if (n_start == 0) {
+        if (exhausted) break;
+        n_start = stage_starts<Model, Geom, R, kLR>(a, stage.start, span, exhausted, my_bad);
+        continue;
+      }
+      const int cnt = __popc(needmask);
+      const int take = cnt < n_start ? cnt : n_start;
+      if (!active) {
+        const int r = __popc(needmask & lt_mask);
+        if (r < take) {
+          const int e = n_start - 1 - r;
+          slot = stage.start.slot[e];
+          pp.r0_w0 = stage.start.w0[e];
+          pp.r0_w1 = stage.start.w1[e];
+          pp.tag = 0u;
 #pragma unroll
-          for (int d = 0; d < D; ++d) X[d] = static_cast<R>(a.nodes[node * D + d]);
+          for (int d = 0; d < D; ++d) X[d] = stage.start.x[d][e];
           Y = R(1);
           Z = R(0);
           n = 0;
 #pragma unroll
           for (int j = 0; j < NL; ++j) L[j] = R(0);
-          if (!Geom::inside_open(X)) {
-            // Node on the boundary: tau = 0, u = g (Eq. 2.1).  Outside the
-            // closed domain: invalid input, NaN score, counted.
-            R s = Model::g(a.mc, X);
-            if (!Geom::inside_closed(X)) {
-              s = R(NAN);
-              ++my_bad;
-            }
-#pragma unroll
-            for (int d = 0; d < D; ++d) xe[d] = X[d];
-            write_result<D, R, kLR>(a, slot, s, 0, xe, L);
-            need = true;
-          } else {
-            active = true;
-          }
+          active = true;
+        }
+      }
+      n_start -= take;
+      needmask = __ballot_sync(kFull, !active);
+    }
+    if (!__any_sync(kFull, active)) break;
+
+    // ---- advance the lane's path by one unit
+    int code = kStepContinue;
+    bool done = false;
+    if (active) {
+      code = path_unit_code<Model, Geom, R, kLR>(a, k, pp, a.rk, a.max_steps, X, Y, Z, n, Xn, L);
+      done = code != kStepContinue || n >= a.max_steps;
+      if (done) {
+        my_steps += static_cast<unsigned long long>(n);
+        if (code == kStepContinue) {
+          code = kStepCapped;
+          ++my_capped;
         }
       }
     }
-    if (!__any_sync(kFull, active)) break;
-    if (!active) continue;
 
-    // ---- advance the lane's path
-    R s = R(0);
-    bool done = path_unit<Model, Geom, R, kLR>(a, k, pp, a.rk, a.max_steps, X, Y, Z, n, s, xe, L);
-    int32_t st = n;
-    if (!done && n >= a.max_steps) {
-      // step cap: score at the projection on the nearest face, counted
+    // ---- ended paths
+    if constexpr (kLR) {
+      if (done) {
+        R xe[D], s;
+        int32_t st = n;
+        if (code == kStepCapped) {
 #pragma unroll
-      for (int d = 0; d < D; ++d) xe[d] = X[d];
-      Geom::project(Geom::nearest_face(X), xe);
-      s = Model::g(a.mc, xe) * Y + Z;
-      st = -a.max_steps;
-      ++my_capped;
-      done = true;
+          for (int d = 0; d < D; ++d) xe[d] = X[d];
+          Geom::project(Geom::nearest_face(X), xe);
+          s = Model::g(a.mc, xe) * Y + Z;
+          st = -a.max_steps;
+        } else {
+          s = exit_score<Model, Geom, R>(a.mc, code, X, Xn, Y, Z, xe);
+        }
+        write_result<D, R, true>(a, slot, s, st, xe, L);
+        active = false;
+      }
+    } else {
+      const unsigned dm = __ballot_sync(kFull, done);
+      if (dm) {
+        const int nd = __popc(dm);
+        if (n_exit + nd > 32) {
+          flush_exits<Model, Geom, R>(a, stage.exit, n_exit);
+          n_exit = 0;
+        }
+        if (done) {
+          const int e = n_exit + __popc(dm & lt_mask);
+          ExitQueue<D, R> &q = stage.exit;
+          q.slot[e] = slot;
+          q.st[e] = code == kStepCapped ? -a.max_steps : n;
+          q.code[e] = code;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            q.x[d][e] = X[d];
+            q.xn[d][e] = Xn[d];
+          }
+          q.y[e] = Y;
+          q.z[e] = Z;
+          active = false;
+        }
+        n_exit += nd;
+      }
     }
-    if (done) {
-      write_result<D, R, kLR>(a, slot, s, st, xe, L);
-      my_steps += static_cast<unsigned long long>(n);
-      active = false;
-      need = true;
-    }
+  }
+  if constexpr (!kLR) {
+    if (n_exit > 0) flush_exits<Model, Geom, R>(a, stage.exit, n_exit);
   }
 
   // ---- per-warp totals
