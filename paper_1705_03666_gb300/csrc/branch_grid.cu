@@ -122,7 +122,7 @@ __device__ __forceinline__ bool grid_exit(const GridArgs &a, const float *x0, co
   for (int j = 0; j < Geom::kFaces; ++j) {
     const float e = Geom::template face_dist<float>(j, x0) * Geom::template face_dist<float>(j, x1) * inv;
     if (e < 18.0f) {
-      const float p = __expf(-e);
+      const float p = exp_fast(-e);
       P = P + p * (1.0f - P);
       if (p > pb) {
         pb = p;

@@ -170,36 +170,62 @@ __device__ __forceinline__ float neg2log(float u) {
   return fmaf(-1.3862943611198906f, ef, -4.0f * t * p);
 }
 
+// Hardware approximations (PTX .approx.ftz: one special-function-unit
+// operation each).  Subnormal arguments and results are flushed to zero; the
+// kernels pass normal numbers (uniforms >= 2^-24, radii clamped at 1e-30,
+// centred angles at least 2^-24 away from 0), where the flush changes nothing
+// and the subnormal scaling the non-ftz forms add around the operation is
+// left out.
+__device__ __forceinline__ float ex2_approx(float x) {  // 2^x, about 2 ulp relative
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {  // log2 x, abs. error ~2^-22 near 1
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {  // abs. error < 2^-21.4 on [-pi, pi]
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1) {
   // hardware log2 (absolute error ~2^-22 near u = 1, where it may return 0:
   // y is kept positive for the rsqrt)
-  const float y = fmaxf(-1.3862943611198906f * __log2f(unif_f(a)), 1.0e-30f);
-  const float mr = -(y * rsqrtf(y));
-  float s, c;
-  __sincosf(6.28318530717958648f * (unif_f(b) - 0.5f), &s, &c);
-  z0 = mr * c;
-  z1 = mr * s;
+  const float y = fmaxf(-1.3862943611198906f * lg2_approx(unif_f(a)), 1.0e-30f);
+  const float mr = -(y * rsqrt_approx(y));
+  const float th = 6.28318530717958648f * (unif_f(b) - 0.5f);
+  z0 = mr * cos_approx(th);
+  z1 = mr * sin_approx(th);
 }
 
 // sin(pi x), cos(pi x) for x in [0, 1] (points of the closed unit box).  FP32:
 // hardware sin/cos of pi x in [0, pi], absolute error below 2^-21.4 -- used
 // for drift and source values inside the domain, never for boundary data.
 __device__ __forceinline__ void sincospi01(float x, float *s, float *c) {
-  __sincosf(3.14159265358979324f * x, s, c);
+  const float t = 3.14159265358979324f * x;
+  *s = sin_approx(t);
+  *c = cos_approx(t);
 }
 __device__ __forceinline__ void sincospi01(double x, double *s, double *c) { sincospi(x, s, c); }
 
 // e^x for moderate x: FP32 hardware exp2 of x log2 e (about 2 ulp).
-__device__ __forceinline__ float exp_fast(float x) { return __expf(x); }
+__device__ __forceinline__ float exp_fast(float x) { return ex2_approx(1.4426950408889634f * x); }
 __device__ __forceinline__ double exp_fast(double x) { return exp(x); }
-
-// 2^x by the hardware unit (about 2 ulp relative).
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // ---------------------------------------------------------------------------
 // Compensated (Neumaier) FP64 accumulator and its exact merge.

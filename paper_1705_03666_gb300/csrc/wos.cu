@@ -33,10 +33,9 @@ struct WosArgs {
 
 // A jump of length d in direction 2 pi U.
 __device__ __forceinline__ void wos_dir(float U, float &cx, float &sy) {
-  float s, c;
-  __sincosf(6.28318530717958648f * (U - 0.5f), &s, &c);  // centred: cos(2pi U) = -c
-  cx = -c;
-  sy = -s;
+  const float th = 6.28318530717958648f * (U - 0.5f);  // centred: cos(2pi U) = -cos(th)
+  cx = -cos_approx(th);
+  sy = -sin_approx(th);
 }
 __device__ __forceinline__ void wos_dir(double U, double &cx, double &sy) {
   sincospi(2.0 * U, &sy, &cx);
