@@ -181,7 +181,7 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
           path_end = min(a.end[i], path + a.K);
           pi = a.prob[i];
           const BatchProblem &P = a.probs[pi];
-          k = make_step_const(a.dt[i], P.sigma, P.c_kill);
+          k = make_step_const(a.dt[i], P.sigma, P.c_kill, P.bridge != 0);
           shift = a.shift ? a.shift[i] : 0.0;
           shift_f = static_cast<float>(shift);
           s1 = F2Sum();

@@ -102,8 +102,9 @@ __device__ __forceinline__ uint4 philox10_path(uint32_t j, const PhiloxPath &pp,
 // the FP64 oracle draw the same U from the same word).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float unif_f(uint32_t w) {
-  // 1 + k 2^-23 minus (1 - 2^-24): exact (Sterbenz), = (2k+1) 2^-24
-  return __int_as_float(0x3f800000u | (w >> 9)) - 0.999999940395355224609375f;
+  // 1 + k 2^-23 minus (1 - 2^-24): exact (Sterbenz), = (2k+1) 2^-24.  The
+  // exponent bits are added (they do not overlap k), one shift-and-add.
+  return __int_as_float((w >> 9) + 0x3f800000u) - 0.999999940395355224609375f;
 }
 __device__ __forceinline__ double unif_d(uint32_t w) {
   return static_cast<double>((w >> 9) * 2u + 1u) * 5.9604644775390625e-08;  // 2^-24
@@ -201,6 +202,14 @@ __device__ __forceinline__ float cos_approx(float x) {
   asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+
+// Smallest of three (one three-input min in binary32).
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
 
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1) {

@@ -187,21 +187,24 @@ struct Box {
     const R v = x[j >> 1];
     return (j & 1) ? R(1) - v : v;
   }
-  // Screening of a step X -> X' (X in the closed box).  Per axis k,
-  //   m[k] = min(x_k x'_k, (1 - x_k)(1 - x'_k)), the d d' of the axis' face
-  //          that can be within bridge reach (the other one cannot while
-  //          sigma^2 dt <= 1/36);
-  // mn = the smallest m[k].  mn > 0 puts X' strictly inside the box: with x_k
-  // in [0, 1], both products of an axis are positive only for x'_k in (0, 1)
-  // (a rounded product keeps its sign; an underflow to zero gives mn = 0).
+  // Screening of a step X -> X' (X in the closed box): the smallest
+  //   d d' = min over k of min(x_k x'_k, (1 - x_k)(1 - x'_k))
+  // over the face of each axis that can be within bridge reach (the other
+  // one cannot while sigma^2 dt <= 1/36).  A result > 0 puts X' strictly
+  // inside the box: with x_k in [0, 1], both products of an axis are positive
+  // only for x'_k in (0, 1) (a rounded product keeps its sign; an underflow
+  // to zero gives 0).
   template <typename R>
-  __device__ __forceinline__ static void screen_min(const R *x0, const R *x1, R *m, R &mn) {
-    mn = R(1);
+  __device__ __forceinline__ static R screen_mn(const R *x0, const R *x1) {
+    R p[2 * D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      m[k] = fmin(x0[k] * x1[k], (R(1) - x0[k]) * (R(1) - x1[k]));
-      mn = fmin(mn, m[k]);
+      p[2 * k] = x0[k] * x1[k];
+      p[2 * k + 1] = (R(1) - x0[k]) * (R(1) - x1[k]);
     }
+    if constexpr (D == 1) return fmin(p[0], p[1]);
+    else if constexpr (D == 2) return fmin(min3(p[0], p[1], p[2]), p[3]);
+    else return fmin(min3(p[0], p[1], p[2]), min3(p[3], p[4], p[5]));
   }
   // Second smallest of m[0..D-1] (D <= 3): below the reach threshold means
   // the step is within reach of two faces (an edge or a corner).

@@ -58,22 +58,25 @@ struct PathArgs {
 template <typename R> struct StepConst;
 template <> struct StepConst<float> {
   float dt, sdt, thr, l2cdt, inv_s2dt;
-  float b2;  // -2 log2(e) / (sigma^2 dt): exp(-2 m / (sigma^2 dt)) = 2^(b2 m)
+  float b2;    // -2 log2(e) / (sigma^2 dt): exp(-2 m / (sigma^2 dt)) = 2^(b2 m)
+  float boff;  // 0 with the bridge test, -inf without (every bound below is 0)
   StepConst() = default;
   __device__ __forceinline__ StepConst(const PathArgs &a)
       : dt(a.dt_f), sdt(a.sdt_f), thr(a.thr_f), l2cdt(a.l2cdt_f),
         inv_s2dt(static_cast<float>(a.inv_s2dt)),
-        b2(static_cast<float>(-2.0 * 1.4426950408889634 * a.inv_s2dt)) {}
+        b2(static_cast<float>(-2.0 * 1.4426950408889634 * a.inv_s2dt)),
+        boff(a.bridge ? 0.0f : -INFINITY) {}
   // half-space crossing probability for a step with d d' = m
   __device__ __forceinline__ float cross_p(float m) const { return ex2_approx(b2 * m); }
   // Bound on every crossing probability of a step whose smallest d d' over
   // D candidate faces is m: 1 - prod_j (1 - p_j) <= D p(m), raised by the
   // factor 2^(2^-12) = 1 + 1.7e-4, which covers the near-tie window (2^-18
   // relative) and the rounding of the exponents (< 1e-5 relative for the
-  // probabilities above 2^-26 that a uniform can fall below).
+  // probabilities above 2^-26 that a uniform can fall below).  0 without the
+  // bridge test.
   template <int D> __device__ __forceinline__ float cross_bound(float m) const {
     constexpr float kOff = (D == 1 ? 0.0f : D == 2 ? 1.0f : 1.5849625007211562f) + 2.44140625e-4f;
-    return ex2_approx(fmaf(b2, m, kOff));
+    return ex2_approx(fmaf(b2, m, kOff + boff));
   }
   __device__ __forceinline__ float kill(float, int32_t n_next) const {
     return ex2_approx(static_cast<float>(n_next) * l2cdt);
@@ -86,20 +89,23 @@ template <> struct StepConst<float> {
 };
 template <> struct StepConst<double> {
   double dt, sdt, thr, e, inv_s2dt;
+  double boff;  // 0 with the bridge test, -inf without
   __device__ __forceinline__ StepConst(const PathArgs &a)
-      : dt(a.dt_d), sdt(a.sdt_d), thr(a.thr_d), e(a.ecdt_d), inv_s2dt(a.inv_s2dt) {}
+      : dt(a.dt_d), sdt(a.sdt_d), thr(a.thr_d), e(a.ecdt_d), inv_s2dt(a.inv_s2dt),
+        boff(a.bridge ? 0.0 : -INFINITY) {}
   __device__ __forceinline__ double kill(double y, int32_t) const { return y * e; }
   __device__ __forceinline__ double exp_neg(double a) const { return exp(-a); }
   __device__ __forceinline__ double cross_p(double m) const { return exp(-2.0 * m * inv_s2dt); }
   template <int D> __device__ __forceinline__ double cross_bound(double m) const {
-    return static_cast<double>(D) * 1.0000001 * exp(-2.0 * m * inv_s2dt);
+    return static_cast<double>(D) * 1.0000001 * exp(boff - 2.0 * m * inv_s2dt);
   }
 };
 
-// FP32 step constants for time step dt, generator (1/2) sigma^2 Lap and a
-// constant killing rate c, rounded from the same FP64 expressions the host
-// uses for PathArgs.
-__device__ __forceinline__ StepConst<float> make_step_const(double dt, double sigma, double c) {
+// FP32 step constants for time step dt, generator (1/2) sigma^2 Lap, a
+// constant killing rate c and the bridge test on or off, rounded from the
+// same FP64 expressions the host uses for PathArgs.
+__device__ __forceinline__ StepConst<float> make_step_const(double dt, double sigma, double c,
+                                                            bool bridge) {
   StepConst<float> k;
   k.dt = static_cast<float>(dt);
   k.sdt = static_cast<float>(sigma * sqrt(dt));
@@ -107,6 +113,7 @@ __device__ __forceinline__ StepConst<float> make_step_const(double dt, double si
   k.l2cdt = static_cast<float>(c * dt * 1.4426950408889634);
   k.inv_s2dt = static_cast<float>(1.0 / (sigma * sigma * dt));
   k.b2 = static_cast<float>(-2.0 * 1.4426950408889634 / (sigma * sigma * dt));
+  k.boff = bridge ? 0.0f : -INFINITY;
   return k;
 }
 
@@ -237,24 +244,24 @@ __device__ __forceinline__ int em_step(const Env &a, const StepConst<R> &k, R *X
       if (jbest >= 0) return jbest;
     }
   } else {
-    R m[D], mn;
-    Geom::screen_min(X, Xn, m, mn);
-    // mn > 0: X' strictly inside; otherwise the exact test decides
-    if (!(mn > R(0)) && !Geom::inside_closed(Xn)) return kStepHardExit;
-    if (a.bridge) {
-      const R U = unif<R>(uw);
-      // At most steps U lies above every crossing probability the step can
-      // have (and above its near-tie window): one bound decides that, and the
-      // probability itself is formed only below it.  A step within reach of
-      // one face crosses with exp(-2 min d d' / (sigma^2 dt)); a step within
-      // reach of two or more faces (an edge or a corner) takes the general
-      // combination.
-      if (U < k.template cross_bound<D>(mn)) {
+    const R mn = Geom::screen_mn(X, Xn);
+    // mn > 0 puts X' strictly inside.  U lies above every crossing
+    // probability the step can have (and above its near-tie window) at most
+    // steps: one bound decides that, and the probability itself is formed
+    // only below it.  Both tests share one branch.
+    const R U = unif<R>(uw);
+    const R bnd = k.template cross_bound<D>(mn);
+    if (!(mn > R(0)) || U < bnd) {
+      if (!(mn > R(0)) && !Geom::inside_closed(Xn)) return kStepHardExit;
+      if (U < bnd) {
+        // A step within reach of one face crosses with
+        // exp(-2 min d d' / (sigma^2 dt)); a step within reach of two or more
+        // faces (an edge or a corner) takes the general combination.
+        R prod[D];
+        int face[D];
+        Geom::screen(X, Xn, prod, face);
         bool cross;
-        if (Geom::second_min(m) < k.thr) {
-          R prod[D];
-          int face[D];
-          Geom::screen(X, Xn, prod, face);
+        if (Geom::second_min(prod) < k.thr) {
           cross = bridge_exit<D, R>(k, prod, face, U) >= 0;
         } else {
           const R p = k.cross_p(mn);
@@ -264,9 +271,6 @@ __device__ __forceinline__ int em_step(const Env &a, const StepConst<R> &k, R *X
           }
         }
         if (cross) {
-          R prod[D];
-          int face[D];
-          Geom::screen(X, Xn, prod, face);
           int jbest = face[0];
           R pmin = prod[0];
 #pragma unroll
