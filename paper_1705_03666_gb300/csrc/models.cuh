@@ -31,6 +31,7 @@ template <> __device__ __forceinline__ double prm<double>(const ModelConst &mc, 
 struct LaplaceExpCos {
   static constexpr int D = 2;
   static constexpr bool kDrift = false, kSource = false;
+  static constexpr unsigned kDriftAxes = 0u;  // axes whose drift can be nonzero
   static constexpr int kKill = 0;  // 0: none, 1: constant, 2: variable
   template <typename R>
   __device__ __forceinline__ static void coeffs(const ModelConst &, const R *, R *, R &) {}
@@ -50,6 +51,7 @@ struct LaplaceExpCos {
 struct EllipticManufactured {
   static constexpr int D = 3;
   static constexpr bool kDrift = true, kSource = true;
+  static constexpr unsigned kDriftAxes = 3u;  // b2 = 0
   static constexpr int kKill = 1;  // c = -1
   template <typename R>
   __device__ __forceinline__ static void coeffs(const ModelConst &, const R *x, R *b, R &f) {
@@ -85,6 +87,7 @@ struct EllipticManufactured {
 struct PoissonFourier {
   static constexpr int D = 2;
   static constexpr bool kDrift = true, kSource = true;
+  static constexpr unsigned kDriftAxes = 3u;
   static constexpr int kKill = 0;
   template <typename R>
   __device__ __forceinline__ static void sines(R t, R *s) {  // s[j-1] = sin(j pi t), t in [0,1]

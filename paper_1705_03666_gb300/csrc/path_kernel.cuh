@@ -228,8 +228,15 @@ __device__ __forceinline__ int em_step(const Env &a, const StepConst<R> &k, R *X
   } else if constexpr (Model::kDrift || Model::kSource) {
     Model::coeffs(a.mc, X, b, f);
   }
+  // (an axis without drift skips b dt: X + 0 dt is X exactly, so the result
+  // is the same)
 #pragma unroll
-  for (int d = 0; d < D; ++d) Xn[d] = X[d] + b[d] * k.dt + k.sdt * xi[d];
+  for (int d = 0; d < D; ++d) {
+    if ((Model::kDriftAxes >> d) & 1u)
+      Xn[d] = X[d] + b[d] * k.dt + k.sdt * xi[d];
+    else
+      Xn[d] = X[d] + k.sdt * xi[d];
+  }
   R Zn = Z;
   if constexpr (Model::kSource) Zn = Z + f * Y * k.dt;
   R Yn = Y;
