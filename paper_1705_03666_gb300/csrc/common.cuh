@@ -187,9 +187,9 @@ __device__ __forceinline__ float lg2_approx(float x) {  // log2 x, abs. error ~2
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float rsqrt_approx(float x) {
+__device__ __forceinline__ float sqrt_approx(float x) {
   float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float sin_approx(float x) {  // abs. error < 2^-21.4 on [-pi, pi]
@@ -213,11 +213,16 @@ __device__ __forceinline__ double min3(double a, double b, double c) { return fm
 
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1) {
-  // hardware log2 (absolute error ~2^-22 near u = 1, where it may return 0:
-  // y is kept positive for the rsqrt)
-  const float y = fmaxf(-1.3862943611198906f * lg2_approx(unif_f(a)), 1.0e-30f);
-  const float mr = -(y * rsqrt_approx(y));
-  const float th = 6.28318530717958648f * (unif_f(b) - 0.5f);
+  // hardware log2 (absolute error ~2^-22 near u = 1, where it may return 0
+  // or a tiny positive value: y is clamped at 0) and hardware square root
+  const float y = fmaxf(-1.3862943611198906f * lg2_approx(unif_f(a)), 0.0f);
+  const float mr = -sqrt_approx(y);
+  // theta = 2 pi (U_b - 1/2) from x = 1 + k 2^-23 (k = b >> 9, exponent bits
+  // added): U_b - 1/2 = (x - 3/2) + 2^-24 with x - 3/2 exact, so theta is one
+  // subtraction and one FMA, rounded once (the same value as 2 pi (U_b - 1/2)
+  // formed from the uniform)
+  const float xb = __int_as_float((b >> 9) + 0x3f800000u);
+  const float th = fmaf(xb - 1.5f, 6.28318530717958648f, 6.28318530717958648f * 0x1p-24f);
   z0 = mr * cos_approx(th);
   z1 = mr * sin_approx(th);
 }

@@ -556,6 +556,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
   for (;;) {
     // ---- idle lanes take staged paths; the stash is refilled when empty
     unsigned needmask = __ballot_sync(kFull, !active);
+    if (needmask) {
     while (needmask) {
       if (n_start == 0) {
         if (exhausted) break;
@@ -586,6 +587,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
       needmask = __ballot_sync(kFull, !active);
     }
     if (!__any_sync(kFull, active)) break;
+    }
 
     // ---- advance the lane's path by one unit
     int code = kStepContinue;
