@@ -316,13 +316,16 @@ __device__ __forceinline__ uint32_t low_bytes_word(uint32_t a, uint32_t b, uint3
   return __byte_perm(__byte_perm(a, b, 0x0400u), c, 0x4210u);
 }
 
-// One loop unit of a path.  d <= 2: one step n from Philox block n (normals
-// BM(w0, w1), bridge uniform w2).  d = 3: steps 4q .. 4q+3 from blocks 3q,
-// 3q+1, 3q+2, formed as the steps need them: normals z0..z11 = BM of the word
-// pairs (w0,w1) .. (w10,w11), step 4q+j takes z[3j..3j+2] and the uniform of
-// low_bytes_word(w[3j], w[3j+1], w[3j+2]).  n counts the steps taken; the unit
-// stops at an exit (returns its code, X the start and Xn the end of the
-// exiting step) or at max_steps (returns kStepContinue).
+// One loop unit of a path: up to four steps.  d <= 2: step n from Philox
+// block n (normals BM(w0, w1), bridge uniform w2).  d = 3: steps 4q .. 4q+3
+// from blocks 3q, 3q+1, 3q+2: normals z0..z11 = BM of the word pairs
+// (w0,w1) .. (w10,w11), step 4q+j takes z[3j..3j+2] and the uniform of
+// low_bytes_word(w[3j], w[3j+1], w[3j+2]).  The unit's random numbers are
+// formed before its first step: they do not depend on the path, so their
+// integer work can interleave with the steps' floating-point work.  n counts
+// the steps taken; the unit stops at an exit (returns its code, X the start
+// and Xn the end of the exiting step) or at max_steps (returns
+// kStepContinue).
 template <class Model, class Geom, typename R, bool kLR, class Env>
 __device__ __forceinline__ int path_unit_code(const Env &a, const StepConst<R> &k,
                                               const PhiloxPath &pp, const RoundKeys &rk,
@@ -332,39 +335,40 @@ __device__ __forceinline__ int path_unit_code(const Env &a, const StepConst<R> &
   int code;
   if constexpr (D == 3) {
     const uint32_t q3 = 3u * (static_cast<uint32_t>(n) >> 2);
-    do {
-      const uint4 A = philox10_path(q3, pp, rk);
-      R xi[3], z3;
-      box_muller<R>(A.x, A.y, xi[0], xi[1]);
-      box_muller<R>(A.z, A.w, xi[2], z3);
-      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, low_bytes_word(A.x, A.y, A.z), n, Xn, L);
+    const uint4 A = philox10_path(q3, pp, rk);
+    const uint4 B = philox10_path(q3 + 1u, pp, rk);
+    const uint4 C = philox10_path(q3 + 2u, pp, rk);
+    R z[12];
+    box_muller<R>(A.x, A.y, z[0], z[1]);
+    box_muller<R>(A.z, A.w, z[2], z[3]);
+    box_muller<R>(B.x, B.y, z[4], z[5]);
+    box_muller<R>(B.z, B.w, z[6], z[7]);
+    box_muller<R>(C.x, C.y, z[8], z[9]);
+    box_muller<R>(C.z, C.w, z[10], z[11]);
+    const uint32_t u[4] = {low_bytes_word(A.x, A.y, A.z), low_bytes_word(A.w, B.x, B.y),
+                           low_bytes_word(B.z, B.w, C.x), low_bytes_word(C.y, C.z, C.w)};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z + 3 * j, u[j], n, Xn, L);
       ++n;
       if (code != kStepContinue || n >= max_steps) break;
-      const uint4 B = philox10_path(q3 + 1u, pp, rk);
-      xi[0] = z3;
-      box_muller<R>(B.x, B.y, xi[1], xi[2]);
-      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, low_bytes_word(A.w, B.x, B.y), n, Xn, L);
-      ++n;
-      if (code != kStepContinue || n >= max_steps) break;
-      const uint4 C = philox10_path(q3 + 2u, pp, rk);
-      R z9;
-      box_muller<R>(B.z, B.w, xi[0], xi[1]);
-      box_muller<R>(C.x, C.y, xi[2], z9);
-      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, low_bytes_word(B.z, B.w, C.x), n, Xn, L);
-      ++n;
-      if (code != kStepContinue || n >= max_steps) break;
-      xi[0] = z9;
-      box_muller<R>(C.z, C.w, xi[1], xi[2]);
-      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, low_bytes_word(C.y, C.z, C.w), n, Xn, L);
-      ++n;
-    } while (false);
+    }
   } else {
-    const uint4 A = philox10_path(static_cast<uint32_t>(n), pp, rk);
-    R xi[2], z1;
-    box_muller<R>(A.x, A.y, xi[0], z1);
-    xi[1] = z1;
-    code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, xi, A.z, n, Xn, L);
-    ++n;
+    constexpr int kU = 4;
+    R z[2 * kU];
+    uint32_t u[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const uint4 A = philox10_path(static_cast<uint32_t>(n) + static_cast<uint32_t>(j), pp, rk);
+      box_muller<R>(A.x, A.y, z[2 * j], z[2 * j + 1]);
+      u[j] = A.z;
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z + 2 * j, u[j], n, Xn, L);
+      ++n;
+      if (code != kStepContinue || n >= max_steps) break;
+    }
   }
   return code;
 }
