@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
   uint32_t id = 0, t = 0, tend = 0, j = 0, u_off = 0;
   int ti = 0;
   bool start = false;
-  uint32_t node = 0, tree = 0, next_id = 0;
+  PhiloxPath pp{0, 0, 3u};  // the (tree, node, tag 3) half of Philox round one
+  uint32_t next_id = 0;
   int64_t particles = 0;
   int32_t nsteps = 0;
   uint64_t slot = 0;
@@ -175,8 +176,8 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
           slot = q;
           const unsigned long long g = a.begin + q;
           nc.locate(g, a.n_trees, a.end, a.nodes);
-          node = static_cast<uint32_t>(nc.node);
-          tree = static_cast<uint32_t>(g - nc.lo + a.tree_offset);
+          pp = philox_path(static_cast<uint32_t>(g - nc.lo + a.tree_offset),
+                           static_cast<uint32_t>(nc.node), 3u, a.rk);
           X[0] = nc.x[0];
           X[1] = D > 1 ? nc.x[D > 1 ? 1 : 0] : 0.f;
           for (int k = 0; k < a.m; ++k) PROD(k) = 1.0f;
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
 
     if (start) {
       // lifetime of the current particle (block 0 of its stream)
-      const uint4 w = philox10(id << 20, tree, node, 3u, a.rk);
+      const uint4 w = philox10_path(id << 20, pp, a.rk);  // = Philox((id << 20, tree, node, 3))
       const float ltk = 0.5f * neg2log(unif_f(w.x)) * a.inv_beta * a.tps;
       const uint64_t e = ltk >= 4294967040.0f ? 4294967295ull : static_cast<uint64_t>(__float2uint_rz(ltk));
       const uint64_t te = static_cast<uint64_t>(t) + e;
@@ -232,12 +233,12 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
       if (ti < a.m && a.T[ti] < nxt) nxt = a.T[ti];
       if (kBounded && nxt - t > a.dt_ticks) nxt = t + a.dt_ticks;
       const float h = static_cast<float>(nxt - t) * a.inv_tps;
-      const uint4 v = philox10((id << 20) | j, tree, node, 3u, a.rk);
+      const uint4 v = philox10_path((id << 20) | j, pp, a.rk);
       ++j;
       ++nsteps;
       float z0, z1;
       box_muller<float>(v.x, v.y, z0, z1);
-      const float sh = sqrtf(h);
+      const float sh = sqrt_approx(h);
       float Xn[2] = {X[0] + sh * z0, D > 1 ? X[1] + sh * z1 : 0.f};
       if constexpr (kBounded) {
         float xe[2] = {0.f, 0.f};

@@ -34,7 +34,7 @@ constexpr int kMaxOffspring = 7;
 constexpr unsigned kBranchChunk = 64;  // trees claimed per warp-level atomic
 
 struct BranchArgs {
-  const double *nodes_xt;       // [n][D + 1]: position, then time t
+  const float4 *nodes_f;        // [n]: (x1, x2 or 0, t, 0) in binary32
   uint64_t n_trees, tree_offset;
   uint64_t begin, end;          // tree index range of this wave
   unsigned long long *cursor;
@@ -74,8 +74,9 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
   // current particle
   float x0 = 0.f, x1 = 0.f, tb = 0.f;
   uint32_t id = 0;
-  // current tree
-  uint32_t node = 0, tree = 0, next_id = 0;
+  // current tree: the (tree, node, tag 1) half of Philox round one
+  PhiloxPath pp{0, 0, 1u};
+  uint32_t next_id = 0;
   float t = 0.f;
   float prod = 1.0f, weight = 1.0f;
   int64_t particles = 0;
@@ -99,12 +100,12 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
           const uint64_t nd = a.end <= 0xffffffffull
                                   ? static_cast<uint32_t>(g) / static_cast<uint32_t>(a.n_trees)
                                   : g / a.n_trees;
-          node = static_cast<uint32_t>(nd);
-          tree = static_cast<uint32_t>(g - nd * a.n_trees + a.tree_offset);
-          const double *xt = a.nodes_xt + nd * (D + 1);
-          x0 = static_cast<float>(xt[0]);
-          x1 = D == 2 ? static_cast<float>(xt[1]) : 0.f;
-          t = static_cast<float>(xt[D]);
+          const uint32_t tree = static_cast<uint32_t>(g - nd * a.n_trees + a.tree_offset);
+          pp = philox_path(tree, static_cast<uint32_t>(nd), 1u, a.rk);
+          const float4 xt = a.nodes_f[nd];  // converted once per call, not per tree
+          x0 = xt.x;
+          x1 = xt.y;
+          t = xt.z;
           tb = 0.f;
           id = 0;
           next_id = 1;
@@ -121,14 +122,14 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
     if (!active) continue;
 
     // ---- one particle segment
-    const uint4 w = philox10(id, tree, node, 1u, a.rk);
+    const uint4 w = philox10_path(id, pp, a.rk);  // = Philox((id, tree, node, 1))
     const float life = 0.5f * neg2log(unif_f(w.x)) * a.inv_beta;  // -ln U / beta
     float tend = tb + life;
     const bool reaches = tend >= t;
     if (reaches) tend = t;
     float z0, z1;
     box_muller<float>(w.y, w.z, z0, z1);
-    const float h = sqrtf(tend - tb);
+    const float h = sqrt_approx(tend - tb);
     x0 += h * z0;
     if (D == 2) x1 += h * z1;
     ++segments;

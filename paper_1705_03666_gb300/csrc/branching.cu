@@ -9,6 +9,18 @@
 
 namespace pdd {
 
+// Space-time nodes in binary32 (x1, x2 or 0, t, 0): the branching kernel
+// starts a tree every few segments, and converting the FP64 coordinates there
+// would put three conversions per tree on the 1/64-rate FP64 pipe.
+__global__ void node_xt_f32_kernel(const double *xt, int64_t n, int d, float4 *out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double *p = xt + i * (d + 1);
+    out[i] = make_float4(static_cast<float>(p[0]), d == 2 ? static_cast<float>(p[1]) : 0.0f,
+                         static_cast<float>(p[d]), 0.0f);
+  }
+}
+
 template <int D>
 static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t n,
                                 const pdd_branch_params *bp, double *d_mean, double *d_se,
@@ -17,7 +29,8 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
   const uint64_t total = static_cast<uint64_t>(n) * N;
   const uint64_t wave = std::min<uint64_t>(total, ctx->wave_max_paths);
   const size_t acc_off = 256;
-  const size_t score_off = align_up(acc_off + static_cast<size_t>(n) * sizeof(NodeAcc), 256);
+  const size_t xt_off = align_up(acc_off + static_cast<size_t>(n) * sizeof(NodeAcc), 256);
+  const size_t score_off = align_up(xt_off + static_cast<size_t>(n) * sizeof(float4), 256);
   const size_t bytes = align_up(score_off + wave * sizeof(float), 256);
   pdd_status st = ensure_scratch(ctx, bytes);
   if (st != PDD_OK) return st;
@@ -25,13 +38,17 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
   auto *counters = reinterpret_cast<unsigned long long *>(base);
   auto *cursor = counters + 4;
   auto *acc = reinterpret_cast<NodeAcc *>(base + acc_off);
+  auto *xt_f = reinterpret_cast<float4 *>(base + xt_off);
   float *score = reinterpret_cast<float *>(base + score_off);
-  PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, score_off, ctx->stream));
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, xt_off, ctx->stream));
+  node_xt_f32_kernel<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 4096)), 256, 0,
+                       ctx->stream>>>(d_nodes_xt, n, D, xt_f);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
 
   const double *prm = ctx->params.data();
   BranchArgs a;
   std::memset(&a, 0, sizeof a);
-  a.nodes_xt = d_nodes_xt;
+  a.nodes_f = xt_f;
   a.n_trees = N;
   a.tree_offset = static_cast<uint64_t>(bp->tree_offset);
   a.cursor = cursor;
