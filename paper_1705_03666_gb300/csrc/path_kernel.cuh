@@ -316,16 +316,48 @@ __device__ __forceinline__ uint32_t low_bytes_word(uint32_t a, uint32_t b, uint3
   return __byte_perm(__byte_perm(a, b, 0x0400u), c, 0x4210u);
 }
 
-// One loop unit of a path: up to four steps.  d <= 2: step n from Philox
-// block n (normals BM(w0, w1), bridge uniform w2).  d = 3: steps 4q .. 4q+3
-// from blocks 3q, 3q+1, 3q+2: normals z0..z11 = BM of the word pairs
-// (w0,w1) .. (w10,w11), step 4q+j takes z[3j..3j+2] and the uniform of
-// low_bytes_word(w[3j], w[3j+1], w[3j+2]).  The unit's random numbers are
-// formed before its first step: they do not depend on the path, so their
-// integer work can interleave with the steps' floating-point work.  n counts
-// the steps taken; the unit stops at an exit (returns its code, X the start
-// and Xn the end of the exiting step) or at max_steps (returns
-// kStepContinue).
+// Random numbers of the four-step unit that starts at step n (in 3-D n is a
+// multiple of 4): normals z[D j .. D j + D - 1] and the bridge-uniform word
+// u[j] of step n + j.  d <= 2: step n + j from Philox block n + j (normals
+// BM(w0, w1), uniform word w2).  d = 3: blocks 3q, 3q+1, 3q+2 for q = n / 4:
+// normals z0..z11 = BM of the word pairs (w0,w1) .. (w10,w11), step 4q + j
+// takes z[3j..3j+2] and low_bytes_word(w[3j], w[3j+1], w[3j+2]).
+template <int D, typename R>
+__device__ __forceinline__ void unit_randoms(int32_t n, const PhiloxPath &pp, const RoundKeys &rk,
+                                             R *z, uint32_t *u) {
+  if constexpr (D == 3) {
+    const uint32_t q3 = 3u * (static_cast<uint32_t>(n) >> 2);
+    const uint4 A = philox10_path(q3, pp, rk);
+    const uint4 B = philox10_path(q3 + 1u, pp, rk);
+    const uint4 C = philox10_path(q3 + 2u, pp, rk);
+    box_muller<R>(A.x, A.y, z[0], z[1]);
+    box_muller<R>(A.z, A.w, z[2], z[3]);
+    box_muller<R>(B.x, B.y, z[4], z[5]);
+    box_muller<R>(B.z, B.w, z[6], z[7]);
+    box_muller<R>(C.x, C.y, z[8], z[9]);
+    box_muller<R>(C.z, C.w, z[10], z[11]);
+    u[0] = low_bytes_word(A.x, A.y, A.z);
+    u[1] = low_bytes_word(A.w, B.x, B.y);
+    u[2] = low_bytes_word(B.z, B.w, C.x);
+    u[3] = low_bytes_word(C.y, C.z, C.w);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 A = philox10_path(static_cast<uint32_t>(n) + static_cast<uint32_t>(j), pp, rk);
+      R z1;
+      box_muller<R>(A.x, A.y, z[D * j], z1);
+      if constexpr (D == 2) z[D * j + 1] = z1;
+      u[j] = A.z;
+    }
+  }
+}
+
+// One loop unit of a path: up to four steps, with the random numbers of
+// unit_randoms.  They are formed before the unit's first step: they do not
+// depend on the path, so their integer work can interleave with the steps'
+// floating-point work.  n counts the steps taken; the unit stops at an exit
+// (returns its code, X the start and Xn the end of the exiting step) or at
+// max_steps (returns kStepContinue).
 template <class Model, class Geom, typename R, bool kLR, class Env>
 __device__ __forceinline__ int path_unit_code(const Env &a, const StepConst<R> &k,
                                               const PhiloxPath &pp, const RoundKeys &rk,
@@ -333,42 +365,14 @@ __device__ __forceinline__ int path_unit_code(const Env &a, const StepConst<R> &
                                               R *Xn, R *L) {
   constexpr int D = Model::D;
   int code;
-  if constexpr (D == 3) {
-    const uint32_t q3 = 3u * (static_cast<uint32_t>(n) >> 2);
-    const uint4 A = philox10_path(q3, pp, rk);
-    const uint4 B = philox10_path(q3 + 1u, pp, rk);
-    const uint4 C = philox10_path(q3 + 2u, pp, rk);
-    R z[12];
-    box_muller<R>(A.x, A.y, z[0], z[1]);
-    box_muller<R>(A.z, A.w, z[2], z[3]);
-    box_muller<R>(B.x, B.y, z[4], z[5]);
-    box_muller<R>(B.z, B.w, z[6], z[7]);
-    box_muller<R>(C.x, C.y, z[8], z[9]);
-    box_muller<R>(C.z, C.w, z[10], z[11]);
-    const uint32_t u[4] = {low_bytes_word(A.x, A.y, A.z), low_bytes_word(A.w, B.x, B.y),
-                           low_bytes_word(B.z, B.w, C.x), low_bytes_word(C.y, C.z, C.w)};
+  R z[4 * D];
+  uint32_t u[4];
+  unit_randoms<D, R>(n, pp, rk, z, u);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z + 3 * j, u[j], n, Xn, L);
-      ++n;
-      if (code != kStepContinue || n >= max_steps) break;
-    }
-  } else {
-    constexpr int kU = 4;
-    R z[2 * kU];
-    uint32_t u[kU];
-#pragma unroll
-    for (int j = 0; j < kU; ++j) {
-      const uint4 A = philox10_path(static_cast<uint32_t>(n) + static_cast<uint32_t>(j), pp, rk);
-      box_muller<R>(A.x, A.y, z[2 * j], z[2 * j + 1]);
-      u[j] = A.z;
-    }
-#pragma unroll
-    for (int j = 0; j < kU; ++j) {
-      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z + 2 * j, u[j], n, Xn, L);
-      ++n;
-      if (code != kStepContinue || n >= max_steps) break;
-    }
+  for (int j = 0; j < 4; ++j) {
+    code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z + D * j, u[j], n, Xn, L);
+    ++n;
+    if (code != kStepContinue || n >= max_steps) break;
   }
   return code;
 }

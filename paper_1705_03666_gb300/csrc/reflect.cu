@@ -16,9 +16,11 @@
 // L} - 1) / phi, Y *= e^{phi L}; then the time part as in the path kernel
 // (left point).  Absorbing faces keep the hard-exit and bridge tests.
 // Y is formed as exp(n c dt + sum phi L) so binary32 rounding does not
-// accumulate along the path.  A generic per-face loop (not the screened
-// fast path of path_kernel.cuh): reflecting problems are not the hot
-// configuration.
+// accumulate along the path.  Per step, one test over the reflecting faces
+// (the reflection's own reach test) and one bound over the absorbing faces
+// (smallest d d' > 0 and U above 2D exp(-2 min d d' / (sigma^2 dt))) skip
+// the per-face work at most steps; the decisions are those of the per-face
+// loops.
 #include <cmath>
 #include <cstring>
 
@@ -44,63 +46,203 @@ struct ReflectArgs {
   ModelConst mc;
 };
 
-__device__ __forceinline__ float m_cospi(float x) { return cospif(x); }
-__device__ __forceinline__ double m_cospi(double x) { return cospi(x); }
-__device__ __forceinline__ float m_sin(float x) { return sinf(x); }
-__device__ __forceinline__ double m_sin(double x) { return sin(x); }
+// Special functions of the reflection branch.  A reflecting problem's paths
+// linger near their reflecting faces, so this branch runs, diverged, at most
+// warp-steps: binary32 takes the hardware approximations (relative errors of
+// order 1e-7 against the 1e-4 per-path and 1e-5 per-node parity bars),
+// binary64 the accurate library functions.  expm1 stays accurate: its
+// argument phi L is small, where exp(v) - 1 would cancel.
+__device__ __forceinline__ float rb_exp(float x) { return exp_fast(x); }
+__device__ __forceinline__ double rb_exp(double x) { return exp(x); }
+__device__ __forceinline__ float rb_cos(float x) { return cos_approx(x); }   // |x| <= 1 here
+__device__ __forceinline__ double rb_cos(double x) { return cos(x); }
+__device__ __forceinline__ float rb_sin(float x) { return sin_approx(x); }
+__device__ __forceinline__ double rb_sin(double x) { return sin(x); }
+__device__ __forceinline__ float rb_sinpi(float x) { return sin_approx(3.14159265358979324f * x); }
+__device__ __forceinline__ double rb_sinpi(double x) { return sinpi(x); }
+__device__ __forceinline__ float rb_cospi(float x) { return cos_approx(3.14159265358979324f * x); }
+__device__ __forceinline__ double rb_cospi(double x) { return cospi(x); }
 
 // Outward-normal derivative of the family's exact solution on face j.
 template <class Model> struct RobinData;
 template <> struct RobinData<LaplaceExpCos> {
   template <typename R>
   __device__ static R dudn(int j, const R *x) {
-    const R e = m_exp(x[0]);
-    const R g = (j >> 1) == 0 ? e * m_cos(x[1]) : -e * m_sin(x[1]);
+    const R e = rb_exp(x[0]);
+    const R g = (j >> 1) == 0 ? e * rb_cos(x[1]) : -e * rb_sin(x[1]);
     return (j & 1) ? g : -g;
   }
   template <typename R>
-  __device__ static R u(const R *x) { return m_exp(x[0]) * m_cos(x[1]); }
+  __device__ static R u(const R *x) { return rb_exp(x[0]) * rb_cos(x[1]); }
 };
 template <> struct RobinData<EllipticManufactured> {
   template <typename R>
   __device__ static R dudn(int j, const R *x) {
     constexpr double kPi = 3.14159265358979323846;
     const int k = j >> 1;
-    const R ez = m_exp(x[2]);
+    const R ez = rb_exp(x[2]);
     R g;
-    if (k == 0) g = R(kPi) * m_cospi(x[0]) * m_sinpi(x[1]) * ez;
-    else if (k == 1) g = R(kPi) * m_sinpi(x[0]) * m_cospi(x[1]) * ez;
-    else g = m_sinpi(x[0]) * m_sinpi(x[1]) * ez;
+    if (k == 0) g = R(kPi) * rb_cospi(x[0]) * rb_sinpi(x[1]) * ez;
+    else if (k == 1) g = R(kPi) * rb_sinpi(x[0]) * rb_cospi(x[1]) * ez;
+    else g = rb_sinpi(x[0]) * rb_sinpi(x[1]) * ez;
     return (j & 1) ? g : -g;
   }
   template <typename R>
-  __device__ static R u(const R *x) { return m_sinpi(x[0]) * m_sinpi(x[1]) * m_exp(x[2]); }
+  __device__ static R u(const R *x) { return rb_sinpi(x[0]) * rb_sinpi(x[1]) * rb_exp(x[2]); }
 };
 
 template <typename R> __device__ __forceinline__ R r_exp(R v);
-template <> __device__ __forceinline__ float r_exp<float>(float v) { return expf(v); }
+template <> __device__ __forceinline__ float r_exp<float>(float v) { return exp_fast(v); }
 template <> __device__ __forceinline__ double r_exp<double>(double v) { return exp(v); }
 template <typename R> __device__ __forceinline__ R r_expm1(R v);
 template <> __device__ __forceinline__ float r_expm1<float>(float v) { return expm1f(v); }
 template <> __device__ __forceinline__ double r_expm1<double>(double v) { return expm1(v); }
 template <typename R> __device__ __forceinline__ R r_log(R v);
-template <> __device__ __forceinline__ float r_log<float>(float v) { return logf(v); }
+template <> __device__ __forceinline__ float r_log<float>(float v) {
+  return 0.6931471805599453f * lg2_approx(v);
+}
 template <> __device__ __forceinline__ double r_log<double>(double v) { return log(v); }
+__device__ __forceinline__ float r_sqrt(float v) { return sqrt_approx(fmaxf(v, 0.0f)); }
+__device__ __forceinline__ double r_sqrt(double v) { return sqrt(v); }
+
+// Step constants of the reflecting kernel in the path precision.
+template <typename R>
+struct ReflectConst {
+  R dt, sdt, s2dt, cdt, phi, inv_s2dt;
+  R b2;    // -2 log2(e) / (sigma^2 dt): exp(-2 m / (sigma^2 dt)) = 2^(b2 m)
+  R boff;  // log2(2D) + 2^-12 with the bridge test, -inf without
+};
+
+// Bound on the absorbing faces' crossing probability of a step whose smallest
+// d d' over them is m: P = 1 - prod (1 - p_j) <= sum p_j <= 2D exp(-2 m /
+// (sigma^2 dt)), raised by 2^(2^-12) for the rounding of the exponents.
+__device__ __forceinline__ float reflect_bound(const ReflectConst<float> &k, float m) {
+  return ex2_approx(fmaf(k.b2, m, k.boff));
+}
+__device__ __forceinline__ double reflect_bound(const ReflectConst<double> &k, double m) {
+  return exp2(k.b2 * m + k.boff);
+}
+
+// One step of a reflecting path from X (Z, sphil and n its running sums):
+// the Euler-Maruyama move with normals xi, Lepingle's reflection on the
+// reflecting faces within reach, and the absorbing exit tests with the bridge
+// uniform word wu.  Returns true when the path left through an absorbing
+// face (xe its exit point, Zn its source sum); otherwise X, Z advance.
+template <class Model, typename R>
+__device__ __forceinline__ bool reflect_step(const ReflectArgs &a, const ReflectConst<R> &k,
+                                             const PhiloxPath &pp4, R *X, R &Z, R &sphil,
+                                             int32_t n, const R *xi, uint32_t wu, R *xe, R &Zn) {
+  constexpr int D = Model::D;
+  using G = Box<D>;
+  R b[3] = {R(0), R(0), R(0)}, f = R(0);
+  Model::template coeffs<R>(a.mc, X, b, f);
+  // Y at the step's start; needed every step only with a source term
+  constexpr bool kYStep = Model::kSource;
+  const R Y = kYStep ? r_exp<R>(static_cast<R>(n) * k.cdt + sphil) : R(0);
+  R Xn[3];
+#pragma unroll
+  for (int q = 0; q < D; ++q) Xn[q] = X[q] + b[q] * k.dt + k.sdt * xi[q];
+
+  // ---- reflection on the reflecting faces within reach.  The bridge
+  // minimum is formed for every reflecting face and step (full lanes: paths
+  // linger near these faces, so a branch on reach would run, diverged, at
+  // most warp-steps); only an actual reflection (L > 0) branches.
+  R zr = R(0), yr = Y;
+  bool have_y = kYStep;
+  const uint4 rw = philox10_path(static_cast<uint32_t>(n), pp4, a.rk);  // = Philox((n, p, i, 4))
+#pragma unroll
+  for (int j = 0; j < 2 * D; ++j) {
+    if (!((a.mask >> j) & 1)) continue;
+    const R y0 = G::template face_dist<R>(j, X), y1 = G::template face_dist<R>(j, Xn);
+    const bool reach = R(2) * y0 * y1 * k.inv_s2dt < R(18);
+    const int q = j >> 1;
+    const uint32_t wk = q == 0 ? rw.x : q == 1 ? rw.y : rw.z;
+    const R dy = y1 - y0;
+    const R mn = R(0.5) * (y0 + y1 - r_sqrt(dy * dy - R(2) * k.s2dt * r_log<R>(unif<R>(wk))));
+    const R L = (reach && mn < R(0)) ? -mn : R(0);
+    if (L > R(0)) {
+      if (j & 1) Xn[q] = fmin(Xn[q] - L, R(1));
+      else Xn[q] = fmax(Xn[q] + L, R(0));
+      R xp[3] = {Xn[0], Xn[1], Xn[2]};
+      xp[q] = R(j & 1);
+      const R psi = RobinData<Model>::template dudn<R>(j, xp) - k.phi * RobinData<Model>::template u<R>(xp);
+      if (!have_y) {
+        yr = r_exp<R>(static_cast<R>(n) * k.cdt + sphil);
+        have_y = true;
+      }
+      const R g1 = k.phi != R(0) ? r_expm1<R>(k.phi * L) / k.phi : L;
+      zr += psi * yr * g1;
+      yr *= r_exp<R>(k.phi * L);
+      sphil += k.phi * L;
+    }
+  }
+  Zn = kYStep ? Z + f * Y * k.dt + zr : Z + zr;
+
+  // ---- exit through absorbing faces.  am > 0 puts X' strictly inside the
+  // absorbing faces (the reflecting ones keep it in [0, 1]); above the bound
+  // no absorbing crossing is possible.  Below, the exact tests.
+  R am = R(1);
+#pragma unroll
+  for (int j = 0; j < 2 * D; ++j)
+    if (!((a.mask >> j) & 1))
+      am = fmin(am, G::template face_dist<R>(j, X) * G::template face_dist<R>(j, Xn));
+  const R U = unif<R>(wu);
+  bool out = false;
+  if (!(am > R(0)) || U < reflect_bound(k, am)) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) xe[q] = Xn[q];
+    if (!G::template inside_closed<R>(Xn)) {
+      G::template segment_exit<R>(X, Xn, xe);
+      out = true;
+    } else if (a.bridge) {
+      R P = R(0), pb = R(-1);
+      int jb = -1;
+#pragma unroll
+      for (int j = 0; j < 2 * D; ++j) {
+        if ((a.mask >> j) & 1) continue;
+        const R e = R(2) * G::template face_dist<R>(j, X) * G::template face_dist<R>(j, Xn) * k.inv_s2dt;
+        if (e < R(18)) {
+          const R p = r_exp<R>(-e);
+          P = P + p * (R(1) - P);
+          if (p > pb) {
+            pb = p;
+            jb = j;
+          }
+        }
+      }
+      if (jb >= 0 && U < P) {
+#pragma unroll
+        for (int j = 0; j < 2 * D; ++j)
+          if (j == jb) G::template project<R>(j, xe);
+        out = true;
+      }
+    }
+  }
+  if (out) return true;
+#pragma unroll
+  for (int q = 0; q < D; ++q) X[q] = Xn[q];
+  Z = Zn;
+  return false;
+}
 
 template <class Model, typename R>
 __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_constant__ ReflectArgs a) {
   constexpr int D = Model::D;
   using G = Box<D>;
   const unsigned lane = threadIdx.x & 31u;
-  const R dt = static_cast<R>(a.dt), sdt = static_cast<R>(a.sdt), s2dt = static_cast<R>(a.s2dt);
-  const R cdt = static_cast<R>(a.cdt), phi = static_cast<R>(a.phi);
-  const R inv_s2dt = R(1) / s2dt;
+  ReflectConst<R> k;
+  k.dt = static_cast<R>(a.dt);
+  k.sdt = static_cast<R>(a.sdt);
+  k.s2dt = static_cast<R>(a.s2dt);
+  k.cdt = static_cast<R>(a.cdt);
+  k.phi = static_cast<R>(a.phi);
+  k.inv_s2dt = R(1) / k.s2dt;
+  k.b2 = static_cast<R>(-2.0 * 1.4426950408889634 / a.s2dt);
+  k.boff = a.bridge ? static_cast<R>((D == 2 ? 2.0 : 2.584962500721156) + 2.44140625e-4)
+                    : static_cast<R>(-INFINITY);
   R X[3] = {R(0), R(0), R(0)};
   R Z = R(0), sphil = R(0);  // source sum; phi * (local time so far)
-  PhiloxPath pp{0, 0, 0};
-  uint32_t path = 0, node = 0;
-  uint32_t W[12];
-  R N12[12];
+  PhiloxPath pp{0, 0, 0}, pp4{0, 0, 4u};
   int32_t n = 0;
   uint64_t slot = 0;
   bool active = false, need = true;
@@ -109,11 +251,6 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
   WarpQueue wq;
   NodeCache<R, D> nc;
   const unsigned long long total = a.end - a.begin;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    W[k] = 0;
-    N12[k] = R(0);
-  }
 
   for (;;) {
     while (__any_sync(kFull, need)) {
@@ -122,20 +259,21 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
         slot = q;
         const unsigned long long g = a.begin + q;
         nc.locate(g, a.n_paths, a.end, a.nodes);
-        node = static_cast<uint32_t>(nc.node);
-        path = static_cast<uint32_t>(g - nc.lo + a.path_offset);
+        const uint32_t node = static_cast<uint32_t>(nc.node);
+        const uint32_t path = static_cast<uint32_t>(g - nc.lo + a.path_offset);
         pp = philox_path(path, node, 0u, a.rk);
+        pp4 = philox_path(path, node, 4u, a.rk);
 #pragma unroll
-        for (int k = 0; k < D; ++k) X[k] = nc.x[k];
+        for (int q2 = 0; q2 < D; ++q2) X[q2] = nc.x[q2];
         n = 0;
         Z = R(0);
         sphil = R(0);
         bool on_abs = !G::template inside_closed<R>(X);
         const bool bad = on_abs;
 #pragma unroll
-        for (int k = 0; k < D; ++k)
-          on_abs = on_abs || (X[k] <= R(0) && !((a.mask >> (2 * k)) & 1)) ||
-                   (X[k] >= R(1) && !((a.mask >> (2 * k + 1)) & 1));
+        for (int q2 = 0; q2 < D; ++q2)
+          on_abs = on_abs || (X[q2] <= R(0) && !((a.mask >> (2 * q2)) & 1)) ||
+                   (X[q2] >= R(1) && !((a.mask >> (2 * q2 + 1)) & 1));
         if (bad) {
           score[slot] = R(NAN);
           if (a.steps) a.steps[slot] = 0;
@@ -153,129 +291,37 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
     if (!__any_sync(kFull, active)) break;
     if (!active) continue;
 
-    // ---- normals and the bridge uniform (stream layout of the path kernel)
-    R xi[3] = {R(0), R(0), R(0)};
-    uint32_t wu;
-    if constexpr (D <= 2) {
-      const uint4 w = philox10_path(static_cast<uint32_t>(n), pp, a.rk);
-      box_muller<R>(w.x, w.y, xi[0], xi[1]);
-      if (D == 1) xi[1] = R(0);
-      wu = w.z;
-    } else {
-      const int jj = n & 3;
-      if (jj == 0) {
-        const uint32_t q3 = 3u * static_cast<uint32_t>(n >> 2);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const uint4 w = philox10_path(q3 + b, pp, a.rk);
-          W[4 * b] = w.x;
-          W[4 * b + 1] = w.y;
-          W[4 * b + 2] = w.z;
-          W[4 * b + 3] = w.w;
-        }
-#pragma unroll
-        for (int p2 = 0; p2 < 6; ++p2) box_muller<R>(W[2 * p2], W[2 * p2 + 1], N12[2 * p2], N12[2 * p2 + 1]);
+    // ---- one unit: up to four steps, random numbers formed up front (the
+    // stream layout of the path kernel).  The step loop is not unrolled: each
+    // step carries the accurate special functions of its rare branches, and
+    // four inlined copies ran 1.5x slower.
+    R z[4 * D];
+    uint32_t u[4];
+    unit_randoms<D, R>(n, pp, a.rk, z, u);
+    bool out = false, capped = false;
+    R xe[3] = {R(0), R(0), R(0)}, Zn = R(0);
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      out = reflect_step<Model, R>(a, k, pp4, X, Z, sphil, n, z, u[0], xe, Zn);
+      ++n;
+      if (out) break;
+      if (n >= a.max_steps) {
+        capped = true;
+        break;
       }
-      uint32_t w0, w1, w2;
-      switch (jj) {
-        case 0: xi[0] = N12[0]; xi[1] = N12[1]; xi[2] = N12[2]; w0 = W[0]; w1 = W[1]; w2 = W[2]; break;
-        case 1: xi[0] = N12[3]; xi[1] = N12[4]; xi[2] = N12[5]; w0 = W[3]; w1 = W[4]; w2 = W[5]; break;
-        case 2: xi[0] = N12[6]; xi[1] = N12[7]; xi[2] = N12[8]; w0 = W[6]; w1 = W[7]; w2 = W[8]; break;
-        default: xi[0] = N12[9]; xi[1] = N12[10]; xi[2] = N12[11]; w0 = W[9]; w1 = W[10]; w2 = W[11]; break;
-      }
-      wu = ((w2 & 255u) << 24) | ((w1 & 255u) << 16) | ((w0 & 255u) << 8);
+#pragma unroll
+      for (int i = 0; i < 3 * D; ++i) z[i] = z[i + D];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[i] = u[i + 1];
     }
-
-    // ---- Euler-Maruyama step (left point)
-    R b[3] = {R(0), R(0), R(0)}, f = R(0);
-    Model::template coeffs<R>(a.mc, X, b, f);
-    // Y at the step's start; needed every step only with a source term
-    constexpr bool kYStep = Model::kSource;
-    const R Y = kYStep ? r_exp<R>(static_cast<R>(n) * cdt + sphil) : R(0);
-    R Xn[3];
-#pragma unroll
-    for (int k = 0; k < D; ++k) Xn[k] = X[k] + b[k] * dt + sdt * xi[k];
-
-    // ---- reflection on reflecting faces within reach
-    R yr = Y, zr = R(0);
-    bool have_y = kYStep;
-    bool have_r = false;
-    uint4 rw = make_uint4(0, 0, 0, 0);
-#pragma unroll
-    for (int j = 0; j < 2 * D; ++j) {
-      if (!((a.mask >> j) & 1)) continue;
-      const R y0 = G::template face_dist<R>(j, X), y1 = G::template face_dist<R>(j, Xn);
-      if (R(2) * y0 * y1 * inv_s2dt >= R(18)) continue;
-      if (!have_r) {
-        rw = philox10(static_cast<uint32_t>(n), path, node, 4u, a.rk);
-        have_r = true;
-      }
-      const int k = j >> 1;
-      const uint32_t wk = k == 0 ? rw.x : k == 1 ? rw.y : rw.z;
-      const R dy = y1 - y0;
-      const R mn = R(0.5) * (y0 + y1 - m_sqrt(dy * dy - R(2) * s2dt * r_log<R>(unif<R>(wk))));
-      const R L = mn < R(0) ? -mn : R(0);
-      if (L > R(0)) {
-        if (j & 1) Xn[k] = fmin(Xn[k] - L, R(1));
-        else Xn[k] = fmax(Xn[k] + L, R(0));
-        R xp[3] = {Xn[0], Xn[1], Xn[2]};
-        xp[k] = R(j & 1);
-        const R psi = RobinData<Model>::template dudn<R>(j, xp) - phi * RobinData<Model>::template u<R>(xp);
-        if (!have_y) {
-          yr = r_exp<R>(static_cast<R>(n) * cdt + sphil);
-          have_y = true;
-        }
-        const R g1 = phi != R(0) ? r_expm1<R>(phi * L) / phi : L;
-        zr += psi * yr * g1;
-        yr *= r_exp<R>(phi * L);
-        sphil += phi * L;
-      }
-    }
-    const R Zn = kYStep ? Z + f * Y * dt + zr : Z + zr;
-
-    // ---- exit through absorbing faces
-    bool out = false;
-    R xe[3] = {Xn[0], Xn[1], Xn[2]};
-    if (!G::template inside_closed<R>(Xn)) {
-      G::template segment_exit<R>(X, Xn, xe);
-      out = true;
-    } else if (a.bridge) {
-      R P = R(0), pb = R(-1);
-      int jb = -1;
-#pragma unroll
-      for (int j = 0; j < 2 * D; ++j) {
-        if ((a.mask >> j) & 1) continue;
-        const R e = R(2) * G::template face_dist<R>(j, X) * G::template face_dist<R>(j, Xn) * inv_s2dt;
-        if (e < R(18)) {
-          const R p = r_exp<R>(-e);
-          P = P + p * (R(1) - P);
-          if (p > pb) {
-            pb = p;
-            jb = j;
-          }
-        }
-      }
-      if (jb >= 0 && unif<R>(wu) < P) {
-#pragma unroll
-        for (int j = 0; j < 2 * D; ++j)
-          if (j == jb) G::template project<R>(j, xe);
-        out = true;
-      }
-    }
-    ++n;
     if (out) {
-      const R Yn = r_exp<R>(static_cast<R>(n) * cdt + sphil);  // n already advanced
+      const R Yn = r_exp<R>(static_cast<R>(n) * k.cdt + sphil);  // n already advanced
       score[slot] = Model::template g<R>(a.mc, xe) * Yn + Zn;
       if (a.steps) a.steps[slot] = n;
       my_steps += static_cast<unsigned long long>(n);
       active = false;
       need = true;
-      continue;
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) X[k] = Xn[k];
-    Z = Zn;
-    if (n >= a.max_steps) {
+    } else if (capped) {
       // cap: score at the projection on the nearest absorbing face
       int jn = -1;
       R dn = R(1e30);
@@ -292,8 +338,8 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
 #pragma unroll
       for (int j = 0; j < 2 * D; ++j)
         if (j == jn) G::template project<R>(j, xc);
-      const R Yn = r_exp<R>(static_cast<R>(n) * cdt + sphil);
-      score[slot] = Model::template g<R>(a.mc, xc) * Yn + Zn;
+      const R Yn = r_exp<R>(static_cast<R>(n) * k.cdt + sphil);
+      score[slot] = Model::template g<R>(a.mc, xc) * Yn + Z;
       if (a.steps) a.steps[slot] = -n;
       my_steps += static_cast<unsigned long long>(n);
       ++my_capped;
@@ -302,10 +348,10 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
     }
   }
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) {
-    my_steps += __shfl_xor_sync(kFull, my_steps, s);
-    my_capped += __shfl_xor_sync(kFull, my_capped, s);
-    my_bad += __shfl_xor_sync(kFull, my_bad, s);
+  for (int s2 = 16; s2 > 0; s2 >>= 1) {
+    my_steps += __shfl_xor_sync(kFull, my_steps, s2);
+    my_capped += __shfl_xor_sync(kFull, my_capped, s2);
+    my_bad += __shfl_xor_sync(kFull, my_bad, s2);
   }
   if (lane == 0) {
     if (my_steps) atomicAdd(&a.counters[0], my_steps);
