@@ -310,6 +310,27 @@ struct LShape {
     const R da = R(0.5) - a;
     return m_sqrt(da * da + b * b);
   }
+  // Lower bound on the smallest face_dist(j, x0) * face_dist(j, x1) over the
+  // six faces (x0 in the closed domain), without square roots: the sides'
+  // products are exact; a notch edge's distance to a point beside it
+  // (a < 1/2), sqrt(da^2 + b^2), is bounded below by max(da, |b|), and is b
+  // itself beyond it.  A result > 0 puts x1 inside the closed domain: a
+  // point in the notch has b < 0 on the edge y = 1/2 (face 4), whose product
+  // with x0's nonnegative bound is then <= 0.
+  template <typename R>
+  __device__ __forceinline__ static R notch_dist_lb(int j, const R *x) {
+    const R a = j == 4 ? x[0] : x[1];
+    const R b = R(0.5) - (j == 4 ? x[1] : x[0]);
+    return a >= R(0.5) ? b : fmax(R(0.5) - a, fabs(b));
+  }
+  template <typename R>
+  __device__ __forceinline__ static R screen_lb(const R *x0, const R *x1) {
+    const R s0 = x0[0] * x1[0], s1 = (R(1) - x0[0]) * (R(1) - x1[0]);
+    const R s2 = x0[1] * x1[1], s3 = (R(1) - x0[1]) * (R(1) - x1[1]);
+    const R n4 = notch_dist_lb<R>(4, x0) * notch_dist_lb<R>(4, x1);
+    const R n5 = notch_dist_lb<R>(5, x0) * notch_dist_lb<R>(5, x1);
+    return fmin(min3(s0, s1, s2), min3(s3, n4, n5));
+  }
   template <typename R>
   __device__ __forceinline__ static void project(int j, R *x) {
     if (j < 4) {

@@ -55,6 +55,10 @@ struct PathArgs {
 // over 500 steps); the FP32 path therefore evaluates Y_n from n directly
 // (exp2 of n c dt log2 e, a few ulp, no accumulation).  In FP64 the
 // recurrence is accurate to n ulp and is kept.
+// log2 of a face count (the union bound's factor), counts 1 .. 6.
+constexpr float kLog2Count[7] = {0.0f, 0.0f, 1.0f, 1.5849625007211562f, 2.0f,
+                                 2.321928094887362f, 2.584962500721156f};
+
 template <typename R> struct StepConst;
 template <> struct StepConst<float> {
   float dt, sdt, thr, l2cdt, inv_s2dt;
@@ -75,7 +79,7 @@ template <> struct StepConst<float> {
   // probabilities above 2^-26 that a uniform can fall below).  0 without the
   // bridge test.
   template <int D> __device__ __forceinline__ float cross_bound(float m) const {
-    constexpr float kOff = (D == 1 ? 0.0f : D == 2 ? 1.0f : 1.5849625007211562f) + 2.44140625e-4f;
+    constexpr float kOff = kLog2Count[D] + 2.44140625e-4f;
     return ex2_approx(fmaf(b2, m, kOff + boff));
   }
   __device__ __forceinline__ float kill(float, int32_t n_next) const {
@@ -244,11 +248,17 @@ __device__ __forceinline__ int em_step(const Env &a, const StepConst<R> &k, R *X
   Y = Yn;
   Z = Zn;
   if constexpr (!Geom::kFastScreen) {
-    if (!Geom::inside_closed(Xn)) return kStepHardExit;
-    // general domains: every face within reach, P = 1 - prod (1 - p_j)
-    if (a.bridge) {
-      const int jbest = bridge_generic<Geom, R>(k, X, Xn, unif<R>(uw));
-      if (jbest >= 0) return jbest;
+    // general domains: a lower bound on the smallest d d' (> 0: X' inside)
+    // and the union bound over all faces screen the step; below the bound,
+    // the exact tests (every face within reach, P = 1 - prod (1 - p_j))
+    const R mnb = Geom::screen_lb(X, Xn);
+    const R U = unif<R>(uw);
+    if (!(mnb > R(0)) || U < k.template cross_bound<Geom::kFaces>(mnb)) {
+      if (!Geom::inside_closed(Xn)) return kStepHardExit;
+      if (a.bridge) {
+        const int jbest = bridge_generic<Geom, R>(k, X, Xn, U);
+        if (jbest >= 0) return jbest;
+      }
     }
   } else {
     const R mn = Geom::screen_mn(X, Xn);
