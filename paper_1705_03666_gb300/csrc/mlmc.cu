@@ -41,52 +41,82 @@ struct MlmcArgs {
   ModelConst mc;
 };
 
+// Constants of one walk's step: length dt, sigma, 1 / (sigma^2 dt) and the
+// screening bound's exponent scale -2 log2(e) / (sigma^2 dt) and offset
+// (log2 of the face count + 2^-12 with the bridge test, -inf without).
+template <typename R>
+struct MlmcStep {
+  R dt, sig, inv, b2, boff;
+};
+template <typename R>
+__device__ __forceinline__ MlmcStep<R> mlmc_step_const(double dt, double s2, int faces, bool bridge) {
+  MlmcStep<R> c;
+  c.dt = static_cast<R>(dt);
+  c.sig = static_cast<R>(sqrt(s2));
+  c.inv = R(1) / (static_cast<R>(s2) * c.dt);
+  c.b2 = static_cast<R>(-2.0 * 1.4426950408889634 / (s2 * dt));
+  c.boff = bridge ? static_cast<R>(log2(static_cast<double>(faces)) + 2.44140625e-4)
+                  : static_cast<R>(-INFINITY);
+  return c;
+}
+// Bound on the step's crossing probability over all faces (the union bound
+// at the smallest d d' m, raised by 2^(2^-12) for the exponents' rounding).
+__device__ __forceinline__ float mlmc_bound(const MlmcStep<float> &c, float m) {
+  return ex2_approx(fmaf(c.b2, m, c.boff));
+}
+__device__ __forceinline__ double mlmc_bound(const MlmcStep<double> &c, double m) {
+  return exp2(c.b2 * m + c.boff);
+}
+
 template <class Model, class Geom, typename R>
 struct MlmcWalk {
   R X[2], Y, Z, s;
   bool done;
 
-  // one Euler step of length dt with the (unscaled-by-sigma) increment dW
-  __device__ __forceinline__ void step(const MlmcArgs &a, R dt, const R *dW, R U) {
+  // One Euler step with the (unscaled-by-sigma) increment dW.  A lower bound
+  // on the smallest d d' (> 0: X' inside) and the union bound screen the
+  // step; below the bound, the exact tests.
+  __device__ __forceinline__ void step(const MlmcArgs &a, const MlmcStep<R> &c, const R *dW, R U) {
     constexpr int D = Model::D;
-    const R sig = static_cast<R>(sqrt(a.s2));
     R b[2] = {R(0), R(0)}, f = R(0);
     if constexpr (Model::kDrift || Model::kSource) Model::coeffs(a.mc, X, b, f);
     R Xn[2] = {X[0], X[1]};
 #pragma unroll
-    for (int k = 0; k < D; ++k) Xn[k] = X[k] + b[k] * dt + sig * dW[k];
-    const R Zn = Model::kSource ? Z + f * Y * dt : Z;
-    if (!Geom::inside_closed(Xn)) {
-      R xe[2];
-      Geom::segment_exit(X, Xn, xe);
-      s = Model::g(a.mc, xe) * Y + Zn;
-      done = true;
-      return;
-    }
-    if (a.bridge) {
-      const R inv = R(1) / (static_cast<R>(a.s2) * dt);
-      R P = R(0), pb = R(-1);
-      int jb = -1;
-#pragma unroll
-      for (int j = 0; j < Geom::kFaces; ++j) {
-        const R e = R(2) * Geom::face_dist(j, X) * Geom::face_dist(j, Xn) * inv;
-        if (e < R(18)) {
-          const R p = exp_fast(-e);
-          P = P + p * (R(1) - P);
-          if (p > pb) {
-            pb = p;
-            jb = j;
-          }
-        }
-      }
-      if (jb >= 0 && U < P) {
-        R xe[2] = {Xn[0], Xn[1]};
-#pragma unroll
-        for (int j = 0; j < Geom::kFaces; ++j)
-          if (j == jb) Geom::project(j, xe);
+    for (int k = 0; k < D; ++k) Xn[k] = X[k] + b[k] * c.dt + c.sig * dW[k];
+    const R Zn = Model::kSource ? Z + f * Y * c.dt : Z;
+    const R mn = Geom::screen_lb(X, Xn);
+    if (!(mn > R(0)) || U < mlmc_bound(c, mn)) {
+      if (!Geom::inside_closed(Xn)) {
+        R xe[2];
+        Geom::segment_exit(X, Xn, xe);
         s = Model::g(a.mc, xe) * Y + Zn;
         done = true;
         return;
+      }
+      if (a.bridge) {
+        R P = R(0), pb = R(-1);
+        int jb = -1;
+#pragma unroll
+        for (int j = 0; j < Geom::kFaces; ++j) {
+          const R e = R(2) * Geom::face_dist(j, X) * Geom::face_dist(j, Xn) * c.inv;
+          if (e < R(18)) {
+            const R p = exp_fast(-e);
+            P = P + p * (R(1) - P);
+            if (p > pb) {
+              pb = p;
+              jb = j;
+            }
+          }
+        }
+        if (jb >= 0 && U < P) {
+          R xe[2] = {Xn[0], Xn[1]};
+#pragma unroll
+          for (int j = 0; j < Geom::kFaces; ++j)
+            if (j == jb) Geom::project(j, xe);
+          s = Model::g(a.mc, xe) * Y + Zn;
+          done = true;
+          return;
+        }
       }
     }
     X[0] = Xn[0];
@@ -109,13 +139,16 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
   constexpr int D = Model::D;
   const unsigned lane = threadIdx.x & 31u;
   R *out = static_cast<R *>(a.score);
-  const R dtf = static_cast<R>(a.dtf), sdtf = static_cast<R>(a.sdtf);
-  const R dtc = dtf * static_cast<R>(a.refine);
+  const R sdtf = static_cast<R>(a.sdtf);
+  const MlmcStep<R> cf = mlmc_step_const<R>(a.dtf, a.s2, Geom::kFaces, a.bridge != 0);
+  const MlmcStep<R> cc = mlmc_step_const<R>(static_cast<double>(static_cast<R>(a.dtf) *
+                                                                static_cast<R>(a.refine)),
+                                            a.s2, Geom::kFaces, a.bridge != 0);
   MlmcWalk<Model, Geom, R> fw, cw;
   R dWc[2] = {R(0), R(0)};
   PhiloxPath pp{0, 0, 0};
   uint64_t slot = 0;
-  int32_t k = 0;
+  int32_t k = 0, kc = 0;  // fine steps; fine steps since the last coarse step
   bool active = false, need = true;
   unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
   WarpQueue wq;
@@ -141,6 +174,7 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
           cw.done = a.level == 0;
           dWc[0] = dWc[1] = R(0);
           k = 0;
+          kc = 0;
           if (!Geom::inside_closed(fw.X)) {
             out[slot] = out[a.wave + slot] = out[2 * a.wave + slot] = R(NAN);
             if (a.steps) a.steps[slot] = 0;
@@ -168,13 +202,14 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
     box_muller<R>(w.x, w.y, z0, z1);
     const R dW[2] = {sdtf * z0, D > 1 ? sdtf * z1 : R(0)};
     const R U = unif<R>(w.z);
-    if (!fw.done) fw.step(a, dtf, dW, U);
+    if (!fw.done) fw.step(a, cf, dW, U);
     dWc[0] += dW[0];
     dWc[1] += dW[1];
     ++k;
-    if (a.level > 0 && k % a.refine == 0) {
-      if (!cw.done) cw.step(a, dtc, dWc, U);
+    if (a.level > 0 && ++kc == a.refine) {
+      if (!cw.done) cw.step(a, cc, dWc, U);
       dWc[0] = dWc[1] = R(0);
+      kc = 0;
     }
     bool finish = fw.done && cw.done;
     if (!finish && k >= a.max_steps) {

@@ -209,6 +209,12 @@ struct Box {
     else if constexpr (D == 2) return fmin(min3(p[0], p[1], p[2]), p[3]);
     else return fmin(min3(p[0], p[1], p[2]), min3(p[3], p[4], p[5]));
   }
+  // The exact smallest d d' is also the lower bound general callers screen
+  // with (LShape::screen_lb).
+  template <typename R>
+  __device__ __forceinline__ static R screen_lb(const R *x0, const R *x1) {
+    return screen_mn<R>(x0, x1);
+  }
   // Second smallest of m[0..D-1] (D <= 3): below the reach threshold means
   // the step is within reach of two faces (an edge or a corner).
   template <typename R>
