@@ -149,9 +149,10 @@ PDD_API pdd_status pdd_set_stream(pdd_ctx *ctx, void *cuda_stream);
  * and, if non-NULL, d_npaths[n] (int64).  A node on the boundary gets
  * u = g(x_i) with zero error.  Path i of node j uses the Philox stream
  * (key = seed, counter = (block, path_offset + i, j, 0)); the per-step use of
- * that stream is fixed (2-D: one block per step, normals from words 0-1 by
- * Box-Muller, bridge uniform from word 2; 3-D: three blocks per four steps,
- * normals from the word pairs, bridge uniforms from the words' low bytes).
+ * that stream is fixed: three blocks per four steps (2-D: step 4q+j takes
+ * its normals from words 2j, 2j+1 of blocks 3q..3q+2 by Box-Muller and its
+ * bridge uniform from word 8+j; 3-D: normals from the word pairs, bridge
+ * uniforms from the words' low bytes).
  * With diag non-NULL the call synchronises and returns PDD_ECAP if some path
  * hit max_steps, PDD_EINVAL if a node lies outside the closed domain (its
  * mean is NaN either way).                                                 */

@@ -423,12 +423,12 @@ static int nearest_face(int geom, int dim, const double *x) {
 /*                                                                          */
 /* Stream layout: word k of path p of node i is word (k mod 4) of            */
 /*   Philox4x32-10(key = (seed lo, seed hi), ctr = (k div 4, p, i, 0)).      */
-/* Step n draws d normals xi_n and one uniform U_n:                          */
-/*   d = 1: xi = BM(w[4n], w[4n+1]).first,          U = w[4n+2]              */
-/*   d = 2: xi = BM(w[4n], w[4n+1]),                U = w[4n+2]              */
-/*   d = 3, n = 4q + j: blocks 3q..3q+2 give words v0..v11 and normals     */
-/*                    z0..z11 = BM(v0,v1), ..., BM(v10,v11); xi = z[3j..3j+2], */
-/*                    U from the low bytes of v[3j], v[3j+1], v[3j+2]        */
+/* Step n = 4q + j draws d normals xi_n and one uniform U_n from the twelve  */
+/* words v0..v11 of blocks 3q, 3q+1, 3q+2:                                  */
+/*   d = 1: xi = BM(v[2j], v[2j+1]).first,          U = v[8+j]               */
+/*   d = 2: xi = BM(v[2j], v[2j+1]),                U = v[8+j]               */
+/*   d = 3: normals z0..z11 = BM(v0,v1), ..., BM(v10,v11); xi = z[3j..3j+2], */
+/*          U from the low bytes of v[3j], v[3j+1], v[3j+2]                  */
 /*                                                                          */
 /* Step n -> n+1 (left-point rule for Y and Z, Eq. 2.8):                     */
 /*   X' = X + b(X) dt + sigma sqrt(dt) xi,  Y' = Y exp(c(X) dt),             */
@@ -498,18 +498,27 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
     if (xexit) for (int k = 0; k < 3; ++k) xexit[k] = X[k];
     return;
   }
-  uint32_t A[4] = {0, 0, 0, 0}, W12[12];
+  uint32_t W12[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   double N12[12];
   for (int64_t n = 0; n < M->max_steps; ++n) {
     double xi[3] = {0, 0, 0}, U;
     if (dim <= 2) {
-      uint32_t ctr[4] = {(uint32_t)n, path, node, 0u};
-      orc_philox4x32_10(ctr, key, A);
+      /* d = 1, 2: steps 4q .. 4q+3 use the 12 words w[0..11] of blocks 3q,
+       * 3q+1, 3q+2; step 4q+j takes the normals BM(w[2j], w[2j+1]) (d = 1:
+       * the first) and the uniform of w[8+j].                             */
+      uint32_t q = (uint32_t)(n >> 2);
+      int j = (int)(n & 3);
+      if (j == 0) {
+        for (int b = 0; b < 3; ++b) {
+          uint32_t cb[4] = {3u * q + (uint32_t)b, path, node, 0u};
+          orc_philox4x32_10(cb, key, W12 + 4 * b);
+        }
+      }
       double z0, z1;
-      box_muller(A[0], A[1], &z0, &z1);
+      box_muller(W12[2 * j], W12[2 * j + 1], &z0, &z1);
       xi[0] = z0;
       if (dim == 2) xi[1] = z1;
-      U = unif(A[2]);
+      U = unif(W12[8 + j]);
     } else {
       /* d = 3: steps 4q .. 4q+3 use the 12 words w[0..11] of blocks 3q,
        * 3q+1, 3q+2; normals nrm[0..11] = Box-Muller of the word pairs

@@ -326,12 +326,14 @@ __device__ __forceinline__ uint32_t low_bytes_word(uint32_t a, uint32_t b, uint3
   return __byte_perm(__byte_perm(a, b, 0x0400u), c, 0x4210u);
 }
 
-// Random numbers of the four-step unit that starts at step n (in 3-D n is a
-// multiple of 4): normals z[D j .. D j + D - 1] and the bridge-uniform word
-// u[j] of step n + j.  d <= 2: step n + j from Philox block n + j (normals
-// BM(w0, w1), uniform word w2).  d = 3: blocks 3q, 3q+1, 3q+2 for q = n / 4:
-// normals z0..z11 = BM of the word pairs (w0,w1) .. (w10,w11), step 4q + j
-// takes z[3j..3j+2] and low_bytes_word(w[3j], w[3j+1], w[3j+2]).
+// Random numbers of the four-step unit that starts at step n = 4q: normals
+// z[D j .. D j + D - 1] and the bridge-uniform word u[j] of step n + j, from
+// the twelve words w0..w11 of Philox blocks 3q, 3q+1, 3q+2.  d <= 2: step
+// 4q + j takes BM(w[2j], w[2j+1]) (d = 1: the first) and the uniform word
+// w[8+j].  d = 3: normals z0..z11 = BM of the word pairs (w0,w1) ..
+// (w10,w11), step 4q + j takes z[3j..3j+2] and low_bytes_word(w[3j],
+// w[3j+1], w[3j+2]).  Either way 0.75 blocks per step, the least that holds
+// the step's normals and a 23-bit uniform.
 template <int D, typename R>
 __device__ __forceinline__ void unit_randoms(int32_t n, const PhiloxPath &pp, const RoundKeys &rk,
                                              R *z, uint32_t *u) {
@@ -351,14 +353,21 @@ __device__ __forceinline__ void unit_randoms(int32_t n, const PhiloxPath &pp, co
     u[2] = low_bytes_word(B.z, B.w, C.x);
     u[3] = low_bytes_word(C.y, C.z, C.w);
   } else {
+    const uint32_t q3 = 3u * (static_cast<uint32_t>(n) >> 2);
+    const uint4 A = philox10_path(q3, pp, rk);
+    const uint4 B = philox10_path(q3 + 1u, pp, rk);
+    const uint4 C = philox10_path(q3 + 2u, pp, rk);
+    const uint32_t w[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const uint4 A = philox10_path(static_cast<uint32_t>(n) + static_cast<uint32_t>(j), pp, rk);
       R z1;
-      box_muller<R>(A.x, A.y, z[D * j], z1);
+      box_muller<R>(w[2 * j], w[2 * j + 1], z[D * j], z1);
       if constexpr (D == 2) z[D * j + 1] = z1;
-      u[j] = A.z;
     }
+    u[0] = C.x;
+    u[1] = C.y;
+    u[2] = C.z;
+    u[3] = C.w;
   }
 }
 
