@@ -416,25 +416,36 @@ struct GradRec {
   float L[kMaxLR];
 };
 
-// Result of one path: its score (forward mode) or its gradient record.
+// Result of one path, in two parts: the score (forward mode: the score
+// plane; gradient mode: the record's first four words, score and exit point)
+// with the step count, and, in gradient mode, the likelihood-ratio sums.
 template <int D, typename R, bool kLR>
-__device__ __forceinline__ void write_result(const PathArgs &a, uint64_t slot, R s, int32_t st,
-                                             const R *xe, const R *L) {
+__device__ __forceinline__ void write_score(const PathArgs &a, uint64_t slot, R s, int32_t st,
+                                            const R *xe) {
   if constexpr (kLR) {
-    GradRec *rec = static_cast<GradRec *>(a.score) + slot;
-    float4 *o = reinterpret_cast<float4 *>(rec);
+    float4 *o = reinterpret_cast<float4 *>(static_cast<GradRec *>(a.score) + slot);
     o[0] = make_float4(static_cast<float>(s), static_cast<float>(xe[0]),
                        D > 1 ? static_cast<float>(xe[D > 1 ? 1 : 0]) : 0.f,
                        D > 2 ? static_cast<float>(xe[D > 2 ? 2 : 0]) : 0.f);
-    const float c = a.lr_scale;
-#pragma unroll
-    for (int q = 0; q < kMaxLR / 4; ++q)
-      o[1 + q] = make_float4(c * static_cast<float>(L[4 * q]), c * static_cast<float>(L[4 * q + 1]),
-                             c * static_cast<float>(L[4 * q + 2]), c * static_cast<float>(L[4 * q + 3]));
   } else {
     static_cast<R *>(a.score)[slot] = s;
   }
   if (a.steps) a.steps[slot] = st;
+}
+template <typename R>
+__device__ __forceinline__ void write_lr_sums(const PathArgs &a, uint64_t slot, const R *L) {
+  float4 *o = reinterpret_cast<float4 *>(static_cast<GradRec *>(a.score) + slot);
+  const float c = a.lr_scale;
+#pragma unroll
+  for (int q = 0; q < kMaxLR / 4; ++q)
+    o[1 + q] = make_float4(c * static_cast<float>(L[4 * q]), c * static_cast<float>(L[4 * q + 1]),
+                           c * static_cast<float>(L[4 * q + 2]), c * static_cast<float>(L[4 * q + 3]));
+}
+template <int D, typename R, bool kLR>
+__device__ __forceinline__ void write_result(const PathArgs &a, uint64_t slot, R s, int32_t st,
+                                             const R *xe, const R *L) {
+  write_score<D, R, kLR>(a, slot, s, st, xe);
+  if constexpr (kLR) write_lr_sums<R>(a, slot, L);
 }
 
 // Per-warp staging in shared memory (one column per lane).  Claiming and
@@ -457,14 +468,10 @@ struct ExitQueue {
   int32_t st[32], code[32];     // step count (or -max_steps) and exit code
   R x[D][32], xn[D][32], y[32], z[32];
 };
-template <int D, typename R, bool kQueue>
+template <int D, typename R>
 struct PathStage {
   StartStash<D, R> start;
   ExitQueue<D, R> exit;
-};
-template <int D, typename R>
-struct PathStage<D, R, false> {
-  StartStash<D, R> start;
 };
 
 // Exit code of a path stopped by the step cap: scored at the projection of
@@ -529,8 +536,9 @@ __device__ __forceinline__ int stage_starts(const PathArgs &a, StartStash<Model:
 }
 
 // Called by all 32 lanes: score the first cnt parked paths, one per lane, and
-// write their results.
-template <class Model, class Geom, typename R>
+// write their scores (gradient mode: the record's score and exit point; the
+// likelihood-ratio sums were written when the path ended).
+template <class Model, class Geom, typename R, bool kLR>
 __device__ __forceinline__ void flush_exits(const PathArgs &a, ExitQueue<Model::D, R> &q, int cnt) {
   constexpr int D = Model::D;
   const int lane = static_cast<int>(threadIdx.x & 31u);
@@ -552,8 +560,7 @@ __device__ __forceinline__ void flush_exits(const PathArgs &a, ExitQueue<Model::
     } else {
       s = exit_score<Model, Geom, R>(a.mc, code, X, Xn, q.y[lane], q.z[lane], xe);
     }
-    R L0[1] = {R(0)};
-    write_result<D, R, false>(a, q.slot[lane], s, q.st[lane], xe, L0);
+    write_score<D, R, kLR>(a, q.slot[lane], s, q.st[lane], xe);
   }
   __syncwarp();
 }
@@ -563,8 +570,8 @@ __global__ void __launch_bounds__(kPathBlock)
 path_kernel(const __grid_constant__ PathArgs a) {
   constexpr int D = Model::D;
   constexpr int NL = kLR ? kMaxLR : 1;
-  __shared__ PathStage<D, R, !kLR> stage_all[kPathBlock / 32];
-  PathStage<D, R, !kLR> &stage = stage_all[threadIdx.x >> 5];
+  __shared__ PathStage<D, R> stage_all[kPathBlock / 32];
+  PathStage<D, R> &stage = stage_all[threadIdx.x >> 5];
   R L[NL];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -631,53 +638,35 @@ path_kernel(const __grid_constant__ PathArgs a) {
       }
     }
 
-    // ---- ended paths
-    if constexpr (kLR) {
+    // ---- ended paths: parked, and scored 32 at a time (gradient mode writes
+    // the likelihood-ratio sums at once)
+    const unsigned dm = __ballot_sync(kFull, done);
+    if (dm) {
+      const int nd = __popc(dm);
+      if (n_exit + nd > 32) {
+        flush_exits<Model, Geom, R, kLR>(a, stage.exit, n_exit);
+        n_exit = 0;
+      }
       if (done) {
-        R xe[D], s;
-        int32_t st = n;
-        if (code == kStepCapped) {
+        if constexpr (kLR) write_lr_sums<R>(a, slot, L);
+        const int e = n_exit + __popc(dm & lt_mask);
+        ExitQueue<D, R> &q = stage.exit;
+        q.slot[e] = slot;
+        q.st[e] = code == kStepCapped ? -a.max_steps : n;
+        q.code[e] = code;
 #pragma unroll
-          for (int d = 0; d < D; ++d) xe[d] = X[d];
-          Geom::project(Geom::nearest_face(X), xe);
-          s = Model::g(a.mc, xe) * Y + Z;
-          st = -a.max_steps;
-        } else {
-          s = exit_score<Model, Geom, R>(a.mc, code, X, Xn, Y, Z, xe);
+        for (int d = 0; d < D; ++d) {
+          q.x[d][e] = X[d];
+          q.xn[d][e] = Xn[d];
         }
-        write_result<D, R, true>(a, slot, s, st, xe, L);
+        q.y[e] = Y;
+        q.z[e] = Z;
         active = false;
       }
-    } else {
-      const unsigned dm = __ballot_sync(kFull, done);
-      if (dm) {
-        const int nd = __popc(dm);
-        if (n_exit + nd > 32) {
-          flush_exits<Model, Geom, R>(a, stage.exit, n_exit);
-          n_exit = 0;
-        }
-        if (done) {
-          const int e = n_exit + __popc(dm & lt_mask);
-          ExitQueue<D, R> &q = stage.exit;
-          q.slot[e] = slot;
-          q.st[e] = code == kStepCapped ? -a.max_steps : n;
-          q.code[e] = code;
-#pragma unroll
-          for (int d = 0; d < D; ++d) {
-            q.x[d][e] = X[d];
-            q.xn[d][e] = Xn[d];
-          }
-          q.y[e] = Y;
-          q.z[e] = Z;
-          active = false;
-        }
-        n_exit += nd;
-      }
+      n_exit += nd;
     }
   }
-  if constexpr (!kLR) {
-    if (n_exit > 0) flush_exits<Model, Geom, R>(a, stage.exit, n_exit);
-  }
+  if (n_exit > 0) flush_exits<Model, Geom, R, kLR>(a, stage.exit, n_exit);
 
   // ---- per-warp totals
 #pragma unroll
