@@ -214,9 +214,9 @@ __device__ __forceinline__ double min3(double a, double b, double c) { return fm
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1) {
   // hardware log2 (absolute error ~2^-22 near u = 1, where it may return 0
-  // or a tiny positive value: y is clamped at 0) and hardware square root
-  const float y = fmaxf(-1.3862943611198906f * lg2_approx(unif_f(a)), 0.0f);
-  const float mr = -sqrt_approx(y);
+  // or a tiny positive value: its magnitude is taken, an operand modifier
+  // rather than a clamp) and hardware square root
+  const float mr = -sqrt_approx(fabsf(1.3862943611198906f * lg2_approx(unif_f(a))));
   // theta = 2 pi (U_b - 1/2) from x = 1 + k 2^-23 (k = b >> 9, exponent bits
   // added): U_b - 1/2 = (x - 3/2) + 2^-24 with x - 3/2 exact, so theta is one
   // subtraction and one FMA, rounded once (the same value as 2 pi (U_b - 1/2)
