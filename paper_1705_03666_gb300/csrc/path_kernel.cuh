@@ -377,7 +377,7 @@ __device__ __forceinline__ void unit_randoms(int32_t n, const PhiloxPath &pp, co
 // floating-point work.  n counts the steps taken; the unit stops at an exit
 // (returns its code, X the start and Xn the end of the exiting step) or at
 // max_steps (returns kStepContinue).
-template <class Model, class Geom, typename R, bool kLR, class Env>
+template <class Model, class Geom, typename R, bool kLR, bool kSplitCap, class Env>
 __device__ __forceinline__ int path_unit_code(const Env &a, const StepConst<R> &k,
                                               const PhiloxPath &pp, const RoundKeys &rk,
                                               int32_t max_steps, R *X, R &Y, R &Z, int32_t &n,
@@ -387,11 +387,36 @@ __device__ __forceinline__ int path_unit_code(const Env &a, const StepConst<R> &
   R z[4 * D];
   uint32_t u[4];
   unit_randoms<D, R>(n, pp, rk, z, u);
+  // kSplitCap: a unit that cannot reach the step cap tests only for exits;
+  // one that can (rare: a path near max_steps) takes the steps one at a time
+  // with the cap test, its random numbers shifted down by static indices.
+  // Without it (kernels whose own body is large, where the second copy of
+  // the unit cost more than the tests it saves), every step tests both.
+  if (!kSplitCap) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z + D * j, u[j], n, Xn, L);
-    ++n;
-    if (code != kStepContinue || n >= max_steps) break;
+    for (int j = 0; j < 4; ++j) {
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z + D * j, u[j], n, Xn, L);
+      ++n;
+      if (code != kStepContinue || n >= max_steps) break;
+    }
+  } else if (n <= max_steps - 4) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z + D * j, u[j], n, Xn, L);
+      ++n;
+      if (code != kStepContinue) break;
+    }
+  } else {
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      code = em_step<Model, Geom, R, kLR>(a, k, X, Y, Z, z, u[0], n, Xn, L);
+      ++n;
+      if (code != kStepContinue || n >= max_steps) break;
+#pragma unroll
+      for (int i = 0; i < 3 * D; ++i) z[i] = z[i + D];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[i] = u[i + 1];
+    }
   }
   return code;
 }
@@ -403,7 +428,8 @@ __device__ __forceinline__ bool path_unit(const Env &a, const StepConst<R> &k, c
                                           const RoundKeys &rk, int32_t max_steps, R *X, R &Y,
                                           R &Z, int32_t &n, R &s, R *xe, R *L) {
   R Xn[Model::D];
-  const int code = path_unit_code<Model, Geom, R, kLR>(a, k, pp, rk, max_steps, X, Y, Z, n, Xn, L);
+  const int code =
+      path_unit_code<Model, Geom, R, kLR, false>(a, k, pp, rk, max_steps, X, Y, Z, n, Xn, L);
   if (code == kStepContinue) return false;
   s = exit_score<Model, Geom, R>(a.mc, code, X, Xn, Y, Z, xe);
   return true;
@@ -627,7 +653,7 @@ path_kernel(const __grid_constant__ PathArgs a) {
     int code = kStepContinue;
     bool done = false;
     if (active) {
-      code = path_unit_code<Model, Geom, R, kLR>(a, k, pp, a.rk, a.max_steps, X, Y, Z, n, Xn, L);
+      code = path_unit_code<Model, Geom, R, kLR, true>(a, k, pp, a.rk, a.max_steps, X, Y, Z, n, Xn, L);
       done = code != kStepContinue || n >= a.max_steps;
       if (done) {
         my_steps += static_cast<unsigned long long>(n);
