@@ -385,19 +385,23 @@ PDD_API pdd_status pdd_branching_grid_solve(pdd_ctx *ctx, const double *d_nodes,
  * residual is scaled and solved to 1e-4 in FP32, the correction added in
  * FP64; same FP64 stopping rule; iterations count the FP32 ones), or Jacobi
  * sweeps (stop when max |u^{k+1} - u^k| < tol), at most max_iter
- * iterations.
+ * iterations; or directly (DST): the operator with Dirichlet data on a
+ * rectangle is diagonal in the discrete sine basis, so four dense FP64
+ * products of the sine matrices and a division by the eigenvalues give the
+ * discrete solution to rounding (at most 8192 interior points per axis;
+ * max_iter and tol are not used, *iters is 0).
  * d_u is [n[1]][n[0]] FP64 (row = y), written in full.  *iters and *resid
  * (host) receive the iteration count and the final residual measure; the call
  * synchronises.  Returns PDD_ETIMEOUT when max_iter ran out first (d_u holds
  * the last iterate).                                                      */
-enum { PDD_STENCIL_CG = 0, PDD_STENCIL_JACOBI = 1, PDD_STENCIL_CG_MIXED = 2 };
+enum { PDD_STENCIL_CG = 0, PDD_STENCIL_JACOBI = 1, PDD_STENCIL_CG_MIXED = 2, PDD_STENCIL_DST = 3 };
 
 typedef struct {
   double lo[3], hi[3];
   int32_t n[3];
   int32_t iface_axis;
   int32_t iface_side;
-  int32_t method;       /* PDD_STENCIL_CG, _JACOBI or _CG_MIXED */
+  int32_t method;       /* PDD_STENCIL_CG, _JACOBI, _CG_MIXED or _DST */
   int64_t max_iter;
   double tol;
 } pdd_subdomain;

@@ -251,7 +251,7 @@ class Context:
         sd = _lib.Subdomain((ctypes.c_double * 3)(lo[0], lo[1], 0.0),
                             (ctypes.c_double * 3)(hi[0], hi[1], 0.0),
                             (ctypes.c_int32 * 3)(nx, ny, 1), int(iface_axis), int(iface_side),
-                            {"cg": 0, "jacobi": 1, "cg_mixed": 2}[method], int(max_iter), float(tol))
+                            {"cg": 0, "jacobi": 1, "cg_mixed": 2, "dst": 3}[method], int(max_iter), float(tol))
         it, res = ctypes.c_int64(0), ctypes.c_double(0.0)
         with torch.cuda.device(self.device):
             self._bind_stream()
@@ -492,12 +492,12 @@ def interface_values(theta, phi, pdd_ctx: Context, nodes, **mc):
 
 def laplace_pdd_solve(ctx: Context, *, n_nodes: int = 16, n_paths: int = 10_000, dt: float = 1e-3,
                       seed: int, grid=(129, 129), precision: str = "fp64",
-                      method: str = "cg_mixed", tol: float = 1e-12) -> dict:
+                      method: str = "dst", tol: float = 1e-12) -> dict:
     """The two stages of PDD for the Laplace problem Eq. 1.1 on the unit square
     split at x = 1/2 (Sec. 2.1, Fig. 2.2): stage one estimates u at n_nodes
     interface nodes (1/2, k/(n_nodes+1)) by pdd_interface_solve; stage two
     interpolates them (not-a-knot spline) and solves each half independently
-    by pdd_subdomain_solve.  Returns the node estimates and the two subdomain
+    by pdd_subdomain_solve (by default directly, by sine transforms).  Returns the node estimates and the two subdomain
     grids ([ny][nx] each; they share the interface column x = 1/2)."""
     if ctx.prob["problem"] != "laplace_expcos" or ctx.prob["geometry"] != "unit_square":
         raise ValueError("laplace_pdd_solve needs the Laplace problem on the unit square")

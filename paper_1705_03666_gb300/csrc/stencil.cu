@@ -11,13 +11,19 @@
 //      (u[i+1,j] - 2u + u[i-1,j]) / hx^2 + (u[i,j+1] - 2u + u[i,j-1]) / hy^2 = 0
 //    by conjugate gradients in FP64 or as FP32 CG inside FP64 iterative
 //    refinement (one CTA, vectors L2-resident, fixed-order block reductions),
-//    or Jacobi sweeps, all bounded by max_iter.
+//    or Jacobi sweeps, all bounded by max_iter; or directly by discrete sine
+//    transforms (dst.cu).
 #include <cmath>
 #include <cstring>
 
 #include "ctx.hpp"
 
 namespace pdd {
+
+// Direct solve by discrete sine transforms (dst.cu).
+size_t dst_scratch_bytes(int nx, int ny);
+pdd_status dst_solve(pdd_ctx *ctx, double *d_u, int nx, int ny, double hx, double hy, char *work,
+                     int64_t *it_d, double *res_d);
 
 constexpr int kStencilBlock = 1024;
 
@@ -422,8 +428,10 @@ pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const dou
   if (m < 2 || !d_iface_s || !d_iface_vals) return fail(ctx, PDD_EINVAL, "need >= 2 interface nodes");
   if (sd->max_iter < 0 || !(sd->tol >= 0.0)) return fail(ctx, PDD_EINVAL, "bad stopping rule");
   if (sd->method != PDD_STENCIL_CG && sd->method != PDD_STENCIL_JACOBI &&
-      sd->method != PDD_STENCIL_CG_MIXED)
+      sd->method != PDD_STENCIL_CG_MIXED && sd->method != PDD_STENCIL_DST)
     return fail(ctx, PDD_EINVAL, "unknown method");
+  if (sd->method == PDD_STENCIL_DST && (nx - 2 > 8192 || ny - 2 > 8192))
+    return fail(ctx, PDD_EINVAL, "the sine-transform solve takes at most 8192 interior points per axis");
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const int K = static_cast<int>(m) + 1;
   const size_t npts = static_cast<size_t>(nx) * ny;
@@ -433,7 +441,9 @@ pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const dou
   const size_t off_v = off_w + 4 * knot_bytes;
   const size_t vec = align_up(npts * sizeof(double), 256);
   const size_t off_out = off_v + 3 * vec;
-  pdd_status st = ensure_scratch(ctx, off_out + 256);
+  const size_t off_dst = off_out + 256;
+  const size_t dst_bytes = sd->method == PDD_STENCIL_DST ? dst_scratch_bytes(nx, ny) : 0;
+  pdd_status st = ensure_scratch(ctx, off_dst + dst_bytes);
   if (st != PDD_OK) return st;
   char *base = static_cast<char *>(ctx->scratch);
   double *s = reinterpret_cast<double *>(base + off_s), *y = reinterpret_cast<double *>(base + off_y);
@@ -458,7 +468,10 @@ pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const dou
   const double ihx2 = 1.0 / (hx * hx), ihy2 = 1.0 / (hy * hy);
   const auto ev = prof_slot(ctx);
   if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
-  if (sd->method == PDD_STENCIL_CG)
+  if (sd->method == PDD_STENCIL_DST) {
+    st = dst_solve(ctx, d_u, nx, ny, hx, hy, base + off_dst, it_d, res_d);
+    if (st != PDD_OK) return st;
+  } else if (sd->method == PDD_STENCIL_CG)
     cg_kernel<<<1, kStencilBlock, 0, ctx->stream>>>(d_u, nx, ny, ihx2, ihy2, v0, v1, v2,
                                                     sd->max_iter, sd->tol, it_d, res_d);
   else if (sd->method == PDD_STENCIL_CG_MIXED) {
@@ -489,6 +502,7 @@ pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const dou
   PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   *iters = h_it;
   *resid = h_res;
+  if (sd->method == PDD_STENCIL_DST) return PDD_OK;  // direct: no stopping rule
   if (h_it >= sd->max_iter && !(h_res <= sd->tol))
     return fail(ctx, PDD_ETIMEOUT, "stopping rule not met after %lld iterations (%.3e)",
                 static_cast<long long>(h_it), h_res);

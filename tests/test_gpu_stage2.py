@@ -127,3 +127,36 @@ def test_two_stage_pdd_solve_end_to_end(api, orc):
     # and the Monte Carlo node values are within their standard errors
     exact = np.exp(0.5) * np.cos(s)
     assert np.all(np.abs(r["mean"].cpu().numpy() - exact) <= 4.5 * r["se"].cpu().numpy() + 2e-3)
+
+
+@pytest.mark.parametrize("side,lo,hi", [(1, (0.0, 0.0), (0.5, 1.0)), (0, (0.5, 0.0), (1.0, 1.0))])
+def test_dst_matches_direct_solve(api, orc, side, lo, hi):
+    """The sine-transform solve is the discrete solution itself: against the
+    oracle's sparse direct solve and the FP64 CG on the same data."""
+    s = W.nodes_cfg1(16)[:, 1]
+    rng = np.random.default_rng(5)
+    vals = np.exp(0.5) * np.cos(s) + 1e-3 * rng.standard_normal(16)
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.subdomain_solve(lo, hi, (129, 129), 0, side, torch.from_numpy(s),
+                                torch.from_numpy(vals), method="dst")
+        c = ctx.subdomain_solve(lo, hi, (129, 129), 0, side, torch.from_numpy(s),
+                                torch.from_numpy(vals), method="cg", tol=1e-14)
+    ref = _oracle_subdomain(orc, lo, hi, (129, 129), side, s, vals)
+    assert r["status"] == 0 and r["iters"] == 0 and r["resid"] <= 1e-12, r["resid"]
+    assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-11
+    assert float((r["u"] - c["u"]).abs().max()) < 1e-10
+
+
+@pytest.mark.parametrize("n", [(97, 201), (3, 3), (3, 40), (40, 3), (4, 5)])
+def test_dst_on_anisotropic_ragged_and_degenerate_grids(api, orc, n):
+    """Grid sizes not multiples of the 32-point tiles, hx != hy, and one
+    interior point per axis."""
+    s = np.linspace(0.05, 0.95, 9)
+    vals = np.exp(0.5) * np.cos(s)
+    lo, hi = (0.0, 0.0), (0.5, 1.0)
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.subdomain_solve(lo, hi, n, 0, 1, torch.from_numpy(s), torch.from_numpy(vals),
+                                method="dst")
+    ref = _oracle_subdomain(orc, lo, hi, n, 1, s, vals)
+    assert r["status"] == 0 and r["resid"] <= 1e-12, r["resid"]
+    assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-11
