@@ -18,7 +18,7 @@
 
 namespace pdd {
 
-constexpr int kDstTile = 32;
+constexpr int kDstTile = 16;  // 16 x 16 outputs per block: the FP64 rate is per SM, so more blocks
 
 // S[i][k] = sin(pi (i+1)(k+1) / (n+1)), i, k < n: the product is reduced
 // modulo 2(n+1) in integers, so sinpi sees an exact argument in [0, 2).
@@ -51,7 +51,7 @@ __global__ void dst_rhs_kernel(const double *u, int nx, int ny, double ihx2, dou
   }
 }
 
-// C[M][N] = A[M][K] B[K][N], FP64, row-major; 32 x 32 output tiles staged
+// C[M][N] = A[M][K] B[K][N], FP64, row-major; 16 x 16 output tiles staged
 // through shared memory, one output per thread.
 __global__ void __launch_bounds__(kDstTile * kDstTile)
 dst_gemm_kernel(const double *A, const double *B, double *C, int M, int N, int K) {
@@ -94,16 +94,19 @@ __global__ void dst_scatter_kernel(const double *U, int nx, int ny, double *u) {
   }
 }
 
-// One block: ||F - A U||_2 / ||F||_2 over the interior (0 when F = 0), in a
-// fixed order; *it = 0 (a direct solve).
-__global__ void dst_residual_kernel(const double *u, const double *F, int nx, int ny,
-                                    double ihx2, double ihy2, int64_t *it, double *res) {
-  __shared__ double sr[1024], sb[1024];
+// ||F - A U||_2 / ||F||_2 over the interior (0 when F = 0), in a fixed
+// order: each block sums a fixed slice of points (part[2 b], part[2 b + 1]),
+// then one block adds the partials in block order; *it = 0 (a direct solve).
+constexpr int kDstResBlocks = 64;
+__global__ void dst_residual_part_kernel(const double *u, const double *F, int nx, int ny,
+                                         double ihx2, double ihy2, double *part) {
+  __shared__ double sr[256], sb[256];
   const int P = nx - 2, Q = ny - 2;
   const int64_t total = static_cast<int64_t>(P) * Q;
   const double diag = 2.0 * ihx2 + 2.0 * ihy2;
   double r2 = 0.0, b2 = 0.0;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int j = static_cast<int>(t / P), i = static_cast<int>(t - static_cast<int64_t>(j) * P);
     const int64_t c = static_cast<int64_t>(j + 1) * nx + i + 1;
     // interior neighbours only: the boundary ones are in F
@@ -125,9 +128,20 @@ __global__ void dst_residual_kernel(const double *u, const double *F, int nx, in
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    *it = 0;
-    *res = sb[0] > 0.0 ? sqrt(sr[0] / sb[0]) : sqrt(sr[0]);
+    part[2 * blockIdx.x] = sr[0];
+    part[2 * blockIdx.x + 1] = sb[0];
   }
+}
+__global__ void dst_residual_final_kernel(const double *part, int nparts, int64_t *it,
+                                          double *res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double r2 = 0.0, b2 = 0.0;
+  for (int b = 0; b < nparts; ++b) {
+    r2 += part[2 * b];
+    b2 += part[2 * b + 1];
+  }
+  *it = 0;
+  *res = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
 }
 
 static unsigned dst_grid(int64_t work) {
@@ -143,7 +157,7 @@ static void dst_gemm(cudaStream_t st, const double *A, const double *B, double *
 size_t dst_scratch_bytes(int nx, int ny) {
   const size_t P = static_cast<size_t>(nx - 2), Q = static_cast<size_t>(ny - 2);
   return align_up(P * P * sizeof(double), 256) + align_up(Q * Q * sizeof(double), 256) +
-         2 * align_up(P * Q * sizeof(double), 256);
+         2 * align_up(P * Q * sizeof(double), 256) + 2 * kDstResBlocks * sizeof(double);
 }
 
 // d_u holds the Dirichlet data on the boundary (interior ignored); on return
@@ -173,7 +187,10 @@ pdd_status dst_solve(pdd_ctx *ctx, double *d_u, int nx, int ny, double hx, doubl
   dst_scatter_kernel<<<dst_grid(pq), 256, 0, st>>>(F, nx, ny, d_u);
   // the residual against the right-hand side, rebuilt from the boundary
   dst_rhs_kernel<<<dst_grid(pq), 256, 0, st>>>(d_u, nx, ny, ihx2, ihy2, T);
-  dst_residual_kernel<<<1, 1024, 0, st>>>(d_u, T, nx, ny, ihx2, ihy2, it_d, res_d);
+  double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(T) +
+                                            align_up(static_cast<size_t>(P) * Q * sizeof(double), 256));
+  dst_residual_part_kernel<<<kDstResBlocks, 256, 0, st>>>(d_u, T, nx, ny, ihx2, ihy2, part);
+  dst_residual_final_kernel<<<1, 32, 0, st>>>(part, kDstResBlocks, it_d, res_d);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
   return PDD_OK;
 }
