@@ -160,3 +160,23 @@ def test_dst_on_anisotropic_ragged_and_degenerate_grids(api, orc, n):
     ref = _oracle_subdomain(orc, lo, hi, n, 1, s, vals)
     assert r["status"] == 0 and r["resid"] <= 1e-12, r["resid"]
     assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-11
+
+
+def test_dst_limits_and_dirichlet_only_data(api):
+    """Axes beyond 8192 interior points are refused (EINVAL, before any
+    allocation); on a small ragged grid the interior of the direct solution
+    obeys the discrete maximum principle."""
+    from paper_1705_03666_gb300._lib import PDDError
+    s = np.array([0.25, 0.5, 0.75])
+    with api.Context(W.laplace_expcos()) as ctx:
+        with pytest.raises(PDDError):
+            ctx.subdomain_solve((0.0, 0.0), (0.5, 1.0), (8195, 3), 0, 1, torch.from_numpy(s),
+                                torch.from_numpy(np.zeros(3)), method="dst")
+        r = ctx.subdomain_solve((0.0, 0.0), (0.5, 1.0), (33, 17), 0, 1, torch.from_numpy(s),
+                                torch.from_numpy(np.exp(0.5) * np.cos(s)), method="dst")
+    assert r["status"] == 0 and r["iters"] == 0
+    u = r["u"].cpu().numpy()
+    assert np.all(np.isfinite(u))
+    # discrete maximum principle: the interior lies within the boundary's range
+    bd = np.concatenate([u[0], u[-1], u[:, 0], u[:, -1]])
+    assert u[1:-1, 1:-1].max() <= bd.max() + 1e-12 and u[1:-1, 1:-1].min() >= bd.min() - 1e-12
