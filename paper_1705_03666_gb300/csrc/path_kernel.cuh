@@ -6,9 +6,10 @@
 // warp's stash of set-up paths (refilled 32 indices at a time from an atomic
 // cursor), so no lane waits for a long path of another node (lane refill) and
 // the only idle time is at the very end of the wave.
-// A path's score and exit step go to a per-path slot; a separate reduction
-// (reduce.cu) forms the per-node mean and standard error in a fixed order, so
-// the result does not depend on which lane ran which path.
+// Ended paths are parked per warp and scored 32 at a time; a path's score and
+// exit step go to a per-path slot, and a separate reduction (reduce.cuh) forms
+// the per-node mean and standard error in a fixed order, so the result does
+// not depend on which lane ran which path.
 //
 // Per step (Eq. 2.8, Dirichlet/elliptic reduction of Sec. 2.2, left-point rule):
 //   X' = X + b(X) dt + sigma sqrt(dt) xi,  Y' = Y e^{c(X) dt},  Z' = Z + f(X) Y dt,
@@ -17,7 +18,9 @@
 // U < P = 1 - prod_j (1 - exp(-2 d_j d'_j / (sigma^2 dt))) over faces with
 // 2 d_j d'_j < 18 sigma^2 dt (exit point = X' projected on the face with the
 // largest term).  P is accumulated without cancellation (bridge_exit) and
-// near-ties of the FP32 path are decided in FP64.
+// near-ties of the FP32 path are decided in FP64.  Both tests sit behind one
+// screen: the smallest d d' (> 0 proves X' inside) and a union bound on P
+// above which no crossing is possible, so most steps form neither.
 // Score = g(X_tau) Y' + Z' (Eq. 2.7).
 #pragma once
 
