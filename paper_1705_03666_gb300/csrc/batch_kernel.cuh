@@ -139,6 +139,7 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
   const uint64_t c_hi = static_cast<uint64_t>(a.chunk_off[jhi]);
   unsigned long long *cursor = a.cursor + C;
   BatchLane L;
+  float x0[3] = {0.f, 0.f, 0.f};  // the chunk's node, converted once per chunk
   StepConst<float> k;
   int32_t pi = 0;
   uint32_t node = 0;
@@ -187,9 +188,12 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
           s1 = F2Sum();
           s2 = F2Sum();
           cnt = 0;
-          L.X[0] = static_cast<float>(a.nodes[i * 3 + 0]);
-          L.X[1] = static_cast<float>(a.nodes[i * 3 + 1]);
-          L.X[2] = static_cast<float>(a.nodes[i * 3 + 2]);
+          x0[0] = static_cast<float>(a.nodes[i * 3 + 0]);
+          x0[1] = static_cast<float>(a.nodes[i * 3 + 1]);
+          x0[2] = static_cast<float>(a.nodes[i * 3 + 2]);
+          L.X[0] = x0[0];
+          L.X[1] = x0[1];
+          L.X[2] = x0[2];
           if (!batch_inside<M, G>(L.X)) {
             // node on (or, invalid, outside) the boundary: every path scores g
             const bool closed = batch_closed<M, G>(L.X);
@@ -236,9 +240,9 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
       my_steps += static_cast<unsigned long long>(L.n);
       ++path;
       if (path < path_end) {
-        L.X[0] = static_cast<float>(a.nodes[static_cast<uint64_t>(node) * 3 + 0]);
-        L.X[1] = static_cast<float>(a.nodes[static_cast<uint64_t>(node) * 3 + 1]);
-        L.X[2] = static_cast<float>(a.nodes[static_cast<uint64_t>(node) * 3 + 2]);
+        L.X[0] = x0[0];
+        L.X[1] = x0[1];
+        L.X[2] = x0[2];
         L.Y = 1.f;
         L.Z = 0.f;
         L.n = 0;
