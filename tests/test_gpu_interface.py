@@ -241,3 +241,43 @@ def test_autotune_picks_a_shape_and_keeps_results(api):
         after = ctx.interface_solve(nodes, **kw)["mean"]
     assert 1 <= t["blocks_per_sm"] <= 8 and t["ms"] > 0
     assert torch.equal(before, after)
+
+
+@pytest.mark.parametrize("max_steps", [13, 30])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_step_cap_matches_oracle_path_by_path(api, orc, max_steps, precision):
+    """Paths stopped by the step cap (a cap that falls inside a unit of four
+    steps, after whole units) score g at the projection on the nearest face
+    and report -max_steps, path by path as in the oracle."""
+    w = W.workload(2)
+    nodes = w["nodes"][::512]
+    kw = dict(seed=w["seed"] + 7, dt=1e-5, n_paths=300, max_steps=max_steps)
+    with api.Context(w["prob"]) as ctx:
+        g = ctx.interface_solve(torch.from_numpy(nodes), precision=precision, dump_paths=True,
+                                diag=True, **kw)
+    o = orc.interface_solve(w["prob"], nodes, dump_paths=True, **kw)
+    stg = g["steps"].cpu().numpy()
+    assert (stg == -max_steps).mean() > 0.9            # most paths hit the cap
+    assert g["capped"] == int((stg == -max_steps).sum())
+    tol = 1e-11 if precision == "fp64" else PATH_TOL_FP32
+    c = _compare(g, o, tol)
+    assert c["flip_frac"] <= (1e-4 if precision == "fp64" else FLIP_MAX_FP32), c["flip_frac"]
+    assert c["node_rel"].max() <= NODE_REL_TOL
+
+
+def test_batch_step_cap_matches_interface_solve(api):
+    """The batch kernels' cap scoring (batch_capped) and the path kernel's
+    (parked and scored with the exit queue) give the same paths."""
+    w = W.workload(2)
+    nodes = w["nodes"][::256]
+    n, N, dt = len(nodes), 2000, 1e-5
+    with api.Context(w["prob"]) as ctx:
+        r = ctx.batch_solve([w["prob"]], torch.from_numpy(nodes), torch.zeros(n, dtype=torch.int32),
+                            torch.full((n,), dt, dtype=torch.float64), seed=3, n_pilot=200,
+                            n_min=N, n_max=N, target_se=1.0, max_steps=21, diag=True)
+        p = ctx.interface_solve(torch.from_numpy(nodes), seed=3, dt=dt, n_paths=N,
+                                precision="fp32", max_steps=21, diag=True)
+    assert r["capped"] > 0 and r["capped"] == p["capped"]
+    assert r["path_steps"] == p["path_steps"]
+    np.testing.assert_allclose(r["mean"].cpu().numpy(), p["mean"].cpu().numpy(), rtol=1e-9,
+                               atol=1e-12)
