@@ -18,6 +18,7 @@ PDD_OK, PDD_EINVAL, PDD_ENOMEM, PDD_ECUDA, PDD_ETIMEOUT, PDD_ECAP = range(6)
 GEOMETRY = {"interval": 0, "unit_square": 1, "l_shape": 2, "unit_cube": 3, "free_space": 4}
 PROBLEM = {"laplace_expcos": 1, "elliptic_manufactured": 2, "poisson_fourier": 3, "kpp": 7}
 PRECISION = {"fp32": 0, "fp64": 1}
+STENCIL = {"cg": 0, "jacobi": 1, "cg_mixed": 2, "dst": 3}
 
 
 class Problem(ctypes.Structure):

@@ -251,7 +251,7 @@ class Context:
         sd = _lib.Subdomain((ctypes.c_double * 3)(lo[0], lo[1], 0.0),
                             (ctypes.c_double * 3)(hi[0], hi[1], 0.0),
                             (ctypes.c_int32 * 3)(nx, ny, 1), int(iface_axis), int(iface_side),
-                            {"cg": 0, "jacobi": 1, "cg_mixed": 2, "dst": 3}[method], int(max_iter), float(tol))
+                            _lib.STENCIL[method], int(max_iter), float(tol))
         it, res = ctypes.c_int64(0), ctypes.c_double(0.0)
         with torch.cuda.device(self.device):
             self._bind_stream()

@@ -64,3 +64,21 @@ def test_struct_layouts(lib):
     assert ctypes.sizeof(lib.WosParams) == 48
     assert ctypes.sizeof(lib.GridBranchParams) == 48
     assert ctypes.sizeof(lib.MlmcParams) == 48
+
+
+def test_enum_values_match_header(lib):
+    """The binding's tables of geometry, problem, precision, stencil method
+    and status codes carry the values include/pdd.h gives them."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "pdd.h")).read()
+    vals = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\b(PDD_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)}
+    tables = [(lib.GEOMETRY, "PDD_GEOM_"), (lib.PROBLEM, "PDD_PROB_"),
+              (lib.PRECISION, "PDD_"), (lib.STENCIL, "PDD_STENCIL_")]
+    for table, prefix in tables:
+        for name, v in table.items():
+            assert vals[prefix + name.upper()] == v, (prefix + name.upper(), v)
+    for name in ("PDD_OK", "PDD_EINVAL", "PDD_ENOMEM", "PDD_ECUDA", "PDD_ETIMEOUT", "PDD_ECAP"):
+        assert vals[name] == getattr(lib, name), name
