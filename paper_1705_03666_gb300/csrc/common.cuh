@@ -146,7 +146,9 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, R &z0, R &z1)
 // sin(2 pi U_b) = -sin theta.  -2 ln U_a comes from the hardware log2,
 // whose absolute error (~2^-22 near U_a = 1) gives r = sqrt(-2 ln U_a) an
 // error ~1e-7 / r: relatively large only for the rare tiny radii, where the
-// displacement r sqrt(dt) itself is tiny.  The square root is y * rsqrt(y).
+// displacement r sqrt(dt) itself is tiny.  The radius is the hardware square
+// root of the magnitude of the scaled log2 (near U_a = 1 the log2 may come
+// out 0 or tiny and positive).
 //
 // -2 ln u accurate to 2e-7 relative for all u in (0, 1) (used where a single
 // log sets a decision, e.g. branching lifetimes), from the atanh series:
@@ -173,8 +175,9 @@ __device__ __forceinline__ float neg2log(float u) {
 
 // Hardware approximations (PTX .approx.ftz: one special-function-unit
 // operation each).  Subnormal arguments and results are flushed to zero; the
-// kernels pass normal numbers (uniforms >= 2^-24, radii clamped at 1e-30,
-// centred angles at least 2^-24 away from 0), where the flush changes nothing
+// kernels pass normal numbers or zero (uniforms >= 2^-24, squared radii 0 or
+// above 1e-8, centred angles at least 2^-24 away from 0), where the flush
+// changes nothing
 // and the subnormal scaling the non-ftz forms add around the operation is
 // left out.
 __device__ __forceinline__ float ex2_approx(float x) {  // 2^x, about 2 ulp relative
