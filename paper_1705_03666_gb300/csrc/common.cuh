@@ -177,9 +177,8 @@ __device__ __forceinline__ float neg2log(float u) {
 // operation each).  Subnormal arguments and results are flushed to zero; the
 // kernels pass normal numbers or zero (uniforms >= 2^-24, squared radii 0 or
 // above 1e-8, centred angles at least 2^-24 away from 0), where the flush
-// changes nothing
-// and the subnormal scaling the non-ftz forms add around the operation is
-// left out.
+// changes nothing and the subnormal scaling the non-ftz forms add around the
+// operation is left out.
 __device__ __forceinline__ float ex2_approx(float x) {  // 2^x, about 2 ulp relative
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
