@@ -220,7 +220,8 @@ constexpr int kStepHardExit = -1;   // >= 0: bridge exit through that face
 // One Euler-Maruyama step with the exit test.  On kStepContinue, X, Y, Z
 // advance; on an exit, X keeps the start of the step, Xn receives its end,
 // Y and Z receive their exit values, and the caller resolves the exit point
-// (exit_score) once per unit.  With kLR the drift-weight likelihood-ratio
+// (exit_score): the path kernel 32 paths at a time from its exit queue, the
+// other kernels through path_unit.  With kLR the drift-weight likelihood-ratio
 // sums L are advanced by this step's noise (the exiting step included).
 template <class Model, class Geom, typename R, bool kLR, class Env>
 __device__ __forceinline__ int em_step(const Env &a, const StepConst<R> &k, R *X, R &Y, R &Z,
