@@ -293,8 +293,9 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
 
     // ---- one unit: up to four steps, random numbers formed up front (the
     // stream layout of the path kernel).  The step loop is not unrolled: each
-    // step carries the accurate special functions of its rare branches, and
-    // four inlined copies ran 1.5x slower.
+    // step carries sizeable rare branches (a reflection with its Robin
+    // weights, the exact absorbing tests), and four inlined copies ran 1.5x
+    // slower.
     R z[4 * D];
     uint32_t u[4];
     unit_randoms<D, R>(n, pp, a.rk, z, u);
