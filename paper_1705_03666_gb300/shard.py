@@ -6,10 +6,15 @@ without communication: by node (block distribution) or by path range.  The
 only exchange before stage two is an all-gather of per-node (count, mean, M2)
 triples, merged with Chan's formula where one node's paths span ranks.
 Works with any torch.distributed backend (gloo on CPU tensors, NCCL on CUDA
-tensors); the solves themselves run in libpdd.so.
+tensors); the solves themselves run in libpdd.so.  The same exchange can go
+through a key-value store with a deadline instead (publish / collect), so
+that the survivors of a lost rank carry on without it.
 """
 from __future__ import annotations
 
+import time
+
+import numpy as np
 import torch
 import torch.distributed as dist
 
@@ -84,3 +89,91 @@ def allreduce_paths(local: torch.Tensor, group=None) -> torch.Tensor:
     for p in parts[1:]:
         acc = chan_merge(acc, p)
     return acc
+
+
+# ---------------------------------------------------------------------------
+# Exchange through a key-value store with a deadline, for runs that must
+# survive the loss of a rank.  A rank that fails between steps only takes its
+# own units with it (the paper's remark on fault tolerance in Sec. 2): with
+# path-range sharding the survivors' samples still give an unbiased estimate
+# with a wider standard error; with node sharding the lost block is
+# recomputed by the survivors, and because every path's random numbers come
+# from (seed, node id, path index) the recomputed values are the ones the
+# lost rank would have produced.  No collective is involved, so a missing
+# rank cannot block the others beyond the deadline.
+# ---------------------------------------------------------------------------
+
+def publish(store, tag: str, rank: int, table: torch.Tensor) -> None:
+    """Post this rank's [rows, 3] (count, mean, M2) table under `tag`."""
+    t = table.detach().to("cpu", torch.float64).contiguous()
+    store.set(f"{tag}/{rank}", t.numpy().tobytes())
+
+
+def collect(store, tag: str, ranks, timeout_s: float, poll_s: float = 0.01):
+    """Wait up to `timeout_s` seconds for the tables that `ranks` publish
+    under `tag`.  Returns ({rank: [rows, 3] table} for the ranks that
+    published, sorted list of the ranks that did not)."""
+    deadline = time.monotonic() + timeout_s
+    pending = sorted(set(int(r) for r in ranks))
+    got = {}
+    while True:
+        for r in list(pending):
+            key = f"{tag}/{r}"
+            if store.check([key]):
+                buf = np.frombuffer(store.get(key), dtype=np.float64).copy()
+                got[r] = torch.from_numpy(buf).reshape(-1, 3)
+                pending.remove(r)
+        if not pending or time.monotonic() >= deadline:
+            return got, pending
+        time.sleep(poll_s)
+
+
+def merge_surviving_paths(got: dict) -> torch.Tensor:
+    """Path-range sharding after `collect`: merge the surviving ranks' tables
+    in rank order (the result is the estimate over their path ranges)."""
+    if not got:
+        raise RuntimeError("no rank published its table")
+    ranks = sorted(got)
+    acc = got[ranks[0]]
+    for r in ranks[1:]:
+        acc = chan_merge(acc, got[r])
+    return acc
+
+
+def lost_node_share(n_total: int, world: int, lost, alive, rank: int) -> list[tuple[int, int]]:
+    """Node sharding: the half-open node ranges `rank` (a survivor) recomputes
+    when the ranks in `lost` are gone.  Each lost rank's block is split over
+    the survivors in rank order by the block rule."""
+    alive = sorted(alive)
+    me = alive.index(rank)
+    out = []
+    for r in sorted(lost):
+        lo, hi = node_block(n_total, world, r)
+        a, b = node_block(hi - lo, len(alive), me)
+        if b > a:
+            out.append((lo + a, lo + b))
+    return out
+
+
+def assemble_nodes(n_total: int, world: int, got: dict, lost=(), redo: dict | None = None):
+    """Node sharding: the full [n_total, 3] table from the blocks that
+    arrived (`got`, keyed by owning rank) and, for the `lost` ranks' blocks,
+    the survivors' recomputed rows (`redo`, keyed by survivor: its
+    `lost_node_share` pieces, concatenated in order).  Rows nobody supplied
+    keep count 0 (finalize gives mean 0, se 0, count 0 there)."""
+    out = torch.zeros((n_total, 3), dtype=torch.float64)
+    for r, t in got.items():
+        lo, hi = node_block(n_total, world, r)
+        if t.shape[0] != hi - lo:
+            raise ValueError(f"rank {r} published {t.shape[0]} rows for block [{lo}, {hi})")
+        out[lo:hi] = t
+    alive = sorted(got)
+    for r, t in (redo or {}).items():
+        pieces = lost_node_share(n_total, world, lost, alive, r)
+        if t.shape[0] != sum(b - a for a, b in pieces):
+            raise ValueError(f"rank {r} recomputed {t.shape[0]} rows for pieces {pieces}")
+        k = 0
+        for a, b in pieces:
+            out[a:b] = t[k:k + b - a]
+            k += b - a
+    return out
