@@ -3,11 +3,22 @@
 #include <cmath>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ctx.hpp"
 
 using pdd::fail;
 
 namespace {
+
+// Named NVTX range around an entry point's host work and launches (a span
+// on a profiler's timeline; a no-op when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 bool finite_params(const pdd_problem *p) {
   for (int i = 0; i < p->n_params; ++i)
@@ -136,6 +147,7 @@ pdd_status pdd_interface_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                                int64_t *d_npaths, pdd_diag *diag) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::interface_solve_impl(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths, diag);
 }
 
@@ -144,6 +156,7 @@ pdd_status pdd_branching_solve(pdd_ctx *ctx, const double *d_nodes_xt, int64_t n
                                int64_t *d_nkept, pdd_diag *diag) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   if (bp && bp->reserved != 0) return fail(ctx, PDD_EINVAL, "reserved must be 0");
   return pdd::branching_solve_impl(ctx, d_nodes_xt, n, bp, d_mean, d_se, d_nkept, diag);
 }
@@ -153,6 +166,7 @@ pdd_status pdd_subdomain_solve(pdd_ctx *ctx, const pdd_subdomain *sd, const doub
                                int64_t *iters, double *resid) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::subdomain_solve_impl(ctx, sd, d_iface_s, d_iface_vals, m, d_u, iters, resid);
 }
 
@@ -162,6 +176,7 @@ pdd_status pdd_interface_grad(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                               pdd_diag *diag) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::interface_grad_impl(ctx, d_nodes, n, mc, d_grad_out, d_jac, d_jac_se, d_dtheta,
                                   d_dphi, diag);
 }
@@ -169,6 +184,7 @@ pdd_status pdd_interface_grad(pdd_ctx *ctx, const double *d_nodes, int64_t n,
 pdd_status pdd_set_params(pdd_ctx *ctx, const double *params, int32_t n_params) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   if (n_params != ctx->prob.n_params) return fail(ctx, PDD_EINVAL, "n_params differs");
   if (n_params > 0 && !params) return fail(ctx, PDD_EINVAL, "params is NULL");
   pdd_problem p = ctx->prob;
@@ -189,6 +205,7 @@ pdd_status pdd_batch_solve(pdd_ctx *ctx, const pdd_problem *problems, int32_t n_
                            pdd_diag *diag) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::batch_solve_impl(ctx, problems, n_problems, nodes, bp, d_mean, d_se, d_npaths,
                                use_graph, diag);
 }
@@ -198,6 +215,7 @@ pdd_status pdd_interface_solve_naive(pdd_ctx *ctx, const double *d_nodes, int64_
                                      int64_t *d_npaths) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::interface_solve_naive_impl(ctx, d_nodes, n, mc, d_mean, d_se, d_npaths);
 }
 
@@ -206,6 +224,7 @@ pdd_status pdd_autotune(pdd_ctx *ctx, const double *d_nodes, int64_t n, const pd
                         double *best_ms) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::autotune_impl(ctx, d_nodes, n, mc, d_scratch_out, repeats, best_blocks_per_sm,
                             best_ms);
 }
@@ -216,6 +235,7 @@ pdd_status pdd_autotune_batch(pdd_ctx *ctx, const pdd_problem *problems, int32_t
                               double *best_ms) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::autotune_batch_impl(ctx, problems, n_problems, nodes, bp, d_scratch_out, repeats,
                                   best_chunk, best_ms);
 }
@@ -224,6 +244,7 @@ pdd_status pdd_wos_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n, const p
                          double *d_mean, double *d_se, int64_t *d_npaths, pdd_diag *diag) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   if (wp && wp->reserved != 0) return fail(ctx, PDD_EINVAL, "reserved must be 0");
   return pdd::wos_solve_impl(ctx, d_nodes, n, wp, d_mean, d_se, d_npaths, diag);
 }
@@ -234,6 +255,7 @@ pdd_status pdd_branching_grid_solve(pdd_ctx *ctx, const double *d_nodes, int64_t
                                     double *d_se, int64_t *d_nkept, pdd_diag *diag) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::branching_grid_solve_impl(ctx, d_nodes, n, h_times, m, bp, d_mean, d_se, d_nkept,
                                         diag);
 }
@@ -243,6 +265,7 @@ pdd_status pdd_mlmc_level(pdd_ctx *ctx, const double *d_nodes, int64_t n, const 
                           pdd_diag *diag) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::mlmc_level_impl(ctx, d_nodes, n, mp, d_mean, d_var, d_fine_mean, d_coarse_mean, diag);
 }
 
@@ -274,6 +297,7 @@ pdd_status pdd_normals(pdd_ctx *ctx, uint64_t seed, uint32_t c1, uint32_t c2, ui
                        int64_t n_pairs, float *d_z, float *d_u) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::normals_impl(ctx, seed, c1, c2, c3, n_pairs, d_z, d_u);
 }
 
@@ -281,6 +305,7 @@ pdd_status pdd_philox_stream(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t 
                              uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out) {
   if (!ctx) return PDD_EINVAL;
   ctx->last_error.clear();
+  const TraceRange trace(__func__);
   return pdd::philox_stream_impl(ctx, seed, j0, c1, c2, c3, n_blocks, d_out);
 }
 
