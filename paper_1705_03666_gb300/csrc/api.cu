@@ -3,7 +3,10 @@
 #include <cmath>
 #include <new>
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
+#define PDD_HAVE_NVTX 1
+#endif
 
 #include "ctx.hpp"
 
@@ -12,10 +15,15 @@ using pdd::fail;
 namespace {
 
 // Named NVTX range around an entry point's host work and launches (a span
-// on a profiler's timeline; a no-op when no tool is attached).
+// on a profiler's timeline; a no-op when no tool is attached, and compiled
+// out where the toolkit has no NVTX headers).
 struct TraceRange {
+#ifdef PDD_HAVE_NVTX
   explicit TraceRange(const char *name) { nvtxRangePushA(name); }
   ~TraceRange() { nvtxRangePop(); }
+#else
+  explicit TraceRange(const char *) {}
+#endif
   TraceRange(const TraceRange &) = delete;
   TraceRange &operator=(const TraceRange &) = delete;
 };
