@@ -508,7 +508,9 @@ PDD_API void pdd_destroy(pdd_ctx *ctx);
 /* Static description of a status code. */
 PDD_API const char *pdd_status_string(pdd_status status);
 
-/* One-line description of the last failure on ctx ("" if none). */
+/* One-line description of the last failure on ctx ("" if none).  With
+ * ctx = NULL: why the calling thread's last pdd_create failed ("" if it
+ * succeeded).                                                             */
 PDD_API const char *pdd_last_error(const pdd_ctx *ctx);
 
 #ifdef __cplusplus

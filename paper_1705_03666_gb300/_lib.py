@@ -168,13 +168,15 @@ class PDDError(RuntimeError):
         self.status = status
 
 
-def check(status: int, ctx=None, allow=(PDD_OK,)) -> int:
+def check(status: int, ctx=None, allow=(PDD_OK,), create: bool = False) -> int:
+    """Raise PDDError unless status is allowed; the message adds the
+    context's last error, or (create=True) why pdd_create failed."""
     if status in allow:
         return status
     lib = load()
     msg = lib.pdd_status_string(status).decode()
-    if ctx:
-        extra = lib.pdd_last_error(ctx).decode()
+    if ctx or create:
+        extra = lib.pdd_last_error(ctx if ctx else None).decode()
         if extra:
             msg = f"{msg}: {extra}"
     raise PDDError(status, msg)

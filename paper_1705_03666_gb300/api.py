@@ -42,7 +42,7 @@ class Context:
         with torch.cuda.device(self.device):
             st = self.lib.pdd_create(ctypes.byref(h), ctypes.byref(p), self.device.index,
                                      _stream_handle(self.device))
-        _lib.check(st)
+        _lib.check(st, create=True)
         self.handle = h
 
     # ------------------------------------------------------------------

@@ -2,6 +2,7 @@
 // context lifetime and dispatch to the kernel translation units.
 #include <cmath>
 #include <new>
+#include <string>
 
 #if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
@@ -13,6 +14,15 @@
 using pdd::fail;
 
 namespace {
+
+// Reason the calling thread's last pdd_create failed ("" after a success):
+// there is no context yet to hold it.
+thread_local std::string g_create_error;
+
+pdd_status create_fail(pdd_status st, const char *why) {
+  g_create_error = why;
+  return st;
+}
 
 // Named NVTX range around an entry point's host work and launches (a span
 // on a profiler's timeline; a no-op when no tool is attached, and compiled
@@ -104,19 +114,19 @@ const char *check_problem(const pdd_problem *p) {
 extern "C" {
 
 pdd_status pdd_create(pdd_ctx **out, const pdd_problem *problem, int device, void *cuda_stream) {
-  if (!out || !problem) return PDD_EINVAL;
+  g_create_error.clear();
+  if (!out || !problem) return create_fail(PDD_EINVAL, "out or problem is NULL");
   *out = nullptr;
-  if (const char *why = check_problem(problem)) {
-    (void)why;
-    return PDD_EINVAL;
-  }
+  if (const char *why = check_problem(problem)) return create_fail(PDD_EINVAL, why);
+  if (device < 0) return create_fail(PDD_EINVAL, "device must be >= 0");
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+  const cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device >= ndev) {
     cudaGetLastError();
-    return device < 0 ? PDD_EINVAL : PDD_ECUDA;
+    return create_fail(PDD_ECUDA, e != cudaSuccess ? cudaGetErrorString(e) : "no such device");
   }
   pdd_ctx *ctx = new (std::nothrow) pdd_ctx();
-  if (!ctx) return PDD_ENOMEM;
+  if (!ctx) return create_fail(PDD_ENOMEM, "host allocation of the context failed");
   ctx->device = device;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   ctx->prob = *problem;
@@ -129,9 +139,9 @@ pdd_status pdd_create(pdd_ctx **out, const pdd_problem *problem, int device, voi
   }
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
-    cudaGetLastError();
+    const cudaError_t e2 = cudaGetLastError();
     delete ctx;
-    return PDD_ECUDA;
+    return create_fail(PDD_ECUDA, cudaGetErrorString(e2));
   }
   *out = ctx;
   return PDD_OK;
@@ -349,7 +359,7 @@ const char *pdd_status_string(pdd_status s) {
 }
 
 const char *pdd_last_error(const pdd_ctx *ctx) {
-  return ctx ? ctx->last_error.c_str() : "";
+  return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
 }
 
 }  // extern "C"

@@ -53,6 +53,20 @@ def test_create_rejects_invalid_problem_without_gpu(lib):
     kp = np.array([1.0, 1.0, 4.0, 2.0, 0.0, 0.0, 0.5, 0.0, 0.0, 0.5])
     kpp = lib.Problem(7, 4, 2, kp.size, kp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0)
     assert cdll.pdd_create(ctypes.byref(h), ctypes.byref(kpp), 0, None) == lib.PDD_EINVAL
+    # the reason is kept per thread and read with a NULL context
+    assert cdll.pdd_last_error(None) == b"q must sum to 1"
+    assert cdll.pdd_create(ctypes.byref(h), ctypes.byref(neg), 0, None) == lib.PDD_EINVAL
+    assert cdll.pdd_last_error(None) == b"sigma must be > 0"
+    assert cdll.pdd_create(ctypes.byref(h), ctypes.byref(bad), 0, None) == lib.PDD_EINVAL
+    assert cdll.pdd_last_error(None) == b"ELLIPTIC_MANUFACTURED needs dim 3 on the unit cube"
+    assert cdll.pdd_create(None, ctypes.byref(neg), 0, None) == lib.PDD_EINVAL
+    assert cdll.pdd_last_error(None) == b"out or problem is NULL"
+    ok = lib.Problem(1, 1, 2, 0, params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0)
+    assert cdll.pdd_create(ctypes.byref(h), ctypes.byref(ok), -1, None) == lib.PDD_EINVAL
+    assert cdll.pdd_last_error(None) == b"device must be >= 0"
+    with pytest.raises(lib.PDDError, match="sigma must be > 0"):
+        lib.check(lib.PDD_EINVAL if cdll.pdd_create(ctypes.byref(h), ctypes.byref(neg), 0, None)
+                  else lib.PDD_OK, create=True)
 
 
 def test_struct_layouts(lib):
