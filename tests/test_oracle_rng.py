@@ -4,8 +4,9 @@ Philox4x32-10 is the counter-based generator of Salmon, Moraes, Dror and Shaw
 (SC'11).  The oracle's copy is pinned here by what its published design fixes:
 the Weyl key increments are the golden ratio and sqrt(3)-1 scaled by 2^32, the
 multipliers are the published odd 32-bit constants, each output word depends
-on every counter bit (avalanche), distinct counters give distinct blocks, and
-the output is statistically uniform.  The uniform and normal maps are checked
+on every counter bit (avalanche), distinct counters give distinct blocks, the
+output is statistically uniform, and its blocks equal those of an independent
+implementation (Triton's, run on the CPU by its interpreter).  The uniform and normal maps are checked
 for range, exactness in binary32 and the moments / KS statistic of N(0,1).
 """
 import math
@@ -90,3 +91,61 @@ def test_normal_moments_and_ks(orc):
     # the two halves of a Box-Muller pair are uncorrelated
     r = np.corrcoef(z[0::2], z[1::2])[0, 1]
     assert abs(r) < 4.0 / math.sqrt(n / 2)
+
+
+_TRITON_PHILOX = r'''
+import json, os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+
+@triton.jit
+def blocks(ctr_ptr, out_ptr, seed):
+    i = tl.arange(0, 2)
+    z = tl.zeros_like(i)
+    c0 = tl.load(ctr_ptr + 0 + z)
+    c1 = tl.load(ctr_ptr + 1 + z)
+    c2 = tl.load(ctr_ptr + 2 + z)
+    c3 = tl.load(ctr_ptr + 3 + z)
+    a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
+    tl.store(out_ptr + 4 * i + 0, a.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + 4 * i + 1, b.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + 4 * i + 2, c.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + 4 * i + 3, d.to(tl.int32, bitcast=True))
+
+res = []
+for ctr, key in json.load(sys.stdin):
+    ct = torch.tensor([c - (1 << 32) if c >= 1 << 31 else c for c in ctr], dtype=torch.int32)
+    out = torch.zeros(8, dtype=torch.int32)
+    seed = key[0] | (key[1] << 32)
+    seed = seed - (1 << 64) if seed >= 1 << 63 else seed
+    blocks[(1,)](ct, out, seed)
+    res.append([int(v) & 0xFFFFFFFF for v in out[:4].tolist()])
+print(json.dumps(res))
+'''
+
+
+def test_philox_matches_an_independent_implementation(orc, tmp_path):
+    """The oracle's blocks equal those of another implementation of
+    Philox4x32-10 written from the same paper: Triton's, run by its CPU
+    interpreter in a child process (counter words c0..c3, key = the two
+    32-bit halves of the seed), over edge and random counters and keys."""
+    import json
+    import subprocess
+    import sys
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(1705)
+    cases = [([0, 0, 0, 0], [0, 0]),
+             ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2),
+             ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0]),
+             ([1, 0, 0, 0], [0, 0]), ([0, 0, 0, 1], [0, 0]), ([0, 0, 0, 0], [0, 1])]
+    for _ in range(26):
+        cases.append(([int(v) for v in rng.integers(0, 2**32, 4)],
+                      [int(v) for v in rng.integers(0, 2**32, 2)]))
+    p = subprocess.run([sys.executable, "-c", _TRITON_PHILOX], input=json.dumps(cases),
+                       capture_output=True, text=True, timeout=300)
+    if p.returncode != 0:
+        pytest.skip(f"Triton CPU interpreter unavailable: {p.stderr.strip()[-200:]}")
+    theirs = json.loads(p.stdout.strip().splitlines()[-1])
+    for (ctr, key), t in zip(cases, theirs):
+        mine = [int(v) for v in orc.philox4x32_10(ctr, key)]
+        assert mine == t, (ctr, key, [hex(v) for v in mine], [hex(v) for v in t])
