@@ -118,18 +118,59 @@ def _oracle_sample(prob, nodes, node_ids, n_paths, threads):
     return time.perf_counter() - t0, r["total_steps"]
 
 
-def cpu_baseline(target_s: float = 12.0) -> dict:
+def cpu_baseline(api=None, dev=None, target_s: float = 12.0) -> dict:
     """The FP64 oracle on the host cores, every 64th node, paths sized so the
-    run takes about target_s seconds."""
+    run takes about target_s seconds.  With the library (api, dev) the same
+    sample also gives the parity record of the timed workload: the GPU paths
+    of those nodes (node_offset = their index in the full list, so the
+    full run's streams) against the oracle's, path by path."""
+    import oracle
     threads = os.cpu_count() or 1
     ids = np.arange(0, 4096, 64)
     nodes = WORKLOAD["nodes"][ids]
     dt_cal, steps_cal = _oracle_sample(WORKLOAD["prob"], nodes, ids, 200, threads)
     n_paths = int(max(200, min(20000, 200 * target_s / max(dt_cal, 1e-3))))
-    el, steps = _oracle_sample(WORKLOAD["prob"], nodes, ids, n_paths, threads)
-    return {"value": steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(ids)} nodes (every 64th) x {n_paths} paths, dt=1e-4, FP64, "
-                      f"{steps:.3e} path-steps in {el:.2f} s"}
+    t0 = time.perf_counter()
+    o = oracle.interface_solve(WORKLOAD["prob"], nodes, node_ids=ids, seed=WORKLOAD["seed"],
+                               dt=WORKLOAD["dt"], n_paths=n_paths, n_threads=threads,
+                               dump_paths=api is not None)
+    el, steps = time.perf_counter() - t0, o["total_steps"]
+    out = {"value": steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{len(ids)} nodes (every 64th) x {n_paths} paths, dt=1e-4, FP64, "
+                     f"{steps:.3e} path-steps in {el:.2f} s"}
+    if api is not None:
+        out["parity"] = _parity_record(api, dev, ids, n_paths, o)
+    return out
+
+
+def _parity_record(api, dev, ids, n_paths, o) -> dict:
+    """Exit flips and per-node agreement of the benchmark's FP32 paths with
+    the FP64 oracle on the sampled nodes (tests/parity.py classification)."""
+    import torch
+    from tests import parity
+    w = WORKLOAD
+    kw = dict(seed=w["seed"], dt=w["dt"], n_paths=n_paths, precision="fp32", bridge=True)
+    sc, st, ex = [], [], []
+    with api.Context(w["prob"], dev) as ctx:
+        for i in ids:
+            r = ctx.interface_solve(torch.from_numpy(w["nodes"][i:i + 1]), node_offset=int(i),
+                                    dump_paths=True, **kw)
+            sc.append(r["score"].cpu().numpy())
+            st.append(r["steps"].cpu().numpy())
+            ex.append(r["exit"].cpu().numpy())
+    g = {"score": np.concatenate(sc), "steps": np.concatenate(st), "exit": np.concatenate(ex)}
+    c = parity.compare_paths(g, o, prob=w["prob"], geometry="unit_cube")
+    return {"sample": f"{len(ids)} nodes (every 64th) x {n_paths} paths on the timed run's "
+                      "streams (node_offset = node index)",
+            "exit_flip_frac": c["flip_frac"], "step_flips": c["step_flips"],
+            "face_flips": c["face_flips"], "same_exit_score_mismatches": c["mismatch"],
+            "max_path_rel_same_exit": c["max_path_rel"],
+            "max_ratio_to_path_bound": c["max_bound_ratio"],
+            "max_node_rel_same_exit": c["node_rel_max"],
+            "max_node_rel_all_paths": float(np.max(np.abs(g["score"].mean(1) - o["score"].mean(1))
+                                                   / np.abs(o["score"].mean(1)))),
+            "node_tolerance": 1e-5,
+            "path_bound": "2^-22 ((n + 8) |grad g(x_exit)| + 16 (1 + |s|)), n = exit step"}
 
 
 def run_reference(args):
@@ -291,8 +332,7 @@ def run_pdd(args):
                    "nodes": n, "paths_per_node": n_paths,
                    "dt": w["dt"], "path_precision": "fp32 paths, fp64 reductions",
                    "bridge": True, "path_steps_per_step": steps_per_call,
-                   "l2": "flushed between steps (256 MiB write outside the timed events); "
-                         "per-path scratch 1.6 GB > L2",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"independent batches per GPU x{world}"},
         "nodes_per_s": nodes_per_s, "median_se": se_median,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
@@ -303,7 +343,7 @@ def run_pdd(args):
                      "peak_basis": f"{n_sm} SMs x 4 warp-issue/clk x 32 lanes x {f_mhz:.0f} MHz "
                                    "(median SM clock sampled during the timed region)"},
         "clocks": clk,
-        "gpu_launches": int(args.steps * (launches_per_step + 2)),
+        "gpu_launches": int(args.steps * (launches_per_step + 1)),
         "e2e": {"value": world * e2e_steps * steps_per_call / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(nodes_h.numel() * 8),
                 "d2h_bytes_per_step": int(n * 24)},
@@ -315,7 +355,9 @@ def run_pdd(args):
     if others is not None:
         line["other_workloads"] = others
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        cb = cpu_baseline(api, dev)
+        line["parity"] = cb.pop("parity")
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -511,11 +553,12 @@ def run_other_workloads(api, dev) -> dict:
     return out
 
 
-def run_batch_once(api, dev, scale: float = 0.05) -> dict:
+def run_batch_once(api, dev, scale: float = 1.0) -> dict:
     """The heterogeneous adaptive batch (unit square / L-shape / unit cube,
-    per-node dt in {1e-3, 1e-4}) at a reduced scale: target SE 1e-4/sqrt(scale)
-    and n_max = 1e6 * scale; one warm-up call builds and replays the graph,
-    one timed replay."""
+    per-node dt in {1e-3, 1e-4}), at full scale by default (target SE 1e-4,
+    n_max = 1e6), or reduced: target SE 1e-4/sqrt(scale), n_max = 1e6 * scale;
+    one warm-up call builds and replays the graph, one timed replay.  Reports
+    nodes/s over all nodes and over the nodes that reached the target SE."""
     import torch
     w = W.workload(3)
     stream = torch.cuda.Stream(dev)
@@ -535,10 +578,16 @@ def run_batch_once(api, dev, scale: float = 0.05) -> dict:
         stream.synchronize()
         ms = b0.elapsed_time(b1)
         npaths = r["n"].double()
-        out = {"workload": w["name"] + f" at scale {scale}", "ms": ms,
+        se = r["se"]
+        at_target = int((se <= kw["target_se"]).sum())
+        out = {"workload": w["name"] + (f" at scale {scale}" if scale != 1.0 else " (full scale)"),
+               "ms": ms,
                "path_steps": steps, "path_steps_per_s": steps / (ms / 1e3),
                "nodes": int(r["n"].numel()), "nodes_per_s": r["n"].numel() / (ms / 1e3),
-               "paths": float(npaths.sum()), "median_se": float(r["se"].median()),
+               "nodes_at_target_se": at_target,
+               "nodes_per_s_at_target_se": at_target / (ms / 1e3),
+               "nodes_at_n_max": int((r["n"] >= kw["n_max"]).sum()),
+               "paths": float(npaths.sum()), "median_se": float(se.median()),
                "target_se": kw["target_se"], "n_max": kw["n_max"],
                "launch": "pilot + main persistent launches in one captured CUDA graph"}
         ctx.close()
@@ -547,7 +596,8 @@ def run_batch_once(api, dev, scale: float = 0.05) -> dict:
 
 KERNEL_SOURCES = ("paper_1705_03666_gb300/csrc/path_kernel.cuh",
                   "paper_1705_03666_gb300/csrc/models.cuh",
-                  "paper_1705_03666_gb300/csrc/common.cuh")
+                  "paper_1705_03666_gb300/csrc/common.cuh",
+                  "paper_1705_03666_gb300/csrc/nodefix.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -588,7 +638,8 @@ def main():
     ap.add_argument("--no-naive", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-others", action="store_true")
-    ap.add_argument("--batch-scale", type=float, default=0.05)
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="scale of the adaptive batch (1.0: SE* = 1e-4, n_max = 1e6)")
     ap.add_argument("--paths", type=int, default=None,
                     help="paths per node (profiling runs only; the benchmark uses 1e5)")
     args = ap.parse_args()

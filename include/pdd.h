@@ -109,11 +109,31 @@ typedef struct {
   int64_t path_offset;   /* index of the first path (resume/extend a run) */
   int32_t precision;     /* PDD_FP32 or PDD_FP64 path arithmetic */
   int32_t bridge;        /* 1: Brownian-bridge exit test, 0: plain test */
+  int64_t node_offset;   /* stream index of the first node: node j of the call
+                            draws the streams of node node_offset + j, so a
+                            block of a larger node list solved on its own (one
+                            rank of a node-sharded run) reproduces the
+                            single-call paths; node_offset + n <= 2^32 */
 } pdd_mc_params;
 
-/* Optional diagnostics.  Inputs: the two optional device buffers receive, for
- * every (node, path) in node-major order, the path's score (FP64) and its exit
- * step (0 for a node on the boundary, -max_steps for a capped path).
+/* Per-node flags (pdd_diag.d_node_flags), OR-ed. */
+enum {
+  PDD_NODE_ON_BOUNDARY = 1, /* node on the boundary: u = g exactly, no steps */
+  PDD_NODE_OUTSIDE = 2,     /* node outside the closed domain (or a score
+                               beyond 2^30 in magnitude): mean and se are NaN */
+  PDD_NODE_CAPPED = 4,      /* some path / walk hit the step cap (counted) */
+  PDD_NODE_DISCARDED = 8,   /* branching: some trees were pruned (discarded) */
+  PDD_NODE_EMPTY = 16,      /* no sample kept: mean and se are NaN */
+  PDD_NODE_SE_UNMET = 32    /* adaptive batch: N_i stopped at n_max with the
+                               standard error still above target_se */
+};
+
+/* Optional diagnostics.  Inputs: the optional device buffers receive, for
+ * every (node, path) in node-major order, the path's score (FP64), its exit
+ * step (0 for a node on the boundary, -max_steps for a capped path) and
+ * (pdd_interface_solve only) its exit point (FP64 [dim], the projection on
+ * the nearest face for a capped path), and per node its flags
+ * (PDD_NODE_*; pdd_interface_solve, pdd_branching_solve, pdd_batch_solve).
  * Outputs (host, valid when the call returns): total Euler steps taken and the
  * number of capped paths/trees. */
 typedef struct {
@@ -124,6 +144,8 @@ typedef struct {
                               L_1..L_16, or NULL */
   int64_t path_steps;      /* out */
   int64_t capped;          /* out */
+  double *d_path_exit;     /* [n * n_paths][dim] or NULL */
+  int32_t *d_node_flags;   /* [n] or NULL */
 } pdd_diag;
 
 typedef struct pdd_ctx pdd_ctx;
@@ -148,11 +170,16 @@ PDD_API pdd_status pdd_set_stream(pdd_ctx *ctx, void *cuda_stream);
  * Sec. 2.1).  Writes d_mean[n], d_se[n] (standard error of the mean, FP64)
  * and, if non-NULL, d_npaths[n] (int64).  A node on the boundary gets
  * u = g(x_i) with zero error.  Path i of node j uses the Philox stream
- * (key = seed, counter = (block, path_offset + i, j, 0)); the per-step use of
+ * (key = seed, counter = (block, path_offset + i, node_offset + j, 0)); the
+ * per-step use of
  * that stream is fixed: three blocks per four steps (2-D: step 4q+j takes
  * its normals from words 2j, 2j+1 of blocks 3q..3q+2 by Box-Muller and its
  * bridge uniform from word 8+j; 3-D: normals from the word pairs, bridge
  * uniforms from the words' low bytes).
+ * The per-node mean and standard error come from exact integer sums of the
+ * scores and their squares (each truncated once to 2^-60), so they are
+ * bitwise independent of scheduling and launch shape, and no per-path score
+ * is stored: the call needs 112 bytes of context scratch per node.
  * With diag non-NULL the call synchronises and returns PDD_ECAP if some path
  * hit max_steps, PDD_EINVAL if a node lies outside the closed domain (its
  * mean is NaN either way).                                                 */
@@ -446,9 +473,13 @@ PDD_API pdd_status pdd_autotune_batch(pdd_ctx *ctx, const pdd_problem *problems,
  * which do not depend on scheduling):
  *   blocks_per_sm    resident 256-thread blocks per SM for the persistent
  *                    path kernels (0 = the occupancy maximum);
- *   wave_max_paths   paths per wave: each wave stores one score per path in
- *                    the context's scratch (4 or 8 bytes per path) and is
- *                    reduced before the next starts (0 = default 2^29).     */
+ *   wave_max_paths   paths per wave of the kernels that store one score per
+ *                    path in the context's scratch (Walk on Spheres,
+ *                    reflecting faces, branching, multilevel, gradient; 4 or
+ *                    8 bytes per path), each wave reduced before the next
+ *                    starts (0 = default 2^29).  pdd_interface_solve with
+ *                    absorbing faces stores no per-path score and runs all
+ *                    paths in one launch.                                   */
 PDD_API pdd_status pdd_set_tuning(pdd_ctx *ctx, int blocks_per_sm,
                                   int64_t wave_max_paths);
 

@@ -96,7 +96,7 @@ def _load():
             lib.orc_philox_constants.argtypes = [up]
             lib.orc_interface_solve.argtypes = [P, dp, ctypes.c_int64, lp, M,
                                                 ctypes.c_int64, dp, dp, lp, dp,
-                                                ip, lp, lp]
+                                                ip, dp, lp, lp]
             lib.orc_interface_solve.restype = ctypes.c_int
             lib.orc_interface_jacobian.argtypes = [P, dp, ctypes.c_int64, M, dp, dp, dp, ip]
             lib.orc_interface_jacobian.restype = ctypes.c_int
@@ -203,8 +203,8 @@ def interface_solve(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
     node_ids (optional) gives the node index each node's random streams use
     (default: its position), so a subset of a large node list can be
     recomputed on the same streams.  Returns a dict with mean, se, n (per
-    node), total_steps, capped, and, when dump_paths, score[n, N] and
-    steps[n, N] per path."""
+    node), total_steps, capped, and, when dump_paths, score[n, N],
+    steps[n, N] and exit[n, N, dim] (exit point) per path."""
     lib = _load()
     nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, int(prob["dim"]))
     n = nodes.shape[0]
@@ -214,6 +214,7 @@ def interface_solve(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
     npaths = np.zeros(n, dtype=np.int64)
     score = np.zeros((n, n_paths)) if dump_paths else None
     steps = np.zeros((n, n_paths), dtype=np.int32) if dump_paths else None
+    xexit = np.zeros((n, n_paths, int(prob["dim"]))) if dump_paths else None
     ts, tc = ctypes.c_int64(0), ctypes.c_int64(0)
     ids = None if node_ids is None else np.ascontiguousarray(node_ids, dtype=np.int64)
     if ids is not None and ids.shape != (n,):
@@ -224,14 +225,14 @@ def interface_solve(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
                                  _ptr(mean, ctypes.c_double), _ptr(se, ctypes.c_double),
                                  _ptr(npaths, ctypes.c_int64),
                                  _ptr(score, ctypes.c_double),
-                                 _ptr(steps, ctypes.c_int32), ctypes.byref(ts),
-                                 ctypes.byref(tc))
+                                 _ptr(steps, ctypes.c_int32), _ptr(xexit, ctypes.c_double),
+                                 ctypes.byref(ts), ctypes.byref(tc))
     if rc != 0:
         raise ValueError("oracle interface_solve: invalid arguments")
     out = {"mean": mean, "se": se, "n": npaths, "total_steps": ts.value,
            "capped": tc.value}
     if dump_paths:
-        out["score"], out["steps"] = score, steps
+        out["score"], out["steps"], out["exit"] = score, steps, xexit
     return out
 
 

@@ -695,6 +695,7 @@ typedef struct {
   int64_t *npaths;
   double *path_score;
   int32_t *path_steps;
+  double *path_exit;       /* [n][N][dim] exit points, or NULL */
   int64_t *steps_per_node, *capped_per_node;
   int64_t path_offset;
   const int64_t *node_ids; /* stream node index per node, or NULL (= i) */
@@ -710,8 +711,11 @@ static void solve_node(void *vp, int64_t i) {
     double s;
     int32_t st;
     uint32_t sid = (uint32_t)(S->node_ids ? S->node_ids[i] : i);
+    double xe[3];
     simulate_path(S->P, S->M, sid, (uint32_t)(p + S->path_offset),
-                  S->nodes + i * dim, &s, &st, NULL, NULL, NULL);
+                  S->nodes + i * dim, &s, &st, xe, NULL, NULL);
+    if (S->path_exit)
+      for (int k = 0; k < dim; ++k) S->path_exit[(i * N + p) * dim + k] = xe[k];
     double delta = s - mean;
     mean += delta / (double)(p + 1);
     m2 += delta * (s - mean);
@@ -731,15 +735,15 @@ int orc_interface_solve(const orc_problem *P, const double *nodes, int64_t n,
                         const int64_t *node_ids, const orc_mc *M,
                         int64_t path_offset, double *mean,
                         double *se, int64_t *npaths, double *path_score,
-                        int32_t *path_steps, int64_t *total_steps,
-                        int64_t *total_capped) {
+                        int32_t *path_steps, double *path_exit,
+                        int64_t *total_steps, int64_t *total_capped) {
   if (!P || !M || n < 0 || M->n_paths < 1 || M->dt <= 0.0 || P->dim < 1 ||
       P->dim > 3 || M->max_steps < 1)
     return 1;
   int64_t *spn = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   int64_t *cpn = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   solve_ctx S = {P, M, nodes, mean, se, npaths, path_score, path_steps,
-                 spn, cpn, path_offset, node_ids};
+                 path_exit, spn, cpn, path_offset, node_ids};
   parallel_for(n, M->n_threads, solve_node, &S);
   int64_t ts = 0, tc = 0;
   for (int64_t i = 0; i < n; ++i) { ts += spn[i]; tc += cpn[i]; }

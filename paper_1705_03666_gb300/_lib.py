@@ -31,7 +31,7 @@ class MCParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
                 ("n_paths", ctypes.c_int64), ("max_steps", ctypes.c_int64),
                 ("path_offset", ctypes.c_int64), ("precision", ctypes.c_int32),
-                ("bridge", ctypes.c_int32)]
+                ("bridge", ctypes.c_int32), ("node_offset", ctypes.c_int64)]
 
 
 class BranchParams(ctypes.Structure):
@@ -83,7 +83,13 @@ class WosParams(ctypes.Structure):
 class Diag(ctypes.Structure):
     _fields_ = [("d_path_score", ctypes.c_void_p), ("d_path_steps", ctypes.c_void_p),
                 ("d_path_aux", ctypes.c_void_p), ("path_steps", ctypes.c_int64),
-                ("capped", ctypes.c_int64)]
+                ("capped", ctypes.c_int64), ("d_path_exit", ctypes.c_void_p),
+                ("d_node_flags", ctypes.c_void_p)]
+
+
+# per-node flags (pdd_diag.d_node_flags)
+NODE_FLAGS = {"on_boundary": 1, "outside": 2, "capped": 4, "discarded": 8, "empty": 16,
+              "se_unmet": 32}
 
 
 _lock = threading.Lock()

@@ -86,14 +86,17 @@ class Context:
     # ------------------------------------------------------------------
     def interface_solve(self, nodes, *, seed: int, dt: float, n_paths: int,
                         max_steps: int = 2**31 - 1, precision: str = "fp32",
-                        bridge: bool = True, path_offset: int = 0,
+                        bridge: bool = True, path_offset: int = 0, node_offset: int = 0,
                         dump_paths: bool = False, diag: bool = False, out=None) -> dict:
         """pdd_interface_solve on torch tensors.
 
         nodes: [n, dim] float64 (CUDA tensor, or a CPU tensor that is copied).
+        node_offset: stream index of the first node (a node block of a larger
+        list draws that list's streams).
         Returns mean, se (float64 [n]) and n (int64 [n]) as CUDA tensors; with
-        diag or dump_paths also path_steps / capped (host ints) and, with
-        dump_paths, score [n, n_paths] float64 and steps [n, n_paths] int32."""
+        diag or dump_paths also path_steps / capped (host ints) and flags
+        (int32 [n], PDD_NODE_* bits) and, with dump_paths, score [n, n_paths]
+        float64, steps [n, n_paths] int32 and exit [n, n_paths, dim] float64."""
         dim = int(self.prob["dim"])
         nodes = _dev_f64(nodes, self.device).reshape(-1, dim)
         n = nodes.shape[0]
@@ -104,16 +107,21 @@ class Context:
         else:
             mean, se, npaths = out
         mc = _lib.MCParams(int(seed) & (2**64 - 1), float(dt), int(n_paths), int(max_steps),
-                           int(path_offset), _lib.PRECISION[precision], int(bool(bridge)))
+                           int(path_offset), _lib.PRECISION[precision], int(bool(bridge)),
+                           int(node_offset))
         res = {"mean": mean, "se": se, "n": npaths}
         dg = None
         if diag or dump_paths:
             dg = _lib.Diag()
+            res["flags"] = torch.zeros(n, dtype=_I32, device=self.device)
+            dg.d_node_flags = res["flags"].data_ptr()
             if dump_paths:
                 res["score"] = torch.empty((n, int(n_paths)), dtype=_F64, device=self.device)
                 res["steps"] = torch.empty((n, int(n_paths)), dtype=_I32, device=self.device)
+                res["exit"] = torch.empty((n, int(n_paths), dim), dtype=_F64, device=self.device)
                 dg.d_path_score = res["score"].data_ptr()
                 dg.d_path_steps = res["steps"].data_ptr()
+                dg.d_path_exit = res["exit"].data_ptr()
         with torch.cuda.device(self.device):
             self._bind_stream()
             st = self.lib.pdd_interface_solve(self.handle, nodes.data_ptr(), n, ctypes.byref(mc),

@@ -397,7 +397,7 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
     B.combo = combo;
     B.bridge = bp->bridge ? 1 : 0;
     B.sigma = P.sigma;
-    B.c_kill = P.kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0;
+    B.c_kill = constant_kill(P.kind);
     B.mc.n_params = P.n_params;
     for (int i = 0; i < P.n_params; ++i) {
       if (!std::isfinite(P.params[i])) return fail(ctx, PDD_EINVAL, "non-finite parameter");

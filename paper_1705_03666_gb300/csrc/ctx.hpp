@@ -67,6 +67,13 @@ inline int reflect_mask(const pdd_ctx *ctx) {
   return static_cast<int>(ctx->params[0]);
 }
 
+// The paper's constant killing rate c of a family (Eq. 2.3 in the elliptic
+// form; 0 where the family has no killing): the 3-D manufactured problem
+// (1/2) Lap u + b . grad u - u = F has c = -1.
+inline double constant_kill(int kind) {
+  return kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0;
+}
+
 inline pdd_status fail(pdd_ctx *ctx, pdd_status st, const char *fmt, ...) {
   if (ctx) {
     char buf[512];

@@ -162,6 +162,8 @@ pdd_status interface_grad_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   if (mc->n_paths < 1) return fail(ctx, PDD_EINVAL, "n_paths < 1");
   if (mc->path_offset < 0 || mc->path_offset + mc->n_paths > (int64_t(1) << 32))
     return fail(ctx, PDD_EINVAL, "path indices must fit in 32 bits");
+  if (mc->node_offset < 0 || mc->node_offset + n > (int64_t(1) << 32))
+    return fail(ctx, PDD_EINVAL, "node stream indices must fit in 32 bits");
   if (!(mc->dt > 0.0) || !std::isfinite(mc->dt)) return fail(ctx, PDD_EINVAL, "dt must be > 0");
   if (ctx->prob.sigma * ctx->prob.sigma * mc->dt > 1.0 / 36.0)
     return fail(ctx, PDD_EINVAL, "sigma^2 dt must be <= 1/36");
@@ -203,6 +205,7 @@ pdd_status interface_grad_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   a.nodes = d_nodes;
   a.n_paths = N;
   a.path_offset = static_cast<uint64_t>(mc->path_offset);
+  a.node_offset = static_cast<uint32_t>(mc->node_offset);
   a.cursor = cursor;
   a.counters = counters;
   a.score = rec;

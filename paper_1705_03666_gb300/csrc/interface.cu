@@ -5,7 +5,6 @@
 
 #include "ctx.hpp"
 #include "path_kernel.cuh"
-#include "reduce.cuh"
 
 namespace pdd {
 
@@ -59,25 +58,11 @@ pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t
 }
 
 // Scratch layout for one interface solve (offsets in bytes):
-//   [0, 256)            counters (4 x u64) and the wave cursor
-//   [256, +n*24)        per-node running (count, mean, M2)
-//   [.., +wave*sizeof R) per-path scores of the current wave
-struct SolveLayout {
-  size_t acc_off, score_off, total;
-};
-
-template <typename R>
-static SolveLayout solve_layout(int64_t n, uint64_t wave) {
-  SolveLayout L;
-  L.acc_off = 256;
-  L.score_off = align_up(L.acc_off + static_cast<size_t>(n) * sizeof(NodeAcc), 256);
-  L.total = align_up(L.score_off + wave * sizeof(R), 256);
-  return L;
-}
-
-static double constant_kill(int kind) {
-  return kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0;
-}
+//   [0, 256)          counters (4 x u64) and the queue cursor
+//   [256, +n*112)     per-node exact sums (NodeFix)
+// No per-path score is stored: the path kernel adds every score to its node's
+// integer sums when the path ends, in one launch over all paths.
+constexpr size_t kFixOff = 256;
 
 template <class Model, class Geom, typename R>
 static pdd_status run_paths(pdd_ctx *ctx, const double *d_nodes, int64_t n,
@@ -85,73 +70,62 @@ static pdd_status run_paths(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                             int64_t *d_npaths, pdd_diag *diag) {
   const uint64_t N = static_cast<uint64_t>(mc->n_paths);
   const uint64_t total = static_cast<uint64_t>(n) * N;
-  const uint64_t wave = std::min<uint64_t>(total, ctx->wave_max_paths);
-  const SolveLayout L = solve_layout<R>(n, wave);
-  pdd_status st = ensure_scratch(ctx, L.total);
+  const size_t bytes = align_up(kFixOff + static_cast<size_t>(n) * sizeof(NodeFix), 256);
+  pdd_status st = ensure_scratch(ctx, bytes);
   if (st != PDD_OK) return st;
   char *base = static_cast<char *>(ctx->scratch);
   auto *counters = reinterpret_cast<unsigned long long *>(base);
   auto *cursor = counters + 4;
-  auto *acc = reinterpret_cast<NodeAcc *>(base + L.acc_off);
-  R *score = reinterpret_cast<R *>(base + L.score_off);
-  PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, L.score_off, ctx->stream));
+  auto *fix = reinterpret_cast<NodeFix *>(base + kFixOff);
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, bytes, ctx->stream));
 
   PathArgs a;
   std::memset(&a, 0, sizeof a);
   a.nodes = d_nodes;
   a.n_paths = N;
   a.path_offset = static_cast<uint64_t>(mc->path_offset);
+  a.node_offset = static_cast<uint32_t>(mc->node_offset);
   a.cursor = cursor;
   a.counters = counters;
-  a.score = score;
+  a.fix = fix;
+  a.begin = 0;
+  a.end = total;
   a.rk = make_round_keys(mc->seed);
   const double sig = ctx->prob.sigma, dt = mc->dt;
+  const double c_kill = constant_kill(ctx->prob.kind);
   a.inv_s2dt = 1.0 / (sig * sig * dt);
   a.dt_d = dt;
   a.sdt_d = sig * std::sqrt(dt);
   a.thr_d = 9.0 * sig * sig * dt;
-  a.ecdt_d = std::exp(constant_kill(ctx->prob.kind) * dt);
+  a.ecdt_d = std::exp(c_kill * dt);
   a.dt_f = static_cast<float>(a.dt_d);
   a.sdt_f = static_cast<float>(a.sdt_d);
   a.thr_f = static_cast<float>(a.thr_d);
-  a.l2cdt_f = static_cast<float>(constant_kill(ctx->prob.kind) * dt * 1.4426950408889634);
+  a.l2cdt_f = static_cast<float>(c_kill * dt * 1.4426950408889634);
   a.max_steps = static_cast<int32_t>(mc->max_steps);
   a.bridge = mc->bridge ? 1 : 0;
   a.mc = ctx->mc;
+  if (diag) {
+    a.dump_score = diag->d_path_score;
+    a.steps = diag->d_path_steps;
+    a.dump_exit = diag->d_path_exit;
+  }
 
   auto kern = path_kernel<Model, Geom, R>;
   int bps = 0;
   PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlock, 0));
   if (bps < 1) bps = 1;
   if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
-  const uint64_t lanes_needed = (wave + 31) / 32;  // warps needed at most
   uint64_t grid = static_cast<uint64_t>(bps) * ctx->num_sms;
-  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (lanes_needed * 32 + kPathBlock - 1) / kPathBlock));
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + kPathBlock - 1) / kPathBlock));
 
-  for (uint64_t b0 = 0; b0 < total; b0 += wave) {
-    const uint64_t b1 = std::min(total, b0 + wave);
-    if (b0 > 0) PDD_CUDA_TRY(ctx, cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), ctx->stream));
-    a.begin = b0;
-    a.end = b1;
-    a.steps = (diag && diag->d_path_steps) ? diag->d_path_steps + b0 : nullptr;
-    const auto ev = prof_slot(ctx);
-    if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
-    kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);
-    PDD_CUDA_TRY(ctx, cudaGetLastError());
-    if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
-    const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
-    reduce_wave_kernel<R><<<static_cast<unsigned>(node_hi - node_lo + 1), kReduceBlock, 0,
-                            ctx->stream>>>(score, b0, b1, N, node_lo, acc);
-    PDD_CUDA_TRY(ctx, cudaGetLastError());
-    if (diag && diag->d_path_score) {
-      const uint64_t cnt = b1 - b0;
-      const unsigned g = static_cast<unsigned>(std::min<uint64_t>((cnt + 255) / 256, 8192));
-      widen_scores_kernel<R><<<g, 256, 0, ctx->stream>>>(score, diag->d_path_score + b0, cnt);
-      PDD_CUDA_TRY(ctx, cudaGetLastError());
-    }
-  }
-  finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(
-      acc, n, d_mean, d_se, d_npaths);
+  const auto ev = prof_slot(ctx);
+  if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
+  kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
+  fix_finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(
+      fix, n, d_mean, d_se, d_npaths, diag ? diag->d_node_flags : nullptr);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
 
   if (diag) {
@@ -183,6 +157,8 @@ pdd_status interface_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   if (mc->n_paths < 1) return fail(ctx, PDD_EINVAL, "n_paths < 1");
   if (mc->path_offset < 0 || mc->path_offset + mc->n_paths > (int64_t(1) << 32))
     return fail(ctx, PDD_EINVAL, "path indices must fit in 32 bits");
+  if (mc->node_offset < 0 || mc->node_offset + n > (int64_t(1) << 32))
+    return fail(ctx, PDD_EINVAL, "node stream indices must fit in 32 bits");
   if (!(mc->dt > 0.0) || !std::isfinite(mc->dt)) return fail(ctx, PDD_EINVAL, "dt must be > 0");
   if (mc->max_steps < 1 || mc->max_steps > 2147483647LL)
     return fail(ctx, PDD_EINVAL, "max_steps out of range");

@@ -26,7 +26,8 @@ naive_node_kernel(const __grid_constant__ PathArgs a, uint32_t node, double *acc
     for (int d = 0; d < D; ++d) X[d] = static_cast<float>(a.nodes[static_cast<uint64_t>(node) * D + d]);
     float Y = 1.f, Z = 0.f, s = 0.f;
     int32_t n = 0;
-    const PhiloxPath pp = philox_path(static_cast<uint32_t>(p + a.path_offset), node, 0u, a.rk);
+    const PhiloxPath pp =
+        philox_path(static_cast<uint32_t>(p + a.path_offset), node + a.node_offset, 0u, a.rk);
     bool done = !Geom::inside_open(X);
     if (done) s = Model::g(a.mc, X);
     while (!done && n < a.max_steps)
@@ -91,9 +92,10 @@ static pdd_status run_naive(pdd_ctx *ctx, const double *d_nodes, int64_t n, cons
   a.nodes = d_nodes;
   a.n_paths = static_cast<uint64_t>(mc->n_paths);
   a.path_offset = static_cast<uint64_t>(mc->path_offset);
+  a.node_offset = static_cast<uint32_t>(mc->node_offset);
   a.rk = make_round_keys(mc->seed);
   const double sig = ctx->prob.sigma, dt = mc->dt;
-  const double c_kill = ctx->prob.kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0;
+  const double c_kill = constant_kill(ctx->prob.kind);
   a.inv_s2dt = 1.0 / (sig * sig * dt);
   a.dt_f = static_cast<float>(dt);
   a.sdt_f = static_cast<float>(sig * std::sqrt(dt));
@@ -122,6 +124,7 @@ pdd_status interface_solve_naive_impl(pdd_ctx *ctx, const double *d_nodes, int64
   if (!mc || n < 0 || n > (int64_t(1) << 32) || mc->n_paths < 1 || !(mc->dt > 0.0) ||
       mc->max_steps < 1 || mc->max_steps > 2147483647LL || mc->precision != PDD_FP32 ||
       mc->path_offset < 0 || mc->path_offset + mc->n_paths > (int64_t(1) << 32) ||
+      mc->node_offset < 0 || mc->node_offset + n > (int64_t(1) << 32) ||
       ctx->prob.sigma * ctx->prob.sigma * mc->dt > 1.0 / 36.0)
     return fail(ctx, PDD_EINVAL, "invalid parameters for the naive solve (FP32 only)");
   if (reflect_mask(ctx) != 0)

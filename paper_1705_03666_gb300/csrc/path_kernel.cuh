@@ -6,10 +6,11 @@
 // warp's stash of set-up paths (refilled 32 indices at a time from an atomic
 // cursor), so no lane waits for a long path of another node (lane refill) and
 // the only idle time is at the very end of the wave.
-// Ended paths are parked per warp and scored 32 at a time; a path's score and
-// exit step go to a per-path slot, and a separate reduction (reduce.cuh) forms
-// the per-node mean and standard error in a fixed order, so the result does
-// not depend on which lane ran which path.
+// Ended paths are parked per warp and scored 32 at a time, and the scores are
+// added at once to exact per-node integer sums (nodefix.cuh), so the per-node
+// mean and standard error do not depend on which lane ran which path and no
+// per-path score is stored (the gradient mode keeps a per-path record for its
+// Jacobian reduction).
 //
 // Per step (Eq. 2.8, Dirichlet/elliptic reduction of Sec. 2.2, left-point rule):
 //   X' = X + b(X) dt + sigma sqrt(dt) xi,  Y' = Y e^{c(X) dt},  Z' = Z + f(X) Y dt,
@@ -26,6 +27,7 @@
 
 #include "common.cuh"
 #include "models.cuh"
+#include "nodefix.cuh"
 
 namespace pdd {
 
@@ -35,10 +37,14 @@ struct PathArgs {
   const double *nodes;          // [n_nodes][D]
   uint64_t n_paths;             // paths per node
   uint64_t path_offset;         // first path index
-  uint64_t begin, end;          // global index range of this wave
+  uint32_t node_offset;         // stream index of node 0 (node j draws node_offset + j)
+  uint64_t begin, end;          // global index range of this launch (a wave)
   unsigned long long *cursor;   // queue cursor for this wave (starts at 0)
   unsigned long long *counters; // [0] path steps, [1] capped, [2] bad nodes
-  void *score;                  // R[end - begin]
+  NodeFix *fix;                 // forward mode: per-node exact sums [n_nodes]
+  void *score;                  // gradient mode: GradRec[end - begin]
+  double *dump_score;           // forward mode, optional: score per path [end - begin]
+  double *dump_exit;            // forward mode, optional: exit point per path [end - begin][D]
   int32_t *steps;               // [end - begin] or null
   RoundKeys rk;
   double inv_s2dt;              // 1 / (sigma^2 dt)
@@ -446,20 +452,15 @@ struct GradRec {
   float L[kMaxLR];
 };
 
-// Result of one path, in two parts: the score (forward mode: the score
-// plane; gradient mode: the record's first four words, score and exit point)
-// with the step count, and, in gradient mode, the likelihood-ratio sums.
-template <int D, typename R, bool kLR>
+// Gradient mode: the record's first four words (score and exit point) with
+// the step count, and the likelihood-ratio sums.
+template <int D, typename R>
 __device__ __forceinline__ void write_score(const PathArgs &a, uint64_t slot, R s, int32_t st,
                                             const R *xe) {
-  if constexpr (kLR) {
-    float4 *o = reinterpret_cast<float4 *>(static_cast<GradRec *>(a.score) + slot);
-    o[0] = make_float4(static_cast<float>(s), static_cast<float>(xe[0]),
-                       D > 1 ? static_cast<float>(xe[D > 1 ? 1 : 0]) : 0.f,
-                       D > 2 ? static_cast<float>(xe[D > 2 ? 2 : 0]) : 0.f);
-  } else {
-    static_cast<R *>(a.score)[slot] = s;
-  }
+  float4 *o = reinterpret_cast<float4 *>(static_cast<GradRec *>(a.score) + slot);
+  o[0] = make_float4(static_cast<float>(s), static_cast<float>(xe[0]),
+                     D > 1 ? static_cast<float>(xe[D > 1 ? 1 : 0]) : 0.f,
+                     D > 2 ? static_cast<float>(xe[D > 2 ? 2 : 0]) : 0.f);
   if (a.steps) a.steps[slot] = st;
 }
 template <typename R>
@@ -471,11 +472,25 @@ __device__ __forceinline__ void write_lr_sums(const PathArgs &a, uint64_t slot, 
     o[1 + q] = make_float4(c * static_cast<float>(L[4 * q]), c * static_cast<float>(L[4 * q + 1]),
                            c * static_cast<float>(L[4 * q + 2]), c * static_cast<float>(L[4 * q + 3]));
 }
-template <int D, typename R, bool kLR>
-__device__ __forceinline__ void write_result(const PathArgs &a, uint64_t slot, R s, int32_t st,
-                                             const R *xe, const R *L) {
-  write_score<D, R, kLR>(a, slot, s, st, xe);
-  if constexpr (kLR) write_lr_sums<R>(a, slot, L);
+
+// Node of global path index g (32-bit division when the indices fit).
+__device__ __forceinline__ uint64_t path_node(const PathArgs &a, uint64_t g) {
+  if (a.end <= 0xffffffffull)
+    return static_cast<uint32_t>(g) / static_cast<uint32_t>(a.n_paths);
+  return g / a.n_paths;
+}
+
+// Forward mode: optional per-path record (score, exit step, exit point) for
+// parity checks, in the caller's buffers.
+template <int D, typename R>
+__device__ __forceinline__ void dump_path(const PathArgs &a, uint64_t slot, R s, int32_t st,
+                                          const R *xe) {
+  if (a.dump_score) a.dump_score[slot] = static_cast<double>(s);
+  if (a.steps) a.steps[slot] = st;
+  if (a.dump_exit) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) a.dump_exit[slot * D + d] = static_cast<double>(xe[d]);
+  }
 }
 
 // Per-warp staging in shared memory (one column per lane).  Claiming and
@@ -527,30 +542,40 @@ __device__ __forceinline__ int stage_starts(const PathArgs &a, StartStash<Model:
   bool interior = false;
   R x[D];
   PhiloxPath pp{0, 0, 0};
+  uint64_t node = 0;
+  R s0 = R(0);
   if (q < span) {
     const unsigned long long g = a.begin + q;
-    uint64_t node;
-    if (a.end <= 0xffffffffull) {  // 32-bit division when the indices fit
-      node = static_cast<uint32_t>(g) / static_cast<uint32_t>(a.n_paths);
-    } else {
-      node = g / a.n_paths;
-    }
+    node = path_node(a, g);
     const uint64_t path = g - node * a.n_paths + a.path_offset;
-    pp = philox_path(static_cast<uint32_t>(path), static_cast<uint32_t>(node), 0u, a.rk);
+    pp = philox_path(static_cast<uint32_t>(path), static_cast<uint32_t>(node) + a.node_offset, 0u,
+                     a.rk);
 #pragma unroll
     for (int d = 0; d < D; ++d) x[d] = static_cast<R>(a.nodes[node * D + d]);
     interior = Geom::inside_open(x);
     if (!interior) {
-      R s = Model::g(a.mc, x);
+      s0 = Model::g(a.mc, x);
       if (!Geom::inside_closed(x)) {
-        s = R(NAN);
+        s0 = R(NAN);
         ++my_bad;
       }
-      R L0[kLR ? kMaxLR : 1];
+      if constexpr (kLR) {
+        R L0[kMaxLR];
 #pragma unroll
-      for (int j = 0; j < (kLR ? kMaxLR : 1); ++j) L0[j] = R(0);
-      write_result<D, R, kLR>(a, q, s, 0, x, L0);
+        for (int j = 0; j < kMaxLR; ++j) L0[j] = R(0);
+        write_score<D, R>(a, q, s0, 0, x);
+        write_lr_sums<R>(a, q, L0);
+      } else {
+        dump_path<D, R>(a, q, s0, 0, x);
+      }
     }
+  }
+  if constexpr (!kLR) {
+    // starts on the boundary (u = g, tau = 0) or outside the closed domain
+    // (NaN) go straight into the node's sums
+    const bool at_bnd = q < span && !interior;
+    if (__any_sync(kFull, at_bnd))
+      fix_commit<R>(a.fix, at_bnd, node, s0, false, true);
   }
   const unsigned im = __ballot_sync(kFull, interior);
   if (interior) {
@@ -566,13 +591,16 @@ __device__ __forceinline__ int stage_starts(const PathArgs &a, StartStash<Model:
 }
 
 // Called by all 32 lanes: score the first cnt parked paths, one per lane, and
-// write their scores (gradient mode: the record's score and exit point; the
-// likelihood-ratio sums were written when the path ended).
+// add the scores to their nodes' sums (gradient mode: write the record's score
+// and exit point; the likelihood-ratio sums were written when the path ended).
 template <class Model, class Geom, typename R, bool kLR>
 __device__ __forceinline__ void flush_exits(const PathArgs &a, ExitQueue<Model::D, R> &q, int cnt) {
   constexpr int D = Model::D;
   const int lane = static_cast<int>(threadIdx.x & 31u);
   __syncwarp();
+  R s = R(0);
+  uint64_t node = 0;
+  bool capped = false;
   if (lane < cnt) {
     R X[D], Xn[D], xe[D];
 #pragma unroll
@@ -581,8 +609,8 @@ __device__ __forceinline__ void flush_exits(const PathArgs &a, ExitQueue<Model::
       Xn[d] = q.xn[d][lane];
     }
     const int code = q.code[lane];
-    R s;
-    if (code == kStepCapped) {
+    capped = code == kStepCapped;
+    if (capped) {
 #pragma unroll
       for (int d = 0; d < D; ++d) xe[d] = X[d];
       Geom::project(Geom::nearest_face(X), xe);
@@ -590,8 +618,14 @@ __device__ __forceinline__ void flush_exits(const PathArgs &a, ExitQueue<Model::
     } else {
       s = exit_score<Model, Geom, R>(a.mc, code, X, Xn, q.y[lane], q.z[lane], xe);
     }
-    write_score<D, R, kLR>(a, q.slot[lane], s, q.st[lane], xe);
+    if constexpr (kLR) {
+      write_score<D, R>(a, q.slot[lane], s, q.st[lane], xe);
+    } else {
+      node = path_node(a, a.begin + q.slot[lane]);
+      dump_path<D, R>(a, q.slot[lane], s, q.st[lane], xe);
+    }
   }
+  if constexpr (!kLR) fix_commit<R>(a.fix, lane < cnt, node, s, capped, false);
   __syncwarp();
 }
 

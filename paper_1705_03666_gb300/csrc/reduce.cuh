@@ -11,6 +11,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "nodefix.cuh"
 
 namespace pdd {
 
@@ -138,14 +139,18 @@ reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
   }
 }
 
+// Mean, standard error and count per node; with `flags`, PDD_NODE_EMPTY is
+// OR-ed into the node's flags when no sample was kept (the kernels OR in the
+// rarer events themselves).
 static __global__ void finalize_kernel(const NodeAcc *acc, int64_t n_nodes, double *mean,
-                                double *se, int64_t *npaths) {
+                                       double *se, int64_t *npaths, int32_t *flags = nullptr) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n_nodes) return;
   const NodeAcc A = acc[i];
   mean[i] = A.n > 0.0 ? A.mean : static_cast<double>(NAN);  // no sample kept
   se[i] = A.n > 1.0 ? sqrt(A.m2 / (A.n - 1.0) / A.n) : (A.n > 0.0 ? 0.0 : static_cast<double>(NAN));
   if (npaths) npaths[i] = static_cast<int64_t>(A.n);
+  if (flags && !(A.n > 0.0)) flags[i] |= kNodeEmpty;
 }
 
 template <typename R>

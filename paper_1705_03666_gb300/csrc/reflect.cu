@@ -35,16 +35,28 @@ namespace pdd {
 struct ReflectArgs {
   const double *nodes;
   uint64_t n_paths, path_offset, begin, end;
+  uint32_t node_offset;          // stream index of node 0
   unsigned long long *cursor;
   unsigned long long *counters;  // [0] steps, [1] capped, [2] bad nodes
   void *score;
   int32_t *steps;
+  int32_t *flags;                // per-node flags or null (rare events, atomicOr)
+  double *exit;                  // exit point per path [end - begin][D] or null
   RoundKeys rk;
   double dt, sdt, s2dt, cdt, phi;  // dt, sigma sqrt(dt), sigma^2 dt, c dt, Robin phi
   int32_t mask;                    // bit j: face j reflects
   int32_t max_steps, bridge;
   ModelConst mc;
 };
+
+// Optional per-path exit point (parity checks).
+template <int D, typename R>
+__device__ __forceinline__ void dump_exit_point(double *exit, uint64_t slot, const R *x) {
+  if (exit) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) exit[slot * D + d] = static_cast<double>(x[d]);
+  }
+}
 
 // Special functions of the reflection branch.  A reflecting problem's paths
 // linger near their reflecting faces, so this branch runs, diverged, at most
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
         slot = q;
         const unsigned long long g = a.begin + q;
         nc.locate(g, a.n_paths, a.end, a.nodes);
-        const uint32_t node = static_cast<uint32_t>(nc.node);
+        const uint32_t node = static_cast<uint32_t>(nc.node) + a.node_offset;
         const uint32_t path = static_cast<uint32_t>(g - nc.lo + a.path_offset);
         pp = philox_path(path, node, 0u, a.rk);
         pp4 = philox_path(path, node, 4u, a.rk);
@@ -277,11 +289,15 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
         if (bad) {
           score[slot] = R(NAN);
           if (a.steps) a.steps[slot] = 0;
+          dump_exit_point<D>(a.exit, slot, X);
+          if (a.flags) atomicOr(a.flags + nc.node, kNodeOutside);
           ++my_bad;
           need = true;
         } else if (on_abs) {
           score[slot] = Model::template g<R>(a.mc, X);
           if (a.steps) a.steps[slot] = 0;
+          dump_exit_point<D>(a.exit, slot, X);
+          if (a.flags) atomicOr(a.flags + nc.node, kNodeOnBoundary);
           need = true;
         } else {
           active = true;
@@ -319,6 +335,7 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
       const R Yn = r_exp<R>(static_cast<R>(n) * k.cdt + sphil);  // n already advanced
       score[slot] = Model::template g<R>(a.mc, xe) * Yn + Zn;
       if (a.steps) a.steps[slot] = n;
+      dump_exit_point<D>(a.exit, slot, xe);
       my_steps += static_cast<unsigned long long>(n);
       active = false;
       need = true;
@@ -342,6 +359,8 @@ __global__ void __launch_bounds__(kPathBlock) reflect_kernel(const __grid_consta
       const R Yn = r_exp<R>(static_cast<R>(n) * k.cdt + sphil);
       score[slot] = Model::template g<R>(a.mc, xc) * Yn + Z;
       if (a.steps) a.steps[slot] = -n;
+      dump_exit_point<D>(a.exit, slot, xc);
+      if (a.flags) atomicOr(a.flags + nc.node, kNodeCapped);
       my_steps += static_cast<unsigned long long>(n);
       ++my_capped;
       active = false;
@@ -377,11 +396,14 @@ static pdd_status run_reflect(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   auto *acc = reinterpret_cast<NodeAcc *>(base + acc_off);
   R *score = reinterpret_cast<R *>(base + score_off);
   PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, score_off, ctx->stream));
+  int32_t *flags = diag ? diag->d_node_flags : nullptr;
+  if (flags) PDD_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, static_cast<size_t>(n) * 4, ctx->stream));
   ReflectArgs a;
   std::memset(&a, 0, sizeof a);
   a.nodes = d_nodes;
   a.n_paths = N;
   a.path_offset = static_cast<uint64_t>(mc->path_offset);
+  a.node_offset = static_cast<uint32_t>(mc->node_offset);
   a.cursor = counters + 4;
   a.counters = counters;
   a.score = score;
@@ -390,12 +412,13 @@ static pdd_status run_reflect(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   a.dt = mc->dt;
   a.sdt = sig * std::sqrt(mc->dt);
   a.s2dt = sig * sig * mc->dt;
-  a.cdt = (ctx->prob.kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0) * mc->dt;
+  a.cdt = constant_kill(ctx->prob.kind) * mc->dt;
   a.mask = static_cast<int32_t>(ctx->params[0]);
   a.phi = ctx->params[1];
   a.max_steps = static_cast<int32_t>(mc->max_steps);
   a.bridge = mc->bridge ? 1 : 0;
   a.mc = ctx->mc;
+  a.flags = flags;
   auto kern = reflect_kernel<Model, R>;
   int bps = 0;
   PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlock, 0));
@@ -409,6 +432,7 @@ static pdd_status run_reflect(pdd_ctx *ctx, const double *d_nodes, int64_t n,
     a.begin = b0;
     a.end = b1;
     a.steps = (diag && diag->d_path_steps) ? diag->d_path_steps + b0 : nullptr;
+    a.exit = (diag && diag->d_path_exit) ? diag->d_path_exit + b0 * Model::D : nullptr;
     const auto ev = prof_slot(ctx);
     if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
     kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);
@@ -425,8 +449,8 @@ static pdd_status run_reflect(pdd_ctx *ctx, const double *d_nodes, int64_t n,
       PDD_CUDA_TRY(ctx, cudaGetLastError());
     }
   }
-  finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(acc, n, d_mean,
-                                                                                d_se, d_npaths);
+  finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(
+      acc, n, d_mean, d_se, d_npaths, flags);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
   if (diag) {
     unsigned long long h[4] = {0, 0, 0, 0};

@@ -1,14 +1,13 @@
 // static_solve.cu -- pdd_interface_solve_static: the interface solve for
 // callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph capture that forbids allocation, allocators that own the whole device
-// pool, real-time or embedded loops where allocation latency and failure are
-// unacceptable, or plug-in hosts that only hand out pre-allocated buffers.
-// This entry point runs the same path kernel and per-node reduction as
-// pdd_interface_solve, but its scratch (counters, per-node running sums, one
-// wave of per-path scores) lives in a file-scope __device__ array of fixed
-// size instead of context-owned memory, and it needs no context.  It calls no
+// Some callers cannot call cudaMalloc at all: allocators that own the whole
+// device pool, real-time or embedded loops where allocation latency and
+// failure are unacceptable, or plug-in hosts that only hand out pre-allocated
+// buffers.  This entry point runs the same path kernel and per-node
+// finalisation as pdd_interface_solve, but its scratch (counters and the
+// per-node exact sums) lives in a file-scope __device__ array of fixed size
+// instead of context-owned memory, and it needs no context.  It calls no
 // cudaMalloc, cudaFree or allocating library routine.
 #include <cmath>
 #include <cstring>
@@ -16,36 +15,58 @@
 
 #include "ctx.hpp"
 #include "path_kernel.cuh"
-#include "reduce.cuh"
 
 namespace pdd {
 namespace {
 
-// 32 MiB on every GPU that loads the library, held until process exit.
-constexpr size_t kStaticScratchBytes = size_t(32) << 20;
+// 8 MiB on every GPU that loads the library, held until process exit:
+// 256 bytes of counters and 112 bytes of exact sums per node.
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;
 constexpr int64_t kStaticMaxNodes = 65536;
-constexpr size_t kStaticAccOff = 256;
-constexpr size_t kStaticScoreOff = kStaticAccOff + kStaticMaxNodes * sizeof(NodeAcc);
+constexpr size_t kStaticFixOff = 256;
+static_assert(kStaticFixOff + kStaticMaxNodes * sizeof(NodeFix) <= kStaticScratchBytes,
+              "static scratch too small for its node limit");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+bool g_loaded[kMaxDevices] = {};
 
-// Device address of the static scratch on `device` (current).  The host-side
-// name g_static_scratch is only a stand-in; the address must come from the
-// runtime, once per device.
-cudaError_t scratch_address(int device, void **out) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[device]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+// Load every kernel this entry point can launch (module loading may be lazy),
+// once per device, so that no later call has to load one.
+cudaError_t load_kernels() {
+  cudaFuncAttributes fa;
+  const void *kernels[] = {
+      reinterpret_cast<const void *>(path_kernel<LaplaceExpCos, Box<2>, float>),
+      reinterpret_cast<const void *>(path_kernel<LaplaceExpCos, Box<2>, double>),
+      reinterpret_cast<const void *>(path_kernel<EllipticManufactured, Box<3>, float>),
+      reinterpret_cast<const void *>(path_kernel<EllipticManufactured, Box<3>, double>),
+      reinterpret_cast<const void *>(path_kernel<PoissonFourier, Box<2>, float>),
+      reinterpret_cast<const void *>(path_kernel<PoissonFourier, Box<2>, double>),
+      reinterpret_cast<const void *>(fix_finalize_kernel)};
+  for (const void *k : kernels) {
+    const cudaError_t e = cudaFuncGetAttributes(&fa, k);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = p;
   }
-  *out = g_scratch_addr[device];
   return cudaSuccess;
+}
+
+// Device address of the static scratch on the current device.  The host-side
+// name g_static_scratch is only a stand-in; the address comes from the
+// runtime, looked up on every call (no allocation), so a module reloaded
+// after a device reset is never reached through a stale pointer.  The first
+// call on a device also loads the kernels.
+cudaError_t scratch_address(int device, void **out) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_loaded[device]) {
+      const cudaError_t e = load_kernels();
+      if (e != cudaSuccess) return e;
+      g_loaded[device] = true;
+    }
+  }
+  return cudaGetSymbolAddress(out, g_static_scratch);
 }
 
 bool supported(const pdd_problem *p) {
@@ -73,13 +94,10 @@ pdd_status run_static(char *base, int device, cudaStream_t stream, const pdd_pro
                       double *d_se, int64_t *d_npaths) {
   const uint64_t N = static_cast<uint64_t>(mc->n_paths);
   const uint64_t total = static_cast<uint64_t>(n) * N;
-  const uint64_t wave = std::min<uint64_t>(total, (kStaticScratchBytes - kStaticScoreOff) / sizeof(R));
   auto *counters = reinterpret_cast<unsigned long long *>(base);
-  auto *cursor = counters + 4;
-  auto *acc = reinterpret_cast<NodeAcc *>(base + kStaticAccOff);
-  R *score = reinterpret_cast<R *>(base + kStaticScoreOff);
+  auto *fix = reinterpret_cast<NodeFix *>(base + kStaticFixOff);
   // the array keeps the previous call's contents: clear what must start at 0
-  if (cudaMemsetAsync(base, 0, kStaticAccOff + static_cast<size_t>(n) * sizeof(NodeAcc), stream) !=
+  if (cudaMemsetAsync(base, 0, kStaticFixOff + static_cast<size_t>(n) * sizeof(NodeFix), stream) !=
       cudaSuccess)
     return PDD_ECUDA;
 
@@ -88,12 +106,15 @@ pdd_status run_static(char *base, int device, cudaStream_t stream, const pdd_pro
   a.nodes = d_nodes;
   a.n_paths = N;
   a.path_offset = static_cast<uint64_t>(mc->path_offset);
-  a.cursor = cursor;
+  a.node_offset = static_cast<uint32_t>(mc->node_offset);
+  a.cursor = counters + 4;
   a.counters = counters;
-  a.score = score;
+  a.fix = fix;
+  a.begin = 0;
+  a.end = total;
   a.rk = make_round_keys(mc->seed);
   const double sig = prob->sigma, dt = mc->dt;
-  const double c_kill = prob->kind == PDD_PROB_ELLIPTIC_MANUFACTURED ? -1.0 : 0.0;
+  const double c_kill = constant_kill(prob->kind);
   a.inv_s2dt = 1.0 / (sig * sig * dt);
   a.dt_d = dt;
   a.sdt_d = sig * std::sqrt(dt);
@@ -117,20 +138,10 @@ pdd_status run_static(char *base, int device, cudaStream_t stream, const pdd_pro
       cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     return PDD_ECUDA;
   uint64_t grid = static_cast<uint64_t>(std::max(bps, 1)) * static_cast<uint64_t>(num_sms);
-  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (wave + kPathBlock - 1) / kPathBlock));
-  for (uint64_t b0 = 0; b0 < total; b0 += wave) {
-    const uint64_t b1 = std::min(total, b0 + wave);
-    if (b0 > 0 && cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), stream) != cudaSuccess)
-      return PDD_ECUDA;
-    a.begin = b0;
-    a.end = b1;
-    kern<<<static_cast<unsigned>(grid), kPathBlock, 0, stream>>>(a);
-    const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
-    reduce_wave_kernel<R><<<static_cast<unsigned>(node_hi - node_lo + 1), kReduceBlock, 0, stream>>>(
-        score, b0, b1, N, node_lo, acc);
-  }
-  finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(acc, n, d_mean, d_se,
-                                                                           d_npaths);
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + kPathBlock - 1) / kPathBlock));
+  kern<<<static_cast<unsigned>(grid), kPathBlock, 0, stream>>>(a);
+  fix_finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
+      fix, n, d_mean, d_se, d_npaths, nullptr);
   return cudaGetLastError() == cudaSuccess ? PDD_OK : PDD_ECUDA;
 }
 
@@ -159,6 +170,7 @@ extern "C" pdd_status pdd_interface_solve_static(const pdd_problem *problem, int
   if (mc->n_paths < 1 || mc->path_offset < 0 ||
       mc->path_offset + mc->n_paths > (int64_t(1) << 32))
     return PDD_EINVAL;
+  if (mc->node_offset < 0 || mc->node_offset + n > (int64_t(1) << 32)) return PDD_EINVAL;
   if (!(mc->dt > 0.0) || !std::isfinite(mc->dt) ||
       problem->sigma * problem->sigma * mc->dt > 1.0 / 36.0)
     return PDD_EINVAL;

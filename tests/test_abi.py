@@ -71,13 +71,42 @@ def test_create_rejects_invalid_problem_without_gpu(lib):
 
 def test_struct_layouts(lib):
     assert ctypes.sizeof(lib.Problem) == 32
-    assert ctypes.sizeof(lib.MCParams) == 48
-    assert ctypes.sizeof(lib.Diag) == 40
+    assert ctypes.sizeof(lib.MCParams) == 56
+    assert ctypes.sizeof(lib.Diag) == 56
     assert ctypes.sizeof(lib.BranchParams) == 40
     assert ctypes.sizeof(lib.Subdomain) == 88
     assert ctypes.sizeof(lib.WosParams) == 48
     assert ctypes.sizeof(lib.GridBranchParams) == 48
     assert ctypes.sizeof(lib.MlmcParams) == 48
+
+
+def test_struct_layouts_match_c_compiler(lib, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the header's struct."""
+    import os
+    structs = {"Problem": "pdd_problem", "MCParams": "pdd_mc_params", "Diag": "pdd_diag",
+               "BranchParams": "pdd_branch_params", "GridBranchParams": "pdd_grid_branch_params",
+               "MlmcParams": "pdd_mlmc_params", "Subdomain": "pdd_subdomain",
+               "BatchNodes": "pdd_batch_nodes", "BatchParams": "pdd_batch_params",
+               "WosParams": "pdd_wos_params"}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdd.h"', "int main(void) {"]
+    expect = []
+    for py, c in structs.items():
+        cls = getattr(lib, py)
+        lines.append(f'  printf("%zu\\n", sizeof({c}));')
+        expect.append(ctypes.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({c}, {name}));')
+            expect.append(getattr(cls, name).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == expect
 
 
 def test_enum_values_match_header(lib):
@@ -96,3 +125,5 @@ def test_enum_values_match_header(lib):
             assert vals[prefix + name.upper()] == v, (prefix + name.upper(), v)
     for name in ("PDD_OK", "PDD_EINVAL", "PDD_ENOMEM", "PDD_ECUDA", "PDD_ETIMEOUT", "PDD_ECAP"):
         assert vals[name] == getattr(lib, name), name
+    for name, v in lib.NODE_FLAGS.items():
+        assert vals["PDD_NODE_" + name.upper()] == v, name

@@ -13,6 +13,7 @@ import pytest
 import torch
 
 from paper_1705_03666_gb300 import workloads as W
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -111,13 +112,8 @@ def test_lshape_matches_oracle(api, orc):
     with api.Context(prob) as ctx:
         g = ctx.interface_solve(torch.from_numpy(nodes), precision="fp32", dump_paths=True, **kw)
     o = orc.interface_solve(prob, nodes, dump_paths=True, **kw)
-    sg, stg = g["score"].cpu().numpy(), g["steps"].cpu().numpy()
-    matched = (stg == o["steps"]) & (np.abs(sg - o["score"]) <= 1e-4 * np.maximum(1, np.abs(o["score"])))
-    assert 1 - matched.mean() <= 2e-3
-    cnt = matched.sum(1)
-    mg = np.where(matched, sg, 0).sum(1) / cnt
-    mo = np.where(matched, o["score"], 0).sum(1) / cnt
-    assert np.max(np.abs(mg - mo) / np.abs(mo)) <= 1e-5
+    c = parity.compare_paths(g, o, prob=prob, geometry="l_shape")
+    parity.check("l_shape fp32", c, flip_max=2e-4)
     exact = np.exp(nodes[:, 0]) * np.cos(nodes[:, 1])
     m, se = g["mean"].cpu().numpy(), g["se"].cpu().numpy()
     assert np.all(np.abs(m - exact) <= 4 * se + 5e-3)

@@ -17,9 +17,9 @@ from paper_1705_03666_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-FLIP_MAX_FP32 = 2e-3
-NODE_REL_TOL = 1e-5
-PATH_TOL_FP32 = 1e-4
+from tests import parity
+
+FLIP_MAX_FP32 = 2e-4   # measured on GB300: no flips in these cases
 
 
 @pytest.fixture(scope="module")
@@ -31,17 +31,9 @@ def api():
     return a
 
 
-def _check(g, o, path_tol, flip_max):
-    sg, stg = g["score"].cpu().numpy(), g["steps"].cpu().numpy()
-    so, sto = o["score"], o["steps"]
-    m = (stg == sto) & (np.abs(sg - so) <= path_tol * np.maximum(1.0, np.abs(so)))
-    assert 1.0 - m.mean() <= flip_max, 1.0 - m.mean()
-    cnt = m.sum(1)
-    assert cnt.min() > 0
-    mg = np.where(m, sg, 0.0).sum(1) / cnt
-    mo = np.where(m, so, 0.0).sum(1) / cnt
-    rel = np.abs(mg - mo) / np.maximum(np.abs(mo), 0.1)
-    assert rel.max() <= NODE_REL_TOL, rel.max()
+def _check(name, g, o, geometry, prob, flip_max, path_tol=None):
+    c = parity.compare_paths(g, o, path_tol=path_tol, prob=prob, geometry=geometry)
+    parity.check(name, c, flip_max=flip_max)
 
 
 def _solve(api, prob, nodes, **kw):
@@ -49,6 +41,7 @@ def _solve(api, prob, nodes, **kw):
         return ctx.interface_solve(torch.from_numpy(nodes), dump_paths=True, diag=True, **kw)
 
 
+GEOM = {"cube": "unit_cube", "square": "unit_square", "lshape": "l_shape", "robin": "unit_square"}
 CASES = {
     "cube": (W.elliptic_manufactured(), W.workload(2)["nodes"][::256], 1e-3),
     "square": (W.laplace_expcos(), W.nodes_cfg1(16), 1e-3),
@@ -63,7 +56,7 @@ def test_fp32_matches_oracle_without_bridge(api, orc, name):
     kw = dict(seed=W.SEED_BASE + 41, dt=dt, n_paths=1500, bridge=False)
     g = _solve(api, prob, nodes, precision="fp32", **kw)
     o = orc.interface_solve(prob, nodes, dump_paths=True, **kw)
-    _check(g, o, PATH_TOL_FP32, FLIP_MAX_FP32)
+    _check(f"bridge off {name} fp32", g, o, GEOM[name], prob, FLIP_MAX_FP32)
     assert g["capped"] == 0
 
 
@@ -73,7 +66,7 @@ def test_fp64_matches_oracle_without_bridge(api, orc, name):
     kw = dict(seed=W.SEED_BASE + 42, dt=dt, n_paths=500, bridge=False)
     g = _solve(api, prob, nodes, precision="fp64", **kw)
     o = orc.interface_solve(prob, nodes, dump_paths=True, **kw)
-    _check(g, o, 1e-11, 1e-4)
+    _check(f"bridge off {name} fp64", g, o, GEOM[name], None, 1e-4, path_tol=1e-11)
     np.testing.assert_allclose(g["mean"].cpu().numpy(), o["mean"], rtol=1e-9)
 
 
