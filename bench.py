@@ -11,9 +11,11 @@ nodes per second at the achieved standard error).
 
 --impl reference times the FP64 CPU oracle (the slow, obviously correct
 restatement of the method) on the host cores, on a bounded node/path sample of
-the same workload.  Under torchrun each rank runs its own full-size batch (a
-different seed): the units are independent, so there is no collective on the
-data path and the scaling is weak.
+the same workload.  Under torchrun (N ranks) the run's node list is N copies
+of the 4096 nodes, copy r keyed by stream indices [r 4096, (r + 1) 4096):
+rank r solves its copy (node_offset) and every step ends with the method's
+one exchange, an all-gather of the per-node (count, mean, M2) triples over
+NCCL; per-GPU work is fixed, so the scaling is weak.
 """
 from __future__ import annotations
 
@@ -44,6 +46,10 @@ WORKLOAD = W.workload(2)
 # elementary operation or minimal transcendental sequence counted once;
 # derivation in the design notes.
 ALG_SLOTS_PER_PATH_STEP = 105
+# Algorithmic issue slots per particle segment of the branching estimator
+# (one Philox block 40, the lifetime's logarithm 2, a Box-Muller pair 10, the
+# move 4, psi 3, the tree product 1).
+ALG_SLOTS_PER_SEGMENT = 60
 
 
 def _env_rank():
@@ -216,13 +222,24 @@ def run_pdd(args):
     __graft_entry__.build()
     from paper_1705_03666_gb300 import api
 
+    from paper_1705_03666_gb300 import shard
+
     w = WORKLOAD
-    seed = w["seed"] + 1000 * rank
+    seed = w["seed"]
     nodes_h = torch.from_numpy(w["nodes"]).pin_memory()
     nodes = nodes_h.to(dev)
     n = nodes.shape[0]
+    node_offset, n_total = shard.copy_block(n, world, rank)
     n_paths = args.paths or w["n_paths"]
-    kw = dict(seed=seed, dt=w["dt"], n_paths=n_paths, precision="fp32", bridge=True)
+    kw = dict(seed=seed, dt=w["dt"], n_paths=n_paths, precision="fp32", bridge=True,
+              node_offset=node_offset)
+
+    def exchange(res):
+        """The method's one exchange step (N > 1): all-gather of the per-node
+        (count, mean, M2) triples of every rank's node block."""
+        if world == 1:
+            return None
+        return shard.allgather_nodes(shard.triples(res["mean"], res["se"], res["n"]), n_total)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     ctx = api.Context(w["prob"], dev)
@@ -234,7 +251,7 @@ def run_pdd(args):
     steps_per_call = r["path_steps"]
     se_median = float(out[1].median())
     for _ in range(max(0, args.warmup - 1)):
-        ctx.interface_solve(nodes, out=out, **kw)
+        exchange(ctx.interface_solve(nodes, out=out, **kw))
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream(dev)
@@ -251,7 +268,7 @@ def run_pdd(args):
     for i in range(args.steps):
         flush.zero_()                       # L2 flush between steps (outside the events)
         evs[i][0].record(stream)
-        ctx.interface_solve(nodes, out=out, **kw)
+        exchange(ctx.interface_solve(nodes, out=out, **kw))
         evs[i][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -265,6 +282,12 @@ def run_pdd(args):
     if world > 1:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
     t_total = float(t_max.item())
+    # path-steps of one step over all ranks (each rank's node copy has its own
+    # streams, so its own count)
+    steps_all = torch.tensor([float(steps_per_call)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(steps_all, op=dist.ReduceOp.SUM)
+    steps_all = float(steps_all.item())
 
     # end to end through the public API with host buffers: pinned H2D of the
     # nodes and D2H of (mean, se, n) inside the timed region
@@ -278,16 +301,21 @@ def run_pdd(args):
     for _ in range(e2e_steps):
         d_nodes = nodes_h.to(dev, non_blocking=True)
         res = ctx.interface_solve(d_nodes, out=out, **kw)
+        exchange(res)
         host_out[0].copy_(res["mean"], non_blocking=True)
         host_out[1].copy_(res["se"], non_blocking=True)
         host_out[2].copy_(res["n"], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        e_max = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(e_max, op=dist.ReduceOp.MAX)
+        e2e_s = float(e_max.item())
 
     # the plain one-node-per-launch form at the same paths per node (equal SE)
     naive = None
-    if not args.no_naive:
+    if not args.no_naive and world == 1:
         torch.cuda.synchronize()
         n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         n0.record(stream)
@@ -301,7 +329,7 @@ def run_pdd(args):
     ctx.close()
 
     batch = None
-    if not args.no_batch:
+    if not args.no_batch and world == 1:
         batch = run_batch_once(api, dev, scale=args.batch_scale)
     others = None
     if not args.no_others and world == 1:
@@ -312,7 +340,7 @@ def run_pdd(args):
             dist.destroy_process_group()
         return
 
-    value = world * args.steps * steps_per_call / t_total
+    value = args.steps * steps_all / t_total
     nodes_per_s = world * args.steps * n / t_total
     avg_kernel_s = kern_ms / 1e3 / max(1, kern_launches)
     launches_per_step = kern_launches / max(1, args.steps)
@@ -331,9 +359,12 @@ def run_pdd(args):
                    f"{w['name']} (profiling case: {n_paths} paths/node)",
                    "nodes": n, "paths_per_node": n_paths,
                    "dt": w["dt"], "path_precision": "fp32 paths, fp64 reductions",
-                   "bridge": True, "path_steps_per_step": steps_per_call,
+                   "bridge": True, "path_steps_per_step": steps_all,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"independent batches per GPU x{world}"},
+                   "parallelism": ("one GPU" if world == 1 else
+                                   f"node blocks: {world} copies of the node list "
+                                   f"({world * n} nodes, one copy per GPU by node_offset), "
+                                   "all-gather of per-node (n, mean, M2) over NCCL each step")},
         "nodes_per_s": nodes_per_s, "median_se": se_median,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "G issue-slots/s", "frac": achieved / peak, "traffic": traffic,
@@ -344,7 +375,7 @@ def run_pdd(args):
                                    "(median SM clock sampled during the timed region)"},
         "clocks": clk,
         "gpu_launches": int(args.steps * (launches_per_step + 1)),
-        "e2e": {"value": world * e2e_steps * steps_per_call / e2e_s, "unit": UNIT,
+        "e2e": {"value": e2e_steps * steps_all / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(nodes_h.numel() * 8),
                 "d2h_bytes_per_step": int(n * 24)},
     }
@@ -393,11 +424,18 @@ def run_other_workloads(api, dev) -> dict:
                   max_depth=w["max_depth"])
         r = ctx.branching_solve(nodes, diag=True, **kw)
         ms, _ = _timed(stream, lambda: ctx.branching_solve(nodes, **kw))
+        seg_s = r["segments"] / (ms / 1e3)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         out["kpp_branching"] = {"workload": w["name"], "ms": ms,
                                 "trees_per_s": len(w["nodes"]) * w["n_trees"] / (ms / 1e3),
-                                "segments_per_s": r["segments"] / (ms / 1e3),
+                                "segments_per_s": seg_s,
                                 "nodes_per_s": len(w["nodes"]) / (ms / 1e3),
-                                "median_se": float(r["se"].median())}
+                                "median_se": float(r["se"].median()),
+                                "precision": "fp32 positions, float-float tree products, "
+                                             "fp64 node sums",
+                                "issue_roofline_frac_at_2070mhz": ALG_SLOTS_PER_SEGMENT * seg_s
+                                / (n_sm * 4 * 32 * 2070e6),
+                                "alg_slots_per_segment": ALG_SLOTS_PER_SEGMENT}
         # Algorithm 3.1's time-point sharing on the same 1024 space-time
         # nodes: 64 positions x 16 times, one tree per sample for all times
         pos = torch.from_numpy(np.ascontiguousarray(w["nodes"][::16, :2])).to(dev)

@@ -230,7 +230,9 @@ PDD_API pdd_status pdd_set_params(pdd_ctx *ctx, const double *params,
  * (rebuilt when any argument or the scratch changes) and replayed; this
  * needs a non-default stream.  Writes d_mean[n], d_se[n] and, if non-NULL,
  * d_npaths[n] (= N_i).  diag (optional) reports total steps / capped paths
- * and synchronises.                                                        */
+ * and synchronises; its d_node_flags receives PDD_NODE_SE_UNMET for the nodes
+ * whose final standard error is above target_se and PDD_NODE_OUTSIDE for
+ * the nodes without an estimate.                                           */
 typedef struct {
   const double *d_nodes;     /* [n][3] FP64 (z ignored by 2-D problems) */
   const int32_t *d_problem;  /* [n] index into the problems array */
@@ -301,8 +303,11 @@ typedef struct {
  * non-NULL, d_nkept[n] (trees kept after pruning).  Tree s of node i uses
  * the Philox stream (key = seed, counter = (particle id, tree_offset + s, i,
  * 1)) with depth-first particle ids.  psi kinds: const, sigmoid,
- * travelling wave, sine (problem parameters, see pdd_problem).  Positions,
- * times, the product and the weights are FP32, the per-node sums FP64.
+ * travelling wave, sine (problem parameters, see pdd_problem).  Positions
+ * and times are FP32; a tree's product of psi values and marks alpha_k / q_k
+ * is accumulated as a float-float value (error-free binary32 products,
+ * ~2^-44 relative per factor) and rounded once to binary32; the per-node sums
+ * are FP64.  Per-node flags: PDD_NODE_DISCARDED, PDD_NODE_EMPTY.
  * With diag non-NULL the call synchronises; diag->d_path_score receives
  * per-tree scores (NaN if discarded),
  * d_path_steps per-tree segment counts (negative if discarded), path_steps
@@ -327,9 +332,9 @@ PDD_API pdd_status pdd_branching_solve(pdd_ctx *ctx, const double *d_nodes_xt,
  * Dirichlet data, 2-D families (LAPLACE_EXPCOS on the square or L-shape,
  * POISSON_FOURIER).  Writes, per node, d_mean (mean of P_l - P_{l-1}, or of
  * P_0), d_var (its sample variance) and, if non-NULL, the fine and coarse
- * means.  The caller sums the levels: mean = sum of means, se = sqrt(sum
- * var_l / n_paths_l).  diag as for pdd_interface_solve (path_steps counts
- * fine steps; d_path_score receives P_l - P_{l-1} per pair).            */
+ * means.  pdd_mlmc_solve runs the levels and combines them.  diag as for
+ * pdd_interface_solve (path_steps counts fine steps; d_path_score receives
+ * P_l - P_{l-1} per pair).                                                */
 typedef struct {
   uint64_t seed;
   int64_t n_paths;     /* pairs per node at this level */
@@ -345,6 +350,23 @@ PDD_API pdd_status pdd_mlmc_level(pdd_ctx *ctx, const double *d_nodes, int64_t n
                                   const pdd_mlmc_params *mp, double *d_mean,
                                   double *d_var, double *d_fine_mean,
                                   double *d_coarse_mean, pdd_diag *diag);
+
+/* The multilevel estimate (Sec. 2.1, Giles' method): levels 0 .. n_levels-1
+ * of pdd_mlmc_level (mp gives seed, dt0, refine, precision, bridge and the
+ * step cap; mp->level and mp->n_paths are ignored), level l with
+ * n_per_level[l] pairs per node (host array), and per node
+ *   d_mean = sum_l mean_l,   d_se = sqrt(sum_l var_l / n_per_level[l])
+ * (independent levels), summed in level order on the device.  d_level_mean
+ * and d_level_var ([n_levels][n] FP64, optional) receive the levels' means
+ * and variances; without them the library keeps the levels in a buffer of
+ * its own (2 n_levels n doubles, grown on demand, freed by pdd_destroy).
+ * 1 <= n_levels <= 13.  diag: summed path_steps and capped counts
+ * (PDD_ECAP if any walk hit the cap).                                      */
+PDD_API pdd_status pdd_mlmc_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                                  const pdd_mlmc_params *mp, int32_t n_levels,
+                                  const int64_t *n_per_level, double *d_mean,
+                                  double *d_se, double *d_level_mean,
+                                  double *d_level_var, pdd_diag *diag);
 
 /* Parameters of the time-grid branching estimator. */
 typedef struct {

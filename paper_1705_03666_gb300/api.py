@@ -138,8 +138,9 @@ class Context:
         """pdd_branching_solve: nodes_xt [n, dim+1] float64 (position, then t).
 
         Returns mean, se, n (trees kept); with diag/dump_trees also segments
-        (total) and discarded (host ints); with dump_trees score [n, n_trees]
-        (NaN = discarded) and segs [n, n_trees] (negative = discarded)."""
+        (total) and discarded (host ints) and flags (int32 [n], PDD_NODE_*);
+        with dump_trees score [n, n_trees] (NaN = discarded) and segs
+        [n, n_trees] (negative = discarded)."""
         dim = int(self.prob["dim"])
         nodes_xt = _dev_f64(nodes_xt, self.device).reshape(-1, dim + 1)
         n = nodes_xt.shape[0]
@@ -155,6 +156,8 @@ class Context:
         dg = None
         if diag or dump_trees:
             dg = _lib.Diag()
+            res["flags"] = torch.zeros(n, dtype=_I32, device=self.device)
+            dg.d_node_flags = res["flags"].data_ptr()
             if dump_trees:
                 res["score"] = torch.empty((n, int(n_trees)), dtype=_F64, device=self.device)
                 res["segs"] = torch.empty((n, int(n_trees)), dtype=_I32, device=self.device)
@@ -239,14 +242,33 @@ class Context:
         return res
 
     def mlmc_solve(self, nodes, *, seed: int, dt0: float, n_per_level, refine: int = 2,
-                   precision: str = "fp32", bridge: bool = True) -> dict:
-        """Multilevel estimate: sum of the level means, se = sqrt(sum var_l / N_l)."""
-        levels = [self.mlmc_level(nodes, seed=seed, dt0=dt0, level=l, n_paths=int(N),
-                                  refine=refine, precision=precision, bridge=bridge)
-                  for l, N in enumerate(n_per_level)]
-        mean = sum(L["mean"] for L in levels)
-        se = torch.sqrt(sum(L["var"] / float(N) for L, N in zip(levels, n_per_level)))
-        return {"mean": mean, "se": se, "levels": levels}
+                   max_steps: int = 2**31 - 1, precision: str = "fp32", bridge: bool = True,
+                   diag: bool = False) -> dict:
+        """pdd_mlmc_solve: the multilevel estimate (levels summed on the device).
+        Returns mean, se [n] and levels (per level: mean, var [n])."""
+        nodes = _dev_f64(nodes, self.device).reshape(-1, int(self.prob["dim"]))
+        n = nodes.shape[0]
+        L = len(n_per_level)
+        counts = (ctypes.c_int64 * L)(*[int(N) for N in n_per_level])
+        mean = torch.empty(n, dtype=_F64, device=self.device)
+        se = torch.empty(n, dtype=_F64, device=self.device)
+        lmean = torch.empty((L, n), dtype=_F64, device=self.device)
+        lvar = torch.empty((L, n), dtype=_F64, device=self.device)
+        mp = _lib.MlmcParams(int(seed) & (2**64 - 1), 0, int(max_steps), float(dt0), 0,
+                             int(refine), _lib.PRECISION[precision], int(bool(bridge)))
+        dg = _lib.Diag() if diag else None
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_mlmc_solve(self.handle, nodes.data_ptr(), n, ctypes.byref(mp), L,
+                                         counts, mean.data_ptr(), se.data_ptr(),
+                                         lmean.data_ptr(), lvar.data_ptr(),
+                                         ctypes.byref(dg) if dg is not None else None)
+        res = {"mean": mean, "se": se,
+               "levels": [{"mean": lmean[l], "var": lvar[l]} for l in range(L)],
+               "status": _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ECAP))}
+        if dg is not None:
+            res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
+        return res
 
     def subdomain_solve(self, lo, hi, n, iface_axis: int, iface_side: int, iface_s, iface_vals,
                         *, method: str = "cg", max_iter: int = 100000, tol: float = 1e-12,
@@ -351,6 +373,10 @@ class Context:
         bp = _lib.BatchParams(int(seed) & (2**64 - 1), int(n_pilot), int(n_min), int(n_max),
                               float(target_se), int(max_steps), int(chunk), int(bool(bridge)))
         dg = _lib.Diag() if diag else None
+        flags = None
+        if dg is not None:
+            flags = torch.zeros(n, dtype=_I32, device=self.device)
+            dg.d_node_flags = flags.data_ptr()
         with torch.cuda.device(self.device):
             self._bind_stream()
             st = self.lib.pdd_batch_solve(self.handle, arr, len(probs), ctypes.byref(bn),
@@ -362,6 +388,7 @@ class Context:
                "_keep": (nodes, pidx, dts)}
         if dg is not None:
             res["path_steps"], res["capped"] = int(dg.path_steps), int(dg.capped)
+            res["flags"] = flags
         return res
 
     def interface_solve_naive(self, nodes, *, seed: int, dt: float, n_paths: int,

@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import hashlib
 import os
+import zipfile
 
 import numpy as np
 import torch
@@ -77,18 +78,34 @@ class Checkpoint:
                 "next_path": self.next_path}
 
     def save(self, path: str) -> None:
-        """Write atomically (a temporary file renamed over `path`)."""
+        """Write atomically and durably: a temporary file, flushed to the disk,
+        renamed over `path`, and the directory entry flushed too, so that a
+        crash leaves either the previous checkpoint or this one."""
         tmp = f"{path}.tmp"
         with open(tmp, "wb") as f:
             np.savez(f, table=self.table.numpy(), next_path=np.int64(self.next_path),
                      digest=np.array(self.digest))
+            f.flush()
+            os.fsync(f.fileno())
         os.replace(tmp, path)
+        d = os.open(os.path.dirname(os.path.abspath(path)), os.O_RDONLY)
+        try:
+            os.fsync(d)
+        finally:
+            os.close(d)
 
     @classmethod
     def load(cls, path: str) -> "Checkpoint":
-        with np.load(path) as z:
-            table = z["table"]
-            return cls(str(z["digest"]), table.shape[0], int(z["next_path"]), table)
+        try:
+            with np.load(path) as z:
+                table = z["table"]
+                ck = cls(str(z["digest"]), table.shape[0], int(z["next_path"]), table)
+        except (OSError, ValueError, KeyError, EOFError, zipfile.BadZipFile) as e:  # truncated
+            raise ValueError(f"checkpoint file {path} is unreadable (truncated or corrupt): "
+                             f"{e}") from e
+        if table.ndim != 2 or table.shape[1] != 3:
+            raise ValueError(f"checkpoint file {path} holds a table of shape {table.shape}")
+        return ck
 
     def check(self, prob: dict, nodes, **run) -> None:
         if run_digest(prob, nodes, **run) != self.digest:

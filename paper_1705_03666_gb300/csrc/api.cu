@@ -287,6 +287,17 @@ pdd_status pdd_mlmc_level(pdd_ctx *ctx, const double *d_nodes, int64_t n, const 
   return pdd::mlmc_level_impl(ctx, d_nodes, n, mp, d_mean, d_var, d_fine_mean, d_coarse_mean, diag);
 }
 
+pdd_status pdd_mlmc_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                          const pdd_mlmc_params *mp, int32_t n_levels,
+                          const int64_t *n_per_level, double *d_mean, double *d_se,
+                          double *d_level_mean, double *d_level_var, pdd_diag *diag) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  const TraceRange trace(__func__);
+  return pdd::mlmc_solve_impl(ctx, d_nodes, n, mp, n_levels, n_per_level, d_mean, d_se,
+                              d_level_mean, d_level_var, diag);
+}
+
 pdd_status pdd_profile(pdd_ctx *ctx, int enable) {
   if (!ctx) return PDD_EINVAL;
   ctx->profiling = enable != 0;
@@ -332,6 +343,7 @@ void pdd_destroy(pdd_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
   for (int k = 0; k < 3; ++k) {
     if (ctx->batch_side[k]) cudaStreamDestroy(ctx->batch_side[k]);

@@ -194,6 +194,19 @@ __global__ void batch_final(int64_t n, const int32_t *perm, const int64_t *cstar
   if (n_out) n_out[i] = static_cast<int64_t>(nt);
 }
 
+// Per-node flags of the adaptive batch: the target standard error not
+// reached (N_i stopped at n_max, or the final variance exceeded the pilot's),
+// or no estimate (a node outside the closed domain or of an unknown problem).
+__global__ void batch_flags(int64_t n, const double *mean, const double *se, double target_se,
+                            int32_t *flags) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  int32_t f = 0;
+  if (isnan(mean[i])) f |= kNodeOutside;
+  else if (se[i] > target_se) f |= kNodeSeUnmet;
+  flags[i] = f;
+}
+
 namespace {
 
 int combo_of(const pdd_problem &p) {
@@ -499,6 +512,11 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
     if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
     PDD_CUDA_TRY(ctx, cudaGraphLaunch(ctx->batch_graph, ctx->stream));
     if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
+  }
+  if (diag && diag->d_node_flags) {
+    batch_flags<<<static_cast<unsigned>((nodes->n + 255) / 256), 256, 0, ctx->stream>>>(
+        nodes->n, d_mean, d_se, bp->target_se, diag->d_node_flags);
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
   }
   if (diag) {
     unsigned long long h[4] = {0, 0, 0, 0};

@@ -27,7 +27,9 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
                                 int64_t *d_nkept, pdd_diag *diag) {
   const uint64_t N = static_cast<uint64_t>(bp->n_trees);
   const uint64_t total = static_cast<uint64_t>(n) * N;
-  const uint64_t wave = std::min<uint64_t>(total, ctx->wave_max_paths);
+  // at most 2^31 trees per wave (the kernel indexes a wave's trees in 32 bits)
+  const uint64_t wave = std::min<uint64_t>(std::min<uint64_t>(total, ctx->wave_max_paths),
+                                           uint64_t(1) << 31);
   const size_t acc_off = 256;
   const size_t xt_off = align_up(acc_off + static_cast<size_t>(n) * sizeof(NodeAcc), 256);
   const size_t score_off = align_up(xt_off + static_cast<size_t>(n) * sizeof(float4), 256);
@@ -58,6 +60,7 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
   a.inv_beta = static_cast<float>(1.0 / prm[0]);
   a.psi_kind = static_cast<int32_t>(prm[1]);
   a.psi_prm = static_cast<float>(prm[2]);
+  a.psi_l2 = static_cast<float>(prm[2] * 1.4426950408889634);
   a.K = static_cast<int32_t>(prm[3]);
   double cum = 0.0;
   for (int k = 0; k <= a.K; ++k) {
@@ -68,8 +71,14 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
   }
   a.max_particles = bp->max_particles;
   a.max_depth = bp->max_depth;
+  int32_t *flags = diag ? diag->d_node_flags : nullptr;
+  if (flags) PDD_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, static_cast<size_t>(n) * 4, ctx->stream));
+  a.flags = flags;
+  // two children with probability one and the classical weight (KPP)
+  const bool binary = a.K == 2 && prm[4] == 0.0 && prm[5] == 0.0 && prm[6] == 1.0 &&
+                      prm[5 + a.K + 2] == 1.0;
 
-  auto kern = branch_kernel<D>;
+  auto kern = binary ? branch_kernel<D, true> : branch_kernel<D, false>;
   int bps = 0;
   PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kBranchBlock, 0));
   if (bps < 1) bps = 1;
@@ -100,7 +109,7 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
     }
   }
   finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(
-      acc, n, d_mean, d_se, d_nkept);
+      acc, n, d_mean, d_se, d_nkept, flags);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
   if (diag) {
     unsigned long long h[4] = {0, 0, 0, 0};

@@ -34,6 +34,10 @@ struct pdd_ctx {
   // library-owned scratch, grown on demand
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
+  // a second library-owned buffer for results an entry point keeps across
+  // its own calls of other entry points (which use `scratch`)
+  void *aux = nullptr;
+  size_t aux_bytes = 0;
   std::string last_error;
   // launch shape of the path kernels (warps per block fixed at compile time;
   // resident blocks per SM chosen by the occupancy query or the tuner)
@@ -119,6 +123,25 @@ inline pdd_status ensure_scratch(pdd_ctx *ctx, size_t bytes) {
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Make sure the auxiliary buffer holds at least `bytes`.
+inline pdd_status ensure_aux(pdd_ctx *ctx, size_t bytes) {
+  if (ctx->aux_bytes >= bytes) return PDD_OK;
+  if (ctx->aux) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    cudaFree(ctx->aux);
+    ctx->aux = nullptr;
+    ctx->aux_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&ctx->aux, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, PDD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->aux_bytes = bytes;
+  return PDD_OK;
+}
+
 // Event pair for the next profiled launch (nullptr events when profiling is
 // off or event creation failed).
 inline std::pair<cudaEvent_t, cudaEvent_t> prof_slot(pdd_ctx *ctx) {
@@ -177,6 +200,10 @@ pdd_status reflect_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
 pdd_status mlmc_level_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n, const pdd_mlmc_params *mp,
                            double *d_mean, double *d_var, double *d_fine, double *d_coarse,
                            pdd_diag *diag);
+pdd_status mlmc_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                           const pdd_mlmc_params *mp, int32_t n_levels,
+                           const int64_t *h_n_per_level, double *d_mean, double *d_se,
+                           double *d_level_mean, double *d_level_var, pdd_diag *diag);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

@@ -377,4 +377,77 @@ pdd_status mlmc_level_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n, const
 #undef PDD_MLMC
 }
 
+// The multilevel estimate from its levels, per node, in level order:
+// mean = sum_l mean_l, se = sqrt(sum_l var_l / N_l) (independent levels).
+struct LevelCounts {
+  double n[13];
+};
+static __global__ void mlmc_combine_kernel(const double *lmean, const double *lvar, int64_t n,
+                                           int32_t L, LevelCounts N, double *mean, double *se) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  double m = 0.0, v = 0.0;
+  for (int l = 0; l < L; ++l) {
+    m += lmean[static_cast<int64_t>(l) * n + i];
+    v += lvar[static_cast<int64_t>(l) * n + i] / N.n[l];
+  }
+  mean[i] = m;
+  se[i] = sqrt(v);
+}
+
+pdd_status mlmc_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
+                           const pdd_mlmc_params *mp, int32_t n_levels,
+                           const int64_t *h_n_per_level, double *d_mean, double *d_se,
+                           double *d_level_mean, double *d_level_var, pdd_diag *diag) {
+  if (!mp || !h_n_per_level) return fail(ctx, PDD_EINVAL, "params or path counts NULL");
+  if (n_levels < 1 || n_levels > 13) return fail(ctx, PDD_EINVAL, "n_levels must be in [1, 13]");
+  for (int l = 0; l < n_levels; ++l)
+    if (h_n_per_level[l] < 1) return fail(ctx, PDD_EINVAL, "level %d has no pairs", l);
+  if (n < 0 || n > (int64_t(1) << 32)) return fail(ctx, PDD_EINVAL, "n out of range");
+  if (diag) {
+    diag->path_steps = 0;
+    diag->capped = 0;
+  }
+  if (n == 0) return PDD_OK;
+  if (!d_mean || !d_se) return fail(ctx, PDD_EINVAL, "null buffer");
+  PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  // level means and variances: the caller's buffers, or the auxiliary buffer
+  // (the level calls use the context scratch themselves)
+  double *lm = d_level_mean, *lv = d_level_var;
+  const size_t plane = static_cast<size_t>(n) * n_levels * sizeof(double);
+  if (!lm || !lv) {
+    const pdd_status st = ensure_aux(ctx, 2 * plane);
+    if (st != PDD_OK) return st;
+    if (!lm) lm = static_cast<double *>(ctx->aux);
+    if (!lv) lv = reinterpret_cast<double *>(static_cast<char *>(ctx->aux) + plane);
+  }
+  LevelCounts N{};
+  pdd_status worst = PDD_OK;
+  int64_t steps = 0, capped = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    pdd_mlmc_params lp = *mp;
+    lp.level = l;
+    lp.n_paths = h_n_per_level[l];
+    N.n[l] = static_cast<double>(h_n_per_level[l]);
+    pdd_diag ld{};
+    const pdd_status st = mlmc_level_impl(ctx, d_nodes, n, &lp, lm + static_cast<size_t>(l) * n,
+                                          lv + static_cast<size_t>(l) * n, nullptr, nullptr,
+                                          diag ? &ld : nullptr);
+    if (st != PDD_OK && st != PDD_ECAP) return st;
+    if (st == PDD_ECAP) worst = PDD_ECAP;
+    steps += ld.path_steps;
+    capped += ld.capped;
+  }
+  mlmc_combine_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(
+      lm, lv, n, n_levels, N, d_mean, d_se);
+  PDD_CUDA_TRY(ctx, cudaGetLastError());
+  if (diag) {
+    diag->path_steps = steps;
+    diag->capped = capped;
+    if (worst == PDD_ECAP) return fail(ctx, PDD_ECAP, "%lld walks hit max_steps",
+                                       static_cast<long long>(capped));
+  }
+  return PDD_OK;
+}
+
 }  // namespace pdd

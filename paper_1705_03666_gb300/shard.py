@@ -26,6 +26,14 @@ def node_block(n: int, world: int, rank: int) -> tuple[int, int]:
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+def copy_block(n: int, world: int, rank: int) -> tuple[int, int]:
+    """Weak scaling by node blocks: the run's node list is `world` copies of
+    an n-node list, copy r being nodes [r n, (r + 1) n) with their own
+    stream indices; `rank` solves its copy (node_offset = r n) and the
+    all-gather assembles the world x n table.  Returns (node_offset, total)."""
+    return rank * n, world * n
+
+
 def path_block(n_paths: int, world: int, rank: int) -> tuple[int, int]:
     """Half-open path-index range of `rank` (same rule as node_block)."""
     return node_block(n_paths, world, rank)
@@ -39,7 +47,10 @@ def triples(mean: torch.Tensor, se: torch.Tensor, count: torch.Tensor) -> torch.
 
 
 def chan_merge(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
-    """Merge two [n, 3] (count, mean, M2) tables (Chan, Golub, LeVeque)."""
+    """Merge two [n, 3] (count, mean, M2) tables (Chan, Golub, LeVeque).  A
+    row with count 0 on one side takes the other side's row as it is, so an
+    empty side's mean (NaN where nothing was sampled) never enters the
+    arithmetic."""
     na, ma, m2a = a.unbind(1)
     nb, mb, m2b = b.unbind(1)
     nt = na + nb
@@ -47,15 +58,20 @@ def chan_merge(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
     d = mb - ma
     mean = ma + d * nb / safe
     m2 = m2a + m2b + d * d * na * nb / safe
-    return torch.stack([nt, mean, m2], 1)
+    merged = torch.stack([nt, mean, m2], 1)
+    merged = torch.where((na == 0)[:, None], b, merged)
+    return torch.where((nb == 0)[:, None], a, merged)
 
 
 def finalize(t: torch.Tensor):
-    """mean, standard error, count from a (count, mean, M2) table."""
+    """mean, standard error, count from a (count, mean, M2) table; a row
+    with count 0 (no sample: a node nobody supplied) gives NaN mean and se,
+    as the library's own finalisation does."""
     c, m, m2 = t.unbind(1)
+    nan = torch.full_like(m, float("nan"))
     se = torch.where(c > 1, torch.sqrt(m2 / (c - 1).clamp(min=1) / c.clamp(min=1)),
                      torch.zeros_like(m))
-    return m, se, c.to(torch.int64)
+    return torch.where(c > 0, m, nan), torch.where(c > 0, se, nan), c.to(torch.int64)
 
 
 def allgather_nodes(local: torch.Tensor, n_total: int, group=None) -> torch.Tensor:
@@ -64,7 +80,8 @@ def allgather_nodes(local: torch.Tensor, n_total: int, group=None) -> torch.Tens
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
     lo, hi = node_block(n_total, world, rank)
-    assert local.shape[0] == hi - lo
+    if local.shape[0] != hi - lo:
+        raise ValueError(f"rank {rank} holds {local.shape[0]} rows for block [{lo}, {hi})")
     width = max(node_block(n_total, world, r)[1] - node_block(n_total, world, r)[0]
                 for r in range(world))
     pad = torch.zeros((width, 3), dtype=torch.float64, device=local.device)
@@ -128,6 +145,35 @@ def collect(store, tag: str, ranks, timeout_s: float, poll_s: float = 0.01):
         time.sleep(poll_s)
 
 
+def agree(store, tag: str, got: dict, lost) -> tuple[dict, list, list]:
+    """Make every rank act on the same (alive, lost) split after `collect`.
+
+    Each rank's collect has its own deadline, so a rank that published close
+    to it can be seen by one survivor and missed by another.  The first rank
+    to get here writes its own view under `tag`/view (compare-and-set on an
+    unset key, so only one write succeeds) and every rank adopts the stored
+    view.  Returns (the agreed alive ranks' tables, agreed lost ranks,
+    agreed alive ranks); a table this rank's own collect missed is read from
+    the store (the writer saw it published).  A rank absent from the agreed
+    alive list has been declared lost: its table is not used and it
+    recomputes nothing."""
+    alive = sorted(int(r) for r in got)
+    mine = ",".join(str(r) for r in alive) + "|" + ",".join(str(int(r)) for r in sorted(lost))
+    stored = store.compare_set(f"{tag}/view", "", mine)
+    view = stored.decode() if isinstance(stored, (bytes, bytearray)) else str(stored)
+    a, l = view.split("|")
+    alive_a = [int(r) for r in a.split(",") if r]
+    lost_a = [int(r) for r in l.split(",") if r]
+    out = {}
+    for r in alive_a:
+        if r in got:
+            out[r] = got[r]
+        else:
+            buf = np.frombuffer(store.get(f"{tag}/{r}"), dtype=np.float64).copy()
+            out[r] = torch.from_numpy(buf).reshape(-1, 3)
+    return out, lost_a, alive_a
+
+
 def merge_surviving_paths(got: dict) -> torch.Tensor:
     """Path-range sharding after `collect`: merge the surviving ranks' tables
     in rank order (the result is the estimate over their path ranges)."""
@@ -160,7 +206,7 @@ def assemble_nodes(n_total: int, world: int, got: dict, lost=(), redo: dict | No
     arrived (`got`, keyed by owning rank) and, for the `lost` ranks' blocks,
     the survivors' recomputed rows (`redo`, keyed by survivor: its
     `lost_node_share` pieces, concatenated in order).  Rows nobody supplied
-    keep count 0 (finalize gives mean 0, se 0, count 0 there)."""
+    keep count 0 (finalize gives NaN mean and se, count 0 there)."""
     out = torch.zeros((n_total, 3), dtype=torch.float64)
     for r, t in got.items():
         lo, hi = node_block(n_total, world, r)

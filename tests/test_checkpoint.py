@@ -80,3 +80,19 @@ def test_save_load_round_trip(tmp_path):
     np.testing.assert_allclose(r["se"], 0.5, rtol=1e-14)
     with pytest.raises(ValueError):
         ck.add({"mean": np.zeros(1), "se": np.zeros(1), "n": np.ones(1)}, 1)
+
+
+def test_truncated_checkpoint_gives_a_clear_error(orc, tmp_path):
+    prob, nodes, run = _setup()
+    path = str(tmp_path / "ck.npz")
+    C.solve_resumable(_oracle_solve(orc, prob, []), prob, nodes, n_paths=200, piece=100,
+                      path=path, **run)
+    raw = open(path, "rb").read()
+    for cut in (0, 10, len(raw) // 2):
+        with open(path, "wb") as f:
+            f.write(raw[:cut])
+        with pytest.raises(ValueError, match="unreadable"):
+            C.Checkpoint.load(path)
+        with pytest.raises(ValueError, match="unreadable"):
+            C.solve_resumable(_oracle_solve(orc, prob, []), prob, nodes, n_paths=300, piece=100,
+                              path=path, **run)

@@ -103,6 +103,9 @@ def test_adaptive_counts_follow_pilot_variance(api):
     assert np.all(np.abs(ratio - 1.0) < 0.02)
     assert 0.85 < np.median(se[ok] / se_t) < 1.15   # the pilot is unbiased for var
     assert r["capped"] == 0 and r["path_steps"] > 0
+    # per-node flags: the target not reached exactly where se > target_se
+    flags = r["flags"].cpu().numpy()
+    assert np.array_equal((flags & 32) != 0, se > se_t) and np.any(se > se_t)
 
 
 def test_lshape_matches_oracle(api, orc):

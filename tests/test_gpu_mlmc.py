@@ -97,3 +97,37 @@ def test_edge_cases(api):
     with api.Context(W.elliptic_manufactured()) as ctx:
         with pytest.raises(Exception):
             ctx.mlmc_level(torch.tensor([[0.5, 0.5, 0.5]]), seed=1, dt0=1e-3, level=1, n_paths=4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mlmc_solve_equals_oracle_level_sums(api, orc, precision):
+    """pdd_mlmc_solve combines its levels on the device: mean = sum of the
+    level means, se = sqrt(sum var_l / N_l).  Against the oracle's levels on
+    the same streams, summed here: FP64 to rounding; FP32 within the pairs'
+    exit flips (the per-pair comparison above) and 1e-5 of the scale."""
+    nodes = W.nodes_cfg1(6)
+    counts = [3000, 1500, 800]
+    kw = dict(seed=W.SEED_BASE + 65, dt0=4e-3)
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.mlmc_solve(torch.from_numpy(nodes), n_per_level=counts, precision=precision,
+                           diag=True, **kw)
+        lv = [ctx.mlmc_level(torch.from_numpy(nodes), level=l, n_paths=N, precision=precision,
+                             **kw) for l, N in enumerate(counts)]
+    ol = [orc.mlmc_level(W.laplace_expcos(), nodes, level=l, n_paths=N, **kw)
+          for l, N in enumerate(counts)]
+    om = sum(L["mean"] for L in ol)
+    ose = np.sqrt(sum(L["var"] / N for L, N in zip(ol, counts)))
+    m, se = r["mean"].cpu().numpy(), r["se"].cpu().numpy()
+    # the combination is exactly the level results summed in level order
+    gm = sum(L["mean"].cpu().numpy() for L in lv)
+    np.testing.assert_array_equal(m, gm)
+    for l in range(len(counts)):
+        assert torch.equal(r["levels"][l]["mean"], lv[l]["mean"])
+        assert torch.equal(r["levels"][l]["var"], lv[l]["var"])
+    if precision == "fp64":
+        np.testing.assert_allclose(m, om, rtol=1e-10, atol=1e-13)
+        np.testing.assert_allclose(se, ose, rtol=1e-8)
+    else:
+        assert np.all(np.abs(m - om) <= 0.5 * ose)
+        np.testing.assert_allclose(se, ose, rtol=0.05)
+    assert r["path_steps"] > 0 and r["capped"] == 0

@@ -38,6 +38,15 @@ def _worker(rank, world, port, mode, out_dir):
         t = shard.triples(torch.from_numpy(r["mean"]), torch.from_numpy(r["se"]),
                           torch.from_numpy(r["n"]))
         full = shard.allgather_nodes(t, n)
+    elif mode == "copies":
+        # the benchmark's multi-GPU layout: rank r solves copy r of the node
+        # list (node ids r n .. r n + n - 1), the all-gather assembles all
+        off, total = shard.copy_block(n, world, rank)
+        r = oracle.interface_solve(w["prob"], nodes, node_ids=np.arange(off, off + n),
+                                   n_paths=600, **kw)
+        t = shard.triples(torch.from_numpy(r["mean"]), torch.from_numpy(r["se"]),
+                          torch.from_numpy(r["n"]))
+        full = shard.allgather_nodes(t, total)
     else:
         lo, hi = shard.path_block(600, world, rank)
         r = oracle.interface_solve(w["prob"], nodes, n_paths=hi - lo, path_offset=lo, **kw)
@@ -50,7 +59,7 @@ def _worker(rank, world, port, mode, out_dir):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("mode", ["nodes", "paths"])
+@pytest.mark.parametrize("mode", ["nodes", "paths", "copies"])
 def test_two_rank_stage_one_matches_single_process(tmp_path, mode):
     import oracle
     world = 2
@@ -58,6 +67,8 @@ def test_two_rank_stage_one_matches_single_process(tmp_path, mode):
                        start_method="spawn", join=True)
     w = W.workload(2)
     nodes = w["nodes"][::256]
+    if mode == "copies":
+        nodes = np.concatenate([nodes] * world)
     ref = oracle.interface_solve(w["prob"], nodes, seed=w["seed"], dt=1e-3, n_paths=600)
     for r in range(world):
         got = np.load(tmp_path / f"{mode}_{r}.npy")

@@ -45,7 +45,12 @@ def _solve(oracle, w, nodes, lo, hi, p_lo, p_hi):
                          torch.from_numpy(r["n"]))
 
 
-def _worker(rank, port, mode, fail_rank, out_dir):
+def _worker(rank, port, mode, fail_rank, out_dir, late=None):
+    """late = (late_rank, slow_rank): late_rank publishes just after the
+    first deadline, and slow_rank starts collecting later, so that one
+    survivor sees the late table and another does not."""
+    import time
+
     import torch.distributed as dist
 
     import oracle
@@ -61,9 +66,22 @@ def _worker(rank, port, mode, fail_rank, out_dir):
         t = _solve(oracle, w, nodes, 0, n, p_lo, p_hi)
     if rank == fail_rank:
         raise RuntimeError("injected failure: this rank leaves before publishing")
+    if late is not None:   # start the exchange together, so the delays are what differ
+        store.set(f"ready/{rank}", b"1")
+        store.wait([f"ready/{r}" for r in range(WORLD)], datetime.timedelta(seconds=60))
+    if late is not None and rank == late[0]:
+        time.sleep(DEADLINE_S + 1.0)          # misses the first deadline
     shard.publish(store, "stage1", rank, t)
+    if late is not None and rank == late[1]:
+        time.sleep(2.0)                       # its deadline ends later: sees the late table
     got, lost = shard.collect(store, "stage1", range(WORLD), DEADLINE_S)
-    alive = sorted(got)
+    np.save(os.path.join(out_dir, f"{mode}_{rank}_seen.npy"), np.array(sorted(got), dtype=np.int64))
+    got, lost, alive = shard.agree(store, "stage1", got, lost)
+    if rank not in alive:
+        # declared lost by the agreed view: its table is not used
+        np.save(os.path.join(out_dir, f"{mode}_{rank}_declared_lost.npy"), np.array([rank]))
+        shard.publish(store, "done", rank, torch.zeros((0, 3), dtype=torch.float64))
+        return
     if mode == "nodes":
         pieces = shard.lost_node_share(n, WORLD, lost, alive, rank)
         parts = [_solve(oracle, w, nodes, a, b, 0, N_PATHS) for a, b in pieces]
@@ -85,10 +103,10 @@ def _worker(rank, port, mode, fail_rank, out_dir):
         assert not late
 
 
-def _run(tmp_path, mode, fail_rank):
+def _run(tmp_path, mode, fail_rank, late=None):
     ctx = mproc.get_context("spawn")
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, port, mode, fail_rank, str(tmp_path)))
+    procs = [ctx.Process(target=_worker, args=(r, port, mode, fail_rank, str(tmp_path), late))
              for r in range(WORLD)]
     for p in procs:
         p.start()
@@ -113,6 +131,28 @@ def test_lost_node_block_is_recomputed_by_the_survivors(tmp_path):
         assert list(np.load(tmp_path / f"nodes_{r}_lost.npy")) == [fail]
         np.testing.assert_allclose(got[0], ref["mean"], rtol=1e-12, atol=1e-14)
         np.testing.assert_allclose(got[1], ref["se"], rtol=1e-9)
+        assert np.array_equal(got[2], ref["n"].astype(np.float64))
+
+
+def test_rank_publishing_at_the_deadline_gets_one_agreed_view(tmp_path):
+    """Rank 2 publishes just after rank 1's deadline; rank 0 collects later
+    and sees it, rank 1 does not.  Without an agreed view rank 1 would redo
+    rank 2's block alone while rank 0 waited for nothing to redo.  With it,
+    all ranks act on the first view written (rank 1's: rank 2 lost), the
+    survivors recompute rank 2's block and reproduce the single-process
+    estimate; rank 2 learns that it was declared lost."""
+    import oracle
+    codes = _run(tmp_path, "nodes", fail_rank=-1, late=(2, 0))
+    assert all(c == 0 for c in codes), codes
+    seen = {r: list(np.load(tmp_path / f"nodes_{r}_seen.npy")) for r in range(WORLD)}
+    assert seen[1] == [0, 1] and seen[0] == [0, 1, 2]      # the two survivors disagreed
+    assert (tmp_path / "nodes_2_declared_lost.npy").exists()
+    w, nodes = _problem()
+    ref = oracle.interface_solve(w["prob"], nodes, seed=w["seed"], dt=1e-3, n_paths=N_PATHS)
+    for r in (0, 1):
+        got = np.load(tmp_path / f"nodes_{r}.npy")
+        assert list(np.load(tmp_path / f"nodes_{r}_lost.npy")) == [2]
+        np.testing.assert_allclose(got[0], ref["mean"], rtol=1e-12, atol=1e-14)
         assert np.array_equal(got[2], ref["n"].astype(np.float64))
 
 
@@ -154,4 +194,18 @@ def test_store_exchange_helpers_on_one_process():
     t0 = shard.assemble_nodes(n, world, blocks)            # nobody redid the block
     assert t0[4:7, 0].tolist() == [0, 0, 0]
     m, se, c = shard.finalize(t0)
-    assert c[4:7].tolist() == [0, 0, 0] and se[4:7].tolist() == [0, 0, 0]
+    assert c[4:7].tolist() == [0, 0, 0]
+    assert torch.isnan(m[4:7]).all() and torch.isnan(se[4:7]).all()   # no estimate there
+    # an empty side never enters the merge, even with a NaN mean
+    e = torch.tensor([[0.0, float("nan"), 0.0], [2.0, 1.0, 0.5]], dtype=torch.float64)
+    f = torch.tensor([[3.0, 2.0, 1.0], [0.0, float("nan"), 0.0]], dtype=torch.float64)
+    mg = shard.chan_merge(e, f)
+    assert torch.equal(mg, torch.tensor([[3.0, 2.0, 1.0], [2.0, 1.0, 0.5]], dtype=torch.float64))
+    # the agreed view: the first writer wins, later callers adopt it and read
+    # the tables they missed from the store
+    st = torch.distributed.HashStore()
+    shard.publish(st, "v", 0, a)
+    shard.publish(st, "v", 2, a)
+    g1, l1, al1 = shard.agree(st, "v", {0: a, 2: a}, [1])
+    g2, l2, al2 = shard.agree(st, "v", {0: a}, [1, 2])
+    assert al1 == al2 == [0, 2] and l1 == l2 == [1] and sorted(g2) == [0, 2]
