@@ -24,6 +24,11 @@ Parity status per function (what pins it is listed in the tests):
                      harmonic data with Neumann/Robin faces, 3-D Robin)
   spline_interface   pinned (reproduces cubics exactly; library routine)
   subdomain_solve    pinned (dense solve, exact harmonic at O(h^2))
+  plane_interface    pinned (reproduces linear data exactly, interpolates at
+                     the nodes, converges for smooth data; library routine)
+  elliptic_box_solve pinned (dense assembly on a tiny grid, exact for a
+                     quadratic with constant drift, O(h^2) to the manufactured
+                     3-D solution)
 """
 from __future__ import annotations
 
@@ -90,6 +95,7 @@ def _load():
                                               ctypes.c_uint32, ctypes.c_uint32,
                                               ctypes.c_uint32, ctypes.c_int64, up]
             lib.orc_eval_coeffs.argtypes = [P, dp, dp]
+            lib.orc_eval_coeffs_many.argtypes = [P, dp, ctypes.c_int64, dp]
             lib.orc_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_int64, dp, dp]
@@ -192,6 +198,19 @@ def eval_coeffs(prob: dict, x) -> np.ndarray:
     out = np.zeros(6)
     lib.orc_eval_coeffs(ctypes.byref(P), _ptr(xx, ctypes.c_double),
                         _ptr(out, ctypes.c_double))
+    return out
+
+
+def eval_coeffs_many(prob: dict, x) -> np.ndarray:
+    """(b0, b1, b2, c, f, g) of the problem at points x [n, d] -> [n, 6]."""
+    lib = _load()
+    P, keep = _problem(prob)
+    x = np.asarray(x, dtype=np.float64)
+    xx = np.zeros((x.shape[0], 3))
+    xx[:, :x.shape[1]] = x
+    out = np.zeros((x.shape[0], 6))
+    lib.orc_eval_coeffs_many(ctypes.byref(P), _ptr(xx, ctypes.c_double), x.shape[0],
+                             _ptr(out, ctypes.c_double))
     return out
 
 
@@ -446,5 +465,95 @@ def stencil_solve(u_boundary: np.ndarray, h, sigma: float = 1.0) -> np.ndarray:
                 else:
                     rhs[r] += w * u[tuple(q)]
     A = sp.csr_matrix((vals, (rows, cols)), shape=(nint, nint))
+    u[interior] = spla.spsolve(A, rhs)
+    return u
+
+
+def plane_boundary_points(axis: int, pos: float, n_bnd: int) -> np.ndarray:
+    """Points on the perimeter of the internal plane x_axis = pos of the unit
+    cube: n_bnd per edge (equispaced, corners included once), as 3-D points."""
+    t = np.linspace(0.0, 1.0, n_bnd + 1)[:-1]
+    s = np.concatenate([t, np.ones_like(t), 1.0 - t, np.zeros_like(t)])
+    r = np.concatenate([np.zeros_like(t), t, np.ones_like(t), 1.0 - t])
+    other = [a for a in range(3) if a != axis]
+    pts = np.zeros((s.size, 3))
+    pts[:, axis] = pos
+    pts[:, other[0]] = s
+    pts[:, other[1]] = r
+    return pts
+
+
+def plane_interface(prob: dict, axis: int, pos: float, nodes, values, query, n_bnd: int = 32):
+    """Interface interpolation on an internal plane x_axis = pos of the unit
+    cube (Sec. 2.1: the nodal values become Dirichlet data on the interface;
+    Chebyshev or RBF interpolation are named there): a radial basis function
+    interpolant with the cubic kernel |r|^3 and a linear polynomial term
+    (SciPy's RBFInterpolator, a library routine) through the Monte Carlo
+    nodes on the plane and n_bnd points per edge of the plane's perimeter,
+    where the boundary data g are known, evaluated at the query points."""
+    other = [a for a in range(3) if a != axis]
+    nodes = np.asarray(nodes, dtype=np.float64)
+    bnd = plane_boundary_points(axis, pos, n_bnd)
+    gb = eval_coeffs_many(prob, bnd)[:, 5]
+    pts = np.concatenate([nodes[:, other], bnd[:, other]])
+    vals = np.concatenate([np.asarray(values, dtype=np.float64), gb])
+    return rbf_interp(pts, vals, np.asarray(query, dtype=np.float64)[:, other])
+
+
+def rbf_interp(points, values, query):
+    """Cubic radial basis function interpolant |r|^3 with a linear polynomial
+    term through (points, values), evaluated at query (SciPy's
+    RBFInterpolator)."""
+    from scipy.interpolate import RBFInterpolator
+    return RBFInterpolator(np.asarray(points, dtype=np.float64),
+                           np.asarray(values, dtype=np.float64), kernel="cubic",
+                           degree=1)(np.asarray(query, dtype=np.float64))
+
+
+def elliptic_box_solve(prob: dict, u_boundary: np.ndarray, lo, hi) -> np.ndarray:
+    """Exact solution of the finite-difference system of the elliptic
+    problem (1/2) sigma^2 Lap u + b . grad u + c u + f = 0 (Eq. 2.3 without
+    time) on the box [lo, hi] with the tensor grid of u_boundary's shape
+    ([n2][n1][n0], or [n1][n0] in 2-D), Dirichlet data in its boundary layer:
+    7-point (5-point) second differences and central first differences,
+    c and f at the grid point.  Direct sparse solve (SciPy)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    u = np.array(u_boundary, dtype=np.float64, copy=True)
+    dim = u.ndim
+    shape = u.shape                      # array axis k <-> coordinate dim - 1 - k
+    h = [(hi[a] - lo[a]) / (shape[dim - 1 - a] - 1) for a in range(dim)]
+    grids = [lo[a] + h[a] * np.arange(shape[dim - 1 - a]) for a in range(dim)]
+    mesh = np.meshgrid(*[grids[dim - 1 - k] for k in range(dim)], indexing="ij")
+    X = np.stack([mesh[dim - 1 - a] for a in range(dim)], -1)     # [..., dim], x first
+    interior = np.zeros(shape, dtype=bool)
+    interior[tuple(slice(1, -1) for _ in range(dim))] = True
+    idx = -np.ones(shape, dtype=np.int64)
+    nint = int(interior.sum())
+    idx[interior] = np.arange(nint)
+    coef = eval_coeffs_many(prob, X[interior])
+    s2 = float(prob.get("sigma", 1.0)) ** 2
+    rows = [np.arange(nint)]
+    cols = [np.arange(nint)]
+    diag = coef[:, 3].copy()
+    for a in range(dim):
+        diag -= s2 / h[a] ** 2
+    vals = [diag]
+    rhs = -coef[:, 4].copy()
+    pts = np.argwhere(interior)
+    for a in range(dim):
+        k = dim - 1 - a                  # array axis of coordinate a
+        for sgn in (-1, 1):
+            w = 0.5 * s2 / h[a] ** 2 + sgn * coef[:, a] / (2.0 * h[a])
+            q = pts.copy()
+            q[:, k] += sgn
+            j = idx[tuple(q.T)]
+            inner = j >= 0
+            rows.append(np.arange(nint)[inner])
+            cols.append(j[inner])
+            vals.append(w[inner])
+            rhs[~inner] -= w[~inner] * u[tuple(q[~inner].T)]
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nint, nint))
     u[interior] = spla.spsolve(A, rhs)
     return u

@@ -304,6 +304,11 @@ void orc_eval_coeffs(const orc_problem *P, const double *x, double *out) {
   out[5] = coef_g(P, x);
 }
 
+/* The same at n points x[n][3]: out[n][6].                                  */
+void orc_eval_coeffs_many(const orc_problem *P, const double *x, int64_t n, double *out) {
+  for (int64_t i = 0; i < n; ++i) orc_eval_coeffs(P, x + 3 * i, out + 6 * i);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Geometry.  Boxes [0,1]^d and the L-shape [0,1]^2 minus (1/2,1]x(1/2,1].  */
 /* ------------------------------------------------------------------------ */
