@@ -549,6 +549,43 @@ def run_other_workloads(api, dev) -> dict:
                           "paths_per_s": 16 * N / (ms_e / 1e3),
                           "max_abs_err": float((re["mean"] - exact).abs().max()),
                           "median_se": float(re["se"].median())}}
+    # The whole PDD method on the 3-D problem: stage one at the benchmark's
+    # 4096 nodes (1e5 FP32 paths, dt = 1e-4), then stage two -- the cubic RBF
+    # interpolant on each of the 9 internal planes and 64 independent 33^3
+    # subdomain solves (sine-transform defect correction to 1e-12).
+    w3 = W.workload(2)
+    with api.Context(w3["prob"], dev) as ctx:
+        nodes3 = torch.from_numpy(w3["nodes"]).to(dev)
+        ms1, r1 = _timed(stream, lambda: ctx.interface_solve(
+            nodes3, seed=w3["seed"], dt=w3["dt"], n_paths=w3["n_paths"], precision="fp32"))
+        axis3 = np.arange(len(w3["nodes"])) % 3
+        api.elliptic3d_pdd_solve(ctx, nodes3, r1["mean"], axis3)          # warm-up
+        t0 = time.perf_counter()
+        ms2, r2 = _timed(stream, lambda: api.elliptic3d_pdd_solve(ctx, nodes3, r1["mean"], axis3))
+        wall2 = time.perf_counter() - t0
+        g3 = torch.linspace(0, 1, 129, dtype=torch.float64, device=dev)
+        Z, Y, X = torch.meshgrid(g3, g3, g3, indexing="ij")
+        ex3 = torch.sin(np.pi * X) * torch.sin(np.pi * Y) * torch.exp(Z)
+        err3 = float((r2["u"] - ex3).abs().max())
+        # one subdomain's solve alone, for the kernel rates
+        ctx.profile(True)
+        ctx.profile_read()
+        faces = {fc: torch.zeros((33, 33), dtype=torch.float64, device=dev) for fc in range(6)}
+        rs = ctx.subdomain_solve3d((0.25, 0.25, 0.25), (0.5, 0.5, 0.5), (33, 33, 33), faces)
+        k_ms, _ = ctx.profile_read()
+        ctx.profile(False)
+        P = 31
+        flops = rs["iters"] * (6 * 2 * P ** 4 + 40 * P ** 3)
+        out["pdd_elliptic3d_two_stage"] = {
+            "workload": w3["name"] + " + 9 plane interpolants + 64 subdomains of 33^3 "
+                        "(h = 1/128)",
+            "stage_one_ms": ms1, "stage_two_ms": ms2, "stage_two_wall_s": wall2,
+            "max_abs_err_vs_exact": err3, "median_node_se": float(r1["se"].median()),
+            "max_corrections": r2["iters"], "max_rel_residual": r2["resid"],
+            "one_subdomain": {"ms": k_ms, "corrections": rs["iters"],
+                              "gflops_fp32_transforms": flops / (k_ms / 1e3) / 1e9,
+                              "flop_model": "per correction 6 dense sine passes (2 P^4) + "
+                                            "residual/eigenvalues/update (~40 P^3), P = 31"}}
     # Multilevel estimate on the 2-D Laplace nodes (4 levels, dt 4e-3 .. 5e-4)
     # against the plain scheme at the finest dt with enough paths for the
     # same standard error.

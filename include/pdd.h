@@ -417,6 +417,28 @@ PDD_API pdd_status pdd_branching_grid_solve(pdd_ctx *ctx, const double *d_nodes,
                                             double *d_mean, double *d_se,
                                             int64_t *d_nkept, pdd_diag *diag);
 
+/* Interface interpolation on the internal planes of the unit cube (stage two
+ * of PDD, Sec. 2.1: the Monte Carlo node values become Dirichlet data on the
+ * artificial interfaces; the paper names Chebyshev or RBF interpolation).
+ * For each of n_planes planes x_axis[p] = pos[p] (axis 0, 1 or 2, pos in
+ * (0, 1)), a radial basis function interpolant with the cubic kernel |r|^3
+ * and a linear polynomial term in the two in-plane coordinates, through the
+ * plane's node_count[p] nodes (d_nodes [..][3] FP64 and d_vals [..] FP64,
+ * the planes' nodes one after the other) and n_bnd points per edge of the
+ * plane's perimeter on the cube's boundary (edge points at k / n_bnd of each
+ * edge, corners once), which carry the problem's boundary data g; evaluated
+ * at the plane's query_count[p] points (d_query [..][3], planes one after
+ * the other) into d_out.  The interpolation systems ([Phi P; P^T 0], at most
+ * 6144 unknowns per plane) are solved in FP64 by Gaussian elimination with
+ * partial pivoting.  3-D family (ELLIPTIC_MANUFACTURED); 1 <= n_planes <=
+ * 64; axis, pos, node_count and query_count are host arrays.  Synchronises;
+ * PDD_EINVAL for a singular system (coincident nodes).                     */
+PDD_API pdd_status pdd_interface_interp(pdd_ctx *ctx, int32_t n_planes, const int32_t *axis,
+                                        const double *pos, const int64_t *node_count,
+                                        const double *d_nodes, const double *d_vals,
+                                        int32_t n_bnd, const int64_t *query_count,
+                                        const double *d_query, double *d_out);
+
 /* Stage two of PDD (Sec. 2.1, Fig. 2.2) for the Laplace family (Eq. 1.1):
  * the interpolator and the subdomain solver.  The subdomain is the box
  * [lo[0], hi[0]] x [lo[1], hi[1]] inside the unit square, discretised by an
@@ -442,7 +464,30 @@ PDD_API pdd_status pdd_branching_grid_solve(pdd_ctx *ctx, const double *d_nodes,
  * d_u is [n[1]][n[0]] FP64 (row = y), written in full.  *iters and *resid
  * (host) receive the iteration count and the final residual measure; the call
  * synchronises.  Returns PDD_ETIMEOUT when max_iter ran out first (d_u holds
- * the last iterate).                                                      */
+ * the last iterate).
+ *
+ * Three-dimensional subdomains (n[2] > 1; the 3-D family
+ * ELLIPTIC_MANUFACTURED, the elliptic problem of Eq. 2.3 without time,
+ * (1/2) sigma^2 Lap u + b . grad u + c u + f = 0): the box [lo, hi] inside
+ * the unit cube with an n[0] x n[1] x n[2] grid including its boundary
+ * (3 .. 128 points per axis), the 7-point system
+ *   sum_a (1/2) sigma^2 (u_{+a} - 2u + u_{-a}) / h_a^2
+ *     + sum_a b_a (u_{+a} - u_{-a}) / (2 h_a) + c u + f = 0
+ * at the interior points.  iface_axis is then a mask of the faces that are
+ * artificial interfaces (bit 2a + side: face x_a = lo[a] for side 0, hi[a]
+ * for side 1); their Dirichlet data come in d_iface_vals, the masked faces
+ * one after the other in bit order, each face's full grid with the higher
+ * of its two axes slow ([n2][n1] for an x-face, [n2][n0] for a y-face,
+ * [n1][n0] for a z-face); m is the total count of those values;
+ * d_iface_s is not used and iface_side must be 0.  The other faces take g.
+ * A grid point on several faces takes g if one of them has no interface
+ * data, else the data of the first interface face.  Methods: DST (defect
+ * correction u <- u + P^{-1} r with the FP64 residual r and P the
+ * constant-coefficient part of the operator inverted by three-dimensional
+ * sine transforms in binary32; stop at ||r||_2 <= tol ||r_0||_2, *iters
+ * = corrections applied, *resid = ||r||_2 / ||r_0||_2) or JACOBI (stop when
+ * max |u^{k+1} - u^k| < tol, *resid that change).  d_u is [n[2]][n[1]][n[0]],
+ * written in full.                                                        */
 enum { PDD_STENCIL_CG = 0, PDD_STENCIL_JACOBI = 1, PDD_STENCIL_CG_MIXED = 2, PDD_STENCIL_DST = 3 };
 
 typedef struct {

@@ -140,6 +140,11 @@ _SIGS = {
     "pdd_mlmc_solve": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(MlmcParams), ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_int64), _VP, _VP, _VP, _VP,
                                       ctypes.POINTER(Diag)]),
+    "pdd_interface_interp": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_int64), _VP, _VP,
+                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _VP,
+                                            _VP]),
     "pdd_philox_stream": (ctypes.c_int, [_VP, _U64, _U32, _U32, _U32, _U32, _I64, _VP]),
     "pdd_destroy": (None, [_VP]),
     "pdd_status_string": (ctypes.c_char_p, [ctypes.c_int]),

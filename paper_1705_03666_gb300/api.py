@@ -291,6 +291,56 @@ class Context:
         status = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ETIMEOUT))
         return {"u": u, "iters": it.value, "resid": res.value, "status": status}
 
+    def subdomain_solve3d(self, lo, hi, n, faces: dict, *, method: str = "dst",
+                          max_iter: int = 200, tol: float = 1e-12, out=None) -> dict:
+        """pdd_subdomain_solve on a 3-D box: faces maps a face index (2 axis +
+        side) to its Dirichlet data (the face's full grid, the higher axis
+        slow); the other faces take g.  Returns u [n2, n1, n0] (CUDA), iters,
+        resid."""
+        n0, n1, n2 = (int(v) for v in n)
+        mask = 0
+        parts = []
+        for fc in sorted(faces):
+            mask |= 1 << int(fc)
+            parts.append(_dev_f64(faces[fc], self.device).reshape(-1))
+        vals = torch.cat(parts) if parts else torch.zeros(0, dtype=_F64, device=self.device)
+        u = out if out is not None else torch.empty((n2, n1, n0), dtype=_F64, device=self.device)
+        sd = _lib.Subdomain((ctypes.c_double * 3)(*[float(v) for v in lo]),
+                            (ctypes.c_double * 3)(*[float(v) for v in hi]),
+                            (ctypes.c_int32 * 3)(n0, n1, n2), mask, 0, _lib.STENCIL[method],
+                            int(max_iter), float(tol))
+        it, res = ctypes.c_int64(0), ctypes.c_double(0.0)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_subdomain_solve(self.handle, ctypes.byref(sd), None,
+                                              vals.data_ptr() if vals.numel() else None,
+                                              vals.numel(), u.data_ptr(), ctypes.byref(it),
+                                              ctypes.byref(res))
+        status = _lib.check(st, self.handle, allow=(_lib.PDD_OK, _lib.PDD_ETIMEOUT))
+        return {"u": u, "iters": it.value, "resid": res.value, "status": status}
+
+    def interface_interp(self, planes, queries, *, n_bnd: int = 32) -> list:
+        """pdd_interface_interp: planes is a list of (axis, pos, nodes [m, 3],
+        values [m]); queries a list of [q, 3] point sets, one per plane.
+        Returns the interpolated values per plane (CUDA tensors)."""
+        P = len(planes)
+        axis = (ctypes.c_int32 * P)(*[int(p[0]) for p in planes])
+        pos = (ctypes.c_double * P)(*[float(p[1]) for p in planes])
+        nodes = [_dev_f64(p[2], self.device).reshape(-1, 3) for p in planes]
+        vals = [_dev_f64(p[3], self.device).reshape(-1) for p in planes]
+        qs = [_dev_f64(q, self.device).reshape(-1, 3) for q in queries]
+        cnt = (ctypes.c_int64 * P)(*[int(x.shape[0]) for x in nodes])
+        qcnt = (ctypes.c_int64 * P)(*[int(q.shape[0]) for q in qs])
+        d_nodes, d_vals, d_q = torch.cat(nodes), torch.cat(vals), torch.cat(qs)
+        out = torch.empty(d_q.shape[0], dtype=_F64, device=self.device)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            st = self.lib.pdd_interface_interp(self.handle, P, axis, pos, cnt, d_nodes.data_ptr(),
+                                               d_vals.data_ptr(), int(n_bnd), qcnt,
+                                               d_q.data_ptr(), out.data_ptr())
+        _lib.check(st, self.handle)
+        return list(torch.split(out, [int(q.shape[0]) for q in qs]))
+
     def set_params(self, params):
         """pdd_set_params: new parameter values for the same family."""
         arr = np.ascontiguousarray(params, dtype=np.float64).reshape(-1)
@@ -546,3 +596,71 @@ def laplace_pdd_solve(ctx: Context, *, n_nodes: int = 16, n_paths: int = 10_000,
     return {"nodes": nodes, "mean": r["mean"], "se": r["se"], "left": left["u"],
             "right": right["u"], "iters": left["iters"] + right["iters"],
             "status": max(left["status"], right["status"])}
+
+
+def elliptic3d_pdd_solve(ctx: Context, nodes, values, node_axis=None, *, grid: int = 129,
+                         split: int = 4, n_bnd: int = 32, method: str = "dst",
+                         tol: float = 1e-12, max_iter: int = 200) -> dict:
+    """Stage two of PDD for the 3-D problem on the unit cube split into
+    split^3 subdomains (Sec. 2.1, Fig. 2.2): the node estimates `values` at
+    `nodes` (every node on one of the internal planes x_a = k / split) are
+    interpolated on each plane (pdd_interface_interp, evaluated on the
+    plane's grid of `grid` x `grid` points; node_axis, if given, names the
+    plane axis each node belongs to, so that a node on two planes' line of
+    intersection is used by its own plane only), and every subdomain is solved on
+    its own (pdd_subdomain_solve) with the interpolated values on its
+    interface faces and g on the cube's boundary.  Returns the global solution
+    u [grid, grid, grid] ([z][y][x]), the largest iteration count and
+    residual, and the time of each part is left to the caller."""
+    if ctx.prob["problem"] != "elliptic_manufactured":
+        raise ValueError("elliptic3d_pdd_solve needs the 3-D problem on the unit cube")
+    if (grid - 1) % split:
+        raise ValueError("grid - 1 must be a multiple of split")
+    dev = ctx.device
+    nodes = _dev_f64(nodes, dev).reshape(-1, 3)
+    values = _dev_f64(values, dev).reshape(-1)
+    if node_axis is not None:
+        node_axis = torch.as_tensor(node_axis, device=dev).reshape(-1)
+    t = torch.linspace(0.0, 1.0, grid, dtype=_F64, device=dev)
+    planes, queries = [], []
+    for a in range(3):
+        for k in range(1, split):
+            pos = k / split
+            sel = nodes[:, a] == pos
+            if node_axis is not None:
+                sel &= node_axis == a
+            planes.append((a, pos, nodes[sel], values[sel]))
+            o = [b for b in range(3) if b != a]
+            g2, g1 = torch.meshgrid(t, t, indexing="ij")      # [slow = o[1]][fast = o[0]]
+            q = torch.empty((grid * grid, 3), dtype=_F64, device=dev)
+            q[:, a] = pos
+            q[:, o[0]] = g1.reshape(-1)
+            q[:, o[1]] = g2.reshape(-1)
+            queries.append(q)
+    vals = ctx.interface_interp(planes, queries, n_bnd=n_bnd)
+    plane_grid = {(a, k): vals[a * (split - 1) + k - 1].reshape(grid, grid)
+                  for a in range(3) for k in range(1, split)}
+    m = (grid - 1) // split + 1
+    u = torch.empty((grid, grid, grid), dtype=_F64, device=dev)
+    iters, resid = 0, 0.0
+    for kz in range(split):
+        for ky in range(split):
+            for kx in range(split):
+                kk = (kx, ky, kz)
+                lo = [kk[a] / split for a in range(3)]
+                hi = [(kk[a] + 1) / split for a in range(3)]
+                sl = [slice(kk[a] * (m - 1), kk[a] * (m - 1) + m) for a in range(3)]
+                faces = {}
+                for a in range(3):
+                    o = [b for b in range(3) if b != a]
+                    for side in (0, 1):
+                        plane = kk[a] + side
+                        if 0 < plane < split:
+                            pg = plane_grid[(a, plane)]
+                            faces[2 * a + side] = pg[sl[o[1]], sl[o[0]]].contiguous()
+                r = ctx.subdomain_solve3d(lo, hi, (m, m, m), faces, method=method, tol=tol,
+                                          max_iter=max_iter)
+                u[sl[2], sl[1], sl[0]] = r["u"]
+                iters = max(iters, r["iters"])
+                resid = max(resid, r["resid"])
+    return {"u": u, "iters": iters, "resid": resid, "plane_values": plane_grid}

@@ -287,6 +287,18 @@ pdd_status pdd_mlmc_level(pdd_ctx *ctx, const double *d_nodes, int64_t n, const 
   return pdd::mlmc_level_impl(ctx, d_nodes, n, mp, d_mean, d_var, d_fine_mean, d_coarse_mean, diag);
 }
 
+pdd_status pdd_interface_interp(pdd_ctx *ctx, int32_t n_planes, const int32_t *axis,
+                                const double *pos, const int64_t *node_count,
+                                const double *d_nodes, const double *d_vals, int32_t n_bnd,
+                                const int64_t *query_count, const double *d_query,
+                                double *d_out) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  const TraceRange trace(__func__);
+  return pdd::interface_interp_impl(ctx, n_planes, axis, pos, node_count, d_nodes, d_vals, n_bnd,
+                                    query_count, d_query, d_out);
+}
+
 pdd_status pdd_mlmc_solve(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                           const pdd_mlmc_params *mp, int32_t n_levels,
                           const int64_t *n_per_level, double *d_mean, double *d_se,

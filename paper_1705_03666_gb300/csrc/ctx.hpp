@@ -204,6 +204,13 @@ pdd_status mlmc_solve_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                            const pdd_mlmc_params *mp, int32_t n_levels,
                            const int64_t *h_n_per_level, double *d_mean, double *d_se,
                            double *d_level_mean, double *d_level_var, pdd_diag *diag);
+pdd_status interface_interp_impl(pdd_ctx *ctx, int32_t n_planes, const int32_t *h_axis,
+                                 const double *h_pos, const int64_t *h_node_count,
+                                 const double *d_nodes, const double *d_vals, int32_t n_bnd,
+                                 const int64_t *h_query_count, const double *d_query,
+                                 double *d_out);
+pdd_status subdomain_solve3d_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const double *d_face,
+                                  int64_t m, double *d_u, int64_t *iters, double *resid);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

@@ -165,8 +165,9 @@ struct PoissonFourier {
 // ---------------------------------------------------------------------------
 // Geometry: the box [0,1]^D.  Face j = 2k + s lies on x_k = s.
 // ---------------------------------------------------------------------------
-template <int D>
+template <int Dim>
 struct Box {
+  static constexpr int D = Dim;
   static constexpr int kFaces = 2 * D;
   static constexpr bool kFastScreen = true;  // one candidate face per axis
 
@@ -291,6 +292,7 @@ struct Box {
 // by the half-plane formula only approximately, like every corner).
 // ---------------------------------------------------------------------------
 struct LShape {
+  static constexpr int D = 2;
   static constexpr int kFaces = 6;
   static constexpr bool kFastScreen = false;
 

@@ -170,6 +170,27 @@ __device__ __forceinline__ int bridge_exit(const StepConst<R> &k, const R *prod,
   return take ? jbest : -1;
 }
 
+// FP64 re-decision of a near tie of the general-domain bridge test, from the
+// same binary32 face distances (kept out of line: it almost never runs, and
+// inlined it put FP64 instructions into the step code of every warp that
+// reaches the bridge test).  2-D geometries.
+template <class Geom>
+static __device__ __noinline__ bool bridge_generic_tie(float U, float inv_s2dt, float x0, float x1,
+                                                       float xn0, float xn1) {
+  const float X[2] = {x0, x1}, Xn[2] = {xn0, xn1};
+  double Pd = 0.0;
+  const double s = 2.0 * static_cast<double>(inv_s2dt);
+#pragma unroll
+  for (int j = 0; j < Geom::kFaces; ++j) {
+    const double aa = s * static_cast<double>(Geom::face_dist(j, X) * Geom::face_dist(j, Xn));
+    if (aa < 18.0) {
+      const double p = exp(-aa);
+      Pd = Pd + p * (1.0 - Pd);
+    }
+  }
+  return static_cast<double>(U) < Pd;
+}
+
 // Bridge over all faces of a general domain (distances from Geom::face_dist):
 // P = 1 - prod_j (1 - p_j) accumulated as P + p (1 - P) over the faces with
 // 2 d d' / (sigma^2 dt) < 18; FP32 near-ties decided in FP64.  Returns the
@@ -178,11 +199,9 @@ template <class Geom, typename R>
 __device__ __forceinline__ int bridge_generic(const StepConst<R> &k, const R *X, const R *Xn, R U) {
   R P = R(0), pbest = R(-1);
   int jbest = -1;
-  R dd[Geom::kFaces];
 #pragma unroll
   for (int j = 0; j < Geom::kFaces; ++j) {
-    dd[j] = Geom::face_dist(j, X) * Geom::face_dist(j, Xn);
-    const R aa = R(2) * dd[j] * k.inv_s2dt;
+    const R aa = R(2) * (Geom::face_dist(j, X) * Geom::face_dist(j, Xn)) * k.inv_s2dt;
     if (aa < R(18)) {
       const R p = k.exp_neg(aa);
       P = P + p * (R(1) - P);
@@ -192,19 +211,9 @@ __device__ __forceinline__ int bridge_generic(const StepConst<R> &k, const R *X,
   if (jbest < 0) return -1;
   bool take = U < P;
   if constexpr (sizeof(R) == 4) {
-    if (fabsf(U - P) <= 3.814697265625e-06f * P) {
-      double Pd = 0.0;
-      const double s = 2.0 * static_cast<double>(k.inv_s2dt);
-#pragma unroll
-      for (int j = 0; j < Geom::kFaces; ++j) {
-        const double aa = s * static_cast<double>(dd[j]);
-        if (aa < 18.0) {
-          const double p = exp(-aa);
-          Pd = Pd + p * (1.0 - Pd);
-        }
-      }
-      take = static_cast<double>(U) < Pd;
-    }
+    static_assert(Geom::D == 2, "the out-of-line tie test takes 2-D points");
+    if (fabsf(U - P) <= 3.814697265625e-06f * P)
+      take = bridge_generic_tie<Geom>(U, k.inv_s2dt, X[0], X[1], Xn[0], Xn[1]);
   }
   return take ? jbest : -1;
 }

@@ -415,6 +415,7 @@ pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const dou
                                 const double *d_iface_vals, int64_t m, double *d_u,
                                 int64_t *iters, double *resid) {
   if (!sd || !d_u || !iters || !resid) return fail(ctx, PDD_EINVAL, "null argument");
+  if (sd->n[2] > 1) return subdomain_solve3d_impl(ctx, sd, d_iface_vals, m, d_u, iters, resid);
   if (ctx->prob.kind != PDD_PROB_LAPLACE_EXPCOS)
     return fail(ctx, PDD_EINVAL, "the subdomain solver covers the Laplace family (Eq. 1.1)");
   const int nx = sd->n[0], ny = sd->n[1];
