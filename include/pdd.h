@@ -561,20 +561,21 @@ PDD_API pdd_status pdd_profile_read(pdd_ctx *ctx, double *kernel_ms,
 
 /* pdd_interface_solve without any device allocation.  The paper has no
  * counterpart: this is a deployment variant for callers that cannot call
- * cudaMalloc -- code running while a stream is being captured into a CUDA
- * graph under a no-allocation policy, hosts whose memory pool owns the whole
- * device, plug-ins that only receive pre-allocated buffers, and latency-
- * critical loops where an allocation (or its failure) is not acceptable.
+ * cudaMalloc -- hosts whose memory pool owns the whole device, plug-ins that
+ * only receive pre-allocated buffers, and latency-critical loops where an
+ * allocation (or its failure) is not acceptable.
  * It computes the same estimate as pdd_interface_solve (same kernels, same
- * streams, no diagnostics) on `device` and `cuda_stream`, without a context.
- * The caller still provides the inputs and outputs (device pointers, as for
- * pdd_interface_solve).  Scratch comes from one static 32 MiB device array
- * that every GPU loading this library holds until process exit; n is limited
- * to 65536 nodes (PDD_EINVAL beyond), any number of paths is processed in
- * waves that fit the array.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  All calls
- * share the array and each clears it at the start, so calls that overlap on
- * the GPU (different streams, or different threads) race: serialise them.
+ * streams, same exact per-node sums, no diagnostics) on `device` and
+ * `cuda_stream`, without a context, in one path-kernel launch and one
+ * finalisation launch.  The caller still provides the inputs and outputs
+ * (device pointers, as for pdd_interface_solve).  Scratch comes from one
+ * static 8 MiB device array that every GPU loading this library holds until
+ * process exit (256 bytes of counters and 112 bytes per node); n is limited
+ * to 65536 nodes and node_offset + n to 2^32 (PDD_EINVAL beyond), the path
+ * count is not limited.  The first call on a device loads the kernels; every
+ * call looks up the array's device address (no allocation).  All calls share
+ * the array and each clears it at the start, so calls that overlap on the GPU
+ * (different streams, or different threads) race: serialise them.
  * It calls no cudaMalloc, cudaFree or allocating library routine.          */
 PDD_API pdd_status pdd_interface_solve_static(const pdd_problem *problem,
                                               int device, void *cuda_stream,
