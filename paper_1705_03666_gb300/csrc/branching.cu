@@ -69,6 +69,9 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
     a.cum[k] = static_cast<float>(cum);
     a.ratio[k] = static_cast<float>(q > 0.0 ? al / q : 0.0);
   }
+  // (with 2^32 trees per node every index below 2^32 - 1 is in node 0)
+  branch_divisor(N < (uint64_t(1) << 32) ? static_cast<uint32_t>(N) : 0xffffffffu, &a.nt_m,
+                 &a.nt_s1, &a.nt_s2);
   a.max_particles = bp->max_particles;
   a.max_depth = bp->max_depth;
   int32_t *flags = diag ? diag->d_node_flags : nullptr;
@@ -78,7 +81,17 @@ static pdd_status run_branching(pdd_ctx *ctx, const double *d_nodes_xt, int64_t 
   const bool binary = a.K == 2 && prm[4] == 0.0 && prm[5] == 0.0 && prm[6] == 1.0 &&
                       prm[5 + a.K + 2] == 1.0;
 
-  auto kern = binary ? branch_kernel<D, true> : branch_kernel<D, false>;
+  // the KPP law gets one instantiation per initial-data kind; other laws read
+  // the kind at run time
+  void (*kern)(BranchArgs) = branch_kernel<D, false, -1>;
+  if (binary) {
+    switch (a.psi_kind) {
+      case 0: kern = branch_kernel<D, true, 0>; break;
+      case 1: kern = branch_kernel<D, true, 1>; break;
+      case 2: kern = branch_kernel<D, true, 2>; break;
+      default: kern = branch_kernel<D, true, 3>; break;
+    }
+  }
   int bps = 0;
   PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kBranchBlock, 0));
   if (bps < 1) bps = 1;

@@ -44,10 +44,15 @@ struct ThreadSums;
 template <bool kSkipNaN>
 struct ThreadSums<float, kSkipNaN> {
   F2Sum s1, s2;
-  unsigned long long kept = 0;
+  unsigned kept = 0;  // below 2^32: a wave holds at most 2^31 scores
   __device__ __forceinline__ void add(float v, float K) {
-    if (kSkipNaN && isnan(v)) return;
-    ++kept;
+    if (kSkipNaN) {  // a NaN score is replaced by K, which adds exactly zero
+      const bool ok = !isnan(v);
+      kept += ok ? 1u : 0u;
+      v = ok ? v : K;
+    } else {
+      ++kept;
+    }
     const float d = v - K;  // d + dl = v - K exactly
     const float bb = d - v;
     const float dl = (v - (d - bb)) + (-K - bb);
@@ -97,7 +102,27 @@ reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
   const R Kr = kSkipNaN ? R(0) : s[0];
   const double K = static_cast<double>(Kr);
   ThreadSums<R, kSkipNaN> ts;
-  for (uint64_t i = threadIdx.x; i < cnt; i += kReduceBlock) ts.add(s[i], Kr);
+  if constexpr (sizeof(R) == 4) {
+    // binary32 scores: scalar up to a 16-byte boundary, then four per load
+    // with several loads in flight per thread (the reduction is bound by
+    // memory latency otherwise), then the scalar tail
+    uint64_t head = ((16u - (reinterpret_cast<uintptr_t>(s) & 15u)) & 15u) / 4u;
+    if (head > cnt) head = cnt;
+    if (threadIdx.x < head) ts.add(s[threadIdx.x], Kr);
+    const float4 *v = reinterpret_cast<const float4 *>(s + head);
+    const uint64_t n4 = (cnt - head) / 4;
+#pragma unroll 4
+    for (uint64_t j = threadIdx.x; j < n4; j += kReduceBlock) {
+      const float4 q = __ldcs(v + j);
+      ts.add(q.x, Kr);
+      ts.add(q.y, Kr);
+      ts.add(q.z, Kr);
+      ts.add(q.w, Kr);
+    }
+    for (uint64_t i = head + 4 * n4 + threadIdx.x; i < cnt; i += kReduceBlock) ts.add(s[i], Kr);
+  } else {
+    for (uint64_t i = threadIdx.x; i < cnt; i += kReduceBlock) ts.add(s[i], Kr);
+  }
   CSum s1, s2;
   ts.out(s1, s2);
   unsigned long long kept = ts.kept;

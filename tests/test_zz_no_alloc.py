@@ -55,13 +55,22 @@ def _static_call(lib, prob, nodes, mc, out=None):
 
 
 CASES = [(2, "fp32", 16, 3001), (1, "fp64", 1, 2000), (5, "fp32", 32, 1500),
-         (5, "fp64", 128, 500), (2, "fp64", 2, 2100)]
+         (5, "fp64", 128, 500), (2, "fp64", 2, 2100), ("pf", "fp32", 1, 4000),
+         ("pf", "fp64", 1, 1000)]
+
+
+def _workload(k):
+    if k == "pf":   # the random-coefficient Poisson family on workload 1's 16 square nodes
+        w = dict(W.workload(1))
+        w["prob"] = W.poisson_fourier(5)
+        return w
+    return W.workload(k)
 
 
 @pytest.mark.parametrize("k,precision,stride,n_paths", CASES)
 def test_static_matches_context_solve_twice(lib, k, precision, stride, n_paths):
     from paper_1705_03666_gb300 import api
-    w = W.workload(k)
+    w = _workload(k)
     nodes = torch.from_numpy(np.ascontiguousarray(w["nodes"][::stride])).cuda()
     kw = dict(seed=w["seed"], dt=1e-3, n_paths=n_paths, precision=precision)
     with api.Context(w["prob"]) as ctx:
