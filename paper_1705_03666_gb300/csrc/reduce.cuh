@@ -46,13 +46,20 @@ struct ThreadSums<float, kSkipNaN> {
   F2Sum s1, s2;
   unsigned kept = 0;  // below 2^32: a wave holds at most 2^31 scores
   __device__ __forceinline__ void add(float v, float K) {
-    if (kSkipNaN) {  // a NaN score is replaced by K, which adds exactly zero
+    if constexpr (kSkipNaN) {
+      // K = 0 here: a NaN score is replaced by 0, which adds exactly zero,
+      // and the shift needs no split
       const bool ok = !isnan(v);
       kept += ok ? 1u : 0u;
-      v = ok ? v : K;
-    } else {
-      ++kept;
+      v = ok ? v : 0.0f;
+      s1.add(v);
+      const float q = v * v;
+      const float e = fmaf(v, v, -q);
+      s2.add(q);
+      s2.lo += e;
+      return;
     }
+    ++kept;
     const float d = v - K;  // d + dl = v - K exactly
     const float bb = d - v;
     const float dl = (v - (d - bb)) + (-K - bb);
