@@ -4,14 +4,18 @@
 //
 //   0. the nodes are grouped by domain/family (stable partition on the
 //      device); chunk lists follow that order, one kernel per family;
-//   1. pilot: n_pilot paths per node (lane-chunk queue, batch_kernel);
-//   2. per node: pilot mean and variance s^2, path count
+//   1. pilot: n_pilot paths per node (lane-chunk queue, batch_kernel), their
+//      scores added to the node's exact sums (nodefix.cuh);
+//   2. per node: pilot mean and variance s^2 from those sums, path count
 //      N_i = clamp(ceil(s^2 / SE*^2), max(n_min, n_pilot), n_max);
 //   3. exclusive scan of the per-node chunk counts of paths [n_pilot, N_i);
-//   4. main pass over that device-built work list (same persistent kernel);
-//   5. per node: pilot and main partials merged in chunk order (Chan).
+//   4. main pass over that device-built work list (same persistent kernel),
+//      adding to the same sums;
+//   5. per node: mean, standard error and count from the sums.
 // Paths [0, N_i) of node i are the streams pdd_interface_solve would use, so
-// the pilot paths are part of the final estimate.
+// the pilot paths are part of the final estimate, and a batch with a fixed
+// count N reproduces pdd_interface_solve's estimate bit for bit (integer sums
+// do not depend on the order in which paths are added).
 #include <cmath>
 #include <cstring>
 
@@ -75,7 +79,7 @@ batch_partition(int64_t n, const int32_t *prob, int32_t n_probs, int4 combo_of_p
 
 // Pilot work list: every node gets paths [0, n_pilot).
 __global__ void batch_pilot_setup(int64_t n, int64_t n_pilot, int32_t K, int64_t *chunk_off,
-                                  int64_t *first, int64_t *end, double *shift) {
+                                  int64_t *first, int64_t *end) {
   const int64_t cpn = (n_pilot + K - 1) / K;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i <= n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -83,45 +87,33 @@ __global__ void batch_pilot_setup(int64_t n, int64_t n_pilot, int32_t K, int64_t
     if (i < n) {
       first[i] = 0;
       end[i] = n_pilot;
-      shift[i] = 0.0;
     }
   }
 }
 
-// Per node: merge the pilot chunk partials (fixed order) into (n, mean, M2),
-// choose N_i and write the main work list's per-node entries.
-// Kp: paths per pilot chunk; K: paths per main-pass chunk.  Runs over
-// positions j (node i = perm[j]): the pilot chunks of position j are
-// [j cpn, (j + 1) cpn); count2 is written by position (the main scan's order)
-// and the other outputs by node.  Positions of invalid nodes get no chunks.
-__global__ void batch_pilot_stats(int64_t n, int64_t n_pilot, int32_t Kp, int32_t K,
-                                  const int32_t *perm, const int64_t *cstart,
-                                  const ChunkPartial *part, double inv_se2, int64_t n_min,
-                                  int64_t n_max, NodeAcc *pilot, int64_t *first2, int64_t *end2,
-                                  double *shift2, int64_t *count2) {
+// Per node, from the exact sums of its pilot paths: the sample variance,
+// N_i and the main work list's per-node entries.  K: paths per main-pass
+// chunk.  Runs over positions j (node i = perm[j]); count2 is written by
+// position (the main scan's order) and the other outputs by node.  Positions
+// of invalid nodes (problem index out of range) get no chunks and are marked
+// invalid in the sums, so that they finish with NaN and a count of 0.
+__global__ void batch_pilot_stats(int64_t n, int64_t n_pilot, int32_t K, const int32_t *perm,
+                                  const int64_t *cstart, NodeFix *fix, double inv_se2,
+                                  int64_t n_min, int64_t n_max, int64_t *first2, int64_t *end2,
+                                  int64_t *count2) {
   const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (j >= n) return;
   const int64_t i = perm[j];
   if (j >= cstart[4]) {
-    pilot[i] = NodeAcc{0.0, 0.0, 0.0};
+    fix[i].bad = 1;
     first2[i] = end2[i] = n_pilot;
-    shift2[i] = 0.0;
     count2[j] = 0;
     return;
   }
-  const int64_t cpn = (n_pilot + Kp - 1) / Kp;
-  double nt = 0.0, mean = 0.0, m2 = 0.0;
-  for (int64_t c = 0; c < cpn; ++c) {
-    const ChunkPartial P = part[j * cpn + c];
-    if (P.n <= 0.0) continue;
-    const double mb = P.s1 / P.n;
-    const double m2b = fmax(0.0, P.s2 - P.s1 * mb);
-    const double tot = nt + P.n, d = mb - mean;
-    mean += d * (P.n / tot);
-    m2 += m2b + d * d * (nt * P.n / tot);
-    nt = tot;
-  }
-  pilot[i] = NodeAcc{nt, mean, m2};
+  const NodeFix F = fix[i];
+  double mean, m2;
+  fix_moments(F, &mean, &m2);
+  const double nt = static_cast<double>(F.n);
   const double var = nt > 1.0 ? m2 / (nt - 1.0) : 0.0;
   double want = ceil(var * inv_se2);
   const int64_t lo = max(n_min, n_pilot);
@@ -130,7 +122,6 @@ __global__ void batch_pilot_stats(int64_t n, int64_t n_pilot, int32_t Kp, int32_
   if (isnan(var)) Ni = lo;
   first2[i] = n_pilot;
   end2[i] = Ni;
-  shift2[i] = mean;
   count2[j] = (Ni - n_pilot + K - 1) / K;
 }
 
@@ -159,39 +150,6 @@ batch_scan(int64_t n, const int64_t *count, int64_t *off) {
     off[i] = acc;
     acc += count[i];
   }
-}
-
-// Per node: pilot triple merged with the main chunk partials (shifted by the
-// pilot mean) in chunk order; writes mean, standard error and path count.
-__global__ void batch_final(int64_t n, const int32_t *perm, const int64_t *cstart,
-                            const NodeAcc *pilot, const int64_t *off2, const double *shift2,
-                            const ChunkPartial *part2, double *mean_out, double *se_out,
-                            int64_t *n_out) {
-  const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (j >= n) return;
-  const int64_t i = perm[j];
-  if (j >= cstart[4]) {  // problem index out of range
-    mean_out[i] = se_out[i] = static_cast<double>(NAN);
-    if (n_out) n_out[i] = 0;
-    return;
-  }
-  const NodeAcc A = pilot[i];
-  double nt = A.n, mean = A.mean, m2 = A.m2;
-  const double K = shift2[i];
-  for (int64_t c = off2[j]; c < off2[j + 1]; ++c) {
-    const ChunkPartial P = part2[c];
-    if (P.n <= 0.0) continue;
-    const double mb_shift = P.s1 / P.n;
-    const double mb = K + mb_shift;
-    const double m2b = fmax(0.0, P.s2 - P.s1 * mb_shift);
-    const double tot = nt + P.n, d = mb - mean;
-    mean += d * (P.n / tot);
-    m2 += m2b + d * d * (nt * P.n / tot);
-    nt = tot;
-  }
-  mean_out[i] = mean;
-  se_out[i] = nt > 1.0 ? sqrt(m2 / (nt - 1.0) / nt) : 0.0;
-  if (n_out) n_out[i] = static_cast<int64_t>(nt);
 }
 
 // Per-node flags of the adaptive batch: the target standard error not
@@ -223,12 +181,11 @@ int combo_of(const pdd_problem &p) {
 }
 
 struct BatchLayout {
-  size_t off_first, off_end, off_shift, off_chunk, off_first2, off_end2, off_shift2, off_cnt2,
-      off_chunk2, off_pilot, off_perm, off_cstart, off_part, off_part2, total;
-  int64_t pilot_chunks, main_chunks_max;
+  size_t off_first, off_end, off_chunk, off_first2, off_end2, off_cnt2, off_chunk2, off_fix,
+      off_perm, off_cstart, total;
 };
 
-BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K, int32_t Kp) {
+BatchLayout batch_layout(int64_t n) {
   BatchLayout L;
   size_t o = 256;
   auto take = [&](size_t bytes) {
@@ -239,22 +196,14 @@ BatchLayout batch_layout(int64_t n, const pdd_batch_params *bp, int32_t K, int32
   const size_t nn = static_cast<size_t>(n);
   L.off_first = take(nn * 8);
   L.off_end = take(nn * 8);
-  L.off_shift = take(nn * 8);
   L.off_chunk = take((nn + 1) * 8);
   L.off_first2 = take(nn * 8);
   L.off_end2 = take(nn * 8);
-  L.off_shift2 = take(nn * 8);
   L.off_cnt2 = take(nn * 8);
   L.off_chunk2 = take((nn + 1) * 8);
-  L.off_pilot = take(nn * sizeof(NodeAcc));
+  L.off_fix = take(nn * sizeof(NodeFix));
   L.off_perm = take(nn * sizeof(int32_t));
   L.off_cstart = take(8 * sizeof(int64_t));
-  L.pilot_chunks = n * ((bp->n_pilot + Kp - 1) / Kp);
-  const int64_t extra = std::max<int64_t>(0, bp->n_max - bp->n_pilot);
-  L.main_chunks_max = n * ((extra + K - 1) / K);
-  L.off_part = take(static_cast<size_t>(L.pilot_chunks) * sizeof(ChunkPartial));
-  L.off_part2 = take(static_cast<size_t>(std::max<int64_t>(1, L.main_chunks_max)) *
-                     sizeof(ChunkPartial));
   L.total = o;
   return L;
 }
@@ -320,26 +269,23 @@ static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const Batc
   auto *counters = reinterpret_cast<unsigned long long *>(base);
   auto *first = reinterpret_cast<int64_t *>(base + Lay.off_first);
   auto *end = reinterpret_cast<int64_t *>(base + Lay.off_end);
-  auto *shift = reinterpret_cast<double *>(base + Lay.off_shift);
   auto *chunk = reinterpret_cast<int64_t *>(base + Lay.off_chunk);
   auto *first2 = reinterpret_cast<int64_t *>(base + Lay.off_first2);
   auto *end2 = reinterpret_cast<int64_t *>(base + Lay.off_end2);
-  auto *shift2 = reinterpret_cast<double *>(base + Lay.off_shift2);
   auto *cnt2 = reinterpret_cast<int64_t *>(base + Lay.off_cnt2);
   auto *chunk2 = reinterpret_cast<int64_t *>(base + Lay.off_chunk2);
-  auto *pilot = reinterpret_cast<NodeAcc *>(base + Lay.off_pilot);
+  auto *fix = reinterpret_cast<NodeFix *>(base + Lay.off_fix);
   auto *perm = reinterpret_cast<int32_t *>(base + Lay.off_perm);
   auto *cstart = reinterpret_cast<int64_t *>(base + Lay.off_cstart);
   auto *cursors = counters + 8;  // one per family
-  auto *part = reinterpret_cast<ChunkPartial *>(base + Lay.off_part);
-  auto *part2 = reinterpret_cast<ChunkPartial *>(base + Lay.off_part2);
   const int64_t n = nodes->n;
   const unsigned nb = static_cast<unsigned>((n + 255) / 256);
 
   PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, 256, ctx->stream));
+  PDD_CUDA_TRY(ctx, cudaMemsetAsync(fix, 0, static_cast<size_t>(n) * sizeof(NodeFix), ctx->stream));
   batch_partition<<<1, kScanBlock, 0, ctx->stream>>>(n, nodes->d_problem, n_probs, combo_of_prob,
                                                      perm, cstart, counters + 2);
-  batch_pilot_setup<<<nb + 1, 256, 0, ctx->stream>>>(n, bp->n_pilot, Kp, chunk, first, end, shift);
+  batch_pilot_setup<<<nb + 1, 256, 0, ctx->stream>>>(n, bp->n_pilot, Kp, chunk, first, end);
   BatchArgs a = proto;
   a.perm = perm;
   a.cstart = cstart;
@@ -347,31 +293,26 @@ static pdd_status enqueue_batch(pdd_ctx *ctx, const BatchArgs &proto, const Batc
   a.chunk_off = chunk;
   a.first = first;
   a.end = end;
-  a.shift = shift;
   a.cursor = cursors;
   a.counters = counters;
-  a.partial = part;
+  a.fix = fix;
   pdd_status st = launch_families(ctx, a, grid);
   if (st != PDD_OK) return st;
-  batch_pilot_stats<<<nb, 256, 0, ctx->stream>>>(n, bp->n_pilot, Kp, K, perm, cstart, part,
+  batch_pilot_stats<<<nb, 256, 0, ctx->stream>>>(n, bp->n_pilot, K, perm, cstart, fix,
                                                  1.0 / (bp->target_se * bp->target_se),
-                                                 bp->n_min, bp->n_max, pilot, first2, end2, shift2,
-                                                 cnt2);
+                                                 bp->n_min, bp->n_max, first2, end2, cnt2);
   batch_scan<<<1, kScanBlock, 0, ctx->stream>>>(n, cnt2, chunk2);
   PDD_CUDA_TRY(ctx, cudaMemsetAsync(cursors, 0, 4 * sizeof(unsigned long long), ctx->stream));
   a.K = K;
   a.chunk_off = chunk2;
   a.first = first2;
   a.end = end2;
-  a.shift = shift2;
-  a.partial = part2;
   const auto ev = prof_slot(ctx);
   if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
   st = launch_families(ctx, a, grid);
   if (st != PDD_OK) return st;
   if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
-  batch_final<<<nb, 256, 0, ctx->stream>>>(n, perm, cstart, pilot, chunk2, shift2, part2, d_mean,
-                                           d_se, d_npaths);
+  fix_finalize_kernel<<<nb, 256, 0, ctx->stream>>>(fix, n, d_mean, d_se, d_npaths, nullptr);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
   return PDD_OK;
 }
@@ -459,7 +400,7 @@ pdd_status batch_solve_impl(pdd_ctx *ctx, const pdd_problem *problems, int32_t n
   const double pilot_paths = static_cast<double>(nodes->n) * static_cast<double>(bp->n_pilot);
   const double per_lane = pilot_paths / (8.0 * max_grid * kBatchBlock);
   const int32_t Kp = static_cast<int32_t>(std::max(1.0, std::min<double>(K, std::floor(per_lane))));
-  const BatchLayout Lay = batch_layout(nodes->n, bp, K, Kp);
+  const BatchLayout Lay = batch_layout(nodes->n);
   pdd_status st = ensure_scratch(ctx, Lay.total);
   if (st != PDD_OK) return st;
   st = ensure_side_streams(ctx);

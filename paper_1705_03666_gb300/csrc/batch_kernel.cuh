@@ -43,10 +43,6 @@ struct BatchProblem {
   double c_kill;  // constant killing rate (paper's c)
 };
 
-struct ChunkPartial {  // n, sum (s - K_i), sum (s - K_i)^2
-  double n, s1, s2;
-};
-
 struct BatchArgs {
   const double *nodes;      // [n][3] (z ignored by 2-D families)
   const int32_t *prob;      // [n] index into probs
@@ -62,11 +58,10 @@ struct BatchArgs {
   const int64_t *chunk_off;
   const int64_t *first;
   const int64_t *end;
-  const double *shift;      // [n] per-node shift K_i of the sums
   int32_t K;
   unsigned long long *cursor;  // [4]: one per family
   unsigned long long *counters;  // [0] path steps, [1] capped, [2] bad nodes
-  ChunkPartial *partial;    // [chunk_off[n]]
+  NodeFix *fix;             // [n] exact per-node sums (both passes add to them)
   RoundKeys rk;
   int32_t max_steps;
   int32_t n_probs;
@@ -86,26 +81,49 @@ struct BatchLane {
   PhiloxPath pp;
 };
 
-// One loop unit (path_unit) of a path of family Model on domain Geom.
-// Returns true when the path exited (score in s); the caller handles the cap.
-template <class Model, class Geom>
-__device__ __forceinline__ bool batch_unit(const BatchEnv &env, const StepConst<float> &k,
-                                           const RoundKeys &rk, int32_t max_steps, BatchLane &L,
-                                           float &s) {
-  float xe[Model::D], lr[1];
-  return path_unit<Model, Geom, float, false>(env, k, L.pp, rk, max_steps, L.X, L.Y, L.Z, L.n, s,
-                                              xe, lr);
-}
+// Ended paths of a warp, parked until 32 can be scored together: the start
+// and end of the last step (or the position of a capped path), Y, Z, the
+// exit code and the node and problem the path belongs to.
+struct BatchExitQueue {
+  float x[3][32], xn[3][32];
+  float y[32], z[32];
+  int32_t code[32];
+  uint32_t node[32];
+  int32_t prob[32];
+};
 
-// Score of a capped path: g at the projection on the nearest face.
+// Called by all 32 lanes: score the first cnt parked paths, one per lane,
+// and add the scores to their nodes' exact sums.
 template <class Model, class Geom>
-__device__ __forceinline__ float batch_capped(const ModelConst &mc, const BatchLane &L) {
+__device__ __forceinline__ void batch_flush(const BatchArgs &a, BatchExitQueue &q, int cnt) {
   constexpr int D = Model::D;
-  float xe[D];
+  const int lane = static_cast<int>(threadIdx.x & 31u);
+  __syncwarp();
+  float s = 0.f;
+  uint32_t node = 0;
+  bool capped = false;
+  if (lane < cnt) {
+    float X[D], Xn[D], xe[D];
 #pragma unroll
-  for (int d = 0; d < D; ++d) xe[d] = L.X[d];
-  Geom::project(Geom::nearest_face(xe), xe);
-  return Model::g(mc, xe) * L.Y + L.Z;
+    for (int d = 0; d < D; ++d) {
+      X[d] = q.x[d][lane];
+      Xn[d] = q.xn[d][lane];
+    }
+    const int code = q.code[lane];
+    const ModelConst &mc = a.probs[q.prob[lane]].mc;
+    node = q.node[lane];
+    capped = code == kStepCapped;
+    if (capped) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) xe[d] = X[d];
+      Geom::project(Geom::nearest_face(X), xe);
+      s = Model::g(mc, xe) * q.y[lane] + q.z[lane];
+    } else {
+      s = exit_score<Model, Geom, float>(mc, code, X, Xn, q.y[lane], q.z[lane], xe);
+    }
+  }
+  fix_commit<float>(a.fix, lane < cnt, node, s, capped, false);
+  __syncwarp();
 }
 
 template <class Model, class Geom>
@@ -130,6 +148,9 @@ __global__ void __launch_bounds__(kBatchBlock)
 batch_kernel(const __grid_constant__ BatchArgs a) {
   using M = typename ComboTraits<C>::M;
   using G = typename ComboTraits<C>::G;
+  constexpr int D = M::D;
+  __shared__ BatchExitQueue queue_all[kBatchBlock / 32];
+  BatchExitQueue &queue = queue_all[threadIdx.x >> 5];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
   // this family's positions and chunks
@@ -138,24 +159,21 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
   const uint64_t c_lo = static_cast<uint64_t>(a.chunk_off[jlo]);
   const uint64_t c_hi = static_cast<uint64_t>(a.chunk_off[jhi]);
   unsigned long long *cursor = a.cursor + C;
-  BatchLane L;
+  float X[3] = {0.f, 0.f, 0.f}, Xn[3];
+  float Y = 1.f, Z = 0.f;
+  int32_t n = 0;
+  PhiloxPath pp{0, 0, 0};
   float x0[3] = {0.f, 0.f, 0.f};  // the chunk's node, converted once per chunk
   StepConst<float> k;
   int32_t pi = 0;
   uint32_t node = 0;
   int64_t path = 0, path_end = 0;
-  uint64_t chunk = 0;
-  // per-chunk sums of (s - K_i) and its square as two-float values on the
-  // FP32 pipe (FP64 adds per path, at 1/64 rate in divergent code, were a
-  // visible cost); the chunk partial is written in FP64
-  float shift_f = 0.f;
-  double shift = 0.0;
-  F2Sum s1, s2;
-  int32_t cnt = 0;
   bool active = false, need = true;
+  int n_exit = 0;  // parked paths (warp-uniform)
   unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
 
   for (;;) {
+    // ---- lanes without a path take the next chunk (warp-aggregated claims)
     for (;;) {
       const unsigned needmask = __ballot_sync(kFull, need);
       if (!needmask) break;
@@ -168,7 +186,6 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
         need = false;
         const unsigned long long c = c_lo + base + __popc(needmask & lt_mask);
         if (c < c_hi) {
-          chunk = c;
           // position owning chunk c: last j in [jlo, jhi) with chunk_off[j] <= c
           int64_t lo = jlo, hi = jhi;
           while (hi - lo > 1) {
@@ -183,83 +200,84 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
           pi = a.prob[i];
           const BatchProblem &P = a.probs[pi];
           k = make_step_const(a.dt[i], P.sigma, P.c_kill, P.bridge != 0);
-          shift = a.shift ? a.shift[i] : 0.0;
-          shift_f = static_cast<float>(shift);
-          s1 = F2Sum();
-          s2 = F2Sum();
-          cnt = 0;
-          x0[0] = static_cast<float>(a.nodes[i * 3 + 0]);
-          x0[1] = static_cast<float>(a.nodes[i * 3 + 1]);
-          x0[2] = static_cast<float>(a.nodes[i * 3 + 2]);
-          L.X[0] = x0[0];
-          L.X[1] = x0[1];
-          L.X[2] = x0[2];
-          if (!batch_inside<M, G>(L.X)) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) x0[d] = static_cast<float>(a.nodes[i * 3 + d]);
+          if (!batch_inside<M, G>(x0)) {
             // node on (or, invalid, outside) the boundary: every path scores g
-            const bool closed = batch_closed<M, G>(L.X);
-            const double v = closed ? static_cast<double>(M::g(P.mc, L.X)) - shift
-                                    : static_cast<double>(NAN);
+            const bool closed = batch_closed<M, G>(x0);
             if (!closed) ++my_bad;
-            const double cn = static_cast<double>(path_end - path);
-            a.partial[chunk] = ChunkPartial{cn, cn * v, cn * v * v};
+            fix_add_repeated<float>(a.fix, node, closed ? M::g(P.mc, x0) : NAN,
+                                    path_end - path);
             need = true;
           } else {
-            L.Y = 1.f;
-            L.Z = 0.f;
-            L.n = 0;
-            L.pp = philox_path(static_cast<uint32_t>(path), node, 0u, a.rk);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) X[d] = x0[d];
+            Y = 1.f;
+            Z = 0.f;
+            n = 0;
+            pp = philox_path(static_cast<uint32_t>(path), node, 0u, a.rk);
             active = true;
           }
         }
       }
     }
     if (!__any_sync(kFull, active)) break;
-    if (!active) continue;
 
-    const BatchProblem &P = a.probs[pi];
-    const BatchEnv env{P.mc, P.bridge};
-    float s = 0.f;
-    bool done = batch_unit<M, G>(env, k, a.rk, a.max_steps, L, s);
-    if (!done && L.n >= a.max_steps) {
-      s = batch_capped<M, G>(P.mc, L);
-      ++my_capped;
-      done = true;
-    }
-    if (done) {
-      // s - shift_f split exactly into two floats (the shift is rounded to
-      // FP32 once per chunk; the FP64 partial corrects for shift - shift_f)
-      const float d = s - shift_f;
-      const float bb = d - s;
-      const float dl = (s - (d - bb)) + (-shift_f - bb);
-      s1.add(d);
-      s1.lo += dl;
-      const float q = d * d;
-      s2.add(q);
-      s2.lo += fmaf(d, d, -q) + 2.0f * d * dl;
-      ++cnt;
-      my_steps += static_cast<unsigned long long>(L.n);
-      ++path;
-      if (path < path_end) {
-        L.X[0] = x0[0];
-        L.X[1] = x0[1];
-        L.X[2] = x0[2];
-        L.Y = 1.f;
-        L.Z = 0.f;
-        L.n = 0;
-        L.pp = philox_path(static_cast<uint32_t>(path), node, 0u, a.rk);
-      } else {
-        // sums of v = s - shift_f; with e = shift - shift_f the partial holds
-        // sum (v - e) = S1 - n e and sum (v - e)^2 = S2 - 2 e S1 + n e^2
-        const double n_d = static_cast<double>(cnt);
-        const double S1 = static_cast<double>(s1.hi) + static_cast<double>(s1.lo);
-        const double S2 = static_cast<double>(s2.hi) + static_cast<double>(s2.lo);
-        const double e = shift - static_cast<double>(shift_f);
-        a.partial[chunk] = ChunkPartial{n_d, S1 - n_d * e, S2 - 2.0 * e * S1 + n_d * e * e};
-        active = false;
-        need = true;
+    // ---- advance the lane's path by one unit
+    int code = kStepContinue;
+    bool done = false;
+    if (active) {
+      const BatchEnv env{a.probs[pi].mc, a.probs[pi].bridge};
+      code = path_unit_code<M, G, float, false, true>(env, k, pp, a.rk, a.max_steps, X, Y, Z, n,
+                                                     Xn, nullptr);
+      done = code != kStepContinue || n >= a.max_steps;
+      if (done) {
+        my_steps += static_cast<unsigned long long>(n);
+        if (code == kStepContinue) {
+          code = kStepCapped;
+          ++my_capped;
+        }
       }
     }
+
+    // ---- ended paths: parked, scored 32 at a time; the lane goes on with
+    // the next path of its chunk at once
+    const unsigned dm = __ballot_sync(kFull, done);
+    if (dm) {
+      const int nd = __popc(dm);
+      if (n_exit + nd > 32) {
+        batch_flush<M, G>(a, queue, n_exit);
+        n_exit = 0;
+      }
+      if (done) {
+        const int e = n_exit + __popc(dm & lt_mask);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          queue.x[d][e] = X[d];
+          queue.xn[d][e] = Xn[d];
+        }
+        queue.y[e] = Y;
+        queue.z[e] = Z;
+        queue.code[e] = code;
+        queue.node[e] = node;
+        queue.prob[e] = pi;
+        ++path;
+        if (path < path_end) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) X[d] = x0[d];
+          Y = 1.f;
+          Z = 0.f;
+          n = 0;
+          pp = philox_path(static_cast<uint32_t>(path), node, 0u, a.rk);
+        } else {
+          active = false;
+          need = true;
+        }
+      }
+      n_exit += nd;
+    }
   }
+  if (n_exit > 0) batch_flush<M, G>(a, queue, n_exit);
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) {
     my_steps += __shfl_xor_sync(kFull, my_steps, m);
@@ -272,7 +290,5 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
     if (my_bad) atomicAdd(&a.counters[2], my_bad);
   }
 }
-
-
 
 }  // namespace pdd

@@ -142,6 +142,28 @@ __device__ __forceinline__ void fix_commit(NodeFix *fix, bool has, uint64_t node
   }
 }
 
+// One lane adds `count` paths of node `node` that all score s (a node on the
+// boundary: tau = 0 for every path, so u = g there), or, for NaN s (a node
+// outside the closed domain), counts them as invalid.  Per-lane atomics:
+// such nodes are rare, and count * digit stays far below 2^63.
+template <typename R>
+__device__ __forceinline__ void fix_add_repeated(NodeFix *fix, uint64_t node, R s,
+                                                 long long count) {
+  unsigned long long *w = reinterpret_cast<unsigned long long *>(fix + node);
+  if (!(fabs(s) < R(0x1p30))) {
+    atomicAdd(w + kFixBad, static_cast<unsigned long long>(count));
+    return;
+  }
+  int32_t d[2 * kFixDigits];
+  fix_limbs(s, d, d + kFixDigits);
+  atomicAdd(w, static_cast<unsigned long long>(count));
+#pragma unroll
+  for (int k = 0; k < 2 * kFixDigits; ++k)
+    if (d[k] != 0)
+      atomicAdd(w + 1 + k, static_cast<unsigned long long>(count * static_cast<long long>(d[k])));
+  atomicAdd(w + kFixBoundary, static_cast<unsigned long long>(count));
+}
+
 // Double-double helpers for the finalisation (Dekker/Knuth error-free
 // transformations with FMA).
 struct DD {
@@ -185,31 +207,39 @@ __device__ __forceinline__ DD fix_total(const long long *l) {
   return t;
 }
 
+// Mean and the sum of squared deviations M2 of a node's scores from its
+// exact sums: mean = S1/n, M2 = S2 - S1^2/n in double-double (M2 = 0 when
+// every path started on the boundary, or with one path).  Both NaN when a
+// path was invalid or nothing was scored.
+__device__ __forceinline__ void fix_moments(const NodeFix &F, double *mean, double *m2) {
+  const double nn = static_cast<double>(F.n);
+  *mean = static_cast<double>(NAN);
+  *m2 = static_cast<double>(NAN);
+  if (F.bad != 0 || F.n <= 0) return;
+  const DD S1 = fix_total(F.s1), S2 = fix_total(F.s2);
+  const DD mu = dd_div(S1, nn);
+  *mean = mu.hi + mu.lo;
+  *m2 = 0.0;
+  if (F.boundary != F.n && F.n > 1) {
+    const DD q = dd_mul(S1, mu);
+    const DD d = dd_add(S2, DD{-q.hi, -q.lo});
+    *m2 = fmax(0.0, d.hi + d.lo);
+  }
+}
+
 // Mean, standard error of the mean, path count and flags per node from the
-// exact sums: mean = S1/n, M2 = S2 - S1^2/n in double-double, se =
-// sqrt(M2 / (n - 1) / n).  NaN when a path was invalid or nothing was scored.
+// exact sums: se = sqrt(M2 / (n - 1) / n), 0 when every path started on the
+// boundary (tau = 0, the estimate is exact) or with one path; NaN when a
+// path was invalid or nothing was scored.
 static __global__ void fix_finalize_kernel(const NodeFix *fix, int64_t n_nodes, double *mean,
                                            double *se, int64_t *npaths, int32_t *flags) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n_nodes) return;
   const NodeFix F = fix[i];
   const double nn = static_cast<double>(F.n);
-  double m = static_cast<double>(NAN), e = static_cast<double>(NAN);
-  if (F.bad == 0 && F.n > 0) {
-    const DD S1 = fix_total(F.s1), S2 = fix_total(F.s2);
-    const DD mu = dd_div(S1, nn);
-    m = mu.hi + mu.lo;
-    if (F.boundary == F.n) {
-      e = 0.0;  // every path started on the boundary: tau = 0, the estimate is exact
-    } else if (F.n > 1) {
-      const DD q = dd_mul(S1, mu);
-      const DD m2 = dd_add(S2, DD{-q.hi, -q.lo});
-      const double M2 = fmax(0.0, m2.hi + m2.lo);
-      e = sqrt(M2 / (nn - 1.0) / nn);
-    } else {
-      e = 0.0;
-    }
-  }
+  double m, M2;
+  fix_moments(F, &m, &M2);
+  const double e = F.n > 1 ? sqrt(M2 / (nn - 1.0) / nn) : M2;  // M2 is 0 or NaN for n <= 1
   mean[i] = m;
   se[i] = e;
   if (npaths) npaths[i] = F.n;

@@ -2,8 +2,9 @@
 persistent launch per pass, optionally captured in a CUDA graph).
 
 The batch runs node i's paths on the streams pdd_interface_solve uses, with
-the same step arithmetic, so a non-adaptive batch (n_min = n_max = N) must
-reproduce pdd_interface_solve's node means up to the order of the FP64 sums.
+the same step arithmetic and the same exact per-node sums, so a non-adaptive
+batch (n_min = n_max = N) must reproduce pdd_interface_solve's node means and
+standard errors bit for bit.
 The adaptive path counts must follow the pilot variances, and the L-shape
 (which only the batch and the plain solve support) is checked against the
 oracle path by path.
@@ -76,8 +77,9 @@ def test_fixed_count_batch_equals_interface_solve(api, use_graph):
     assert np.array_equal(m1, m2)
     assert np.all(r1["n"].cpu().numpy() == N)
     ref_m, ref_s = _reference_by_group(api, mix, seed, N)
-    np.testing.assert_allclose(m1, ref_m, rtol=1e-11, atol=1e-13)
-    np.testing.assert_allclose(r1["se"].cpu().numpy(), ref_s, rtol=1e-7)
+    # both add each node's scores to exact integer sums: the same bits
+    np.testing.assert_array_equal(m1, ref_m)
+    np.testing.assert_array_equal(r1["se"].cpu().numpy(), ref_s)
 
 
 def test_adaptive_counts_follow_pilot_variance(api):
