@@ -218,18 +218,22 @@ PDD_API pdd_status pdd_set_params(pdd_ctx *ctx, const double *params,
  * Nodes may belong to different problems (up to 4 pdd_problem entries:
  * LAPLACE_EXPCOS on the unit square or the L-shape, ELLIPTIC_MANUFACTURED on
  * the unit cube, POISSON_FOURIER on the unit square) and carry their own
- * time step.  Per node i (paths are FP32, sums FP64):
+ * time step.  Per node i (paths are FP32; every score goes into the node's
+ * exact integer sums, as in pdd_interface_solve):
  *   1. a pilot of n_pilot paths gives the sample variance s_i^2;
  *   2. N_i = clamp(ceil(s_i^2 / target_se^2), max(n_min, n_pilot), n_max);
  *   3. paths n_pilot .. N_i - 1 are added and the estimate uses all N_i.
  * Node i's path p uses the same Philox stream as pdd_interface_solve
- * (counter = (block, p, i, 0)).  The work list of the second pass is built
+ * (counter = (block, p, i, 0)), and the sums are the same, so with
+ * n_min = n_max = N the results equal pdd_interface_solve's bit for bit.
+ * The work list of the second pass is built
  * on the device, and one persistent launch consumes it (lanes take chunks of
  * `chunk` consecutive paths of one node), so the call has no host round trip.
  * With use_graph != 0 the whole sequence is captured once into a CUDA graph
  * (rebuilt when any argument or the scratch changes) and replayed; this
  * needs a non-default stream.  Writes d_mean[n], d_se[n] and, if non-NULL,
- * d_npaths[n] (= N_i).  diag (optional) reports total steps / capped paths
+ * d_npaths[n] (= N_i; 0 for a node outside the closed domain or of an
+ * unknown problem, whose mean and se are NaN).  diag (optional) reports total steps / capped paths
  * and synchronises; its d_node_flags receives PDD_NODE_SE_UNMET for the nodes
  * whose final standard error is above target_se and PDD_NODE_OUTSIDE for
  * the nodes without an estimate.                                           */
