@@ -67,6 +67,7 @@ struct GridArgs {
   float beta_f, inv_beta;
   int32_t psi_kind;
   float psi_prm;
+  float psi_l2;                   // psi_prm log2(e)
   int32_t K, m;
   uint32_t dt_ticks;
   int32_t bridge;
@@ -77,14 +78,16 @@ struct GridArgs {
   int32_t max_depth;
 };
 
+// psi at a particle's position (the hardware exp2 and reciprocal, a few ulp,
+// as in the free-space trees).
 template <int D>
 __device__ __forceinline__ float grid_psi(const GridArgs &a, const float *x) {
   switch (a.psi_kind) {
     case 0: return a.psi_prm;
-    case 1: return __fdividef(1.0f, 1.0f + expf(-a.psi_prm * x[0]));
+    case 1: return rcp_approx(1.0f + ex2_approx(-a.psi_l2 * x[0]));
     case 2: {
-      const float e = 1.0f + expf(a.psi_prm * x[0]);
-      return 1.0f - __fdividef(1.0f, e * e);
+      const float e = 1.0f + ex2_approx(a.psi_l2 * x[0]);
+      return 1.0f - rcp_approx(e * e);
     }
     default: return sinpif(x[0]) * (D > 1 ? sinpif(x[1]) : 1.0f);
   }
@@ -212,28 +215,31 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
     }
     if (!active) continue;
 
-    if (start) {
-      // lifetime of the current particle (block 0 of its stream)
-      const uint4 w = philox10_path(id << 20, pp, a.rk);  // = Philox((id << 20, tree, node, 3))
-      const float ltk = 0.5f * neg2log(unif_f(w.x)) * a.inv_beta * a.tps;
+    // one Philox block per trip: on the trip that starts a particle, block 0
+    // of its stream (lifetime and offspring count), else the block of its
+    // next step (Philox((id << 20 | j, tree, node, 3)))
+    const bool starting = start;
+    const uint4 v = philox10_path(starting ? id << 20 : (id << 20) | j, pp, a.rk);
+    if (starting) {
+      const float ltk = 0.5f * neg2log(unif_f(v.x)) * a.inv_beta * a.tps;
       const uint64_t e = ltk >= 4294967040.0f ? 4294967295ull : static_cast<uint64_t>(__float2uint_rz(ltk));
       const uint64_t te = static_cast<uint64_t>(t) + e;
       tend = te < Tm ? static_cast<uint32_t>(te) : Tm;
-      u_off = w.w;
+      u_off = v.w;
       // ti (first grid time after t) is carried: a child starts where its
       // parent's walk ended, after the parent scored any grid time equal to t
       j = 1;
       start = false;
     }
 
-    // one step of the current particle (none when its lifetime is under a tick)
+    // one step of the current particle (none on its starting trip, and none
+    // at all when its lifetime is under a tick)
     bool pdone = false;
-    if (t < tend) {
+    if (!starting && t < tend) {
       uint32_t nxt = tend;
       if (ti < a.m && a.T[ti] < nxt) nxt = a.T[ti];
       if (kBounded && nxt - t > a.dt_ticks) nxt = t + a.dt_ticks;
       const float h = static_cast<float>(nxt - t) * a.inv_tps;
-      const uint4 v = philox10_path((id << 20) | j, pp, a.rk);
       ++j;
       ++nsteps;
       float z0, z1;
@@ -390,6 +396,7 @@ static pdd_status run_grid(pdd_ctx *ctx, const double *d_nodes, int64_t n, const
   a.inv_tps = static_cast<float>(1.0 / tps);
   a.psi_kind = static_cast<int32_t>(prm[1]);
   a.psi_prm = static_cast<float>(prm[2]);
+  a.psi_l2 = static_cast<float>(prm[2] * 1.4426950408889634);
   a.K = static_cast<int32_t>(prm[3]);
   a.m = m;
   a.dt_ticks = dt_ticks;
@@ -425,12 +432,12 @@ static pdd_status run_grid(pdd_ctx *ctx, const double *d_nodes, int64_t n, const
     PDD_CUDA_TRY(ctx, cudaGetLastError());
     if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
     const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
-    for (int k = 0; k < m; ++k) {
-      reduce_wave_kernel<float, true><<<static_cast<unsigned>(node_hi - node_lo + 1), kReduceBlock,
-                                         0, ctx->stream>>>(score + k * wave, b0, b1, N, node_lo,
-                                                           acc + static_cast<size_t>(k) * n);
-      PDD_CUDA_TRY(ctx, cudaGetLastError());
-    }
+    // the m time planes in one launch (blockIdx.y = plane)
+    reduce_wave_kernel<float, true>
+        <<<dim3(static_cast<unsigned>(node_hi - node_lo + 1), static_cast<unsigned>(m)),
+           kReduceBlock, 0, ctx->stream>>>(score, b0, b1, N, node_lo, acc, wave,
+                                           static_cast<uint64_t>(n));
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
     if (diag && diag->d_path_score) {
       const uint64_t cnt = b1 - b0;
       const unsigned g = static_cast<unsigned>(std::min<uint64_t>((cnt * m + 255) / 256, 8192));

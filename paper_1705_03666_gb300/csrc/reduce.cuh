@@ -99,7 +99,12 @@ struct ThreadSums<double, kSkipNaN> {
 template <typename R, bool kSkipNaN = false>
 __global__ void __launch_bounds__(kReduceBlock)
 reduce_wave_kernel(const R *__restrict__ score, uint64_t begin, uint64_t end,
-                   uint64_t n_paths, uint64_t node_lo, NodeAcc *acc) {
+                   uint64_t n_paths, uint64_t node_lo, NodeAcc *acc,
+                   uint64_t score_plane = 0, uint64_t acc_plane = 0) {
+  // blockIdx.y selects a plane (score + y score_plane, acc + y acc_plane):
+  // several score planes of one wave reduced by one launch
+  score += blockIdx.y * score_plane;
+  acc += blockIdx.y * acc_plane;
   const uint64_t node = node_lo + blockIdx.x;
   const uint64_t lo = max(begin, node * n_paths);
   const uint64_t hi = min(end, (node + 1) * n_paths);
