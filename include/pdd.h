@@ -510,6 +510,24 @@ PDD_API pdd_status pdd_subdomain_solve(pdd_ctx *ctx, const pdd_subdomain *sd,
                                        double *d_u, int64_t *iters,
                                        double *resid);
 
+/* Several three-dimensional subdomains solved together (the subdomains of
+ * stage two are independent problems, Sec. 2): n_boxes entries of sds, each
+ * a 3-D box as for pdd_subdomain_solve (its own lo, hi and interface mask),
+ * all with the same grid size n, method (DST or JACOBI), max_iter and tol.
+ * d_face holds each box's interface data as pdd_subdomain_solve takes them,
+ * box after box (m values in all); d_u is [n_boxes][n[2]][n[1]][n[0]] FP64,
+ * written in full.  Each box runs its own stopping rule; *iters and *resid
+ * (host) get the largest count and residual measure over the boxes, and
+ * iters_each / resid_each (host arrays of n_boxes, may be NULL) each box's
+ * own.  A box's result is bit-identical to its pdd_subdomain_solve.  At most
+ * 65535 boxes; PDD_EINVAL for mixed sizes or rules, PDD_ETIMEOUT when a box
+ * ran out of max_iter (d_u then holds its last iterate).  Synchronises. */
+PDD_API pdd_status pdd_subdomain_solve_batch(pdd_ctx *ctx, const pdd_subdomain *sds,
+                                             int32_t n_boxes, const double *d_face,
+                                             int64_t m, double *d_u, int64_t *iters,
+                                             double *resid, int64_t *iters_each,
+                                             double *resid_each);
+
 /* The plain GPU form of pdd_interface_solve, kept as a comparison baseline:
  * one kernel launch per node, one thread per path, block sums added to FP64
  * node accumulators with atomics (so the last bits depend on scheduling), no

@@ -111,6 +111,11 @@ _SIGS = {
     "pdd_subdomain_solve": (ctypes.c_int, [_VP, ctypes.POINTER(Subdomain), _VP, _VP, _I64, _VP,
                                            ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_double)]),
+    "pdd_subdomain_solve_batch": (ctypes.c_int, [_VP, ctypes.POINTER(Subdomain), ctypes.c_int32,
+                                                 _VP, _I64, _VP, ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_double)]),
     "pdd_interface_grad": (ctypes.c_int, [_VP, _VP, _I64, ctypes.POINTER(MCParams), _VP, _VP,
                                           _VP, _VP, _VP, ctypes.POINTER(Diag)]),
     "pdd_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),

@@ -188,6 +188,17 @@ pdd_status pdd_subdomain_solve(pdd_ctx *ctx, const pdd_subdomain *sd, const doub
   return pdd::subdomain_solve_impl(ctx, sd, d_iface_s, d_iface_vals, m, d_u, iters, resid);
 }
 
+pdd_status pdd_subdomain_solve_batch(pdd_ctx *ctx, const pdd_subdomain *sds, int32_t n_boxes,
+                                     const double *d_face, int64_t m, double *d_u,
+                                     int64_t *iters, double *resid, int64_t *iters_each,
+                                     double *resid_each) {
+  if (!ctx) return PDD_EINVAL;
+  ctx->last_error.clear();
+  const TraceRange trace(__func__);
+  return pdd::subdomain_solve3d_batch_impl(ctx, sds, n_boxes, d_face, m, d_u, iters, resid,
+                                           iters_each, resid_each);
+}
+
 pdd_status pdd_interface_grad(pdd_ctx *ctx, const double *d_nodes, int64_t n,
                               const pdd_mc_params *mc, const double *d_grad_out, double *d_jac,
                               double *d_jac_se, double *d_dtheta, double *d_dphi,

@@ -211,6 +211,10 @@ pdd_status interface_interp_impl(pdd_ctx *ctx, int32_t n_planes, const int32_t *
                                  double *d_out);
 pdd_status subdomain_solve3d_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const double *d_face,
                                   int64_t m, double *d_u, int64_t *iters, double *resid);
+pdd_status subdomain_solve3d_batch_impl(pdd_ctx *ctx, const pdd_subdomain *sds, int32_t nb,
+                                        const double *d_face, int64_t m, double *d_u,
+                                        int64_t *iters, double *resid, int64_t *iters_each,
+                                        double *resid_each);
 pdd_status philox_stream_impl(pdd_ctx *ctx, uint64_t seed, uint32_t j0, uint32_t c1,
                               uint32_t c2, uint32_t c3, int64_t n_blocks, uint32_t *d_out);
 

@@ -302,7 +302,12 @@ pdd_status interface_interp_impl(pdd_ctx *ctx, int32_t n_planes, const int32_t *
 }
 
 // ---------------------------------------------------------------------------
-// Subdomain solve on a 3-D box
+// Subdomain solves on 3-D boxes.  The subdomains of stage two are independent
+// problems (Sec. 2), so one call solves a batch of boxes of the same grid
+// size together: every kernel below takes the box from blockIdx.y, and a box
+// whose correction loop has stopped is skipped (live[b] == 0).  A batch of
+// one box is the single solve; each box's arithmetic does not depend on the
+// others, so a box gets the same bits alone or in a batch.
 // ---------------------------------------------------------------------------
 constexpr int kBox3MaxInterior = 126;  // interior points per axis (sine matrix in shared memory)
 constexpr int kBox3Block = 256;
@@ -318,15 +323,25 @@ struct Box3 {
 __device__ __forceinline__ int64_t box3_index(const Box3 &B, int i, int j, int k) {
   return (static_cast<int64_t>(k) * B.n[1] + j) * B.n[0] + i;
 }
+__device__ __forceinline__ int64_t box3_total(const Box3 &B) {
+  return static_cast<int64_t>(B.n[0]) * B.n[1] * B.n[2];
+}
+__device__ __forceinline__ int64_t box3_np(const Box3 &B) {
+  return static_cast<int64_t>(B.P[0]) * B.P[1] * B.P[2];
+}
 
 // Dirichlet data and coefficients: boundary layer of u from the faces (a
 // point on a face without interface data -- the physical boundary -- takes g;
 // otherwise the interface face of lowest index), interior u = 0, and per
 // interior point b, c and f of the family.
 template <class Model>
-__global__ void box3_setup_kernel(Box3 B, ModelConst mc, const double *face, double *u,
+__global__ void box3_setup_kernel(const Box3 *boxes, ModelConst mc, const double *face, double *u,
                                   double *coef) {
-  const int64_t total = static_cast<int64_t>(B.n[0]) * B.n[1] * B.n[2];
+  const Box3 B = boxes[blockIdx.y];
+  const int64_t total = box3_total(B);
+  const int64_t np = box3_np(B);
+  u += blockIdx.y * total;
+  coef += blockIdx.y * 4 * np;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int i = static_cast<int>(e % B.n[0]);
@@ -343,7 +358,6 @@ __global__ void box3_setup_kernel(Box3 B, ModelConst mc, const double *face, dou
       double b[3], f = 0.0;
       Model::template coeffs<double>(mc, x, b, f);
       const int64_t q = (static_cast<int64_t>(k - 1) * B.P[1] + (j - 1)) * B.P[0] + (i - 1);
-      const int64_t np = static_cast<int64_t>(B.P[0]) * B.P[1] * B.P[2];
       coef[q] = b[0];
       coef[np + q] = b[1];
       coef[2 * np + q] = b[2];
@@ -375,11 +389,17 @@ __global__ void box3_setup_kernel(Box3 B, ModelConst mc, const double *face, dou
   }
 }
 
-// r = -f - A u at the interior points (FP64), and the block's sum of r^2.
+// r = -f - A u at the interior points (FP64), and the block's sum of r^2
+// (part[box][block]).
 __global__ void __launch_bounds__(kBox3Block)
-box3_residual_kernel(Box3 B, double s2, double c, const double *u, const double *coef, double *r,
-                     double *part) {
-  const int64_t np = static_cast<int64_t>(B.P[0]) * B.P[1] * B.P[2];
+box3_residual_kernel(const Box3 *boxes, const int32_t *live, double s2, double c, const double *u,
+                     const double *coef, double *r, double *part) {
+  if (!live[blockIdx.y]) return;
+  const Box3 B = boxes[blockIdx.y];
+  const int64_t np = box3_np(B);
+  u += blockIdx.y * box3_total(B);
+  coef += blockIdx.y * 4 * np;
+  r += blockIdx.y * np;
   const double w0 = 0.5 * s2 / (B.h[0] * B.h[0]), w1 = 0.5 * s2 / (B.h[1] * B.h[1]),
                w2 = 0.5 * s2 / (B.h[2] * B.h[2]);
   const double d0 = 0.5 / B.h[0], d1 = 0.5 / B.h[1], d2 = 0.5 / B.h[2];
@@ -409,15 +429,23 @@ box3_residual_kernel(Box3 B, double s2, double c, const double *u, const double 
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < kBox3Block / 32; ++w) t += sh[w];
-    part[blockIdx.x] = t;
+    part[static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x] = t;
   }
 }
 
-// Sum of the block partials in block order (one thread): deterministic.
-__global__ void box3_norm_kernel(const double *part, int nblk, double *out) {
+// Per box: the sum of its block partials in block order (deterministic), as
+// a 2-norm (residual) or the largest (Jacobi change); one thread per box.
+template <bool kMax>
+__global__ void box3_combine_kernel(const double *part, int nblk, int nb, const int32_t *live,
+                                    double *out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb || !live[b]) return;
   double t = 0.0;
-  for (int b = 0; b < nblk; ++b) t += part[b];
-  *out = sqrt(t);
+  for (int k = 0; k < nblk; ++k) {
+    const double v = part[static_cast<int64_t>(b) * nblk + k];
+    t = kMax ? fmax(t, v) : t + v;
+  }
+  out[b] = kMax ? t : sqrt(t);
 }
 
 // The sine matrices S_a[k][j] = sin(pi (k+1)(j+1) / (P_a + 1)), binary32,
@@ -432,43 +460,50 @@ __global__ void box3_sine_kernel(int P, float *S) {
   }
 }
 
-// out = S applied along axis AX of the P0 x P1 x P2 array in (x fastest):
-// out[.., k, ..] = sum_j S[k][j] in[.., j, ..].  The matrix is staged in
-// shared memory; threads of a warp take consecutive outputs, so along axes 1
-// and 2 their reads are coalesced and along axis 0 they read the same line.
+// out = S applied along axis AX of the P0 x P1 x P2 array of box blockIdx.y
+// (x fastest): out[.., k, ..] = sum_j S[k][j] in[.., j, ..].  The matrix is
+// staged in shared memory; threads of a warp take consecutive outputs, so
+// along axes 1 and 2 their reads are coalesced and along axis 0 they read the
+// same line.
 template <int AX>
 __global__ void __launch_bounds__(kBox3Block)
-box3_dst_kernel(int P0, int P1, int P2, const float *__restrict__ S, const float *__restrict__ in,
-                float *__restrict__ out, const double *__restrict__ rnorm,
-                const double *__restrict__ in64) {
+box3_dst_kernel(int P0, int P1, int P2, const int32_t *live, const float *__restrict__ S,
+                const float *__restrict__ in, float *__restrict__ out,
+                const double *__restrict__ rnorm, const double *__restrict__ in64) {
+  if (!live[blockIdx.y]) return;
   extern __shared__ float Ss[];
   const int P = AX == 0 ? P0 : (AX == 1 ? P1 : P2);
   for (int e = threadIdx.x; e < P * P; e += blockDim.x) Ss[e] = S[e];
   __syncthreads();
   const int64_t np = static_cast<int64_t>(P0) * P1 * P2;
+  const int64_t off = blockIdx.y * np;
   const int64_t stride = AX == 0 ? 1 : (AX == 1 ? P0 : static_cast<int64_t>(P0) * P1);
   for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < np;
        q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int kk = static_cast<int>((q / stride) % P);
-    const int64_t base = q - kk * stride;
+    const int64_t base = off + q - kk * stride;
     const float *row = Ss + kk * P;
     float acc = 0.f;
     if (in64) {  // first pass: the FP64 residual scaled by 1 / |r|_2, then rounded
-      const double inv = 1.0 / *rnorm;
+      const double inv = 1.0 / rnorm[blockIdx.y];
       for (int j = 0; j < P; ++j)
         acc = fmaf(row[j], static_cast<float>(in64[base + j * stride] * inv), acc);
     } else {
       for (int j = 0; j < P; ++j) acc = fmaf(row[j], in[base + j * stride], acc);
     }
-    out[q] = acc;
+    out[off + q] = acc;
   }
 }
 
 // Division by the eigenvalues of (1/2) sigma^2 Lap_h + c in the sine basis,
 // lambda = sum_a (sigma^2 / h_a^2) (cos(pi k_a / (P_a + 1)) - 1) + c, and the
 // normalisation of the two transforms, 8 / prod_a (P_a + 1).
-__global__ void box3_eig_kernel(Box3 B, double s2, double c, float *v) {
-  const int64_t np = static_cast<int64_t>(B.P[0]) * B.P[1] * B.P[2];
+__global__ void box3_eig_kernel(const Box3 *boxes, const int32_t *live, double s2, double c,
+                                float *v) {
+  if (!live[blockIdx.y]) return;
+  const Box3 B = boxes[blockIdx.y];
+  const int64_t np = box3_np(B);
+  v += blockIdx.y * np;
   const double norm = 8.0 / ((B.P[0] + 1.0) * (B.P[1] + 1.0) * (B.P[2] + 1.0));
   for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < np;
        q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -483,9 +518,14 @@ __global__ void box3_eig_kernel(Box3 B, double s2, double c, float *v) {
 }
 
 // u += (correction * |r|) at the interior points (undoing the scaling).
-__global__ void box3_update_kernel(Box3 B, const float *v, const double *rnorm, double *u) {
-  const int64_t np = static_cast<int64_t>(B.P[0]) * B.P[1] * B.P[2];
-  const double sc = *rnorm;
+__global__ void box3_update_kernel(const Box3 *boxes, const int32_t *live, const float *v,
+                                   const double *rnorm, double *u) {
+  if (!live[blockIdx.y]) return;
+  const Box3 B = boxes[blockIdx.y];
+  const int64_t np = box3_np(B);
+  v += blockIdx.y * np;
+  u += blockIdx.y * box3_total(B);
+  const double sc = rnorm[blockIdx.y];
   for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < np;
        q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int i = static_cast<int>(q % B.P[0]) + 1;
@@ -496,11 +536,16 @@ __global__ void box3_update_kernel(Box3 B, const float *v, const double *rnorm, 
 }
 
 // One Jacobi sweep (the plain reference method): u' = (-f - offdiag(A) u) / diag,
-// the block's largest change in part.
+// the block's largest change in part[box][block].
 __global__ void __launch_bounds__(kBox3Block)
-box3_jacobi_kernel(Box3 B, double s2, double c, const double *u, double *un, const double *coef,
-                   double *part) {
-  const int64_t np = static_cast<int64_t>(B.P[0]) * B.P[1] * B.P[2];
+box3_jacobi_kernel(const Box3 *boxes, const int32_t *live, double s2, double c, const double *u,
+                   double *un, const double *coef, double *part) {
+  if (!live[blockIdx.y]) return;
+  const Box3 B = boxes[blockIdx.y];
+  const int64_t np = box3_np(B);
+  u += blockIdx.y * box3_total(B);
+  un += blockIdx.y * box3_total(B);
+  coef += blockIdx.y * 4 * np;
   const double w0 = 0.5 * s2 / (B.h[0] * B.h[0]), w1 = 0.5 * s2 / (B.h[1] * B.h[1]),
                w2 = 0.5 * s2 / (B.h[2] * B.h[2]);
   const double d0 = 0.5 / B.h[0], d1 = 0.5 / B.h[1], d2 = 0.5 / B.h[2];
@@ -529,68 +574,93 @@ box3_jacobi_kernel(Box3 B, double s2, double c, const double *u, double *un, con
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < kBox3Block / 32; ++w) t = fmax(t, sh[w]);
-    part[blockIdx.x] = t;
+    part[static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x] = t;
   }
 }
 
-__global__ void box3_max_kernel(const double *part, int nblk, double *out) {
-  double t = 0.0;
-  for (int b = 0; b < nblk; ++b) t = fmax(t, part[b]);
-  *out = t;
-}
-
-pdd_status subdomain_solve3d_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const double *d_face,
-                                  int64_t m, double *d_u, int64_t *iters, double *resid) {
+// A batch of nb boxes with the same grid size and method: the faces of box b
+// follow those of box b - 1 in d_face, and d_u is [nb][n2][n1][n0].  *iters
+// and *resid (if non-null) get the largest count and relative residual over
+// the boxes; iters_each / resid_each (host, nb entries, may be null) get each
+// box's own.
+pdd_status subdomain_solve3d_batch_impl(pdd_ctx *ctx, const pdd_subdomain *sds, int32_t nb,
+                                        const double *d_face, int64_t m, double *d_u,
+                                        int64_t *iters, double *resid, int64_t *iters_each,
+                                        double *resid_each) {
+  if (!sds || nb < 1 || nb > 65535) return fail(ctx, PDD_EINVAL, "batch of 1 .. 65535 boxes");
   if (ctx->prob.kind != PDD_PROB_ELLIPTIC_MANUFACTURED || ctx->prob.dim != 3)
     return fail(ctx, PDD_EINVAL, "the 3-D subdomain solver covers the 3-D family");
   if (reflect_mask(ctx) != 0)
     return fail(ctx, PDD_EINVAL, "the 3-D subdomain solver takes Dirichlet data only");
-  Box3 B{};
-  for (int a = 0; a < 3; ++a) {
-    if (sd->n[a] < 3 || sd->n[a] - 2 > kBox3MaxInterior)
-      return fail(ctx, PDD_EINVAL, "3-D grids take 3 .. %d points per axis", kBox3MaxInterior + 2);
-    if (!(sd->hi[a] > sd->lo[a]) || sd->lo[a] < 0.0 || sd->hi[a] > 1.0)
-      return fail(ctx, PDD_EINVAL, "box must be non-empty and inside the unit cube");
-    B.lo[a] = sd->lo[a];
-    B.n[a] = sd->n[a];
-    B.P[a] = sd->n[a] - 2;
-    B.h[a] = (sd->hi[a] - sd->lo[a]) / (sd->n[a] - 1);
-  }
-  if (sd->iface_axis < 0 || sd->iface_axis > 63 || sd->iface_side != 0)
-    return fail(ctx, PDD_EINVAL, "3-D: iface_axis is a mask of interface faces (0..63), "
-                                 "iface_side must be 0");
-  if (sd->method != PDD_STENCIL_DST && sd->method != PDD_STENCIL_JACOBI)
-    return fail(ctx, PDD_EINVAL, "3-D methods: PDD_STENCIL_DST or PDD_STENCIL_JACOBI");
-  if (sd->max_iter < 1 || !(sd->tol >= 0.0)) return fail(ctx, PDD_EINVAL, "bad stopping rule");
-  B.mask = sd->iface_axis;
+  const pdd_subdomain &S0 = sds[0];
+  std::vector<Box3> boxes(static_cast<size_t>(nb));
   int64_t off = 0;
-  for (int fc = 0; fc < 6; ++fc) {
-    B.face_off[fc] = off;
-    if ((B.mask >> fc) & 1) {
-      const int a = fc >> 1;
-      off += static_cast<int64_t>(B.n[a == 0 ? 1 : 0]) * B.n[a == 2 ? 1 : 2];
+  for (int32_t b = 0; b < nb; ++b) {
+    const pdd_subdomain *sd = sds + b;
+    Box3 &B = boxes[static_cast<size_t>(b)];
+    for (int a = 0; a < 3; ++a) {
+      if (sd->n[a] < 3 || sd->n[a] - 2 > kBox3MaxInterior)
+        return fail(ctx, PDD_EINVAL, "3-D grids take 3 .. %d points per axis", kBox3MaxInterior + 2);
+      if (sd->n[a] != S0.n[a])
+        return fail(ctx, PDD_EINVAL, "the boxes of a batch share one grid size");
+      if (!(sd->hi[a] > sd->lo[a]) || sd->lo[a] < 0.0 || sd->hi[a] > 1.0)
+        return fail(ctx, PDD_EINVAL, "box must be non-empty and inside the unit cube");
+      B.lo[a] = sd->lo[a];
+      B.n[a] = sd->n[a];
+      B.P[a] = sd->n[a] - 2;
+      B.h[a] = (sd->hi[a] - sd->lo[a]) / (sd->n[a] - 1);
+    }
+    if (sd->iface_axis < 0 || sd->iface_axis > 63 || sd->iface_side != 0)
+      return fail(ctx, PDD_EINVAL, "3-D: iface_axis is a mask of interface faces (0..63), "
+                                   "iface_side must be 0");
+    if (sd->method != PDD_STENCIL_DST && sd->method != PDD_STENCIL_JACOBI)
+      return fail(ctx, PDD_EINVAL, "3-D methods: PDD_STENCIL_DST or PDD_STENCIL_JACOBI");
+    if (sd->method != S0.method || sd->max_iter != S0.max_iter || !(sd->tol == S0.tol))
+      return fail(ctx, PDD_EINVAL, "the boxes of a batch share one method and stopping rule");
+    if (sd->max_iter < 1 || !(sd->tol >= 0.0)) return fail(ctx, PDD_EINVAL, "bad stopping rule");
+    B.mask = sd->iface_axis;
+    for (int fc = 0; fc < 6; ++fc) {
+      B.face_off[fc] = off;
+      if ((B.mask >> fc) & 1) {
+        const int a = fc >> 1;
+        off += static_cast<int64_t>(B.n[a == 0 ? 1 : 0]) * B.n[a == 2 ? 1 : 2];
+      }
     }
   }
   if (m != off) return fail(ctx, PDD_EINVAL, "expected %lld face values, got %lld",
                             static_cast<long long>(off), static_cast<long long>(m));
   if (off > 0 && !d_face) return fail(ctx, PDD_EINVAL, "null face data");
+  if (!d_u) return fail(ctx, PDD_EINVAL, "null output");
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
 
-  const int64_t total = static_cast<int64_t>(B.n[0]) * B.n[1] * B.n[2];
-  const int64_t np = static_cast<int64_t>(B.P[0]) * B.P[1] * B.P[2];
+  const Box3 &B0 = boxes[0];
+  const bool jacobi = S0.method == PDD_STENCIL_JACOBI;
+  const int64_t total = static_cast<int64_t>(B0.n[0]) * B0.n[1] * B0.n[2];
+  const int64_t np = static_cast<int64_t>(B0.P[0]) * B0.P[1] * B0.P[2];
+  const size_t NB = static_cast<size_t>(nb);
   const int nblk = static_cast<int>(std::min<int64_t>((np + kBox3Block - 1) / kBox3Block, 1024));
-  const size_t off_coef = 256;
-  const size_t off_r = align_up(off_coef + 4 * np * sizeof(double), 256);
-  const size_t off_part = align_up(off_r + np * sizeof(double), 256);
-  const size_t off_un = align_up(off_part + 1024 * sizeof(double), 256);
-  const size_t off_v0 = align_up(off_un + (sd->method == PDD_STENCIL_JACOBI ? total : 0) * sizeof(double), 256);
-  const size_t off_v1 = align_up(off_v0 + np * sizeof(float), 256);
-  const size_t off_S = align_up(off_v1 + np * sizeof(float), 256);
-  const size_t bytes = align_up(off_S + 3 * kBox3MaxInterior * kBox3MaxInterior * sizeof(float), 256);
-  pdd_status st = ensure_scratch(ctx, bytes);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  const size_t off_rn = take(NB * sizeof(double));
+  const size_t off_live = take(NB * sizeof(int32_t));
+  const size_t off_box = take(NB * sizeof(Box3));
+  const size_t off_coef = take(NB * 4 * np * sizeof(double));
+  const size_t off_r = take(NB * np * sizeof(double));
+  const size_t off_part = take(NB * nblk * sizeof(double));
+  const size_t off_un = take(jacobi ? NB * total * sizeof(double) : 0);
+  const size_t off_v0 = take(NB * np * sizeof(float));
+  const size_t off_v1 = take(NB * np * sizeof(float));
+  const size_t off_S = take(3 * kBox3MaxInterior * kBox3MaxInterior * sizeof(float));
+  pdd_status st = ensure_scratch(ctx, o);
   if (st != PDD_OK) return st;
   char *base = static_cast<char *>(ctx->scratch);
-  double *rn = reinterpret_cast<double *>(base);        // |r|_2 (Jacobi: largest change)
+  double *rn = reinterpret_cast<double *>(base + off_rn);  // per box: |r|_2 (Jacobi: largest change)
+  int32_t *live = reinterpret_cast<int32_t *>(base + off_live);
+  Box3 *d_boxes = reinterpret_cast<Box3 *>(base + off_box);
   double *coef = reinterpret_cast<double *>(base + off_coef);
   double *r = reinterpret_cast<double *>(base + off_r);
   double *part = reinterpret_cast<double *>(base + off_part);
@@ -600,78 +670,141 @@ pdd_status subdomain_solve3d_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const d
   for (int a = 0; a < 3; ++a)
     S[a] = reinterpret_cast<float *>(base + off_S) + a * kBox3MaxInterior * kBox3MaxInterior;
 
+  // host state of the correction loop (copied to and from the device
+  // synchronously, so these buffers outlive every copy)
+  std::vector<int32_t> h_live(NB, 1);
+  std::vector<double> h_rn(NB, 0.0), h_r0(NB, -1.0), h_res(NB, 0.0);
+  std::vector<int64_t> h_it(NB, 0);
+  PDD_CUDA_TRY(ctx, cudaMemcpyAsync(d_boxes, boxes.data(), NB * sizeof(Box3),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+  PDD_CUDA_TRY(ctx, cudaMemcpyAsync(live, h_live.data(), NB * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, ctx->stream));
   const unsigned gset = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 4096));
-  box3_setup_kernel<EllipticManufactured><<<gset, 256, 0, ctx->stream>>>(B, ctx->mc, d_face, d_u,
-                                                                         coef);
+  box3_setup_kernel<EllipticManufactured><<<dim3(gset, nb), 256, 0, ctx->stream>>>(
+      d_boxes, ctx->mc, d_face, d_u, coef);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
   const double s2 = ctx->prob.sigma * ctx->prob.sigma;
   const double c = constant_kill(ctx->prob.kind);
+  const unsigned gcomb = static_cast<unsigned>((nb + 127) / 128);
   const auto ev = prof_slot(ctx);
   if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
-  int64_t it = 0;
-  double res = 0.0;
-  if (sd->method == PDD_STENCIL_JACOBI) {
-    double *cur = d_u, *nxt = un;
-    PDD_CUDA_TRY(ctx, cudaMemcpyAsync(un, d_u, total * sizeof(double), cudaMemcpyDeviceToDevice,
+  // read the per-box measures, then decide per box whether it goes on
+  auto read_measures = [&]() -> pdd_status {
+    PDD_CUDA_TRY(ctx, cudaMemcpyAsync(h_rn.data(), rn, NB * sizeof(double), cudaMemcpyDeviceToHost,
                                       ctx->stream));
-    for (it = 1; it <= sd->max_iter; ++it) {
-      box3_jacobi_kernel<<<nblk, kBox3Block, 0, ctx->stream>>>(B, s2, c, cur, nxt, coef, part);
-      box3_max_kernel<<<1, 1, 0, ctx->stream>>>(part, nblk, rn);
+    PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return PDD_OK;
+  };
+  auto push_live = [&]() -> pdd_status {
+    PDD_CUDA_TRY(ctx, cudaMemcpyAsync(live, h_live.data(), NB * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    return PDD_OK;
+  };
+  if (jacobi) {
+    // each box sweeps between its own two buffers; a box that stops keeps its
+    // latest iterate where its own step count left it
+    PDD_CUDA_TRY(ctx, cudaMemcpyAsync(un, d_u, NB * total * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    const unsigned gj = static_cast<unsigned>(nblk);
+    int n_live = nb;
+    for (int64_t it = 1; it <= S0.max_iter && n_live > 0; ++it) {
+      const bool odd = (it & 1) != 0;
+      box3_jacobi_kernel<<<dim3(gj, nb), kBox3Block, 0, ctx->stream>>>(
+          d_boxes, live, s2, c, odd ? d_u : un, odd ? un : d_u, coef, part);
       PDD_CUDA_TRY(ctx, cudaGetLastError());
-      std::swap(cur, nxt);
-      if (it % 16 == 0 || it == sd->max_iter) {
-        PDD_CUDA_TRY(ctx, cudaMemcpyAsync(&res, rn, sizeof res, cudaMemcpyDeviceToHost, ctx->stream));
-        PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        if (res < sd->tol) break;
+      for (size_t b = 0; b < NB; ++b)
+        if (h_live[b]) h_it[b] = it;
+      if (it % 16 == 0 || it == S0.max_iter) {
+        box3_combine_kernel<true><<<gcomb, 128, 0, ctx->stream>>>(part, nblk, nb, live, rn);
+        PDD_CUDA_TRY(ctx, cudaGetLastError());
+        st = read_measures();
+        if (st != PDD_OK) return st;
+        for (size_t b = 0; b < NB; ++b) {
+          if (!h_live[b]) continue;
+          h_res[b] = h_rn[b];
+          if (h_rn[b] < S0.tol || it == S0.max_iter) {
+            h_live[b] = 0;
+            --n_live;
+          }
+        }
+        st = push_live();
+        if (st != PDD_OK) return st;
       }
     }
-    if (it > sd->max_iter) it = sd->max_iter;
-    if (cur != d_u)
-      PDD_CUDA_TRY(ctx, cudaMemcpyAsync(d_u, cur, total * sizeof(double), cudaMemcpyDeviceToDevice,
-                                        ctx->stream));
+    // a box whose last sweep was odd holds its iterate in un
+    for (size_t b = 0; b < NB; ++b)
+      if (h_it[b] & 1)
+        PDD_CUDA_TRY(ctx, cudaMemcpyAsync(d_u + b * total, un + b * total, total * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
   } else {
     for (int a = 0; a < 3; ++a) {
-      box3_sine_kernel<<<static_cast<unsigned>((B.P[a] * B.P[a] + 255) / 256), 256, 0, ctx->stream>>>(
-          B.P[a], S[a]);
+      box3_sine_kernel<<<static_cast<unsigned>((B0.P[a] * B0.P[a] + 255) / 256), 256, 0, ctx->stream>>>(
+          B0.P[a], S[a]);
       PDD_CUDA_TRY(ctx, cudaGetLastError());
     }
     int smax = 0;
-    for (int a = 0; a < 3; ++a) smax = std::max(smax, B.P[a] * B.P[a]);
+    for (int a = 0; a < 3; ++a) smax = std::max(smax, B0.P[a] * B0.P[a]);
     const size_t smem = static_cast<size_t>(smax) * sizeof(float);
     PDD_CUDA_TRY(ctx, cudaFuncSetAttribute(box3_dst_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
     PDD_CUDA_TRY(ctx, cudaFuncSetAttribute(box3_dst_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
     PDD_CUDA_TRY(ctx, cudaFuncSetAttribute(box3_dst_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
     const unsigned gt = static_cast<unsigned>(std::min<int64_t>((np + kBox3Block - 1) / kBox3Block, 2048));
-    double r0 = -1.0;
-    for (it = 0;; ++it) {
-      box3_residual_kernel<<<nblk, kBox3Block, 0, ctx->stream>>>(B, s2, c, d_u, coef, r, part);
-      box3_norm_kernel<<<1, 1, 0, ctx->stream>>>(part, nblk, rn);
+    const dim3 gr(static_cast<unsigned>(nblk), nb), gd(gt, nb);
+    for (int64_t it = 0;; ++it) {
+      box3_residual_kernel<<<gr, kBox3Block, 0, ctx->stream>>>(d_boxes, live, s2, c, d_u, coef, r,
+                                                              part);
+      box3_combine_kernel<false><<<gcomb, 128, 0, ctx->stream>>>(part, nblk, nb, live, rn);
       PDD_CUDA_TRY(ctx, cudaGetLastError());
-      PDD_CUDA_TRY(ctx, cudaMemcpyAsync(&res, rn, sizeof res, cudaMemcpyDeviceToHost, ctx->stream));
-      PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-      if (r0 < 0.0) r0 = res;
-      if (res <= sd->tol * r0 || res == 0.0 || it >= sd->max_iter) break;
+      st = read_measures();
+      if (st != PDD_OK) return st;
+      int n_live = 0;
+      for (size_t b = 0; b < NB; ++b) {
+        if (!h_live[b]) continue;
+        if (h_r0[b] < 0.0) h_r0[b] = h_rn[b];
+        h_it[b] = it;
+        h_res[b] = h_r0[b] > 0.0 ? h_rn[b] / h_r0[b] : 0.0;
+        if (h_rn[b] <= S0.tol * h_r0[b] || h_rn[b] == 0.0 || it >= S0.max_iter)
+          h_live[b] = 0;
+        else
+          ++n_live;
+      }
+      if (n_live == 0) break;
+      st = push_live();
+      if (st != PDD_OK) return st;
       // forward transform (x from the scaled FP64 residual, then y, z), the
       // eigenvalues, the inverse transform (x, y, z), the update
-      box3_dst_kernel<0><<<gt, kBox3Block, smem, ctx->stream>>>(B.P[0], B.P[1], B.P[2], S[0], nullptr, v0, rn, r);
-      box3_dst_kernel<1><<<gt, kBox3Block, smem, ctx->stream>>>(B.P[0], B.P[1], B.P[2], S[1], v0, v1, nullptr, nullptr);
-      box3_dst_kernel<2><<<gt, kBox3Block, smem, ctx->stream>>>(B.P[0], B.P[1], B.P[2], S[2], v1, v0, nullptr, nullptr);
-      box3_eig_kernel<<<gt, kBox3Block, 0, ctx->stream>>>(B, s2, c, v0);
-      box3_dst_kernel<0><<<gt, kBox3Block, smem, ctx->stream>>>(B.P[0], B.P[1], B.P[2], S[0], v0, v1, nullptr, nullptr);
-      box3_dst_kernel<1><<<gt, kBox3Block, smem, ctx->stream>>>(B.P[0], B.P[1], B.P[2], S[1], v1, v0, nullptr, nullptr);
-      box3_dst_kernel<2><<<gt, kBox3Block, smem, ctx->stream>>>(B.P[0], B.P[1], B.P[2], S[2], v0, v1, nullptr, nullptr);
-      box3_update_kernel<<<gt, kBox3Block, 0, ctx->stream>>>(B, v1, rn, d_u);
+      box3_dst_kernel<0><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[0], nullptr, v0, rn, r);
+      box3_dst_kernel<1><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[1], v0, v1, nullptr, nullptr);
+      box3_dst_kernel<2><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[2], v1, v0, nullptr, nullptr);
+      box3_eig_kernel<<<gd, kBox3Block, 0, ctx->stream>>>(d_boxes, live, s2, c, v0);
+      box3_dst_kernel<0><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[0], v0, v1, nullptr, nullptr);
+      box3_dst_kernel<1><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[1], v1, v0, nullptr, nullptr);
+      box3_dst_kernel<2><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[2], v0, v1, nullptr, nullptr);
+      box3_update_kernel<<<gd, kBox3Block, 0, ctx->stream>>>(d_boxes, live, v1, rn, d_u);
       PDD_CUDA_TRY(ctx, cudaGetLastError());
     }
-    res = r0 > 0.0 ? res / r0 : 0.0;
   }
   if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
   PDD_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  *iters = it;
-  *resid = res;
-  if (sd->method == PDD_STENCIL_DST ? res > sd->tol : res >= sd->tol)
-    return fail(ctx, PDD_ETIMEOUT, "max_iter reached before the tolerance");
+  int64_t it_max = 0;
+  double res_max = 0.0;
+  bool unmet = false;
+  for (size_t b = 0; b < NB; ++b) {
+    it_max = std::max(it_max, h_it[b]);
+    res_max = std::max(res_max, h_res[b]);
+    unmet |= jacobi ? h_res[b] >= S0.tol : h_res[b] > S0.tol;
+    if (iters_each) iters_each[b] = h_it[b];
+    if (resid_each) resid_each[b] = h_res[b];
+  }
+  if (iters) *iters = it_max;
+  if (resid) *resid = res_max;
+  if (unmet) return fail(ctx, PDD_ETIMEOUT, "max_iter reached before the tolerance");
   return PDD_OK;
+}
+
+pdd_status subdomain_solve3d_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const double *d_face,
+                                  int64_t m, double *d_u, int64_t *iters, double *resid) {
+  return subdomain_solve3d_batch_impl(ctx, sd, 1, d_face, m, d_u, iters, resid, nullptr, nullptr);
 }
 
 }  // namespace pdd

@@ -173,3 +173,54 @@ def test_rejections(api):
     with api.Context(W.laplace_expcos()) as ctx:
         with pytest.raises(PDDError):   # 3-D grids need the 3-D family
             ctx.subdomain_solve3d((0, 0, 0), (0.25, 0.25, 0.25), (9, 9, 9), {})
+
+
+@pytest.mark.parametrize("method,tol", [("dst", 1e-13), ("jacobi", 1e-13)])
+def test_batch_equals_single_solves(api, method, tol):
+    """pdd_subdomain_solve_batch: each box of a batch (own position, own
+    interface mask) gets the bits of its own pdd_subdomain_solve, and the
+    boxes stop at their own iteration counts."""
+    prob = W.elliptic_manufactured()
+    rng = np.random.default_rng(21)
+    n = (11, 9, 13) if method == "dst" else (7, 7, 9)
+    boxes = []
+    for b, (mask, lo) in enumerate([(0b000000, (0.0, 0.0, 0.0)), (0b101010, (0.25, 0.5, 0.0)),
+                                    (0b010101, (0.5, 0.25, 0.5)), (0b111111, (0.75, 0.75, 0.75))]):
+        hi = tuple(v + 0.25 for v in lo)
+        boxes.append((lo, hi, _box_data(lo, hi, n, mask, rng)))
+    kw = dict(method=method, tol=tol, max_iter=20000 if method == "jacobi" else 200)
+    with api.Context(prob) as ctx:
+        rb = ctx.subdomain_solve3d_batch(boxes, n, **kw)
+        singles = [ctx.subdomain_solve3d(lo, hi, n, faces, **kw) for lo, hi, faces in boxes]
+    assert rb["status"] == 0
+    for b, r in enumerate(singles):
+        assert torch.equal(rb["u"][b], r["u"]), b
+        assert rb["iters_each"][b] == r["iters"] and rb["resid_each"][b] == r["resid"]
+    assert rb["iters"] == max(r["iters"] for r in singles)
+    print(f"batch of 4 boxes ({method}): iterations {rb['iters_each']}")
+
+
+def test_batch_rejections(api):
+    import ctypes
+    prob = W.elliptic_manufactured()
+    from paper_1705_03666_gb300 import _lib
+    with api.Context(prob) as ctx:
+        boxes = [((0, 0, 0), (0.25, 0.25, 0.25), {}), ((0.25, 0, 0), (0.5, 0.25, 0.25), {})]
+        r = ctx.subdomain_solve3d_batch(boxes, (9, 9, 9))
+        assert r["status"] == 0 and r["u"].shape == (2, 9, 9, 9)
+        with pytest.raises(_lib.PDDError):   # a box outside the cube
+            ctx.subdomain_solve3d_batch([((0.5, 0, 0), (1.5, 0.25, 0.25), {})], (9, 9, 9))
+        # two grid sizes, or two methods, in one batch (through the C ABI)
+        u = torch.empty(2 * 11 * 11 * 11, dtype=torch.float64, device="cuda")
+        for second in ((9, 9, 9, "dst"), (11, 11, 11, "jacobi")):
+            sds = (_lib.Subdomain * 2)()
+            for b, (nn, meth) in enumerate([((11, 11, 11), "dst"), (second[:3], second[3])]):
+                sds[b] = _lib.Subdomain((ctypes.c_double * 3)(0.25 * b, 0, 0),
+                                        (ctypes.c_double * 3)(0.25 * b + 0.25, 0.25, 0.25),
+                                        (ctypes.c_int32 * 3)(*nn), 0, 0, _lib.STENCIL[meth],
+                                        200, 1e-12)
+            it, res = ctypes.c_int64(0), ctypes.c_double(0.0)
+            st = ctx.lib.pdd_subdomain_solve_batch(ctx.handle, sds, 2, None, 0, u.data_ptr(),
+                                                   ctypes.byref(it), ctypes.byref(res), None,
+                                                   None)
+            assert st == _lib.PDD_EINVAL
