@@ -24,6 +24,8 @@
 // a subdomain (|b| / |grad| against the Laplacian's scale), so the error
 // contracts by roughly ten per iteration, down to the FP64 residual
 // tolerance.  A plain Jacobi sweep is kept as the reference method.
+#include <cooperative_groups.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -117,27 +119,58 @@ __global__ void rbf_assemble_kernel(const RbfPlane *planes, int32_t n_planes, co
   }
 }
 
-// Gaussian elimination with partial pivoting and back substitution, in
-// place, one block per plane.  On return rhs holds [w; c].  A zero pivot
-// sets *singular.
-__global__ void __launch_bounds__(kRbfBlock)
+// Gaussian elimination with partial pivoting and back substitution, one
+// thread-block cluster of kRbfCluster blocks per plane (the systems are
+// dense FP64 and GB300's FP64 rate is per SM, so a plane's elimination is
+// spread over several SMs).  Rows are not moved: block r of the cluster owns
+// rows i = r (mod kRbfCluster) and keeps its rows' "already a pivot" flags;
+// step k takes as pivot the unused row with the largest |A[i][k]| (lowest
+// index on ties), every block reads that row, and each block eliminates
+// column k from its own unused rows.  One cluster barrier per step: the
+// blocks' pivot candidates sit in double-buffered shared slots read across
+// the cluster, and a block only writes its own rows, which no other block
+// reads before the next barrier (the pivot row is read after it).  Then the
+// first block back-substitutes in pivot order.  On return rhs holds [w; c].
+// A zero pivot sets *singular.
+constexpr int kRbfCluster = 8;
+
+__global__ void __cluster_dims__(kRbfCluster, 1, 1) __launch_bounds__(kRbfBlock)
 rbf_solve_kernel(const RbfPlane *planes, int32_t n_planes, double *sys, int *singular) {
-  const int p = blockIdx.x;
-  if (p >= n_planes) return;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int p = blockIdx.x / kRbfCluster;
+  const int r = static_cast<int>(cluster.block_rank());
+  if (p >= n_planes) return;  // whole clusters: every block of it returns
   const int64_t M = planes[p].M;
   double *A = sys + planes[p].sys0, *b = A + M * M;
-  extern __shared__ double rowk[];  // pivot row, M doubles
+  // dynamic shared memory: the pivot row (M doubles, with its right-hand
+  // side last), then (first block) the solution and the pivot order, then
+  // the used flags of this block's rows
+  extern __shared__ double dsm[];
+  double *rowk = dsm;                                   // M + 1
+  double *x = rowk + M + 1;                             // M (block 0)
+  int32_t *perm = reinterpret_cast<int32_t *>(x + M);  // M (block 0)
+  unsigned char *used = reinterpret_cast<unsigned char *>(perm + M);  // M / kRbfCluster + 1
+  __shared__ double cand_v[2];
+  __shared__ int64_t cand_i[2];
   __shared__ double red_v[kRbfBlock / 32];
   __shared__ int64_t red_i[kRbfBlock / 32];
-  __shared__ int64_t piv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int64_t nrow = (M - r + kRbfCluster - 1) / kRbfCluster;  // rows r, r + C, ...
+  __shared__ int64_t steps;  // elimination steps completed (M unless a pivot was missing)
+  for (int64_t t = tid; t < nrow; t += blockDim.x) used[t] = 0;
+  if (tid == 0) steps = M;
+  __syncthreads();
   for (int64_t k = 0; k < M; ++k) {
-    // pivot: the largest |A[i][k]|, i >= k (lowest index on ties)
+    const int slot = static_cast<int>(k & 1);
+    // this block's candidate: the largest |A[i][k]| over its unused rows
     double best = -1.0;
-    int64_t bi = k;
-    for (int64_t i = k + tid; i < M; i += blockDim.x) {
+    int64_t bi = M;
+    for (int64_t t = tid; t < nrow; t += blockDim.x) {
+      if (used[t]) continue;
+      const int64_t i = r + t * kRbfCluster;
       const double v = fabs(A[i * M + k]);
-      if (v > best) { best = v; bi = i; }
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
       const double ov = __shfl_xor_sync(kFull, best, o);
@@ -151,29 +184,44 @@ rbf_solve_kernel(const RbfPlane *planes, int32_t n_planes, double *sys, int *sin
       int64_t bj = red_i[0];
       for (int w = 1; w < nw; ++w)
         if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bj)) { bv = red_v[w]; bj = red_i[w]; }
+      cand_v[slot] = bv;
+      cand_i[slot] = bj;
+    }
+    // the candidates of step k, and every block's rows as updated in step
+    // k - 1, are visible across the cluster after this barrier
+    cluster.sync();
+    __shared__ int64_t piv;
+    if (tid == 0) {
+      double bv = -1.0;
+      int64_t bj = M;
+      for (int q = 0; q < kRbfCluster; ++q) {
+        const double v = *cluster.map_shared_rank(&cand_v[slot], q);
+        const int64_t ii = *cluster.map_shared_rank(&cand_i[slot], q);
+        if (v > bv || (v == bv && ii < bj)) { bv = v; bj = ii; }
+      }
       piv = bj;
-      if (!(bv > 0.0)) *singular = 1;
+      if (r == 0) {
+        perm[k] = static_cast<int32_t>(bj);
+        if (!(bv > 0.0)) *singular = 1;
+      }
+      if (bj < M && bj % kRbfCluster == r) used[bj / kRbfCluster] = 1;
     }
     __syncthreads();
     const int64_t pr = piv;
-    if (pr != k) {
-      for (int64_t j = tid; j < M; j += blockDim.x) {
-        const double t = A[k * M + j];
-        A[k * M + j] = A[pr * M + j];
-        A[pr * M + j] = t;
-      }
-      if (tid == 0) {
-        const double t = b[k];
-        b[k] = b[pr];
-        b[pr] = t;
-      }
+    if (pr >= M) {  // no unused row left (singular; flagged above)
+      if (tid == 0) steps = k;
+      break;
     }
+    // the pivot row (columns k .. M - 1) and its right-hand side, read
+    // through L2: its owner wrote it in an earlier step
+    for (int64_t j = k + tid; j < M; j += blockDim.x) rowk[j] = __ldcg(A + pr * M + j);
+    if (tid == 0) rowk[M] = __ldcg(b + pr);
     __syncthreads();
-    for (int64_t j = k + tid; j < M; j += blockDim.x) rowk[j] = A[k * M + j];
-    __syncthreads();
-    const double akk = rowk[k], bk = b[k];
-    // rows below: multiplier, then the row update (a warp per row)
-    for (int64_t i = k + 1 + warp; i < M; i += nw) {
+    const double akk = rowk[k], bk = rowk[M];
+    // this block's unused rows: multiplier, then the row update (a warp per row)
+    for (int64_t t = warp; t < nrow; t += nw) {
+      if (used[t]) continue;
+      const int64_t i = r + t * kRbfCluster;
       const double l = A[i * M + k] / akk;
       __syncwarp();  // every lane has read A[i][k] before lane 0 clears it
       for (int64_t j = k + 1 + lane; j < M; j += 32) A[i * M + j] = fma(-l, rowk[j], A[i * M + j]);
@@ -182,16 +230,30 @@ rbf_solve_kernel(const RbfPlane *planes, int32_t n_planes, double *sys, int *sin
         b[i] = fma(-l, bk, b[i]);
       }
     }
-    __syncthreads();
   }
-  // back substitution: x_k = b_k / A_kk, then b_i -= A_ik x_k for i < k
+  // every row's final state is written before the first block reads it
+  cluster.sync();
+  if (r != 0) return;
+  if (steps < M) {  // incomplete elimination: no solution
+    for (int64_t k = tid; k < M; k += blockDim.x) b[k] = static_cast<double>(NAN);
+    return;
+  }
+  // back substitution in pivot order: x_k = (b_pk - sum_{j>k} A_pk,j x_j) / A_pk,k
   for (int64_t k = M - 1; k >= 0; --k) {
-    if (tid == 0) b[k] = b[k] / A[k * M + k];
+    const int64_t pk = perm[k];
+    double acc = 0.0;
+    for (int64_t j = k + 1 + tid; j < M; j += blockDim.x) acc = fma(__ldcg(A + pk * M + j), x[j], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (lane == 0) red_v[warp] = acc;
     __syncthreads();
-    const double xk = b[k];
-    for (int64_t i = tid; i < k; i += blockDim.x) b[i] = fma(-A[i * M + k], xk, b[i]);
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red_v[w];
+      x[k] = (__ldcg(b + pk) - s) / __ldcg(A + pk * M + k);
+    }
     __syncthreads();
   }
+  for (int64_t k = tid; k < M; k += blockDim.x) b[k] = x[k];
 }
 
 __global__ void rbf_eval_kernel(const RbfPlane *planes, int32_t n_planes, const double *pts,
@@ -282,10 +344,13 @@ pdd_status interface_interp_impl(pdd_ctx *ctx, int32_t n_planes, const int32_t *
                 static_cast<unsigned>(n_planes));
   rbf_assemble_kernel<<<g2, 256, 0, ctx->stream>>>(d_pl, n_planes, pts, pv, sys);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
-  const size_t smem = static_cast<size_t>(Mmax) * sizeof(double);
+  // pivot row + solution (doubles), pivot order (int32), used flags (bytes)
+  const size_t smem = static_cast<size_t>(2 * Mmax + 1) * sizeof(double) +
+                      static_cast<size_t>(Mmax) * sizeof(int32_t) +
+                      static_cast<size_t>(Mmax / kRbfCluster + 8);
   PDD_CUDA_TRY(ctx, cudaFuncSetAttribute(rbf_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem)));
-  rbf_solve_kernel<<<static_cast<unsigned>(n_planes), kRbfBlock, smem, ctx->stream>>>(
+  rbf_solve_kernel<<<static_cast<unsigned>(n_planes) * kRbfCluster, kRbfBlock, smem, ctx->stream>>>(
       d_pl, n_planes, sys, singular);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
   int64_t qmax = 0;
