@@ -511,7 +511,9 @@ def run_other_workloads(api, dev) -> dict:
                                            (ad["u"] - a["u"]).abs().max(),
                                            (bd["u"] - bb["u"]).abs().max())),
                                        "method": "direct: four FP64 products of the 127 x 127 "
-                                                 "sine matrices per subdomain"},
+                                                 "sine matrices per subdomain",
+                                       # 2 subdomains x 4 products x 2 P^3 flops, P = 127
+                                       "gflops_fp64": 2 * 4 * 2 * 127 ** 3 / (ms_d / 1e3) / 1e9},
                                "bytes_model": "13 vector accesses per point per CG iteration",
                                "residence": "L2/shared-resident (0.27 MB per vector)"}
         # the whole two-stage method on this workload: stage one at its 16

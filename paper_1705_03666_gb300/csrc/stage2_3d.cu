@@ -560,24 +560,34 @@ box3_dst_kernel(int P0, int P1, int P2, const int32_t *live, const float *__rest
   }
 }
 
+// cos(pi k / (P_a + 1)) - 1 for k = 1 .. P_a on each axis (cm1[a][k - 1]),
+// formed once per solve: the eigenvalue factors of the 1-D second difference.
+__global__ void box3_cos_kernel(int P0, int P1, int P2, double *cm1) {
+  const int a = blockIdx.y;
+  const int P = a == 0 ? P0 : (a == 1 ? P1 : P2);
+  for (int k = threadIdx.x; k < P; k += blockDim.x)
+    cm1[a * kBox3MaxInterior + k] = cospi(static_cast<double>(k + 1) / (P + 1)) - 1.0;
+}
+
 // Division by the eigenvalues of (1/2) sigma^2 Lap_h + c in the sine basis,
 // lambda = sum_a (sigma^2 / h_a^2) (cos(pi k_a / (P_a + 1)) - 1) + c, and the
 // normalisation of the two transforms, 8 / prod_a (P_a + 1).
 __global__ void box3_eig_kernel(const Box3 *boxes, const int32_t *live, double s2, double c,
-                                float *v) {
+                                const double *__restrict__ cm1, float *v) {
   if (!live[blockIdx.y]) return;
   const Box3 B = boxes[blockIdx.y];
   const int64_t np = box3_np(B);
   v += blockIdx.y * np;
   const double norm = 8.0 / ((B.P[0] + 1.0) * (B.P[1] + 1.0) * (B.P[2] + 1.0));
+  const double e0 = s2 / (B.h[0] * B.h[0]), e1 = s2 / (B.h[1] * B.h[1]),
+               e2 = s2 / (B.h[2] * B.h[2]);
   for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < np;
        q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int k0 = static_cast<int>(q % B.P[0]) + 1;
-    const int k1 = static_cast<int>((q / B.P[0]) % B.P[1]) + 1;
-    const int k2 = static_cast<int>(q / (static_cast<int64_t>(B.P[0]) * B.P[1])) + 1;
-    const double lam = s2 / (B.h[0] * B.h[0]) * (cospi(static_cast<double>(k0) / (B.P[0] + 1)) - 1.0) +
-                       s2 / (B.h[1] * B.h[1]) * (cospi(static_cast<double>(k1) / (B.P[1] + 1)) - 1.0) +
-                       s2 / (B.h[2] * B.h[2]) * (cospi(static_cast<double>(k2) / (B.P[2] + 1)) - 1.0) + c;
+    const int k0 = static_cast<int>(q % B.P[0]);
+    const int k1 = static_cast<int>((q / B.P[0]) % B.P[1]);
+    const int k2 = static_cast<int>(q / (static_cast<int64_t>(B.P[0]) * B.P[1]));
+    const double lam = e0 * cm1[k0] + e1 * cm1[kBox3MaxInterior + k1] +
+                       e2 * cm1[2 * kBox3MaxInterior + k2] + c;
     v[q] = static_cast<float>(static_cast<double>(v[q]) * (norm / lam));
   }
 }
@@ -720,6 +730,7 @@ pdd_status subdomain_solve3d_batch_impl(pdd_ctx *ctx, const pdd_subdomain *sds, 
   const size_t off_v0 = take(NB * np * sizeof(float));
   const size_t off_v1 = take(NB * np * sizeof(float));
   const size_t off_S = take(3 * kBox3MaxInterior * kBox3MaxInterior * sizeof(float));
+  const size_t off_cm1 = take(3 * kBox3MaxInterior * sizeof(double));
   pdd_status st = ensure_scratch(ctx, o);
   if (st != PDD_OK) return st;
   char *base = static_cast<char *>(ctx->scratch);
@@ -734,6 +745,7 @@ pdd_status subdomain_solve3d_batch_impl(pdd_ctx *ctx, const pdd_subdomain *sds, 
   float *S[3];
   for (int a = 0; a < 3; ++a)
     S[a] = reinterpret_cast<float *>(base + off_S) + a * kBox3MaxInterior * kBox3MaxInterior;
+  double *cm1 = reinterpret_cast<double *>(base + off_cm1);
 
   // host state of the correction loop (copied to and from the device
   // synchronously, so these buffers outlive every copy)
@@ -807,6 +819,8 @@ pdd_status subdomain_solve3d_batch_impl(pdd_ctx *ctx, const pdd_subdomain *sds, 
           B0.P[a], S[a]);
       PDD_CUDA_TRY(ctx, cudaGetLastError());
     }
+    box3_cos_kernel<<<dim3(1, 3), 128, 0, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], cm1);
+    PDD_CUDA_TRY(ctx, cudaGetLastError());
     int smax = 0;
     for (int a = 0; a < 3; ++a) smax = std::max(smax, B0.P[a] * B0.P[a]);
     const size_t smem = static_cast<size_t>(smax) * sizeof(float);
@@ -841,7 +855,7 @@ pdd_status subdomain_solve3d_batch_impl(pdd_ctx *ctx, const pdd_subdomain *sds, 
       box3_dst_kernel<0><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[0], nullptr, v0, rn, r);
       box3_dst_kernel<1><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[1], v0, v1, nullptr, nullptr);
       box3_dst_kernel<2><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[2], v1, v0, nullptr, nullptr);
-      box3_eig_kernel<<<gd, kBox3Block, 0, ctx->stream>>>(d_boxes, live, s2, c, v0);
+      box3_eig_kernel<<<gd, kBox3Block, 0, ctx->stream>>>(d_boxes, live, s2, c, cm1, v0);
       box3_dst_kernel<0><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[0], v0, v1, nullptr, nullptr);
       box3_dst_kernel<1><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[1], v1, v0, nullptr, nullptr);
       box3_dst_kernel<2><<<gd, kBox3Block, smem, ctx->stream>>>(B0.P[0], B0.P[1], B0.P[2], live, S[2], v0, v1, nullptr, nullptr);
