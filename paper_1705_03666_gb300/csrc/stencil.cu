@@ -13,6 +13,8 @@
 //    refinement (one CTA, vectors L2-resident, fixed-order block reductions),
 //    or Jacobi sweeps, all bounded by max_iter; or directly by discrete sine
 //    transforms (dst.cu).
+#include <cooperative_groups.h>
+
 #include <cmath>
 #include <cstring>
 
@@ -264,6 +266,91 @@ cg_kernel(double *u, int nx, int ny, double ihx2, double ihy2, double *r, double
   }
 }
 
+// The same conjugate gradients on a thread-block cluster of kCgCluster
+// blocks (FP64 arithmetic runs at a per-SM rate, and one block held the
+// solve to one SM): block b owns the grid rows [b ny / C, (b + 1) ny / C).
+// Each iteration: the block's part of q = A p (reading its neighbours' rows
+// of p through L2), the cluster-wide p.q (every block sums the C block
+// partials in rank order, read from each other's shared memory, so all
+// blocks take the same alpha), the update of u and r, the cluster-wide r.r,
+// and p = r + beta p.  Three cluster barriers per iteration: before q = A p
+// (p complete), after each partial sum.
+constexpr int kCgCluster = 8;
+
+__global__ void __cluster_dims__(kCgCluster, 1, 1) __launch_bounds__(kStencilBlock)
+cg_cluster_kernel(double *u, int nx, int ny, double ihx2, double ihy2, double *r, double *p,
+                  double *q, int64_t max_iter, double tol, int64_t *iters_out, double *resid_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ double sh[33];
+  __shared__ double slot_pq, slot_rr;
+  const int rank = static_cast<int>(cluster.block_rank());
+  const int j0 = static_cast<int>(static_cast<int64_t>(rank) * ny / kCgCluster);
+  const int j1 = static_cast<int>(static_cast<int64_t>(rank + 1) * ny / kCgCluster);
+  const int k0 = j0 * nx, k1 = j1 * nx;
+  const double diag = 2.0 * ihx2 + 2.0 * ihy2;
+  auto cluster_sum = [&](double *slot, double v_block) -> double {
+    if (threadIdx.x == 0) *slot = v_block;
+    cluster.sync();
+    double t = 0.0;
+    for (int b = 0; b < kCgCluster; ++b) t += *cluster.map_shared_rank(slot, b);
+    return t;
+  };
+  double rr_loc = 0.0;
+  for (int k = k0 + threadIdx.x; k < k1; k += kStencilBlock) {
+    const int i = k % nx, j = k / nx;
+    double v = 0.0;
+    if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1)
+      v = ihx2 * (u[k - 1] + u[k + 1]) + ihy2 * (u[k - nx] + u[k + nx]) - diag * u[k];
+    r[k] = v;
+    p[k] = v;
+    rr_loc += v * v;
+  }
+  double rr = cluster_sum(&slot_rr, block_sum(rr_loc, sh));
+  const double bnorm = sqrt(rr);
+  int64_t it = 0;
+  double res = bnorm > 0.0 ? 1.0 : 0.0;
+  while (it < max_iter && bnorm > 0.0 && sqrt(rr) > tol * bnorm) {
+    cluster.sync();  // p complete (and every block done reading slot_rr)
+    double pq_loc = 0.0;
+    for (int k = k0 + threadIdx.x; k < k1; k += kStencilBlock) {
+      const int i = k % nx, j = k / nx;
+      double v = 0.0;
+      const double pk = __ldcg(p + k);
+      if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
+        const double pw = i > 1 ? __ldcg(p + k - 1) : 0.0, pe = i < nx - 2 ? __ldcg(p + k + 1) : 0.0;
+        const double ps = j > 1 ? __ldcg(p + k - nx) : 0.0, pn = j < ny - 2 ? __ldcg(p + k + nx) : 0.0;
+        v = diag * pk - ihx2 * (pw + pe) - ihy2 * (ps + pn);
+      }
+      q[k] = v;
+      pq_loc += pk * v;
+    }
+    const double pq = cluster_sum(&slot_pq, block_sum(pq_loc, sh));
+    const double alpha = rr / pq;
+    double rn_loc = 0.0;
+    for (int k = k0 + threadIdx.x; k < k1; k += kStencilBlock) {
+      const int i = k % nx, j = k / nx;
+      if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
+        u[k] += alpha * __ldcg(p + k);
+        const double rk = r[k] - alpha * q[k];
+        r[k] = rk;
+        rn_loc += rk * rk;
+      }
+    }
+    const double rn = cluster_sum(&slot_rr, block_sum(rn_loc, sh));
+    const double beta = rn / rr;
+    rr = rn;
+    for (int k = k0 + threadIdx.x; k < k1; k += kStencilBlock) p[k] = r[k] + beta * __ldcg(p + k);
+    ++it;
+    res = sqrt(rr) / bnorm;
+  }
+  cluster.sync();  // no block leaves while another may read its slots
+  if (rank == 0 && threadIdx.x == 0) {
+    *iters_out = it;
+    *resid_out = res;
+  }
+}
+
 // Mixed-precision conjugate gradients (iterative refinement): the FP64
 // residual r = b - A u is formed, scaled to unit norm and rounded to FP32;
 // CG in FP32 (vectors, arithmetic and fixed-tree block sums) solves A e = r
@@ -472,9 +559,15 @@ pdd_status subdomain_solve_impl(pdd_ctx *ctx, const pdd_subdomain *sd, const dou
   if (sd->method == PDD_STENCIL_DST) {
     st = dst_solve(ctx, d_u, nx, ny, hx, hy, base + off_dst, it_d, res_d);
     if (st != PDD_OK) return st;
-  } else if (sd->method == PDD_STENCIL_CG)
-    cg_kernel<<<1, kStencilBlock, 0, ctx->stream>>>(d_u, nx, ny, ihx2, ihy2, v0, v1, v2,
-                                                    sd->max_iter, sd->tol, it_d, res_d);
+  } else if (sd->method == PDD_STENCIL_CG) {
+    // a cluster of kCgCluster blocks when every block gets at least one row
+    if (ny >= kCgCluster)
+      cg_cluster_kernel<<<kCgCluster, kStencilBlock, 0, ctx->stream>>>(
+          d_u, nx, ny, ihx2, ihy2, v0, v1, v2, sd->max_iter, sd->tol, it_d, res_d);
+    else
+      cg_kernel<<<1, kStencilBlock, 0, ctx->stream>>>(d_u, nx, ny, ihx2, ihy2, v0, v1, v2,
+                                                      sd->max_iter, sd->tol, it_d, res_d);
+  }
   else if (sd->method == PDD_STENCIL_CG_MIXED) {
     // the three FP32 vectors in shared memory when they fit (129 x 129: 200 KB)
     const size_t smem = 3 * npts * sizeof(float);

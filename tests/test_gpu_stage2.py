@@ -47,6 +47,21 @@ def test_cg_matches_direct_solve(api, orc, side, lo, hi, method):
     assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-10
 
 
+@pytest.mark.parametrize("n", [(37, 45), (9, 5), (200, 9)])
+def test_cg_on_ragged_grids(api, orc, n):
+    """FP64 CG on grids whose rows split unevenly over the blocks of the
+    solve's cluster (45 and 9 rows over 8 blocks), and on a grid with fewer
+    rows than blocks (one block)."""
+    s = np.array([0.15, 0.4, 0.55, 0.85])
+    vals = np.exp(0.5) * np.cos(s)
+    with api.Context(W.laplace_expcos()) as ctx:
+        r = ctx.subdomain_solve((0.0, 0.0), (0.5, 1.0), n, 0, 1, torch.from_numpy(s),
+                                torch.from_numpy(vals), method="cg", tol=1e-13)
+    ref = _oracle_subdomain(orc, (0.0, 0.0), (0.5, 1.0), n, 1, s, vals)
+    assert r["status"] == 0 and r["resid"] <= 1e-13
+    assert np.max(np.abs(r["u"].cpu().numpy() - ref)) < 1e-10
+
+
 def test_jacobi_matches_direct_solve(api, orc):
     s = np.array([0.2, 0.45, 0.6, 0.9])
     vals = np.exp(0.5) * np.cos(s)
