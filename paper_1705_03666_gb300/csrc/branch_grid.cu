@@ -142,7 +142,9 @@ __device__ __forceinline__ bool grid_exit(const GridArgs &a, const float *x0, co
   return true;
 }
 
-template <class Geom, int D>
+// kBinary: two children with probability one and the classical weight (the
+// KPP law), so the offspring count and the mark are constants.
+template <class Geom, int D, bool kBinary>
 __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_constant__ GridArgs a) {
   constexpr bool kBounded = GeomTraits<Geom>::kBounded;
   const unsigned lane = threadIdx.x & 31u;
@@ -270,23 +272,32 @@ __global__ void __launch_bounds__(kBranchBlock) branch_grid_kernel(const __grid_
         pdone = true;
       } else {
         // lifetime over before T_m: branch
-        const float u3 = unif_f(u_off);
-        int k = a.K;
-        for (int kk = 0; kk <= a.K; ++kk) {
-          if (u3 < a.cum[kk]) {
-            k = kk;
-            break;
+        int k = 2;
+        if constexpr (!kBinary) {
+          const float u3 = unif_f(u_off);
+          k = a.K;
+          for (int kk = 0; kk <= a.K; ++kk) {
+            if (u3 < a.cum[kk]) {
+              k = kk;
+              break;
+            }
           }
+          const float r = a.ratio[k];
+          if (r != 1.0f)  // classical weights: nothing to do
+            for (int kk = ti; kk < a.m; ++kk) PROD(kk) *= r;
         }
-        const float r = a.ratio[k];
-        if (r != 1.0f)  // classical weights: nothing to do
-          for (int kk = ti; kk < a.m; ++kk) PROD(kk) *= r;
         particles += k;
         if (particles > a.max_particles || sp + k > a.max_depth) {
           bad = true;
           tree_done = true;
         } else if (k == 0) {
           pdone = true;
+        } else if constexpr (kBinary) {
+          stk[sp++] = make_float4(X[0], X[1], __uint_as_float(tend),
+                                  __uint_as_float((next_id + 1) | (static_cast<uint32_t>(ti) << 16)));
+          id = next_id;
+          next_id += 2;
+          start = true;  // continue with the first child from (X, tend)
         } else {
           for (int c = k - 1; c >= 1; --c)
             stk[sp++] = make_float4(X[0], X[1], __uint_as_float(tend),
@@ -412,7 +423,10 @@ static pdd_status run_grid(pdd_ctx *ctx, const double *d_nodes, int64_t n, const
   a.max_particles = bp->max_particles;
   a.max_depth = bp->max_depth;
 
-  auto kern = branch_grid_kernel<Geom, D>;
+  // two children with probability one and the classical weight (KPP)
+  const bool binary = a.K == 2 && prm[4] == 0.0 && prm[5] == 0.0 && prm[6] == 1.0 &&
+                      prm[5 + a.K + 2] == 1.0;
+  auto kern = binary ? branch_grid_kernel<Geom, D, true> : branch_grid_kernel<Geom, D, false>;
   int bps = 0;
   PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kBranchBlock, 0));
   if (bps < 1) bps = 1;
