@@ -131,17 +131,22 @@ enum {
 /* Optional diagnostics.  Inputs: the optional device buffers receive, for
  * every (node, path) in node-major order, the path's score (FP64), its exit
  * step (0 for a node on the boundary, -max_steps for a capped path) and
- * (pdd_interface_solve only) its exit point (FP64 [dim], the projection on
- * the nearest face for a capped path), and per node its flags
- * (PDD_NODE_*; pdd_interface_solve, pdd_branching_solve, pdd_batch_solve).
+ * (pdd_interface_solve, pdd_wos_solve) its exit point (FP64 [dim], the
+ * projection on the nearest face for a capped path or a stopped walk), and
+ * per node its flags (PDD_NODE_*; pdd_interface_solve, pdd_branching_solve,
+ * pdd_batch_solve).
  * Outputs (host, valid when the call returns): total Euler steps taken and the
  * number of capped paths/trees. */
 typedef struct {
   double *d_path_score;    /* [n * n_paths] or NULL */
   int32_t *d_path_steps;   /* [n * n_paths] or NULL */
-  double *d_path_aux;      /* pdd_interface_grad only: [n * n_paths][18] per-path
+  double *d_path_aux;      /* pdd_interface_grad: [n * n_paths][18] per-path
                               exit point (x, y) and likelihood-ratio sums
-                              L_1..L_16, or NULL */
+                              L_1..L_16; pdd_mlmc_level: [n * n_paths][8] per
+                              pair the fine and coarse scores, their exit
+                              steps (fine steps; coarse steps; negative when
+                              capped) and exit points (x, y each; 0 for the
+                              coarse walk at level 0); or NULL */
   int64_t path_steps;      /* out */
   int64_t capped;          /* out */
   double *d_path_exit;     /* [n * n_paths][dim] or NULL */

@@ -109,7 +109,7 @@ def _load():
             lib.orc_jacobian_width.argtypes = [P]
             lib.orc_jacobian_width.restype = ctypes.c_int
             lib.orc_wos_solve.argtypes = [P, dp, ctypes.c_int64, lp, M, ctypes.c_double,
-                                          dp, dp, lp, dp, ip, lp]
+                                          dp, dp, lp, dp, ip, lp, dp]
             lib.orc_wos_solve.restype = ctypes.c_int
             lib.orc_branching_solve.argtypes = [P, dp, ctypes.c_int64, M,
                                                 ctypes.c_int64, ctypes.c_int32,
@@ -120,7 +120,7 @@ def _load():
                                                      dp, dp, lp, lp, dp, ip]
             lib.orc_branching_grid_solve.restype = ctypes.c_int
             lib.orc_mlmc_level.argtypes = [P, dp, ctypes.c_int64, M, ctypes.c_int32,
-                                           ctypes.c_int32, dp, dp, dp, dp, dp, ip, lp]
+                                           ctypes.c_int32, dp, dp, dp, dp, dp, ip, lp, dp]
             lib.orc_mlmc_level.restype = ctypes.c_int
             lib.orc_grid_ticks_per_unit.argtypes = [ctypes.c_double]
             lib.orc_grid_ticks_per_unit.restype = ctypes.c_double
@@ -287,7 +287,8 @@ def interface_jacobian(prob: dict, nodes, *, seed, dt, n_paths, max_steps=10**7,
 def wos_solve(prob: dict, nodes, *, seed, n_paths, eps, max_steps=10**6, n_threads=None,
               dump_paths=False, node_ids=None):
     """Walk on Spheres for Eq. 1.1 (Sec. 2.1): mean, se, n per node, total
-    steps, and with dump_paths per-path score[n, N] and steps[n, N]."""
+    steps, and with dump_paths per-path score[n, N], steps[n, N] and the
+    projected stopping point exit[n, N, 2]."""
     lib = _load()
     nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, int(prob["dim"]))
     n = nodes.shape[0]
@@ -297,18 +298,20 @@ def wos_solve(prob: dict, nodes, *, seed, n_paths, eps, max_steps=10**6, n_threa
     cnt = np.zeros(n, dtype=np.int64)
     score = np.zeros((n, n_paths)) if dump_paths else None
     steps = np.zeros((n, n_paths), dtype=np.int32) if dump_paths else None
+    exitp = np.zeros((n, n_paths, 2)) if dump_paths else None
     ids = None if node_ids is None else np.ascontiguousarray(node_ids, dtype=np.int64)
     ts = ctypes.c_int64(0)
     rc = lib.orc_wos_solve(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n,
                            _ptr(ids, ctypes.c_int64), ctypes.byref(M), float(eps),
                            _ptr(mean, ctypes.c_double), _ptr(se, ctypes.c_double),
                            _ptr(cnt, ctypes.c_int64), _ptr(score, ctypes.c_double),
-                           _ptr(steps, ctypes.c_int32), ctypes.byref(ts))
+                           _ptr(steps, ctypes.c_int32), ctypes.byref(ts),
+                           _ptr(exitp, ctypes.c_double))
     if rc != 0:
         raise ValueError("oracle wos_solve: invalid arguments")
     out = {"mean": mean, "se": se, "n": cnt, "total_steps": ts.value}
     if dump_paths:
-        out["score"], out["steps"] = score, steps
+        out["score"], out["steps"], out["exit"] = score, steps, exitp
     return out
 
 
@@ -385,17 +388,21 @@ def mlmc_level(prob: dict, nodes, *, seed, dt0, level, refine=2, n_paths, max_st
     mean, var, fm, cm = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)
     diff = np.zeros((n, n_paths)) if dump_paths else None
     steps = np.zeros((n, n_paths), dtype=np.int32) if dump_paths else None
+    aux = np.zeros((n, n_paths, 8)) if dump_paths else None
     cap = ctypes.c_int64(0)
     rc = lib.orc_mlmc_level(ctypes.byref(P), _ptr(nodes, ctypes.c_double), n, ctypes.byref(M),
                             int(level), int(refine), _ptr(mean, ctypes.c_double),
                             _ptr(var, ctypes.c_double), _ptr(fm, ctypes.c_double),
                             _ptr(cm, ctypes.c_double), _ptr(diff, ctypes.c_double),
-                            _ptr(steps, ctypes.c_int32), ctypes.byref(cap))
+                            _ptr(steps, ctypes.c_int32), ctypes.byref(cap),
+                            _ptr(aux, ctypes.c_double))
     if rc != 0:
         raise ValueError("oracle mlmc_level: invalid arguments")
     out = {"mean": mean, "var": var, "fine_mean": fm, "coarse_mean": cm, "capped": cap.value}
     if dump_paths:
-        out["diff"], out["steps"] = diff, steps
+        # aux per pair: fine score, coarse score, fine exit step, coarse exit
+        # step (in coarse steps; negative: capped), fine and coarse exit points
+        out["diff"], out["steps"], out["aux"] = diff, steps, aux
     return out
 
 

@@ -999,6 +999,7 @@ typedef struct {
   double X[3], Y, Z;
   int done;
   double score;
+  double xe[3];  /* exit point, set when the walk ends */
 } mlmc_walk;
 
 /* One Euler-Maruyama step of a walk with time step dt and Brownian increment
@@ -1019,6 +1020,7 @@ static void mlmc_step(const orc_problem *P, const orc_mc *M, double dt, const do
     double xe[3] = {0, 0, 0};
     segment_exit(geom, dim, w->X, Xn, xe);
     w->score = coef_g(P, xe) * Yn + Zn;
+    for (int k = 0; k < 3; ++k) w->xe[k] = xe[k];
     w->done = 1;
     return;
   }
@@ -1037,6 +1039,7 @@ static void mlmc_step(const orc_problem *P, const orc_mc *M, double dt, const do
       double xe[3] = {Xn[0], Xn[1], Xn[2]};
       face_project(geom, jbest, xe);
       w->score = coef_g(P, xe) * Yn + Zn;
+      for (int k = 0; k < 3; ++k) w->xe[k] = xe[k];
       w->done = 1;
       return;
     }
@@ -1050,6 +1053,7 @@ static void mlmc_cap(const orc_problem *P, mlmc_walk *w) {
   double xe[3] = {w->X[0], w->X[1], w->X[2]};
   face_project(P->geometry, nearest_face(P->geometry, P->dim, w->X), xe);
   w->score = coef_g(P, xe) * w->Y + w->Z;
+  for (int k = 0; k < 3; ++k) w->xe[k] = xe[k];
   w->done = 1;
 }
 
@@ -1061,6 +1065,7 @@ typedef struct {
   double *mean, *var, *fine_mean, *coarse_mean, *path_diff;
   int32_t *path_steps;
   int64_t *capped;
+  double *path_aux;  /* [n][N][8] per-walk records (scores, exit steps, exit points), or NULL */
 } mlmc_ctx;
 
 static void mlmc_node(void *vp, int64_t i) {
@@ -1077,7 +1082,7 @@ static void mlmc_node(void *vp, int64_t i) {
   for (int64_t p = 0; p < N; ++p) {
     mlmc_walk fw, cw;
     memset(&fw, 0, sizeof fw);
-    for (int k = 0; k < dim; ++k) fw.X[k] = C->nodes[i * dim + k];
+    for (int k = 0; k < dim; ++k) fw.X[k] = fw.xe[k] = C->nodes[i * dim + k];
     fw.Y = 1.0;
     cw = fw;
     if (!inside_open(P->geometry, dim, fw.X)) {
@@ -1086,7 +1091,7 @@ static void mlmc_node(void *vp, int64_t i) {
     }
     if (l == 0) cw.done = 1;
     double dWc[3] = {0, 0, 0};
-    int64_t k = 0;
+    int64_t k = 0, kf = 0, kc = 0;  /* fine steps; exit steps of the two walks */
     while (!(fw.done && cw.done) && k < M->max_steps) {
       uint32_t ctr[4] = {(uint32_t)k, (uint32_t)p, (uint32_t)i, 16u + (uint32_t)l}, w[4];
       orc_philox4x32_10(ctr, key, w);
@@ -1094,16 +1099,33 @@ static void mlmc_node(void *vp, int64_t i) {
       box_muller(w[0], w[1], &z0, &z1);
       const double dW[3] = {sdf * z0, dim > 1 ? sdf * z1 : 0.0, 0.0};
       const double U = unif(w[2]);
-      if (!fw.done) mlmc_step(P, M, dtf, dW, U, &fw);
+      if (!fw.done) {
+        mlmc_step(P, M, dtf, dW, U, &fw);
+        if (fw.done) kf = k + 1;
+      }
       for (int d = 0; d < dim; ++d) dWc[d] += dW[d];
       ++k;
       if (l > 0 && k % R == 0) {
-        if (!cw.done) mlmc_step(P, M, dtf * R, dWc, U, &cw);
+        if (!cw.done) {
+          mlmc_step(P, M, dtf * R, dWc, U, &cw);
+          if (cw.done) kc = k / R;
+        }
         dWc[0] = dWc[1] = dWc[2] = 0.0;
       }
     }
-    if (!fw.done) { mlmc_cap(P, &fw); ++caps; }
-    if (l > 0 && !cw.done) { mlmc_cap(P, &cw); ++caps; }
+    if (!fw.done) { mlmc_cap(P, &fw); kf = -k; ++caps; }
+    if (l > 0 && !cw.done) { mlmc_cap(P, &cw); kc = -(k / R); ++caps; }
+    if (C->path_aux) {
+      double *o = C->path_aux + (i * N + p) * 8;
+      o[0] = fw.score;
+      o[1] = l > 0 ? cw.score : 0.0;
+      o[2] = (double)kf;
+      o[3] = l > 0 ? (double)kc : 0.0;
+      o[4] = fw.xe[0];
+      o[5] = dim > 1 ? fw.xe[1] : 0.0;
+      o[6] = l > 0 ? cw.xe[0] : 0.0;
+      o[7] = l > 0 && dim > 1 ? cw.xe[1] : 0.0;
+    }
     const double y = l > 0 ? fw.score - cw.score : fw.score;
     const double d = y - m;
     m += d / (double)(p + 1);
@@ -1123,13 +1145,13 @@ static void mlmc_node(void *vp, int64_t i) {
 int orc_mlmc_level(const orc_problem *P, const double *nodes, int64_t n, const orc_mc *M,
                    int32_t level, int32_t refine, double *mean, double *var,
                    double *fine_mean, double *coarse_mean, double *path_diff,
-                   int32_t *path_steps, int64_t *total_capped) {
+                   int32_t *path_steps, int64_t *total_capped, double *path_aux) {
   if (!P || !M || n < 0 || M->n_paths < 1 || !(M->dt > 0.0) || P->dim < 1 || P->dim > 2 ||
       M->max_steps < 1 || level < 0 || level > 12 || refine < 2 || refine > 16)
     return 1;
   int64_t *cap = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   mlmc_ctx C = {P, M, nodes, level, refine, mean, var, fine_mean, coarse_mean,
-                path_diff, path_steps, cap};
+                path_diff, path_steps, cap, path_aux};
   parallel_for(n, M->n_threads, mlmc_node, &C);
   int64_t tc = 0;
   for (int64_t i = 0; i < n; ++i) tc += cap[i];
@@ -1417,6 +1439,7 @@ typedef struct {
   double *path_score;
   int32_t *path_steps;
   int64_t *steps_per_node;
+  double *path_exit;  /* [n][N][2] stopping points (projected), or NULL */
 } wos_ctx;
 
 static void wos_node(void *vp, int64_t i) {
@@ -1456,6 +1479,10 @@ static void wos_node(void *vp, int64_t i) {
     steps_total += n;
     if (W->path_score) W->path_score[i * N + p] = sc;
     if (W->path_steps) W->path_steps[i * N + p] = (int32_t)n;
+    if (W->path_exit) {
+      W->path_exit[(i * N + p) * 2] = X[0];
+      W->path_exit[(i * N + p) * 2 + 1] = X[1];
+    }
   }
   W->mean[i] = mean;
   W->se[i] = N > 1 ? sqrt(m2 / (double)(N - 1) / (double)N) : 0.0;
@@ -1466,12 +1493,13 @@ static void wos_node(void *vp, int64_t i) {
 int orc_wos_solve(const orc_problem *P, const double *nodes, int64_t n,
                   const int64_t *node_ids, const orc_mc *M, double eps,
                   double *mean, double *se, int64_t *npaths, double *path_score,
-                  int32_t *path_steps, int64_t *total_steps) {
+                  int32_t *path_steps, int64_t *total_steps, double *path_exit) {
   if (!P || P->kind != ORC_PROB_LAPLACE_EXPCOS || P->dim != 2 || !M ||
       M->n_paths < 1 || !(eps > 0.0))
     return 1;
   int64_t *spn = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
-  wos_ctx W = {P, M, nodes, node_ids, eps, mean, se, npaths, path_score, path_steps, spn};
+  wos_ctx W = {P,          M,          nodes, node_ids, eps, mean, se, npaths,
+               path_score, path_steps, spn,   path_exit};
   parallel_for(n, M->n_threads, wos_node, &W);
   int64_t ts = 0;
   for (int64_t i = 0; i < n; ++i) ts += spn[i];

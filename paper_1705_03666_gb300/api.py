@@ -228,8 +228,10 @@ class Context:
             if dump_paths:
                 res["diff"] = torch.empty((n, int(n_paths)), dtype=_F64, device=self.device)
                 res["steps"] = torch.empty((n, int(n_paths)), dtype=_I32, device=self.device)
+                res["aux"] = torch.empty((n, int(n_paths), 8), dtype=_F64, device=self.device)
                 dg.d_path_score = res["diff"].data_ptr()
                 dg.d_path_steps = res["steps"].data_ptr()
+                dg.d_path_aux = res["aux"].data_ptr()
         with torch.cuda.device(self.device):
             self._bind_stream()
             st = self.lib.pdd_mlmc_level(self.handle, nodes.data_ptr(), n, ctypes.byref(mp),
@@ -543,8 +545,10 @@ class Context:
             if dump_paths:
                 res["score"] = torch.empty((n, int(n_paths)), dtype=_F64, device=self.device)
                 res["steps"] = torch.empty((n, int(n_paths)), dtype=_I32, device=self.device)
+                res["exit"] = torch.empty((n, int(n_paths), 2), dtype=_F64, device=self.device)
                 dg.d_path_score = res["score"].data_ptr()
                 dg.d_path_steps = res["steps"].data_ptr()
+                dg.d_path_exit = res["exit"].data_ptr()
         with torch.cuda.device(self.device):
             self._bind_stream()
             st = self.lib.pdd_wos_solve(self.handle, nodes.data_ptr(), n, ctypes.byref(wp),

@@ -35,6 +35,7 @@ struct MlmcArgs {
   unsigned long long *counters;  // [0] fine steps, [1] capped walks, [2] bad nodes
   void *score;                   // R[3][wave]: difference, fine, coarse
   int32_t *steps;
+  double *aux;                   // [end - begin][8] per-walk records, or null
   RoundKeys rk;
   double dtf, sdtf, s2;          // fine step, sqrt(fine step), sigma^2
   int32_t level, refine, max_steps, bridge;
@@ -71,6 +72,7 @@ __device__ __forceinline__ double mlmc_bound(const MlmcStep<double> &c, double m
 template <class Model, class Geom, typename R>
 struct MlmcWalk {
   R X[2], Y, Z, s;
+  R xe[2];  // exit point (set when the walk ends)
   bool done;
 
   // One Euler step with the (unscaled-by-sigma) increment dW.  A lower bound
@@ -87,7 +89,6 @@ struct MlmcWalk {
     const R mn = Geom::screen_lb(X, Xn);
     if (!(mn > R(0)) || U < mlmc_bound(c, mn)) {
       if (!Geom::inside_closed(Xn)) {
-        R xe[2];
         Geom::segment_exit(X, Xn, xe);
         s = Model::g(a.mc, xe) * Y + Zn;
         done = true;
@@ -109,7 +110,8 @@ struct MlmcWalk {
           }
         }
         if (jb >= 0 && U < P) {
-          R xe[2] = {Xn[0], Xn[1]};
+          xe[0] = Xn[0];
+          xe[1] = Xn[1];
 #pragma unroll
           for (int j = 0; j < Geom::kFaces; ++j)
             if (j == jb) Geom::project(j, xe);
@@ -124,7 +126,8 @@ struct MlmcWalk {
     Z = Zn;
   }
   __device__ __forceinline__ void cap(const MlmcArgs &a) {
-    R xe[2] = {X[0], X[1]};
+    xe[0] = X[0];
+    xe[1] = X[1];
     const int jn = Geom::nearest_face(X);
 #pragma unroll
     for (int j = 0; j < Geom::kFaces; ++j)
@@ -149,11 +152,26 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
   PhiloxPath pp{0, 0, 0};
   uint64_t slot = 0;
   int32_t k = 0, kc = 0;  // fine steps; fine steps since the last coarse step
+  int32_t kf = 0, kcs = 0;  // exit steps of the fine and coarse walks
   bool active = false, need = true;
   unsigned long long my_steps = 0, my_capped = 0, my_bad = 0;
   WarpQueue wq;
   NodeCache<R, D> nc;
   const unsigned long long total = a.end - a.begin;
+  // per-walk record of a finished pair (parity checks): scores, exit steps
+  // (fine steps, coarse steps) and exit points of the fine and coarse walks
+  auto write_aux = [&]() {
+    if (!a.aux) return;
+    double *o = a.aux + 8 * slot;
+    o[0] = static_cast<double>(fw.s);
+    o[1] = a.level == 0 ? 0.0 : static_cast<double>(cw.s);
+    o[2] = static_cast<double>(kf);
+    o[3] = a.level == 0 ? 0.0 : static_cast<double>(kcs);
+    o[4] = static_cast<double>(fw.xe[0]);
+    o[5] = static_cast<double>(fw.xe[1]);
+    o[6] = a.level == 0 ? 0.0 : static_cast<double>(cw.xe[0]);
+    o[7] = a.level == 0 ? 0.0 : static_cast<double>(cw.xe[1]);
+  };
   for (;;) {
     if (claim_time(active)) {
       need = !active;
@@ -175,9 +193,15 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
           dWc[0] = dWc[1] = R(0);
           k = 0;
           kc = 0;
+          kf = 0;
+          kcs = 0;
+          fw.xe[0] = cw.xe[0] = fw.X[0];
+          fw.xe[1] = cw.xe[1] = fw.X[1];
           if (!Geom::inside_closed(fw.X)) {
             out[slot] = out[a.wave + slot] = out[2 * a.wave + slot] = R(NAN);
             if (a.steps) a.steps[slot] = 0;
+            fw.s = cw.s = R(NAN);
+            write_aux();
             ++my_bad;
             need = true;
           } else if (!Geom::inside_open(fw.X)) {
@@ -186,6 +210,8 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
             out[a.wave + slot] = g0;
             out[2 * a.wave + slot] = a.level == 0 ? R(0) : g0;
             if (a.steps) a.steps[slot] = 0;
+            fw.s = cw.s = g0;
+            write_aux();
             need = true;
           } else {
             active = true;
@@ -202,12 +228,18 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
     box_muller<R>(w.x, w.y, z0, z1);
     const R dW[2] = {sdtf * z0, D > 1 ? sdtf * z1 : R(0)};
     const R U = unif<R>(w.z);
-    if (!fw.done) fw.step(a, cf, dW, U);
+    if (!fw.done) {
+      fw.step(a, cf, dW, U);
+      if (fw.done) kf = k + 1;
+    }
     dWc[0] += dW[0];
     dWc[1] += dW[1];
     ++k;
     if (a.level > 0 && ++kc == a.refine) {
-      if (!cw.done) cw.step(a, cc, dWc, U);
+      if (!cw.done) {
+        cw.step(a, cc, dWc, U);
+        if (cw.done) kcs = k / a.refine;
+      }
       dWc[0] = dWc[1] = R(0);
       kc = 0;
     }
@@ -215,10 +247,12 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
     if (!finish && k >= a.max_steps) {
       if (!fw.done) {
         fw.cap(a);
+        kf = -k;
         ++my_capped;
       }
       if (!cw.done) {
         cw.cap(a);
+        kcs = -(k / a.refine);
         ++my_capped;
       }
       finish = true;
@@ -228,6 +262,7 @@ __global__ void __launch_bounds__(kPathBlock) mlmc_kernel(const __grid_constant_
       out[a.wave + slot] = fw.s;
       out[2 * a.wave + slot] = a.level == 0 ? R(0) : cw.s;
       if (a.steps) a.steps[slot] = k;
+      write_aux();
       my_steps += static_cast<unsigned long long>(k);
       active = false;
     }
@@ -303,6 +338,7 @@ static pdd_status run_mlmc(pdd_ctx *ctx, const double *d_nodes, int64_t n, const
     a.begin = b0;
     a.end = b1;
     a.steps = (diag && diag->d_path_steps) ? diag->d_path_steps + b0 : nullptr;
+    a.aux = (diag && diag->d_path_aux) ? diag->d_path_aux + 8 * b0 : nullptr;
     const auto ev = prof_slot(ctx);
     if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
     kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);

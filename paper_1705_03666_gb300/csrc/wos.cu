@@ -25,6 +25,7 @@ struct WosArgs {
   unsigned long long *counters;  // [0] jumps, [1] capped, [2] bad nodes
   void *score;
   int32_t *steps;
+  double *exit;                  // [end - begin][2] stopping points (projected), or null
   RoundKeys rk;
   double eps;
   int32_t max_steps;
@@ -85,6 +86,10 @@ __global__ void __launch_bounds__(kPathBlock) wos_kernel(const __grid_constant__
       if (pending) {
         score[slot] = LaplaceExpCos::g<R>(a.mc, X);
         if (a.steps) a.steps[slot] = n;
+        if (a.exit) {
+          a.exit[2 * slot] = static_cast<double>(X[0]);
+          a.exit[2 * slot + 1] = static_cast<double>(X[1]);
+        }
         my_steps += static_cast<unsigned long long>(n);
         pending = false;
       }
@@ -103,6 +108,10 @@ __global__ void __launch_bounds__(kPathBlock) wos_kernel(const __grid_constant__
           if (!Geom::inside_closed(X)) {
             score[slot] = R(NAN);
             if (a.steps) a.steps[slot] = 0;
+            if (a.exit) {
+              a.exit[2 * slot] = static_cast<double>(X[0]);
+              a.exit[2 * slot + 1] = static_cast<double>(X[1]);
+            }
             ++my_bad;
             need = true;
           } else {
@@ -187,6 +196,7 @@ static pdd_status run_wos(pdd_ctx *ctx, const double *d_nodes, int64_t n, const 
     a.begin = b0;
     a.end = b1;
     a.steps = (diag && diag->d_path_steps) ? diag->d_path_steps + b0 : nullptr;
+    a.exit = (diag && diag->d_path_exit) ? diag->d_path_exit + 2 * b0 : nullptr;
     const auto ev = prof_slot(ctx);
     if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
     kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);

@@ -2,7 +2,8 @@
 Eq. 3.2 absorbing boundaries) against the FP64 oracle on shared Philox
 streams.  Integer tick times make every walk's cut points identical on both
 sides; binary32 positions can move a rare exit decision, which changes that
-tree's step count ("flip", counted).  Node means over matched trees agree to
+tree's step count ("flip", counted).  Every other tree agrees at every grid
+time within a per-tree binary32 bound, and node means over them agree to
 1e-5 relative at every grid time."""
 import numpy as np
 import pytest
@@ -13,7 +14,8 @@ from paper_1705_03666_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 NODE_REL_TOL = 1e-5
-TREE_TOL = 1e-4
+TREE_FACTOR = 4.0      # per-tree bound in units of 2^-22 (steps + 8) max(1, |s|); measured 1.33
+FLIP_MAX = 2e-4        # measured on GB300: no flips in these cases
 T8 = np.arange(1, 9) / 8.0
 
 
@@ -27,24 +29,33 @@ def api():
 
 
 def _parity(api, orc, prob, nodes, times, flip_max, **kw):
+    """Tree by tree: a different step count, or a tree pruned on one side
+    only, is a flip (counted); every other tree must agree at every grid
+    time within the per-tree bound TREE_FACTOR 2^-22 (steps + 8) max(1, |s|)
+    (binary32 positions and per-time products; none may exceed it).  Node
+    means over the unflipped trees within 1e-5 at every grid time."""
     o = orc.branching_grid_solve(prob, nodes, times, dump_trees=True, **kw)
     with api.Context(prob) as ctx:
         g = ctx.branching_grid_solve(torch.from_numpy(nodes), times, dump_trees=True, **kw)
     sg, so = g["score"].cpu().numpy(), o["score"]
     stg, sto = g["tree_steps"].cpu().numpy(), o["steps"]
     nan_g, nan_o = np.isnan(sg).any(2), np.isnan(so).any(2)
-    ok = ~nan_g & ~nan_o
-    close = np.all(np.abs(sg - so) <= TREE_TOL * np.maximum(1.0, np.abs(so)), axis=2)
-    matched = ok & (stg == sto) & close
-    flip = 1.0 - matched.sum() / max(1, ok.sum())
-    assert flip <= flip_max, flip
-    # pruning decisions agree except on flipped trees
-    assert np.mean(nan_g != nan_o) <= flip_max
-    cnt = matched.sum(1)
+    same = (stg == sto) & (nan_g == nan_o)
+    m = same & ~nan_o
+    unit = 2.0 ** -22 * (np.abs(sto)[:, :, None] + 8.0) * np.maximum(1.0, np.abs(so))
+    ratio = np.where(m[:, :, None], np.abs(sg - so) / unit, 0.0)
+    mismatch = int((ratio.max(2) > TREE_FACTOR).sum())
+    flip = 1.0 - same.mean()
+    cnt = m.sum(1)
     assert cnt.min() > 0
-    mg = np.where(matched[:, :, None], sg, 0).sum(1) / cnt[:, None]
-    mo = np.where(matched[:, :, None], so, 0).sum(1) / cnt[:, None]
+    mg = np.where(m[:, :, None], sg, 0).sum(1) / cnt[:, None]
+    mo = np.where(m[:, :, None], so, 0).sum(1) / cnt[:, None]
     rel = np.abs(mg - mo) / np.maximum(np.abs(mo), 0.05)
+    print(f"[parity] grid trees {prob['geometry']} {prob['params'][1]:.0f}: flips {flip:.2e} "
+          f"({int((~same).sum())} of {same.size}), mismatches {mismatch}, max ratio to "
+          f"2^-22 (steps + 8) {ratio.max():.3f}, max node rel {rel.max():.2e}")
+    assert mismatch == 0, ratio.max()
+    assert flip <= flip_max, flip
     assert rel.max() <= NODE_REL_TOL, rel.max()
     return g, o, flip
 
@@ -53,24 +64,24 @@ def test_bounded_square_travelling_wave(api, orc):
     beta = 4.0
     prob = W.kpp("travelling", np.sqrt(beta / 3), beta, geometry="unit_square")
     nodes = np.array([[0.5, 0.5], [0.25, 0.3], [0.8, 0.6], [0.05, 0.5], [0.5, 0.97]])
-    g, o, flip = _parity(api, orc, prob, nodes, T8, 2e-3, seed=W.SEED_BASE + 41, n_trees=3000, dt=1e-3)
+    g, o, flip = _parity(api, orc, prob, nodes, T8, FLIP_MAX, seed=W.SEED_BASE + 41, n_trees=3000, dt=1e-3)
     assert g["steps"] > 0
 
 
 def test_bounded_lshape_constant_and_interval_sine(api, orc):
     prob = W.kpp("const", 0.3, 2.0, geometry="l_shape")
     nodes = np.array([[0.25, 0.75], [0.45, 0.45], [0.75, 0.25], [0.49, 0.2]])
-    _parity(api, orc, prob, nodes, T8, 2e-3, seed=5, n_trees=3000, dt=2e-3)
+    _parity(api, orc, prob, nodes, T8, FLIP_MAX, seed=5, n_trees=3000, dt=2e-3)
     prob = W.kpp("sine", 0.0, 1e-12, dim=1, geometry="interval")
     _parity(api, orc, prob, np.array([[0.5], [0.2], [0.9]]), np.array([0.02, 0.05, 0.1, 0.2]),
-            2e-3, seed=6, n_trees=3000, dt=1e-4)
+            FLIP_MAX, seed=6, n_trees=3000, dt=1e-4)
 
 
 def test_bridge_off_and_marked_law(api, orc):
     prob = W.kpp("travelling", 0.5, 1.0, geometry="unit_square", q=(0.2, 0.3, 0.5),
                  alpha=(0.5, -0.2, 0.7))
     nodes = np.array([[0.5, 0.5], [0.3, 0.8]])
-    _parity(api, orc, prob, nodes, T8, 2e-3, seed=7, n_trees=3000, dt=1e-3, bridge=False)
+    _parity(api, orc, prob, nodes, T8, FLIP_MAX, seed=7, n_trees=3000, dt=1e-3, bridge=False)
 
 
 @pytest.mark.parametrize("dim", [1, 2])
@@ -78,12 +89,12 @@ def test_free_space_grid(api, orc, dim):
     prob = W.kpp("sigmoid", 4.0, 1.0, dim=dim)
     nodes = W.nodes_kpp(n_x2=4, n_t=1)[:, :dim]
     times = np.arange(1, 17) / 16.0
-    _parity(api, orc, prob, nodes, times, 1e-3, seed=W.SEED_BASE + 42, n_trees=2000)
+    _parity(api, orc, prob, nodes, times, FLIP_MAX, seed=W.SEED_BASE + 42, n_trees=2000)
 
 
 def test_pruning_matches_oracle(api, orc):
     prob = W.kpp("const", 0.5, 3.0, dim=1)
-    g, o, _ = _parity(api, orc, prob, np.array([[0.0]]), np.array([0.5, 1.0]), 1e-3, seed=8,
+    g, o, _ = _parity(api, orc, prob, np.array([[0.0]]), np.array([0.5, 1.0]), FLIP_MAX, seed=8,
                       n_trees=2000, max_particles=6, max_depth=4)
     assert o["discarded"][0] > 100
     with api.Context(prob) as ctx:

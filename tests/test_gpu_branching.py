@@ -1,9 +1,10 @@
 """GPU parity of pdd_branching_solve against the FP64 oracle (shared streams).
 
 Each tree consumes the same Philox words on both sides (depth-first particle
-ids), so trees are compared one by one: segment counts must match and scores
-agree to FP32 rounding of the positions, except for the rare tree whose
-FP32 time bookkeeping lands on the other side of t (counted).  Node means are
+ids), so trees are compared one by one: a tree whose FP32 time bookkeeping
+lands on the other side of t changes its segment count (a structure flip,
+counted), and every other tree's score must agree within a per-tree bound
+from the FP32 rounding of its positions and psi values (no exceptions).  Node means are
 also pinned to the closed forms of Sec. 3.1-3.2 and, at full size, to a
 Crank-Nicolson solution of the 1-D PDE (the data depend on x1 only).
 """
@@ -24,18 +25,37 @@ def api():
     return a
 
 
-def _tree_compare(g, o):
+# Per-tree bound on the score difference of trees with the same structure,
+# in units of 2^-22 (segments + 4) max(1, |s|): every segment rounds the
+# particle's binary32 position and evaluates psi with the hardware exp2 and
+# reciprocal (a few ulp), and the float-float product adds ~2^-44 per factor.
+# Measured on GB300: at most 1.08 of the unit.
+TREE_FACTOR = 4.0
+
+
+def _tree_compare(g, o, name):
+    """Tree by tree: a different segment count, or a tree pruned on one side
+    only, is a structure flip (counted); every other tree must agree within
+    the per-tree bound (none may exceed it).  Node means over the unflipped
+    trees, relative difference."""
     sg, so = g["score"].cpu().numpy(), o["score"]
     gg, go = g["segs"].cpu().numpy(), o["segments"]
-    both_nan = np.isnan(sg) & np.isnan(so)
-    close = np.abs(sg - so) <= 1e-5 * np.maximum(1.0, np.abs(so))
-    matched = (gg == go) & (both_nan | close)
-    m = matched & ~np.isnan(so)
+    nan_g, nan_o = np.isnan(sg), np.isnan(so)
+    same = (gg == go) & (nan_g == nan_o)
+    unit = 2.0 ** -22 * (np.abs(go) + 4.0) * np.maximum(1.0, np.abs(so))
+    ratio = np.where(same & ~nan_o, np.abs(sg - so) / unit, 0.0)
+    mismatch = int((ratio > TREE_FACTOR).sum())
+    m = same & ~nan_o
     cnt = m.sum(1)
     mg = np.where(m, sg, 0).sum(1) / np.maximum(cnt, 1)
     mo = np.where(m, so, 0).sum(1) / np.maximum(cnt, 1)
     rel = np.abs(mg - mo) / np.maximum(np.abs(mo), 1e-3)
-    return 1.0 - matched.mean(), rel
+    flips = 1.0 - same.mean()
+    print(f"[parity] {name}: tree flips {flips:.2e} ({int((~same).sum())} of {same.size}), "
+          f"mismatches {mismatch}, max ratio to 2^-22 (segs + 4) {ratio.max():.3f}, "
+          f"max node rel {rel.max():.2e}")
+    assert mismatch == 0, (name, ratio.max())
+    return flips, rel
 
 
 @pytest.mark.parametrize("prob_args,dim", [
@@ -54,8 +74,7 @@ def test_trees_match_oracle(api, orc, prob_args, dim):
     with api.Context(prob) as ctx:
         g = ctx.branching_solve(torch.from_numpy(nodes), dump_trees=True, **kw)
     o = orc.branching_solve(prob, nodes, dump_trees=True, **kw)
-    flips, rel = _tree_compare(g, o)
-    print(f"{prob_args['psi']}: tree flips {flips:.2e}, max node rel {rel.max():.2e}")
+    flips, rel = _tree_compare(g, o, f"trees {prob_args['psi']} d={dim}")
     assert flips <= 1e-4
     assert rel.max() <= 1e-5
     assert g["segments"] == int(np.abs(o["segments"]).sum())

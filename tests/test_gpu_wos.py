@@ -2,21 +2,22 @@
 the FP64 oracle on shared Philox streams (tag 2).  The FP64 kernel must
 reproduce every walk's jump count and score to rounding; the FP32 kernel's
 walks may stop one jump apart where a distance sits at eps to within
-binary32 rounding (counted, rare), and node means over matched walks agree
-to 1e-5 relative.  Binary32 positions carry ~1e-7 of rounding after a walk
-and the final distance has a density ~1/eps near eps, so at eps = 1e-4 a few
-walks in a thousand stop one jump apart (more near the L-shape's re-entrant
-corner, where walks take more jumps)."""
+binary32 rounding, or at points far apart after rounding grew over the
+jumps (counted exit flips), every other walk agrees within its binary32
+bound, and node means over those walks agree to 1e-5 relative."""
 import numpy as np
 import pytest
 import torch
 
 from paper_1705_03666_gb300 import workloads as W
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-NODE_REL_TOL = 1e-5
-FLIP_MAX_FP32 = 1e-2
+# exit flips measured on GB300 (eps = 1e-4): 4.7e-5 on the square, 5.8e-3 on
+# the L-shape, almost all of them stopping points more than 1e-3 apart after
+# the same number of jumps (see test_fp32_matches_oracle)
+FLIP_MAX_FP32 = {"unit_square": 2e-4, "l_shape": 1e-2}
 L_NODES = np.array([[0.25, 0.75], [0.75, 0.25], [0.4, 0.4], [0.1, 0.5], [0.5, 0.45],
                     [0.45, 0.5], [0.49, 0.49], [0.05, 0.95]])
 
@@ -30,12 +31,6 @@ def api():
     return a
 
 
-def _matched(g, o, tol):
-    sg, stg = g["score"].cpu().numpy(), g["steps"].cpu().numpy()
-    m = (stg == o["steps"]) & (np.abs(sg - o["score"]) <= tol * np.maximum(1.0, np.abs(o["score"])))
-    return m, sg
-
-
 @pytest.mark.parametrize("geom,nodes", [("unit_square", W.nodes_cfg1(16)), ("l_shape", L_NODES)])
 def test_fp64_walk_by_walk(api, orc, geom, nodes):
     prob = W.laplace_expcos(geom)
@@ -43,9 +38,9 @@ def test_fp64_walk_by_walk(api, orc, geom, nodes):
     o = orc.wos_solve(prob, nodes, dump_paths=True, **kw)
     with api.Context(prob) as ctx:
         g = ctx.wos_solve(torch.from_numpy(nodes), precision="fp64", dump_paths=True, diag=True, **kw)
-    m, sg = _matched(g, o, 1e-9)
-    assert m.mean() >= 1 - 1e-4, 1 - m.mean()
-    if m.all():
+    c = parity.compare_paths(g, o, path_tol=1e-9, geometry=geom)
+    parity.check(f"wos {geom} fp64", c, flip_max=1e-4)
+    if c["same"].all():
         np.testing.assert_allclose(g["mean"].cpu().numpy(), o["mean"], rtol=1e-11, atol=1e-12)
         np.testing.assert_allclose(g["se"].cpu().numpy(), o["se"], rtol=1e-8, atol=1e-13)
     assert g["path_steps"] == int(g["steps"].cpu().numpy().astype(np.int64).sum())
@@ -54,17 +49,22 @@ def test_fp64_walk_by_walk(api, orc, geom, nodes):
 
 @pytest.mark.parametrize("geom,nodes", [("unit_square", W.nodes_cfg1(16)), ("l_shape", L_NODES)])
 def test_fp32_matches_oracle(api, orc, geom, nodes):
+    """Walk by walk: a walk that stops after another number of jumps, on
+    another face, or at a point more than 1e-3 from the oracle's is an exit
+    flip (counted); every other walk's score must lie within the binary32
+    per-path bound of the parity helper (n = jumps, plus |grad g| times the
+    distance of the two stopping points), and the node means over them
+    within 1e-5.  A jump x -> x + d(x) e can double a position error (d has
+    unit gradient), so over a dozen jumps binary32 rounding can grow to
+    ~1e-3 on a few walks; the L-shape's walks take more jumps near its
+    re-entrant corner, hence its larger flip fraction."""
     prob = W.laplace_expcos(geom)
     kw = dict(seed=W.SEED_BASE + 11, n_paths=4000, eps=1e-4)
     o = orc.wos_solve(prob, nodes, dump_paths=True, **kw)
     with api.Context(prob) as ctx:
         g = ctx.wos_solve(torch.from_numpy(nodes), precision="fp32", dump_paths=True, **kw)
-    m, sg = _matched(g, o, 1e-4)
-    assert 1 - m.mean() <= FLIP_MAX_FP32, 1 - m.mean()
-    cnt = m.sum(1)
-    mg = np.where(m, sg, 0).sum(1) / cnt
-    mo = np.where(m, o["score"], 0).sum(1) / cnt
-    assert np.all(np.abs(mg - mo) <= NODE_REL_TOL * np.maximum(np.abs(mo), 0.1)), np.abs(mg - mo).max()
+    c = parity.compare_paths(g, o, prob=prob, geometry=geom)
+    parity.check(f"wos {geom} fp32", c, flip_max=FLIP_MAX_FP32[geom])
 
 
 def test_path_offset_waves_and_launch_shape(api, orc):
