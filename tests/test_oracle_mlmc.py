@@ -55,3 +55,26 @@ def test_level_variances_decay(orc):
         assert np.all(V[l + 1] < 0.95 * V[l]), (l, V[l], V[l + 1])
     # the finest pair of levels decays at least like R^-1/4 per level on average
     assert np.all(V[4] < V[1] * 0.5 ** 0.75)
+
+
+def test_dumped_walk_records(orc):
+    """The per-pair records: the pair's difference is the fine score minus
+    the coarse score; each walk's exit point lies on the boundary with its
+    score g there (e^x cos y; no source or killing in this family); the fine
+    walk's exit step is the pair's step count or less, and the coarse exit
+    step times the refinement is within one coarse step of it."""
+    prob = W.laplace_expcos()
+    nodes = np.array([[0.3, 0.4], [0.6, 0.7]])
+    r = orc.mlmc_level(prob, nodes, seed=5, dt0=4e-3, level=2, refine=2, n_paths=400,
+                       dump_paths=True)
+    a = r["aux"]
+    np.testing.assert_array_equal(r["diff"], a[..., 0] - a[..., 1])
+    for which in (0, 1):
+        x = a[..., 4 + 2 * which:6 + 2 * which]
+        on = (x == 0.0) | (x == 1.0)
+        assert on.any(-1).all()
+        np.testing.assert_allclose(a[..., which], np.exp(x[..., 0]) * np.cos(x[..., 1]),
+                                   rtol=1e-13)
+    kf, kc = a[..., 2], a[..., 3]
+    assert np.all((kf > 0) & (kf <= r["steps"]) & (kc > 0))
+    assert np.all(np.maximum(kf, 2 * kc) == r["steps"])

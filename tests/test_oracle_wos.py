@@ -46,3 +46,20 @@ def test_boundary_node_and_streams(orc):
     sub = orc.wos_solve(W.laplace_expcos(), nodes[1:], node_ids=[1], seed=1, n_paths=50,
                         eps=1e-4, dump_paths=True)
     assert np.array_equal(sub["score"][0], r["score"][1])
+
+
+def test_dumped_stopping_points(orc):
+    """The per-walk records: each stopping point lies on the boundary (a
+    coordinate exactly on a face plane: 0, 1, or 1/2 on the L-shape's notch)
+    and the walk's score is g there, e^x cos y."""
+    for geom in ("unit_square", "l_shape"):
+        prob = W.laplace_expcos(geom)
+        nodes = np.array([[0.3, 0.4], [0.45, 0.2]])
+        r = orc.wos_solve(prob, nodes, seed=3, n_paths=300, eps=1e-3, dump_paths=True)
+        x = r["exit"]
+        planes = (0.0, 1.0, 0.5) if geom == "l_shape" else (0.0, 1.0)
+        on = np.zeros(x.shape[:2], dtype=bool)
+        for v in planes:
+            on |= (x[..., 0] == v) | (x[..., 1] == v)
+        assert on.all()
+        np.testing.assert_allclose(r["score"], np.exp(x[..., 0]) * np.cos(x[..., 1]), rtol=1e-15)
