@@ -50,6 +50,13 @@ ALG_SLOTS_PER_PATH_STEP = 105
 # (one Philox block 40, the lifetime's logarithm 2, a Box-Muller pair 10, the
 # move 4, psi 3, the tree product 1).
 ALG_SLOTS_PER_SEGMENT = 60
+# Algorithmic issue slots per path-step of the 2-D Poisson-Fourier path
+# (three quarters of a Philox block 30, word-to-uniform maps 6, a Box-Muller
+# pair 10, the drift -- sine and cosine of x and y, two eight-term Chebyshev
+# recurrences and two eight-term sums -- 38, the Euler update 5, the exit
+# tests 14, loop control 3); the gradient adds the 16 likelihood-ratio FMAs.
+ALG_SLOTS_PER_STEP_POISSON = 106
+ALG_SLOTS_PER_STEP_POISSON_GRAD = 122
 
 
 def _env_rank():
@@ -475,10 +482,18 @@ def run_other_workloads(api, dev) -> dict:
         gout = torch.ones(len(w["nodes"]), dtype=torch.float64, device=dev)
         ctx.interface_grad(nodes, grad_out=gout, jacobian=False, **kw)
         ms_g, _ = _timed(stream, lambda: ctx.interface_grad(nodes, grad_out=gout, **kw))
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = n_sm * 4 * 32 * 2070e6
         out["poisson_fourier_gradient"] = {
             "workload": w["name"], "forward_ms": ms_f, "gradient_ms": ms_g,
             "path_steps_per_s_forward": r["path_steps"] / (ms_f / 1e3),
             "path_steps_per_s_gradient": r["path_steps"] / (ms_g / 1e3),
+            "issue_roofline_frac_forward_at_2070mhz":
+                ALG_SLOTS_PER_STEP_POISSON * r["path_steps"] / (ms_f / 1e3) / peak,
+            "issue_roofline_frac_gradient_at_2070mhz":
+                ALG_SLOTS_PER_STEP_POISSON_GRAD * r["path_steps"] / (ms_g / 1e3) / peak,
+            "alg_slots_per_path_step": {"forward": ALG_SLOTS_PER_STEP_POISSON,
+                                        "gradient": ALG_SLOTS_PER_STEP_POISSON_GRAD},
             "outputs": "jacobian [2048, 80] + vjp (dtheta[64], dphi[16])"}
     w = W.workload(1)
     with api.Context(w["prob"], dev) as ctx:
