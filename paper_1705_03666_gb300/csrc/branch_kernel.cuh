@@ -145,7 +145,7 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
   uint32_t pw0 = 0;
   uint32_t next_id = 1;
   float ph = 1.0f, pl = 0.0f;
-  int32_t segments = 0;
+  uint32_t seg0 = 0;   // my_cnt at the tree's start
   // the lane's run of trees [g, gend) within the wave (at most 2^31 trees),
   // the next run [ng, ngend) held in reserve
   uint32_t g = 0, gend = 0, ng = 0, ngend = 0;
@@ -159,6 +159,7 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
   uint32_t nw0 = 0, nw1 = 0;
   bool active = false;
   unsigned long long my_segs = 0;
+  uint32_t my_cnt = 0, my_folded = 0;  // segments run by the lane (mod 2^32)
   uint32_t my_disc = 0;
   const uint32_t total = static_cast<uint32_t>(a.end - a.begin);
   const uint32_t lanes = gridDim.x * blockDim.x;
@@ -203,7 +204,7 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
     sp = 0;
     ph = 1.0f;
     pl = 0.0f;
-    segments = 0;
+    seg0 = my_cnt;
   };
   // move to the reserve run when the current one is used up; false if none
   auto have_tree = [&]() -> bool {
@@ -244,6 +245,8 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
       begin_tree();
       active = true;
     }
+    my_segs += my_cnt - my_folded;
+    my_folded = my_cnt;
     if (!__any_sync(kFull, active)) {
       if (exhausted) break;
       continue;
@@ -263,7 +266,7 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
       const float h = sqrt_approx(tend - tb);
       x0 += h * z0;
       if (D == 2) x1 += h * z1;
-      ++segments;
+      ++my_cnt;
       uint32_t k = 2;
       float mark = 1.0f;
       if constexpr (!kBinary) {
@@ -318,13 +321,15 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
       if (done) {
         // the tree is done: its score, then the next tree of the lane's runs
         a.score[g] = bad ? NAN : ph + pl;
-        if (a.segs) a.segs[g] = bad ? -segments : segments;
+        if (a.segs) {
+          const int32_t segments = static_cast<int32_t>(my_cnt - seg0);
+          a.segs[g] = bad ? -segments : segments;
+        }
         if (bad) {
           ++my_disc;
           if (a.flags) atomicOr(a.flags + node, kNodeDiscarded);
         }
       }
-      my_segs += done ? static_cast<unsigned long long>(segments) : 0ull;
       g += done ? 1u : 0u;
       if (done && g >= gend) {
         g = ng;
@@ -343,7 +348,7 @@ branch_kernel(const __grid_constant__ BranchArgs a) {
         sp = 0;
         ph = 1.0f;
         pl = 0.0f;
-        segments = 0;
+        seg0 = my_cnt;
       }
     }
   }
