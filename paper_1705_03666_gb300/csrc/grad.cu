@@ -10,9 +10,9 @@
 //                      transition of the discrete scheme; the bridge uniform
 //                      and the exit rule do not depend on phi).
 // The path kernel runs in its gradient mode and writes one 80-byte record per
-// path (score, exit point, L); jac_reduce_kernel forms the per-node means of the
-// 80 components with compensated sums in a fixed order; vjp_kernel contracts them
-// with a cotangent over the nodes.
+// path (score, exit point, L); jac_reduce_kernel and jac_merge_kernel form the
+// per-node means of the 80 components with compensated sums in a fixed order;
+// vjp_kernel contracts them with a cotangent over the nodes.
 #include <cmath>
 #include <cstring>
 
@@ -30,48 +30,99 @@ constexpr int kJacGroups = kJacBlock / kJacLanes;
 // Per node (one block): for each path record, thread m of a path group forms
 // cos(m pi x) and, by the Chebyshev recurrence from cos(pi y), cos(n pi y) for
 // n = 0..7, and accumulates its eight theta components (8m + n) and the two
-// phi components m and 8 + m (s * L_j) with their squares as two-float sums
-// on the FP32 pipe (~48-bit; FP64 is a 1/64-rate pipe here); the 32 groups
-// are combined in FP64 in a fixed order and merged into the node's running
-// (count, mean, M2) per component (Chan).
-__global__ void __launch_bounds__(kJacBlock)
+// phi components m and 8 + m (s * L_j) with their squares.  A group takes
+// its records four at a time (records grp + 32 r of the block, r = 0..3):
+// thread m forms cos(pi y) of record m mod 4 once and the group shares the
+// four values by shuffles; the four contributions of each component are
+// summed in binary32 (error <= 3 u of their absolute sum) and the block sum
+// goes into a two-float sum on the FP32 pipe (~48-bit; FP64 is a 1/64-rate
+// pipe here), so a row carries at most 3 u of its mean absolute contribution
+// beyond the contributions' own evaluation.  The squares, which feed only the
+// standard error, take the same four-record blocks by FMA.  A node's records
+// of the wave are split into `parts` contiguous ranges, one block each (so
+// that a wave of a few hundred nodes still fills the GPU); a block combines
+// its 32 groups in FP64 in a fixed order and writes the part's two sums per
+// component, and jac_merge_kernel adds the parts in order and merges them
+// into the node's running (count, mean, M2) per component (Chan).
+// Merge a batch of nb records with sums S1, S2 of one component into the
+// node's running (count, mean, M2) (Chan).
+__device__ __forceinline__ void jac_chan_merge(NodeAcc *jacc, uint64_t node, int comp, double S1,
+                                               double S2, double nb) {
+  const double mean_b = S1 / nb;
+  const double m2_b = fmax(0.0, S2 - S1 * mean_b);
+  NodeAcc A = jacc[node * kJacW + comp];
+  const double nt = A.n + nb;
+  const double d = mean_b - A.mean;
+  A.mean = A.mean + d * (nb / nt);
+  A.m2 = A.m2 + m2_b + d * d * (A.n * nb / nt);
+  A.n = nt;
+  jacc[node * kJacW + comp] = A;
+}
+
+__global__ void __launch_bounds__(kJacBlock, 3)
 jac_reduce_kernel(const GradRec *__restrict__ rec, uint64_t begin, uint64_t end,
-                  uint64_t n_paths, uint64_t node_lo, NodeAcc *jacc) {
-  const uint64_t node = node_lo + blockIdx.x;
-  const uint64_t lo = max(begin, node * n_paths);
-  const uint64_t hi = min(end, (node + 1) * n_paths);
-  if (lo >= hi) return;
+                  uint64_t n_paths, uint64_t node_lo, int parts, double2 *part_sums,
+                  NodeAcc *jacc) {
+  constexpr int kRecs = 4;  // records per group and block
+  const uint64_t node = node_lo + blockIdx.x / parts;
+  const uint64_t part = blockIdx.x % parts;
+  const uint64_t nlo = max(begin, node * n_paths);
+  const uint64_t nhi = min(end, (node + 1) * n_paths);
+  const uint64_t ncnt = nhi > nlo ? nhi - nlo : 0;
+  const uint64_t lo = nlo + ncnt * part / parts;
+  const uint64_t hi = nlo + ncnt * (part + 1) / parts;
+  double2 *out = part_sums + static_cast<uint64_t>(blockIdx.x) * kJacW;
+  if (lo >= hi) {  // an empty part adds zeros
+    if (parts > 1 && threadIdx.x < kJacW) out[threadIdx.x] = make_double2(0.0, 0.0);
+    return;
+  }
   const GradRec *r = rec + (lo - begin);
   const uint64_t cnt = hi - lo;
   const int m = threadIdx.x % kJacLanes, grp = threadIdx.x / kJacLanes;
   const float fm = static_cast<float>(m);
   F2Sum s1[10], s2[10];  // two-float sums on the FP32 pipe (see reduce.cuh)
-  for (uint64_t p = grp; p < cnt; p += kJacGroups) {
-    const float x = r[p].x, y = r[p].y;
-    const float cxm = cospif(fm * x);
-    float sy1, cy1;
-    sincospif(y, &sy1, &cy1);
-    const float two_c = 2.0f * cy1;
-    float cprev = 1.0f, ccur = cy1;
-    float v[10];
-    v[0] = cxm;
-    v[1] = cxm * cy1;
+  // block-uniform trip count (the shuffles need every lane of the warp);
+  // records past the end contribute exact zeros
+  const uint64_t trips = (cnt + kJacGroups * kRecs - 1) / (kJacGroups * kRecs);
+  for (uint64_t it = 0; it < trips; ++it) {
+    const uint64_t base = it * (kJacGroups * kRecs) + grp;
+    const uint64_t py = min(base + kJacGroups * (m % kRecs), cnt - 1);
+    const float cy_own = cospif(r[py].y);
+    float t1[10], t2[10];
 #pragma unroll
-    for (int n = 2; n < 8; ++n) {
-      const float cn = two_c * ccur - cprev;
-      cprev = ccur;
-      ccur = cn;
-      v[n] = cxm * cn;
+    for (int c = 0; c < 10; ++c) t1[c] = t2[c] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kRecs; ++q) {
+      const uint64_t p = base + kJacGroups * q;
+      const bool ok = p < cnt;
+      const uint64_t pc = ok ? p : cnt - 1;
+      const float cy1 = __shfl_sync(kFull, cy_own, q, kJacLanes);
+      const float cxm = ok ? cospif(fm * r[pc].x) : 0.0f;
+      const float two_c = 2.0f * cy1;
+      float cprev = 1.0f, ccur = cy1;
+      float v[10];
+      v[0] = cxm;
+      v[1] = cxm * cy1;
+#pragma unroll
+      for (int n = 2; n < 8; ++n) {
+        const float cn = two_c * ccur - cprev;
+        cprev = ccur;
+        ccur = cn;
+        v[n] = cxm * cn;
+      }
+      const float sc = r[pc].s;
+      v[8] = ok ? sc * r[pc].L[m] : 0.0f;
+      v[9] = ok ? sc * r[pc].L[8 + m] : 0.0f;
+#pragma unroll
+      for (int c = 0; c < 10; ++c) {
+        t1[c] += v[c];
+        t2[c] = fmaf(v[c], v[c], t2[c]);
+      }
     }
-    const float sc = r[p].s;
-    v[8] = sc * r[p].L[m];
-    v[9] = sc * r[p].L[8 + m];
 #pragma unroll
     for (int c = 0; c < 10; ++c) {
-      s1[c].add(v[c]);
-      const float q = v[c] * v[c];
-      s2[c].add(q);
-      s2[c].lo += fmaf(v[c], v[c], -q);
+      s1[c].add(t1[c]);
+      s2[c].add(t2[c]);
     }
   }
   __shared__ double sh1[kJacGroups][kJacLanes * 10], sh2[kJacGroups][kJacLanes * 10];
@@ -91,17 +142,31 @@ jac_reduce_kernel(const GradRec *__restrict__ rec, uint64_t begin, uint64_t end,
     }
     const int mm = t / 10, c = t % 10;
     const int comp = c < 8 ? 8 * mm + c : (c == 8 ? 64 + mm : 72 + mm);
-    const double nb = static_cast<double>(cnt);
-    const double mean_b = S1 / nb;
-    const double m2_b = fmax(0.0, S2 - S1 * mean_b);
-    NodeAcc A = jacc[node * kJacW + comp];
-    const double nt = A.n + nb;
-    const double d = mean_b - A.mean;
-    A.mean = A.mean + d * (nb / nt);
-    A.m2 = A.m2 + m2_b + d * d * (A.n * nb / nt);
-    A.n = nt;
-    jacc[node * kJacW + comp] = A;
+    if (parts > 1)
+      out[comp] = make_double2(S1, S2);
+    else  // one part: merged here (part_sums unused)
+      jac_chan_merge(jacc, node, comp, S1, S2, static_cast<double>(cnt));
   }
+}
+
+// One block per node of the wave, one thread per component: the parts' sums
+// added in part order, then merged into the node's running (count, mean, M2)
+// (Chan).
+__global__ void jac_merge_kernel(const double2 *part_sums, uint64_t begin, uint64_t end,
+                                 uint64_t n_paths, uint64_t node_lo, int parts, NodeAcc *jacc) {
+  const int comp = threadIdx.x;
+  if (comp >= kJacW) return;
+  const uint64_t node = node_lo + blockIdx.x;
+  const uint64_t lo = max(begin, node * n_paths);
+  const uint64_t hi = min(end, (node + 1) * n_paths);
+  if (lo >= hi) return;
+  double S1 = 0.0, S2 = 0.0;
+  for (int q = 0; q < parts; ++q) {
+    const double2 v = part_sums[(static_cast<uint64_t>(blockIdx.x) * parts + q) * kJacW + comp];
+    S1 += v.x;
+    S2 += v.y;
+  }
+  jac_chan_merge(jacc, node, comp, S1, S2, static_cast<double>(hi - lo));
 }
 
 __global__ void jac_finalize_kernel(const NodeAcc *jacc, int64_t count, double *jac,
@@ -189,7 +254,13 @@ pdd_status interface_grad_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   const size_t jacc_off = 256;
   const size_t jac_off = align_up(jacc_off + static_cast<size_t>(n) * kJacW * sizeof(NodeAcc), 256);
   const size_t rec_off = align_up(jac_off + static_cast<size_t>(n) * kJacW * sizeof(double), 256);
-  const size_t bytes = align_up(rec_off + wave * sizeof(GradRec), 256);
+  // parts per node in the Jacobian reduction: four while a node has at least
+  // 4 x 8192 paths (a wave then holds few nodes), fewer below (fixed by
+  // n_paths, so the reduction order does not depend on the device)
+  const int parts = static_cast<int>(std::min<uint64_t>(4, std::max<uint64_t>(1, N / 8192)));
+  const uint64_t part_blocks = parts > 1 ? (wave / N + 2) * parts : 0;  // N >= 16384 here
+  const size_t part_off = align_up(rec_off + wave * sizeof(GradRec), 256);
+  const size_t bytes = align_up(part_off + part_blocks * kJacW * sizeof(double2), 256);
   pdd_status st = ensure_scratch(ctx, bytes);
   if (st != PDD_OK) return st;
   char *base = static_cast<char *>(ctx->scratch);
@@ -198,6 +269,7 @@ pdd_status interface_grad_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   auto *jacc = reinterpret_cast<NodeAcc *>(base + jacc_off);
   double *jac = reinterpret_cast<double *>(base + jac_off);
   auto *rec = reinterpret_cast<GradRec *>(base + rec_off);
+  auto *part_sums = reinterpret_cast<double2 *>(base + part_off);
   PDD_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, jac_off, ctx->stream));
 
   PathArgs a;
@@ -245,9 +317,14 @@ pdd_status interface_grad_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
     PDD_CUDA_TRY(ctx, cudaGetLastError());
     if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
     const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
-    jac_reduce_kernel<<<static_cast<unsigned>(node_hi - node_lo + 1), kJacBlock, 0, ctx->stream>>>(
-        rec, b0, b1, N, node_lo, jacc);
+    const unsigned nw = static_cast<unsigned>(node_hi - node_lo + 1);
+    jac_reduce_kernel<<<nw * parts, kJacBlock, 0, ctx->stream>>>(rec, b0, b1, N, node_lo, parts,
+                                                                  part_sums, jacc);
     PDD_CUDA_TRY(ctx, cudaGetLastError());
+    if (parts > 1) {
+      jac_merge_kernel<<<nw, 128, 0, ctx->stream>>>(part_sums, b0, b1, N, node_lo, parts, jacc);
+      PDD_CUDA_TRY(ctx, cudaGetLastError());
+    }
     if (diag && (diag->d_path_score || diag->d_path_aux)) {
       const uint64_t cnt = b1 - b0;
       const unsigned g = static_cast<unsigned>(std::min<uint64_t>((cnt + 255) / 256, 8192));

@@ -127,3 +127,43 @@ def test_autograd_vjp(api):
     ref = (wgt[:, None] * J).sum(0).cpu()
     np.testing.assert_allclose(theta.grad.numpy(), ref[:64].numpy(), rtol=1e-10, atol=1e-12)
     np.testing.assert_allclose(phi.grad.numpy(), ref[64:].numpy(), rtol=1e-10, atol=1e-12)
+
+
+def _contributions(sc, xe, L):
+    """Per-path contributions of the Poisson-Fourier Jacobian row: cos(m pi x)
+    cos(n pi y) at the exit point for theta_{8m+n}, s L_j for phi_j."""
+    k = np.arange(8) * np.pi
+    cx, cy = np.cos(xe[..., 0, None] * k), np.cos(xe[..., 1, None] * k)
+    th = (cx[..., :, None] * cy[..., None, :]).reshape(cx.shape[:-1] + (64,))
+    return np.concatenate([th, sc[..., None] * L], -1)
+
+
+def test_jacobian_reduction_in_parts(api):
+    # 40 000 paths per node: each node's records are reduced in four parts
+    # and merged in part order; with a wave of 50 000 paths the nodes also
+    # straddle waves.  Either way a row is the mean of the kernel's own
+    # records' contributions (to 2^-20 of their mean magnitude, the binary32
+    # evaluation) and its standard error theirs.
+    w = W.workload(5)
+    nodes = torch.from_numpy(w["nodes"][::700])
+    kw = dict(seed=w["seed"], dt=1e-3, n_paths=40000)
+    rows = []
+    with api.Context(w["prob"]) as ctx:
+        for wave in (0, 8 * 50000):
+            ctx.set_tuning(0, wave)
+            g = ctx.interface_grad(nodes, dump_paths=True, **kw)
+            aux = g["aux"].cpu().numpy()
+            c = _contributions(g["score"].cpu().numpy(), aux[..., 0:2], aux[..., 2:])
+            J = g["jac"].cpu().numpy()
+            unit = 2.0 ** -20 * np.abs(c).mean(1) + 1e-12
+            ratio = np.abs(J - c.mean(1)) / unit
+            print(f"[parity] Jacobian in parts (wave {wave or 'default'}): "
+                  f"{ratio.max():.3f} of 2^-20 mean |c|")
+            assert ratio.max() <= 1.0, ratio.max()
+            se = c.std(1, ddof=1) / np.sqrt(c.shape[1])
+            np.testing.assert_allclose(g["jac_se"].cpu().numpy(), se, rtol=1e-3, atol=1e-12)
+            rows.append((J, unit))
+        ctx.set_tuning(0, 0)
+    # the same paths either way (records are per path), so the two rows are
+    # within both reductions' bounds of each other
+    assert np.all(np.abs(rows[0][0] - rows[1][0]) <= rows[0][1] + rows[1][1])
