@@ -340,7 +340,7 @@ def run_pdd(args):
         batch = run_batch_once(api, dev, scale=args.batch_scale)
     others = None
     if not args.no_others and world == 1:
-        others = run_other_workloads(api, dev)
+        others = run_other_workloads(api, dev, pf_paths=args.pf_paths)
 
     if rank != 0:
         if world > 1:
@@ -412,7 +412,7 @@ def _timed(stream, fn):
     return e0.elapsed_time(e1), out
 
 
-def run_other_workloads(api, dev) -> dict:
+def run_other_workloads(api, dev, pf_paths=None) -> dict:
     """One timed call (after one warm-up) of each other workload at full size:
     KPP branching (1024 space-time nodes x 1e5 trees), the Poisson-Fourier
     forward solve and its gradient (2048 nodes x 1e5 paths, dt = 1e-3),
@@ -476,7 +476,7 @@ def run_other_workloads(api, dev) -> dict:
     w = W.workload(5)
     with api.Context(w["prob"], dev) as ctx:
         nodes = torch.from_numpy(w["nodes"]).to(dev)
-        kw = dict(seed=w["seed"], dt=w["dt"], n_paths=w["n_paths"])
+        kw = dict(seed=w["seed"], dt=w["dt"], n_paths=pf_paths or w["n_paths"])
         r = ctx.interface_solve(nodes, diag=True, precision="fp32", **kw)
         ms_f, _ = _timed(stream, lambda: ctx.interface_solve(nodes, precision="fp32", **kw))
         gout = torch.ones(len(w["nodes"]), dtype=torch.float64, device=dev)
@@ -485,7 +485,8 @@ def run_other_workloads(api, dev) -> dict:
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = n_sm * 4 * 32 * 2070e6
         out["poisson_fourier_gradient"] = {
-            "workload": w["name"], "forward_ms": ms_f, "gradient_ms": ms_g,
+            "workload": w["name"], "n_paths": kw["n_paths"], "forward_ms": ms_f,
+            "gradient_ms": ms_g,
             "path_steps_per_s_forward": r["path_steps"] / (ms_f / 1e3),
             "path_steps_per_s_gradient": r["path_steps"] / (ms_g / 1e3),
             "issue_roofline_frac_forward_at_2070mhz":
@@ -742,6 +743,9 @@ def main():
                     help="scale of the adaptive batch (1.0: SE* = 1e-4, n_max = 1e6)")
     ap.add_argument("--paths", type=int, default=None,
                     help="paths per node (profiling runs only; the benchmark uses 1e5)")
+    ap.add_argument("--pf-paths", type=int, default=None,
+                    help="paths per node of the Poisson-Fourier forward/gradient workload "
+                         "(profiling runs only; the benchmark uses 1e5)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -130,6 +130,27 @@ __device__ __forceinline__ StepConst<float> make_step_const(double dt, double si
   return k;
 }
 
+// FP64 re-decision of a near tie of the 2-D box bridge test from the same
+// binary32 products d_j d'_j, kept out of line: it almost never runs, and
+// inlined its FP64 code enlarged the 2-D kernels enough to stall them on
+// instruction fetch (the gradient pass 156 -> 121 ms once it moved out; the
+// 3-D kernel measured faster with its three-face form inline, 850 against
+// 857 ms).
+static __device__ __noinline__ bool bridge_box2_tie(float U, float inv_s2dt, float p0, float p1) {
+  const float pr[2] = {p0, p1};
+  double Pd = 0.0;
+  const double s = 2.0 * static_cast<double>(inv_s2dt);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const double aa = s * static_cast<double>(pr[c]);
+    if (aa < 18.0) {
+      const double p = exp(-aa);
+      Pd = Pd + p * (1.0 - Pd);
+    }
+  }
+  return static_cast<double>(U) < Pd;
+}
+
 // Brownian-bridge exit probability over the faces within reach,
 // P = 1 - prod_j (1 - p_j), p_j = exp(-2 d_j d'_j / (sigma^2 dt)), accumulated
 // as P <- P + p_j (1 - P) (no cancellation, so accurate for tiny P).  FP32
@@ -154,17 +175,21 @@ __device__ __forceinline__ int bridge_exit(const StepConst<R> &k, const R *prod,
   bool take = U < P;
   if constexpr (sizeof(R) == 4) {
     if (fabsf(U - P) <= 3.814697265625e-06f * P) {  // near tie: FP64 from the same products
-      double Pd = 0.0;
-      const double s = 2.0 * static_cast<double>(k.inv_s2dt);
+      if constexpr (NC == 2) {
+        take = bridge_box2_tie(U, k.inv_s2dt, prod[0], prod[1]);
+      } else {
+        double Pd = 0.0;
+        const double s = 2.0 * static_cast<double>(k.inv_s2dt);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const double aa = s * static_cast<double>(prod[c]);
-        if (aa < 18.0) {
-          const double p = exp(-aa);
-          Pd = Pd + p * (1.0 - Pd);
+        for (int c = 0; c < NC; ++c) {
+          const double aa = s * static_cast<double>(prod[c]);
+          if (aa < 18.0) {
+            const double p = exp(-aa);
+            Pd = Pd + p * (1.0 - Pd);
+          }
         }
+        take = static_cast<double>(U) < Pd;
       }
-      take = static_cast<double>(U) < Pd;
     }
   }
   return take ? jbest : -1;
