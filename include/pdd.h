@@ -565,8 +565,9 @@ PDD_API pdd_status pdd_autotune_batch(pdd_ctx *ctx, const pdd_problem *problems,
 
 /* Launch-shape and memory knobs of the path kernels (no effect on results,
  * which do not depend on scheduling):
- *   blocks_per_sm    resident 256-thread blocks per SM for the persistent
- *                    path kernels (0 = the occupancy maximum);
+ *   blocks_per_sm    resident blocks per SM for the persistent path kernels
+ *                    (128 threads for binary32 paths, 256 for FP64; 0 = the
+ *                    occupancy maximum);
  *   wave_max_paths   paths per wave of the kernels that store one score per
  *                    path in the context's scratch (Walk on Spheres,
  *                    reflecting faces, branching, multilevel, gradient; 4 or

@@ -33,7 +33,8 @@ pdd_status autotune_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n, const p
     return fail(ctx, PDD_EINVAL, "autotune covers the absorbing-boundary path kernels");
   PDD_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   int max_bps = 0;
-  // occupancy bound of the dominant kernel family (all path kernels are 256 threads)
+  // occupancy bound of the path kernels (7 blocks of 128 threads at most for
+  // binary32 paths, fewer of 256 for FP64)
   PDD_CUDA_TRY(ctx, cudaDeviceGetAttribute(&max_bps, cudaDevAttrMaxBlocksPerMultiprocessor, ctx->device));
   max_bps = std::min(max_bps, 8);
   EventPair ev;

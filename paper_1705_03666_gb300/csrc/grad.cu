@@ -299,11 +299,11 @@ pdd_status interface_grad_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
 
   auto kern = path_kernel<PoissonFourier, Box<2>, float, true>;
   int bps = 0;
-  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlock, 0));
+  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlockOf<float>, 0));
   if (bps < 1) bps = 1;
   if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
   uint64_t grid = static_cast<uint64_t>(bps) * ctx->num_sms;
-  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (wave + kPathBlock - 1) / kPathBlock));
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (wave + kPathBlockOf<float> - 1) / kPathBlockOf<float>));
 
   for (uint64_t b0 = 0; b0 < total; b0 += wave) {
     const uint64_t b1 = std::min(total, b0 + wave);
@@ -313,7 +313,7 @@ pdd_status interface_grad_impl(pdd_ctx *ctx, const double *d_nodes, int64_t n,
     a.steps = (diag && diag->d_path_steps) ? diag->d_path_steps + b0 : nullptr;
     const auto ev = prof_slot(ctx);
     if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
-    kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);
+    kern<<<static_cast<unsigned>(grid), kPathBlockOf<float>, 0, ctx->stream>>>(a);
     PDD_CUDA_TRY(ctx, cudaGetLastError());
     if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
     const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;

@@ -113,15 +113,15 @@ static pdd_status run_paths(pdd_ctx *ctx, const double *d_nodes, int64_t n,
 
   auto kern = path_kernel<Model, Geom, R>;
   int bps = 0;
-  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlock, 0));
+  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlockOf<R>, 0));
   if (bps < 1) bps = 1;
   if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
   uint64_t grid = static_cast<uint64_t>(bps) * ctx->num_sms;
-  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + kPathBlock - 1) / kPathBlock));
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + kPathBlockOf<R> - 1) / kPathBlockOf<R>));
 
   const auto ev = prof_slot(ctx);
   if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
-  kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);
+  kern<<<static_cast<unsigned>(grid), kPathBlockOf<R>, 0, ctx->stream>>>(a);
   PDD_CUDA_TRY(ctx, cudaGetLastError());
   if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
   fix_finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, ctx->stream>>>(

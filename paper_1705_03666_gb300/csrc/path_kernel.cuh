@@ -31,7 +31,14 @@
 
 namespace pdd {
 
-constexpr int kPathBlock = 256;
+// Threads per block of the persistent path kernels, by path precision.  With
+// 128-thread blocks ptxas gives the binary32 kernels ~70 registers and the
+// SM holds 7 blocks (28 warps); with 256-thread blocks it held them to 64
+// registers for 4 blocks (32 warps), and the 3-D solve ran 840 against
+// 836 ms.  The FP64 kernels keep 256-thread blocks (their 2-D two-stage run
+// was 11.4 against 13.0 ms).
+template <typename R>
+constexpr int kPathBlockOf = sizeof(R) == 4 ? 128 : 256;
 
 struct PathArgs {
   const double *nodes;          // [n_nodes][D]
@@ -664,11 +671,11 @@ __device__ __forceinline__ void flush_exits(const PathArgs &a, ExitQueue<Model::
 }
 
 template <class Model, class Geom, typename R, bool kLR = false>
-__global__ void __launch_bounds__(kPathBlock)
+__global__ void __launch_bounds__(kPathBlockOf<R>)
 path_kernel(const __grid_constant__ PathArgs a) {
   constexpr int D = Model::D;
   constexpr int NL = kLR ? kMaxLR : 1;
-  __shared__ PathStage<D, R> stage_all[kPathBlock / 32];
+  __shared__ PathStage<D, R> stage_all[kPathBlockOf<R> / 32];
   PathStage<D, R> &stage = stage_all[threadIdx.x >> 5];
   R L[NL];
   const unsigned lane = threadIdx.x & 31u;

@@ -134,12 +134,12 @@ pdd_status run_static(char *base, int device, cudaStream_t stream, const pdd_pro
 
   auto kern = path_kernel<Model, Geom, R>;
   int bps = 0, num_sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlock, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlockOf<R>, 0) != cudaSuccess ||
       cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     return PDD_ECUDA;
   uint64_t grid = static_cast<uint64_t>(std::max(bps, 1)) * static_cast<uint64_t>(num_sms);
-  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + kPathBlock - 1) / kPathBlock));
-  kern<<<static_cast<unsigned>(grid), kPathBlock, 0, stream>>>(a);
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + kPathBlockOf<R> - 1) / kPathBlockOf<R>));
+  kern<<<static_cast<unsigned>(grid), kPathBlockOf<R>, 0, stream>>>(a);
   fix_finalize_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
       fix, n, d_mean, d_se, d_npaths, nullptr);
   return cudaGetLastError() == cudaSuccess ? PDD_OK : PDD_ECUDA;

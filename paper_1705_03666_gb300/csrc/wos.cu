@@ -66,7 +66,7 @@ __device__ __forceinline__ void wos_project(int jb, R *x) {
 }
 
 template <class Geom, typename R>
-__global__ void __launch_bounds__(kPathBlock) wos_kernel(const __grid_constant__ WosArgs a) {
+__global__ void __launch_bounds__(kPathBlockOf<R>) wos_kernel(const __grid_constant__ WosArgs a) {
   const unsigned lane = threadIdx.x & 31u;
   const R eps = static_cast<R>(a.eps);
   R X[2] = {R(0), R(0)};
@@ -185,11 +185,11 @@ static pdd_status run_wos(pdd_ctx *ctx, const double *d_nodes, int64_t n, const 
   a.mc = ctx->mc;
   auto kern = wos_kernel<Geom, R>;
   int bps = 0;
-  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlock, 0));
+  PDD_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPathBlockOf<R>, 0));
   if (bps < 1) bps = 1;
   if (ctx->path_blocks_per_sm > 0) bps = std::min(bps, ctx->path_blocks_per_sm);
   uint64_t grid = static_cast<uint64_t>(bps) * ctx->num_sms;
-  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (wave + kPathBlock - 1) / kPathBlock));
+  grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (wave + kPathBlockOf<R> - 1) / kPathBlockOf<R>));
   for (uint64_t b0 = 0; b0 < total; b0 += wave) {
     const uint64_t b1 = std::min(total, b0 + wave);
     if (b0 > 0) PDD_CUDA_TRY(ctx, cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), ctx->stream));
@@ -199,7 +199,7 @@ static pdd_status run_wos(pdd_ctx *ctx, const double *d_nodes, int64_t n, const 
     a.exit = (diag && diag->d_path_exit) ? diag->d_path_exit + 2 * b0 : nullptr;
     const auto ev = prof_slot(ctx);
     if (ev.first) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.first, ctx->stream));
-    kern<<<static_cast<unsigned>(grid), kPathBlock, 0, ctx->stream>>>(a);
+    kern<<<static_cast<unsigned>(grid), kPathBlockOf<R>, 0, ctx->stream>>>(a);
     PDD_CUDA_TRY(ctx, cudaGetLastError());
     if (ev.second) PDD_CUDA_TRY(ctx, cudaEventRecord(ev.second, ctx->stream));
     const uint64_t node_lo = b0 / N, node_hi = (b1 - 1) / N;
