@@ -564,8 +564,10 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
      * j with distances y (start) and y' (free end), the Brownian bridge's
      * minimum over the step is m = (y + y' - sqrt((y' - y)^2 - 2 sigma^2 dt
      * ln U')) / 2 with U' uniform; the local time increment is L = max(0,
-     * -m) and the end point is pushed in by L.  U' for axis k is word k of
-     * Philox((n, p, i, 4)); it matters only when 2 y y' / (sigma^2 dt) < 18
+     * -m) and the end point is pushed in by L.  U' for axis k comes from the
+     * tag-4 stream: word k of Philox((n, p, i, 4)) in 3-D, word
+     * 2 (n mod 2) + k of Philox((n / 2, p, i, 4)) in 2-D (one block for two
+     * steps); it matters only when 2 y y' / (sigma^2 dt) < 18
      * (else L = 0 for every U' >= 2^-24).  Along the local time the
      * weights solve dY = phi Y dxi, dZ = psi Y dxi exactly for psi frozen
      * at the end point projected on face j: Z gains psi Y (e^{phi L} - 1) /
@@ -580,13 +582,15 @@ static void simulate_path(const orc_problem *P, const orc_mc *M, uint32_t node,
         double y0 = face_dist(geom, j, X), y1 = face_dist(geom, j, Xn);
         if (2.0 * y0 * y1 / (sig * sig * dt) >= 18.0) continue;
         if (!have_r) {
-          uint32_t cr[4] = {(uint32_t)n, path, node, 4u};
+          uint32_t blk = dim == 2 ? (uint32_t)(n / 2) : (uint32_t)n;
+          uint32_t cr[4] = {blk, path, node, 4u};
           orc_philox4x32_10(cr, key, R);
           have_r = 1;
         }
         int k = j >> 1;
+        int word = dim == 2 ? 2 * (int)(n % 2) + k : k;
         double dy = y1 - y0;
-        double mn = 0.5 * (y0 + y1 - sqrt(dy * dy - 2.0 * sig * sig * dt * log(unif(R[k]))));
+        double mn = 0.5 * (y0 + y1 - sqrt(dy * dy - 2.0 * sig * sig * dt * log(unif(R[word]))));
         double L = mn < 0.0 ? -mn : 0.0;
         if (L > 0.0) {
           if (j & 1) { Xn[k] -= L; if (Xn[k] > 1.0) Xn[k] = 1.0; }

@@ -9,9 +9,11 @@
 // half-space reflection: with distances y (start) and y' (free end), the
 // Brownian bridge's minimum is m = (y + y' - sqrt((y' - y)^2 - 2 sigma^2 dt
 // ln U')) / 2, the local time L = max(0, -m), and the end point moves in by
-// L.  U' for axis k is word k of Philox((n, p, i, 4)), drawn only when a
-// reflecting face is within reach (2 y y' / (sigma^2 dt) < 18; beyond, L = 0
-// for every U' >= 2^-24).  Along the local time the weights are integrated
+// L.  U' for axis k comes from the tag-4 stream Philox((b, p, i, 4)): in 3-D
+// word k of block b = n; in 2-D word 2 (n mod 2) + k of block b = n / 2, so
+// one block serves two steps.  It matters only when a reflecting face is
+// within reach (2 y y' / (sigma^2 dt) < 18; beyond, L = 0 for every
+// U' >= 2^-24).  Along the local time the weights are integrated
 // exactly with psi frozen at the end point's projection: Z += psi Y (e^{phi
 // L} - 1) / phi, Y *= e^{phi L}; then the time part as in the path kernel
 // (left point).  Absorbing faces keep the hard-exit and bridge tests.
@@ -137,12 +139,13 @@ __device__ __forceinline__ double reflect_bound(const ReflectConst<double> &k, d
 
 // One step of a reflecting path from X (Z, sphil and n its running sums):
 // the Euler-Maruyama move with normals xi, Lepingle's reflection on the
-// reflecting faces within reach, and the absorbing exit tests with the bridge
-// uniform word wu.  Returns true when the path left through an absorbing
+// reflecting faces within reach (axis k's uniform word: word wo + k of the
+// tag-4 block rw), and the absorbing exit tests with the bridge uniform word
+// wu.  Returns true when the path left through an absorbing
 // face (xe its exit point, Zn its source sum); otherwise X, Z advance.
 template <class Model, typename R>
 __device__ __forceinline__ bool reflect_step(const ReflectArgs &a, const ReflectConst<R> &k,
-                                             const PhiloxPath &pp4, R *X, R &Z, R &sphil,
+                                             const uint4 &rw, int wo, R *X, R &Z, R &sphil,
                                              int32_t n, const R *xi, uint32_t wu, R *xe, R &Zn) {
   constexpr int D = Model::D;
   using G = Box<D>;
@@ -161,14 +164,14 @@ __device__ __forceinline__ bool reflect_step(const ReflectArgs &a, const Reflect
   // most warp-steps); only an actual reflection (L > 0) branches.
   R zr = R(0), yr = Y;
   bool have_y = kYStep;
-  const uint4 rw = philox10_path(static_cast<uint32_t>(n), pp4, a.rk);  // = Philox((n, p, i, 4))
 #pragma unroll
   for (int j = 0; j < 2 * D; ++j) {
     if (!((a.mask >> j) & 1)) continue;
     const R y0 = G::template face_dist<R>(j, X), y1 = G::template face_dist<R>(j, Xn);
     const bool reach = R(2) * y0 * y1 * k.inv_s2dt < R(18);
     const int q = j >> 1;
-    const uint32_t wk = q == 0 ? rw.x : q == 1 ? rw.y : rw.z;
+    const int w = wo + q;
+    const uint32_t wk = w == 0 ? rw.x : w == 1 ? rw.y : w == 2 ? rw.z : rw.w;
     const R dy = y1 - y0;
     const R mn = R(0.5) * (y0 + y1 - r_sqrt(dy * dy - R(2) * k.s2dt * r_log<R>(unif<R>(wk))));
     const R L = (reach && mn < R(0)) ? -mn : R(0);
@@ -317,9 +320,15 @@ __global__ void __launch_bounds__(kPathBlockOf<R>) reflect_kernel(const __grid_c
     unit_randoms<D, R>(n, pp, a.rk, z, u);
     bool out = false, capped = false;
     R xe[3] = {R(0), R(0), R(0)}, Zn = R(0);
+    uint4 rw = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
-      out = reflect_step<Model, R>(a, k, pp4, X, Z, sphil, n, z, u[0], xe, Zn);
+      // the tag-4 block: one per two steps in 2-D (n is 4q + j here), one per
+      // step in 3-D
+      if (D == 3 || (j & 1) == 0)
+        rw = philox10_path(static_cast<uint32_t>(D == 3 ? n : n >> 1), pp4, a.rk);
+      out = reflect_step<Model, R>(a, k, rw, D == 2 ? 2 * (j & 1) : 0, X, Z, sphil, n, z, u[0],
+                                   xe, Zn);
       ++n;
       if (out) break;
       if (n >= a.max_steps) {
