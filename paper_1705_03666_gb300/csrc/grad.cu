@@ -27,23 +27,6 @@ constexpr int kJacLanes = 8;    // threads per path: thread m owns cos(m pi x)
 constexpr int kJacBlock = 256;  // 32 path groups x 8
 constexpr int kJacGroups = kJacBlock / kJacLanes;
 
-// Per node (one block): for each path record, thread m of a path group forms
-// cos(m pi x) and, by the Chebyshev recurrence from cos(pi y), cos(n pi y) for
-// n = 0..7, and accumulates its eight theta components (8m + n) and the two
-// phi components m and 8 + m (s * L_j) with their squares.  A group takes
-// its records four at a time (records grp + 32 r of the block, r = 0..3):
-// thread m forms cos(pi y) of record m mod 4 once and the group shares the
-// four values by shuffles; the four contributions of each component are
-// summed in binary32 (error <= 3 u of their absolute sum) and the block sum
-// goes into a two-float sum on the FP32 pipe (~48-bit; FP64 is a 1/64-rate
-// pipe here), so a row carries at most 3 u of its mean absolute contribution
-// beyond the contributions' own evaluation.  The squares, which feed only the
-// standard error, take the same four-record blocks by FMA.  A node's records
-// of the wave are split into `parts` contiguous ranges, one block each (so
-// that a wave of a few hundred nodes still fills the GPU); a block combines
-// its 32 groups in FP64 in a fixed order and writes the part's two sums per
-// component, and jac_merge_kernel adds the parts in order and merges them
-// into the node's running (count, mean, M2) per component (Chan).
 // Merge a batch of nb records with sums S1, S2 of one component into the
 // node's running (count, mean, M2) (Chan).
 __device__ __forceinline__ void jac_chan_merge(NodeAcc *jacc, uint64_t node, int comp, double S1,
@@ -59,6 +42,26 @@ __device__ __forceinline__ void jac_chan_merge(NodeAcc *jacc, uint64_t node, int
   jacc[node * kJacW + comp] = A;
 }
 
+// Per part of a node's records (one block): for each path record, thread m
+// of a path group forms cos(m pi x) and, by the Chebyshev recurrence from
+// cos(pi y), cos(n pi y) for n = 0..7, and accumulates its eight theta components (8m + n) and the two
+// phi components m and 8 + m (s * L_j) with their squares.  A group takes
+// its records four at a time (records grp + 32 r of the block, r = 0..3):
+// thread m forms cos(pi y) of record m mod 4 once and the group shares the
+// four values by shuffles; the four contributions of each component are
+// summed in binary32 (error <= 3 u of their absolute sum) and the block sum
+// goes into a two-float sum on the FP32 pipe (~48-bit; FP64 is a 1/64-rate
+// pipe here), so a row carries at most 3 u of its mean absolute contribution
+// beyond the contributions' own evaluation.  The squares, which feed only the
+// standard error, take the same four-record blocks by FMA.  A node's records
+// of the wave are split into `parts` contiguous ranges, one block each (so
+// that a wave of a few hundred nodes still fills the GPU); a block combines
+// its 32 groups in FP64 in a fixed order and writes the part's two sums per
+// component, and jac_merge_kernel adds the parts in order and merges them
+// into the node's running (count, mean, M2) per component (Chan); with one
+// part the block merges its sums itself.  Launch
+// bounds of three blocks per SM (80 registers): at 105 registers and two
+// blocks the kernel was 24 % slower.
 __global__ void __launch_bounds__(kJacBlock, 3)
 jac_reduce_kernel(const GradRec *__restrict__ rec, uint64_t begin, uint64_t end,
                   uint64_t n_paths, uint64_t node_lo, int parts, double2 *part_sums,
