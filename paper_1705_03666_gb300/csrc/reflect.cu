@@ -46,6 +46,10 @@ struct ReflectArgs {
   double *exit;                  // exit point per path [end - begin][D] or null
   RoundKeys rk;
   double dt, sdt, s2dt, cdt, phi;  // dt, sigma sqrt(dt), sigma^2 dt, c dt, Robin phi
+  // the binary32 step constants, rounded on the host (dt, sdt, s2dt, cdt, phi,
+  // 1 / s2dt, b2, boff of ReflectConst): formed in the kernel from the FP64
+  // fields, they were re-formed inside the step loop on the FP64 pipe
+  float kf[8];
   int32_t mask;                    // bit j: face j reflects
   int32_t max_steps, bridge;
   ModelConst mc;
@@ -246,15 +250,25 @@ __global__ void __launch_bounds__(kPathBlockOf<R>) reflect_kernel(const __grid_c
   using G = Box<D>;
   const unsigned lane = threadIdx.x & 31u;
   ReflectConst<R> k;
-  k.dt = static_cast<R>(a.dt);
-  k.sdt = static_cast<R>(a.sdt);
-  k.s2dt = static_cast<R>(a.s2dt);
-  k.cdt = static_cast<R>(a.cdt);
-  k.phi = static_cast<R>(a.phi);
-  k.inv_s2dt = R(1) / k.s2dt;
-  k.b2 = static_cast<R>(-2.0 * 1.4426950408889634 / a.s2dt);
-  k.boff = a.bridge ? static_cast<R>((D == 2 ? 2.0 : 2.584962500721156) + 2.44140625e-4)
-                    : static_cast<R>(-INFINITY);
+  if constexpr (sizeof(R) == 4) {
+    k.dt = a.kf[0];
+    k.sdt = a.kf[1];
+    k.s2dt = a.kf[2];
+    k.cdt = a.kf[3];
+    k.phi = a.kf[4];
+    k.inv_s2dt = a.kf[5];
+    k.b2 = a.kf[6];
+    k.boff = a.kf[7];
+  } else {
+    k.dt = a.dt;
+    k.sdt = a.sdt;
+    k.s2dt = a.s2dt;
+    k.cdt = a.cdt;
+    k.phi = a.phi;
+    k.inv_s2dt = 1.0 / k.s2dt;
+    k.b2 = -2.0 * 1.4426950408889634 / a.s2dt;
+    k.boff = a.bridge ? (D == 2 ? 2.0 : 2.584962500721156) + 2.44140625e-4 : -INFINITY;
+  }
   R X[3] = {R(0), R(0), R(0)};
   R Z = R(0), sphil = R(0);  // source sum; phi * (local time so far)
   PhiloxPath pp{0, 0, 0}, pp4{0, 0, 4u};
@@ -426,6 +440,16 @@ static pdd_status run_reflect(pdd_ctx *ctx, const double *d_nodes, int64_t n,
   a.phi = ctx->params[1];
   a.max_steps = static_cast<int32_t>(mc->max_steps);
   a.bridge = mc->bridge ? 1 : 0;
+  {
+    const float s2dt_f = static_cast<float>(a.s2dt);
+    const float kf[8] = {static_cast<float>(a.dt), static_cast<float>(a.sdt), s2dt_f,
+                         static_cast<float>(a.cdt), static_cast<float>(a.phi), 1.0f / s2dt_f,
+                         static_cast<float>(-2.0 * 1.4426950408889634 / a.s2dt),
+                         a.bridge ? static_cast<float>((Model::D == 2 ? 2.0 : 2.584962500721156) +
+                                                       2.44140625e-4)
+                                  : -INFINITY};
+    for (int i = 0; i < 8; ++i) a.kf[i] = kf[i];
+  }
   a.mc = ctx->mc;
   a.flags = flags;
   auto kern = reflect_kernel<Model, R>;
